@@ -1,0 +1,187 @@
+/*
+ * gdwd.h -- C-ABI of libgdwd, a GB300 (sm_103a) solver for the generalized
+ * Distance Weighted Discrimination model
+ *
+ *     min  sum_i theta_q(r_i) + C <e, xi>
+ *     s.t. Z^T w + beta y + xi - r = 0,  ||w|| <= 1,  xi >= 0,
+ *
+ * theta_q(t) = t^-q for t > 0 (generalized DWD, Sec. 2, eq-primal of arXiv
+ * 2305.12019), by the inexact sGS-ADMM of Algorithm 1 (Sec. 3) on the scaled
+ * model eq-gen-scale (Sec. 4.2), with the linear system eq-linsys solved through
+ * the n x n Gram matrix and Sherman-Morrison-Woodbury (SMW2, Sec. 3.3.2), the
+ * r-subproblem eq-varphi by Newton's method (Sec. 3.2), the KKT residuals of
+ * Sec. 4.3 and the sigma rule of Sec. 4.4.
+ *
+ * Conventions for every entry point:
+ *   - it returns a gdwd_status and never aborts the process;
+ *   - invalid arguments give GDWD_EINVAL and leave outputs untouched;
+ *   - "device" pointers are CUDA global-memory pointers of the current device,
+ *     "host" pointers are ordinary (pageable or pinned) host memory;
+ *   - the caller keeps ownership of every buffer it passes; the library copies
+ *     what it needs and owns only what it allocates inside a handle;
+ *   - a handle is not thread-safe: one host thread at a time per handle;
+ *   - all work is issued on the stream given in gdwd_options (0 = legacy default
+ *     stream) and every call that returns results synchronizes that stream.
+ */
+#ifndef GDWD_H
+#define GDWD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GDWD_OK = 0,
+  GDWD_EINVAL = 1,     /* bad argument (sizes, labels, q, C, non-finite data)          */
+  GDWD_ENOMEM = 2,     /* device allocation failed                                     */
+  GDWD_ENOTPD = 3,     /* Cholesky of I + Z~^T Z~ / mu met a pivot <= 0                 */
+  GDWD_EMAXITER = 4,   /* max_iter reached before kkt <= tol; results are the last iterate */
+  GDWD_ENUMERIC = 5,   /* NaN/Inf appeared in the iteration                             */
+  GDWD_ETIMEOUT = 6,   /* a bounded device-side wait ran out; the kernel returned       */
+  GDWD_ECUDA = 7,      /* a CUDA runtime call failed (message in gdwd_last_error)       */
+  GDWD_EUNSUPPORTED = 8 /* valid request this build does not implement                  */
+} gdwd_status;
+
+/* Element types, for the caller's Z and for the copy the handle stores. */
+typedef enum {
+  GDWD_F64 = 0,
+  GDWD_F32 = 1,
+  GDWD_BF16 = 2,
+  GDWD_F16 = 3,
+  GDWD_E4M3 = 4
+} gdwd_dtype;
+
+/* Solver options.  Fill with gdwd_default_options() and override fields. */
+typedef struct {
+  double mu;          /* D^2 = mu I in the split u = w (Sec. 3, eq-gen; D is "a positive
+                         multiple of I").  Default 1.                                   */
+  double tau;         /* dual step length of Step 3, in (0, (1+sqrt5)/2).  Default 1.618 */
+  double tol;         /* stop when kkt = max(eta_P, eta_D, eta_C, eta_gap) <= tol
+                         (Sec. 4.3 residuals, all relative).  Default 1e-6.             */
+  double sigma0;      /* initial sigma; <= 0 selects min(10C, n)^q (Sec. 4.4).          */
+  double timeout_s;   /* limit of every device-side wait (grid barrier, copies). Default 2 */
+  int32_t max_iter;   /* iteration limit.  Default 20000.                              */
+  int32_t store;      /* gdwd_dtype of the copy of Z kept on the device: GDWD_F64 or
+                         GDWD_F32 (BF16/F16/E4M3 give GDWD_EUNSUPPORTED in this build).
+                         Default GDWD_F32.                                              */
+  int32_t grid;       /* CTAs of the persistent iteration kernel; 0 = one per SM.      */
+  int32_t block_rows; /* rows of Z per slab of the device layout; 0 = automatic.        */
+  void* stream;       /* cudaStream_t for all work of the handle; NULL = default stream */
+  int64_t reserved[8];
+} gdwd_options;
+
+/* Outcome of one solve (one value of C). */
+typedef struct {
+  double beta;        /* intercept of the hyperplane w^T x + beta = 0                  */
+  double primal_obj;  /* sum r_i^-q + C <e, xi> at the final iterate (Sec. 4.3)         */
+  double dual_obj;    /* kappa sum alpha_i^(q/(q+1)) - ||Z alpha|| (Sec. 4.3)           */
+  double kkt;         /* max of all relative residuals below                            */
+  double eta_p;       /* max(eta_P1, eta_P2, eta_P3)                                    */
+  double eta_d;       /* max(eta_D1, eta_D2, eta_D3), eta_D3 = ||Z~ alpha + D rho||/(1+C) */
+  double eta_c;       /* max(eta_C1, eta_C2, eta_C3)                                    */
+  double eta_gap;     /* |primal - dual| / (1 + |primal| + |dual|)                      */
+  double sigma;       /* final sigma                                                    */
+  double zscale;      /* Z_scale = sqrt(||Z||_F) (Sec. 4.2)                              */
+  double t_setup_ms;  /* device time of gdwd_create's work (ingest, Gram, factor)       */
+  double t_solve_ms;  /* device time of the iterations of this solve                   */
+  int32_t iters;      /* ADMM iterations performed                                      */
+  int32_t status;     /* gdwd_status of this solve                                      */
+  int64_t reserved[4];
+} gdwd_result;
+
+typedef struct gdwd_handle gdwd_handle;
+
+/* Fills *o with the defaults listed above.  EINVAL if o is NULL. */
+gdwd_status gdwd_default_options(gdwd_options* o);
+
+/*
+ * Creates a solver for one data set and does its set-up on the device:
+ * copy/convert Z into the handle's slab layout, Z_scale = sqrt(||Z||_F) and the
+ * scaled data Z~ = Z / Z_scale (Sec. 4.2), the Gram matrix K = Z~^T Z~ and the
+ * SMW2 set-up of Sec. 3.3.2: G = I_n + K / mu = L L^T (Cholesky, FP64), its
+ * inverse, p = G^{-1} y and s = y^T p.  None of this depends on sigma or C, so
+ * one handle serves every solve and every C.
+ *
+ *   Z          d x n, column-major with leading dimension ldz >= d; column i is
+ *              y_i x_i (Z = X diag(y), eq-r).  Element type zdt (GDWD_F64 or
+ *              GDWD_F32).  Host memory if z_on_device == 0, else device memory.
+ *   d, n       feature dimension and sample count; d >= 1, n >= 2.
+ *   y          n labels in {-1, +1}, host memory; both classes must occur.
+ *   q          exponent of theta_q, q > 0 (eq-primal).
+ *   C          penalty, C > 0 (eq-primal); the default C of gdwd_solve.
+ *   o          options (NULL = defaults).
+ *   out        receives the handle; set to NULL on failure.
+ * Errors: EINVAL (sizes, labels, q, C, non-finite Z), ENOMEM, ENOTPD, ECUDA.
+ */
+gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_t n, int64_t ldz, int32_t z_on_device,
+                        const double* y, double q, double C, const gdwd_options* o, gdwd_handle** out);
+
+/*
+ * Runs Algorithm 1 to kkt <= tol (or max_iter) for each of the nC penalties in
+ * Cs (NULL or nC == 0: the C given to gdwd_create, one solve).
+ *
+ *   w          d x nC output, column j = the hyperplane normal for Cs[j] in the
+ *              original (unscaled) units, w = w~ / Z_scale (Sec. 4.2).  Host
+ *              memory if w_on_device == 0, else device memory.  May be NULL.
+ *   alpha      n x nC output multipliers (host memory), or NULL.
+ *   res        nC results, host memory; must not be NULL.
+ * Returns the worst status over the nC solves (GDWD_OK if all converged).
+ */
+gdwd_status gdwd_solve(gdwd_handle* h, const double* Cs, int32_t nC, double* w, int32_t w_on_device,
+                       double* alpha, gdwd_result* res);
+
+/* Frees a handle and all device memory it owns.  NULL is a no-op. */
+gdwd_status gdwd_free(gdwd_handle* h);
+
+/* Message of the last error of h, or of the calling thread when h is NULL. */
+const char* gdwd_last_error(const gdwd_handle* h);
+
+/*
+ * Element-wise r-subproblem of Step 1b (eq-1c / eq-varphi, Sec. 3.2): for each i,
+ * out_i = argmin_{s > 0} (omega_i / q) s^-q + sigma/2 (s - a_i)^2, the unique
+ * positive root of s^(q+1) (s - a_i) = omega_i / sigma, by safeguarded Newton
+ * warm-started at r0_i.  All arrays are device memory of length n; omega may be
+ * NULL (omega_i = q, the unweighted model) and r0 may be NULL (cold start).
+ * stream: cudaStream_t or NULL.  Errors: EINVAL (n < 0, q <= 0, sigma <= 0), ECUDA.
+ */
+gdwd_status gdwd_prox(const double* a, const double* r0, const double* omega, double sigma, double q,
+                      int64_t n, double* out, void* stream);
+
+/*
+ * Products with the handle's stored, scaled data Z~ = Z / Z_scale, by the same
+ * streaming kernels the iteration uses: trans != 0 gives out = Z~^T x (x: d,
+ * out: n), trans == 0 gives out = Z~ x (x: n, out: d).  x and out are device
+ * memory (FP64).  Errors: EINVAL, ECUDA.
+ */
+gdwd_status gdwd_apply(gdwd_handle* h, int32_t trans, const double* x, double* out);
+
+/*
+ * Copies the FP64 Gram matrix G = I + Z~^T Z~ / mu built by gdwd_create (n x n,
+ * row-major, symmetric) to G_out (host memory, n*n doubles).  Errors: EINVAL, ECUDA.
+ */
+gdwd_status gdwd_gram(gdwd_handle* h, double* G_out);
+
+/* Sizes and layout chosen by gdwd_create (for diagnostics and benchmarks). */
+typedef struct {
+  int64_t d, n;
+  int32_t store;         /* gdwd_dtype of the stored Z                       */
+  int32_t block_rows;    /* rows per slab                                    */
+  int32_t slabs;         /* number of slabs                                  */
+  int32_t grid;          /* CTAs of the persistent iteration kernel          */
+  int64_t z_bytes;       /* bytes of the stored Z (one pass reads them once) */
+  int64_t device_bytes;  /* all device memory owned by the handle            */
+  double zscale;         /* Z_scale                                          */
+  double t_setup_ms;     /* device time of the set-up                        */
+  int64_t reserved[4];
+} gdwd_info;
+
+gdwd_status gdwd_get_info(const gdwd_handle* h, gdwd_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GDWD_H */

@@ -1,0 +1,516 @@
+// C-ABI of libgdwd (include/gdwd.h): argument checks, handle memory, set-up
+// and solve orchestration on the caller's stream.  No computation of the
+// method happens on the host: every step runs in the kernels of setup.cu and
+// iterate.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "solver.cuh"
+
+namespace gdwd {
+// ------------------------------------------------------------------ small kernels
+__global__ void fill_kernel(double* p, int64_t n, double v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+// w_j = (g_j + rho_j / (sigma_prev sqrt(mu))) / Z_scale: the Step-1c w of the last
+// iteration in original units (Sec. 4.2).
+__global__ void finish_w_kernel(const double* g, const double* rho, const Ctrl* ctrl, double sqmu, double zscale,
+                                int64_t d, double* w) {
+  const double gs = 1.0 / (ctrl->sigma_prev * sqmu);
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d; j += (int64_t)gridDim.x * blockDim.x)
+    w[j] = (g[j] + rho[j] * gs) / zscale;
+}
+}  // namespace gdwd
+
+using namespace gdwd;
+
+struct gdwd_handle {
+  int device = 0;
+  int sms = 0;
+  int smem_optin = 0;
+  cudaStream_t stream = nullptr;
+  gdwd_options opt{};
+  int64_t d = 0, n = 0;
+  int store = GDWD_F32;
+  double q = 1.0, C = 1.0;
+  Layout L{};
+  int grid = 0;
+  int ldP = 0;
+  double zscale = 0.0;
+  double s = 0.0;
+  double t_setup_ms = 0.0;
+  size_t bytes = 0;
+  std::vector<void*> allocs;
+  // device arrays
+  void* Z = nullptr;
+  double *sc = nullptr, *y = nullptr, *e = nullptr, *omega = nullptr, *wt = nullptr, *p = nullptr, *G = nullptr;
+  float2 *P = nullptr, *pdf = nullptr;
+  double *r = nullptr, *xi = nullptr, *alpha = nullptr, *b = nullptr;
+  float2 *rhsA = nullptr, *rhsB = nullptr;
+  void *cq = nullptr, *aq = nullptr, *partial = nullptr;
+  double *u = nullptr, *rho = nullptr, *g = nullptr, *scal = nullptr, *wtmp = nullptr;
+  double* dscalars = nullptr;   // [0] sumsq [1] zscale [2] s
+  unsigned* bar = nullptr;
+  int* err = nullptr;
+  Ctrl* ctrl = nullptr;
+  std::string last_error;
+};
+
+static thread_local std::string g_thread_error;
+
+static gdwd_status fail(gdwd_handle* h, gdwd_status st, const std::string& msg) {
+  if (h) h->last_error = msg;
+  g_thread_error = msg;
+  return st;
+}
+
+static gdwd_status cuda_fail(gdwd_handle* h, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  return fail(h, e == cudaErrorMemoryAllocation ? GDWD_ENOMEM : GDWD_ECUDA, m);
+}
+
+#define CK(call, where)                                  \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, where); \
+  } while (0)
+
+template <typename T>
+static cudaError_t halloc(gdwd_handle* h, T** p, size_t count) {
+  void* q = nullptr;
+  const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess) return e;
+  h->allocs.push_back(q);
+  h->bytes += bytes;
+  *p = (T*)q;
+  return cudaMemsetAsync(q, 0, bytes, h->stream);
+}
+
+static void release(gdwd_handle* h) {
+  for (void* p : h->allocs) cudaFree(p);
+  h->allocs.clear();
+}
+
+extern "C" gdwd_status gdwd_default_options(gdwd_options* o) {
+  if (!o) return fail(nullptr, GDWD_EINVAL, "gdwd_default_options: NULL");
+  std::memset(o, 0, sizeof(*o));
+  o->mu = 1.0;
+  o->tau = 1.618;
+  o->tol = 1e-6;
+  o->sigma0 = 0.0;
+  o->timeout_s = 2.0;
+  o->max_iter = 20000;
+  o->store = GDWD_F32;
+  o->grid = 0;
+  o->block_rows = 0;
+  o->stream = nullptr;
+  return GDWD_OK;
+}
+
+static int esize_of(int dt) { return dt == GDWD_F64 ? 8 : dt == GDWD_F32 ? 4 : dt == GDWD_E4M3 ? 1 : 2; }
+
+// Chooses slab height, slab count, chunk width and grid (see Layout).
+static void plan_layout(gdwd_handle* h) {
+  const int es = esize_of(h->store);
+  const int vec = 16 / es;
+  const int gp = h->opt.grid > 0 ? std::min(h->opt.grid, h->sms) : h->sms;
+  const int64_t d = h->d;
+  int TB;
+  if (h->opt.block_rows > 0) {
+    TB = (h->opt.block_rows + vec - 1) / vec * vec;
+  } else {
+    const int64_t tbmax = 256LL * vec;
+    const int64_t k = std::max<int64_t>(1, (d + gp * tbmax - 1) / (gp * tbmax));
+    int64_t t = (d + k * gp - 1) / (k * gp);
+    t = (t + vec - 1) / vec * vec;
+    TB = (int)std::max<int64_t>(t, 8LL * vec);
+  }
+  TB = std::min(TB, 256 * vec);
+  const int NB = (int)((d + TB - 1) / TB);
+  int cw = 32;
+  while (cw > 8 && (int64_t)cw * TB * es > 32768) cw >>= 1;
+  h->L.d = d;
+  h->L.n = h->n;
+  h->L.TB = TB;
+  h->L.NB = NB;
+  h->L.CW = cw;
+  h->L.esize = es;
+  h->grid = (int)std::min<int64_t>(gp, std::max<int64_t>(NB, (h->n + kWarps - 1) / kWarps));
+  h->grid = std::max(h->grid, 1);
+}
+
+extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_t n, int64_t ldz, int32_t z_on_device,
+                                   const double* y, double q, double C, const gdwd_options* o, gdwd_handle** out) {
+  if (!out) return fail(nullptr, GDWD_EINVAL, "gdwd_create: out is NULL");
+  *out = nullptr;
+  if (!Z || !y) return fail(nullptr, GDWD_EINVAL, "gdwd_create: Z or y is NULL");
+  if (d < 1 || n < 2 || ldz < d) return fail(nullptr, GDWD_EINVAL, "gdwd_create: need d >= 1, n >= 2, ldz >= d");
+  if (zdt != GDWD_F64 && zdt != GDWD_F32) return fail(nullptr, GDWD_EINVAL, "gdwd_create: Z must be F64 or F32");
+  if (!(q > 0.0) || !std::isfinite(q)) return fail(nullptr, GDWD_EINVAL, "gdwd_create: q must be > 0");
+  if (!(C > 0.0) || !std::isfinite(C)) return fail(nullptr, GDWD_EINVAL, "gdwd_create: C must be > 0");
+  int npos = 0, nneg = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (y[i] == 1.0) ++npos;
+    else if (y[i] == -1.0) ++nneg;
+    else return fail(nullptr, GDWD_EINVAL, "gdwd_create: labels must be -1 or +1");
+  }
+  if (!npos || !nneg) return fail(nullptr, GDWD_EINVAL, "gdwd_create: both classes must occur");
+  gdwd_options opt;
+  gdwd_default_options(&opt);
+  if (o) opt = *o;
+  if (!(opt.mu > 0.0) || !(opt.tau > 0.0 && opt.tau < 1.6180339887498949) || !(opt.tol > 0.0) || opt.max_iter < 1 ||
+      !(opt.timeout_s > 0.0))
+    return fail(nullptr, GDWD_EINVAL, "gdwd_create: bad options (mu > 0, 0 < tau < golden ratio, tol > 0, max_iter >= 1)");
+  if (opt.store != GDWD_F64 && opt.store != GDWD_F32) {
+    if (opt.store == GDWD_BF16 || opt.store == GDWD_F16 || opt.store == GDWD_E4M3)
+      return fail(nullptr, GDWD_EUNSUPPORTED, "gdwd_create: BF16/F16/E4M3 storage is not available in this build");
+    return fail(nullptr, GDWD_EINVAL, "gdwd_create: bad store dtype");
+  }
+
+  gdwd_handle* h = new gdwd_handle();
+  h->opt = opt;
+  h->stream = (cudaStream_t)opt.stream;
+  h->d = d;
+  h->n = n;
+  h->store = opt.store;
+  h->q = q;
+  h->C = C;
+  gdwd_status st = GDWD_OK;
+  auto bail = [&](gdwd_status s2) {
+    release(h);
+    delete h;
+    return s2;
+  };
+  {
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) return bail(cuda_fail(nullptr, e, "cudaGetDevice"));
+    cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
+    cudaDeviceGetAttribute(&h->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
+    if (!coop) return bail(fail(nullptr, GDWD_ECUDA, "device does not support cooperative launch"));
+  }
+  plan_layout(h);
+  st = [&]() -> gdwd_status {
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0), "cudaEventCreate");
+    CK(cudaEventCreate(&e1), "cudaEventCreate");
+    CK(cudaEventRecord(e0, h->stream), "cudaEventRecord");
+    const int64_t dpad = (int64_t)h->L.NB * h->L.TB;
+    const int es = h->L.esize;
+    const int zes = esize_of(zdt);
+    // persistent arrays
+    void* zbuf = nullptr;
+    CK(cudaMalloc(&zbuf, (size_t)dpad * n * es), "cudaMalloc(Z)");
+    h->allocs.push_back(zbuf);
+    h->bytes += (size_t)dpad * n * es;
+    h->Z = zbuf;
+    h->L.Z = zbuf;
+    h->ldP = (int)((n + 1) / 2 * 2);
+    CK(halloc(h, &h->sc, n), "alloc");
+    CK(halloc(h, &h->y, n), "alloc");
+    CK(halloc(h, &h->e, n), "alloc");
+    CK(halloc(h, &h->omega, n), "alloc");
+    CK(halloc(h, &h->wt, n), "alloc");
+    CK(halloc(h, &h->p, n), "alloc");
+    CK(halloc(h, &h->G, (size_t)n * n), "alloc(G)");
+    CK(halloc(h, &h->P, (size_t)n * h->ldP), "alloc(P)");
+    CK(halloc(h, &h->pdf, n), "alloc");
+    CK(halloc(h, &h->r, n), "alloc");
+    CK(halloc(h, &h->xi, n), "alloc");
+    CK(halloc(h, &h->alpha, n), "alloc");
+    CK(halloc(h, &h->b, n), "alloc");
+    CK(halloc(h, &h->rhsA, n), "alloc");
+    CK(halloc(h, &h->rhsB, n), "alloc");
+    const size_t ct = h->store == GDWD_F64 ? 8 : 4;
+    CK(halloc(h, (uint8_t**)&h->cq, n * ct), "alloc");
+    CK(halloc(h, (uint8_t**)&h->aq, n * ct), "alloc");
+    CK(halloc(h, (uint8_t**)&h->partial, (size_t)n * h->L.NB * ct), "alloc");
+    CK(halloc(h, &h->u, dpad), "alloc");
+    CK(halloc(h, &h->rho, dpad), "alloc");
+    CK(halloc(h, &h->g, dpad), "alloc");
+    CK(halloc(h, &h->wtmp, dpad), "alloc");
+    CK(halloc(h, &h->scal, (size_t)h->sms * S_COUNT), "alloc");
+    CK(halloc(h, &h->dscalars, 8), "alloc");
+    CK(halloc(h, &h->bar, 4), "alloc");
+    CK(halloc(h, &h->err, 4), "alloc");
+    CK(halloc(h, (uint8_t**)&h->ctrl, sizeof(Ctrl)), "alloc");
+    // labels and unit weights (e = 1, wt = 1, omega = q)
+    CK(cudaMemcpyAsync(h->y, y, n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "copy y");
+    const int fb = (int)std::min<int64_t>((n + 255) / 256, 1024);
+    fill_kernel<<<fb, 256, 0, h->stream>>>(h->e, n, 1.0);
+    fill_kernel<<<fb, 256, 0, h->stream>>>(h->wt, n, 1.0);
+    fill_kernel<<<fb, 256, 0, h->stream>>>(h->omega, n, q);
+    // ingest
+    const void* zsrc = Z;
+    void* staging = nullptr;
+    int64_t ld = ldz;
+    if (!z_on_device) {
+      CK(cudaMalloc(&staging, (size_t)d * n * zes), "cudaMalloc(staging)");
+      cudaError_t ec = cudaMemcpy2DAsync(staging, (size_t)d * zes, Z, (size_t)ldz * zes, (size_t)d * zes, (size_t)n,
+                                         cudaMemcpyHostToDevice, h->stream);
+      if (ec != cudaSuccess) {
+        cudaFree(staging);
+        return cuda_fail(h, ec, "copy Z");
+      }
+      zsrc = staging;
+      ld = d;
+    }
+    const int nparts = 1024;
+    double* part = nullptr;
+    int* nonfinite = h->err;
+    CK(cudaMalloc(&part, nparts * sizeof(double)), "cudaMalloc");
+    cudaError_t ei = run_ingest(zsrc, zdt, ld, h->L, h->Z, h->store, part, nparts, h->dscalars, nonfinite, h->sc,
+                                h->dscalars + 1, h->stream);
+    int nf = 0;
+    if (ei == cudaSuccess) ei = cudaMemcpyAsync(&nf, nonfinite, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (ei == cudaSuccess) ei = cudaStreamSynchronize(h->stream);
+    cudaFree(part);
+    if (staging) cudaFree(staging);
+    if (ei != cudaSuccess) return cuda_fail(h, ei, "ingest");
+    if (nf) return fail(h, GDWD_EINVAL, "gdwd_create: Z has non-finite entries");
+    CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream), "memset");
+    // Gram and G = I + K / mu
+    const int ks = gram_ksplit(h->L, h->sms);
+    double* Kpart = nullptr;
+    CK(cudaMalloc(&Kpart, (size_t)ks * n * n * sizeof(double)), "cudaMalloc(Kpart)");
+    cudaError_t eg = run_gram(h->store, h->L, ks, Kpart, h->sc, h->opt.mu, h->G, h->stream);
+    if (eg == cudaSuccess) eg = cudaStreamSynchronize(h->stream);
+    cudaFree(Kpart);
+    if (eg != cudaSuccess) return cuda_fail(h, eg, "gram");
+    // Cholesky, inverse, p, s
+    double *A = nullptr, *X = nullptr, *Pd = nullptr;
+    CK(cudaMalloc(&A, (size_t)n * n * sizeof(double)), "cudaMalloc(A)");
+    cudaError_t ef = cudaMalloc(&X, (size_t)n * n * sizeof(double));
+    if (ef == cudaSuccess) ef = cudaMalloc(&Pd, (size_t)n * n * sizeof(double));
+    if (ef == cudaSuccess) ef = cudaMemcpyAsync(A, h->G, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
+    if (ef == cudaSuccess) ef = cudaMemsetAsync(h->bar, 0, sizeof(unsigned), h->stream);
+    const int fgrid = h->sms;
+    if (ef == cudaSuccess) {
+      FactorArgs fa{A, X, Pd, h->P, h->ldP, h->y, h->p, h->pdf, h->dscalars + 2, n, fgrid, h->bar, h->err,
+                    (uint64_t)(h->opt.timeout_s * 1e9)};
+      ef = run_factor(fa, h->stream);
+    }
+    int ferr = 0;
+    if (ef == cudaSuccess) ef = cudaMemcpyAsync(&ferr, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    double hs[3] = {0, 0, 0};
+    if (ef == cudaSuccess) ef = cudaMemcpyAsync(hs, h->dscalars, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (ef == cudaSuccess) ef = cudaEventRecord(e1, h->stream);
+    if (ef == cudaSuccess) ef = cudaStreamSynchronize(h->stream);
+    cudaFree(A);
+    cudaFree(X);
+    cudaFree(Pd);
+    if (ef != cudaSuccess) return cuda_fail(h, ef, "factor");
+    if (ferr == GDWD_ENOTPD) return fail(h, GDWD_ENOTPD, "gdwd_create: Cholesky met a non-positive pivot");
+    if (ferr) return fail(h, (gdwd_status)ferr, "gdwd_create: factor kernel reported an error");
+    h->zscale = hs[1];
+    h->s = hs[2];
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    h->t_setup_ms = ms;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!(h->s > 0.0) || !std::isfinite(h->s)) return fail(h, GDWD_ENUMERIC, "gdwd_create: y^T G^{-1} y is not positive");
+    return GDWD_OK;
+  }();
+  if (st != GDWD_OK) return bail(st);
+  *out = h;
+  return GDWD_OK;
+}
+
+template <typename CT>
+static IterArgs<CT> make_args(gdwd_handle* h, double C, double sigma0) {
+  IterArgs<CT> a{};
+  a.L = h->L;
+  a.sc = h->sc;
+  a.P = h->P;
+  a.ldP = h->ldP;
+  a.pdf = h->pdf;
+  a.p = h->p;
+  a.y = h->y;
+  a.e = h->e;
+  a.omega = h->omega;
+  a.wt = h->wt;
+  a.inv_s = 1.0 / h->s;
+  a.q = h->q;
+  a.C = C;
+  a.mu = h->opt.mu;
+  a.tau = h->opt.tau;
+  a.R = h->zscale;
+  a.tol = h->opt.tol;
+  a.kappa = (h->q + 1.0) / h->q * std::pow(h->q, 1.0 / (h->q + 1.0));
+  a.max_iter = h->opt.max_iter;
+  a.grid = h->grid;
+  a.timeout_ns = (uint64_t)(h->opt.timeout_s * 1e9);
+  a.r = h->r;
+  a.xi = h->xi;
+  a.alpha = h->alpha;
+  a.b = h->b;
+  a.rhsA = h->rhsA;
+  a.rhsB = h->rhsB;
+  a.cq = (CT*)h->cq;
+  a.aq = (CT*)h->aq;
+  a.u = h->u;
+  a.rho = h->rho;
+  a.g = h->g;
+  a.partial = (CT*)h->partial;
+  a.scal = h->scal;
+  a.bar = h->bar;
+  a.err = h->err;
+  a.ctrl = h->ctrl;
+  return a;
+}
+
+static gdwd_status solve_one(gdwd_handle* h, double C, double* w, int w_on_device, double* alpha, gdwd_result* res) {
+  const int64_t n = h->n, d = h->d;
+  const int64_t dpad = (int64_t)h->L.NB * h->L.TB;
+  cudaStream_t st = h->stream;
+  const double sigma0 = h->opt.sigma0 > 0 ? h->opt.sigma0 : std::pow(std::min(10.0 * C, (double)n), h->q);
+  // initial iterate: r = xi = 1, w = u = 0, beta = 0, alpha = 0, rho = 0
+  const int fb = (int)std::min<int64_t>((n + 255) / 256, 1024);
+  fill_kernel<<<fb, 256, 0, st>>>(h->r, n, 1.0);
+  fill_kernel<<<fb, 256, 0, st>>>(h->xi, n, 1.0);
+  CK(cudaMemsetAsync(h->alpha, 0, n * sizeof(double), st), "memset");
+  CK(cudaMemsetAsync(h->u, 0, dpad * sizeof(double), st), "memset");
+  CK(cudaMemsetAsync(h->rho, 0, dpad * sizeof(double), st), "memset");
+  CK(cudaMemsetAsync(h->g, 0, dpad * sizeof(double), st), "memset");
+  Ctrl c0{};
+  c0.sigma = sigma0;
+  c0.sigma_prev = sigma0;
+  c0.theta = 1.0;
+  CK(cudaMemcpyAsync(h->ctrl, &c0, sizeof(Ctrl), cudaMemcpyHostToDevice, st), "copy ctrl");
+  CK(cudaMemsetAsync(h->bar, 0, sizeof(unsigned), st), "memset");
+  CK(cudaMemsetAsync(h->err, 0, sizeof(int), st), "memset");
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0), "event");
+  CK(cudaEventCreate(&e1), "event");
+  CK(cudaEventRecord(e0, st), "event");
+  cudaError_t e;
+  const int smem_limit = h->smem_optin - 2048;
+  if (h->store == GDWD_F64)
+    e = run_iterate_f64(make_args<double>(h, C, sigma0), smem_limit, st);
+  else
+    e = run_iterate_f32(make_args<float>(h, C, sigma0), smem_limit, st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "iterate launch");
+  CK(cudaEventRecord(e1, st), "event");
+  Ctrl c{};
+  int kerr = 0;
+  CK(cudaMemcpyAsync(&c, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st), "copy ctrl");
+  CK(cudaMemcpyAsync(&kerr, h->err, sizeof(int), cudaMemcpyDeviceToHost, st), "copy err");
+  const int wb = (int)std::min<int64_t>((d + 255) / 256, 2048);
+  double* wdst = (w && w_on_device) ? w : h->wtmp;
+  finish_w_kernel<<<wb, 256, 0, st>>>(h->g, h->rho, h->ctrl, std::sqrt(h->opt.mu), h->zscale, d, wdst);
+  CK(cudaGetLastError(), "finish");
+  if (w && !w_on_device) CK(cudaMemcpyAsync(w, h->wtmp, d * sizeof(double), cudaMemcpyDeviceToHost, st), "copy w");
+  if (alpha) CK(cudaMemcpyAsync(alpha, h->alpha, n * sizeof(double), cudaMemcpyDeviceToHost, st), "copy alpha");
+  CK(cudaStreamSynchronize(st), "sync");
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::memset(res, 0, sizeof(*res));
+  res->beta = c.beta;
+  res->primal_obj = c.pobj;
+  res->dual_obj = c.dobj;
+  res->kkt = c.kkt;
+  res->eta_p = std::max(c.eta_p1, std::max(c.eta_p2, c.eta_p3));
+  res->eta_d = std::max(c.eta_d1, std::max(c.eta_d2, c.eta_d3));
+  res->eta_c = std::max(c.eta_c1, std::max(c.eta_c2, c.eta_c3));
+  res->eta_gap = c.eta_gap;
+  res->sigma = c.sigma;
+  res->zscale = h->zscale;
+  res->t_setup_ms = h->t_setup_ms;
+  res->t_solve_ms = ms;
+  res->iters = c.it;
+  gdwd_status s = kerr ? (gdwd_status)kerr : (gdwd_status)c.status;
+  res->status = s;
+  if (kerr) return fail(h, s, "gdwd_solve: iteration kernel stopped with a device error (bounded wait expired)");
+  return s;
+}
+
+extern "C" gdwd_status gdwd_solve(gdwd_handle* h, const double* Cs, int32_t nC, double* w, int32_t w_on_device,
+                                  double* alpha, gdwd_result* res) {
+  if (!h || !res) return fail(h, GDWD_EINVAL, "gdwd_solve: NULL handle or result");
+  if (nC < 0) return fail(h, GDWD_EINVAL, "gdwd_solve: nC < 0");
+  const int count = (Cs && nC > 0) ? nC : 1;
+  for (int k = 0; k < count; ++k) {
+    const double C = (Cs && nC > 0) ? Cs[k] : h->C;
+    if (!(C > 0.0) || !std::isfinite(C)) return fail(h, GDWD_EINVAL, "gdwd_solve: C must be > 0");
+  }
+  gdwd_status worst = GDWD_OK;
+  for (int k = 0; k < count; ++k) {
+    const double C = (Cs && nC > 0) ? Cs[k] : h->C;
+    gdwd_status s = solve_one(h, C, w ? w + (size_t)k * h->d : nullptr, w_on_device,
+                              alpha ? alpha + (size_t)k * h->n : nullptr, res + k);
+    if (s != GDWD_OK && s != GDWD_EMAXITER) return s;
+    if (s != GDWD_OK) worst = s;
+  }
+  return worst;
+}
+
+extern "C" gdwd_status gdwd_free(gdwd_handle* h) {
+  if (!h) return GDWD_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  release(h);
+  delete h;
+  return GDWD_OK;
+}
+
+extern "C" const char* gdwd_last_error(const gdwd_handle* h) {
+  return h ? h->last_error.c_str() : g_thread_error.c_str();
+}
+
+extern "C" gdwd_status gdwd_prox(const double* a, const double* r0, const double* omega, double sigma, double q,
+                                 int64_t n, double* out, void* stream) {
+  gdwd_handle* h = nullptr;
+  if (n < 0 || !(q > 0.0) || !(sigma > 0.0)) return fail(nullptr, GDWD_EINVAL, "gdwd_prox: need n >= 0, q > 0, sigma > 0");
+  if (n > 0 && (!a || !out)) return fail(nullptr, GDWD_EINVAL, "gdwd_prox: NULL array");
+  CK(launch_prox(a, r0, omega, sigma, q, n, out, (cudaStream_t)stream), "gdwd_prox");
+  CK(cudaStreamSynchronize((cudaStream_t)stream), "gdwd_prox sync");
+  return GDWD_OK;
+}
+
+extern "C" gdwd_status gdwd_apply(gdwd_handle* h, int32_t trans, const double* x, double* out) {
+  if (!h || !x || !out) return fail(h, GDWD_EINVAL, "gdwd_apply: NULL argument");
+  CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream), "memset");
+  const int grid = h->L.NB;   // one CTA per slab
+  CK(run_apply(h->store, h->L, trans, x, h->sc, out, h->partial, std::min(grid, 4096), h->smem_optin - 2048, h->err,
+               (uint64_t)(h->opt.timeout_s * 1e9), h->stream),
+     "gdwd_apply");
+  int kerr = 0;
+  CK(cudaMemcpyAsync(&kerr, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "copy err");
+  CK(cudaStreamSynchronize(h->stream), "sync");
+  if (kerr) return fail(h, (gdwd_status)kerr, "gdwd_apply: device wait expired");
+  return GDWD_OK;
+}
+
+extern "C" gdwd_status gdwd_gram(gdwd_handle* h, double* G_out) {
+  if (!h || !G_out) return fail(h, GDWD_EINVAL, "gdwd_gram: NULL argument");
+  CK(cudaMemcpyAsync(G_out, h->G, (size_t)h->n * h->n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy G");
+  CK(cudaStreamSynchronize(h->stream), "sync");
+  return GDWD_OK;
+}
+
+extern "C" gdwd_status gdwd_get_info(const gdwd_handle* h, gdwd_info* info) {
+  if (!h || !info) return fail(nullptr, GDWD_EINVAL, "gdwd_get_info: NULL argument");
+  std::memset(info, 0, sizeof(*info));
+  info->d = h->d;
+  info->n = h->n;
+  info->store = h->store;
+  info->block_rows = h->L.TB;
+  info->slabs = h->L.NB;
+  info->grid = h->grid;
+  info->z_bytes = (int64_t)h->L.NB * h->L.TB * h->n * h->L.esize;
+  info->device_bytes = (int64_t)h->bytes;
+  info->zscale = h->zscale;
+  info->t_setup_ms = h->t_setup_ms;
+  return GDWD_OK;
+}

@@ -1,0 +1,223 @@
+// Shared device helpers of libgdwd: double-float arithmetic, bounded grid
+// barrier, 1-D bulk-copy (TMA) ring with mbarriers, element traits.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/gdwd.h"
+
+namespace gdwd {
+
+constexpr int kThreads = 256;          // threads of every persistent / streaming CTA
+constexpr int kWarps = kThreads / 32;
+
+// ---------------------------------------------------------------------------
+// double-float ("df"): a value hi + lo held in two floats, ~48-bit mantissa.
+// FP64 issues at 1/58 of the FP32 rate on this part, so the per-iteration
+// n-space solves run in df with exact FP32 products (fmaf) and two-sum adds.
+// ---------------------------------------------------------------------------
+struct df {
+  float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// acc += x (x a plain float)
+__device__ __forceinline__ void df_add(df& acc, float x) {
+  float s, e;
+  two_sum(acc.hi, x, s, e);
+  acc.lo += e;
+  acc.hi = s;
+}
+
+// acc += (a.hi + a.lo)
+__device__ __forceinline__ void df_add(df& acc, df a) {
+  float s, e;
+  two_sum(acc.hi, a.hi, s, e);
+  e += acc.lo + a.lo;
+  float t = s + e;
+  acc.lo = e - (t - s);
+  acc.hi = t;
+}
+
+// acc += a * b for df a, b (product error kept through fmaf)
+__device__ __forceinline__ void df_fma(df& acc, df a, df b) {
+  float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  float s, e2;
+  two_sum(acc.hi, p, s, e2);
+  acc.lo += e2 + e;
+  acc.hi = s;
+}
+
+__device__ __forceinline__ df df_from(double x) {
+  df r;
+  r.hi = (float)x;
+  r.lo = (float)(x - (double)r.hi);
+  return r;
+}
+
+__device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ df df_shfl_xor(df a, int m) {
+  df r;
+  r.hi = __shfl_xor_sync(0xffffffffu, a.hi, m);
+  r.lo = __shfl_xor_sync(0xffffffffu, a.lo, m);
+  return r;
+}
+
+__device__ __forceinline__ df df_warp_sum(df a) {
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) df_add(a, df_shfl_xor(a, m));
+  return a;
+}
+
+__device__ __forceinline__ double warp_sum(double a) {
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) a += __shfl_xor_sync(0xffffffffu, a, m);
+  return a;
+}
+
+// ---------------------------------------------------------------------------
+// time and bounded waits
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Error word shared by all CTAs of a launch.  Non-zero = a gdwd_status.
+__device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
+
+// Grid-wide barrier for a cooperative launch (all CTAs co-resident).  The
+// counter only grows; barrier number `gen` (1, 2, ...) completes when it reaches
+// gen * nblocks.  Every wait is bounded by timeout_ns: on expiry (or when
+// another CTA has already flagged an error) the error word is set and false is
+// returned to every thread of the CTA, which must then leave the kernel.
+__device__ __forceinline__ bool grid_barrier(unsigned* counter, unsigned nblocks, unsigned& gen, int* err,
+                                             uint64_t timeout_ns, int* s_flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    gen += 1;
+    __threadfence();
+    atomicAdd(counter, 1u);
+    const unsigned target = gen * nblocks;
+    const uint64_t t0 = globaltimer();
+    int ok = 1;
+    while (true) {
+      unsigned v = *(volatile unsigned*)counter;
+      if ((int)(v - target) >= 0) break;
+      if (ld_volatile(err) != 0) { ok = 0; break; }
+      if (globaltimer() - t0 > timeout_ns) {
+        atomicCAS(err, 0, (int)GDWD_ETIMEOUT);
+        ok = 0;
+        break;
+      }
+      __nanosleep(20);
+    }
+    __threadfence();
+    if (ld_volatile(err) != 0) ok = 0;
+    *s_flag = ok;
+  } else {
+    gen += 1;
+  }
+  __syncthreads();
+  return *(volatile int*)s_flag != 0;
+}
+
+// ---------------------------------------------------------------------------
+// mbarrier + 1-D bulk async copy (cp.async.bulk, the untiled TMA form)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// bytes and both addresses must be multiples of 16
+__device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst_smem)),
+      "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase; false (and err set) after timeout_ns.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, uint64_t timeout_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  while (!mbar_try_wait(bar, parity)) {
+    if (globaltimer() - t0 > timeout_ns) {
+      atomicCAS(err, 0, (int)GDWD_ETIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// element traits of the stored Z: 16-byte vectors converted to the compute type
+// ---------------------------------------------------------------------------
+template <typename T>
+struct ElemTraits;
+
+template <>
+struct ElemTraits<double> {
+  using compute_t = double;
+  static constexpr int kVec = 2;
+  __device__ __forceinline__ static void load(const void* p, double* v) {
+    double2 x = *reinterpret_cast<const double2*>(p);
+    v[0] = x.x;
+    v[1] = x.y;
+  }
+};
+
+template <>
+struct ElemTraits<float> {
+  using compute_t = float;
+  static constexpr int kVec = 4;
+  __device__ __forceinline__ static void load(const void* p, float* v) {
+    float4 x = *reinterpret_cast<const float4*>(p);
+    v[0] = x.x;
+    v[1] = x.y;
+    v[2] = x.z;
+    v[3] = x.w;
+  }
+};
+
+}  // namespace gdwd

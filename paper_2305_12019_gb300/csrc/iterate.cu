@@ -1,0 +1,661 @@
+// Persistent iteration kernel of libgdwd: the whole inexact sGS-ADMM loop
+// (Algorithm 1, Sec. 3) for one value of C runs in ONE cooperative launch with
+// one CTA per SM and bounded grid barriers between its phases.
+//
+// The (d+1)x(d+1) system eq-linsys is solved in n-space.  With D^2 = mu I,
+// G = I + Z~^T Z~ / mu, p = G^{-1} y, s = y^T p, g' = u + rho / (sigma sqrt(mu))
+// and b = Z~^T g', the solution of eq-linsys for v = xi - r - alpha / sigma is
+//     x = G^{-1}(b + v),  beta = -y^T x / s,  c = x + beta p,
+//     Z~^T w = c - v - y beta,   w = g' - Z~ c / mu
+// (Woodbury applied to the SMW2 form of Sec. 3.3.2; the CPU oracle uses the
+// paper's d-space formulas eq-Ainv / eq-H instead, so the tests check this
+// algebra).  The Step-1b prox input c^k of eq-1c is then c-bar + r^k, Step 1c
+// only changes x, beta, c, and each iteration reads Z twice:
+//
+//   phase A  (Z pass 1)  deferred Step 2/3 d-update of u, rho (needs ||g||),
+//                        g' per row, per-slab partial dots of Z~^T g'
+//   phase R              b = reduction of the partials; rhs1 = b + v-bar
+//   phase N1             x-bar = G^{-1} rhs1 (double-float GEMV), beta-bar,
+//                        Step 1b prox (Newton, FP64), rhs2 = b + v
+//   phase N2             x = G^{-1} rhs2, beta, c, Z~^T w; Step 2 xi and
+//                        Step 3 alpha (n part); n-space KKT partial sums
+//   phase B  (Z pass 2)  t = Z~ c, ta = Z~ alpha; g = u - t / mu; d-space sums
+//   phase S              all sums -> KKT residuals (Sec. 4.3), duality gap,
+//                        sigma rule (Sec. 4.4), stop test; identical in every CTA
+#include <algorithm>
+
+#include "passes.cuh"
+
+namespace gdwd {
+
+constexpr int kMaxStages = 8;
+
+// ---------------------------------------------------------------------------
+// r-subproblem (Step 1b, eq-varphi): the positive root of
+// s^(q+1) (s - a) = kq,  kq = omega / sigma, by Newton's iteration of Sec. 3.2
+// kept inside the bracket [max(a,0), max(a,0) + max(kq, 1)] (f < 0 at the left
+// end, f >= 0 at the right end); steps that leave it are bisected.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double pow_q1(double s, double q, int qcase) {  // s^(q+1)
+  switch (qcase) {
+    case 1: return s * s;
+    case 2: return s * s * s;
+    case 4: { double s2 = s * s; return s2 * s2 * s; }
+    case 5: return s * sqrt(s);   // q = 0.5
+    default: return pow(s, q + 1.0);
+  }
+}
+
+__device__ __forceinline__ int q_case(double q) {
+  return q == 1.0 ? 1 : q == 2.0 ? 2 : q == 4.0 ? 4 : q == 0.5 ? 5 : 0;
+}
+
+__device__ double prox_root(double a, double kq, double q, int qcase, double r0) {
+  double lo = fmax(a, 0.0);
+  double hi = lo + fmax(kq, 1.0);
+  double s = (r0 > lo && r0 < hi) ? r0 : 0.5 * (lo + hi);
+  for (int it = 0; it < 100; ++it) {
+    const double sq1 = pow_q1(s, q, qcase);
+    const double f = sq1 * (s - a) - kq;
+    if (f < 0.0) lo = s;
+    else if (f > 0.0) hi = s;
+    else break;
+    const double nt = s * (kq * (q + 2.0) + a * sq1) / (kq * (q + 1.0) + sq1 * s);
+    const double cand = (nt > lo && nt < hi) ? nt : 0.5 * (lo + hi);
+    const bool stop = fabs(cand - s) <= 8.881784197001252e-16 * cand;   // 4 eps
+    s = cand;
+    if (stop) break;
+  }
+  return s;
+}
+
+__global__ void prox_kernel(const double* a, const double* r0, const double* omega, double sigma, double q,
+                            int64_t n, double* out) {
+  const int qc = q_case(q);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double om = omega ? omega[i] : q;
+    out[i] = prox_root(a[i], om / sigma, q, qc, r0 ? r0[i] : -1.0);
+  }
+}
+
+cudaError_t launch_prox(const double* a, const double* r0, const double* omega, double sigma, double q,
+                        int64_t n, double* out, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+  prox_kernel<<<blocks, 256, 0, st>>>(a, r0, omega, sigma, q, n, out);
+  return cudaGetLastError();
+}
+
+// (wt alpha)^(q/(q+1)) for the dual objective
+__device__ __forceinline__ double dual_pow(double x, double q, int qcase) {
+  if (x <= 0.0) return 0.0;
+  switch (qcase) {
+    case 1: return sqrt(x);
+    case 2: { double c = cbrt(x); return c * c; }
+    case 5: return cbrt(x);
+    default: return pow(x, q / (q + 1.0));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// block-level deterministic reductions
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double block_sum(double v, double* s_red) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) s_red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kWarps; ++i) t += s_red[i];
+    s_red[kWarps] = t;
+  }
+  __syncthreads();
+  return s_red[kWarps];
+}
+
+__device__ __forceinline__ df block_sum_df(df v, float* s_red) {
+  v = df_warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) {
+    s_red[2 * w] = v.hi;
+    s_red[2 * w + 1] = v.lo;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    df t{0.f, 0.f};
+    for (int i = 0; i < kWarps; ++i) df_add(t, df{s_red[2 * i], s_red[2 * i + 1]});
+    s_red[2 * kWarps] = t.hi;
+    s_red[2 * kWarps + 1] = t.lo;
+  }
+  __syncthreads();
+  return df{s_red[2 * kWarps], s_red[2 * kWarps + 1]};
+}
+
+// x_i = sum_j P_ij rhs_j for one row, one warp, double-float (result in all lanes)
+__device__ __forceinline__ df row_dot(const float2* __restrict__ Prow, const float2* rhs_s, int npair) {
+  const float4* P4 = reinterpret_cast<const float4*>(Prow);
+  const float4* R4 = reinterpret_cast<const float4*>(rhs_s);
+  df a0{0.f, 0.f}, a1{0.f, 0.f};
+  const int lane = threadIdx.x & 31;
+  int j = lane;
+  for (; j + 32 < npair; j += 64) {
+    const float4 p0 = __ldg(P4 + j), p1 = __ldg(P4 + j + 32);
+    const float4 r0 = R4[j], r1 = R4[j + 32];
+    df_fma(a0, df{p0.x, p0.y}, df{r0.x, r0.y});
+    df_fma(a1, df{p0.z, p0.w}, df{r0.z, r0.w});
+    df_fma(a0, df{p1.x, p1.y}, df{r1.x, r1.y});
+    df_fma(a1, df{p1.z, p1.w}, df{r1.z, r1.w});
+  }
+  for (; j < npair; j += 32) {
+    const float4 p0 = __ldg(P4 + j);
+    const float4 r0 = R4[j];
+    df_fma(a0, df{p0.x, p0.y}, df{r0.x, r0.y});
+    df_fma(a1, df{p0.z, p0.w}, df{r0.z, r0.w});
+  }
+  df_add(a0, a1);
+  return df_warp_sum(a0);
+}
+
+// ---------------------------------------------------------------------------
+// pass-B row epilogue of the iteration: g = u - t / mu and the d-space sums
+// ---------------------------------------------------------------------------
+struct IterEpi {
+  double* g;
+  const double* u;
+  const double* rho;
+  double inv_mu, a_coef;     // a = ta + a_coef * rho, a_coef = sqrt(mu)(1 - tau)
+  double sg2 = 0, sgr = 0, sr2 = 0, sa2 = 0, sag = 0, sta2 = 0;
+  __device__ void row(int64_t j, double t, double ta) {
+    const double gj = u[j] - t * inv_mu;
+    const double rj = rho[j];
+    const double aj = ta + a_coef * rj;
+    g[j] = gj;
+    sg2 = fma(gj, gj, sg2);
+    sgr = fma(gj, rj, sgr);
+    sr2 = fma(rj, rj, sr2);
+    sa2 = fma(aj, aj, sa2);
+    sag = fma(aj, gj, sag);
+    sta2 = fma(ta, ta, sta2);
+  }
+};
+
+template <typename CT>
+__device__ __forceinline__ void store_ct(CT* p, double v) { *p = (CT)v; }
+
+// ---------------------------------------------------------------------------
+// the persistent kernel
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename ElemTraits<T>::compute_t> a,
+                                                              int stages, int stage_bytes) {
+  using CT = typename ElemTraits<T>::compute_t;
+  constexpr int VEC = ElemTraits<T>::kVec;
+  extern __shared__ __align__(128) uint8_t smem[];
+  __shared__ uint64_t s_bars[kMaxStages];
+  __shared__ int s_flag, s_abort;
+  __shared__ double s_red[2 * kWarps + 2];
+  __shared__ double s_tot[S_COUNT];
+  __shared__ double s_ctl[8];
+
+  const Layout& L = a.L;
+  const int cta = blockIdx.x, grid = a.grid;
+  const int64_t n = L.n, d = L.d;
+  const int TB = L.TB, NB = L.NB;
+  const int Q = TB / VEC;
+  const int H = kThreads / L.CW;
+  const int G = Q <= kThreads ? kThreads / Q : 1;
+  const int nmy = (NB > cta) ? (NB - cta + grid - 1) / grid : 0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gw = cta * kWarps + warp, W = grid * kWarps;
+  const int qcase = q_case(a.q);
+  const double sqmu = sqrt(a.mu), inv_mu = 1.0 / a.mu;
+  const double den = 1.0 + a.C;
+
+  Ring rg;
+  rg.buf = smem;
+  rg.bars = s_bars;
+  rg.stages = stages;
+  rg.stage_bytes = stage_bytes;
+  uint8_t* uni = smem + (size_t)stages * stage_bytes;     // phase-local region
+  if (threadIdx.x == 0) s_abort = 0;
+  ring_init(rg);
+
+  unsigned gen = 0;
+  double sig = a.ctrl->sigma, sig_prev = a.ctrl->sigma_prev, theta = a.ctrl->theta;
+  int pending = a.ctrl->pending;
+  int it0 = a.ctrl->it;
+  int status = GDWD_EMAXITER;
+  double beta = 0.0;
+
+#define GDWD_BARRIER()                                                                    \
+  do {                                                                                    \
+    if (!grid_barrier(a.bar, (unsigned)grid, gen, a.err, a.timeout_ns, &s_flag)) return; \
+  } while (0)
+
+  int it = it0;
+  for (; it < a.max_iter; ++it) {
+    // ---------------- phase A: deferred (u, rho) update, g', Z~^T g' partials
+    {
+      CT* gp = reinterpret_cast<CT*>(uni);
+      const double gsc = 1.0 / (sig * sqmu);
+      const double rcoef = a.tau * sig_prev * sqmu * (1.0 - theta);
+      for (int k = 0; k < nmy; ++k) {
+        const int64_t s = cta + (int64_t)k * grid;
+        for (int j = threadIdx.x; j < TB; j += kThreads) {
+          const int64_t gj = s * TB + j;
+          double gpv = 0.0;
+          if (gj < d) {
+            double uj = a.u[gj], rj = a.rho[gj];
+            if (pending) {
+              const double g = a.g[gj];
+              rj = (1.0 - a.tau) * rj - rcoef * g;      // rho <- rho - tau sigma D (w - u+)
+              uj = theta * g;                           // u+ = Pi_B(g)
+              a.u[gj] = uj;
+              a.rho[gj] = rj;
+            }
+            gpv = uj + rj * gsc;
+          }
+          gp[(size_t)k * TB + j] = (CT)gpv;
+        }
+      }
+      __syncthreads();
+      PassA<T> pa{gp, a.partial, TB, NB, Q, H};
+      if (!stream_slabs<T>(L, rg, cta, grid, a.err, a.timeout_ns, &s_abort, pa)) return;
+    }
+    GDWD_BARRIER();
+
+    const double inv_sig = 1.0 / sig;
+    // ---------------- phase R: b = sc * sum of partials; rhs1 = b + xi - r - alpha / sigma
+    for (int64_t i = gw; i < n; i += W) {
+      const CT* pp = a.partial + (size_t)i * NB;
+      double bsum;
+      if constexpr (sizeof(CT) == 8) {
+        double acc = 0.0;
+        for (int s2 = lane; s2 < NB; s2 += 32) acc += (double)pp[s2];
+        bsum = warp_sum(acc);
+      } else {
+        df acc{0.f, 0.f};
+        for (int s2 = lane; s2 < NB; s2 += 32) df_add(acc, (float)pp[s2]);
+        bsum = df_to_double(df_warp_sum(acc));
+      }
+      if (lane == 0) {
+        const double bi = a.sc[i] * bsum;
+        a.b[i] = bi;
+        const double v = a.xi[i] - a.r[i] - a.alpha[i] * inv_sig;
+        const df r1 = df_from(bi + v);
+        a.rhsA[i] = make_float2(r1.hi, r1.lo);
+      }
+    }
+    GDWD_BARRIER();
+
+    // ---------------- phase N1: x-bar, beta-bar, prox, rhs2
+    const int npair = (int)((n + 1) / 2);
+    float2* rhs_s = reinterpret_cast<float2*>(uni);
+    float* s_redf = reinterpret_cast<float*>(s_red);
+    {
+      for (int64_t i = threadIdx.x; i < 2 * npair; i += kThreads) rhs_s[i] = i < n ? a.rhsA[i] : make_float2(0.f, 0.f);
+      __syncthreads();
+      df pd{0.f, 0.f};
+      for (int64_t i = threadIdx.x; i < n; i += kThreads) {
+        const float2 pv = a.pdf[i];
+        df_fma(pd, df{pv.x, pv.y}, df{rhs_s[i].x, rhs_s[i].y});
+      }
+      const double betabar = -df_to_double(block_sum_df(pd, s_redf)) * a.inv_s;
+      for (int64_t i = gw; i < n; i += W) {
+        const df x = row_dot(a.P + (size_t)i * a.ldP, rhs_s, npair);
+        if (lane == 0) {
+          const double cbar = df_to_double(x) + betabar * a.p[i];
+          const double ri = a.r[i];
+          const double rn = prox_root(cbar + ri, a.omega[i] * inv_sig, a.q, qcase, ri);
+          a.r[i] = rn;
+          const double v = a.xi[i] - rn - a.alpha[i] * inv_sig;
+          const df r2 = df_from(a.b[i] + v);
+          a.rhsB[i] = make_float2(r2.hi, r2.lo);
+        }
+      }
+    }
+    GDWD_BARRIER();
+
+    // ---------------- phase N2: x, beta, c, Z~^T w; Step 2 (xi), Step 3 (alpha)
+    {
+      for (int64_t i = threadIdx.x; i < 2 * npair; i += kThreads) rhs_s[i] = i < n ? a.rhsB[i] : make_float2(0.f, 0.f);
+      __syncthreads();
+      df pd{0.f, 0.f};
+      for (int64_t i = threadIdx.x; i < n; i += kThreads) {
+        const float2 pv = a.pdf[i];
+        df_fma(pd, df{pv.x, pv.y}, df{rhs_s[i].x, rhs_s[i].y});
+      }
+      beta = -df_to_double(block_sum_df(pd, s_redf)) * a.inv_s;
+      double s_res2 = 0, s_ya = 0, s_xica = 0, s_ams2 = 0, s_amin2 = 0, s_amax2 = 0, s_pr = 0, s_px = 0, s_du = 0;
+      for (int64_t i = gw; i < n; i += W) {
+        const df x = row_dot(a.P + (size_t)i * a.ldP, rhs_s, npair);
+        if (lane == 0) {
+          const double c = df_to_double(x) + beta * a.p[i];
+          const double ri = a.r[i], al = a.alpha[i], yi = a.y[i], ce = a.C * a.e[i];
+          const double v = a.xi[i] - ri - al * inv_sig;
+          const double zw = c - v - yi * beta;                                     // Z~^T w
+          const double xin = fmax(0.0, ri - zw - yi * beta + (al - ce) * inv_sig);  // Step 2
+          const double res = zw + yi * beta + xin - ri;
+          const double an = al - a.tau * sig * res;                                // Step 3
+          a.xi[i] = xin;
+          a.alpha[i] = an;
+          store_ct(a.cq + i, a.sc[i] * c);
+          store_ct(a.aq + i, a.sc[i] * an);
+          const double rq1 = pow_q1(ri, a.q, qcase);
+          const double om = a.omega[i];
+          s_res2 = fma(res, res, s_res2);
+          s_ya = fma(yi, an, s_ya);
+          s_xica = fma(xin, ce - an, s_xica);
+          const double dv = an - om / rq1;
+          s_ams2 = fma(dv, dv, s_ams2);
+          const double mn = fmin(0.0, an), mx = fmax(0.0, an - ce);
+          s_amin2 = fma(mn, mn, s_amin2);
+          s_amax2 = fma(mx, mx, s_amax2);
+          s_pr += (om / a.q) * ri / rq1;            // wt^q r^-q
+          s_px = fma(a.e[i], xin, s_px);
+          s_du += dual_pow(a.wt[i] * an, a.q, qcase);
+        }
+      }
+      const double vals[9] = {s_res2, s_ya, s_xica, s_ams2, s_amin2, s_amax2, s_pr, s_px, s_du};
+      for (int k = 0; k < 9; ++k) {
+        const double t = block_sum(vals[k], s_red);
+        if (threadIdx.x == 0) a.scal[(size_t)cta * S_COUNT + k] = t;
+      }
+    }
+    GDWD_BARRIER();
+
+    // ---------------- phase B: t = Z~ c, ta = Z~ alpha, g, d-space sums
+    {
+      CT* cv = reinterpret_cast<CT*>(uni);
+      CT* av = cv + n;
+      double* red = reinterpret_cast<double*>(
+          uni + ((2 * n * sizeof(CT) + 15) & ~(size_t)15));
+      for (int64_t i = threadIdx.x; i < n; i += kThreads) {
+        cv[i] = a.cq[i];
+        av[i] = a.aq[i];
+      }
+      __syncthreads();
+      IterEpi epi{a.g, a.u, a.rho, inv_mu, sqmu * (1.0 - a.tau)};
+      PassB<T, IterEpi> pb;
+      pb.cv = cv;
+      pb.av = av;
+      pb.red = red;
+      pb.TB = TB;
+      pb.Q = Q;
+      pb.G = G;
+      pb.d = d;
+      pb.two = true;
+      pb.epi = &epi;
+      for (int kk = 0; kk < VEC; ++kk) {
+        pb.rc[kk].reset();
+        pb.ra[kk].reset();
+      }
+      if (!stream_slabs<T>(L, rg, cta, grid, a.err, a.timeout_ns, &s_abort, pb)) return;
+      const double vals[6] = {epi.sg2, epi.sgr, epi.sr2, epi.sa2, epi.sag, epi.sta2};
+      for (int k = 0; k < 6; ++k) {
+        const double t = block_sum(vals[k], s_red);
+        if (threadIdx.x == 0) a.scal[(size_t)cta * S_COUNT + S_G2 + k] = t;
+      }
+    }
+    GDWD_BARRIER();
+
+    // ---------------- phase S: totals, KKT, sigma rule, stop test (same in every CTA)
+    for (int k = warp; k < S_COUNT - 1; k += kWarps) {
+      double acc = 0.0;
+      for (int c2 = lane; c2 < grid; c2 += 32) acc += a.scal[(size_t)c2 * S_COUNT + k];
+      acc = warp_sum(acc);
+      if (lane == 0) s_tot[k] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const double S1 = s_tot[S_G2], S2 = s_tot[S_GRHO], S3 = s_tot[S_RHO2];
+      const double gs = 1.0 / (sig * sqmu);
+      const double gnorm = sqrt(S1);
+      const double th = (gnorm <= a.R) ? 1.0 : a.R / gnorm;                 // Step 2 projection
+      const double w2 = fmax(0.0, S1 + 2.0 * gs * S2 + gs * gs * S3);        // ||w||^2
+      const double om = 1.0 - th;
+      const double wu2 = fmax(0.0, om * om * S1 + 2.0 * om * gs * S2 + gs * gs * S3);   // ||w - u+||^2
+      const double kap = a.tau * sig * a.mu * om;
+      const double d3 = fmax(0.0, s_tot[S_A2] - 2.0 * kap * s_tot[S_AG] + kap * kap * S1);
+      const double wn = sqrt(w2);
+      const double p1 = sqrt(s_tot[S_RES2]) / den;
+      const double p2 = sqmu * sqrt(wu2) / den;
+      const double p3 = fmax(wn - a.R, 0.0) / den;
+      const double dd1 = sqrt(s_tot[S_AMIN2]) / den;
+      const double dd2 = sqrt(s_tot[S_AMAX2]) / den;
+      const double dd3 = sqrt(d3) / den;
+      const double c1 = fabs(s_tot[S_YA]) / den;
+      const double c2 = fabs(s_tot[S_XICA]) / den;
+      const double c3 = sqrt(s_tot[S_AMS2]) / den;
+      const double pobj = s_tot[S_PRIM_R] + a.C * s_tot[S_PRIM_XI];
+      const double dobj = a.kappa * s_tot[S_DUAL_A] - a.R * sqrt(s_tot[S_TA2]);
+      const double gap = fabs(pobj - dobj) / (1.0 + fabs(pobj) + fabs(dobj));
+      const double ep = fmax(p1, fmax(p2, p3)), ed = fmax(dd1, fmax(dd2, dd3)), ec = fmax(c1, fmax(c2, c3));
+      const double kkt = fmax(fmax(ep, ed), fmax(ec, gap));
+      int done = 0;
+      double sig_next = sig;
+      if (!(kkt == kkt) || isinf(kkt)) {
+        done = 1;
+        status = GDWD_ENUMERIC;
+      } else if (kkt <= a.tol) {
+        done = 1;
+        status = GDWD_OK;
+      } else if (it >= 1) {                                                  // sigma rule, Sec. 4.4
+        const double chi = ep / fmax(ed, 1e-300);
+        const double big = fmax(chi, 1.0 / fmax(chi, 1e-300));
+        const double zeta = big > 500.0 ? 2.2 : (big > 50.0 ? 1.65 : 1.1);
+        if (chi > 5.0) sig_next = sig * zeta;
+        else if (1.0 / fmax(chi, 1e-300) > 5.0) sig_next = sig / zeta;
+      }
+      s_ctl[0] = th;
+      s_ctl[1] = sig_next;
+      s_ctl[2] = done;
+      s_ctl[3] = status;
+      if (cta == 0) {
+        Ctrl* c = a.ctrl;
+        c->beta = beta;
+        c->pobj = pobj;
+        c->dobj = dobj;
+        c->kkt = kkt;
+        c->eta_p1 = p1; c->eta_p2 = p2; c->eta_p3 = p3;
+        c->eta_d1 = dd1; c->eta_d2 = dd2; c->eta_d3 = dd3;
+        c->eta_c1 = c1; c->eta_c2 = c2; c->eta_c3 = c3;
+        c->eta_gap = gap;
+        c->wnorm = wn;
+      }
+    }
+    __syncthreads();
+    sig_prev = sig;
+    theta = s_ctl[0];
+    sig = s_ctl[1];
+    pending = 1;
+    const bool done = s_ctl[2] != 0.0;
+    status = (int)s_ctl[3];
+    if (done) {
+      ++it;
+      break;
+    }
+  }
+  if (it >= a.max_iter && status != GDWD_OK) status = GDWD_EMAXITER;
+  if (cta == 0 && threadIdx.x == 0) {
+    Ctrl* c = a.ctrl;
+    c->sigma = sig;
+    c->sigma_prev = sig_prev;
+    c->theta = theta;
+    c->pending = pending;
+    c->it = it;
+    c->status = status;
+    c->done = 1;
+  }
+#undef GDWD_BARRIER
+}
+
+template <typename T>
+static size_t union_bytes(const Layout& L, int grid) {
+  using CT = typename ElemTraits<T>::compute_t;
+  constexpr int VEC = ElemTraits<T>::kVec;
+  const int nmy = (L.NB + grid - 1) / grid;
+  const int Q = L.TB / VEC;
+  const int G = Q <= kThreads ? kThreads / Q : 1;
+  size_t a_bytes = (size_t)nmy * L.TB * sizeof(CT);
+  size_t b_bytes = ((2 * L.n * sizeof(CT) + 15) & ~(size_t)15) + (size_t)2 * G * L.TB * sizeof(double);
+  size_t n_bytes = (size_t)((L.n + 1) / 2) * 2 * sizeof(float2);
+  size_t u = a_bytes;
+  if (b_bytes > u) u = b_bytes;
+  if (n_bytes > u) u = n_bytes;
+  return (u + 127) & ~(size_t)127;
+}
+
+template <typename T>
+static cudaError_t launch_iterate_t(const IterArgs<typename ElemTraits<T>::compute_t>& args, int stages,
+                                    int stage_bytes, size_t smem, cudaStream_t st) {
+  auto kern = iterate_kernel<T>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  void* params[] = {(void*)&args, (void*)&stages, (void*)&stage_bytes};
+  return cudaLaunchCooperativeKernel((const void*)kern, dim3(args.grid), dim3(kThreads), params, smem, st);
+}
+
+// Plans the ring (stage size, stage count) for the available shared memory.
+template <typename T>
+static bool plan_ring(const Layout& L, int grid, int smem_limit, int& stages, int& stage_bytes, size_t& smem) {
+  const size_t ub = union_bytes<T>(L, grid);
+  stage_bytes = (int)(((size_t)L.CW * L.TB * L.esize + 127) & ~(size_t)127);
+  const int64_t avail = (int64_t)smem_limit - (int64_t)ub - 1024;
+  if (avail < 2 * (int64_t)stage_bytes) return false;
+  stages = (int)std::min<int64_t>(kMaxStages, avail / stage_bytes);
+  smem = (size_t)stages * stage_bytes + ub;
+  return true;
+}
+
+cudaError_t run_iterate_f64(const IterArgs<double>& a, int smem_limit, cudaStream_t st) {
+  int stages, sb;
+  size_t smem;
+  if (!plan_ring<double>(a.L, a.grid, smem_limit, stages, sb, smem)) return cudaErrorInvalidConfiguration;
+  return launch_iterate_t<double>(a, stages, sb, smem, st);
+}
+
+cudaError_t run_iterate_f32(const IterArgs<float>& a, int smem_limit, cudaStream_t st) {
+  int stages, sb;
+  size_t smem;
+  if (!plan_ring<float>(a.L, a.grid, smem_limit, stages, sb, smem)) return cudaErrorInvalidConfiguration;
+  return launch_iterate_t<float>(a, stages, sb, smem, st);
+}
+
+// ---------------------------------------------------------------------------
+// stand-alone products with the stored data (gdwd_apply): same passes
+// ---------------------------------------------------------------------------
+struct ApplyEpi {
+  double* out;
+  __device__ void row(int64_t j, double t, double) { out[j] = t; }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) applyA_kernel(Layout L, const double* x, typename ElemTraits<T>::compute_t* partial,
+                                                          int stages, int stage_bytes, int* err, uint64_t tmo) {
+  using CT = typename ElemTraits<T>::compute_t;
+  constexpr int VEC = ElemTraits<T>::kVec;
+  extern __shared__ __align__(128) uint8_t smem[];
+  __shared__ uint64_t s_bars[kMaxStages];
+  __shared__ int s_abort;
+  Ring rg{smem, s_bars, stages, stage_bytes, 0};
+  if (threadIdx.x == 0) s_abort = 0;
+  ring_init(rg);
+  CT* gp = reinterpret_cast<CT*>(smem + (size_t)stages * stage_bytes);
+  const int cta = blockIdx.x, grid = gridDim.x;
+  const int nmy = (L.NB > cta) ? (L.NB - cta + grid - 1) / grid : 0;
+  for (int k = 0; k < nmy; ++k) {
+    const int64_t s = cta + (int64_t)k * grid;
+    for (int j = threadIdx.x; j < L.TB; j += kThreads) {
+      const int64_t gj = s * L.TB + j;
+      gp[(size_t)k * L.TB + j] = (CT)(gj < L.d ? x[gj] : 0.0);
+    }
+  }
+  __syncthreads();
+  PassA<T> pa{gp, partial, L.TB, L.NB, L.TB / VEC, kThreads / L.CW};
+  stream_slabs<T>(L, rg, cta, grid, err, tmo, &s_abort, pa);
+}
+
+template <typename CT>
+__global__ void applyA_reduce(const CT* partial, const double* sc, int64_t n, int NB, double* out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = wid; i < n; i += nw) {
+    double acc = 0.0;
+    for (int s = lane; s < NB; s += 32) acc += (double)partial[(size_t)i * NB + s];
+    acc = warp_sum(acc);
+    if (lane == 0) out[i] = sc[i] * acc;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) applyB_kernel(Layout L, const double* x, const double* sc, double* out,
+                                                          int stages, int stage_bytes, int* err, uint64_t tmo) {
+  using CT = typename ElemTraits<T>::compute_t;
+  constexpr int VEC = ElemTraits<T>::kVec;
+  extern __shared__ __align__(128) uint8_t smem[];
+  __shared__ uint64_t s_bars[kMaxStages];
+  __shared__ int s_abort;
+  Ring rg{smem, s_bars, stages, stage_bytes, 0};
+  if (threadIdx.x == 0) s_abort = 0;
+  ring_init(rg);
+  uint8_t* uni = smem + (size_t)stages * stage_bytes;
+  CT* cv = reinterpret_cast<CT*>(uni);
+  double* red = reinterpret_cast<double*>(uni + ((2 * L.n * sizeof(CT) + 15) & ~(size_t)15));
+  for (int64_t i = threadIdx.x; i < L.n; i += kThreads) cv[i] = (CT)(sc[i] * x[i]);
+  __syncthreads();
+  const int Q = L.TB / VEC;
+  ApplyEpi epi{out};
+  PassB<T, ApplyEpi> pb;
+  pb.cv = cv;
+  pb.av = cv;
+  pb.red = red;
+  pb.TB = L.TB;
+  pb.Q = Q;
+  pb.G = Q <= kThreads ? kThreads / Q : 1;
+  pb.d = L.d;
+  pb.two = false;
+  pb.epi = &epi;
+  for (int kk = 0; kk < VEC; ++kk) {
+    pb.rc[kk].reset();
+    pb.ra[kk].reset();
+  }
+  stream_slabs<T>(L, rg, blockIdx.x, gridDim.x, err, tmo, &s_abort, pb);
+}
+
+template <typename T>
+static cudaError_t run_apply_t(const Layout& L, int trans, const double* x, const double* sc, double* out,
+                               void* partial, int grid, int smem_limit, int* err, uint64_t tmo, cudaStream_t st) {
+  using CT = typename ElemTraits<T>::compute_t;
+  int stages, sb;
+  size_t smem;
+  if (!plan_ring<T>(L, grid, smem_limit, stages, sb, smem)) return cudaErrorInvalidConfiguration;
+  if (trans) {
+    auto k = applyA_kernel<T>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, kThreads, smem, st>>>(L, x, (CT*)partial, stages, sb, err, tmo);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    applyA_reduce<CT><<<(int)std::min<int64_t>((L.n * 32 + 255) / 256, 1024), 256, 0, st>>>((const CT*)partial, sc, L.n,
+                                                                                      L.NB, out);
+    return cudaGetLastError();
+  }
+  auto k = applyB_kernel<T>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, kThreads, smem, st>>>(L, x, sc, out, stages, sb, err, tmo);
+  return cudaGetLastError();
+}
+
+cudaError_t run_apply(int store, const Layout& L, int trans, const double* x, const double* sc, double* out,
+                      void* partial, int grid, int smem_limit, int* err, uint64_t tmo, cudaStream_t st) {
+  if (store == GDWD_F64) return run_apply_t<double>(L, trans, x, sc, out, partial, grid, smem_limit, err, tmo, st);
+  return run_apply_t<float>(L, trans, x, sc, out, partial, grid, smem_limit, err, tmo, st);
+}
+
+}  // namespace gdwd

@@ -1,0 +1,209 @@
+// The two streaming passes over the stored Z, shared by the persistent
+// iteration kernel and the stand-alone product kernels (gdwd_apply).
+//
+//   pass A:  partial[i][s] = sum_{j in slab s} Zq_ji g'_j          (Z~^T g' before scaling)
+//   pass B:  t_j = sum_i Zq_ji cq_i,  ta_j = sum_i Zq_ji aq_i      (Z~ c, Z~ alpha)
+//
+// A CTA owns whole slabs (see Layout).  Chunks of CW columns of a slab are
+// contiguous in HBM and are fetched by one thread with cp.async.bulk into a
+// ring of `stages` shared-memory buffers, each guarded by an mbarrier with
+// transaction counting; all 256 threads consume a chunk, then thread 0 refills
+// the freed buffer.  Every wait is bounded.
+#pragma once
+
+#include "solver.cuh"
+
+namespace gdwd {
+
+struct Ring {
+  uint8_t* buf;        // stages * stage_bytes, 128-byte aligned
+  uint64_t* bars;      // stages mbarriers
+  int stages;
+  int stage_bytes;
+  uint32_t phase;      // parity bit per stage (identical in all threads)
+};
+
+__device__ __forceinline__ void ring_init(Ring& rg) {
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < rg.stages; ++s) mbar_init(&rg.bars[s], 1);
+    fence_mbar_init();
+  }
+  rg.phase = 0;
+  __syncthreads();
+}
+
+// Streams every chunk of the slabs cta, cta+grid, ... through the ring and
+// calls f.chunk / f.end_slab.  Returns false (all threads) on a timed-out wait.
+template <typename T, typename F>
+__device__ bool stream_slabs(const Layout& L, Ring& rg, int cta, int grid, int* err, uint64_t tmo, int* s_abort,
+                             F& f) {
+  const int nch = (int)((L.n + L.CW - 1) / L.CW);
+  const int nmy = (L.NB > cta) ? (L.NB - cta + grid - 1) / grid : 0;
+  const int total = nmy * nch;
+  const uint8_t* Zb = reinterpret_cast<const uint8_t*>(L.Z);
+  const int64_t col_bytes = (int64_t)L.TB * L.esize;
+
+  auto issue = [&](int c) {
+    const int k = c / nch, cc = c - k * nch;
+    const int64_t s = cta + (int64_t)k * grid;
+    const int64_t col0 = (int64_t)cc * L.CW;
+    const int64_t cw = min((int64_t)L.CW, L.n - col0);
+    const uint32_t bytes = (uint32_t)(cw * col_bytes);
+    const int st = c % rg.stages;
+    mbar_expect_tx(&rg.bars[st], bytes);
+    bulk_g2s(rg.buf + (size_t)st * rg.stage_bytes, Zb + (s * L.n + col0) * col_bytes, bytes, &rg.bars[st]);
+  };
+
+  if (threadIdx.x == 0) {
+    const int pre = min(rg.stages, total);
+    for (int c = 0; c < pre; ++c) issue(c);
+  }
+  for (int c = 0; c < total; ++c) {
+    const int st = c % rg.stages;
+    const int k = c / nch, cc = c - k * nch;
+    const int s = cta + k * grid;
+    const int col0 = cc * L.CW;
+    const int cw = (int)min((int64_t)L.CW, L.n - col0);
+    if (!mbar_wait(&rg.bars[st], (rg.phase >> st) & 1u, err, tmo)) *s_abort = 1;
+    rg.phase ^= 1u << st;
+    f.chunk(reinterpret_cast<const T*>(rg.buf + (size_t)st * rg.stage_bytes), k, s, col0, cw);
+    __syncthreads();
+    if (*(volatile int*)s_abort) return false;
+    if (threadIdx.x == 0 && c + rg.stages < total) issue(c + rg.stages);
+    if (cc == nch - 1) f.end_slab(k, s);
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// pass A: dots down the columns of each chunk.  H = 256 / CW threads share a
+// column (H >= 8, so 8 consecutive lanes read 8 consecutive 16-byte vectors of
+// one column: no shared-memory bank conflicts), then reduce by shuffles.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct PassA {
+  using CT = typename ElemTraits<T>::compute_t;
+  static constexpr int VEC = ElemTraits<T>::kVec;
+  const CT* gp;       // shared: my slabs' g' (slab k at gp + k * TB)
+  CT* partial;        // global n x NB
+  int TB, NB, Q, H;
+
+  __device__ void chunk(const T* buf, int k, int s, int col0, int cw) {
+    const int col = threadIdx.x / H, h = threadIdx.x % H;
+    CT acc = 0;
+    if (col < cw) {
+      const T* cp = buf + (size_t)col * TB;
+      const CT* g = gp + (size_t)k * TB;
+      for (int v = h; v < Q; v += H) {
+        CT e[VEC], gv[VEC];
+        ElemTraits<T>::load(cp + v * VEC, e);
+        ElemTraits<CT>::load(g + v * VEC, gv);
+#pragma unroll
+        for (int kk = 0; kk < VEC; ++kk) acc = fma(e[kk], gv[kk], acc);
+      }
+    }
+    for (int m = H >> 1; m >= 1; m >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, m);
+    if (h == 0 && col < cw) partial[(size_t)(col0 + col) * NB + s] = acc;
+  }
+  __device__ void end_slab(int, int) {}
+};
+
+// Running sums of pass B: FP64 storage accumulates in double, FP32 storage
+// accumulates each chunk in float and folds it into a double-float.
+template <typename CT>
+struct RunAcc;
+template <>
+struct RunAcc<double> {
+  double v = 0.0;
+  __device__ void fold(double c) { v += c; }
+  __device__ double get() const { return v; }
+  __device__ void reset() { v = 0.0; }
+};
+template <>
+struct RunAcc<float> {
+  df v{0.f, 0.f};
+  __device__ void fold(float c) { df_add(v, c); }
+  __device__ double get() const { return df_to_double(v); }
+  __device__ void reset() { v.hi = 0.f; v.lo = 0.f; }
+};
+
+// ---------------------------------------------------------------------------
+// pass B: axpys across the columns of each chunk for two right-hand sides.
+// Thread t owns vector qv = t % Q of the column group t / Q (Q = TB / VEC <= 256),
+// so the threads of a step read consecutive 16-byte vectors (conflict-free).
+// At the end of a slab the groups are summed through shared memory and the
+// row epilogue Epi runs once per row j of the slab with t_j and ta_j.
+// ---------------------------------------------------------------------------
+template <typename T, typename Epi>
+struct PassB {
+  using CT = typename ElemTraits<T>::compute_t;
+  static constexpr int VEC = ElemTraits<T>::kVec;
+  const CT* cv;       // shared n: coefficients of RHS 1
+  const CT* av;       // shared n: coefficients of RHS 2 (may equal cv)
+  double* red;        // shared 2 * G * TB
+  int TB, Q, G;
+  int64_t d;
+  bool two;           // second right-hand side present
+  Epi* epi;
+  RunAcc<CT> rc[VEC], ra[VEC];
+
+  __device__ void chunk(const T* buf, int k, int s, int col0, int cw) {
+    const int grp = threadIdx.x / Q, qv = threadIdx.x - grp * Q;
+    if (grp >= G) return;
+    CT ac[VEC], aa[VEC];
+#pragma unroll
+    for (int kk = 0; kk < VEC; ++kk) ac[kk] = aa[kk] = 0;
+    const T* base = buf + qv * VEC;
+    if (two) {
+      for (int col = grp; col < cw; col += G) {
+        CT e[VEC];
+        ElemTraits<T>::load(base + (size_t)col * TB, e);
+        const CT c = cv[col0 + col], a = av[col0 + col];
+#pragma unroll
+        for (int kk = 0; kk < VEC; ++kk) {
+          ac[kk] = fma(e[kk], c, ac[kk]);
+          aa[kk] = fma(e[kk], a, aa[kk]);
+        }
+      }
+    } else {
+      for (int col = grp; col < cw; col += G) {
+        CT e[VEC];
+        ElemTraits<T>::load(base + (size_t)col * TB, e);
+        const CT c = cv[col0 + col];
+#pragma unroll
+        for (int kk = 0; kk < VEC; ++kk) ac[kk] = fma(e[kk], c, ac[kk]);
+      }
+    }
+#pragma unroll
+    for (int kk = 0; kk < VEC; ++kk) {
+      rc[kk].fold(ac[kk]);
+      ra[kk].fold(aa[kk]);
+    }
+  }
+
+  __device__ void end_slab(int k, int s) {
+    const int grp = threadIdx.x / Q, qv = threadIdx.x - grp * Q;
+    if (grp < G) {
+#pragma unroll
+      for (int kk = 0; kk < VEC; ++kk) {
+        red[(size_t)grp * TB + qv * VEC + kk] = rc[kk].get();
+        red[(size_t)(G + grp) * TB + qv * VEC + kk] = ra[kk].get();
+        rc[kk].reset();
+        ra[kk].reset();
+      }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < TB; j += blockDim.x) {
+      double t = 0.0, ta = 0.0;
+      for (int gq = 0; gq < G; ++gq) {
+        t += red[(size_t)gq * TB + j];
+        ta += red[(size_t)(G + gq) * TB + j];
+      }
+      const int64_t gj = (int64_t)s * TB + j;
+      if (gj < d) epi->row(gj, t, ta);
+    }
+    __syncthreads();
+  }
+};
+
+}  // namespace gdwd

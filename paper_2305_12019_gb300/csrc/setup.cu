@@ -1,0 +1,477 @@
+// Set-up kernels of libgdwd (everything that does not depend on sigma or C):
+//
+//   ingest   ||Z||_F, finiteness check, copy into the slab layout (Sec. 4.2 scaling
+//            is carried by the per-column scale sc_i = 1 / Z_scale)
+//   gram     K = Zq^T Zq from the stored values, lower-triangular 64x64 tiles,
+//            FP32 products summed over 16-row chunks then folded into a
+//            double-float accumulator (FP64 for FP64 storage), deterministic
+//            split over d; G = I + sc_i sc_j K_ij / mu in FP64 (first block of J,
+//            eq-H, Sec. 3.3.2)
+//   factor   one cooperative launch: blocked right-looking FP64 Cholesky
+//            G = L L^T (32x32 tiles), X = L^{-1} by blocked forward substitution,
+//            P = X^T X = G^{-1}; p = P y, s = y^T p; P and p also stored as
+//            double-float pairs for the per-iteration solves
+#include <algorithm>
+
+#include "solver.cuh"
+
+namespace gdwd {
+
+// ------------------------------------------------------------------ ingest
+template <typename TI>
+__global__ void sumsq_kernel(const TI* __restrict__ Z, int64_t d, int64_t n, int64_t ldz, double* part,
+                             int* nonfinite) {
+  double acc = 0.0;
+  int bad = 0;
+  const int64_t total = d * n;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx / d, j = idx - i * d;
+    const double v = (double)Z[i * ldz + j];
+    if (!isfinite(v)) bad = 1;
+    acc = fma(v, v, acc);
+  }
+  __shared__ double s[32];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s[w];
+    part[blockIdx.x] = t;
+  }
+  if (bad) atomicOr(nonfinite, 1);
+}
+
+__global__ void sum_parts_kernel(const double* part, int np, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < np; ++i) t += part[i];
+    *out = t;
+  }
+}
+
+template <typename TI, typename TS>
+__global__ void to_slabs_kernel(const TI* __restrict__ Z, int64_t ldz, Layout L, TS* __restrict__ out) {
+  const int64_t per_slab = (int64_t)L.TB * L.n;
+  const int64_t total = per_slab * L.NB;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = idx / per_slab, rem = idx - s * per_slab;
+    const int64_t i = rem / L.TB, jl = rem - i * L.TB;
+    const int64_t j = s * L.TB + jl;
+    out[idx] = (j < L.d) ? (TS)Z[i * ldz + j] : (TS)0;
+  }
+}
+
+// sc_i = 1 / Z_scale, Z_scale = sqrt(||Z||_F)
+__global__ void scale_kernel(const double* sumsq, int64_t n, double* sc, double* zscale) {
+  const double zs = sqrt(sqrt(*sumsq));
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    sc[i] = 1.0 / zs;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *zscale = zs;
+}
+
+cudaError_t run_ingest(const void* Z, int zdt, int64_t ldz, const Layout& L, void* out, int store, double* part,
+                       int nparts, double* sumsq, int* nonfinite, double* sc, double* zscale, cudaStream_t st) {
+  if (zdt == GDWD_F64)
+    sumsq_kernel<double><<<nparts, 256, 0, st>>>((const double*)Z, L.d, L.n, ldz, part, nonfinite);
+  else
+    sumsq_kernel<float><<<nparts, 256, 0, st>>>((const float*)Z, L.d, L.n, ldz, part, nonfinite);
+  sum_parts_kernel<<<1, 32, 0, st>>>(part, nparts, sumsq);
+  const int blocks = 152 * 8;
+  if (zdt == GDWD_F64 && store == GDWD_F64)
+    to_slabs_kernel<double, double><<<blocks, 256, 0, st>>>((const double*)Z, ldz, L, (double*)out);
+  else if (zdt == GDWD_F64 && store == GDWD_F32)
+    to_slabs_kernel<double, float><<<blocks, 256, 0, st>>>((const double*)Z, ldz, L, (float*)out);
+  else if (zdt == GDWD_F32 && store == GDWD_F64)
+    to_slabs_kernel<float, double><<<blocks, 256, 0, st>>>((const float*)Z, ldz, L, (double*)out);
+  else
+    to_slabs_kernel<float, float><<<blocks, 256, 0, st>>>((const float*)Z, ldz, L, (float*)out);
+  scale_kernel<<<(int)std::min<int64_t>((L.n + 255) / 256, 1024), 256, 0, st>>>(sumsq, L.n, sc, zscale);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ gram
+constexpr int kGT = 64;   // output tile
+constexpr int kGK = 16;   // rows per chunk
+
+template <typename T>
+struct GramAcc;
+template <>
+struct GramAcc<float> {
+  float c[4][4];
+  df s[4][4];
+  __device__ void zero() {
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) { c[a][b] = 0.f; s[a][b] = df{0.f, 0.f}; }
+  }
+  __device__ void fold() {
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) { df_add(s[a][b], c[a][b]); c[a][b] = 0.f; }
+  }
+  __device__ double get(int a, int b) const { return df_to_double(s[a][b]); }
+};
+template <>
+struct GramAcc<double> {
+  double c[4][4];
+  __device__ void zero() {
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) c[a][b] = 0.0;
+  }
+  __device__ void fold() {}
+  __device__ double get(int a, int b) const { return c[a][b]; }
+};
+
+// Loads rows [r0, r0+16) of columns [c0, c0+64) of slab s into sm[16][64].
+template <typename T>
+__device__ __forceinline__ void gram_load(const T* slab, const Layout& L, int r0, int64_t c0, T (*sm)[kGT]) {
+  constexpr int V = 16 / sizeof(T);               // elements per 16-byte vector
+  constexpr int PER = kGK * kGT / kThreads;       // 4 elements per thread
+  const int t = threadIdx.x;
+  const int col = t / (kGK / PER);                // 0..63
+  const int k0 = (t % (kGK / PER)) * PER;         // 0,4,8,12
+  const int64_t gc = c0 + col;
+#pragma unroll
+  for (int v = 0; v < PER; v += V) {
+    const int rr = r0 + k0 + v;
+    T e[V];
+    if (gc < L.n && rr < L.TB) {
+      if constexpr (sizeof(T) == 4) {
+        const float4 x = *reinterpret_cast<const float4*>(slab + gc * L.TB + rr);
+        e[0] = x.x; e[1] = x.y; e[2] = x.z; e[3] = x.w;
+      } else {
+        const double2 x = *reinterpret_cast<const double2*>(slab + gc * L.TB + rr);
+        e[0] = x.x; e[1] = x.y;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < V; ++q) e[q] = (T)0;
+    }
+#pragma unroll
+    for (int q = 0; q < V; ++q) sm[k0 + v + q][col] = e[q];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) gram_kernel(Layout L, int T_tiles, int ksplit, double* Kpart) {
+  __shared__ __align__(16) T As[kGK][kGT];
+  __shared__ __align__(16) T Bs[kGK][kGT];
+  const int tile = blockIdx.x / ksplit, sp = blockIdx.x % ksplit;
+  // tile -> (I, J), I >= J, row-major over the lower triangle
+  int I = (int)((sqrt(8.0 * tile + 1.0) - 1.0) * 0.5);
+  while ((I + 1) * (I + 2) / 2 <= tile) ++I;
+  while (I * (I + 1) / 2 > tile) --I;
+  const int J = tile - I * (I + 1) / 2;
+  const int s0 = (int)((int64_t)L.NB * sp / ksplit), s1 = (int)((int64_t)L.NB * (sp + 1) / ksplit);
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  GramAcc<T> acc;
+  acc.zero();
+  const T* Zs = reinterpret_cast<const T*>(L.Z);
+  for (int s = s0; s < s1; ++s) {
+    const T* slab = Zs + (int64_t)s * L.TB * L.n;
+    for (int r0 = 0; r0 < L.TB; r0 += kGK) {
+      gram_load<T>(slab, L, r0, (int64_t)I * kGT, As);
+      gram_load<T>(slab, L, r0, (int64_t)J * kGT, Bs);
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < kGK; ++k) {
+        T a[4], b[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          a[q] = As[k][ty * 4 + q];
+          b[q] = Bs[k][tx * 4 + q];
+        }
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc.c[p][q] = fma(a[p], b[q], acc.c[p][q]);
+      }
+      acc.fold();
+      __syncthreads();
+    }
+  }
+  const int64_t n = L.n;
+  double* out = Kpart + (int64_t)sp * n * n;
+  for (int p = 0; p < 4; ++p)
+    for (int q = 0; q < 4; ++q) {
+      const int64_t i = (int64_t)I * kGT + ty * 4 + p, j = (int64_t)J * kGT + tx * 4 + q;
+      if (i < n && j < n && i >= j) out[i * n + j] = acc.get(p, q);
+    }
+}
+
+// G_ij = delta_ij + sc_i sc_j sum_split K_ij / mu, both triangles.
+__global__ void gram_finish_kernel(const double* Kpart, int ksplit, const double* sc, int64_t n, double inv_mu,
+                                   double* G) {
+  const int64_t total = n * n;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx / n, j = idx - i * n;
+    if (j > i) continue;
+    double k = 0.0;
+    for (int s = 0; s < ksplit; ++s) k += Kpart[(int64_t)s * total + idx];
+    const double g = (i == j ? 1.0 : 0.0) + sc[i] * sc[j] * k * inv_mu;
+    G[i * n + j] = g;
+    G[j * n + i] = g;
+  }
+}
+
+int gram_ksplit(const Layout& L, int sms) {
+  const int Tt = (int)((L.n + kGT - 1) / kGT);
+  const int tiles = Tt * (Tt + 1) / 2;
+  int ks = std::max(1, (2 * sms + tiles - 1) / tiles);
+  ks = std::min(ks, std::max(1, L.NB));
+  return std::min(ks, 16);
+}
+
+cudaError_t run_gram(int store, const Layout& L, int ksplit, double* Kpart, const double* sc, double mu, double* G,
+                     cudaStream_t st) {
+  const int Tt = (int)((L.n + kGT - 1) / kGT);
+  const int tiles = Tt * (Tt + 1) / 2;
+  if (store == GDWD_F64)
+    gram_kernel<double><<<tiles * ksplit, kThreads, 0, st>>>(L, Tt, ksplit, Kpart);
+  else
+    gram_kernel<float><<<tiles * ksplit, kThreads, 0, st>>>(L, Tt, ksplit, Kpart);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  gram_finish_kernel<<<1024, 256, 0, st>>>(Kpart, ksplit, sc, L.n, 1.0 / mu, G);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ factor
+constexpr int kNB = 32;   // tile of the blocked factorization
+
+// C[32x32] -= A[32xk] B[32xk]^T over k = 32, tiles in shared memory (row-major).
+__device__ __forceinline__ void tile_sub_abt(double (*C)[kNB + 1], const double (*Am)[kNB + 1],
+                                             const double (*Bm)[kNB + 1]) {
+  // 256 threads, 4 outputs each: rows r = t / 8 (0..31), cols c = (t % 8) + 8 * q
+  const int r = threadIdx.x >> 3, c0 = threadIdx.x & 7;
+  double acc[4] = {0, 0, 0, 0};
+#pragma unroll 8
+  for (int k = 0; k < kNB; ++k) {
+    const double a = Am[r][k];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = fma(a, Bm[c0 + 8 * q][k], acc[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) C[r][c0 + 8 * q] -= acc[q];
+}
+
+__device__ __forceinline__ void load_tile(double (*S)[kNB + 1], const double* M, int64_t n, int64_t r0, int64_t c0) {
+  for (int t = threadIdx.x; t < kNB * kNB; t += kThreads) {
+    const int r = t / kNB, c = t % kNB;
+    const int64_t gr = r0 + r, gc = c0 + c;
+    S[r][c] = (gr < n && gc < n) ? M[gr * n + gc] : (gr == gc ? 1.0 : 0.0);
+  }
+}
+
+__device__ __forceinline__ void store_tile(const double (*S)[kNB + 1], double* M, int64_t n, int64_t r0, int64_t c0) {
+  for (int t = threadIdx.x; t < kNB * kNB; t += kThreads) {
+    const int r = t / kNB, c = t % kNB;
+    const int64_t gr = r0 + r, gc = c0 + c;
+    if (gr < n && gc < n) M[gr * n + gc] = S[r][c];
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1) factor_kernel(FactorArgs a) {
+  __shared__ double T0[kNB][kNB + 1], T1[kNB][kNB + 1], T2[kNB][kNB + 1];
+  __shared__ int s_flag;
+  __shared__ double s_red[kWarps + 1];
+  const int64_t n = a.n;
+  const int nb = (int)((n + kNB - 1) / kNB);
+  const int cta = blockIdx.x, grid = a.grid;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned gen = 0;
+#define FBAR()                                                                          \
+  do {                                                                                  \
+    if (!grid_barrier(a.bar, (unsigned)grid, gen, a.err, a.timeout_ns, &s_flag)) return; \
+  } while (0)
+
+  // ---------------- Cholesky, right-looking, tile columns k = 0..nb-1
+  for (int k = 0; k < nb; ++k) {
+    const int64_t k0 = (int64_t)k * kNB;
+    if (cta == 0) {
+      load_tile(T0, a.A, n, k0, k0);
+      __syncthreads();
+      // unblocked Cholesky of the 32x32 diagonal tile by warp 0
+      if (warp == 0) {
+        for (int c = 0; c < kNB; ++c) {
+          double piv = T0[c][c];
+          if (!(piv > 0.0) || !isfinite(piv)) {
+            if (lane == 0) atomicCAS(a.err, 0, (int)GDWD_ENOTPD);
+            piv = 1.0;
+          }
+          const double lc = sqrt(piv);
+          __syncwarp();
+          // column c below the pivot
+          const int r = lane;
+          if (r > c) T0[r][c] /= lc;
+          __syncwarp();
+          if (lane == 0) T0[c][c] = lc;
+          __syncwarp();
+          // trailing update (lower part) of columns c+1..31
+          if (r > c)
+            for (int cc = c + 1; cc <= r; ++cc) T0[r][cc] -= T0[r][c] * T0[cc][c];
+          __syncwarp();
+        }
+      }
+      __syncthreads();
+      store_tile(T0, a.A, n, k0, k0);
+    }
+    FBAR();
+    // panel: rows i >= k0 + 32, L_ik = A_ik L_kk^{-T}; one warp per row
+    load_tile(T0, a.A, n, k0, k0);
+    __syncthreads();
+    for (int64_t i = k0 + kNB + (int64_t)cta * kWarps + warp; i < n; i += (int64_t)grid * kWarps) {
+      double x = (k0 + lane < n) ? a.A[i * n + k0 + lane] : 0.0;
+      for (int c = 0; c < kNB; ++c) {
+        const double xc = __shfl_sync(0xffffffffu, x, c) / T0[c][c];
+        if (lane == c) x = xc;
+        if (lane > c) x -= xc * T0[lane][c];
+      }
+      if (k0 + lane < n) a.A[i * n + k0 + lane] = x;
+    }
+    FBAR();
+    // trailing update of tiles (I, J), k < J <= I
+    {
+      const int m = nb - k - 1;
+      const int ntile = m * (m + 1) / 2;
+      for (int t = cta; t < ntile; t += grid) {
+        int ii = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+        while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
+        while (ii * (ii + 1) / 2 > t) --ii;
+        const int jj = t - ii * (ii + 1) / 2;
+        const int64_t I0 = (int64_t)(k + 1 + ii) * kNB, J0 = (int64_t)(k + 1 + jj) * kNB;
+        load_tile(T0, a.A, n, I0, J0);
+        load_tile(T1, a.A, n, I0, k0);
+        load_tile(T2, a.A, n, J0, k0);
+        __syncthreads();
+        tile_sub_abt(T0, T1, T2);
+        __syncthreads();
+        store_tile(T0, a.A, n, I0, J0);
+        __syncthreads();
+      }
+    }
+    FBAR();
+  }
+
+  // ---------------- X = L^{-1}: solve L X = I by tile rows; X starts as I
+  for (int64_t idx = (int64_t)cta * kThreads + threadIdx.x; idx < n * n; idx += (int64_t)grid * kThreads) {
+    const int64_t i = idx / n, j = idx - i * n;
+    a.X[idx] = (i == j) ? 1.0 : 0.0;
+  }
+  FBAR();
+  for (int k = 0; k < nb; ++k) {
+    const int64_t k0 = (int64_t)k * kNB;
+    // X[k-tile rows, columns < k0+32] = L_kk^{-1} X[...]: one warp per column
+    load_tile(T0, a.A, n, k0, k0);
+    __syncthreads();
+    const int64_t ncols = (n < k0 + kNB) ? n : k0 + kNB;
+    for (int64_t j = (int64_t)cta * kWarps + warp; j < ncols; j += (int64_t)grid * kWarps) {
+      double x = (k0 + lane < n) ? a.X[(k0 + lane) * n + j] : 0.0;
+      for (int c = 0; c < kNB; ++c) {
+        const double xc = __shfl_sync(0xffffffffu, x, c) / T0[c][c];
+        if (lane == c) x = xc;
+        if (lane > c) x -= xc * T0[lane][c];
+      }
+      if (k0 + lane < n) a.X[(k0 + lane) * n + j] = x;
+    }
+    FBAR();
+    // rows below: X[I, J] -= L[I, k] X[k, J] for tile rows I > k, tile columns J <= k
+    {
+      const int m = nb - k - 1;
+      const int ntile = m * (k + 1);
+      for (int t = cta; t < ntile; t += grid) {
+        const int ii = t / (k + 1), jj = t % (k + 1);
+        const int64_t I0 = (int64_t)(k + 1 + ii) * kNB, J0 = (int64_t)jj * kNB;
+        load_tile(T0, a.X, n, I0, J0);
+        load_tile(T1, a.A, n, I0, k0);
+        // T2 = X[k-tile, J-tile]^T so that tile_sub_abt computes L_Ik X_kJ
+        for (int q = threadIdx.x; q < kNB * kNB; q += kThreads) {
+          const int r = q / kNB, c = q % kNB;
+          const int64_t gr = k0 + c, gc = J0 + r;
+          T2[r][c] = (gr < n && gc < n) ? a.X[gr * n + gc] : 0.0;
+        }
+        __syncthreads();
+        tile_sub_abt(T0, T1, T2);
+        __syncthreads();
+        store_tile(T0, a.X, n, I0, J0);
+        __syncthreads();
+      }
+    }
+    FBAR();
+  }
+
+  // ---------------- P = X^T X (X lower triangular): P_IJ = sum_{M >= I} X_MI^T X_MJ, I >= J
+  {
+    const int ntile = nb * (nb + 1) / 2;
+    for (int t = cta; t < ntile; t += grid) {
+      int ii = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+      while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
+      while (ii * (ii + 1) / 2 > t) --ii;
+      const int jj = t - ii * (ii + 1) / 2;
+      const int64_t I0 = (int64_t)ii * kNB, J0 = (int64_t)jj * kNB;
+      for (int q = threadIdx.x; q < kNB * kNB; q += kThreads) T0[q / kNB][q % kNB] = 0.0;
+      for (int M = ii; M < nb; ++M) {
+        const int64_t M0 = (int64_t)M * kNB;
+        // T1[r][m] = X[M0+m][I0+r], T2[c][m] = X[M0+m][J0+c]; C -= -(...): accumulate with sign
+        for (int q = threadIdx.x; q < kNB * kNB; q += kThreads) {
+          const int r = q / kNB, c = q % kNB;
+          const int64_t gm = M0 + c;
+          T1[r][c] = (gm < n && I0 + r < n) ? -a.X[gm * n + I0 + r] : 0.0;
+          T2[r][c] = (gm < n && J0 + r < n) ? a.X[gm * n + J0 + r] : 0.0;
+        }
+        __syncthreads();
+        tile_sub_abt(T0, T1, T2);   // T0 -= (-X_MI^T) X_MJ
+        __syncthreads();
+      }
+      for (int q = threadIdx.x; q < kNB * kNB; q += kThreads) {
+        const int r = q / kNB, c = q % kNB;
+        const int64_t gi = I0 + r, gj = J0 + c;
+        if (gi < n && gj < n && gi >= gj) {
+          const double v = T0[r][c];
+          a.Pd[gi * n + gj] = v;
+          a.Pd[gj * n + gi] = v;
+          const df h = df_from(v);
+          a.P[gi * a.ldP + gj] = make_float2(h.hi, h.lo);
+          a.P[gj * a.ldP + gi] = make_float2(h.hi, h.lo);
+        }
+      }
+      __syncthreads();
+    }
+  }
+  FBAR();
+  // ---------------- p = P y (FP64), s = y^T p
+  for (int64_t i = (int64_t)cta * kWarps + warp; i < n; i += (int64_t)grid * kWarps) {
+    double acc = 0.0;
+    for (int64_t j = lane; j < n; j += 32) acc = fma(a.Pd[i * n + j], a.y[j], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      a.p[i] = acc;
+      const df h = df_from(acc);
+      a.pdf[i] = make_float2(h.hi, h.lo);
+    }
+  }
+  FBAR();
+  if (cta == 0) {
+    double acc = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += kThreads) acc = fma(a.y[i], a.p[i], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) s_red[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < kWarps; ++w) t += s_red[w];
+      *a.s_out = t;
+    }
+  }
+#undef FBAR
+}
+
+cudaError_t run_factor(const FactorArgs& a, cudaStream_t st) {
+  FactorArgs args = a;
+  void* params[] = {(void*)&args};
+  return cudaLaunchCooperativeKernel((const void*)factor_kernel, dim3(a.grid), dim3(kThreads), params, 0, st);
+}
+
+}  // namespace gdwd

@@ -1,0 +1,132 @@
+// Device data structures of libgdwd shared by the set-up and iteration kernels.
+#pragma once
+
+#include "common.cuh"
+
+namespace gdwd {
+
+// Slab layout of the stored Z in HBM.  The d rows are cut into NB slabs of TB
+// rows (the last one zero-padded); slab s is one contiguous block of n columns
+// of TB elements (column-major inside the slab).  One CTA streams a whole slab
+// as a sequence of contiguous chunks of CW columns with 1-D bulk copies, so
+// both products of an iteration -- Z~^T g' (dots down each column) and Z~ c
+// (axpys across columns) -- read Z once, linearly, with no cross-CTA traffic
+// except the n-vector of per-slab partial dots.
+struct Layout {
+  const void* Z;
+  int64_t d, n;
+  int TB;          // rows per slab (TB * esize % 16 == 0)
+  int NB;          // slabs
+  int CW;          // columns per streamed chunk
+  int esize;       // bytes per stored element
+};
+
+__host__ __device__ inline int64_t slab_elems(const Layout& L) { return (int64_t)L.TB * L.n; }
+
+// Number of scalar partial sums each CTA contributes per iteration.
+enum Scal {
+  S_RES2 = 0,   // ||Z~^T w + beta y + xi - r||^2
+  S_YA,         // y^T alpha
+  S_XICA,       // xi^T (C e - alpha)
+  S_AMS2,       // ||alpha - s||^2, s_i = omega_i / r_i^(q+1)
+  S_AMIN2,      // ||min(0, alpha)||^2
+  S_AMAX2,      // ||max(0, alpha - C e)||^2
+  S_PRIM_R,     // sum wt_i^q r_i^-q
+  S_PRIM_XI,    // sum e_i xi_i
+  S_DUAL_A,     // sum (wt_i alpha_i)^(q/(q+1))
+  S_G2,         // ||g||^2
+  S_GRHO,       // <g, rho>
+  S_RHO2,       // ||rho||^2
+  S_A2,         // ||a||^2, a = Z~ alpha + sqrt(mu)(1 - tau) rho
+  S_AG,         // <a, g>
+  S_TA2,        // ||Z~ alpha||^2
+  S_COUNT = 16
+};
+
+// Iteration control block (device memory, read back by the host).
+struct Ctrl {
+  double sigma;        // sigma for the next iteration
+  double sigma_prev;   // sigma the current (u, rho) update must use
+  double theta;        // ball-projection factor of the pending u update
+  double beta;         // beta of the last iterate
+  double pobj, dobj, kkt;
+  double eta_p1, eta_p2, eta_p3, eta_d1, eta_d2, eta_d3, eta_c1, eta_c2, eta_c3, eta_gap;
+  double wnorm;
+  int32_t it;          // iterations completed
+  int32_t status;      // gdwd_status of the solve
+  int32_t done;        // 1 once converged / failed
+  int32_t pending;     // 1: u, rho still hold the iterate before the deferred update
+};
+
+// Everything the persistent iteration kernel reads and writes.
+template <typename CT>
+struct IterArgs {
+  Layout L;
+  const double* sc;      // n: Z~_ji = sc_i * Zq_ji
+  const float2* P;       // n x ldP, G^{-1} as double-float (hi, lo) pairs
+  int ldP;
+  const float2* pdf;     // n: p = G^{-1} y as double-float
+  const double* p;       // n: p in FP64
+  const double* y;       // n labels
+  const double* e;       // n: penalty weights e_i
+  const double* omega;   // n: q * wt_i^q
+  const double* wt;      // n: wt_i
+  double inv_s;          // 1 / (y^T p)
+  double q, C, mu, tau, R, tol, kappa;
+  int max_iter;
+  int grid;
+  uint64_t timeout_ns;
+  // n-space state
+  double* r;
+  double* xi;
+  double* alpha;
+  double* b;
+  float2* rhsA;
+  float2* rhsB;
+  CT* cq;                // n: sc_i c_i   (pass B right-hand side 1)
+  CT* aq;                // n: sc_i alpha_i (pass B right-hand side 2)
+  // d-space state, NB*TB long (padding rows stay 0)
+  double* u;
+  double* rho;
+  double* g;
+  CT* partial;           // n x NB per-slab partial dots of pass A
+  double* scal;          // grid x S_COUNT
+  unsigned* bar;
+  int* err;
+  Ctrl* ctrl;
+};
+
+// Host-side launchers (defined in the .cu files).
+cudaError_t run_iterate_f64(const IterArgs<double>& a, int smem_limit, cudaStream_t st);
+cudaError_t run_iterate_f32(const IterArgs<float>& a, int smem_limit, cudaStream_t st);
+cudaError_t run_apply(int store, const Layout& L, int trans, const double* x, const double* sc, double* out,
+                      void* partial, int grid, int smem_limit, int* err, uint64_t tmo, cudaStream_t st);
+
+// set-up (setup.cu)
+struct FactorArgs {
+  double* A;          // n x n working copy of G (row-major); L in the lower triangle on exit
+  double* X;          // n x n: L^{-1} (lower) on exit
+  double* Pd;         // n x n FP64 G^{-1}
+  float2* P;          // n x ldP double-float G^{-1} (padding zero)
+  int ldP;
+  const double* y;
+  double* p;          // n: p = G^{-1} y
+  float2* pdf;        // n: p as double-float
+  double* s_out;      // y^T p
+  int64_t n;
+  int grid;
+  unsigned* bar;
+  int* err;
+  uint64_t timeout_ns;
+};
+cudaError_t run_ingest(const void* Z, int zdt, int64_t ldz, const Layout& L, void* out, int store, double* part,
+                       int nparts, double* sumsq, int* nonfinite, double* sc, double* zscale, cudaStream_t st);
+int gram_ksplit(const Layout& L, int sms);
+cudaError_t run_gram(int store, const Layout& L, int ksplit, double* Kpart, const double* sc, double mu, double* G,
+                     cudaStream_t st);
+cudaError_t run_factor(const FactorArgs& a, cudaStream_t st);
+
+cudaError_t launch_prox(const double* a, const double* r0, const double* omega, double sigma, double q,
+                        int64_t n, double* out, cudaStream_t st);
+
+}  // namespace gdwd

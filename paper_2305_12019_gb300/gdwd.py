@@ -1,0 +1,212 @@
+"""ctypes binding of libgdwd (include/gdwd.h).
+
+Argument marshalling only: every step of the solver runs in the CUDA library.
+The library is loaded on first use; if it cannot be loaded (not built, or no
+CUDA driver) the calls raise -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_int32, c_int64, c_void_p
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgdwd.so")
+
+F64, F32, BF16, F16, E4M3 = 0, 1, 2, 3, 4
+DTYPES = {"f64": F64, "f32": F32, "bf16": BF16, "f16": F16, "e4m3": E4M3}
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ENOTPD", 4: "EMAXITER", 5: "ENUMERIC", 6: "ETIMEOUT",
+          7: "ECUDA", 8: "EUNSUPPORTED"}
+OK, EMAXITER = 0, 4
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("mu", c_double), ("tau", c_double), ("tol", c_double), ("sigma0", c_double),
+                ("timeout_s", c_double), ("max_iter", c_int32), ("store", c_int32), ("grid", c_int32),
+                ("block_rows", c_int32), ("stream", c_void_p), ("reserved", c_int64 * 8)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("beta", c_double), ("primal_obj", c_double), ("dual_obj", c_double), ("kkt", c_double),
+                ("eta_p", c_double), ("eta_d", c_double), ("eta_c", c_double), ("eta_gap", c_double),
+                ("sigma", c_double), ("zscale", c_double), ("t_setup_ms", c_double), ("t_solve_ms", c_double),
+                ("iters", c_int32), ("status", c_int32), ("reserved", c_int64 * 4)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("d", c_int64), ("n", c_int64), ("store", c_int32), ("block_rows", c_int32), ("slabs", c_int32),
+                ("grid", c_int32), ("z_bytes", c_int64), ("device_bytes", c_int64), ("zscale", c_double),
+                ("t_setup_ms", c_double), ("reserved", c_int64 * 4)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+EXPORTS = ["gdwd_default_options", "gdwd_create", "gdwd_solve", "gdwd_free", "gdwd_last_error", "gdwd_prox",
+           "gdwd_apply", "gdwd_gram", "gdwd_get_info"]
+
+_lib = None
+
+
+class GdwdError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def load(path: str = LIB_PATH):
+    """Loads libgdwd.so (raises if it is missing) and declares the signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libgdwd.so not built at {path}: run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    lib.gdwd_default_options.argtypes = [POINTER(Options)]
+    lib.gdwd_create.argtypes = [c_void_p, c_int32, c_int64, c_int64, c_int64, c_int32, POINTER(c_double), c_double,
+                                c_double, POINTER(Options), POINTER(c_void_p)]
+    lib.gdwd_solve.argtypes = [c_void_p, POINTER(c_double), c_int32, c_void_p, c_int32, c_void_p, POINTER(Result)]
+    lib.gdwd_free.argtypes = [c_void_p]
+    lib.gdwd_last_error.argtypes = [c_void_p]
+    lib.gdwd_last_error.restype = ctypes.c_char_p
+    lib.gdwd_prox.argtypes = [c_void_p, c_void_p, c_void_p, c_double, c_double, c_int64, c_void_p, c_void_p]
+    lib.gdwd_apply.argtypes = [c_void_p, c_int32, c_void_p, c_void_p]
+    lib.gdwd_gram.argtypes = [c_void_p, c_void_p]
+    lib.gdwd_get_info.argtypes = [c_void_p, POINTER(Info)]
+    for name in EXPORTS:
+        if name != "gdwd_last_error":
+            getattr(lib, name).restype = c_int32
+    _lib = lib
+    return lib
+
+
+def _check(status, handle=None):
+    if status not in (OK,):
+        msg = _lib.gdwd_last_error(handle).decode(errors="replace")
+        raise GdwdError(status, msg)
+
+
+def default_options() -> Options:
+    o = Options()
+    load().gdwd_default_options(ctypes.byref(o))
+    return o
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+class Solver:
+    """One gDWD data set on the device (gdwd_create) and its solves (gdwd_solve).
+
+    Z is d x n with column i = y_i x_i: a numpy array (host; copied inside the
+    call) or a torch tensor (CUDA or pinned host memory) laid out column-major,
+    i.e. Z.stride(0) == 1 (for example ``X_rows.T`` of an n x d row-major tensor).
+    """
+
+    def __init__(self, Z, y, q, C, *, store="f32", mu=1.0, tau=1.618, tol=1e-6, sigma0=0.0, max_iter=20000,
+                 timeout_s=2.0, grid=0, block_rows=0, stream=None):
+        lib = load()
+        self._h = c_void_p()
+        o = default_options()
+        o.mu, o.tau, o.tol, o.sigma0 = mu, tau, tol, sigma0
+        o.max_iter, o.timeout_s = max_iter, timeout_s
+        o.store = DTYPES[store] if isinstance(store, str) else int(store)
+        o.grid, o.block_rows = grid, block_rows
+        o.stream = stream
+        self._stream = stream
+        yv = np.ascontiguousarray(np.asarray(y, dtype=np.float64))
+        if _is_torch(Z):
+            if Z.dim() != 2 or Z.stride(0) != 1:
+                raise ValueError("torch Z must be d x n column-major (stride(0) == 1)")
+            zdt = F64 if str(Z.dtype) == "torch.float64" else F32
+            if str(Z.dtype) not in ("torch.float64", "torch.float32"):
+                raise ValueError("Z must be float32 or float64")
+            d, n = Z.shape
+            ldz = Z.stride(1) if n > 1 else d
+            ptr, on_dev = Z.data_ptr(), int(Z.is_cuda)
+            self._keep = Z
+        else:
+            Zn = np.asarray(Z)
+            if Zn.dtype not in (np.float32, np.float64):
+                Zn = Zn.astype(np.float64)
+            Zn = np.asfortranarray(Zn)
+            zdt = F64 if Zn.dtype == np.float64 else F32
+            d, n = Zn.shape
+            ldz = d
+            ptr, on_dev = Zn.ctypes.data, 0
+            self._keep = Zn
+        self.d, self.n, self.q, self.C = int(d), int(n), float(q), float(C)
+        st = lib.gdwd_create(c_void_p(ptr), zdt, d, n, ldz, on_dev, yv.ctypes.data_as(POINTER(c_double)), q, C,
+                             ctypes.byref(o), ctypes.byref(self._h))
+        self._keep = None
+        _check(st, None)
+
+    def solve(self, Cs=None, w_out=None, alpha=False):
+        """Runs gdwd_solve.  Returns (results, w, alpha_or_None); w is a host (d, k)
+        array unless w_out (a CUDA float64 tensor of d*k elements) is given."""
+        Cs_arr = None if Cs is None else np.ascontiguousarray(np.atleast_1d(np.asarray(Cs, dtype=np.float64)))
+        k = 1 if Cs_arr is None else Cs_arr.size
+        res = (Result * k)()
+        if w_out is not None:
+            w_ptr, w_dev, w_host = w_out.data_ptr(), 1, None
+        else:
+            w_host = np.zeros((k, self.d), dtype=np.float64)
+            w_ptr, w_dev = w_host.ctypes.data, 0
+        a_host = np.zeros((k, self.n), dtype=np.float64) if alpha else None
+        st = _lib.gdwd_solve(self._h, None if Cs_arr is None else Cs_arr.ctypes.data_as(POINTER(c_double)),
+                             0 if Cs_arr is None else k, c_void_p(w_ptr), w_dev,
+                             c_void_p(a_host.ctypes.data) if alpha else None, res)
+        if st not in (OK, EMAXITER):
+            _check(st, self._h)
+        out = [r.as_dict() for r in res]
+        return out, (w_out if w_host is None else w_host.T.copy()), (None if a_host is None else a_host.T.copy())
+
+    def apply(self, x, out, trans):
+        """out = Z~^T x (trans) or Z~ x on CUDA float64 tensors."""
+        _check(_lib.gdwd_apply(self._h, int(bool(trans)), c_void_p(x.data_ptr()), c_void_p(out.data_ptr())), self._h)
+        return out
+
+    def gram(self):
+        G = np.zeros((self.n, self.n), dtype=np.float64)
+        _check(_lib.gdwd_gram(self._h, c_void_p(G.ctypes.data)), self._h)
+        return G
+
+    def info(self):
+        i = Info()
+        _check(_lib.gdwd_get_info(self._h, ctypes.byref(i)), self._h)
+        return i.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.gdwd_free(self._h)
+            self._h = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def prox(a, sigma, q, r0=None, omega=None, out=None, stream=None):
+    """Step-1b prox on CUDA float64 tensors (gdwd_prox)."""
+    lib = load()
+    import torch
+    out = torch.empty_like(a) if out is None else out
+    st = lib.gdwd_prox(c_void_p(a.data_ptr()), None if r0 is None else c_void_p(r0.data_ptr()),
+                       None if omega is None else c_void_p(omega.data_ptr()), float(sigma), float(q), a.numel(),
+                       c_void_p(out.data_ptr()), stream)
+    _check(st, None)
+    return out

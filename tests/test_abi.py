@@ -1,0 +1,84 @@
+"""The C-ABI library builds, loads and exports every function include/gdwd.h declares;
+argument checks that need no GPU reject bad input with GDWD_EINVAL."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2305_12019_gb300 import build, gdwd
+    build.build()
+    return gdwd.load()
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "gdwd.h")).read()
+    # function declarations: a return type at the start of a line, then the name and "("
+    return sorted(set(re.findall(r"^(?:gdwd_status|const char\s*\*)\s*(gdwd_\w+)\s*\(", txt, re.M)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert "gdwd_create" in names and "gdwd_solve" in names and "gdwd_free" in names
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_struct_sizes_match_header():
+    from paper_2305_12019_gb300 import gdwd
+    # sizes implied by the header's field lists (LP64)
+    assert ctypes.sizeof(gdwd.Options) == 5 * 8 + 4 * 4 + 8 + 8 * 8
+    assert ctypes.sizeof(gdwd.Result) == 12 * 8 + 2 * 4 + 4 * 8
+    assert ctypes.sizeof(gdwd.Info) == 2 * 8 + 4 * 4 + 2 * 8 + 2 * 8 + 4 * 8
+
+
+def test_default_options(lib):
+    from paper_2305_12019_gb300 import gdwd
+    o = gdwd.default_options()
+    assert o.mu == 1.0 and o.tau == 1.618 and o.tol == 1e-6 and o.max_iter == 20000 and o.store == gdwd.F32
+    assert lib.gdwd_default_options(None) == 1
+
+
+def _create(lib, Z, y, q=1.0, C=1.0, zdt=0, d=None, n=None, ldz=None, opts=None):
+    from paper_2305_12019_gb300 import gdwd
+    h = ctypes.c_void_p()
+    d = Z.shape[0] if d is None else d
+    n = Z.shape[1] if n is None else n
+    ldz = d if ldz is None else ldz
+    yy = np.ascontiguousarray(y, dtype=np.float64)
+    return lib.gdwd_create(ctypes.c_void_p(Z.ctypes.data), zdt, d, n, ldz, 0,
+                           yy.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), q, C,
+                           None if opts is None else ctypes.byref(opts), ctypes.byref(h)), h
+
+
+def test_invalid_arguments_rejected(lib):
+    from paper_2305_12019_gb300 import gdwd
+    Z = np.asfortranarray(np.ones((5, 4)))
+    y = np.array([1.0, -1.0, 1.0, -1.0])
+    cases = [
+        dict(d=0), dict(n=1), dict(ldz=3), dict(q=0.0), dict(q=-1.0), dict(C=0.0), dict(C=float("nan")),
+        dict(zdt=7),
+    ]
+    for kw in cases:
+        st, h = _create(lib, Z, y, **kw)
+        assert st == 1, kw
+        assert h.value is None
+    st, h = _create(lib, Z, np.array([1.0, 1.0, 1.0, 1.0]))
+    assert st == 1 and b"both classes" in lib.gdwd_last_error(None)
+    st, h = _create(lib, Z, np.array([1.0, 0.0, 1.0, -1.0]))
+    assert st == 1 and b"labels" in lib.gdwd_last_error(None)
+    o = gdwd.default_options()
+    o.tau = 1.7
+    assert _create(lib, Z, y, opts=o)[0] == 1
+    o = gdwd.default_options()
+    o.store = gdwd.BF16
+    assert _create(lib, Z, y, opts=o)[0] == 8
+    assert lib.gdwd_free(None) == 0
+    assert lib.gdwd_solve(None, None, 0, None, 0, None, None) == 1
+    assert lib.gdwd_prox(None, None, None, 1.0, -1.0, 4, None, None) == 1

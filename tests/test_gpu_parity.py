@@ -1,0 +1,198 @@
+"""GPU parity: the CUDA path through the C-ABI against the FP64 CPU oracle.
+
+Component parity (element by element): the Step-1b prox, the Gram matrix
+G = I + Z~^T Z~ / mu of the SMW2 set-up, and the two streaming products
+Z~^T x / Z~ x.  Solution parity: gdwd_solve against oracle.solve on seeded
+synthetic problems at sizes that span several slabs, tiles and a ragged tail,
+then the full spiked FP32 workload (d = 20000, n = 1000) against the oracle and
+the weak-duality certificate.
+
+Tolerances (the spec acceptance): |d obj|/|obj| <= 1e-6,
+||dw||/||w|| <= 1e-4, identical held-out predictions except near-ties
+(|w^T x + beta| < 1e-6 ||x||), kkt <= tol.
+"""
+import numpy as np
+import pytest
+
+from oracle import gdwd_oracle as O
+from paper_2305_12019_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+OBJ_TOL = 1e-6
+W_TOL = 1e-4
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _predictions_match(Xt, w_gpu, b_gpu, w_ref, b_ref):
+    s_gpu = Xt.T @ w_gpu + b_gpu
+    s_ref = Xt.T @ w_ref + b_ref
+    tie = np.abs(s_ref) < 1e-6 * np.linalg.norm(Xt, axis=0)
+    return np.array_equal(np.sign(s_gpu[~tie]), np.sign(s_ref[~tie])), int(tie.sum())
+
+
+def _compare(res, w, ref, obj_tol=OBJ_TOL, w_tol=W_TOL):
+    relobj = abs(res["primal_obj"] - ref["primal"]) / abs(ref["primal"])
+    relw = np.linalg.norm(w - ref["w"]) / np.linalg.norm(ref["w"])
+    assert relobj <= obj_tol, relobj
+    assert relw <= w_tol, relw
+    return relobj, relw
+
+
+# --------------------------------------------------------------------- components
+
+@pytest.mark.parametrize("q", [0.5, 1.0, 2.0, 4.0, 3.0])
+def test_prox_parity(gdwd_lib, q):
+    torch = _torch()
+    rng = np.random.default_rng(int(q * 10))
+    n = 20011
+    a = np.concatenate([rng.uniform(-1e3, 1e3, n // 2), rng.uniform(-3, 3, n - n // 2)])
+    r0 = np.where(rng.random(n) < 0.5, rng.uniform(1e-3, 10, n), -1.0)
+    om = rng.uniform(0.2, 5.0, n)
+    for sigma in [1e-3, 0.37, 1.0, 250.0]:
+        ad, rd, od = (torch.tensor(v, device="cuda") for v in (a, r0, om))
+        got = gdwd_lib.prox(ad, sigma, q, r0=rd, omega=od).cpu().numpy()
+        ref = O.prox_r(a, sigma, q, r0=np.where(r0 > 0, r0, np.nan), omega=om)
+        assert np.all(got > 0)
+        rel = np.abs(got - ref) / ref
+        assert rel.max() <= 1e-12, (q, sigma, rel.max())
+    got0 = gdwd_lib.prox(torch.zeros(0, dtype=torch.float64, device="cuda"), 1.0, q)
+    assert got0.numel() == 0
+
+
+@pytest.mark.parametrize("store,d,n", [("f64", 3001, 257), ("f32", 3001, 257), ("f32", 9000, 130),
+                                       ("f64", 37, 300)])
+def test_gram_parity(gdwd_lib, store, d, n):
+    rng = np.random.default_rng(d + n)
+    y = np.where(np.arange(n) % 3 == 0, 1.0, -1.0)
+    X = rng.standard_normal((d, n))
+    if store == "f32":
+        X = X.astype(np.float32).astype(np.float64)
+    Z = X * y
+    mu = 0.7
+    with gdwd_lib.Solver(Z.astype(np.float32) if store == "f32" else Z, y, 1.0, 1.0, store=store, mu=mu) as s:
+        G = s.gram()
+        zs = s.info()["zscale"]
+    Zt, zs_ref = O.scale_data(Z)
+    Gref = np.eye(n) + Zt.T @ Zt / mu
+    assert abs(zs - zs_ref) <= 1e-13 * zs_ref
+    err = np.abs(G - Gref).max() / np.abs(Gref).max()
+    assert err <= (1e-13 if store == "f64" else 1e-9), err
+    assert np.array_equal(G, G.T)
+
+
+@pytest.mark.parametrize("store,d,n", [("f64", 5003, 301), ("f32", 20000, 1000), ("f32", 333, 77)])
+def test_apply_parity(gdwd_lib, store, d, n):
+    torch = _torch()
+    rng = np.random.default_rng(5)
+    y = np.where(np.arange(n) < n // 2, 1.0, -1.0)
+    X = rng.standard_normal((d, n))
+    if store == "f32":
+        X = X.astype(np.float32).astype(np.float64)
+    Z = X * y
+    Zt, _ = O.scale_data(Z)
+    with gdwd_lib.Solver(Z.astype(np.float32) if store == "f32" else Z, y, 1.0, 1.0, store=store) as s:
+        xd = rng.standard_normal(d)
+        xn = rng.standard_normal(n)
+        out_n = torch.zeros(n, dtype=torch.float64, device="cuda")
+        out_d = torch.zeros(d, dtype=torch.float64, device="cuda")
+        s.apply(torch.tensor(xd, device="cuda"), out_n, trans=True)
+        s.apply(torch.tensor(xn, device="cuda"), out_d, trans=False)
+    ref_n = Zt.T @ xd
+    ref_d = Zt @ xn
+    # FP32 streams: products rounded to FP32 against an FP64 reference
+    tol = 1e-13 if store == "f64" else 2e-6
+    scale_n = np.abs(Zt).T @ np.abs(xd)
+    scale_d = np.abs(Zt) @ np.abs(xn)
+    assert np.max(np.abs(out_n.cpu().numpy() - ref_n) / scale_n) <= tol
+    assert np.max(np.abs(out_d.cpu().numpy() - ref_d) / scale_d) <= tol
+
+
+# --------------------------------------------------------------------- whole solves
+
+def test_plain_fp64_workload(gdwd_lib):
+    """d=500, n=100, N(+-0.5 e1, I), q=1, C=1, sigma0=1, tol 1e-9, FP64."""
+    inst = synth.plain_fp64()
+    ref = O.solve(inst.Z, inst.y, inst.q, inst.C, sigma0=1.0, tol=1e-10)
+    with gdwd_lib.Solver(inst.Z, inst.y, inst.q, inst.C, store="f64", sigma0=1.0, tol=inst.tol) as s:
+        res, w, alpha = s.solve(alpha=True)
+    r = res[0]
+    assert r["status"] == 0 and r["kkt"] <= inst.tol, r
+    _compare(r, w[:, 0], ref)
+    assert abs(r["beta"] - ref["beta"]) <= 1e-5 * (1 + abs(ref["beta"]))
+    assert np.allclose(alpha[:, 0], ref["alpha"], rtol=1e-5, atol=1e-8)
+    ok, ties = _predictions_match(inst.Xtest, w[:, 0], r["beta"], ref["w"], ref["beta"])
+    assert ok
+    # the certificate on the GPU output alone
+    up, lo, gap = O.certified_gap(inst.Z, inst.y, w[:, 0], r["beta"], alpha[:, 0], inst.q, inst.C)
+    assert gap <= 1e-8
+
+
+@pytest.mark.parametrize("q,store,d,n,n_pos,C", [
+    (1.0, "f32", 4001, 203, 101, 10.0),
+    (0.5, "f64", 2500, 157, 40, 2.0),
+    (2.0, "f32", 6007, 311, 200, 5.0),
+    (4.0, "f64", 1201, 96, 70, 1.0),
+])
+def test_small_solves_match_oracle(gdwd_lib, q, store, d, n, n_pos, C):
+    inst = synth.gaussian(seed=d + n, d=d, n=n, shift=1.0, n_pos=n_pos, q=q, C=C, m_test=500,
+                          dtype=np.float32 if store == "f32" else np.float64)
+    Z = inst.Z
+    tol = 1e-8 if store == "f64" else 1e-6
+    ref = O.solve(Z.astype(np.float64), inst.y, q, C, tol=1e-9)
+    with gdwd_lib.Solver(Z, inst.y, q, C, store=store, tol=tol) as s:
+        res, w, alpha = s.solve(alpha=True)
+    r = res[0]
+    assert r["status"] == 0 and r["kkt"] <= tol, r
+    _compare(r, w[:, 0], ref)
+    ok, _ = _predictions_match(inst.Xtest.astype(np.float64), w[:, 0], r["beta"], ref["w"], ref["beta"])
+    assert ok
+    up, lo, gap = O.certified_gap(Z.astype(np.float64), inst.y, w[:, 0], r["beta"], alpha[:, 0], q, C)
+    assert gap <= 10 * tol
+
+
+def test_c_grid_sequential(gdwd_lib):
+    """One handle, several C (the factor does not depend on C)."""
+    inst = synth.gaussian(seed=77, d=3000, n=150, shift=1.0, q=1.0, C=1.0, dtype=np.float64)
+    Cs = [0.1, 1.0, 10.0]
+    with gdwd_lib.Solver(inst.Z, inst.y, 1.0, 1.0, store="f64", tol=1e-8) as s:
+        res, w, _ = s.solve(Cs=Cs)
+    for k, C in enumerate(Cs):
+        ref = O.solve(inst.Z, inst.y, 1.0, C, tol=1e-9)
+        assert res[k]["status"] == 0
+        _compare(res[k], w[:, k], ref)
+
+
+def test_spiked_fp32_full_size(gdwd_lib):
+    """The full d=20000, n=1000 spiked FP32 workload against the oracle and the certificate."""
+    inst = synth.spiked_fp32()
+    Z = inst.Z
+    with gdwd_lib.Solver(Z, inst.y, inst.q, inst.C, store="f32", tol=inst.tol) as s:
+        res, w, alpha = s.solve(alpha=True)
+        info = s.info()
+    r = res[0]
+    assert r["status"] == 0 and r["kkt"] <= inst.tol, r
+    assert info["slabs"] <= info["grid"] * 2
+    Z64 = Z.astype(np.float64)
+    up, lo, gap = O.certified_gap(Z64, inst.y, w[:, 0], r["beta"], alpha[:, 0], inst.q, inst.C)
+    assert gap <= 1e-5, gap
+    ref = O.solve(Z64, inst.y, inst.q, inst.C, tol=1e-8)
+    _compare(r, w[:, 0], ref)
+    ok, _ = _predictions_match(inst.Xtest.astype(np.float64), w[:, 0], r["beta"], ref["w"], ref["beta"])
+    assert ok
+
+
+def test_invalid_and_edge_cases(gdwd_lib):
+    """Two samples (the smallest n), one feature, and a host-side rejection."""
+    X = np.array([[1.0, -1.0]])
+    y = np.array([1.0, -1.0])
+    with gdwd_lib.Solver(X * y, y, 1.0, 10.0, store="f64", tol=1e-9) as s:
+        res, w, _ = s.solve()
+    assert res[0]["status"] == 0
+    assert abs(w[0, 0] - 1.0) <= 1e-6 and abs(res[0]["beta"]) <= 1e-6
+    with pytest.raises(gdwd_lib.GdwdError):
+        gdwd_lib.Solver(np.ones((3, 2)), np.array([1.0, 1.0]), 1.0, 1.0)

@@ -81,7 +81,10 @@ def test_gram_parity(gdwd_lib, store, d, n):
     Gref = np.eye(n) + Zt.T @ Zt / mu
     assert abs(zs - zs_ref) <= 1e-13 * zs_ref
     err = np.abs(G - Gref).max() / np.abs(Gref).max()
-    assert err <= (1e-13 if store == "f64" else 1e-9), err
+    # FP32 storage: products are rounded to FP32 and summed in FP32 over 16-row
+    # chunks before the double-float fold, ~16 * 2^-24 per chunk relative, random
+    # over d/16 chunks: a few 1e-8 of the largest entry.  FP64 storage: FP64 sums.
+    assert err <= (1e-13 if store == "f64" else 5e-8), err
     assert np.array_equal(G, G.T)
 
 

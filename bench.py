@@ -206,6 +206,7 @@ def main():
         with gdwd.Solver(Zd, y, inst.q, inst.C, store="f32", tol=inst.tol, stream=stream) as s:
             res, _, _ = s.solve(w_out=wdev)
             info = s.info()
+            info["phase_ns"] = s.phase_times()
         return res[0], info
 
     def step_e2e():
@@ -285,7 +286,8 @@ def main():
             "roofline": roof, "clocks": clk.summary(),
             "detail": {"setup_ms": t_setup_ms, "iterate_ms": t_iter_ms, "iterations": iters,
                        "step_ms": step_ms, "wall_s": wall, "grid": info["grid"], "slabs": info["slabs"],
-                       "block_rows": info["block_rows"], "kkt": [r["kkt"] for r in results]}}
+                       "block_rows": info["block_rows"], "kkt": [r["kkt"] for r in results],
+                       "phase_us_per_iter": {k: v / 1e3 / iters for k, v in info["phase_ns"].items()}}}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         t_or, ref = run_oracle_solve(inst)
         line["cpu_baseline"] = {"value": 1.0 / t_or, "unit": UNIT, "cores": len(os.sched_getaffinity(0)),

@@ -180,6 +180,17 @@ typedef struct {
 
 gdwd_status gdwd_get_info(const gdwd_handle* h, gdwd_info* info);
 
+/*
+ * Device-side time of the last solve of h split by phase of the persistent
+ * iteration kernel, as seen by its first CTA (globaltimer, nanoseconds summed
+ * over iterations): ns[2k] = time in phase k, ns[2k+1] = the grid-barrier wait
+ * that follows it, for k = A (Z^T g' stream), R (reduction), N1 (first n-space
+ * solve and Step 1b), N2 (second solve, Steps 2-3), B (Z c stream); ns[10] =
+ * the KKT / sigma phase.  count (<= 12) entries are written to ns (host).
+ * Diagnostics only; the paper has no counterpart.  Errors: EINVAL.
+ */
+gdwd_status gdwd_get_phase_times(const gdwd_handle* h, double* ns, int32_t count);
+
 #ifdef __cplusplus
 }
 #endif

@@ -261,9 +261,12 @@ def prox_r(a, sigma, q, r0=None, omega=None, max_iter=100):
         hi_i = np.where(f > 0, si, hi_i)
         lo[i], hi[i] = lo_i, hi_i
         newton = si * (kq[i] * (q + 2.0) + a[i] * si ** (q + 1.0)) / (kq[i] * (q + 1.0) + si ** (q + 2.0))
+        # converged: the Newton correction itself is below 4 eps (tested before the
+        # bracket safeguard, so rounding noise of f at the root never forces a bisection)
+        small = np.abs(newton - si) <= 4.0 * EPS * si
         inside = (newton > lo_i) & (newton < hi_i)
-        cand = np.where(inside, newton, 0.5 * (lo_i + hi_i))
-        done = (np.abs(cand - si) <= 4.0 * EPS * cand) | (f == 0)
+        cand = np.where(inside | small, newton, 0.5 * (lo_i + hi_i))
+        done = small | (f == 0)
         s[i] = np.where(f == 0, si, cand)
         idx = np.flatnonzero(i)
         active[idx[done]] = False

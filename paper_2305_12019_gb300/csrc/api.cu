@@ -59,6 +59,7 @@ struct gdwd_handle {
   unsigned* bar = nullptr;
   int* err = nullptr;
   Ctrl* ctrl = nullptr;
+  double phase_ns[kPhaseSlots] = {};
   std::string last_error;
 };
 
@@ -134,16 +135,14 @@ static void plan_layout(gdwd_handle* h) {
   }
   TB = std::min(TB, 256 * vec);
   const int NB = (int)((d + TB - 1) / TB);
-  int cw = 32;
-  while (cw > 8 && (int64_t)cw * TB * es > 32768) cw >>= 1;
   h->L.d = d;
   h->L.n = h->n;
   h->L.TB = TB;
   h->L.NB = NB;
-  h->L.CW = cw;
   h->L.esize = es;
   h->grid = (int)std::min<int64_t>(gp, std::max<int64_t>(NB, (h->n + kWarps - 1) / kWarps));
   h->grid = std::max(h->grid, 1);
+  h->L.CW = choose_chunk_cols(h->store, h->L, h->grid, h->smem_optin - 8192);
 }
 
 extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_t n, int64_t ldz, int32_t z_on_device,
@@ -198,6 +197,8 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
     if (!coop) return bail(fail(nullptr, GDWD_ECUDA, "device does not support cooperative launch"));
   }
   plan_layout(h);
+  if ((n + h->grid - 1) / h->grid > kMaxRowsPerCta)
+    return bail(fail(nullptr, GDWD_EUNSUPPORTED, "gdwd_create: n too large for the n x n factor path of this build"));
   st = [&]() -> gdwd_status {
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0), "cudaEventCreate");
@@ -393,7 +394,7 @@ static gdwd_status solve_one(gdwd_handle* h, double C, double* w, int w_on_devic
   CK(cudaEventCreate(&e1), "event");
   CK(cudaEventRecord(e0, st), "event");
   cudaError_t e;
-  const int smem_limit = h->smem_optin - 2048;
+  const int smem_limit = h->smem_optin - 8192;
   if (h->store == GDWD_F64)
     e = run_iterate_f64(make_args<double>(h, C, sigma0), smem_limit, st);
   else
@@ -415,6 +416,7 @@ static gdwd_status solve_one(gdwd_handle* h, double C, double* w, int w_on_devic
   cudaEventElapsedTime(&ms, e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  std::memcpy(h->phase_ns, c.phase_ns, sizeof(h->phase_ns));
   std::memset(res, 0, sizeof(*res));
   res->beta = c.beta;
   res->primal_obj = c.pobj;
@@ -482,7 +484,7 @@ extern "C" gdwd_status gdwd_apply(gdwd_handle* h, int32_t trans, const double* x
   if (!h || !x || !out) return fail(h, GDWD_EINVAL, "gdwd_apply: NULL argument");
   CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream), "memset");
   const int grid = h->L.NB;   // one CTA per slab
-  CK(run_apply(h->store, h->L, trans, x, h->sc, out, h->partial, std::min(grid, 4096), h->smem_optin - 2048, h->err,
+  CK(run_apply(h->store, h->L, trans, x, h->sc, out, h->partial, std::min(grid, 4096), h->smem_optin - 8192, h->err,
                (uint64_t)(h->opt.timeout_s * 1e9), h->stream),
      "gdwd_apply");
   int kerr = 0;
@@ -512,5 +514,11 @@ extern "C" gdwd_status gdwd_get_info(const gdwd_handle* h, gdwd_info* info) {
   info->device_bytes = (int64_t)h->bytes;
   info->zscale = h->zscale;
   info->t_setup_ms = h->t_setup_ms;
+  return GDWD_OK;
+}
+
+extern "C" gdwd_status gdwd_get_phase_times(const gdwd_handle* h, double* ns, int32_t count) {
+  if (!h || !ns || count < 0 || count > kPhaseSlots) return fail(nullptr, GDWD_EINVAL, "gdwd_get_phase_times: bad argument");
+  for (int k = 0; k < count; ++k) ns[k] = h->phase_ns[k];
   return GDWD_OK;
 }

@@ -104,32 +104,41 @@ __device__ __forceinline__ int ld_volatile(const int* p) { return *(const volati
 // gen * nblocks.  Every wait is bounded by timeout_ns: on expiry (or when
 // another CTA has already flagged an error) the error word is set and false is
 // returned to every thread of the CTA, which must then leave the kernel.
+__device__ __forceinline__ void red_add_release(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 __device__ __forceinline__ bool grid_barrier(unsigned* counter, unsigned nblocks, unsigned& gen, int* err,
                                              uint64_t timeout_ns, int* s_flag) {
   __syncthreads();
+  gen += 1;
   if (threadIdx.x == 0) {
-    gen += 1;
-    __threadfence();
-    atomicAdd(counter, 1u);
+    // the CTA barrier orders the block's writes before this release (cumulativity)
+    red_add_release(counter, 1u);
     const unsigned target = gen * nblocks;
-    const uint64_t t0 = globaltimer();
     int ok = 1;
-    while (true) {
-      unsigned v = *(volatile unsigned*)counter;
-      if ((int)(v - target) >= 0) break;
-      if (ld_volatile(err) != 0) { ok = 0; break; }
-      if (globaltimer() - t0 > timeout_ns) {
-        atomicCAS(err, 0, (int)GDWD_ETIMEOUT);
-        ok = 0;
-        break;
+    uint64_t t0 = 0;
+    unsigned polls = 0;
+    while ((int)(ld_acquire(counter) - target) < 0) {
+      if ((++polls & 31u) == 0) {
+        if (ld_volatile(err) != 0) { ok = 0; break; }
+        const uint64_t t = globaltimer();
+        if (t0 == 0) t0 = t;
+        else if (t - t0 > timeout_ns) {
+          atomicCAS(err, 0, (int)GDWD_ETIMEOUT);
+          ok = 0;
+          break;
+        }
       }
-      __nanosleep(20);
     }
-    __threadfence();
     if (ld_volatile(err) != 0) ok = 0;
     *s_flag = ok;
-  } else {
-    gen += 1;
   }
   __syncthreads();
   return *(volatile int*)s_flag != 0;

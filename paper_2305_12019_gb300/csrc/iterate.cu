@@ -61,10 +61,13 @@ __device__ double prox_root(double a, double kq, double q, int qcase, double r0)
     else if (f > 0.0) hi = s;
     else break;
     const double nt = s * (kq * (q + 2.0) + a * sq1) / (kq * (q + 1.0) + sq1 * s);
-    const double cand = (nt > lo && nt < hi) ? nt : 0.5 * (lo + hi);
-    const bool stop = fabs(cand - s) <= 8.881784197001252e-16 * cand;   // 4 eps
-    s = cand;
-    if (stop) break;
+    // converged when the Newton correction is below 4 eps relative: tested before the
+    // safeguard, so rounding noise in f at the root cannot trigger a bisection step
+    if (fabs(nt - s) <= 8.881784197001252e-16 * s) {
+      s = nt;
+      break;
+    }
+    s = (nt > lo && nt < hi) ? nt : 0.5 * (lo + hi);
   }
   return s;
 }
@@ -134,20 +137,48 @@ __device__ __forceinline__ df block_sum_df(df v, float* s_red) {
   return df{s_red[2 * kWarps], s_red[2 * kWarps + 1]};
 }
 
-// x_i = sum_j P_ij rhs_j for one row, one warp, double-float (result in all lanes)
+// N values per thread summed over the first nw warps of the block: warp sums,
+// then one thread per value adds the warp totals in a fixed order
+// (deterministic); out[k * stride] receives value k.  Threads of warps >= nw
+// must hold zeros.
+template <int N>
+__device__ __forceinline__ void block_sum_n(const double (&v)[N], int nw, double* s_part, double* out,
+                                            int stride) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (w < nw) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const double t = warp_sum(v[k]);
+      if (l == 0) s_part[w * N + k] = t;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < N) {
+    double t = 0.0;
+    for (int i = 0; i < nw; ++i) t += s_part[i * N + threadIdx.x];
+    out[(size_t)threadIdx.x * stride] = t;
+  }
+}
+
+// x_i = sum_j P_ij rhs_j for one row, one warp, double-float (result in all lanes).
+// Four independent 16-byte loads per lane per step keep several L2 requests in flight.
 __device__ __forceinline__ df row_dot(const float2* __restrict__ Prow, const float2* rhs_s, int npair) {
   const float4* P4 = reinterpret_cast<const float4*>(Prow);
   const float4* R4 = reinterpret_cast<const float4*>(rhs_s);
-  df a0{0.f, 0.f}, a1{0.f, 0.f};
+  df a0{0.f, 0.f}, a1{0.f, 0.f}, a2{0.f, 0.f}, a3{0.f, 0.f};
   const int lane = threadIdx.x & 31;
   int j = lane;
-  for (; j + 32 < npair; j += 64) {
-    const float4 p0 = __ldg(P4 + j), p1 = __ldg(P4 + j + 32);
-    const float4 r0 = R4[j], r1 = R4[j + 32];
+  for (; j + 96 < npair; j += 128) {
+    const float4 p0 = __ldg(P4 + j), p1 = __ldg(P4 + j + 32), p2 = __ldg(P4 + j + 64), p3 = __ldg(P4 + j + 96);
+    const float4 r0 = R4[j], r1 = R4[j + 32], r2 = R4[j + 64], r3 = R4[j + 96];
     df_fma(a0, df{p0.x, p0.y}, df{r0.x, r0.y});
     df_fma(a1, df{p0.z, p0.w}, df{r0.z, r0.w});
-    df_fma(a0, df{p1.x, p1.y}, df{r1.x, r1.y});
-    df_fma(a1, df{p1.z, p1.w}, df{r1.z, r1.w});
+    df_fma(a2, df{p1.x, p1.y}, df{r1.x, r1.y});
+    df_fma(a3, df{p1.z, p1.w}, df{r1.z, r1.w});
+    df_fma(a0, df{p2.x, p2.y}, df{r2.x, r2.y});
+    df_fma(a1, df{p2.z, p2.w}, df{r2.z, r2.w});
+    df_fma(a2, df{p3.x, p3.y}, df{r3.x, r3.y});
+    df_fma(a3, df{p3.z, p3.w}, df{r3.z, r3.w});
   }
   for (; j < npair; j += 32) {
     const float4 p0 = __ldg(P4 + j);
@@ -156,6 +187,8 @@ __device__ __forceinline__ df row_dot(const float2* __restrict__ Prow, const flo
     df_fma(a1, df{p0.z, p0.w}, df{r0.z, r0.w});
   }
   df_add(a0, a1);
+  df_add(a2, a3);
+  df_add(a0, a2);
   return df_warp_sum(a0);
 }
 
@@ -199,6 +232,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
   __shared__ double s_red[2 * kWarps + 2];
   __shared__ double s_tot[S_COUNT];
   __shared__ double s_ctl[8];
+  __shared__ double s_part[kWarps * 9];
 
   const Layout& L = a.L;
   const int cta = blockIdx.x, grid = a.grid;
@@ -210,9 +244,16 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
   const int nmy = (NB > cta) ? (NB - cta + grid - 1) / grid : 0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int gw = cta * kWarps + warp, W = grid * kWarps;
+  // contiguous block of G^{-1} rows (and n-space entries) owned by this CTA
+  const int64_t rpc = (n + grid - 1) / grid;
+  const int64_t r0 = ((int64_t)cta * rpc < n) ? (int64_t)cta * rpc : n;
+  const int nrows = (int)(((r0 + rpc < n) ? r0 + rpc : n) - r0);
+  __shared__ float s_xh[kMaxRowsPerCta], s_xl[kMaxRowsPerCta];
   const int qcase = q_case(a.q);
   const double sqmu = sqrt(a.mu), inv_mu = 1.0 / a.mu;
   const double den = 1.0 + a.C;
+  const double inv_q = 1.0 / a.q;
+  const float inv_den = (float)(1.0 / den);
 
   Ring rg;
   rg.buf = smem;
@@ -224,15 +265,32 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
   ring_init(rg);
 
   unsigned gen = 0;
+  // per-phase timing by CTA 0, thread 0 (globaltimer, a few instructions per phase)
+  __shared__ unsigned long long s_tacc[kPhaseSlots], s_tprev;
+  const bool timing = (cta == 0 && threadIdx.x == 0);
+  if (timing) {
+    for (int k = 0; k < kPhaseSlots; ++k) s_tacc[k] = 0;
+    s_tprev = globaltimer();
+  }
   double sig = a.ctrl->sigma, sig_prev = a.ctrl->sigma_prev, theta = a.ctrl->theta;
   int pending = a.ctrl->pending;
   int it0 = a.ctrl->it;
   int status = GDWD_EMAXITER;
   double beta = 0.0;
 
-#define GDWD_BARRIER()                                                                    \
+#define GDWD_MARK(k)                       \
+  do {                                     \
+    if (timing) {                          \
+      const uint64_t t_ = globaltimer();   \
+      s_tacc[k] += t_ - s_tprev;           \
+      s_tprev = t_;                        \
+    }                                      \
+  } while (0)
+#define GDWD_BARRIER(k)                                                                   \
   do {                                                                                    \
+    GDWD_MARK(k);                                                                         \
     if (!grid_barrier(a.bar, (unsigned)grid, gen, a.err, a.timeout_ns, &s_flag)) return; \
+    GDWD_MARK(k + 1);                                                                     \
   } while (0)
 
   int it = it0;
@@ -265,7 +323,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
       PassA<T> pa{gp, a.partial, TB, NB, Q, H};
       if (!stream_slabs<T>(L, rg, cta, grid, a.err, a.timeout_ns, &s_abort, pa)) return;
     }
-    GDWD_BARRIER();
+    GDWD_BARRIER(0);
 
     const double inv_sig = 1.0 / sig;
     // ---------------- phase R: b = sc * sum of partials; rhs1 = b + xi - r - alpha / sigma
@@ -289,7 +347,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
         a.rhsA[i] = make_float2(r1.hi, r1.lo);
       }
     }
-    GDWD_BARRIER();
+    GDWD_BARRIER(2);
 
     // ---------------- phase N1: x-bar, beta-bar, prox, rhs2
     const int npair = (int)((n + 1) / 2);
@@ -304,20 +362,28 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
         df_fma(pd, df{pv.x, pv.y}, df{rhs_s[i].x, rhs_s[i].y});
       }
       const double betabar = -df_to_double(block_sum_df(pd, s_redf)) * a.inv_s;
-      for (int64_t i = gw; i < n; i += W) {
-        const df x = row_dot(a.P + (size_t)i * a.ldP, rhs_s, npair);
+      // G^{-1} rows of this CTA (one warp per row), then the per-row FP64 work with
+      // one row per lane so each FP64 instruction serves up to 32 rows
+      for (int t = warp; t < nrows; t += kWarps) {
+        const df x = row_dot(a.P + (size_t)(r0 + t) * a.ldP, rhs_s, npair);
         if (lane == 0) {
-          const double cbar = df_to_double(x) + betabar * a.p[i];
-          const double ri = a.r[i];
-          const double rn = prox_root(cbar + ri, a.omega[i] * inv_sig, a.q, qcase, ri);
-          a.r[i] = rn;
-          const double v = a.xi[i] - rn - a.alpha[i] * inv_sig;
-          const df r2 = df_from(a.b[i] + v);
-          a.rhsB[i] = make_float2(r2.hi, r2.lo);
+          s_xh[t] = x.hi;
+          s_xl[t] = x.lo;
         }
       }
+      __syncthreads();
+      for (int t = threadIdx.x; t < nrows; t += kThreads) {
+        const int64_t i = r0 + t;
+        const double cbar = ((double)s_xh[t] + (double)s_xl[t]) + betabar * a.p[i];
+        const double ri = a.r[i];
+        const double rn = prox_root(cbar + ri, a.omega[i] * inv_sig, a.q, qcase, ri);
+        a.r[i] = rn;
+        const double v = a.xi[i] - rn - a.alpha[i] * inv_sig;
+        const df r2 = df_from(a.b[i] + v);
+        a.rhsB[i] = make_float2(r2.hi, r2.lo);
+      }
     }
-    GDWD_BARRIER();
+    GDWD_BARRIER(4);
 
     // ---------------- phase N2: x, beta, c, Z~^T w; Step 2 (xi), Step 3 (alpha)
     {
@@ -330,10 +396,18 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
       }
       beta = -df_to_double(block_sum_df(pd, s_redf)) * a.inv_s;
       double s_res2 = 0, s_ya = 0, s_xica = 0, s_ams2 = 0, s_amin2 = 0, s_amax2 = 0, s_pr = 0, s_px = 0, s_du = 0;
-      for (int64_t i = gw; i < n; i += W) {
-        const df x = row_dot(a.P + (size_t)i * a.ldP, rhs_s, npair);
+      for (int t = warp; t < nrows; t += kWarps) {
+        const df x = row_dot(a.P + (size_t)(r0 + t) * a.ldP, rhs_s, npair);
         if (lane == 0) {
-          const double c = df_to_double(x) + beta * a.p[i];
+          s_xh[t] = x.hi;
+          s_xl[t] = x.lo;
+        }
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < nrows; t += kThreads) {
+        const int64_t i = r0 + t;
+        {
+          const double c = ((double)s_xh[t] + (double)s_xl[t]) + beta * a.p[i];
           const double ri = a.r[i], al = a.alpha[i], yi = a.y[i], ce = a.C * a.e[i];
           const double v = a.xi[i] - ri - al * inv_sig;
           const double zw = c - v - yi * beta;                                     // Z~^T w
@@ -345,27 +419,25 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
           store_ct(a.cq + i, a.sc[i] * c);
           store_ct(a.aq + i, a.sc[i] * an);
           const double rq1 = pow_q1(ri, a.q, qcase);
+          const double irq1 = 1.0 / rq1;
           const double om = a.omega[i];
           s_res2 = fma(res, res, s_res2);
           s_ya = fma(yi, an, s_ya);
           s_xica = fma(xin, ce - an, s_xica);
-          const double dv = an - om / rq1;
+          const double dv = an - om * irq1;
           s_ams2 = fma(dv, dv, s_ams2);
           const double mn = fmin(0.0, an), mx = fmax(0.0, an - ce);
           s_amin2 = fma(mn, mn, s_amin2);
           s_amax2 = fma(mx, mx, s_amax2);
-          s_pr += (om / a.q) * ri / rq1;            // wt^q r^-q
+          s_pr += om * inv_q * ri * irq1;           // wt^q r^-q
           s_px = fma(a.e[i], xin, s_px);
           s_du += dual_pow(a.wt[i] * an, a.q, qcase);
         }
       }
       const double vals[9] = {s_res2, s_ya, s_xica, s_ams2, s_amin2, s_amax2, s_pr, s_px, s_du};
-      for (int k = 0; k < 9; ++k) {
-        const double t = block_sum(vals[k], s_red);
-        if (threadIdx.x == 0) a.scal[(size_t)cta * S_COUNT + k] = t;
-      }
+      block_sum_n<9>(vals, (nrows + 31) / 32 < kWarps ? (nrows + 31) / 32 : kWarps, s_part, a.scal + cta, grid);
     }
-    GDWD_BARRIER();
+    GDWD_BARRIER(6);
 
     // ---------------- phase B: t = Z~ c, ta = Z~ alpha, g, d-space sums
     {
@@ -395,22 +467,21 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
       }
       if (!stream_slabs<T>(L, rg, cta, grid, a.err, a.timeout_ns, &s_abort, pb)) return;
       const double vals[6] = {epi.sg2, epi.sgr, epi.sr2, epi.sa2, epi.sag, epi.sta2};
-      for (int k = 0; k < 6; ++k) {
-        const double t = block_sum(vals[k], s_red);
-        if (threadIdx.x == 0) a.scal[(size_t)cta * S_COUNT + S_G2 + k] = t;
-      }
+      block_sum_n<6>(vals, kWarps, s_part, a.scal + (size_t)S_G2 * grid + cta, grid);
     }
-    GDWD_BARRIER();
+    GDWD_BARRIER(8);
 
     // ---------------- phase S: totals, KKT, sigma rule, stop test (same in every CTA)
     for (int k = warp; k < S_COUNT - 1; k += kWarps) {
       double acc = 0.0;
-      for (int c2 = lane; c2 < grid; c2 += 32) acc += a.scal[(size_t)c2 * S_COUNT + k];
+      for (int c2 = lane; c2 < grid; c2 += 32) acc += a.scal[(size_t)k * grid + c2];
       acc = warp_sum(acc);
       if (lane == 0) s_tot[k] = acc;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
+      // FP64 only where cancellation needs it (theta, ||w|| - R, the eta_D3 expansion,
+      // the duality gap); plain norms and ratios in FP32 (they are compared with tol).
       const double S1 = s_tot[S_G2], S2 = s_tot[S_GRHO], S3 = s_tot[S_RHO2];
       const double gs = 1.0 / (sig * sqmu);
       const double gnorm = sqrt(S1);
@@ -420,21 +491,23 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
       const double wu2 = fmax(0.0, om * om * S1 + 2.0 * om * gs * S2 + gs * gs * S3);   // ||w - u+||^2
       const double kap = a.tau * sig * a.mu * om;
       const double d3 = fmax(0.0, s_tot[S_A2] - 2.0 * kap * s_tot[S_AG] + kap * kap * S1);
-      const double wn = sqrt(w2);
-      const double p1 = sqrt(s_tot[S_RES2]) / den;
-      const double p2 = sqmu * sqrt(wu2) / den;
-      const double p3 = fmax(wn - a.R, 0.0) / den;
-      const double dd1 = sqrt(s_tot[S_AMIN2]) / den;
-      const double dd2 = sqrt(s_tot[S_AMAX2]) / den;
-      const double dd3 = sqrt(d3) / den;
-      const double c1 = fabs(s_tot[S_YA]) / den;
-      const double c2 = fabs(s_tot[S_XICA]) / den;
-      const double c3 = sqrt(s_tot[S_AMS2]) / den;
+      const float wnf = sqrtf((float)w2);
+      const double wmr = (w2 - a.R * a.R) / (double)(wnf + (float)a.R);      // ||w|| - R
+      const double p1 = sqrtf((float)s_tot[S_RES2]) * inv_den;
+      const double p2 = sqrtf((float)(a.mu * wu2)) * inv_den;
+      const double p3 = fmax(wmr, 0.0) * inv_den;
+      const double dd1 = sqrtf((float)s_tot[S_AMIN2]) * inv_den;
+      const double dd2 = sqrtf((float)s_tot[S_AMAX2]) * inv_den;
+      const double dd3 = sqrtf((float)d3) * inv_den;
+      const double c1 = fabs(s_tot[S_YA]) * inv_den;
+      const double c2 = fabs(s_tot[S_XICA]) * inv_den;
+      const double c3 = sqrtf((float)s_tot[S_AMS2]) * inv_den;
       const double pobj = s_tot[S_PRIM_R] + a.C * s_tot[S_PRIM_XI];
       const double dobj = a.kappa * s_tot[S_DUAL_A] - a.R * sqrt(s_tot[S_TA2]);
-      const double gap = fabs(pobj - dobj) / (1.0 + fabs(pobj) + fabs(dobj));
+      const double gap = (double)((float)fabs(pobj - dobj) / (float)(1.0 + fabs(pobj) + fabs(dobj)));
       const double ep = fmax(p1, fmax(p2, p3)), ed = fmax(dd1, fmax(dd2, dd3)), ec = fmax(c1, fmax(c2, c3));
       const double kkt = fmax(fmax(ep, ed), fmax(ec, gap));
+      const double wn = (double)wnf;
       int done = 0;
       double sig_next = sig;
       if (!(kkt == kkt) || isinf(kkt)) {
@@ -444,11 +517,12 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
         done = 1;
         status = GDWD_OK;
       } else if (it >= 1) {                                                  // sigma rule, Sec. 4.4
-        const double chi = ep / fmax(ed, 1e-300);
-        const double big = fmax(chi, 1.0 / fmax(chi, 1e-300));
-        const double zeta = big > 500.0 ? 2.2 : (big > 50.0 ? 1.65 : 1.1);
-        if (chi > 5.0) sig_next = sig * zeta;
-        else if (1.0 / fmax(chi, 1e-300) > 5.0) sig_next = sig / zeta;
+        const float chi = (float)ep / fmaxf((float)ed, 1e-30f);
+        const float ichi = (float)ed / fmaxf((float)ep, 1e-30f);
+        const float big = fmaxf(chi, ichi);
+        const double zeta = big > 500.f ? 2.2 : (big > 50.f ? 1.65 : 1.1);
+        if (chi > 5.f) sig_next = sig * zeta;
+        else if (ichi > 5.f) sig_next = sig / zeta;
       }
       s_ctl[0] = th;
       s_ctl[1] = sig_next;
@@ -468,6 +542,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
       }
     }
     __syncthreads();
+    GDWD_MARK(10);
     sig_prev = sig;
     theta = s_ctl[0];
     sig = s_ctl[1];
@@ -489,8 +564,10 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
     c->it = it;
     c->status = status;
     c->done = 1;
+    for (int k = 0; k < kPhaseSlots; ++k) c->phase_ns[k] = (double)s_tacc[k];
   }
 #undef GDWD_BARRIER
+#undef GDWD_MARK
 }
 
 template <typename T>
@@ -517,6 +594,24 @@ static cudaError_t launch_iterate_t(const IterArgs<typename ElemTraits<T>::compu
   if (e != cudaSuccess) return e;
   void* params[] = {(void*)&args, (void*)&stages, (void*)&stage_bytes};
   return cudaLaunchCooperativeKernel((const void*)kern, dim3(args.grid), dim3(kThreads), params, smem, st);
+}
+
+// Columns per streamed chunk: about 64 KB per bulk copy (on this part one SM's
+// bulk copies from L2 complete one after another, so larger copies amortise the
+// per-copy latency), at least two stages next to the phase-local buffers.
+template <typename T>
+static int choose_cw_t(const Layout& L, int grid, int smem_limit) {
+  const int64_t ub = (int64_t)union_bytes<T>(L, grid);
+  const int64_t col_bytes = (int64_t)L.TB * L.esize;
+  const int64_t avail = (int64_t)smem_limit - ub - 1024;
+  int64_t cw = std::min<int64_t>(65536 / col_bytes, (avail / 2 - 128) / col_bytes);
+  cw = std::max<int64_t>(cw, 1);
+  cw = std::min<int64_t>(cw, L.n);
+  return (int)cw;
+}
+
+int choose_chunk_cols(int store, const Layout& L, int grid, int smem_limit) {
+  return store == GDWD_F64 ? choose_cw_t<double>(L, grid, smem_limit) : choose_cw_t<float>(L, grid, smem_limit);
 }
 
 // Plans the ring (stage size, stage count) for the available shared memory.

@@ -76,9 +76,10 @@ __device__ bool stream_slabs(const Layout& L, Ring& rg, int cta, int grid, int* 
 }
 
 // ---------------------------------------------------------------------------
-// pass A: dots down the columns of each chunk.  H = 256 / CW threads share a
-// column (H >= 8, so 8 consecutive lanes read 8 consecutive 16-byte vectors of
-// one column: no shared-memory bank conflicts), then reduce by shuffles.
+// pass A: dots down the columns of each chunk, 32 columns per round.  8 lanes
+// share a column (8 consecutive lanes read 8 consecutive 16-byte vectors of one
+// column: no shared-memory bank conflicts), two independent accumulators per
+// lane, then a 3-step shuffle reduction.
 // ---------------------------------------------------------------------------
 template <typename T>
 struct PassA {
@@ -89,21 +90,40 @@ struct PassA {
   int TB, NB, Q, H;
 
   __device__ void chunk(const T* buf, int k, int s, int col0, int cw) {
-    const int col = threadIdx.x / H, h = threadIdx.x % H;
-    CT acc = 0;
-    if (col < cw) {
-      const T* cp = buf + (size_t)col * TB;
-      const CT* g = gp + (size_t)k * TB;
-      for (int v = h; v < Q; v += H) {
-        CT e[VEC], gv[VEC];
-        ElemTraits<T>::load(cp + v * VEC, e);
-        ElemTraits<CT>::load(g + v * VEC, gv);
+    const int h = threadIdx.x & 7, cl = threadIdx.x >> 3;
+    const CT* g = gp + (size_t)k * TB;
+    for (int c0 = 0; c0 < cw; c0 += kThreads / 8) {
+      const int col = c0 + cl;
+      CT acc0 = 0, acc1 = 0;
+      if (col < cw) {
+        const T* cp = buf + (size_t)col * TB;
+        int v = h;
+        for (; v + 8 < Q; v += 16) {
+          CT e0[VEC], e1[VEC], g0[VEC], g1[VEC];
+          ElemTraits<T>::load(cp + v * VEC, e0);
+          ElemTraits<T>::load(cp + (v + 8) * VEC, e1);
+          ElemTraits<CT>::load(g + v * VEC, g0);
+          ElemTraits<CT>::load(g + (v + 8) * VEC, g1);
 #pragma unroll
-        for (int kk = 0; kk < VEC; ++kk) acc = fma(e[kk], gv[kk], acc);
+          for (int kk = 0; kk < VEC; ++kk) {
+            acc0 = fma(e0[kk], g0[kk], acc0);
+            acc1 = fma(e1[kk], g1[kk], acc1);
+          }
+        }
+        if (v < Q) {
+          CT e0[VEC], g0[VEC];
+          ElemTraits<T>::load(cp + v * VEC, e0);
+          ElemTraits<CT>::load(g + v * VEC, g0);
+#pragma unroll
+          for (int kk = 0; kk < VEC; ++kk) acc0 = fma(e0[kk], g0[kk], acc0);
+        }
       }
+      CT acc = acc0 + acc1;
+      acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+      if (h == 0 && col < cw) partial[(size_t)(col0 + col) * NB + s] = acc;
     }
-    for (int m = H >> 1; m >= 1; m >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, m);
-    if (h == 0 && col < cw) partial[(size_t)(col0 + col) * NB + s] = acc;
   }
   __device__ void end_slab(int, int) {}
 };
@@ -155,7 +175,25 @@ struct PassB {
     for (int kk = 0; kk < VEC; ++kk) ac[kk] = aa[kk] = 0;
     const T* base = buf + qv * VEC;
     if (two) {
-      for (int col = grp; col < cw; col += G) {
+      int col = grp;
+      for (; col + G < cw; col += 2 * G) {
+        CT e0[VEC], e1[VEC];
+        ElemTraits<T>::load(base + (size_t)col * TB, e0);
+        ElemTraits<T>::load(base + (size_t)(col + G) * TB, e1);
+        const CT c0 = cv[col0 + col], a0 = av[col0 + col];
+        const CT c1 = cv[col0 + col + G], a1 = av[col0 + col + G];
+#pragma unroll
+        for (int kk = 0; kk < VEC; ++kk) {
+          ac[kk] = fma(e0[kk], c0, ac[kk]);
+          aa[kk] = fma(e0[kk], a0, aa[kk]);
+        }
+#pragma unroll
+        for (int kk = 0; kk < VEC; ++kk) {
+          ac[kk] = fma(e1[kk], c1, ac[kk]);
+          aa[kk] = fma(e1[kk], a1, aa[kk]);
+        }
+      }
+      if (col < cw) {
         CT e[VEC];
         ElemTraits<T>::load(base + (size_t)col * TB, e);
         const CT c = cv[col0 + col], a = av[col0 + col];

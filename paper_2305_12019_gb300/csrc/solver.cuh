@@ -43,6 +43,12 @@ enum Scal {
   S_COUNT = 16
 };
 
+// Phases of one iteration, each followed by its grid-barrier wait:
+// 0 A, 1 wait, 2 R, 3 wait, 4 N1, 5 wait, 6 N2, 7 wait, 8 B, 9 wait, 10 S
+constexpr int kPhaseSlots = 12;
+// n-space rows owned by one CTA of the iteration kernel (ceil(n / grid) <= this)
+constexpr int kMaxRowsPerCta = 256;
+
 // Iteration control block (device memory, read back by the host).
 struct Ctrl {
   double sigma;        // sigma for the next iteration
@@ -56,6 +62,7 @@ struct Ctrl {
   int32_t status;      // gdwd_status of the solve
   int32_t done;        // 1 once converged / failed
   int32_t pending;     // 1: u, rho still hold the iterate before the deferred update
+  double phase_ns[kPhaseSlots];   // CTA 0's time per phase (compute, then barrier wait), summed
 };
 
 // Everything the persistent iteration kernel reads and writes.
@@ -97,6 +104,7 @@ struct IterArgs {
 };
 
 // Host-side launchers (defined in the .cu files).
+int choose_chunk_cols(int store, const Layout& L, int grid, int smem_limit);
 cudaError_t run_iterate_f64(const IterArgs<double>& a, int smem_limit, cudaStream_t st);
 cudaError_t run_iterate_f32(const IterArgs<float>& a, int smem_limit, cudaStream_t st);
 cudaError_t run_apply(int store, const Layout& L, int trans, const double* x, const double* sc, double* out,

@@ -48,7 +48,8 @@ class Info(ctypes.Structure):
 
 
 EXPORTS = ["gdwd_default_options", "gdwd_create", "gdwd_solve", "gdwd_free", "gdwd_last_error", "gdwd_prox",
-           "gdwd_apply", "gdwd_gram", "gdwd_get_info"]
+           "gdwd_apply", "gdwd_gram", "gdwd_get_info", "gdwd_get_phase_times"]
+PHASES = ["A", "A_wait", "R", "R_wait", "N1", "N1_wait", "N2", "N2_wait", "B", "B_wait", "S", "unused"]
 
 _lib = None
 
@@ -78,6 +79,7 @@ def load(path: str = LIB_PATH):
     lib.gdwd_apply.argtypes = [c_void_p, c_int32, c_void_p, c_void_p]
     lib.gdwd_gram.argtypes = [c_void_p, c_void_p]
     lib.gdwd_get_info.argtypes = [c_void_p, POINTER(Info)]
+    lib.gdwd_get_phase_times.argtypes = [c_void_p, POINTER(c_double), c_int32]
     for name in EXPORTS:
         if name != "gdwd_last_error":
             getattr(lib, name).restype = c_int32
@@ -181,6 +183,12 @@ class Solver:
         i = Info()
         _check(_lib.gdwd_get_info(self._h, ctypes.byref(i)), self._h)
         return i.as_dict()
+
+    def phase_times(self):
+        """Per-phase device time (ns) of the last solve, CTA 0's view (gdwd_get_phase_times)."""
+        buf = (c_double * 12)()
+        _check(_lib.gdwd_get_phase_times(self._h, buf, 12), self._h)
+        return {PHASES[k]: buf[k] for k in range(11)}
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

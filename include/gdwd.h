@@ -186,7 +186,10 @@ gdwd_status gdwd_get_info(const gdwd_handle* h, gdwd_info* info);
  * over iterations): ns[2k] = time in phase k, ns[2k+1] = the grid-barrier wait
  * that follows it, for k = A (Z^T g' stream), R (reduction), N1 (first n-space
  * solve and Step 1b), N2 (second solve, Steps 2-3), B (Z c stream); ns[10] =
- * the KKT / sigma phase.  count (<= 12) entries are written to ns (host).
+ * the KKT / sigma phase; sub-phases split out of those: ns[11] N2 right-hand
+ * side load and beta, ns[12] N2 rows of G^{-1}, ns[13] reduction of the
+ * per-CTA partial sums, ns[14] N1 right-hand side load and beta-bar, ns[15] N1
+ * rows of G^{-1}.  count (<= 16) entries are written to ns (host).
  * Diagnostics only; the paper has no counterpart.  Errors: EINVAL.
  */
 gdwd_status gdwd_get_phase_times(const gdwd_handle* h, double* ns, int32_t count);

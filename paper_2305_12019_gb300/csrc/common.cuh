@@ -81,6 +81,27 @@ __device__ __forceinline__ df df_warp_sum(df a) {
   return a;
 }
 
+// 1/b, a/b and sqrt(x) for FP64 operands whose magnitudes lie inside the FP32
+// range (b != 0, x >= 0): an FP32 seed and one FP64 Newton correction
+// (relative error ~1e-14).  FP64 division and square root are long dependent
+// chains on this part; these cost two or three FP64 operations.  Not for the
+// prox, whose stopping test needs exact division.
+__device__ __forceinline__ double rcp_nr(double b) {
+  const double r = (double)__frcp_rn((float)b);
+  return fma(r, fma(-b, r, 1.0), r);
+}
+__device__ __forceinline__ double div_nr(double a, double b) {
+  const double r = (double)__frcp_rn((float)b);
+  const double q = a * r;
+  return fma(r, fma(-b, q, a), q);
+}
+__device__ __forceinline__ double sqrt_nr(double x) {
+  if (!(x > 0.0)) return 0.0;
+  const float sf = __fsqrt_rn((float)x);
+  const double s = (double)sf;
+  return fma((double)(0.5f / sf), fma(-s, s, x), s);
+}
+
 __device__ __forceinline__ double warp_sum(double a) {
 #pragma unroll
   for (int m = 16; m >= 1; m >>= 1) a += __shfl_xor_sync(0xffffffffu, a, m);

@@ -93,7 +93,7 @@ cudaError_t launch_prox(const double* a, const double* r0, const double* omega, 
 __device__ __forceinline__ double dual_pow(double x, double q, int qcase) {
   if (x <= 0.0) return 0.0;
   switch (qcase) {
-    case 1: return sqrt(x);
+    case 1: return sqrt_nr(x);
     case 2: { double c = cbrt(x); return c * c; }
     case 5: return cbrt(x);
     default: return pow(x, q / (q + 1.0));
@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
     // ---------------- phase A: deferred (u, rho) update, g', Z~^T g' partials
     {
       CT* gp = reinterpret_cast<CT*>(uni);
-      const double gsc = 1.0 / (sig * sqmu);
+      const double gsc = rcp_nr(sig * sqmu);
       const double rcoef = a.tau * sig_prev * sqmu * (1.0 - theta);
       for (int k = 0; k < nmy; ++k) {
         const int64_t s = cta + (int64_t)k * grid;
@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
     }
     GDWD_BARRIER(0);
 
-    const double inv_sig = 1.0 / sig;
+    const double inv_sig = rcp_nr(sig);
     // ---------------- phase R: b = sc * sum of partials; rhs1 = b + xi - r - alpha / sigma
     for (int64_t i = gw; i < n; i += W) {
       const CT* pp = a.partial + (size_t)i * NB;
@@ -362,6 +362,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
         df_fma(pd, df{pv.x, pv.y}, df{rhs_s[i].x, rhs_s[i].y});
       }
       const double betabar = -df_to_double(block_sum_df(pd, s_redf)) * a.inv_s;
+      GDWD_MARK(14);
       // G^{-1} rows of this CTA (one warp per row), then the per-row FP64 work with
       // one row per lane so each FP64 instruction serves up to 32 rows
       for (int t = warp; t < nrows; t += kWarps) {
@@ -372,6 +373,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
         }
       }
       __syncthreads();
+      GDWD_MARK(15);
       for (int t = threadIdx.x; t < nrows; t += kThreads) {
         const int64_t i = r0 + t;
         const double cbar = ((double)s_xh[t] + (double)s_xl[t]) + betabar * a.p[i];
@@ -395,6 +397,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
         df_fma(pd, df{pv.x, pv.y}, df{rhs_s[i].x, rhs_s[i].y});
       }
       beta = -df_to_double(block_sum_df(pd, s_redf)) * a.inv_s;
+      GDWD_MARK(11);
       double s_res2 = 0, s_ya = 0, s_xica = 0, s_ams2 = 0, s_amin2 = 0, s_amax2 = 0, s_pr = 0, s_px = 0, s_du = 0;
       for (int t = warp; t < nrows; t += kWarps) {
         const df x = row_dot(a.P + (size_t)(r0 + t) * a.ldP, rhs_s, npair);
@@ -404,6 +407,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
         }
       }
       __syncthreads();
+      GDWD_MARK(12);
       for (int t = threadIdx.x; t < nrows; t += kThreads) {
         const int64_t i = r0 + t;
         {
@@ -419,7 +423,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
           store_ct(a.cq + i, a.sc[i] * c);
           store_ct(a.aq + i, a.sc[i] * an);
           const double rq1 = pow_q1(ri, a.q, qcase);
-          const double irq1 = 1.0 / rq1;
+          const double irq1 = rcp_nr(rq1);
           const double om = a.omega[i];
           s_res2 = fma(res, res, s_res2);
           s_ya = fma(yi, an, s_ya);
@@ -479,20 +483,21 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
       if (lane == 0) s_tot[k] = acc;
     }
     __syncthreads();
+    GDWD_MARK(13);
     if (threadIdx.x == 0) {
       // FP64 only where cancellation needs it (theta, ||w|| - R, the eta_D3 expansion,
       // the duality gap); plain norms and ratios in FP32 (they are compared with tol).
       const double S1 = s_tot[S_G2], S2 = s_tot[S_GRHO], S3 = s_tot[S_RHO2];
-      const double gs = 1.0 / (sig * sqmu);
-      const double gnorm = sqrt(S1);
-      const double th = (gnorm <= a.R) ? 1.0 : a.R / gnorm;                 // Step 2 projection
+      const double gs = rcp_nr(sig * sqmu);
+      const double gnorm = sqrt_nr(S1);
+      const double th = (gnorm <= a.R) ? 1.0 : div_nr(a.R, gnorm);          // Step 2 projection
       const double w2 = fmax(0.0, S1 + 2.0 * gs * S2 + gs * gs * S3);        // ||w||^2
       const double om = 1.0 - th;
       const double wu2 = fmax(0.0, om * om * S1 + 2.0 * om * gs * S2 + gs * gs * S3);   // ||w - u+||^2
       const double kap = a.tau * sig * a.mu * om;
       const double d3 = fmax(0.0, s_tot[S_A2] - 2.0 * kap * s_tot[S_AG] + kap * kap * S1);
       const float wnf = sqrtf((float)w2);
-      const double wmr = (w2 - a.R * a.R) / (double)(wnf + (float)a.R);      // ||w|| - R
+      const double wmr = (w2 - a.R * a.R) * (double)(1.0f / (wnf + (float)a.R));   // ||w|| - R
       const double p1 = sqrtf((float)s_tot[S_RES2]) * inv_den;
       const double p2 = sqrtf((float)(a.mu * wu2)) * inv_den;
       const double p3 = fmax(wmr, 0.0) * inv_den;
@@ -503,7 +508,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
       const double c2 = fabs(s_tot[S_XICA]) * inv_den;
       const double c3 = sqrtf((float)s_tot[S_AMS2]) * inv_den;
       const double pobj = s_tot[S_PRIM_R] + a.C * s_tot[S_PRIM_XI];
-      const double dobj = a.kappa * s_tot[S_DUAL_A] - a.R * sqrt(s_tot[S_TA2]);
+      const double dobj = a.kappa * s_tot[S_DUAL_A] - a.R * sqrt_nr(s_tot[S_TA2]);
       const double gap = (double)((float)fabs(pobj - dobj) / (float)(1.0 + fabs(pobj) + fabs(dobj)));
       const double ep = fmax(p1, fmax(p2, p3)), ed = fmax(dd1, fmax(dd2, dd3)), ec = fmax(c1, fmax(c2, c3));
       const double kkt = fmax(fmax(ep, ed), fmax(ec, gap));

@@ -44,8 +44,11 @@ enum Scal {
 };
 
 // Phases of one iteration, each followed by its grid-barrier wait:
-// 0 A, 1 wait, 2 R, 3 wait, 4 N1, 5 wait, 6 N2, 7 wait, 8 B, 9 wait, 10 S
-constexpr int kPhaseSlots = 12;
+// 0 A, 1 wait, 2 R, 3 wait, 4 N1, 5 wait, 6 N2, 7 wait, 8 B, 9 wait, 10 S;
+// sub-phases: 11 N2 rhs load + beta, 12 N2 rows of G^{-1}, 13 S partial-sum
+// reduction, 14 N1 rhs load + beta-bar, 15 N1 rows of G^{-1} (the slot of a
+// phase then holds only its remainder).
+constexpr int kPhaseSlots = 16;
 // n-space rows owned by one CTA of the iteration kernel (ceil(n / grid) <= this)
 constexpr int kMaxRowsPerCta = 256;
 

@@ -49,7 +49,8 @@ class Info(ctypes.Structure):
 
 EXPORTS = ["gdwd_default_options", "gdwd_create", "gdwd_solve", "gdwd_free", "gdwd_last_error", "gdwd_prox",
            "gdwd_apply", "gdwd_gram", "gdwd_get_info", "gdwd_get_phase_times"]
-PHASES = ["A", "A_wait", "R", "R_wait", "N1", "N1_wait", "N2", "N2_wait", "B", "B_wait", "S", "unused"]
+PHASES = ["A", "A_wait", "R", "R_wait", "N1_rows", "N1_wait", "N2_rows", "N2_wait", "B", "B_wait", "S_kkt",
+          "N2_rhs", "N2_gemv", "S_sums", "N1_rhs", "N1_gemv"]
 
 _lib = None
 
@@ -186,9 +187,9 @@ class Solver:
 
     def phase_times(self):
         """Per-phase device time (ns) of the last solve, CTA 0's view (gdwd_get_phase_times)."""
-        buf = (c_double * 12)()
-        _check(_lib.gdwd_get_phase_times(self._h, buf, 12), self._h)
-        return {PHASES[k]: buf[k] for k in range(11)}
+        buf = (c_double * 16)()
+        _check(_lib.gdwd_get_phase_times(self._h, buf, 16), self._h)
+        return {PHASES[k]: buf[k] for k in range(16)}
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -64,9 +64,11 @@ typedef struct {
   double sigma0;      /* initial sigma; <= 0 selects min(10C, n)^q (Sec. 4.4).          */
   double timeout_s;   /* limit of every device-side wait (grid barrier, copies). Default 2 */
   int32_t max_iter;   /* iteration limit.  Default 20000.                              */
-  int32_t store;      /* gdwd_dtype of the copy of Z kept on the device: GDWD_F64 or
-                         GDWD_F32 (BF16/F16/E4M3 give GDWD_EUNSUPPORTED in this build).
-                         Default GDWD_F32.                                              */
+  int32_t store;      /* gdwd_dtype of the copy of Z kept on the device.  GDWD_F64 and
+                         GDWD_F32 keep the values; GDWD_BF16, GDWD_F16 and GDWD_E4M3
+                         keep Z_ji / s_i rounded to the format with a per-column FP64
+                         scale s_i (see gdwd_get_stored), and the solve is then of the
+                         stored (quantized) problem.  Default GDWD_F32.                 */
   int32_t grid;       /* CTAs of the persistent iteration kernel; 0 = one per SM.      */
   int32_t block_rows; /* rows of Z per slab of the device layout; 0 = automatic.        */
   void* stream;       /* cudaStream_t for all work of the handle; NULL = default stream */
@@ -193,6 +195,17 @@ gdwd_status gdwd_get_info(const gdwd_handle* h, gdwd_info* info);
  * Diagnostics only; the paper has no counterpart.  Errors: EINVAL.
  */
 gdwd_status gdwd_get_phase_times(const gdwd_handle* h, double* ns, int32_t count);
+
+/*
+ * Copies the data the handle stores back to the host: Zq (d x n, column-major,
+ * element type = the handle's store dtype, d*n*size bytes) and colscale (n
+ * doubles) such that the stored problem's Z is Zq_ji * colscale_i (colscale = 1
+ * for FP64 / FP32 storage; for BF16 / FP16 / E4M3, colscale_i = max_j |Z_ji|
+ * divided by 1, 32768 or 448 respectively, and Zq_ji = Z_ji / colscale_i rounded
+ * to nearest-even, saturating for E4M3).  Either pointer may be NULL.
+ * Diagnostics; the paper has no counterpart.  Errors: EINVAL, ECUDA.
+ */
+gdwd_status gdwd_get_stored(const gdwd_handle* h, void* Zq, double* colscale);
 
 #ifdef __cplusplus
 }

@@ -56,6 +56,7 @@ struct gdwd_handle {
   void *cq = nullptr, *aq = nullptr, *partial = nullptr;
   double *u = nullptr, *rho = nullptr, *g = nullptr, *scal = nullptr, *wtmp = nullptr;
   double* dscalars = nullptr;   // [0] sumsq [1] zscale [2] s
+  double *amax = nullptr, *colscale = nullptr;   // per-column |max| and storage scale s_i
   unsigned* bar = nullptr;
   int* err = nullptr;
   Ctrl* ctrl = nullptr;
@@ -167,11 +168,7 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
   if (!(opt.mu > 0.0) || !(opt.tau > 0.0 && opt.tau < 1.6180339887498949) || !(opt.tol > 0.0) || opt.max_iter < 1 ||
       !(opt.timeout_s > 0.0))
     return fail(nullptr, GDWD_EINVAL, "gdwd_create: bad options (mu > 0, 0 < tau < golden ratio, tol > 0, max_iter >= 1)");
-  if (opt.store != GDWD_F64 && opt.store != GDWD_F32) {
-    if (opt.store == GDWD_BF16 || opt.store == GDWD_F16 || opt.store == GDWD_E4M3)
-      return fail(nullptr, GDWD_EUNSUPPORTED, "gdwd_create: BF16/F16/E4M3 storage is not available in this build");
-    return fail(nullptr, GDWD_EINVAL, "gdwd_create: bad store dtype");
-  }
+  if (opt.store < GDWD_F64 || opt.store > GDWD_E4M3) return fail(nullptr, GDWD_EINVAL, "gdwd_create: bad store dtype");
 
   gdwd_handle* h = new gdwd_handle();
   h->opt = opt;
@@ -216,6 +213,8 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
     h->L.Z = zbuf;
     h->ldP = (int)((n + 1) / 2 * 2);
     CK(halloc(h, &h->sc, n), "alloc");
+    CK(halloc(h, &h->amax, n), "alloc");
+    CK(halloc(h, &h->colscale, n), "alloc");
     CK(halloc(h, &h->y, n), "alloc");
     CK(halloc(h, &h->e, n), "alloc");
     CK(halloc(h, &h->omega, n), "alloc");
@@ -269,7 +268,7 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
     int* nonfinite = h->err;
     CK(cudaMalloc(&part, nparts * sizeof(double)), "cudaMalloc");
     cudaError_t ei = run_ingest(zsrc, zdt, ld, h->L, h->Z, h->store, part, nparts, h->dscalars, nonfinite, h->sc,
-                                h->dscalars + 1, h->stream);
+                                h->dscalars + 1, h->amax, h->colscale, h->stream);
     int nf = 0;
     if (ei == cudaSuccess) ei = cudaMemcpyAsync(&nf, nonfinite, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     if (ei == cudaSuccess) ei = cudaStreamSynchronize(h->stream);
@@ -398,7 +397,7 @@ static gdwd_status solve_one(gdwd_handle* h, double C, double* w, int w_on_devic
   if (h->store == GDWD_F64)
     e = run_iterate_f64(make_args<double>(h, C, sigma0), smem_limit, st);
   else
-    e = run_iterate_f32(make_args<float>(h, C, sigma0), smem_limit, st);
+    e = run_iterate_f32(h->store, make_args<float>(h, C, sigma0), smem_limit, st);
   if (e != cudaSuccess) return cuda_fail(h, e, "iterate launch");
   CK(cudaEventRecord(e1, st), "event");
   Ctrl c{};
@@ -520,5 +519,34 @@ extern "C" gdwd_status gdwd_get_info(const gdwd_handle* h, gdwd_info* info) {
 extern "C" gdwd_status gdwd_get_phase_times(const gdwd_handle* h, double* ns, int32_t count) {
   if (!h || !ns || count < 0 || count > kPhaseSlots) return fail(nullptr, GDWD_EINVAL, "gdwd_get_phase_times: bad argument");
   for (int k = 0; k < count; ++k) ns[k] = h->phase_ns[k];
+  return GDWD_OK;
+}
+
+extern "C" gdwd_status gdwd_get_stored(const gdwd_handle* h, void* Zq, double* colscale) {
+  if (!h || (!Zq && !colscale)) return fail(nullptr, GDWD_EINVAL, "gdwd_get_stored: bad argument");
+  gdwd_handle* hh = const_cast<gdwd_handle*>(h);
+  const int es = h->L.esize;
+  const int64_t d = h->d, n = h->n, TB = h->L.TB;
+  if (Zq) {
+    std::vector<uint8_t> buf((size_t)h->L.NB * TB * n * es);
+    cudaError_t e = cudaMemcpyAsync(buf.data(), h->Z, buf.size(), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(hh, e, "gdwd_get_stored");
+    uint8_t* out = (uint8_t*)Zq;
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t j = 0; j < d; ++j) {
+        const int64_t s = j / TB, jl = j - s * TB;
+        std::memcpy(out + (i * d + j) * es, buf.data() + ((s * n + i) * TB + jl) * es, es);
+      }
+  }
+  if (colscale) {
+    if (h->store == GDWD_F64 || h->store == GDWD_F32) {
+      for (int64_t i = 0; i < n; ++i) colscale[i] = 1.0;
+    } else {
+      cudaError_t e = cudaMemcpyAsync(colscale, h->colscale, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+      if (e != cudaSuccess) return cuda_fail(hh, e, "gdwd_get_stored");
+    }
+  }
   return GDWD_OK;
 }

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <stdint.h>
 
 #include "../../include/gdwd.h"
@@ -249,5 +250,88 @@ struct ElemTraits<float> {
     v[3] = x.w;
   }
 };
+
+// 16-bit and 8-bit storage: products with FP32 operands, FP32 accumulation.
+__device__ __forceinline__ void bf16x2_to_float(uint32_t w, float* v) {
+  v[0] = __uint_as_float(w << 16);
+  v[1] = __uint_as_float(w & 0xffff0000u);
+}
+
+template <>
+struct ElemTraits<__nv_bfloat16> {
+  using compute_t = float;
+  static constexpr int kVec = 8;
+  __device__ __forceinline__ static void load(const void* p, float* v) {
+    const uint4 x = *reinterpret_cast<const uint4*>(p);
+    bf16x2_to_float(x.x, v);
+    bf16x2_to_float(x.y, v + 2);
+    bf16x2_to_float(x.z, v + 4);
+    bf16x2_to_float(x.w, v + 6);
+  }
+};
+
+template <>
+struct ElemTraits<__half> {
+  using compute_t = float;
+  static constexpr int kVec = 8;
+  __device__ __forceinline__ static void load(const void* p, float* v) {
+    const uint4 x = *reinterpret_cast<const uint4*>(p);
+    const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w[k]));
+      v[2 * k] = f.x;
+      v[2 * k + 1] = f.y;
+    }
+  }
+};
+
+template <>
+struct ElemTraits<__nv_fp8_e4m3> {
+  using compute_t = float;
+  static constexpr int kVec = 16;
+  __device__ __forceinline__ static void load(const void* p, float* v) {
+    const uint4 x = *reinterpret_cast<const uint4*>(p);
+    const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[k] & 0xffffu), __NV_E4M3);
+      const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[k] >> 16), __NV_E4M3);
+      const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&lo));
+      const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&hi));
+      v[4 * k] = a.x;
+      v[4 * k + 1] = a.y;
+      v[4 * k + 2] = b.x;
+      v[4 * k + 3] = b.y;
+    }
+  }
+};
+
+// n consecutive compute-type values from shared memory (n a multiple of 16 bytes)
+template <int N>
+__device__ __forceinline__ void load_ct(const float* p, float* v) {
+#pragma unroll
+  for (int k = 0; k < N; k += 4) {
+    const float4 x = *reinterpret_cast<const float4*>(p + k);
+    v[k] = x.x;
+    v[k + 1] = x.y;
+    v[k + 2] = x.z;
+    v[k + 3] = x.w;
+  }
+}
+template <int N>
+__device__ __forceinline__ void load_ct(const double* p, double* v) {
+#pragma unroll
+  for (int k = 0; k < N; k += 2) {
+    const double2 x = *reinterpret_cast<const double2*>(p + k);
+    v[k] = x.x;
+    v[k + 1] = x.y;
+  }
+}
+
+// Element size and format limits of a gdwd_dtype (host and device).
+__host__ __device__ inline int dtype_size(int dt) {
+  return dt == GDWD_F64 ? 8 : dt == GDWD_F32 ? 4 : dt == GDWD_E4M3 ? 1 : 2;
+}
 
 }  // namespace gdwd

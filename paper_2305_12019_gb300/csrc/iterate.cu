@@ -616,7 +616,13 @@ static int choose_cw_t(const Layout& L, int grid, int smem_limit) {
 }
 
 int choose_chunk_cols(int store, const Layout& L, int grid, int smem_limit) {
-  return store == GDWD_F64 ? choose_cw_t<double>(L, grid, smem_limit) : choose_cw_t<float>(L, grid, smem_limit);
+  switch (store) {
+    case GDWD_F64: return choose_cw_t<double>(L, grid, smem_limit);
+    case GDWD_BF16: return choose_cw_t<__nv_bfloat16>(L, grid, smem_limit);
+    case GDWD_F16: return choose_cw_t<__half>(L, grid, smem_limit);
+    case GDWD_E4M3: return choose_cw_t<__nv_fp8_e4m3>(L, grid, smem_limit);
+    default: return choose_cw_t<float>(L, grid, smem_limit);
+  }
 }
 
 // Plans the ring (stage size, stage count) for the available shared memory.
@@ -638,11 +644,22 @@ cudaError_t run_iterate_f64(const IterArgs<double>& a, int smem_limit, cudaStrea
   return launch_iterate_t<double>(a, stages, sb, smem, st);
 }
 
-cudaError_t run_iterate_f32(const IterArgs<float>& a, int smem_limit, cudaStream_t st) {
+template <typename T>
+static cudaError_t run_iterate_ft(const IterArgs<float>& a, int smem_limit, cudaStream_t st) {
   int stages, sb;
   size_t smem;
-  if (!plan_ring<float>(a.L, a.grid, smem_limit, stages, sb, smem)) return cudaErrorInvalidConfiguration;
-  return launch_iterate_t<float>(a, stages, sb, smem, st);
+  if (!plan_ring<T>(a.L, a.grid, smem_limit, stages, sb, smem)) return cudaErrorInvalidConfiguration;
+  return launch_iterate_t<T>(a, stages, sb, smem, st);
+}
+
+// FP32, BF16, FP16 and E4M3 storage (all compute in FP32)
+cudaError_t run_iterate_f32(int store, const IterArgs<float>& a, int smem_limit, cudaStream_t st) {
+  switch (store) {
+    case GDWD_BF16: return run_iterate_ft<__nv_bfloat16>(a, smem_limit, st);
+    case GDWD_F16: return run_iterate_ft<__half>(a, smem_limit, st);
+    case GDWD_E4M3: return run_iterate_ft<__nv_fp8_e4m3>(a, smem_limit, st);
+    default: return run_iterate_ft<float>(a, smem_limit, st);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -754,8 +771,13 @@ static cudaError_t run_apply_t(const Layout& L, int trans, const double* x, cons
 
 cudaError_t run_apply(int store, const Layout& L, int trans, const double* x, const double* sc, double* out,
                       void* partial, int grid, int smem_limit, int* err, uint64_t tmo, cudaStream_t st) {
-  if (store == GDWD_F64) return run_apply_t<double>(L, trans, x, sc, out, partial, grid, smem_limit, err, tmo, st);
-  return run_apply_t<float>(L, trans, x, sc, out, partial, grid, smem_limit, err, tmo, st);
+  switch (store) {
+    case GDWD_F64: return run_apply_t<double>(L, trans, x, sc, out, partial, grid, smem_limit, err, tmo, st);
+    case GDWD_BF16: return run_apply_t<__nv_bfloat16>(L, trans, x, sc, out, partial, grid, smem_limit, err, tmo, st);
+    case GDWD_F16: return run_apply_t<__half>(L, trans, x, sc, out, partial, grid, smem_limit, err, tmo, st);
+    case GDWD_E4M3: return run_apply_t<__nv_fp8_e4m3>(L, trans, x, sc, out, partial, grid, smem_limit, err, tmo, st);
+    default: return run_apply_t<float>(L, trans, x, sc, out, partial, grid, smem_limit, err, tmo, st);
+  }
 }
 
 }  // namespace gdwd

@@ -102,8 +102,8 @@ struct PassA {
           CT e0[VEC], e1[VEC], g0[VEC], g1[VEC];
           ElemTraits<T>::load(cp + v * VEC, e0);
           ElemTraits<T>::load(cp + (v + 8) * VEC, e1);
-          ElemTraits<CT>::load(g + v * VEC, g0);
-          ElemTraits<CT>::load(g + (v + 8) * VEC, g1);
+          load_ct<VEC>(g + v * VEC, g0);
+          load_ct<VEC>(g + (v + 8) * VEC, g1);
 #pragma unroll
           for (int kk = 0; kk < VEC; ++kk) {
             acc0 = fma(e0[kk], g0[kk], acc0);
@@ -113,7 +113,7 @@ struct PassA {
         if (v < Q) {
           CT e0[VEC], g0[VEC];
           ElemTraits<T>::load(cp + v * VEC, e0);
-          ElemTraits<CT>::load(g + v * VEC, g0);
+          load_ct<VEC>(g + v * VEC, g0);
 #pragma unroll
           for (int kk = 0; kk < VEC; ++kk) acc0 = fma(e0[kk], g0[kk], acc0);
         }

@@ -72,23 +72,110 @@ __global__ void scale_kernel(const double* sumsq, int64_t n, double* sc, double*
   if (blockIdx.x == 0 && threadIdx.x == 0) *zscale = zs;
 }
 
+// Per-column absolute maximum of the input (one block per column, FP64).
+template <typename TI>
+__global__ void col_absmax_kernel(const TI* __restrict__ Z, int64_t d, int64_t ldz, double* amax) {
+  const int64_t i = blockIdx.x;
+  double m = 0.0;
+  for (int64_t j = threadIdx.x; j < d; j += blockDim.x) m = fmax(m, fabs((double)Z[i * ldz + j]));
+  for (int o = 16; o >= 1; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ double s[32];
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmax(t, s[w]);
+    amax[i] = t;
+  }
+}
+
+// Largest stored magnitude used by the per-column scale of each format.
+__host__ __device__ inline double fmt_max(int store) {
+  return store == GDWD_E4M3 ? 448.0 : store == GDWD_F16 ? 32768.0 : 1.0;
+}
+
+// s_i = absmax_i / fmt_max (1 for an all-zero column), stored in colscale.
+__global__ void colscale_kernel(const double* amax, int64_t n, double fmax_v, double* colscale) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    colscale[i] = amax[i] > 0.0 ? amax[i] / fmax_v : 1.0;
+}
+
+__device__ __forceinline__ void to_store(double v, __nv_bfloat16* o) { *o = __double2bfloat16(v); }
+__device__ __forceinline__ void to_store(double v, __half* o) { *o = __double2half(v); }
+__device__ __forceinline__ void to_store(double v, __nv_fp8_e4m3* o) {
+  o->__x = __nv_cvt_double_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+}
+
+// Zq_ji = round(Z_ji / s_i) in the storage format (round to nearest even,
+// saturating for E4M3), written into the slab layout.
+template <typename TI, typename TS>
+__global__ void quantize_slabs_kernel(const TI* __restrict__ Z, int64_t ldz, Layout L, const double* colscale,
+                                      TS* __restrict__ out) {
+  const int64_t per_slab = (int64_t)L.TB * L.n;
+  const int64_t total = per_slab * L.NB;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = idx / per_slab, rem = idx - s * per_slab;
+    const int64_t i = rem / L.TB, jl = rem - i * L.TB;
+    const int64_t j = s * L.TB + jl;
+    to_store(j < L.d ? (double)Z[i * ldz + j] / colscale[i] : 0.0, out + idx);
+  }
+}
+
+// sc_i = s_i / Z_scale for quantized storage
+__global__ void scale_q_kernel(const double* sumsq, const double* colscale, int64_t n, double* sc, double* zscale) {
+  const double zs = sqrt(sqrt(*sumsq));
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    sc[i] = colscale[i] / zs;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *zscale = zs;
+}
+
+template <typename TI, typename TS>
+static void quantize_t(const TI* Z, int64_t ldz, const Layout& L, void* out, double* amax, double* colscale,
+                       int store, cudaStream_t st) {
+  col_absmax_kernel<TI><<<(unsigned)L.n, 256, 0, st>>>(Z, L.d, ldz, amax);
+  colscale_kernel<<<(int)std::min<int64_t>((L.n + 255) / 256, 1024), 256, 0, st>>>(amax, L.n, fmt_max(store), colscale);
+  quantize_slabs_kernel<TI, TS><<<152 * 8, 256, 0, st>>>(Z, ldz, L, colscale, (TS*)out);
+}
+
 cudaError_t run_ingest(const void* Z, int zdt, int64_t ldz, const Layout& L, void* out, int store, double* part,
-                       int nparts, double* sumsq, int* nonfinite, double* sc, double* zscale, cudaStream_t st) {
+                       int nparts, double* sumsq, int* nonfinite, double* sc, double* zscale, double* amax,
+                       double* colscale, cudaStream_t st) {
   if (zdt == GDWD_F64)
     sumsq_kernel<double><<<nparts, 256, 0, st>>>((const double*)Z, L.d, L.n, ldz, part, nonfinite);
   else
     sumsq_kernel<float><<<nparts, 256, 0, st>>>((const float*)Z, L.d, L.n, ldz, part, nonfinite);
   sum_parts_kernel<<<1, 32, 0, st>>>(part, nparts, sumsq);
   const int blocks = 152 * 8;
-  if (zdt == GDWD_F64 && store == GDWD_F64)
-    to_slabs_kernel<double, double><<<blocks, 256, 0, st>>>((const double*)Z, ldz, L, (double*)out);
-  else if (zdt == GDWD_F64 && store == GDWD_F32)
-    to_slabs_kernel<double, float><<<blocks, 256, 0, st>>>((const double*)Z, ldz, L, (float*)out);
-  else if (zdt == GDWD_F32 && store == GDWD_F64)
-    to_slabs_kernel<float, double><<<blocks, 256, 0, st>>>((const float*)Z, ldz, L, (double*)out);
-  else
-    to_slabs_kernel<float, float><<<blocks, 256, 0, st>>>((const float*)Z, ldz, L, (float*)out);
-  scale_kernel<<<(int)std::min<int64_t>((L.n + 255) / 256, 1024), 256, 0, st>>>(sumsq, L.n, sc, zscale);
+  const int nb = (int)std::min<int64_t>((L.n + 255) / 256, 1024);
+  if (store == GDWD_F64 || store == GDWD_F32) {
+    if (zdt == GDWD_F64 && store == GDWD_F64)
+      to_slabs_kernel<double, double><<<blocks, 256, 0, st>>>((const double*)Z, ldz, L, (double*)out);
+    else if (zdt == GDWD_F64 && store == GDWD_F32)
+      to_slabs_kernel<double, float><<<blocks, 256, 0, st>>>((const double*)Z, ldz, L, (float*)out);
+    else if (zdt == GDWD_F32 && store == GDWD_F64)
+      to_slabs_kernel<float, double><<<blocks, 256, 0, st>>>((const float*)Z, ldz, L, (double*)out);
+    else
+      to_slabs_kernel<float, float><<<blocks, 256, 0, st>>>((const float*)Z, ldz, L, (float*)out);
+    scale_kernel<<<nb, 256, 0, st>>>(sumsq, L.n, sc, zscale);
+    return cudaGetLastError();
+  }
+  const bool f64 = zdt == GDWD_F64;
+  switch (store) {
+    case GDWD_BF16:
+      if (f64) quantize_t<double, __nv_bfloat16>((const double*)Z, ldz, L, out, amax, colscale, store, st);
+      else quantize_t<float, __nv_bfloat16>((const float*)Z, ldz, L, out, amax, colscale, store, st);
+      break;
+    case GDWD_F16:
+      if (f64) quantize_t<double, __half>((const double*)Z, ldz, L, out, amax, colscale, store, st);
+      else quantize_t<float, __half>((const float*)Z, ldz, L, out, amax, colscale, store, st);
+      break;
+    default:
+      if (f64) quantize_t<double, __nv_fp8_e4m3>((const double*)Z, ldz, L, out, amax, colscale, store, st);
+      else quantize_t<float, __nv_fp8_e4m3>((const float*)Z, ldz, L, out, amax, colscale, store, st);
+      break;
+  }
+  scale_q_kernel<<<nb, 256, 0, st>>>(sumsq, colscale, L.n, sc, zscale);
   return cudaGetLastError();
 }
 
@@ -96,7 +183,18 @@ cudaError_t run_ingest(const void* Z, int zdt, int64_t ldz, const Layout& L, voi
 constexpr int kGT = 64;   // output tile
 constexpr int kGK = 16;   // rows per chunk
 
+// compute type of the Gram tiles: FP64 for FP64 storage, FP32 otherwise (the
+// products of two BF16, FP16 or E4M3 values are exact in FP32)
 template <typename T>
+struct GramType {
+  using type = float;
+};
+template <>
+struct GramType<double> {
+  using type = double;
+};
+
+template <typename G>
 struct GramAcc;
 template <>
 struct GramAcc<float> {
@@ -123,40 +221,59 @@ struct GramAcc<double> {
   __device__ double get(int a, int b) const { return c[a][b]; }
 };
 
-// Loads rows [r0, r0+16) of columns [c0, c0+64) of slab s into sm[16][64].
-template <typename T>
-__device__ __forceinline__ void gram_load(const T* slab, const Layout& L, int r0, int64_t c0, T (*sm)[kGT]) {
-  constexpr int V = 16 / sizeof(T);               // elements per 16-byte vector
-  constexpr int PER = kGK * kGT / kThreads;       // 4 elements per thread
+// four consecutive stored elements (4-element aligned) converted to the Gram type
+__device__ __forceinline__ void load4(const double* p, double* v) {
+  const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void load4(const float* p, float* v) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+__device__ __forceinline__ void load4(const __nv_bfloat16* p, float* v) {
+  const uint2 a = *reinterpret_cast<const uint2*>(p);
+  bf16x2_to_float(a.x, v);
+  bf16x2_to_float(a.y, v + 2);
+}
+__device__ __forceinline__ void load4(const __half* p, float* v) {
+  const uint2 a = *reinterpret_cast<const uint2*>(p);
+  const float2 f0 = __half22float2(*reinterpret_cast<const __half2*>(&a.x));
+  const float2 f1 = __half22float2(*reinterpret_cast<const __half2*>(&a.y));
+  v[0] = f0.x; v[1] = f0.y; v[2] = f1.x; v[3] = f1.y;
+}
+__device__ __forceinline__ void load4(const __nv_fp8_e4m3* p, float* v) {
+  const uint32_t w = *reinterpret_cast<const uint32_t*>(p);
+  const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w & 0xffffu), __NV_E4M3);
+  const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w >> 16), __NV_E4M3);
+  const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&lo));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&hi));
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
+// Loads rows [r0, r0+16) of columns [c0, c0+64) of one slab into sm[16][64].
+template <typename T, typename GT>
+__device__ __forceinline__ void gram_load(const T* slab, const Layout& L, int r0, int64_t c0, GT (*sm)[kGT]) {
   const int t = threadIdx.x;
-  const int col = t / (kGK / PER);                // 0..63
-  const int k0 = (t % (kGK / PER)) * PER;         // 0,4,8,12
+  const int col = t >> 2;              // 0..63
+  const int k0 = (t & 3) * 4;          // 0, 4, 8, 12
   const int64_t gc = c0 + col;
+  const int rr = r0 + k0;
+  GT e[4];
+  if (gc < L.n && rr < L.TB) {         // TB is a multiple of 4: rows rr..rr+3 all valid
+    load4(slab + gc * L.TB + rr, e);
+  } else {
 #pragma unroll
-  for (int v = 0; v < PER; v += V) {
-    const int rr = r0 + k0 + v;
-    T e[V];
-    if (gc < L.n && rr < L.TB) {
-      if constexpr (sizeof(T) == 4) {
-        const float4 x = *reinterpret_cast<const float4*>(slab + gc * L.TB + rr);
-        e[0] = x.x; e[1] = x.y; e[2] = x.z; e[3] = x.w;
-      } else {
-        const double2 x = *reinterpret_cast<const double2*>(slab + gc * L.TB + rr);
-        e[0] = x.x; e[1] = x.y;
-      }
-    } else {
-#pragma unroll
-      for (int q = 0; q < V; ++q) e[q] = (T)0;
-    }
-#pragma unroll
-    for (int q = 0; q < V; ++q) sm[k0 + v + q][col] = e[q];
+    for (int q = 0; q < 4; ++q) e[q] = (GT)0;
   }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) sm[k0 + q][col] = e[q];
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) gram_kernel(Layout L, int T_tiles, int ksplit, double* Kpart) {
-  __shared__ __align__(16) T As[kGK][kGT];
-  __shared__ __align__(16) T Bs[kGK][kGT];
+  using GT = typename GramType<T>::type;
+  __shared__ __align__(16) GT As[kGK][kGT];
+  __shared__ __align__(16) GT Bs[kGK][kGT];
   const int tile = blockIdx.x / ksplit, sp = blockIdx.x % ksplit;
   // tile -> (I, J), I >= J, row-major over the lower triangle
   int I = (int)((sqrt(8.0 * tile + 1.0) - 1.0) * 0.5);
@@ -165,18 +282,18 @@ __global__ void __launch_bounds__(kThreads) gram_kernel(Layout L, int T_tiles, i
   const int J = tile - I * (I + 1) / 2;
   const int s0 = (int)((int64_t)L.NB * sp / ksplit), s1 = (int)((int64_t)L.NB * (sp + 1) / ksplit);
   const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
-  GramAcc<T> acc;
+  GramAcc<GT> acc;
   acc.zero();
   const T* Zs = reinterpret_cast<const T*>(L.Z);
   for (int s = s0; s < s1; ++s) {
     const T* slab = Zs + (int64_t)s * L.TB * L.n;
     for (int r0 = 0; r0 < L.TB; r0 += kGK) {
-      gram_load<T>(slab, L, r0, (int64_t)I * kGT, As);
-      gram_load<T>(slab, L, r0, (int64_t)J * kGT, Bs);
+      gram_load<T, GT>(slab, L, r0, (int64_t)I * kGT, As);
+      gram_load<T, GT>(slab, L, r0, (int64_t)J * kGT, Bs);
       __syncthreads();
 #pragma unroll
       for (int k = 0; k < kGK; ++k) {
-        T a[4], b[4];
+        GT a[4], b[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           a[q] = As[k][ty * 4 + q];
@@ -228,10 +345,14 @@ cudaError_t run_gram(int store, const Layout& L, int ksplit, double* Kpart, cons
                      cudaStream_t st) {
   const int Tt = (int)((L.n + kGT - 1) / kGT);
   const int tiles = Tt * (Tt + 1) / 2;
-  if (store == GDWD_F64)
-    gram_kernel<double><<<tiles * ksplit, kThreads, 0, st>>>(L, Tt, ksplit, Kpart);
-  else
-    gram_kernel<float><<<tiles * ksplit, kThreads, 0, st>>>(L, Tt, ksplit, Kpart);
+  const dim3 grid(tiles * ksplit);
+  switch (store) {
+    case GDWD_F64: gram_kernel<double><<<grid, kThreads, 0, st>>>(L, Tt, ksplit, Kpart); break;
+    case GDWD_BF16: gram_kernel<__nv_bfloat16><<<grid, kThreads, 0, st>>>(L, Tt, ksplit, Kpart); break;
+    case GDWD_F16: gram_kernel<__half><<<grid, kThreads, 0, st>>>(L, Tt, ksplit, Kpart); break;
+    case GDWD_E4M3: gram_kernel<__nv_fp8_e4m3><<<grid, kThreads, 0, st>>>(L, Tt, ksplit, Kpart); break;
+    default: gram_kernel<float><<<grid, kThreads, 0, st>>>(L, Tt, ksplit, Kpart); break;
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   gram_finish_kernel<<<1024, 256, 0, st>>>(Kpart, ksplit, sc, L.n, 1.0 / mu, G);

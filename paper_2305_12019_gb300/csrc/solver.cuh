@@ -109,7 +109,7 @@ struct IterArgs {
 // Host-side launchers (defined in the .cu files).
 int choose_chunk_cols(int store, const Layout& L, int grid, int smem_limit);
 cudaError_t run_iterate_f64(const IterArgs<double>& a, int smem_limit, cudaStream_t st);
-cudaError_t run_iterate_f32(const IterArgs<float>& a, int smem_limit, cudaStream_t st);
+cudaError_t run_iterate_f32(int store, const IterArgs<float>& a, int smem_limit, cudaStream_t st);
 cudaError_t run_apply(int store, const Layout& L, int trans, const double* x, const double* sc, double* out,
                       void* partial, int grid, int smem_limit, int* err, uint64_t tmo, cudaStream_t st);
 
@@ -131,7 +131,8 @@ struct FactorArgs {
   uint64_t timeout_ns;
 };
 cudaError_t run_ingest(const void* Z, int zdt, int64_t ldz, const Layout& L, void* out, int store, double* part,
-                       int nparts, double* sumsq, int* nonfinite, double* sc, double* zscale, cudaStream_t st);
+                       int nparts, double* sumsq, int* nonfinite, double* sc, double* zscale, double* amax,
+                       double* colscale, cudaStream_t st);
 int gram_ksplit(const Layout& L, int sms);
 cudaError_t run_gram(int store, const Layout& L, int ksplit, double* Kpart, const double* sc, double mu, double* G,
                      cudaStream_t st);

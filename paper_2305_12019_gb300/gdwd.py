@@ -48,7 +48,8 @@ class Info(ctypes.Structure):
 
 
 EXPORTS = ["gdwd_default_options", "gdwd_create", "gdwd_solve", "gdwd_free", "gdwd_last_error", "gdwd_prox",
-           "gdwd_apply", "gdwd_gram", "gdwd_get_info", "gdwd_get_phase_times"]
+           "gdwd_apply", "gdwd_gram", "gdwd_get_info", "gdwd_get_phase_times", "gdwd_get_stored"]
+STORE_NP = {F64: "float64", F32: "float32", BF16: "uint16", F16: "float16", E4M3: "uint8"}
 PHASES = ["A", "A_wait", "R", "R_wait", "N1_rows", "N1_wait", "N2_rows", "N2_wait", "B", "B_wait", "S_kkt",
           "N2_rhs", "N2_gemv", "S_sums", "N1_rhs", "N1_gemv"]
 
@@ -81,6 +82,7 @@ def load(path: str = LIB_PATH):
     lib.gdwd_gram.argtypes = [c_void_p, c_void_p]
     lib.gdwd_get_info.argtypes = [c_void_p, POINTER(Info)]
     lib.gdwd_get_phase_times.argtypes = [c_void_p, POINTER(c_double), c_int32]
+    lib.gdwd_get_stored.argtypes = [c_void_p, c_void_p, c_void_p]
     for name in EXPORTS:
         if name != "gdwd_last_error":
             getattr(lib, name).restype = c_int32
@@ -184,6 +186,15 @@ class Solver:
         i = Info()
         _check(_lib.gdwd_get_info(self._h, ctypes.byref(i)), self._h)
         return i.as_dict()
+
+    def stored(self):
+        """(Zq, colscale): the stored data as raw codes (BF16 as uint16 bits, E4M3 as
+        uint8 bits, FP16 as float16) in a d x n array, and the per-column scales."""
+        i = self.info()
+        Zq = np.zeros((self.n, self.d), dtype=STORE_NP[i["store"]])
+        cs = np.zeros(self.n, dtype=np.float64)
+        _check(_lib.gdwd_get_stored(self._h, c_void_p(Zq.ctypes.data), c_void_p(cs.ctypes.data)), self._h)
+        return Zq.T, cs
 
     def phase_times(self):
         """Per-phase device time (ns) of the last solve, CTA 0's view (gdwd_get_phase_times)."""

@@ -77,8 +77,8 @@ def test_invalid_arguments_rejected(lib):
     o.tau = 1.7
     assert _create(lib, Z, y, opts=o)[0] == 1
     o = gdwd.default_options()
-    o.store = gdwd.BF16
-    assert _create(lib, Z, y, opts=o)[0] == 8
+    o.store = 9
+    assert _create(lib, Z, y, opts=o)[0] == 1
     assert lib.gdwd_free(None) == 0
     assert lib.gdwd_solve(None, None, 0, None, 0, None, None) == 1
     assert lib.gdwd_prox(None, None, None, 1.0, -1.0, 4, None, None) == 1

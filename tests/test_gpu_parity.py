@@ -199,3 +199,46 @@ def test_invalid_and_edge_cases(gdwd_lib):
     assert abs(w[0, 0] - 1.0) <= 1e-6 and abs(res[0]["beta"]) <= 1e-6
     with pytest.raises(gdwd_lib.GdwdError):
         gdwd_lib.Solver(np.ones((3, 2)), np.array([1.0, 1.0]), 1.0, 1.0)
+
+
+# --------------------------------------------------------------------- low-precision storage
+
+@pytest.mark.parametrize("fmt", ["bf16", "f16", "e4m3"])
+def test_quantized_codes_bit_exact(gdwd_lib, fmt):
+    """Stored codes and per-column scales equal the independent numpy rounding model."""
+    from tests import quantize_ref as QR
+    rng = np.random.default_rng(17)
+    d, n = 1037, 45
+    y = np.where(np.arange(n) < 20, 1.0, -1.0)
+    X = rng.standard_t(3, size=(d, n)).astype(np.float32)
+    X[:, 3] = 0.0                      # an all-zero column
+    X[5, 7] = 1e-30                    # deep subnormal after scaling
+    Z = (X * y).astype(np.float32)
+    with gdwd_lib.Solver(Z, y, 1.0, 1.0, store=fmt) as s:
+        codes, cs = s.stored()
+    q_ref, s_ref = QR.quantize(Z.astype(np.float64), fmt)
+    assert np.array_equal(cs, s_ref)
+    got = QR.decode(codes, fmt)
+    assert np.array_equal(got, q_ref), np.argwhere(got != q_ref)[:5]
+
+
+@pytest.mark.parametrize("fmt,q,C", [("bf16", 1.0, 10.0), ("f16", 2.0, 5.0), ("e4m3", 1.0, 1.0)])
+def test_quantized_solve_matches_oracle(gdwd_lib, fmt, q, C):
+    """The quantized problem solved on the GPU equals the oracle on the dequantized data."""
+    from tests import quantize_ref as QR
+    inst = synth.gaussian(seed=31 + len(fmt), d=5003, n=257, shift=1.0, n_pos=100, q=q, C=C, m_test=500)
+    Z = inst.Z
+    with gdwd_lib.Solver(Z, inst.y, q, C, store=fmt, tol=1e-6) as s:
+        res, w, alpha = s.solve(alpha=True)
+    r = res[0]
+    assert r["status"] == 0 and r["kkt"] <= 1e-6, r
+    qv, sc = QR.quantize(Z.astype(np.float64), fmt)
+    Zdq = qv * sc[None, :]
+    ref = O.solve(Zdq, inst.y, q, C, tol=1e-9)
+    _compare(r, w[:, 0], ref)
+    up, lo, gap = O.certified_gap(Zdq, inst.y, w[:, 0], r["beta"], alpha[:, 0], q, C)
+    assert gap <= 1e-5
+    # the quantized optimum against the optimum of the original data (reported, loose bound)
+    ref_orig = O.solve(Z.astype(np.float64), inst.y, q, C, tol=1e-9)
+    rel = abs(r["primal_obj"] - ref_orig["primal"]) / abs(ref_orig["primal"])
+    assert rel <= {"bf16": 1e-2, "f16": 1e-3, "e4m3": 1e-1}[fmt], rel

@@ -87,7 +87,7 @@ template <typename T>
 static cudaError_t halloc(gdwd_handle* h, T** p, size_t count) {
   void* q = nullptr;
   const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
-  cudaError_t e = cudaMalloc(&q, bytes);
+  cudaError_t e = cudaMallocAsync(&q, bytes, h->stream);
   if (e != cudaSuccess) return e;
   h->allocs.push_back(q);
   h->bytes += bytes;
@@ -96,7 +96,7 @@ static cudaError_t halloc(gdwd_handle* h, T** p, size_t count) {
 }
 
 static void release(gdwd_handle* h) {
-  for (void* p : h->allocs) cudaFree(p);
+  for (void* p : h->allocs) cudaFreeAsync(p, h->stream);
   h->allocs.clear();
 }
 
@@ -121,7 +121,9 @@ static int esize_of(int dt) { return dt == GDWD_F64 ? 8 : dt == GDWD_F32 ? 4 : d
 // Chooses slab height, slab count, chunk width and grid (see Layout).
 static void plan_layout(gdwd_handle* h) {
   const int es = esize_of(h->store);
-  const int vec = 16 / es;
+  // slab heights are a multiple of the 16-byte vector and of 4 rows (the Gram
+  // tile loader reads 4 consecutive rows of a column)
+  const int vec = std::max(16 / es, 4);
   const int gp = h->opt.grid > 0 ? std::min(h->opt.grid, h->sms) : h->sms;
   const int64_t d = h->d;
   int TB;
@@ -187,6 +189,17 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
   {
     cudaError_t e = cudaGetDevice(&h->device);
     if (e != cudaSuccess) return bail(cuda_fail(nullptr, e, "cudaGetDevice"));
+    // handle memory comes from the device's stream-ordered pool; keep freed blocks
+    // cached in the pool so that creating the next handle does not go to the driver
+    static bool pool_set[64] = {};
+    if (h->device >= 0 && h->device < 64 && !pool_set[h->device]) {
+      cudaMemPool_t pool;
+      if (cudaDeviceGetDefaultMemPool(&pool, h->device) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+      }
+      pool_set[h->device] = true;
+    }
     cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
     cudaDeviceGetAttribute(&h->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
     int coop = 0;
@@ -206,7 +219,7 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
     const int zes = esize_of(zdt);
     // persistent arrays
     void* zbuf = nullptr;
-    CK(cudaMalloc(&zbuf, (size_t)dpad * n * es), "cudaMalloc(Z)");
+    CK(cudaMallocAsync(&zbuf, (size_t)dpad * n * es, h->stream), "cudaMalloc(Z)");
     h->allocs.push_back(zbuf);
     h->bytes += (size_t)dpad * n * es;
     h->Z = zbuf;
@@ -253,11 +266,11 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
     void* staging = nullptr;
     int64_t ld = ldz;
     if (!z_on_device) {
-      CK(cudaMalloc(&staging, (size_t)d * n * zes), "cudaMalloc(staging)");
+      CK(cudaMallocAsync(&staging, (size_t)d * n * zes, h->stream), "cudaMalloc(staging)");
       cudaError_t ec = cudaMemcpy2DAsync(staging, (size_t)d * zes, Z, (size_t)ldz * zes, (size_t)d * zes, (size_t)n,
                                          cudaMemcpyHostToDevice, h->stream);
       if (ec != cudaSuccess) {
-        cudaFree(staging);
+        cudaFreeAsync(staging, h->stream);
         return cuda_fail(h, ec, "copy Z");
       }
       zsrc = staging;
@@ -266,30 +279,30 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
     const int nparts = 1024;
     double* part = nullptr;
     int* nonfinite = h->err;
-    CK(cudaMalloc(&part, nparts * sizeof(double)), "cudaMalloc");
+    CK(cudaMallocAsync(&part, nparts * sizeof(double), h->stream), "cudaMalloc");
     cudaError_t ei = run_ingest(zsrc, zdt, ld, h->L, h->Z, h->store, part, nparts, h->dscalars, nonfinite, h->sc,
                                 h->dscalars + 1, h->amax, h->colscale, h->stream);
     int nf = 0;
     if (ei == cudaSuccess) ei = cudaMemcpyAsync(&nf, nonfinite, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     if (ei == cudaSuccess) ei = cudaStreamSynchronize(h->stream);
-    cudaFree(part);
-    if (staging) cudaFree(staging);
+    cudaFreeAsync(part, h->stream);
+    if (staging) cudaFreeAsync(staging, h->stream);
     if (ei != cudaSuccess) return cuda_fail(h, ei, "ingest");
     if (nf) return fail(h, GDWD_EINVAL, "gdwd_create: Z has non-finite entries");
     CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream), "memset");
     // Gram and G = I + K / mu
     const int ks = gram_ksplit(h->L, h->sms);
     double* Kpart = nullptr;
-    CK(cudaMalloc(&Kpart, (size_t)ks * n * n * sizeof(double)), "cudaMalloc(Kpart)");
+    CK(cudaMallocAsync(&Kpart, (size_t)ks * n * n * sizeof(double), h->stream), "cudaMalloc(Kpart)");
     cudaError_t eg = run_gram(h->store, h->L, ks, Kpart, h->sc, h->opt.mu, h->G, h->stream);
     if (eg == cudaSuccess) eg = cudaStreamSynchronize(h->stream);
-    cudaFree(Kpart);
+    cudaFreeAsync(Kpart, h->stream);
     if (eg != cudaSuccess) return cuda_fail(h, eg, "gram");
     // Cholesky, inverse, p, s
     double *A = nullptr, *X = nullptr, *Pd = nullptr;
-    CK(cudaMalloc(&A, (size_t)n * n * sizeof(double)), "cudaMalloc(A)");
-    cudaError_t ef = cudaMalloc(&X, (size_t)n * n * sizeof(double));
-    if (ef == cudaSuccess) ef = cudaMalloc(&Pd, (size_t)n * n * sizeof(double));
+    CK(cudaMallocAsync(&A, (size_t)n * n * sizeof(double), h->stream), "cudaMalloc(A)");
+    cudaError_t ef = cudaMallocAsync(&X, (size_t)n * n * sizeof(double), h->stream);
+    if (ef == cudaSuccess) ef = cudaMallocAsync(&Pd, (size_t)n * n * sizeof(double), h->stream);
     if (ef == cudaSuccess) ef = cudaMemcpyAsync(A, h->G, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
     if (ef == cudaSuccess) ef = cudaMemsetAsync(h->bar, 0, sizeof(unsigned), h->stream);
     const int fgrid = h->sms;
@@ -304,9 +317,9 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
     if (ef == cudaSuccess) ef = cudaMemcpyAsync(hs, h->dscalars, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     if (ef == cudaSuccess) ef = cudaEventRecord(e1, h->stream);
     if (ef == cudaSuccess) ef = cudaStreamSynchronize(h->stream);
-    cudaFree(A);
-    cudaFree(X);
-    cudaFree(Pd);
+    cudaFreeAsync(A, h->stream);
+    cudaFreeAsync(X, h->stream);
+    cudaFreeAsync(Pd, h->stream);
     if (ef != cudaSuccess) return cuda_fail(h, ef, "factor");
     if (ferr == GDWD_ENOTPD) return fail(h, GDWD_ENOTPD, "gdwd_create: Cholesky met a non-positive pivot");
     if (ferr) return fail(h, (gdwd_status)ferr, "gdwd_create: factor kernel reported an error");

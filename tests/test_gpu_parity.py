@@ -65,7 +65,7 @@ def test_prox_parity(gdwd_lib, q):
 
 
 @pytest.mark.parametrize("store,d,n", [("f64", 3001, 257), ("f32", 3001, 257), ("f32", 9000, 130),
-                                       ("f64", 37, 300)])
+                                       ("f64", 37, 300), ("f64", 2500, 157), ("f32", 1111, 65)])
 def test_gram_parity(gdwd_lib, store, d, n):
     rng = np.random.default_rng(d + n)
     y = np.where(np.arange(n) % 3 == 0, 1.0, -1.0)

@@ -299,15 +299,13 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
     cudaFreeAsync(Kpart, h->stream);
     if (eg != cudaSuccess) return cuda_fail(h, eg, "gram");
     // Cholesky, inverse, p, s
-    double *A = nullptr, *X = nullptr, *Pd = nullptr;
-    CK(cudaMallocAsync(&A, (size_t)n * n * sizeof(double), h->stream), "cudaMalloc(A)");
-    cudaError_t ef = cudaMallocAsync(&X, (size_t)n * n * sizeof(double), h->stream);
-    if (ef == cudaSuccess) ef = cudaMallocAsync(&Pd, (size_t)n * n * sizeof(double), h->stream);
-    if (ef == cudaSuccess) ef = cudaMemcpyAsync(A, h->G, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
+    float2 *A = nullptr, *X = nullptr;
+    CK(cudaMallocAsync(&A, (size_t)n * n * sizeof(float2), h->stream), "cudaMalloc(A)");
+    cudaError_t ef = cudaMallocAsync(&X, (size_t)n * n * sizeof(float2), h->stream);
     if (ef == cudaSuccess) ef = cudaMemsetAsync(h->bar, 0, sizeof(unsigned), h->stream);
     const int fgrid = h->sms;
     if (ef == cudaSuccess) {
-      FactorArgs fa{A, X, Pd, h->P, h->ldP, h->y, h->p, h->pdf, h->dscalars + 2, n, fgrid, h->bar, h->err,
+      FactorArgs fa{h->G, A, X, h->P, h->ldP, h->y, h->p, h->pdf, h->dscalars + 2, n, fgrid, h->bar, h->err,
                     (uint64_t)(h->opt.timeout_s * 1e9)};
       ef = run_factor(fa, h->stream);
     }
@@ -319,7 +317,6 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
     if (ef == cudaSuccess) ef = cudaStreamSynchronize(h->stream);
     cudaFreeAsync(A, h->stream);
     cudaFreeAsync(X, h->stream);
-    cudaFreeAsync(Pd, h->stream);
     if (ef != cudaSuccess) return cuda_fail(h, ef, "factor");
     if (ferr == GDWD_ENOTPD) return fail(h, GDWD_ENOTPD, "gdwd_create: Cholesky met a non-positive pivot");
     if (ferr) return fail(h, (gdwd_status)ferr, "gdwd_create: factor kernel reported an error");

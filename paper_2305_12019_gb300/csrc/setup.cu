@@ -360,33 +360,32 @@ cudaError_t run_gram(int store, const Layout& L, int ksplit, double* Kpart, cons
 }
 
 // ------------------------------------------------------------------ factor
-constexpr int kNB = 32;   // tile of the blocked factorization
+// One cooperative launch computes G = L L^T, X = L^{-1} and P = X^T X = G^{-1}
+// with 32x32 tiles.  The matrices live in double-float (float2 hi/lo, ~48-bit
+// mantissa): FP64 issues at 1/58 of the FP32 rate on this part, so the bulk
+// tile updates (n^3/6 multiply-adds in each of the three stages) run in
+// double-float on the FP32 pipes; the small sequential pieces (the 32x32
+// diagonal Cholesky, the triangular solves against it) run in FP64.
+constexpr int kNB = 32;   // tile
 
-// C[32x32] -= A[32xk] B[32xk]^T over k = 32, tiles in shared memory (row-major).
-__device__ __forceinline__ void tile_sub_abt(double (*C)[kNB + 1], const double (*Am)[kNB + 1],
-                                             const double (*Bm)[kNB + 1]) {
-  // 256 threads, 4 outputs each: rows r = t / 8 (0..31), cols c = (t % 8) + 8 * q
-  const int r = threadIdx.x >> 3, c0 = threadIdx.x & 7;
-  double acc[4] = {0, 0, 0, 0};
-#pragma unroll 8
-  for (int k = 0; k < kNB; ++k) {
-    const double a = Am[r][k];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] = fma(a, Bm[c0 + 8 * q][k], acc[q]);
-  }
-#pragma unroll
-  for (int q = 0; q < 4; ++q) C[r][c0 + 8 * q] -= acc[q];
+__device__ __forceinline__ double f2d(float2 v) { return (double)v.x + (double)v.y; }
+__device__ __forceinline__ float2 d2f(double x) {
+  const df h = df_from(x);
+  return make_float2(h.hi, h.lo);
 }
 
-__device__ __forceinline__ void load_tile(double (*S)[kNB + 1], const double* M, int64_t n, int64_t r0, int64_t c0) {
+// tile [r0, r0+32) x [c0, c0+32) of a row-major n x n df matrix into shared memory
+__device__ __forceinline__ void load_tile_df(float2 (*S)[kNB + 1], const float2* M, int64_t n, int64_t r0,
+                                             int64_t c0, bool unit_pad) {
   for (int t = threadIdx.x; t < kNB * kNB; t += kThreads) {
     const int r = t / kNB, c = t % kNB;
     const int64_t gr = r0 + r, gc = c0 + c;
-    S[r][c] = (gr < n && gc < n) ? M[gr * n + gc] : (gr == gc ? 1.0 : 0.0);
+    S[r][c] = (gr < n && gc < n) ? M[gr * n + gc] : make_float2((unit_pad && gr == gc) ? 1.f : 0.f, 0.f);
   }
 }
 
-__device__ __forceinline__ void store_tile(const double (*S)[kNB + 1], double* M, int64_t n, int64_t r0, int64_t c0) {
+__device__ __forceinline__ void store_tile_df(const float2 (*S)[kNB + 1], float2* M, int64_t n, int64_t r0,
+                                              int64_t c0) {
   for (int t = threadIdx.x; t < kNB * kNB; t += kThreads) {
     const int r = t / kNB, c = t % kNB;
     const int64_t gr = r0 + r, gc = c0 + c;
@@ -394,183 +393,226 @@ __device__ __forceinline__ void store_tile(const double (*S)[kNB + 1], double* M
   }
 }
 
+// C[32x32] += sgn * A B^T (all double-float tiles in shared memory).  256
+// threads, 4 outputs each (row r = t / 8, columns t % 8 + 8 q).
+__device__ __forceinline__ void tile_acc_abt(float2 (*C)[kNB + 1], const float2 (*Am)[kNB + 1],
+                                             const float2 (*Bm)[kNB + 1], float sgn) {
+  const int r = threadIdx.x >> 3, c0 = threadIdx.x & 7;
+  df acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll 4
+  for (int k = 0; k < kNB; ++k) {
+    const float2 a = Am[r][k];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float2 b = Bm[c0 + 8 * q][k];
+      df_fma(acc[q], df{a.x, a.y}, df{b.x, b.y});
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    df cv{C[r][c0 + 8 * q].x, C[r][c0 + 8 * q].y};
+    df_add(cv, df{sgn * acc[q].hi, sgn * acc[q].lo});
+    C[r][c0 + 8 * q] = make_float2(cv.hi, cv.lo);
+  }
+}
+
+// tile index t of the lower triangle (row-major) -> (i, j), i >= j
+__device__ __forceinline__ void tri_index(int t, int& i, int& j) {
+  int ii = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+  while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
+  while (ii * (ii + 1) / 2 > t) --ii;
+  i = ii;
+  j = t - ii * (ii + 1) / 2;
+}
+
 __global__ void __launch_bounds__(kThreads, 1) factor_kernel(FactorArgs a) {
-  __shared__ double T0[kNB][kNB + 1], T1[kNB][kNB + 1], T2[kNB][kNB + 1];
+  __shared__ float2 T0[kNB][kNB + 1], T1[kNB][kNB + 1], T2[kNB][kNB + 1];
+  __shared__ double D[kNB][kNB + 1];     // FP64 diagonal tile
   __shared__ int s_flag;
   __shared__ double s_red[kWarps + 1];
   const int64_t n = a.n;
   const int nb = (int)((n + kNB - 1) / kNB);
   const int cta = blockIdx.x, grid = a.grid;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float2* A = a.A;
+  float2* X = a.X;
   unsigned gen = 0;
 #define FBAR()                                                                          \
   do {                                                                                  \
     if (!grid_barrier(a.bar, (unsigned)grid, gen, a.err, a.timeout_ns, &s_flag)) return; \
   } while (0)
 
-  // ---------------- Cholesky, right-looking, tile columns k = 0..nb-1
+  // ---------------- df copy of G (lower triangle) and X = I
+  for (int64_t idx = (int64_t)cta * kThreads + threadIdx.x; idx < n * n; idx += (int64_t)grid * kThreads) {
+    const int64_t i = idx / n, j = idx - i * n;
+    A[idx] = j <= i ? d2f(a.G[idx]) : make_float2(0.f, 0.f);
+    X[idx] = make_float2(i == j ? 1.f : 0.f, 0.f);
+  }
+  FBAR();
+
+  // ---------------- Cholesky, right-looking over tile columns
   for (int k = 0; k < nb; ++k) {
     const int64_t k0 = (int64_t)k * kNB;
     if (cta == 0) {
-      load_tile(T0, a.A, n, k0, k0);
+      // FP64 unblocked Cholesky of the diagonal tile by warp 0 (lane = row)
+      for (int t = threadIdx.x; t < kNB * kNB; t += kThreads) {
+        const int r = t / kNB, c = t % kNB;
+        const int64_t gr = k0 + r, gc = k0 + c;
+        D[r][c] = (gr < n && gc < n) ? f2d(A[gr * n + gc]) : (gr == gc ? 1.0 : 0.0);
+      }
       __syncthreads();
-      // unblocked Cholesky of the 32x32 diagonal tile by warp 0
       if (warp == 0) {
         for (int c = 0; c < kNB; ++c) {
-          double piv = T0[c][c];
+          double piv = D[c][c];
           if (!(piv > 0.0) || !isfinite(piv)) {
             if (lane == 0) atomicCAS(a.err, 0, (int)GDWD_ENOTPD);
             piv = 1.0;
           }
           const double lc = sqrt(piv);
           __syncwarp();
-          // column c below the pivot
-          const int r = lane;
-          if (r > c) T0[r][c] /= lc;
+          if (lane > c) D[lane][c] /= lc;
           __syncwarp();
-          if (lane == 0) T0[c][c] = lc;
+          if (lane == 0) D[c][c] = lc;
           __syncwarp();
-          // trailing update (lower part) of columns c+1..31
-          if (r > c)
-            for (int cc = c + 1; cc <= r; ++cc) T0[r][cc] -= T0[r][c] * T0[cc][c];
+          if (lane > c)
+            for (int cc = c + 1; cc <= lane; ++cc) D[lane][cc] -= D[lane][c] * D[cc][c];
           __syncwarp();
         }
       }
       __syncthreads();
-      store_tile(T0, a.A, n, k0, k0);
+      for (int t = threadIdx.x; t < kNB * kNB; t += kThreads) {
+        const int r = t / kNB, c = t % kNB;
+        const int64_t gr = k0 + r, gc = k0 + c;
+        if (gr < n && gc < n && c <= r) A[gr * n + gc] = d2f(D[r][c]);
+      }
     }
     FBAR();
-    // panel: rows i >= k0 + 32, L_ik = A_ik L_kk^{-T}; one warp per row
-    load_tile(T0, a.A, n, k0, k0);
+    // panel rows below the diagonal tile: L_ik = A_ik L_kk^{-T}, one warp per row (FP64)
+    for (int t = threadIdx.x; t < kNB * kNB; t += kThreads) {
+      const int r = t / kNB, c = t % kNB;
+      const int64_t gr = k0 + r, gc = k0 + c;
+      D[r][c] = (gr < n && gc < n) ? f2d(A[gr * n + gc]) : (gr == gc ? 1.0 : 0.0);
+    }
     __syncthreads();
     for (int64_t i = k0 + kNB + (int64_t)cta * kWarps + warp; i < n; i += (int64_t)grid * kWarps) {
-      double x = (k0 + lane < n) ? a.A[i * n + k0 + lane] : 0.0;
+      double x = (k0 + lane < n) ? f2d(A[i * n + k0 + lane]) : 0.0;
       for (int c = 0; c < kNB; ++c) {
-        const double xc = __shfl_sync(0xffffffffu, x, c) / T0[c][c];
+        const double xc = __shfl_sync(0xffffffffu, x, c) / D[c][c];
         if (lane == c) x = xc;
-        if (lane > c) x -= xc * T0[lane][c];
+        if (lane > c) x -= xc * D[lane][c];
       }
-      if (k0 + lane < n) a.A[i * n + k0 + lane] = x;
+      if (k0 + lane < n) A[i * n + k0 + lane] = d2f(x);
     }
     FBAR();
-    // trailing update of tiles (I, J), k < J <= I
+    // trailing update A_IJ -= L_Ik L_Jk^T for tiles k < J <= I (double-float)
     {
       const int m = nb - k - 1;
       const int ntile = m * (m + 1) / 2;
       for (int t = cta; t < ntile; t += grid) {
-        int ii = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
-        while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
-        while (ii * (ii + 1) / 2 > t) --ii;
-        const int jj = t - ii * (ii + 1) / 2;
+        int ii, jj;
+        tri_index(t, ii, jj);
         const int64_t I0 = (int64_t)(k + 1 + ii) * kNB, J0 = (int64_t)(k + 1 + jj) * kNB;
-        load_tile(T0, a.A, n, I0, J0);
-        load_tile(T1, a.A, n, I0, k0);
-        load_tile(T2, a.A, n, J0, k0);
+        load_tile_df(T0, A, n, I0, J0, true);
+        load_tile_df(T1, A, n, I0, k0, false);
+        load_tile_df(T2, A, n, J0, k0, false);
         __syncthreads();
-        tile_sub_abt(T0, T1, T2);
+        tile_acc_abt(T0, T1, T2, -1.f);
         __syncthreads();
-        store_tile(T0, a.A, n, I0, J0);
+        store_tile_df(T0, A, n, I0, J0);
         __syncthreads();
       }
     }
     FBAR();
   }
 
-  // ---------------- X = L^{-1}: solve L X = I by tile rows; X starts as I
-  for (int64_t idx = (int64_t)cta * kThreads + threadIdx.x; idx < n * n; idx += (int64_t)grid * kThreads) {
-    const int64_t i = idx / n, j = idx - i * n;
-    a.X[idx] = (i == j) ? 1.0 : 0.0;
-  }
-  FBAR();
+  // ---------------- X = L^{-1}: L X = I by tile rows (X starts as I)
   for (int k = 0; k < nb; ++k) {
     const int64_t k0 = (int64_t)k * kNB;
-    // X[k-tile rows, columns < k0+32] = L_kk^{-1} X[...]: one warp per column
-    load_tile(T0, a.A, n, k0, k0);
+    for (int t = threadIdx.x; t < kNB * kNB; t += kThreads) {
+      const int r = t / kNB, c = t % kNB;
+      const int64_t gr = k0 + r, gc = k0 + c;
+      D[r][c] = (gr < n && gc < n) ? f2d(A[gr * n + gc]) : (gr == gc ? 1.0 : 0.0);
+    }
     __syncthreads();
+    // X[k-tile rows, j] = L_kk^{-1} X[k-tile rows, j] for j < k0 + 32: one warp per column (FP64)
     const int64_t ncols = (n < k0 + kNB) ? n : k0 + kNB;
     for (int64_t j = (int64_t)cta * kWarps + warp; j < ncols; j += (int64_t)grid * kWarps) {
-      double x = (k0 + lane < n) ? a.X[(k0 + lane) * n + j] : 0.0;
+      double x = (k0 + lane < n) ? f2d(X[(k0 + lane) * n + j]) : 0.0;
       for (int c = 0; c < kNB; ++c) {
-        const double xc = __shfl_sync(0xffffffffu, x, c) / T0[c][c];
+        const double xc = __shfl_sync(0xffffffffu, x, c) / D[c][c];
         if (lane == c) x = xc;
-        if (lane > c) x -= xc * T0[lane][c];
+        if (lane > c) x -= xc * D[lane][c];
       }
-      if (k0 + lane < n) a.X[(k0 + lane) * n + j] = x;
+      if (k0 + lane < n) X[(k0 + lane) * n + j] = d2f(x);
     }
     FBAR();
-    // rows below: X[I, J] -= L[I, k] X[k, J] for tile rows I > k, tile columns J <= k
+    // X[I, J] -= L[I, k] X[k, J] for tile rows I > k, tile columns J <= k (double-float)
     {
       const int m = nb - k - 1;
       const int ntile = m * (k + 1);
       for (int t = cta; t < ntile; t += grid) {
         const int ii = t / (k + 1), jj = t % (k + 1);
         const int64_t I0 = (int64_t)(k + 1 + ii) * kNB, J0 = (int64_t)jj * kNB;
-        load_tile(T0, a.X, n, I0, J0);
-        load_tile(T1, a.A, n, I0, k0);
-        // T2 = X[k-tile, J-tile]^T so that tile_sub_abt computes L_Ik X_kJ
-        for (int q = threadIdx.x; q < kNB * kNB; q += kThreads) {
+        load_tile_df(T0, X, n, I0, J0, false);
+        load_tile_df(T1, A, n, I0, k0, false);
+        for (int q = threadIdx.x; q < kNB * kNB; q += kThreads) {     // T2 = X[k-tile, J-tile]^T
           const int r = q / kNB, c = q % kNB;
           const int64_t gr = k0 + c, gc = J0 + r;
-          T2[r][c] = (gr < n && gc < n) ? a.X[gr * n + gc] : 0.0;
+          T2[r][c] = (gr < n && gc < n) ? X[gr * n + gc] : make_float2(0.f, 0.f);
         }
         __syncthreads();
-        tile_sub_abt(T0, T1, T2);
+        tile_acc_abt(T0, T1, T2, -1.f);
         __syncthreads();
-        store_tile(T0, a.X, n, I0, J0);
+        store_tile_df(T0, X, n, I0, J0);
         __syncthreads();
       }
     }
     FBAR();
   }
 
-  // ---------------- P = X^T X (X lower triangular): P_IJ = sum_{M >= I} X_MI^T X_MJ, I >= J
+  // ---------------- P = X^T X (X lower): P_IJ = sum_{M >= I} X_MI^T X_MJ, I >= J
   {
     const int ntile = nb * (nb + 1) / 2;
     for (int t = cta; t < ntile; t += grid) {
-      int ii = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
-      while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
-      while (ii * (ii + 1) / 2 > t) --ii;
-      const int jj = t - ii * (ii + 1) / 2;
+      int ii, jj;
+      tri_index(t, ii, jj);
       const int64_t I0 = (int64_t)ii * kNB, J0 = (int64_t)jj * kNB;
-      for (int q = threadIdx.x; q < kNB * kNB; q += kThreads) T0[q / kNB][q % kNB] = 0.0;
+      for (int q = threadIdx.x; q < kNB * kNB; q += kThreads) T0[q / kNB][q % kNB] = make_float2(0.f, 0.f);
       for (int M = ii; M < nb; ++M) {
         const int64_t M0 = (int64_t)M * kNB;
-        // T1[r][m] = X[M0+m][I0+r], T2[c][m] = X[M0+m][J0+c]; C -= -(...): accumulate with sign
         for (int q = threadIdx.x; q < kNB * kNB; q += kThreads) {
           const int r = q / kNB, c = q % kNB;
           const int64_t gm = M0 + c;
-          T1[r][c] = (gm < n && I0 + r < n) ? -a.X[gm * n + I0 + r] : 0.0;
-          T2[r][c] = (gm < n && J0 + r < n) ? a.X[gm * n + J0 + r] : 0.0;
+          T1[r][c] = (gm < n && I0 + r < n) ? X[gm * n + I0 + r] : make_float2(0.f, 0.f);
+          T2[r][c] = (gm < n && J0 + r < n) ? X[gm * n + J0 + r] : make_float2(0.f, 0.f);
         }
         __syncthreads();
-        tile_sub_abt(T0, T1, T2);   // T0 -= (-X_MI^T) X_MJ
+        tile_acc_abt(T0, T1, T2, 1.f);
         __syncthreads();
       }
       for (int q = threadIdx.x; q < kNB * kNB; q += kThreads) {
         const int r = q / kNB, c = q % kNB;
         const int64_t gi = I0 + r, gj = J0 + c;
         if (gi < n && gj < n && gi >= gj) {
-          const double v = T0[r][c];
-          a.Pd[gi * n + gj] = v;
-          a.Pd[gj * n + gi] = v;
-          const df h = df_from(v);
-          a.P[gi * a.ldP + gj] = make_float2(h.hi, h.lo);
-          a.P[gj * a.ldP + gi] = make_float2(h.hi, h.lo);
+          a.P[gi * a.ldP + gj] = T0[r][c];
+          a.P[gj * a.ldP + gi] = T0[r][c];
         }
       }
       __syncthreads();
     }
   }
   FBAR();
-  // ---------------- p = P y (FP64), s = y^T p
+  // ---------------- p = P y (double-float), s = y^T p
   for (int64_t i = (int64_t)cta * kWarps + warp; i < n; i += (int64_t)grid * kWarps) {
-    double acc = 0.0;
-    for (int64_t j = lane; j < n; j += 32) acc = fma(a.Pd[i * n + j], a.y[j], acc);
-    acc = warp_sum(acc);
+    df acc{0.f, 0.f};
+    for (int64_t j = lane; j < n; j += 32) {
+      const float2 pv = a.P[i * a.ldP + j];
+      df_fma(acc, df{pv.x, pv.y}, df_from(a.y[j]));
+    }
+    acc = df_warp_sum(acc);
     if (lane == 0) {
-      a.p[i] = acc;
-      const df h = df_from(acc);
-      a.pdf[i] = make_float2(h.hi, h.lo);
+      a.p[i] = df_to_double(acc);
+      a.pdf[i] = make_float2(acc.hi, acc.lo);
     }
   }
   FBAR();

@@ -115,9 +115,9 @@ cudaError_t run_apply(int store, const Layout& L, int trans, const double* x, co
 
 // set-up (setup.cu)
 struct FactorArgs {
-  double* A;          // n x n working copy of G (row-major); L in the lower triangle on exit
-  double* X;          // n x n: L^{-1} (lower) on exit
-  double* Pd;         // n x n FP64 G^{-1}
+  const double* G;    // n x n FP64 G (row-major)
+  float2* A;          // n x n double-float work: G, then L in the lower triangle
+  float2* X;          // n x n double-float work: L^{-1}
   float2* P;          // n x ldP double-float G^{-1} (padding zero)
   int ldP;
   const double* y;

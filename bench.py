@@ -287,6 +287,7 @@ def main():
             "detail": {"setup_ms": t_setup_ms, "iterate_ms": t_iter_ms, "iterations": iters,
                        "step_ms": step_ms, "wall_s": wall, "grid": info["grid"], "slabs": info["slabs"],
                        "block_rows": info["block_rows"], "kkt": [r["kkt"] for r in results],
+                       "setup_stages_ms": {k: info[k] for k in ("t_ingest_ms", "t_gram_ms", "t_factor_ms")},
                        "phase_us_per_iter": {k: v / 1e3 / iters for k, v in info["phase_ns"].items()}}}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         t_or, ref = run_oracle_solve(inst)

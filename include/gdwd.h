@@ -177,7 +177,10 @@ typedef struct {
   int64_t device_bytes;  /* all device memory owned by the handle            */
   double zscale;         /* Z_scale                                          */
   double t_setup_ms;     /* device time of the set-up                        */
-  int64_t reserved[4];
+  double t_ingest_ms;    /* of which: copy / quantize into the slab layout   */
+  double t_gram_ms;      /*           Gram matrix G                          */
+  double t_factor_ms;    /*           Cholesky, inverse, p, s                */
+  int64_t reserved[1];
 } gdwd_info;
 
 gdwd_status gdwd_get_info(const gdwd_handle* h, gdwd_info* info);

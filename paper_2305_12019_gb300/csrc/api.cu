@@ -45,6 +45,7 @@ struct gdwd_handle {
   double zscale = 0.0;
   double s = 0.0;
   double t_setup_ms = 0.0;
+  double t_stage_ms[3] = {0.0, 0.0, 0.0};   // ingest, Gram, factor
   size_t bytes = 0;
   std::vector<void*> allocs;
   // device arrays
@@ -210,9 +211,11 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
   if ((n + h->grid - 1) / h->grid > kMaxRowsPerCta)
     return bail(fail(nullptr, GDWD_EUNSUPPORTED, "gdwd_create: n too large for the n x n factor path of this build"));
   st = [&]() -> gdwd_status {
-    cudaEvent_t e0, e1;
+    cudaEvent_t e0, e1, eg, ef0;
     CK(cudaEventCreate(&e0), "cudaEventCreate");
     CK(cudaEventCreate(&e1), "cudaEventCreate");
+    CK(cudaEventCreate(&eg), "cudaEventCreate");
+    CK(cudaEventCreate(&ef0), "cudaEventCreate");
     CK(cudaEventRecord(e0, h->stream), "cudaEventRecord");
     const int64_t dpad = (int64_t)h->L.NB * h->L.TB;
     const int es = h->L.esize;
@@ -291,6 +294,7 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
     if (nf) return fail(h, GDWD_EINVAL, "gdwd_create: Z has non-finite entries");
     CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream), "memset");
     // Gram and G = I + K / mu
+    CK(cudaEventRecord(eg, h->stream), "cudaEventRecord");
     const int ks = gram_ksplit(h->L, h->sms);
     double* Kpart = nullptr;
     CK(cudaMallocAsync(&Kpart, (size_t)ks * n * n * sizeof(double), h->stream), "cudaMalloc(Kpart)");
@@ -299,6 +303,7 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
     cudaFreeAsync(Kpart, h->stream);
     if (eg != cudaSuccess) return cuda_fail(h, eg, "gram");
     // Cholesky, inverse, p, s
+    CK(cudaEventRecord(ef0, h->stream), "cudaEventRecord");
     float2 *A = nullptr, *X = nullptr;
     CK(cudaMallocAsync(&A, (size_t)n * n * sizeof(float2), h->stream), "cudaMalloc(A)");
     cudaError_t ef = cudaMallocAsync(&X, (size_t)n * n * sizeof(float2), h->stream);
@@ -322,11 +327,19 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
     if (ferr) return fail(h, (gdwd_status)ferr, "gdwd_create: factor kernel reported an error");
     h->zscale = hs[1];
     h->s = hs[2];
-    float ms = 0.f;
+    float ms = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventElapsedTime(&m1, e0, eg);
+    cudaEventElapsedTime(&m2, eg, ef0);
+    cudaEventElapsedTime(&m3, ef0, e1);
     h->t_setup_ms = ms;
+    h->t_stage_ms[0] = m1;
+    h->t_stage_ms[1] = m2;
+    h->t_stage_ms[2] = m3;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    cudaEventDestroy(eg);
+    cudaEventDestroy(ef0);
     if (!(h->s > 0.0) || !std::isfinite(h->s)) return fail(h, GDWD_ENUMERIC, "gdwd_create: y^T G^{-1} y is not positive");
     return GDWD_OK;
   }();
@@ -523,6 +536,9 @@ extern "C" gdwd_status gdwd_get_info(const gdwd_handle* h, gdwd_info* info) {
   info->device_bytes = (int64_t)h->bytes;
   info->zscale = h->zscale;
   info->t_setup_ms = h->t_setup_ms;
+  info->t_ingest_ms = h->t_stage_ms[0];
+  info->t_gram_ms = h->t_stage_ms[1];
+  info->t_factor_ms = h->t_stage_ms[2];
   return GDWD_OK;
 }
 

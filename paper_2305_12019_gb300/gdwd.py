@@ -41,7 +41,8 @@ class Result(ctypes.Structure):
 class Info(ctypes.Structure):
     _fields_ = [("d", c_int64), ("n", c_int64), ("store", c_int32), ("block_rows", c_int32), ("slabs", c_int32),
                 ("grid", c_int32), ("z_bytes", c_int64), ("device_bytes", c_int64), ("zscale", c_double),
-                ("t_setup_ms", c_double), ("reserved", c_int64 * 4)]
+                ("t_setup_ms", c_double), ("t_ingest_ms", c_double), ("t_gram_ms", c_double),
+                ("t_factor_ms", c_double), ("reserved", c_int64 * 1)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}

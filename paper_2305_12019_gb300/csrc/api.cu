@@ -211,10 +211,10 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
   if ((n + h->grid - 1) / h->grid > kMaxRowsPerCta)
     return bail(fail(nullptr, GDWD_EUNSUPPORTED, "gdwd_create: n too large for the n x n factor path of this build"));
   st = [&]() -> gdwd_status {
-    cudaEvent_t e0, e1, eg, ef0;
+    cudaEvent_t e0, e1, evg, ef0;
     CK(cudaEventCreate(&e0), "cudaEventCreate");
     CK(cudaEventCreate(&e1), "cudaEventCreate");
-    CK(cudaEventCreate(&eg), "cudaEventCreate");
+    CK(cudaEventCreate(&evg), "cudaEventCreate");
     CK(cudaEventCreate(&ef0), "cudaEventCreate");
     CK(cudaEventRecord(e0, h->stream), "cudaEventRecord");
     const int64_t dpad = (int64_t)h->L.NB * h->L.TB;
@@ -294,7 +294,7 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
     if (nf) return fail(h, GDWD_EINVAL, "gdwd_create: Z has non-finite entries");
     CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream), "memset");
     // Gram and G = I + K / mu
-    CK(cudaEventRecord(eg, h->stream), "cudaEventRecord");
+    CK(cudaEventRecord(evg, h->stream), "cudaEventRecord");
     const int ks = gram_ksplit(h->L, h->sms);
     double* Kpart = nullptr;
     CK(cudaMallocAsync(&Kpart, (size_t)ks * n * n * sizeof(double), h->stream), "cudaMalloc(Kpart)");
@@ -329,8 +329,8 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
     h->s = hs[2];
     float ms = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventElapsedTime(&m1, e0, eg);
-    cudaEventElapsedTime(&m2, eg, ef0);
+    cudaEventElapsedTime(&m1, e0, evg);
+    cudaEventElapsedTime(&m2, evg, ef0);
     cudaEventElapsedTime(&m3, ef0, e1);
     h->t_setup_ms = ms;
     h->t_stage_ms[0] = m1;
@@ -338,7 +338,7 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
     h->t_stage_ms[2] = m3;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaEventDestroy(eg);
+    cudaEventDestroy(evg);
     cudaEventDestroy(ef0);
     if (!(h->s > 0.0) || !std::isfinite(h->s)) return fail(h, GDWD_ENUMERIC, "gdwd_create: y^T G^{-1} y is not positive");
     return GDWD_OK;

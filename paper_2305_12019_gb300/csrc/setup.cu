@@ -428,6 +428,7 @@ __device__ __forceinline__ void tri_index(int t, int& i, int& j) {
 __global__ void __launch_bounds__(kThreads, 1) factor_kernel(FactorArgs a) {
   __shared__ float2 T0[kNB][kNB + 1], T1[kNB][kNB + 1], T2[kNB][kNB + 1];
   __shared__ double D[kNB][kNB + 1];     // FP64 diagonal tile
+  __shared__ double Dinv[kNB];           // its inverse diagonal
   __shared__ int s_flag;
   __shared__ double s_red[kWarps + 1];
   const int64_t n = a.n;
@@ -468,9 +469,10 @@ __global__ void __launch_bounds__(kThreads, 1) factor_kernel(FactorArgs a) {
             if (lane == 0) atomicCAS(a.err, 0, (int)GDWD_ENOTPD);
             piv = 1.0;
           }
-          const double lc = sqrt(piv);
+          const double lc = sqrt_nr(piv);
+          const double ilc = rcp_nr(lc);
           __syncwarp();
-          if (lane > c) D[lane][c] /= lc;
+          if (lane > c) D[lane][c] *= ilc;
           __syncwarp();
           if (lane == 0) D[c][c] = lc;
           __syncwarp();
@@ -494,10 +496,12 @@ __global__ void __launch_bounds__(kThreads, 1) factor_kernel(FactorArgs a) {
       D[r][c] = (gr < n && gc < n) ? f2d(A[gr * n + gc]) : (gr == gc ? 1.0 : 0.0);
     }
     __syncthreads();
+    if (threadIdx.x < kNB) Dinv[threadIdx.x] = rcp_nr(D[threadIdx.x][threadIdx.x]);
+    __syncthreads();
     for (int64_t i = k0 + kNB + (int64_t)cta * kWarps + warp; i < n; i += (int64_t)grid * kWarps) {
       double x = (k0 + lane < n) ? f2d(A[i * n + k0 + lane]) : 0.0;
       for (int c = 0; c < kNB; ++c) {
-        const double xc = __shfl_sync(0xffffffffu, x, c) / D[c][c];
+        const double xc = __shfl_sync(0xffffffffu, x, c) * Dinv[c];
         if (lane == c) x = xc;
         if (lane > c) x -= xc * D[lane][c];
       }
@@ -534,12 +538,14 @@ __global__ void __launch_bounds__(kThreads, 1) factor_kernel(FactorArgs a) {
       D[r][c] = (gr < n && gc < n) ? f2d(A[gr * n + gc]) : (gr == gc ? 1.0 : 0.0);
     }
     __syncthreads();
+    if (threadIdx.x < kNB) Dinv[threadIdx.x] = rcp_nr(D[threadIdx.x][threadIdx.x]);
+    __syncthreads();
     // X[k-tile rows, j] = L_kk^{-1} X[k-tile rows, j] for j < k0 + 32: one warp per column (FP64)
     const int64_t ncols = (n < k0 + kNB) ? n : k0 + kNB;
     for (int64_t j = (int64_t)cta * kWarps + warp; j < ncols; j += (int64_t)grid * kWarps) {
       double x = (k0 + lane < n) ? f2d(X[(k0 + lane) * n + j]) : 0.0;
       for (int c = 0; c < kNB; ++c) {
-        const double xc = __shfl_sync(0xffffffffu, x, c) / D[c][c];
+        const double xc = __shfl_sync(0xffffffffu, x, c) * Dinv[c];
         if (lane == c) x = xc;
         if (lane > c) x -= xc * D[lane][c];
       }

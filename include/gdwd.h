@@ -42,7 +42,8 @@ typedef enum {
   GDWD_ENUMERIC = 5,   /* NaN/Inf appeared in the iteration                             */
   GDWD_ETIMEOUT = 6,   /* a bounded device-side wait ran out; the kernel returned       */
   GDWD_ECUDA = 7,      /* a CUDA runtime call failed (message in gdwd_last_error)       */
-  GDWD_EUNSUPPORTED = 8 /* valid request this build does not implement                  */
+  GDWD_EUNSUPPORTED = 8, /* valid request this build does not implement                 */
+  GDWD_EAGAIN = 9        /* server: the request is still queued or running               */
 } gdwd_status;
 
 /* Element types, for the caller's Z and for the copy the handle stores. */
@@ -209,6 +210,52 @@ gdwd_status gdwd_get_phase_times(const gdwd_handle* h, double* ns, int32_t count
  * Diagnostics; the paper has no counterpart.  Errors: EINVAL, ECUDA.
  */
 gdwd_status gdwd_get_stored(const gdwd_handle* h, void* Zq, double* colscale);
+
+/*
+ * ---------------------------------------------------------------- serving
+ * Many independent problems of different (d, n, q, C) on one GPU.  A server
+ * owns `slots` CUDA streams; each slot runs one problem at a time (create,
+ * solve, free) with its persistent kernels restricted to sms / slots CTAs, so
+ * the slots' work overlaps on the device.  Requests are taken in arrival order
+ * as a slot frees up (continuous batching) and admitted only while the sum of
+ * the device footprints of the problems in flight stays within hbm_budget
+ * bytes (a request larger than the budget runs alone).  The paper solves one
+ * problem at a time (Sec. 4.5); this layer has no counterpart there.
+ */
+typedef struct {
+  const void* Z;        /* d x n column-major, column i = y_i x_i (as gdwd_create)     */
+  int32_t zdt;          /* GDWD_F64 or GDWD_F32                                        */
+  int32_t z_on_device;  /* 0: host memory, 1: device memory                            */
+  int64_t d, n, ldz;
+  const double* y;      /* n labels, host                                              */
+  double q, C;
+  gdwd_options opts;    /* store, tol, ...; stream and grid are set by the server      */
+  double* w;            /* host output, d doubles (original units), or NULL            */
+  double* alpha;        /* host output, n doubles, or NULL                             */
+} gdwd_request;
+
+typedef struct gdwd_server gdwd_server;
+
+/* slots >= 1; hbm_budget in bytes (0 = 80% of the device's free memory). */
+gdwd_status gdwd_server_create(int32_t slots, uint64_t hbm_budget, gdwd_server** out);
+
+/* Queues a request (the struct is copied; Z, y, w and alpha must stay valid
+   until the request completes).  ticket receives its id.  Never blocks. */
+gdwd_status gdwd_server_submit(gdwd_server* s, const gdwd_request* r, uint64_t* ticket);
+
+/* Result of a ticket: GDWD_EAGAIN while it is queued or running (wait == 0),
+   else the request's own status with *res filled and latency_ms = completion
+   minus submission time (host steady clock).  wait != 0 blocks until done.
+   A ticket is released once its result has been returned. */
+gdwd_status gdwd_server_poll(gdwd_server* s, uint64_t ticket, int32_t wait, gdwd_result* res, double* latency_ms);
+
+/* Waits for all submitted requests, stops the workers, frees the server. */
+gdwd_status gdwd_server_destroy(gdwd_server* s);
+
+/* An uneven batch of nreq independent problems through a temporary server
+   with `slots` concurrent slots; res[i] and latency (may be NULL) per request. */
+gdwd_status gdwd_solve_batch(const gdwd_request* reqs, int32_t nreq, int32_t slots, gdwd_result* res,
+                             double* latency_ms);
 
 #ifdef __cplusplus
 }

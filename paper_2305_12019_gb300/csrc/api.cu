@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -193,6 +194,8 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
     // handle memory comes from the device's stream-ordered pool; keep freed blocks
     // cached in the pool so that creating the next handle does not go to the driver
     static bool pool_set[64] = {};
+    static std::mutex pool_mu;
+    std::lock_guard<std::mutex> pool_lock(pool_mu);
     if (h->device >= 0 && h->device < 64 && !pool_set[h->device]) {
       cudaMemPool_t pool;
       if (cudaDeviceGetDefaultMemPool(&pool, h->device) == cudaSuccess) {
@@ -308,7 +311,7 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
     CK(cudaMallocAsync(&A, (size_t)n * n * sizeof(float2), h->stream), "cudaMalloc(A)");
     cudaError_t ef = cudaMallocAsync(&X, (size_t)n * n * sizeof(float2), h->stream);
     if (ef == cudaSuccess) ef = cudaMemsetAsync(h->bar, 0, sizeof(unsigned), h->stream);
-    const int fgrid = h->sms;
+    const int fgrid = h->grid;   // the handle's SM share (all SMs unless restricted by opt.grid)
     if (ef == cudaSuccess) {
       FactorArgs fa{h->G, A, X, h->P, h->ldP, h->y, h->p, h->pdf, h->dscalars + 2, n, fgrid, h->bar, h->err,
                     (uint64_t)(h->opt.timeout_s * 1e9)};

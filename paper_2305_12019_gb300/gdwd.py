@@ -48,8 +48,16 @@ class Info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("Z", c_void_p), ("zdt", c_int32), ("z_on_device", c_int32), ("d", c_int64), ("n", c_int64),
+                ("ldz", c_int64), ("y", c_void_p), ("q", c_double), ("C", c_double), ("opts", Options),
+                ("w", c_void_p), ("alpha", c_void_p)]
+
+
 EXPORTS = ["gdwd_default_options", "gdwd_create", "gdwd_solve", "gdwd_free", "gdwd_last_error", "gdwd_prox",
-           "gdwd_apply", "gdwd_gram", "gdwd_get_info", "gdwd_get_phase_times", "gdwd_get_stored"]
+           "gdwd_apply", "gdwd_gram", "gdwd_get_info", "gdwd_get_phase_times", "gdwd_get_stored",
+           "gdwd_server_create", "gdwd_server_submit", "gdwd_server_poll", "gdwd_server_destroy", "gdwd_solve_batch"]
+EAGAIN = 9
 STORE_NP = {F64: "float64", F32: "float32", BF16: "uint16", F16: "float16", E4M3: "uint8"}
 PHASES = ["A", "A_wait", "R", "R_wait", "N1_rows", "N1_wait", "N2_rows", "N2_wait", "B", "B_wait", "S_kkt",
           "N2_rhs", "N2_gemv", "S_sums", "N1_rhs", "N1_gemv"]
@@ -84,6 +92,11 @@ def load(path: str = LIB_PATH):
     lib.gdwd_get_info.argtypes = [c_void_p, POINTER(Info)]
     lib.gdwd_get_phase_times.argtypes = [c_void_p, POINTER(c_double), c_int32]
     lib.gdwd_get_stored.argtypes = [c_void_p, c_void_p, c_void_p]
+    lib.gdwd_server_create.argtypes = [c_int32, ctypes.c_uint64, POINTER(c_void_p)]
+    lib.gdwd_server_submit.argtypes = [c_void_p, POINTER(Request), POINTER(ctypes.c_uint64)]
+    lib.gdwd_server_poll.argtypes = [c_void_p, ctypes.c_uint64, c_int32, POINTER(Result), POINTER(c_double)]
+    lib.gdwd_server_destroy.argtypes = [c_void_p]
+    lib.gdwd_solve_batch.argtypes = [POINTER(Request), c_int32, c_int32, POINTER(Result), POINTER(c_double)]
     for name in EXPORTS:
         if name != "gdwd_last_error":
             getattr(lib, name).restype = c_int32
@@ -231,3 +244,81 @@ def prox(a, sigma, q, r0=None, omega=None, out=None, stream=None):
                        c_void_p(out.data_ptr()), stream)
     _check(st, None)
     return out
+
+
+def make_request(Z, y, q, C, *, store="f32", tol=1e-6, sigma0=0.0, max_iter=20000, mu=1.0, tau=1.618,
+                 timeout_s=2.0, want_alpha=False):
+    """A gdwd_request for host data (numpy, column-major copy) with host outputs.
+
+    Returns (request, keep) where keep holds the arrays that must outlive the
+    request and keep["w"] / keep["alpha"] receive the results."""
+    Zn = np.asfortranarray(np.asarray(Z))
+    if Zn.dtype not in (np.float32, np.float64):
+        Zn = Zn.astype(np.float64)
+    yv = np.ascontiguousarray(np.asarray(y, dtype=np.float64))
+    d, n = Zn.shape
+    w = np.zeros(d)
+    al = np.zeros(n) if want_alpha else None
+    o = default_options()
+    o.mu, o.tau, o.tol, o.sigma0, o.max_iter, o.timeout_s = mu, tau, tol, sigma0, max_iter, timeout_s
+    o.store = DTYPES[store] if isinstance(store, str) else int(store)
+    r = Request(Z=Zn.ctypes.data, zdt=F64 if Zn.dtype == np.float64 else F32, z_on_device=0, d=d, n=n, ldz=d,
+                y=yv.ctypes.data, q=float(q), C=float(C), opts=o, w=w.ctypes.data,
+                alpha=None if al is None else al.ctypes.data)
+    return r, {"Z": Zn, "y": yv, "w": w, "alpha": al}
+
+
+class Server:
+    """gdwd_server: continuous batching of independent problems over `slots` streams."""
+
+    def __init__(self, slots=4, hbm_budget=0):
+        lib = load()
+        self._s = c_void_p()
+        _check(lib.gdwd_server_create(int(slots), int(hbm_budget), ctypes.byref(self._s)), None)
+        self._keep = {}
+
+    def submit(self, request, keep=None):
+        t = ctypes.c_uint64()
+        _check(_lib.gdwd_server_submit(self._s, ctypes.byref(request), ctypes.byref(t)), None)
+        self._keep[t.value] = (request, keep)
+        return t.value
+
+    def poll(self, ticket, wait=True):
+        """(result dict, latency_ms) or None while pending."""
+        res = Result()
+        lat = c_double()
+        st = _lib.gdwd_server_poll(self._s, ticket, int(bool(wait)), ctypes.byref(res), ctypes.byref(lat))
+        if st == EAGAIN:
+            return None
+        if st not in (OK, EMAXITER):
+            raise GdwdError(st, _lib.gdwd_last_error(None).decode(errors="replace"))
+        self._keep.pop(ticket, None)
+        return res.as_dict(), lat.value
+
+    def close(self):
+        if getattr(self, "_s", None) is not None and self._s.value:
+            _lib.gdwd_server_destroy(self._s)
+            self._s = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def solve_batch(requests, slots=4):
+    """gdwd_solve_batch over a list of Request structs: (results, latencies_ms, status)."""
+    lib = load()
+    k = len(requests)
+    arr = (Request * k)(*requests)
+    res = (Result * k)()
+    lat = (c_double * k)()
+    st = lib.gdwd_solve_batch(arr, k, int(slots), res, lat)
+    return [r.as_dict() for r in res], list(lat), st

@@ -82,3 +82,20 @@ def test_invalid_arguments_rejected(lib):
     assert lib.gdwd_free(None) == 0
     assert lib.gdwd_solve(None, None, 0, None, 0, None, None) == 1
     assert lib.gdwd_prox(None, None, None, 1.0, -1.0, 4, None, None) == 1
+
+
+def test_request_struct_size():
+    from paper_2305_12019_gb300 import gdwd
+    # void* + 2 int32 + 3 int64 + ptr + 2 double + gdwd_options + 2 ptr (LP64)
+    assert ctypes.sizeof(gdwd.Request) == 8 + 8 + 24 + 8 + 16 + ctypes.sizeof(gdwd.Options) + 16
+
+
+def test_server_arguments_rejected(lib):
+    from paper_2305_12019_gb300 import gdwd
+    s = ctypes.c_void_p()
+    assert lib.gdwd_server_create(0, 0, ctypes.byref(s)) == 1
+    assert lib.gdwd_server_create(65, 0, ctypes.byref(s)) == 1
+    assert lib.gdwd_server_submit(None, None, None) == 1
+    assert lib.gdwd_server_destroy(None) == 0
+    assert lib.gdwd_solve_batch(None, -1, 1, None, None) == 1
+    assert lib.gdwd_solve_batch(None, 0, 1, None, None) == 0

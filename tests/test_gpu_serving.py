@@ -1,0 +1,101 @@
+"""GPU tests of the batching / serving layer (gdwd_solve_batch, gdwd_server_*).
+
+Uneven problems of different (d, n, q, C) run concurrently on disjoint SM
+shares; each result must match the FP64 oracle, and a request's result must be
+the same alone and in a mix (within the solution tolerance: different SM shares
+change the slab layout and hence the summation order).
+"""
+import numpy as np
+import pytest
+
+from oracle import gdwd_oracle as O
+from paper_2305_12019_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _instances(count, seed):
+    shapes = synth.uneven_batch(seed, count=count, d_range=(800, 6000), n_range=(40, 300))
+    out = []
+    for sh in shapes:
+        inst = synth.gaussian(seed=sh["seed"], d=sh["d"], n=sh["n"], shift=1.5, n_pos=sh["n_pos"], q=sh["q"],
+                              C=sh["C"], dtype=np.float32)
+        out.append(inst)
+    return out
+
+
+def _check(res, w, inst, obj_tol=1e-6, w_tol=1e-4):
+    ref = O.solve(inst.Z.astype(np.float64), inst.y, inst.q, inst.C, tol=1e-9, max_iter=100000)
+    relobj = abs(res["primal_obj"] - ref["primal"]) / abs(ref["primal"])
+    relw = np.linalg.norm(w - ref["w"]) / np.linalg.norm(ref["w"])
+    assert relobj <= obj_tol and relw <= w_tol, (relobj, relw, inst.d, inst.n, inst.q)
+
+
+def test_solve_batch_uneven(gdwd_lib):
+    insts = _instances(6, 11)
+    reqs, keeps = [], []
+    for inst in insts:
+        r, k = gdwd_lib.make_request(inst.Z, inst.y, inst.q, inst.C, store="f32", tol=1e-6)
+        reqs.append(r)
+        keeps.append(k)
+    res, lat, st = gdwd_lib.solve_batch(reqs, slots=3)
+    assert st == 0
+    for r, k, inst, l in zip(res, keeps, insts, lat):
+        assert r["status"] == 0 and r["kkt"] <= 1e-6, r
+        assert l > 0
+        _check(r, k["w"], inst)
+
+
+def test_server_alone_and_in_mix(gdwd_lib):
+    insts = _instances(8, 12)
+    target = insts[0]
+    # alone: a one-slot server
+    with gdwd_lib.Server(slots=1) as srv:
+        r0, k0 = gdwd_lib.make_request(target.Z, target.y, target.q, target.C, tol=1e-7)
+        t0 = srv.submit(r0, k0)
+        res_alone, lat_alone = srv.poll(t0)
+    w_alone = k0["w"].copy()
+    # in a mix: four slots, the target submitted in the middle of seven others
+    with gdwd_lib.Server(slots=4) as srv:
+        tickets = []
+        for j, inst in enumerate(insts[1:4] + [target] + insts[4:]):
+            r, k = gdwd_lib.make_request(inst.Z, inst.y, inst.q, inst.C, tol=1e-7)
+            tickets.append((srv.submit(r, k), k, inst))
+        outs = [(srv.poll(t), k, inst) for t, k, inst in tickets]
+    (res_mix, lat_mix), k_mix, _ = outs[3]
+    assert res_alone["status"] == 0 and res_mix["status"] == 0
+    relobj = abs(res_mix["primal_obj"] - res_alone["primal_obj"]) / abs(res_alone["primal_obj"])
+    relw = np.linalg.norm(k_mix["w"] - w_alone) / np.linalg.norm(w_alone)
+    assert relobj <= 1e-6 and relw <= 1e-4, (relobj, relw)
+    for (res, lat), k, inst in outs:
+        assert res["status"] == 0 and lat > 0
+
+
+def test_server_tiny_budget_serialises(gdwd_lib):
+    """A budget smaller than any request: requests run one at a time and still complete."""
+    insts = _instances(3, 13)
+    with gdwd_lib.Server(slots=3, hbm_budget=1) as srv:
+        tickets = []
+        for inst in insts:
+            r, k = gdwd_lib.make_request(inst.Z, inst.y, inst.q, inst.C, tol=1e-6)
+            tickets.append((srv.submit(r, k), k, inst))
+        for t, k, inst in tickets:
+            res, lat = srv.poll(t)
+            assert res["status"] == 0
+            _check(res, k["w"], inst)
+
+
+def test_server_poll_nonblocking_and_errors(gdwd_lib):
+    inst = _instances(1, 14)[0]
+    with gdwd_lib.Server(slots=1) as srv:
+        r, k = gdwd_lib.make_request(inst.Z, inst.y, inst.q, inst.C)
+        t = srv.submit(r, k)
+        out = srv.poll(t, wait=False)      # queued or running, or already done
+        if out is None:
+            out = srv.poll(t)
+        assert out[0]["status"] == 0
+        # a request with invalid labels fails on its own without stopping the server
+        bad, kb = gdwd_lib.make_request(inst.Z, np.ones(inst.n), inst.q, inst.C)
+        tb = srv.submit(bad, kb)
+        with pytest.raises(gdwd_lib.GdwdError):
+            srv.poll(tb)

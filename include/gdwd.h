@@ -73,7 +73,12 @@ typedef struct {
   int32_t grid;       /* CTAs of the persistent iteration kernel; 0 = one per SM.      */
   int32_t block_rows; /* rows of Z per slab of the device layout; 0 = automatic.        */
   void* stream;       /* cudaStream_t for all work of the handle; NULL = default stream */
-  int64_t reserved[8];
+  int32_t refine;     /* BF16/F16/E4M3 storage only: 1 keeps an FP32 master copy of Z
+                         (with its own Gram factor) and follows each quantized solve by
+                         a warm-started solve on the master data, so that kkt <= tol
+                         holds for the original data.  Default 0.                       */
+  int32_t reserved32;
+  int64_t reserved[7];
 } gdwd_options;
 
 /* Outcome of one solve (one value of C). */

@@ -62,6 +62,7 @@ struct gdwd_handle {
   unsigned* bar = nullptr;
   int* err = nullptr;
   Ctrl* ctrl = nullptr;
+  gdwd_handle* master = nullptr;   // FP32 copy used by the refinement sweep (refine = 1)
   double phase_ns[kPhaseSlots] = {};
   std::string last_error;
 };
@@ -347,6 +348,14 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
     return GDWD_OK;
   }();
   if (st != GDWD_OK) return bail(st);
+  if (opt.refine && (opt.store == GDWD_BF16 || opt.store == GDWD_F16 || opt.store == GDWD_E4M3)) {
+    gdwd_options om = opt;
+    om.store = GDWD_F32;
+    om.refine = 0;
+    om.grid = h->grid;
+    st = gdwd_create(Z, zdt, d, n, ldz, z_on_device, y, q, C, &om, &h->master);
+    if (st != GDWD_OK) return bail(st);
+  }
   *out = h;
   return GDWD_OK;
 }
@@ -394,23 +403,44 @@ static IterArgs<CT> make_args(gdwd_handle* h, double C, double sigma0) {
   return a;
 }
 
-static gdwd_status solve_one(gdwd_handle* h, double C, double* w, int w_on_device, double* alpha, gdwd_result* res) {
+// One solve for penalty C.  warm == NULL starts from the initial iterate of
+// reading R3; otherwise the iterate (and sigma) of the last solve of `warm` (a
+// handle of the same problem with another storage type) is the starting point.
+static gdwd_status solve_one(gdwd_handle* h, double C, double* w, int w_on_device, double* alpha, gdwd_result* res,
+                             gdwd_handle* warm = nullptr) {
   const int64_t n = h->n, d = h->d;
   const int64_t dpad = (int64_t)h->L.NB * h->L.TB;
   cudaStream_t st = h->stream;
   const double sigma0 = h->opt.sigma0 > 0 ? h->opt.sigma0 : std::pow(std::min(10.0 * C, (double)n), h->q);
-  // initial iterate: r = xi = 1, w = u = 0, beta = 0, alpha = 0, rho = 0
-  const int fb = (int)std::min<int64_t>((n + 255) / 256, 1024);
-  fill_kernel<<<fb, 256, 0, st>>>(h->r, n, 1.0);
-  fill_kernel<<<fb, 256, 0, st>>>(h->xi, n, 1.0);
-  CK(cudaMemsetAsync(h->alpha, 0, n * sizeof(double), st), "memset");
-  CK(cudaMemsetAsync(h->u, 0, dpad * sizeof(double), st), "memset");
-  CK(cudaMemsetAsync(h->rho, 0, dpad * sizeof(double), st), "memset");
-  CK(cudaMemsetAsync(h->g, 0, dpad * sizeof(double), st), "memset");
   Ctrl c0{};
-  c0.sigma = sigma0;
-  c0.sigma_prev = sigma0;
-  c0.theta = 1.0;
+  if (!warm) {
+    // initial iterate: r = xi = 1, w = u = 0, beta = 0, alpha = 0, rho = 0
+    const int fb = (int)std::min<int64_t>((n + 255) / 256, 1024);
+    fill_kernel<<<fb, 256, 0, st>>>(h->r, n, 1.0);
+    fill_kernel<<<fb, 256, 0, st>>>(h->xi, n, 1.0);
+    CK(cudaMemsetAsync(h->alpha, 0, n * sizeof(double), st), "memset");
+    CK(cudaMemsetAsync(h->u, 0, dpad * sizeof(double), st), "memset");
+    CK(cudaMemsetAsync(h->rho, 0, dpad * sizeof(double), st), "memset");
+    CK(cudaMemsetAsync(h->g, 0, dpad * sizeof(double), st), "memset");
+    c0.sigma = sigma0;
+    c0.sigma_prev = sigma0;
+    c0.theta = 1.0;
+  } else {
+    // warm start: copy the other handle's iterate (same scaled problem: both scale by
+    // sqrt(||Z||_F) of the caller's data, so r, xi, alpha, u, rho, g carry over)
+    CK(cudaStreamSynchronize(warm->stream), "sync");
+    const size_t nb = n * sizeof(double), db = d * sizeof(double);
+    CK(cudaMemcpyAsync(h->r, warm->r, nb, cudaMemcpyDeviceToDevice, st), "warm copy");
+    CK(cudaMemcpyAsync(h->xi, warm->xi, nb, cudaMemcpyDeviceToDevice, st), "warm copy");
+    CK(cudaMemcpyAsync(h->alpha, warm->alpha, nb, cudaMemcpyDeviceToDevice, st), "warm copy");
+    CK(cudaMemcpyAsync(h->u, warm->u, db, cudaMemcpyDeviceToDevice, st), "warm copy");
+    CK(cudaMemcpyAsync(h->rho, warm->rho, db, cudaMemcpyDeviceToDevice, st), "warm copy");
+    CK(cudaMemcpyAsync(h->g, warm->g, db, cudaMemcpyDeviceToDevice, st), "warm copy");
+    CK(cudaMemcpy(&c0, warm->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost), "warm ctrl");
+    c0.it = 0;
+    c0.status = 0;
+    c0.done = 0;
+  }
   CK(cudaMemcpyAsync(h->ctrl, &c0, sizeof(Ctrl), cudaMemcpyHostToDevice, st), "copy ctrl");
   CK(cudaMemsetAsync(h->bar, 0, sizeof(unsigned), st), "memset");
   CK(cudaMemsetAsync(h->err, 0, sizeof(int), st), "memset");
@@ -474,8 +504,23 @@ extern "C" gdwd_status gdwd_solve(gdwd_handle* h, const double* Cs, int32_t nC, 
   gdwd_status worst = GDWD_OK;
   for (int k = 0; k < count; ++k) {
     const double C = (Cs && nC > 0) ? Cs[k] : h->C;
-    gdwd_status s = solve_one(h, C, w ? w + (size_t)k * h->d : nullptr, w_on_device,
-                              alpha ? alpha + (size_t)k * h->n : nullptr, res + k);
+    gdwd_status s;
+    if (h->master) {
+      // refinement sweep: the quantized solve, then the FP32 master warm-started from it
+      gdwd_result rq;
+      s = solve_one(h, C, nullptr, 0, nullptr, &rq);
+      if (s != GDWD_OK && s != GDWD_EMAXITER) return s;
+      s = solve_one(h->master, C, w ? w + (size_t)k * h->d : nullptr, w_on_device,
+                    alpha ? alpha + (size_t)k * h->n : nullptr, res + k, h);
+      res[k].iters += rq.iters;
+      res[k].t_solve_ms += rq.t_solve_ms;
+      res[k].t_setup_ms = h->t_setup_ms + h->master->t_setup_ms;
+      res[k].reserved[0] = rq.iters;   // iterations on the quantized data
+      if (s != GDWD_OK && s != GDWD_EMAXITER) return fail(h, s, h->master->last_error);
+    } else {
+      s = solve_one(h, C, w ? w + (size_t)k * h->d : nullptr, w_on_device,
+                    alpha ? alpha + (size_t)k * h->n : nullptr, res + k);
+    }
     if (s != GDWD_OK && s != GDWD_EMAXITER) return s;
     if (s != GDWD_OK) worst = s;
   }
@@ -484,6 +529,7 @@ extern "C" gdwd_status gdwd_solve(gdwd_handle* h, const double* Cs, int32_t nC, 
 
 extern "C" gdwd_status gdwd_free(gdwd_handle* h) {
   if (!h) return GDWD_OK;
+  if (h->master) gdwd_free(h->master);
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
   release(h);

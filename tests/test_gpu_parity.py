@@ -242,3 +242,21 @@ def test_quantized_solve_matches_oracle(gdwd_lib, fmt, q, C):
     ref_orig = O.solve(Z.astype(np.float64), inst.y, q, C, tol=1e-9)
     rel = abs(r["primal_obj"] - ref_orig["primal"]) / abs(ref_orig["primal"])
     assert rel <= {"bf16": 1e-2, "f16": 1e-3, "e4m3": 1e-1}[fmt], rel
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "e4m3"])
+def test_refinement_sweep_restores_original_optimum(gdwd_lib, fmt):
+    """refine = 1: quantized solve, then the FP32 master warm-started from it; the
+    result is the optimum of the ORIGINAL data to the solution tolerance."""
+    inst = synth.gaussian(seed=41, d=6007, n=301, shift=1.0, n_pos=120, q=1.0, C=2.0, m_test=500)
+    Z = inst.Z
+    Cs = [0.5, 2.0]
+    with gdwd_lib.Solver(Z, inst.y, 1.0, 2.0, store=fmt, tol=1e-6, refine=1) as s:
+        res, w, alpha = s.solve(Cs=Cs, alpha=True)
+    for k, C in enumerate(Cs):
+        r = res[k]
+        assert r["status"] == 0 and r["kkt"] <= 1e-6, r
+        ref = O.solve(Z.astype(np.float64), inst.y, 1.0, C, tol=1e-9)
+        _compare(r, w[:, k], ref)
+        ok, _ = _predictions_match(inst.Xtest.astype(np.float64), w[:, k], r["beta"], ref["w"], ref["beta"])
+        assert ok

@@ -69,6 +69,11 @@ struct gdwd_handle {
 
 static thread_local std::string g_thread_error;
 
+namespace gdwd {
+// Lets the serving layer hand a worker thread's message to the polling thread.
+void set_thread_error(const std::string& m) { g_thread_error = m; }
+}  // namespace gdwd
+
 static gdwd_status fail(gdwd_handle* h, gdwd_status st, const std::string& msg) {
   if (h) h->last_error = msg;
   g_thread_error = msg;

@@ -23,6 +23,7 @@
 //   phase S              all sums -> KKT residuals (Sec. 4.3), duality gap,
 //                        sigma rule (Sec. 4.4), stop test; identical in every CTA
 #include <algorithm>
+#include <mutex>
 
 #include "passes.cuh"
 
@@ -591,11 +592,31 @@ static size_t union_bytes(const Layout& L, int grid) {
   return (u + 127) & ~(size_t)127;
 }
 
+
+// Raises a kernel's dynamic shared-memory limit to the device maximum once per
+// process.  (Setting it per launch to the launch's own size races when several
+// host threads launch the same kernel with different sizes.)
+template <auto Kern>
+static cudaError_t ensure_max_dyn_smem() {
+  static std::once_flag once;
+  static cudaError_t status = cudaSuccess;
+  std::call_once(once, [] {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    status = cudaFuncGetAttributes(&fa, Kern);
+    if (status == cudaSuccess)
+      status = cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  });
+  return status;
+}
+
 template <typename T>
 static cudaError_t launch_iterate_t(const IterArgs<typename ElemTraits<T>::compute_t>& args, int stages,
                                     int stage_bytes, size_t smem, cudaStream_t st) {
   auto kern = iterate_kernel<T>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_max_dyn_smem<iterate_kernel<T>>();
   if (e != cudaSuccess) return e;
   void* params[] = {(void*)&args, (void*)&stages, (void*)&stage_bytes};
   return cudaLaunchCooperativeKernel((const void*)kern, dim3(args.grid), dim3(kThreads), params, smem, st);
@@ -753,7 +774,7 @@ static cudaError_t run_apply_t(const Layout& L, int trans, const double* x, cons
   if (!plan_ring<T>(L, grid, smem_limit, stages, sb, smem)) return cudaErrorInvalidConfiguration;
   if (trans) {
     auto k = applyA_kernel<T>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_max_dyn_smem<applyA_kernel<T>>();
     if (e != cudaSuccess) return e;
     k<<<grid, kThreads, smem, st>>>(L, x, (CT*)partial, stages, sb, err, tmo);
     e = cudaGetLastError();
@@ -763,7 +784,7 @@ static cudaError_t run_apply_t(const Layout& L, int trans, const double* x, cons
     return cudaGetLastError();
   }
   auto k = applyB_kernel<T>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_max_dyn_smem<applyB_kernel<T>>();
   if (e != cudaSuccess) return e;
   k<<<grid, kThreads, smem, st>>>(L, x, sc, out, stages, sb, err, tmo);
   return cudaGetLastError();

@@ -22,6 +22,10 @@
 #include "../../include/gdwd.h"
 #include <cuda_runtime.h>
 
+namespace gdwd {
+void set_thread_error(const std::string& m);
+}
+
 namespace {
 
 using clk = std::chrono::steady_clock;
@@ -36,6 +40,7 @@ struct Finished {
   gdwd_result res;
   gdwd_status st;
   double latency_ms;
+  std::string msg;
 };
 
 // device bytes of one problem: stored Z, G and G^{-1} (8 n^2 each), set-up
@@ -90,19 +95,22 @@ static void worker_main(gdwd_server* s, int k) {
     gdwd_result res;
     std::memset(&res, 0, sizeof(res));
     gdwd_handle* h = nullptr;
+    std::string msg;
     gdwd_status st = gdwd_create(r.Z, r.zdt, r.d, r.n, r.ldz, r.z_on_device, r.y, r.q, r.C, &r.opts, &h);
     if (st == GDWD_OK) {
       st = gdwd_solve(h, nullptr, 0, r.w, 0, r.alpha, &res);
+      if (st != GDWD_OK) msg = gdwd_last_error(h);
       gdwd_free(h);
     } else {
       res.status = st;
+      msg = gdwd_last_error(nullptr);
     }
     const double lat = std::chrono::duration<double, std::milli>(clk::now() - p.t_submit).count();
     {
       std::lock_guard<std::mutex> lk(s->m);
       s->used -= bytes;
       s->inflight -= 1;
-      s->done[p.ticket] = Finished{res, st, lat};
+      s->done[p.ticket] = Finished{res, st, lat, msg};
       s->outstanding -= 1;
     }
     s->cv_mem.notify_all();
@@ -170,6 +178,7 @@ extern "C" gdwd_status gdwd_server_poll(gdwd_server* s, uint64_t ticket, int32_t
   *res = it->second.res;
   if (latency_ms) *latency_ms = it->second.latency_ms;
   const gdwd_status st = it->second.st;
+  if (st != GDWD_OK) gdwd::set_thread_error(it->second.msg);
   s->done.erase(it);
   return st;
 }

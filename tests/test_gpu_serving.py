@@ -25,6 +25,8 @@ def _instances(count, seed):
 
 
 def _check(res, w, inst, obj_tol=1e-6, w_tol=1e-4):
+    # w is pinned by kkt only up to the conditioning of the problem (for q = 4 the
+    # objective is flat in w): the tests solve to kkt <= 1e-7 before comparing w
     ref = O.solve(inst.Z.astype(np.float64), inst.y, inst.q, inst.C, tol=1e-9, max_iter=100000)
     relobj = abs(res["primal_obj"] - ref["primal"]) / abs(ref["primal"])
     relw = np.linalg.norm(w - ref["w"]) / np.linalg.norm(ref["w"])
@@ -35,13 +37,13 @@ def test_solve_batch_uneven(gdwd_lib):
     insts = _instances(6, 11)
     reqs, keeps = [], []
     for inst in insts:
-        r, k = gdwd_lib.make_request(inst.Z, inst.y, inst.q, inst.C, store="f32", tol=1e-6)
+        r, k = gdwd_lib.make_request(inst.Z, inst.y, inst.q, inst.C, store="f32", tol=1e-7)
         reqs.append(r)
         keeps.append(k)
     res, lat, st = gdwd_lib.solve_batch(reqs, slots=3)
-    assert st == 0
+    assert st == 0, (st, [r["status"] for r in res], gdwd_lib.load().gdwd_last_error(None))
     for r, k, inst, l in zip(res, keeps, insts, lat):
-        assert r["status"] == 0 and r["kkt"] <= 1e-6, r
+        assert r["status"] == 0 and r["kkt"] <= 1e-7, r
         assert l > 0
         _check(r, k["w"], inst)
 
@@ -77,7 +79,7 @@ def test_server_tiny_budget_serialises(gdwd_lib):
     with gdwd_lib.Server(slots=3, hbm_budget=1) as srv:
         tickets = []
         for inst in insts:
-            r, k = gdwd_lib.make_request(inst.Z, inst.y, inst.q, inst.C, tol=1e-6)
+            r, k = gdwd_lib.make_request(inst.Z, inst.y, inst.q, inst.C, tol=1e-7)
             tickets.append((srv.submit(r, k), k, inst))
         for t, k, inst in tickets:
             res, lat = srv.poll(t)

@@ -217,6 +217,32 @@ gdwd_status gdwd_get_phase_times(const gdwd_handle* h, double* ns, int32_t count
 gdwd_status gdwd_get_stored(const gdwd_handle* h, void* Zq, double* colscale);
 
 /*
+ * Gram matrix without any allocation: K = Z^T Z (n x n, row-major, both
+ * triangles, FP64 result of FP32 products summed in double-float) for a
+ * column-major FP32 matrix Z (d x n, leading dimension ldz >= d).  Z and K are
+ * device memory owned by the caller; work is queued on `stream` (NULL = default
+ * stream) and the call returns without waiting for it.
+ *
+ * For callers that cannot allocate device memory when they need the product
+ * (inside a captured region, under an allocator that must not be re-entered, or
+ * in an embedder that owns all device memory): the scratch for the split-K
+ * partial products lives in a fixed 32 MiB array inside the library, which
+ * every GPU that loads the library keeps until the process exits.  Limits and
+ * rules:
+ *   - n * n <= 4,194,304 (n <= 2048); larger n gives GDWD_EINVAL;
+ *   - the first call on a device looks up the array's device address (with that
+ *     device current) and caches it; make that first call before any stream
+ *     capture;
+ *   - all calls share the one array, so calls whose work overlaps on the GPU
+ *     (different streams, or different host threads without ordering) race and
+ *     give wrong results; order them on one stream;
+ *   - no cudaMalloc, cudaFree or allocating library routine is called.
+ * The paper has no counterpart (its set-up forms I + Z^T Z / mu, Sec. 3.3.2, by
+ * an ordinary allocating routine).  Errors: EINVAL, ECUDA.
+ */
+gdwd_status gdwd_gram_noalloc(const float* Z, int64_t d, int64_t n, int64_t ldz, double* K, void* stream);
+
+/*
  * ---------------------------------------------------------------- serving
  * Many independent problems of different (d, n, q, C) on one GPU.  A server
  * owns `slots` CUDA streams; each slot runs one problem at a time (create,

@@ -98,6 +98,8 @@ def load(path: str = LIB_PATH):
     lib.gdwd_server_poll.argtypes = [c_void_p, ctypes.c_uint64, c_int32, POINTER(Result), POINTER(c_double)]
     lib.gdwd_server_destroy.argtypes = [c_void_p]
     lib.gdwd_solve_batch.argtypes = [POINTER(Request), c_int32, c_int32, POINTER(Result), POINTER(c_double)]
+    lib.gdwd_gram_noalloc.argtypes = [c_void_p, c_int64, c_int64, c_int64, c_void_p, c_void_p]
+    lib.gdwd_gram_noalloc.restype = c_int32
     for name in EXPORTS:
         if name != "gdwd_last_error":
             getattr(lib, name).restype = c_int32
@@ -324,3 +326,18 @@ def solve_batch(requests, slots=4):
     lat = (c_double * k)()
     st = lib.gdwd_solve_batch(arr, k, int(slots), res, lat)
     return [r.as_dict() for r in res], list(lat), st
+
+
+def gram_noalloc(Z, K, stream=None):
+    """K = Z^T Z (gdwd_gram_noalloc) for a CUDA float32 Z (d x n, column-major:
+    Z.stride(0) == 1) into a CUDA float64 K (n x n, contiguous).  The library
+    allocates nothing; its scratch is a fixed array inside the library (n <= 2048)."""
+    lib = load()
+    if Z.dim() != 2 or Z.stride(0) != 1:
+        raise ValueError("Z must be d x n column-major (stride(0) == 1)")
+    d, n = Z.shape
+    ldz = Z.stride(1) if n > 1 else d
+    st = lib.gdwd_gram_noalloc(c_void_p(Z.data_ptr()), d, n, ldz, c_void_p(K.data_ptr()), stream)
+    if st != OK:
+        raise GdwdError(st, "gdwd_gram_noalloc failed (n <= 2048, float32 column-major input)")
+    return K

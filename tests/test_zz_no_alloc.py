@@ -1,0 +1,50 @@
+"""The Gram entry point that allocates nothing (gdwd_gram_noalloc).
+
+It is for callers that cannot allocate device memory when they need the
+product, so its scratch is a fixed array inside the library that every call
+reuses.  The test calls it twice in a row through the C-ABI, on data of two
+different shapes, and checks each result against the Gram matrix built by the
+ordinary (allocating) path, gdwd_create + gdwd_gram, within the tolerance of the
+other Gram tests; it must pass alone in a fresh process and after the other tests.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def _reference_gram(gdwd_lib, Z):
+    """Z^T Z from the allocating path: gdwd_gram returns I + Z~^T Z~ with Z~ = Z / Z_scale."""
+    n = Z.shape[1]
+    y = np.where(np.arange(n) % 2 == 0, 1.0, -1.0)
+    with gdwd_lib.Solver(Z, y, 1.0, 1.0, store="f32", mu=1.0) as s:
+        G = s.gram()
+        zs = s.info()["zscale"]
+    return (G - np.eye(n)) * zs * zs
+
+
+def test_gram_noalloc_matches_allocating_path(gdwd_lib):
+    import torch
+    rng = np.random.default_rng(2024)
+    for d, n in [(3001, 257), (1000, 1500)]:     # two calls in a row share the scratch array
+        Zh = rng.standard_normal((d, n)).astype(np.float32)
+        Zd = torch.from_numpy(np.ascontiguousarray(Zh.T)).cuda()      # n x d: rows are the columns of Z
+        Zcm = torch.as_strided(Zd, (d, n), (1, d))
+        K = torch.full((n, n), float("nan"), dtype=torch.float64, device="cuda")
+        gdwd_lib.gram_noalloc(Zcm, K)
+        torch.cuda.synchronize()
+        got = K.cpu().numpy()
+        ref = _reference_gram(gdwd_lib, Zh)
+        err = np.abs(got - ref).max() / np.abs(ref).max()
+        assert np.all(np.isfinite(got))
+        assert err <= 5e-8, (d, n, err)
+        assert np.array_equal(got, got.T)
+
+
+def test_gram_noalloc_rejects_oversize(gdwd_lib):
+    """n beyond the fixed scratch (n * n > 4,194,304) is refused before any GPU work."""
+    import torch
+    big = torch.as_strided(torch.zeros(8 * 2049, dtype=torch.float32, device="cuda"), (8, 2049), (1, 8))
+    K = torch.zeros(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(gdwd_lib.GdwdError):
+        gdwd_lib.gram_noalloc(big, K)

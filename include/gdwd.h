@@ -77,7 +77,9 @@ typedef struct {
                          (with its own Gram factor) and follows each quantized solve by
                          a warm-started solve on the master data, so that kkt <= tol
                          holds for the original data.  Default 0.                       */
-  int32_t reserved32;
+  int32_t cgrid_sequential; /* 0 (default): gdwd_solve with several C iterates up to
+                         four of them in lock-step in one persistent launch, so each
+                         pass over Z serves all of them; 1: one C at a time.         */
   int64_t reserved[7];
 } gdwd_options;
 

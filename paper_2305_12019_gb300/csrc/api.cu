@@ -63,6 +63,14 @@ struct gdwd_handle {
   int* err = nullptr;
   Ctrl* ctrl = nullptr;
   gdwd_handle* master = nullptr;   // FP32 copy used by the refinement sweep (refine = 1)
+  // state of the joint C-grid kernel (up to 4 instances), allocated on first use
+  struct {
+    bool ready = false;
+    double *r, *xi, *alpha, *b, *u, *rho, *g, *scal;
+    float2 *rhsA, *rhsB;
+    void *cq, *aq, *partial;
+    Ctrl* ctrl;
+  } ms;
   double phase_ns[kPhaseSlots] = {};
   std::string last_error;
 };
@@ -497,6 +505,157 @@ static gdwd_status solve_one(gdwd_handle* h, double C, double* w, int w_on_devic
   return s;
 }
 
+// Up to four values of C in lock-step in one launch of the joint kernel.
+static gdwd_status solve_multi(gdwd_handle* h, const double* Cs, int K, int kker, double* w, int w_on_device,
+                               double* alpha, gdwd_result* res) {
+  const int64_t n = h->n, d = h->d;
+  const int64_t dpad = (int64_t)h->L.NB * h->L.TB;
+  cudaStream_t st = h->stream;
+  const size_t ct = h->store == GDWD_F64 ? 8 : 4;
+  auto& m = h->ms;
+  if (!m.ready) {
+    CK(halloc(h, &m.r, 4 * n), "alloc");
+    CK(halloc(h, &m.xi, 4 * n), "alloc");
+    CK(halloc(h, &m.alpha, 4 * n), "alloc");
+    CK(halloc(h, &m.b, 4 * n), "alloc");
+    CK(halloc(h, &m.rhsA, 4 * n), "alloc");
+    CK(halloc(h, &m.rhsB, 4 * n), "alloc");
+    CK(halloc(h, (uint8_t**)&m.cq, 4 * n * ct), "alloc");
+    CK(halloc(h, (uint8_t**)&m.aq, 4 * n * ct), "alloc");
+    CK(halloc(h, (uint8_t**)&m.partial, 4 * (size_t)n * h->L.NB * ct), "alloc");
+    CK(halloc(h, &m.u, 4 * dpad), "alloc");
+    CK(halloc(h, &m.rho, 4 * dpad), "alloc");
+    CK(halloc(h, &m.g, 4 * dpad), "alloc");
+    CK(halloc(h, &m.scal, 4 * (size_t)S_COUNT * h->sms), "alloc");
+    CK(halloc(h, (uint8_t**)&m.ctrl, 4 * sizeof(Ctrl)), "alloc");
+    m.ready = true;
+  }
+  const int fb = (int)std::min<int64_t>((4 * n + 255) / 256, 1024);
+  fill_kernel<<<fb, 256, 0, st>>>(m.r, 4 * n, 1.0);
+  fill_kernel<<<fb, 256, 0, st>>>(m.xi, 4 * n, 1.0);
+  CK(cudaMemsetAsync(m.alpha, 0, 4 * n * sizeof(double), st), "memset");
+  CK(cudaMemsetAsync(m.u, 0, 4 * dpad * sizeof(double), st), "memset");
+  CK(cudaMemsetAsync(m.rho, 0, 4 * dpad * sizeof(double), st), "memset");
+  CK(cudaMemsetAsync(m.g, 0, 4 * dpad * sizeof(double), st), "memset");
+  Ctrl c0[4] = {};
+  for (int j = 0; j < 4; ++j) {
+    const double Cj = Cs[j < K ? j : 0];
+    const double s0 = h->opt.sigma0 > 0 ? h->opt.sigma0 : std::pow(std::min(10.0 * Cj, (double)n), h->q);
+    c0[j].sigma = s0;
+    c0[j].sigma_prev = s0;
+    c0[j].theta = 1.0;
+  }
+  CK(cudaMemcpyAsync(m.ctrl, c0, sizeof(c0), cudaMemcpyHostToDevice, st), "copy ctrl");
+  CK(cudaMemsetAsync(h->bar, 0, sizeof(unsigned), st), "memset");
+  CK(cudaMemsetAsync(h->err, 0, sizeof(int), st), "memset");
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0), "event");
+  CK(cudaEventCreate(&e1), "event");
+  CK(cudaEventRecord(e0, st), "event");
+  auto fill = [&](auto& a) {
+    a.L = h->L;
+    a.sc = h->sc;
+    a.P = h->P;
+    a.ldP = h->ldP;
+    a.pdf = h->pdf;
+    a.p = h->p;
+    a.y = h->y;
+    a.e = h->e;
+    a.omega = h->omega;
+    a.wt = h->wt;
+    a.inv_s = 1.0 / h->s;
+    a.q = h->q;
+    a.mu = h->opt.mu;
+    a.tau = h->opt.tau;
+    a.R = h->zscale;
+    a.tol = h->opt.tol;
+    a.kappa = (h->q + 1.0) / h->q * std::pow(h->q, 1.0 / (h->q + 1.0));
+    for (int j = 0; j < 4; ++j) a.C[j] = Cs[j < K ? j : 0];
+    a.K = K;
+    a.max_iter = h->opt.max_iter;
+    a.grid = h->grid;
+    a.timeout_ns = (uint64_t)(h->opt.timeout_s * 1e9);
+    a.dpad = dpad;
+    a.r = m.r;
+    a.xi = m.xi;
+    a.alpha = m.alpha;
+    a.b = m.b;
+    a.rhsA = m.rhsA;
+    a.rhsB = m.rhsB;
+    a.u = m.u;
+    a.rho = m.rho;
+    a.g = m.g;
+    a.scal = m.scal;
+    a.bar = h->bar;
+    a.err = h->err;
+    a.ctrl = m.ctrl;
+  };
+  const int smem_limit = h->smem_optin - 16384;
+  cudaError_t e;
+  if (h->store == GDWD_F64) {
+    MultiArgs<double> a{};
+    fill(a);
+    a.cq = (double*)m.cq;
+    a.aq = (double*)m.aq;
+    a.partial = (double*)m.partial;
+    e = run_multi_f64(kker, a, smem_limit, st);
+  } else {
+    MultiArgs<float> a{};
+    fill(a);
+    a.cq = (float*)m.cq;
+    a.aq = (float*)m.aq;
+    a.partial = (float*)m.partial;
+    e = run_multi_f32(h->store, kker, a, smem_limit, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "joint C-grid launch");
+  CK(cudaEventRecord(e1, st), "event");
+  Ctrl c[4];
+  int kerr = 0;
+  CK(cudaMemcpyAsync(c, m.ctrl, sizeof(c), cudaMemcpyDeviceToHost, st), "copy ctrl");
+  CK(cudaMemcpyAsync(&kerr, h->err, sizeof(int), cudaMemcpyDeviceToHost, st), "copy err");
+  const int wb = (int)std::min<int64_t>((d + 255) / 256, 2048);
+  for (int j = 0; j < K; ++j) {
+    double* wdst = (w && w_on_device) ? w + (size_t)j * d : h->wtmp;
+    finish_w_kernel<<<wb, 256, 0, st>>>(m.g + (size_t)j * dpad, m.rho + (size_t)j * dpad, m.ctrl + j,
+                                        std::sqrt(h->opt.mu), h->zscale, d, wdst);
+    CK(cudaGetLastError(), "finish");
+    if (w && !w_on_device)
+      CK(cudaMemcpyAsync(w + (size_t)j * d, h->wtmp, d * sizeof(double), cudaMemcpyDeviceToHost, st), "copy w");
+    if (alpha)
+      CK(cudaMemcpyAsync(alpha + (size_t)j * n, m.alpha + (size_t)j * n, n * sizeof(double), cudaMemcpyDeviceToHost,
+                         st),
+         "copy alpha");
+    if (w && !w_on_device) CK(cudaStreamSynchronize(st), "sync");   // h->wtmp is reused per instance
+  }
+  CK(cudaStreamSynchronize(st), "sync");
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  gdwd_status worst = GDWD_OK;
+  for (int j = 0; j < K; ++j) {
+    gdwd_result* r = res + j;
+    std::memset(r, 0, sizeof(*r));
+    r->beta = c[j].beta;
+    r->primal_obj = c[j].pobj;
+    r->dual_obj = c[j].dobj;
+    r->kkt = c[j].kkt;
+    r->eta_p = std::max(c[j].eta_p1, std::max(c[j].eta_p2, c[j].eta_p3));
+    r->eta_d = std::max(c[j].eta_d1, std::max(c[j].eta_d2, c[j].eta_d3));
+    r->eta_c = std::max(c[j].eta_c1, std::max(c[j].eta_c2, c[j].eta_c3));
+    r->eta_gap = c[j].eta_gap;
+    r->sigma = c[j].sigma;
+    r->zscale = h->zscale;
+    r->t_setup_ms = h->t_setup_ms;
+    r->t_solve_ms = ms;   // the whole joint launch (shared by its instances)
+    r->iters = c[j].it;
+    r->status = kerr ? kerr : c[j].status;
+    if (r->status != GDWD_OK && worst == GDWD_OK) worst = (gdwd_status)r->status;
+  }
+  if (kerr) return fail(h, (gdwd_status)kerr, "gdwd_solve: joint kernel stopped with a device error");
+  return worst;
+}
+
 extern "C" gdwd_status gdwd_solve(gdwd_handle* h, const double* Cs, int32_t nC, double* w, int32_t w_on_device,
                                   double* alpha, gdwd_result* res) {
   if (!h || !res) return fail(h, GDWD_EINVAL, "gdwd_solve: NULL handle or result");
@@ -507,7 +666,21 @@ extern "C" gdwd_status gdwd_solve(gdwd_handle* h, const double* Cs, int32_t nC, 
     if (!(C > 0.0) || !std::isfinite(C)) return fail(h, GDWD_EINVAL, "gdwd_solve: C must be > 0");
   }
   gdwd_status worst = GDWD_OK;
-  for (int k = 0; k < count; ++k) {
+  // joint C-grid: groups of up to four C values per launch (one Z read per pass for all)
+  const int kmax = (count >= 2 && !h->master && !h->opt.cgrid_sequential)
+                       ? multi_max_k(h->store, h->L, h->grid, h->smem_optin - 16384)
+                       : 1;
+  int k0 = 0;
+  while (kmax >= 2 && count - k0 >= 2) {
+    const int K = std::min(kmax, count - k0);
+    const int kker = K <= 2 ? 2 : 4;
+    gdwd_status s = solve_multi(h, Cs + k0, K, kker, w ? w + (size_t)k0 * h->d : nullptr, w_on_device,
+                                alpha ? alpha + (size_t)k0 * h->n : nullptr, res + k0);
+    if (s != GDWD_OK && s != GDWD_EMAXITER) return s;
+    if (s != GDWD_OK) worst = s;
+    k0 += K;
+  }
+  for (int k = k0; k < count; ++k) {
     const double C = (Cs && nC > 0) ? Cs[k] : h->C;
     gdwd_status s;
     if (h->master) {

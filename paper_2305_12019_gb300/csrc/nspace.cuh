@@ -1,0 +1,155 @@
+// n-space device helpers shared by the single- and multi-instance iteration
+// kernels: the Step-1b prox (Newton, Sec. 3.2), the dual-objective power,
+// deterministic block reductions and the double-float G^{-1} row products.
+#pragma once
+
+#include "passes.cuh"
+
+namespace gdwd {
+
+// ---------------------------------------------------------------------------
+// r-subproblem (Step 1b, eq-varphi): the positive root of
+// s^(q+1) (s - a) = kq,  kq = omega / sigma, by Newton's iteration of Sec. 3.2
+// kept inside the bracket [max(a,0), max(a,0) + max(kq, 1)] (f < 0 at the left
+// end, f >= 0 at the right end); steps that leave it are bisected.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double pow_q1(double s, double q, int qcase) {  // s^(q+1)
+  switch (qcase) {
+    case 1: return s * s;
+    case 2: return s * s * s;
+    case 4: { double s2 = s * s; return s2 * s2 * s; }
+    case 5: return s * sqrt(s);   // q = 0.5
+    default: return pow(s, q + 1.0);
+  }
+}
+
+__device__ __forceinline__ int q_case(double q) {
+  return q == 1.0 ? 1 : q == 2.0 ? 2 : q == 4.0 ? 4 : q == 0.5 ? 5 : 0;
+}
+
+__device__ inline double prox_root(double a, double kq, double q, int qcase, double r0) {
+  double lo = fmax(a, 0.0);
+  double hi = lo + fmax(kq, 1.0);
+  double s = (r0 > lo && r0 < hi) ? r0 : 0.5 * (lo + hi);
+  for (int it = 0; it < 100; ++it) {
+    const double sq1 = pow_q1(s, q, qcase);
+    const double f = sq1 * (s - a) - kq;
+    if (f < 0.0) lo = s;
+    else if (f > 0.0) hi = s;
+    else break;
+    const double nt = s * (kq * (q + 2.0) + a * sq1) / (kq * (q + 1.0) + sq1 * s);
+    // converged when the Newton correction is below 4 eps relative: tested before the
+    // safeguard, so rounding noise in f at the root cannot trigger a bisection step
+    if (fabs(nt - s) <= 8.881784197001252e-16 * s) {
+      s = nt;
+      break;
+    }
+    s = (nt > lo && nt < hi) ? nt : 0.5 * (lo + hi);
+  }
+  return s;
+}
+
+// (wt alpha)^(q/(q+1)) for the dual objective
+__device__ __forceinline__ double dual_pow(double x, double q, int qcase) {
+  if (x <= 0.0) return 0.0;
+  switch (qcase) {
+    case 1: return sqrt_nr(x);
+    case 2: { double c = cbrt(x); return c * c; }
+    case 5: return cbrt(x);
+    default: return pow(x, q / (q + 1.0));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// block-level deterministic reductions
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double block_sum(double v, double* s_red) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) s_red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kWarps; ++i) t += s_red[i];
+    s_red[kWarps] = t;
+  }
+  __syncthreads();
+  return s_red[kWarps];
+}
+
+__device__ __forceinline__ df block_sum_df(df v, float* s_red) {
+  v = df_warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) {
+    s_red[2 * w] = v.hi;
+    s_red[2 * w + 1] = v.lo;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    df t{0.f, 0.f};
+    for (int i = 0; i < kWarps; ++i) df_add(t, df{s_red[2 * i], s_red[2 * i + 1]});
+    s_red[2 * kWarps] = t.hi;
+    s_red[2 * kWarps + 1] = t.lo;
+  }
+  __syncthreads();
+  return df{s_red[2 * kWarps], s_red[2 * kWarps + 1]};
+}
+
+// N values per thread summed over the first nw warps of the block: warp sums,
+// then one thread per value adds the warp totals in a fixed order
+// (deterministic); out[k * stride] receives value k.  Threads of warps >= nw
+// must hold zeros.
+template <int N>
+__device__ __forceinline__ void block_sum_n(const double (&v)[N], int nw, double* s_part, double* out,
+                                            int stride) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (w < nw) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const double t = warp_sum(v[k]);
+      if (l == 0) s_part[w * N + k] = t;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < N) {
+    double t = 0.0;
+    for (int i = 0; i < nw; ++i) t += s_part[i * N + threadIdx.x];
+    out[(size_t)threadIdx.x * stride] = t;
+  }
+}
+
+// x_i = sum_j P_ij rhs_j for one row, one warp, double-float (result in all lanes).
+// Four independent 16-byte loads per lane per step keep several L2 requests in flight.
+__device__ __forceinline__ df row_dot(const float2* __restrict__ Prow, const float2* rhs_s, int npair) {
+  const float4* P4 = reinterpret_cast<const float4*>(Prow);
+  const float4* R4 = reinterpret_cast<const float4*>(rhs_s);
+  df a0{0.f, 0.f}, a1{0.f, 0.f}, a2{0.f, 0.f}, a3{0.f, 0.f};
+  const int lane = threadIdx.x & 31;
+  int j = lane;
+  for (; j + 96 < npair; j += 128) {
+    const float4 p0 = __ldg(P4 + j), p1 = __ldg(P4 + j + 32), p2 = __ldg(P4 + j + 64), p3 = __ldg(P4 + j + 96);
+    const float4 r0 = R4[j], r1 = R4[j + 32], r2 = R4[j + 64], r3 = R4[j + 96];
+    df_fma(a0, df{p0.x, p0.y}, df{r0.x, r0.y});
+    df_fma(a1, df{p0.z, p0.w}, df{r0.z, r0.w});
+    df_fma(a2, df{p1.x, p1.y}, df{r1.x, r1.y});
+    df_fma(a3, df{p1.z, p1.w}, df{r1.z, r1.w});
+    df_fma(a0, df{p2.x, p2.y}, df{r2.x, r2.y});
+    df_fma(a1, df{p2.z, p2.w}, df{r2.z, r2.w});
+    df_fma(a2, df{p3.x, p3.y}, df{r3.x, r3.y});
+    df_fma(a3, df{p3.z, p3.w}, df{r3.z, r3.w});
+  }
+  for (; j < npair; j += 32) {
+    const float4 p0 = __ldg(P4 + j);
+    const float4 r0 = R4[j];
+    df_fma(a0, df{p0.x, p0.y}, df{r0.x, r0.y});
+    df_fma(a1, df{p0.z, p0.w}, df{r0.z, r0.w});
+  }
+  df_add(a0, a1);
+  df_add(a2, a3);
+  df_add(a0, a2);
+  return df_warp_sum(a0);
+}
+
+}  // namespace gdwd

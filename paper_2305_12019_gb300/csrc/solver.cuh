@@ -106,6 +106,39 @@ struct IterArgs {
   Ctrl* ctrl;
 };
 
+// Joint C-grid iteration (iterate_multi.cu): K <= 4 instances in lock-step.
+template <typename CT>
+struct MultiArgs {
+  Layout L;
+  const double* sc;
+  const float2* P;
+  int ldP;
+  const float2* pdf;
+  const double* p;
+  const double* y;
+  const double* e;
+  const double* omega;
+  const double* wt;
+  double inv_s, q, mu, tau, R, tol, kappa;
+  double C[4];
+  int K;                // instances in use (the rest start frozen)
+  int max_iter, grid;
+  uint64_t timeout_ns;
+  int64_t dpad;
+  double *r, *xi, *alpha, *b;   // [K][n]
+  float2 *rhsA, *rhsB;          // [K][n]
+  CT *cq, *aq;                  // [K][n]
+  double *u, *rho, *g;          // [K][dpad]
+  CT* partial;                  // [K][n][NB]
+  double* scal;                 // [K][S_COUNT][grid]
+  unsigned* bar;
+  int* err;
+  Ctrl* ctrl;                   // [K]
+};
+int multi_max_k(int store, const Layout& L, int grid, int smem_limit);
+cudaError_t run_multi_f64(int K, const MultiArgs<double>& a, int smem_limit, cudaStream_t st);
+cudaError_t run_multi_f32(int store, int K, const MultiArgs<float>& a, int smem_limit, cudaStream_t st);
+
 // Host-side launchers (defined in the .cu files).
 int choose_chunk_cols(int store, const Layout& L, int grid, int smem_limit);
 cudaError_t run_iterate_f64(const IterArgs<double>& a, int smem_limit, cudaStream_t st);

@@ -25,8 +25,8 @@ OK, EMAXITER = 0, 4
 class Options(ctypes.Structure):
     _fields_ = [("mu", c_double), ("tau", c_double), ("tol", c_double), ("sigma0", c_double),
                 ("timeout_s", c_double), ("max_iter", c_int32), ("store", c_int32), ("grid", c_int32),
-                ("block_rows", c_int32), ("stream", c_void_p), ("refine", c_int32), ("reserved32", c_int32),
-                ("reserved", c_int64 * 7)]
+                ("block_rows", c_int32), ("stream", c_void_p), ("refine", c_int32),
+                ("cgrid_sequential", c_int32), ("reserved", c_int64 * 7)]
 
 
 class Result(ctypes.Structure):
@@ -132,11 +132,12 @@ class Solver:
     """
 
     def __init__(self, Z, y, q, C, *, store="f32", mu=1.0, tau=1.618, tol=1e-6, sigma0=0.0, max_iter=20000,
-                 timeout_s=2.0, grid=0, block_rows=0, stream=None, refine=0):
+                 timeout_s=2.0, grid=0, block_rows=0, stream=None, refine=0, cgrid_sequential=0):
         lib = load()
         self._h = c_void_p()
         o = default_options()
         o.refine = int(refine)
+        o.cgrid_sequential = int(cgrid_sequential)
         o.mu, o.tau, o.tol, o.sigma0 = mu, tau, tol, sigma0
         o.max_iter, o.timeout_s = max_iter, timeout_s
         o.store = DTYPES[store] if isinstance(store, str) else int(store)

@@ -28,7 +28,9 @@ def test_joint_cgrid_matches_oracle(gdwd_lib, store, d, n, q, Cs):
     inst = synth.gaussian(seed=d + n, d=d, n=n, shift=1.0, n_pos=n // 3, q=q, C=1.0,
                           dtype=np.float64 if store == "f64" else np.float32)
     Z = inst.Z
-    tol = 1e-8 if store == "f64" else 1e-7
+    # FP32 products put a noise floor of ~1e-7 under the residuals of FP32 / BF16
+    # storage, so those solve to the workload tolerance 1e-6
+    tol = 1e-8 if store == "f64" else 1e-6
     with gdwd_lib.Solver(Z, inst.y, q, 1.0, store=store, tol=tol) as s:
         res, w, alpha = s.solve(Cs=Cs, alpha=True)
     for k, C in enumerate(Cs):
@@ -45,9 +47,9 @@ def test_joint_equals_sequential_bf16_six_c(gdwd_lib):
     the one-C-per-launch path on the same stored (quantized) problem."""
     inst = synth.gaussian(seed=77, d=5003, n=257, shift=1.0, n_pos=100, q=1.0, C=1.0)
     Cs = list(np.logspace(-1, 2, 6))
-    with gdwd_lib.Solver(inst.Z, inst.y, 1.0, 1.0, store="bf16", tol=1e-7) as s:
+    with gdwd_lib.Solver(inst.Z, inst.y, 1.0, 1.0, store="bf16", tol=1e-6) as s:
         rj, wj, _ = s.solve(Cs=Cs)
-    with gdwd_lib.Solver(inst.Z, inst.y, 1.0, 1.0, store="bf16", tol=1e-7, cgrid_sequential=1) as s:
+    with gdwd_lib.Solver(inst.Z, inst.y, 1.0, 1.0, store="bf16", tol=1e-6, cgrid_sequential=1) as s:
         rs, ws, _ = s.solve(Cs=Cs)
     for k in range(len(Cs)):
         assert rj[k]["status"] == 0 and rs[k]["status"] == 0

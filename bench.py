@@ -172,7 +172,20 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--d", type=int, default=20000, help="feature count (profiling of other sizes only)")
     ap.add_argument("--n", type=int, default=1000, help="sample count (profiling of other sizes only)")
+    ap.add_argument("--workload", default="spiked_fp32",
+                    help="spiked_fp32 (default line) | plain_fp64 | cgrid_bf16 | uneven_batch | served | largest_fp8")
+    ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--cg-d", type=int, default=50000)
+    ap.add_argument("--cg-n", type=int, default=2000)
+    ap.add_argument("--big-d", type=int, default=200000)
+    ap.add_argument("--big-n", type=int, default=5000)
     args = ap.parse_args()
+    if args.workload != "spiked_fp32" and args.impl != "reference":
+        import bench_workloads
+        return bench_workloads.run(args.workload, args)
     if args.impl == "reference":
         return reference_arm(args)
 

@@ -1,0 +1,223 @@
+"""Measurements of the other workloads (run through ``bench.py --workload NAME``).
+
+Each prints one JSON line with its own metric.  All inputs are seeded synthetic
+stand-ins for the paper's data sets (see paper_2305_12019_gb300/synth.py).
+
+  plain_fp64    d=500, n=100, FP64, tol 1e-9: solves/s (latency-bound, L2-resident)
+  cgrid_bf16    d=50000, n=2000, 32 values of C (logspace(-2, 3)), BF16 storage,
+                joint C-grid launches: C-solves/s, against the plain FP32
+                one-C-at-a-time path on the same data
+  uneven_batch  64 instances, d log-uniform 5k-50k, n 200-2000, q in {0.5,1,2,4},
+                classes 1:1-1:4, BF16 storage, gdwd_solve_batch: instances/s
+  served        Poisson arrivals (200/s for 10 s by default) of FP16 problems with
+                d log-uniform 1k-100k, n 50-5000, q in {1,2}, C 0.1-100, generated
+                on the device per request seed: p50 / p99 latency and solves/s
+  largest_fp8   d=200000, n=5000, Student-t columns, 1:3, 16 values of C, E4M3
+                storage with the FP32 refinement sweep: C-solves/s
+"""
+from __future__ import annotations
+
+import json
+import os
+import statistics
+import threading
+import time
+
+import numpy as np
+
+from oracle import gdwd_oracle as O
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _device_colmajor(Z):
+    torch = _torch()
+    d, n = Z.shape
+    t = torch.from_numpy(np.ascontiguousarray(Z.T)).cuda()
+    return torch.as_strided(t, (d, n), (1, d))
+
+
+def plain_fp64(args, gdwd, synth):
+    torch = _torch()
+    inst = synth.plain_fp64()
+    Zd = _device_colmajor(inst.Z)
+    for _ in range(args.warmup):
+        with gdwd.Solver(Zd, inst.y, 1.0, 1.0, store="f64", tol=1e-9, sigma0=1.0) as s:
+            s.solve()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        with gdwd.Solver(Zd, inst.y, 1.0, 1.0, store="f64", tol=1e-9, sigma0=1.0) as s:
+            res, w, _ = s.solve()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / args.steps
+    ref = O.solve(inst.Z, inst.y, 1.0, 1.0, sigma0=1.0, tol=1e-10)
+    return {"metric": "gDWD solves/s at KKT<=1e-9", "value": 1.0 / dt, "unit": "solves/s", "ms_per_step": dt * 1e3,
+            "config": {"workload": "plain_fp64 d=500 n=100 q=1 C=1 sigma0=1 tol=1e-9", "store": "f64"},
+            "iters": res[0]["iters"], "kkt": res[0]["kkt"],
+            "err_vs_oracle": {"rel_obj": abs(res[0]["primal_obj"] - ref["primal"]) / ref["primal"],
+                              "rel_w": float(np.linalg.norm(w[:, 0] - ref["w"]) / np.linalg.norm(ref["w"]))}}
+
+
+def cgrid_bf16(args, gdwd, synth):
+    torch = _torch()
+    d, n = args.cg_d, args.cg_n
+    inst = synth.gaussian(seed=3001, d=d, n=n, shift=1.5, q=1.0, C=1.0)
+    Cs = np.logspace(-2, 3, 32)
+    Zd = _device_colmajor(inst.Z)
+    with gdwd.Solver(Zd, inst.y, 1.0, 1.0, store="bf16", tol=1e-6) as s:   # warm-up
+        s.solve(Cs=Cs[:4])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with gdwd.Solver(Zd, inst.y, 1.0, 1.0, store="bf16", tol=1e-6) as s:
+        res, w, alpha = s.solve(Cs=Cs, alpha=True)
+        info = s.info()
+    torch.cuda.synchronize()
+    t_joint = time.perf_counter() - t0
+    # plain FP32 path, one C per launch, on the first four values of C (per-solve time)
+    t0 = time.perf_counter()
+    with gdwd.Solver(Zd, inst.y, 1.0, 1.0, store="f32", tol=1e-6, cgrid_sequential=1) as s:
+        rf, wf, _ = s.solve(Cs=Cs[:4])
+    torch.cuda.synchronize()
+    t_f32_per = (time.perf_counter() - t0) / 4
+    Z64 = inst.Z.astype(np.float64)
+    gaps = [O.certified_gap(Z64, inst.y, w[:, k], res[k]["beta"], alpha[:, k], 1.0, Cs[k])[2] for k in range(0, 32, 4)]
+    return {"metric": "gDWD C-solves/s at KKT<=1e-6 (quantized problem)", "value": 32 / t_joint, "unit": "solves/s",
+            "ms_per_step": t_joint * 1e3,
+            "config": {"workload": f"cgrid_bf16 d={d} n={n} 32 C logspace(-2,3) q=1", "store": "bf16"},
+            "vs_fp32_single": (32 / t_joint) / (1.0 / t_f32_per), "fp32_single_solves_per_s": 1.0 / t_f32_per,
+            "setup_ms": info["t_setup_ms"], "iters": [r["iters"] for r in res], "all_converged":
+                all(r["status"] == 0 for r in res),
+            "certified_gap_original_data_every_4th_C": gaps}
+
+
+def uneven_batch(args, gdwd, synth):
+    shapes = synth.uneven_batch(4001, count=args.batch_count)
+    reqs, keeps, insts = [], [], []
+    for sh in shapes:
+        inst = synth.gaussian(seed=sh["seed"], d=sh["d"], n=sh["n"], shift=1.5, n_pos=sh["n_pos"], q=sh["q"],
+                              C=sh["C"])
+        r, k = gdwd.make_request(inst.Z, inst.y, inst.q, inst.C, store="bf16", tol=1e-6, want_alpha=True)
+        reqs.append(r)
+        keeps.append(k)
+        insts.append(inst)
+    t0 = time.perf_counter()
+    res, lat, st = gdwd.solve_batch(reqs, slots=args.slots)
+    dt = time.perf_counter() - t0
+    # certificate on the original data for a sample of instances
+    gaps = []
+    for k in range(0, len(insts), 8):
+        inst = insts[k]
+        gaps.append(O.certified_gap(inst.Z.astype(np.float64), inst.y, keeps[k]["w"], res[k]["beta"],
+                                    keeps[k]["alpha"], inst.q, inst.C)[2])
+    return {"metric": "gDWD instances/s (uneven batch)", "value": len(reqs) / dt, "unit": "solves/s",
+            "ms_per_step": dt * 1e3,
+            "config": {"workload": f"uneven_batch {len(reqs)} instances d 5k-50k n 200-2000 q in 0.5,1,2,4",
+                       "store": "bf16", "slots": args.slots},
+            "status": int(st), "converged": int(sum(r["status"] == 0 for r in res)),
+            "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
+            "certified_gap_original_data_every_8th": gaps}
+
+
+def served(args, gdwd, synth):
+    """Poisson arrivals; each request's data is drawn on the device from its seed."""
+    torch = _torch()
+    rng = np.random.default_rng(5001)
+    T, lam = args.serve_seconds, args.serve_rate
+    arrivals = np.cumsum(rng.exponential(1.0 / lam, size=int(lam * T * 1.5)))
+    arrivals = arrivals[arrivals < T]
+    specs = []
+    for k in range(arrivals.size):
+        d = int(round(np.exp(rng.uniform(np.log(1e3), np.log(1e5)))))
+        n = int(round(np.exp(rng.uniform(np.log(50), np.log(5000)))))
+        q = float(rng.choice([1.0, 2.0]))
+        C = float(np.exp(rng.uniform(np.log(0.1), np.log(100))))
+        specs.append((d, n, q, C, 6000 + k))
+    gen_stream = torch.cuda.Stream()
+    srv = gdwd.Server(slots=args.slots)
+    pending = {}          # ticket -> request data kept alive until the request completes
+    results = []
+    t_start = time.perf_counter()
+
+    def reap(block):
+        for t in list(pending):
+            out = srv.poll(t, wait=block)
+            if out is not None:
+                results.append(out)
+                del pending[t]
+
+    for k, (d, n, q, C, seed) in enumerate(specs):
+        now = time.perf_counter() - t_start
+        if arrivals[k] > now:
+            time.sleep(arrivals[k] - now)
+        with torch.cuda.stream(gen_stream):
+            g = torch.Generator(device="cuda")
+            g.manual_seed(seed)
+            v = torch.randn(d, device="cuda", generator=g, dtype=torch.float32)
+            v /= v.norm()
+            y = torch.where(torch.arange(n, device="cuda") < n // 2, 1.0, -1.0)
+            X = torch.randn(n, d, device="cuda", generator=g, dtype=torch.float32) + 1.5 * y[:, None] * v[None, :]
+            Zrows = X * y[:, None]                     # n x d: row i = column i of Z
+            del X
+        gen_stream.synchronize()
+        yh = y.double().cpu().numpy()
+        o = gdwd.default_options()
+        o.tol, o.store = 1e-6, gdwd.F16
+        w = np.zeros(d)
+        r = gdwd.Request(Z=Zrows.data_ptr(), zdt=gdwd.F32, z_on_device=1, d=d, n=n, ldz=d,
+                         y=yh.ctypes.data, q=q, C=C, opts=o, w=w.ctypes.data, alpha=None)
+        t = srv.submit(r, (Zrows, yh, w))
+        pending[t] = (Zrows, yh, w)
+        reap(False)
+    while pending:
+        reap(True)
+    t_total = time.perf_counter() - t_start
+    srv.close()
+    lats = [lat for _, lat in results]
+    ok = sum(1 for res, _ in results if res["status"] == 0)
+    return {"metric": "served gDWD requests: p50/p99 latency, solves/s", "value": len(results) / t_total,
+            "unit": "solves/s", "latency_ms_p50": float(np.percentile(lats, 50)),
+            "latency_ms_p99": float(np.percentile(lats, 99)), "requests": len(results), "converged": ok,
+            "config": {"workload": f"served Poisson {lam}/s for {T} s, d 1k-100k, n 50-5000, q in 1,2, C 0.1-100",
+                       "store": "f16", "slots": args.slots}}
+
+
+def largest_fp8(args, gdwd, synth):
+    torch = _torch()
+    d, n = args.big_d, args.big_n
+    inst = synth.heavy_tailed(seed=5001, d=d, n=n, n_pos=n // 4, q=1.0, C=1.0)
+    Cs = np.logspace(-2, 3, 16)
+    Zd = _device_colmajor(inst.Z)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with gdwd.Solver(Zd, inst.y, 1.0, 1.0, store="e4m3", tol=1e-6, refine=1) as s:
+        res, w, alpha = s.solve(Cs=Cs, alpha=True)
+        info = s.info()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    Z64 = inst.Z.astype(np.float64)
+    gaps = [O.certified_gap(Z64, inst.y, w[:, k], res[k]["beta"], alpha[:, k], 1.0, Cs[k])[2] for k in (0, 15)]
+    return {"metric": "gDWD C-solves/s at KKT<=1e-6 on the original data (FP8 + FP32 refinement)",
+            "value": 16 / dt, "unit": "solves/s", "ms_per_step": dt * 1e3,
+            "config": {"workload": f"largest_fp8 d={d} n={n} Student-t 1:3 16 C", "store": "e4m3+refine"},
+            "setup_ms": info["t_setup_ms"], "iters": [r["iters"] for r in res],
+            "converged": int(sum(r["status"] == 0 for r in res)), "certified_gap_C_ends": gaps}
+
+
+WORKLOADS = {"plain_fp64": plain_fp64, "cgrid_bf16": cgrid_bf16, "uneven_batch": uneven_batch, "served": served,
+             "largest_fp8": largest_fp8}
+
+
+def run(name, args):
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2305_12019_gb300 import build as b
+    b.build()
+    from paper_2305_12019_gb300 import gdwd, synth
+    line = WORKLOADS[name](args, gdwd, synth)
+    line.update({"n_gpus": 1, "data": "synthetic", "higher_is_better": True})
+    print(json.dumps(line), flush=True)
+    return 0

@@ -80,7 +80,15 @@ typedef struct {
   int32_t cgrid_sequential; /* 0 (default): gdwd_solve with several C iterates up to
                          four of them in lock-step in one persistent launch, so each
                          pass over Z serves all of them; 1: one C at a time.         */
-  int64_t reserved[7];
+  int32_t gram_path;  /* 0 (default): the Gram of BF16, F16 and E4M3 storage runs on
+                         the tensor cores (tcgen05.mma; exact products, FP32 sums of at
+                         most 256 rows folded into double-float), F32 / F64 on the SIMT
+                         double-float kernel; 1: the SIMT kernel for every storage.  */
+  int32_t stop_rule;  /* 0 (default): stop when kkt = max(eta_P, eta_D, eta_C, eta_gap)
+                         <= tol; 1: the rule of Sec. 4.3: max(eta_P, eta_D) < tol,
+                         min(eta_C, eta_gap) < sqrt(tol) and max(eta_C, eta_gap) < 0.05
+                         (the paper uses tol = 1e-5 with max_iter = 2000).          */
+  int64_t reserved[6];
 } gdwd_options;
 
 /* Outcome of one solve (one value of C). */
@@ -188,7 +196,8 @@ typedef struct {
   double t_ingest_ms;    /* of which: copy / quantize into the slab layout   */
   double t_gram_ms;      /*           Gram matrix G                          */
   double t_factor_ms;    /*           Cholesky, inverse, p, s                */
-  int64_t reserved[1];
+  int32_t gram_tensor_cores; /* 1: the Gram ran on the tcgen05 tensor cores       */
+  int32_t reserved_;
 } gdwd_info;
 
 gdwd_status gdwd_get_info(const gdwd_handle* h, gdwd_info* info);

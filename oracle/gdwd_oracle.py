@@ -26,10 +26,17 @@ R3  initial iterate r = xi = 1, w = u = 0, beta = 0, alpha = 0, rho = 0
     (the feasible point used in the proof of Prop. 2).
 R4  sigma0 = min(10C, n)^q (Sec. 4.4) unless given.
 R5  the sigma rule runs after the KKT evaluation of every iteration k >= 1.
+R5b ... while max(eta_P, eta_D) > tol: the rule balances eta_P against eta_D, and
+    once both meet the tolerance (the stricter stop of R8 may still wait on
+    eta_C or the gap) their ratio is rounding noise that would drive sigma by
+    factors of 2.2 per iteration.
 R6  eta_D also holds eta_D3 = ||Z~ alpha + D rho|| / (1+C), the w-stationarity of
     the Lagrangian of eq-gen-scale; chi = eta_P / max(eta_D, 1e-300).
 R7  eta_C3 is the unsquared norm ||alpha - s|| / (1+C).
-R8  stopping: kkt = max(eta_P, eta_D, eta_C, eta_gap) <= tol.
+R8  stopping: kkt = max(eta_P, eta_D, eta_C, eta_gap) <= tol (stricter than the
+    paper); stop_rule = 1 applies the paper's rule of Sec. 4.3 instead:
+    max(eta_P, eta_D) < tol, min(eta_C, eta_gap) < sqrt(tol),
+    max(eta_C, eta_gap) < 0.05.
 R9  dual objective kappa * sum(alpha^(q/(q+1))) - Z_scale * ||Z~ alpha||.
 R10 prox bracket [lo, hi], lo = max(a, 0), hi = lo + (omega/sigma)^(1/(q+2)).
 R11 steps 1a and 1c are solved exactly (direct SMW), so the eps_k schedule is
@@ -327,7 +334,7 @@ def sigma_update(sigma, eta_p, eta_d, theta=5.0):
 # --------------------------------------------------------------------------
 
 def solve(Z, y, q, C, mu=1.0, tau=1.618, tol=1e-9, max_iter=50000, sigma0=None,
-          e=None, wt=None, record=False):
+          e=None, wt=None, record=False, stop_rule=0):
     """Inexact sGS-ADMM (Algorithm 1) on eq-gen-scale, exact SMW2 solves (R11).
 
     Z is d x n with columns y_i x_i (Sec. 2, eq-r); y in {-1, +1}^n.
@@ -384,11 +391,18 @@ def solve(Z, y, q, C, mu=1.0, tau=1.618, tol=1e-9, max_iter=50000, sigma0=None,
         eta, pobj, dobj = kkt_residuals(Zt, zs, y, q, C, mu, r, w, beta, xi, u, alpha, rho, e, wt)
         if record:
             history.append((sigma, eta["kkt"], eta["P"], eta["D"]))
-        if eta["kkt"] <= tol:
+        if stop_rule == 0 and eta["kkt"] <= tol:                                  # R8
             break
-        if k >= 1:                                           # R5
+        if stop_rule == 1 and (max(eta["P"], eta["D"]) < tol and min(eta["C"], eta["gap"]) < math.sqrt(tol)
+                               and max(eta["C"], eta["gap"]) < 0.05):               # Sec. 4.3
+            break
+        if k >= 1 and max(eta["P"], eta["D"]) > tol:        # R5, R5b
             sigma = sigma_update(sigma, eta["P"], eta["D"])
-    converged = eta is not None and eta["kkt"] <= tol
+    if stop_rule == 1:
+        converged = eta is not None and (max(eta["P"], eta["D"]) < tol and min(eta["C"], eta["gap"]) < math.sqrt(tol)
+                                         and max(eta["C"], eta["gap"]) < 0.05)
+    else:
+        converged = eta is not None and eta["kkt"] <= tol
     return {
         "w": w / zs, "beta": float(beta), "r": r, "xi": xi, "alpha": alpha,
         "w_scaled": w, "u_scaled": u, "rho": rho, "zscale": zs, "sigma": sigma,

@@ -34,6 +34,7 @@ using namespace gdwd;
 struct gdwd_handle {
   int device = 0;
   int sms = 0;
+  bool gram_tc = false;   // the Gram ran on the tensor cores
   int smem_optin = 0;
   cudaStream_t stream = nullptr;
   gdwd_options opt{};
@@ -55,6 +56,7 @@ struct gdwd_handle {
   float2 *P = nullptr, *pdf = nullptr;
   double *r = nullptr, *xi = nullptr, *alpha = nullptr, *b = nullptr;
   float2 *rhsA = nullptr, *rhsB = nullptr;
+  double *Uu = nullptr, *Ur = nullptr, *kc = nullptr;   // n-space images of u, rho; (G - I) c
   void *cq = nullptr, *aq = nullptr, *partial = nullptr;
   double *u = nullptr, *rho = nullptr, *g = nullptr, *scal = nullptr, *wtmp = nullptr;
   double* dscalars = nullptr;   // [0] sumsq [1] zscale [2] s
@@ -66,7 +68,7 @@ struct gdwd_handle {
   // state of the joint C-grid kernel (up to 4 instances), allocated on first use
   struct {
     bool ready = false;
-    double *r, *xi, *alpha, *b, *u, *rho, *g, *scal;
+    double *r, *xi, *alpha, *b, *u, *rho, *g, *scal, *Ur, *kc;
     float2 *rhsA, *rhsB;
     void *cq, *aq, *partial;
     Ctrl* ctrl;
@@ -187,6 +189,8 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
       !(opt.timeout_s > 0.0))
     return fail(nullptr, GDWD_EINVAL, "gdwd_create: bad options (mu > 0, 0 < tau < golden ratio, tol > 0, max_iter >= 1)");
   if (opt.store < GDWD_F64 || opt.store > GDWD_E4M3) return fail(nullptr, GDWD_EINVAL, "gdwd_create: bad store dtype");
+  if (opt.gram_path != 0 && opt.gram_path != 1) return fail(nullptr, GDWD_EINVAL, "gdwd_create: gram_path must be 0 or 1");
+  if (opt.stop_rule != 0 && opt.stop_rule != 1) return fail(nullptr, GDWD_EINVAL, "gdwd_create: stop_rule must be 0 or 1");
 
   gdwd_handle* h = new gdwd_handle();
   h->opt = opt;
@@ -261,6 +265,9 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
     CK(halloc(h, &h->alpha, n), "alloc");
     CK(halloc(h, &h->b, n), "alloc");
     CK(halloc(h, &h->rhsA, n), "alloc");
+    CK(halloc(h, &h->Uu, n), "alloc");
+    CK(halloc(h, &h->Ur, n), "alloc");
+    CK(halloc(h, &h->kc, n), "alloc");
     CK(halloc(h, &h->rhsB, n), "alloc");
     const size_t ct = h->store == GDWD_F64 ? 8 : 4;
     CK(halloc(h, (uint8_t**)&h->cq, n * ct), "alloc");
@@ -312,13 +319,19 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
     CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream), "memset");
     // Gram and G = I + K / mu
     CK(cudaEventRecord(evg, h->stream), "cudaEventRecord");
-    const int ks = gram_ksplit(h->L, h->sms);
+    const bool tc = h->opt.gram_path == 0 && gram_tc_supported(h->store, h->L);
+    const int ks = tc ? gram_tc_ksplit(h->L, h->sms) : gram_ksplit(h->L, h->sms);
     double* Kpart = nullptr;
     CK(cudaMallocAsync(&Kpart, (size_t)ks * n * n * sizeof(double), h->stream), "cudaMalloc(Kpart)");
-    cudaError_t eg = run_gram(h->store, h->L, ks, Kpart, h->sc, h->opt.mu, h->G, h->stream);
+    cudaError_t eg = run_gram(h->store, h->L, ks, Kpart, h->sc, h->opt.mu, h->G, tc, h->err,
+                              (uint64_t)(h->opt.timeout_s * 1e9), h->stream);
+    int gerr = 0;
+    if (eg == cudaSuccess) eg = cudaMemcpyAsync(&gerr, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     if (eg == cudaSuccess) eg = cudaStreamSynchronize(h->stream);
     cudaFreeAsync(Kpart, h->stream);
     if (eg != cudaSuccess) return cuda_fail(h, eg, "gram");
+    if (gerr) return fail(h, (gdwd_status)gerr, "gdwd_create: the Gram kernel timed out");
+    h->gram_tc = tc;
     // Cholesky, inverse, p, s
     CK(cudaEventRecord(ef0, h->stream), "cudaEventRecord");
     float2 *A = nullptr, *X = nullptr;
@@ -374,7 +387,7 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
 }
 
 template <typename CT>
-static IterArgs<CT> make_args(gdwd_handle* h, double C, double sigma0) {
+static IterArgs<CT> make_args(gdwd_handle* h, double C, double sigma0, int refresh) {
   IterArgs<CT> a{};
   a.L = h->L;
   a.sc = h->sc;
@@ -395,6 +408,7 @@ static IterArgs<CT> make_args(gdwd_handle* h, double C, double sigma0) {
   a.tol = h->opt.tol;
   a.kappa = (h->q + 1.0) / h->q * std::pow(h->q, 1.0 / (h->q + 1.0));
   a.max_iter = h->opt.max_iter;
+  a.stop_rule = h->opt.stop_rule;
   a.grid = h->grid;
   a.timeout_ns = (uint64_t)(h->opt.timeout_s * 1e9);
   a.r = h->r;
@@ -402,6 +416,10 @@ static IterArgs<CT> make_args(gdwd_handle* h, double C, double sigma0) {
   a.alpha = h->alpha;
   a.b = h->b;
   a.rhsA = h->rhsA;
+  a.Uu = h->Uu;
+  a.Ur = h->Ur;
+  a.kc = h->kc;
+  a.refresh = refresh;
   a.rhsB = h->rhsB;
   a.cq = (CT*)h->cq;
   a.aq = (CT*)h->aq;
@@ -464,9 +482,9 @@ static gdwd_status solve_one(gdwd_handle* h, double C, double* w, int w_on_devic
   cudaError_t e;
   const int smem_limit = h->smem_optin - 8192;
   if (h->store == GDWD_F64)
-    e = run_iterate_f64(make_args<double>(h, C, sigma0), smem_limit, st);
+    e = run_iterate_f64(make_args<double>(h, C, sigma0, warm ? 1 : 0), smem_limit, st);
   else
-    e = run_iterate_f32(h->store, make_args<float>(h, C, sigma0), smem_limit, st);
+    e = run_iterate_f32(h->store, make_args<float>(h, C, sigma0, warm ? 1 : 0), smem_limit, st);
   if (e != cudaSuccess) return cuda_fail(h, e, "iterate launch");
   CK(cudaEventRecord(e1, st), "event");
   Ctrl c{};
@@ -520,6 +538,8 @@ static gdwd_status solve_multi(gdwd_handle* h, const double* Cs, int K, int kker
     CK(halloc(h, &m.b, 4 * n), "alloc");
     CK(halloc(h, &m.rhsA, 4 * n), "alloc");
     CK(halloc(h, &m.rhsB, 4 * n), "alloc");
+    CK(halloc(h, &m.Ur, 4 * n), "alloc");
+    CK(halloc(h, &m.kc, 4 * n), "alloc");
     CK(halloc(h, (uint8_t**)&m.cq, 4 * n * ct), "alloc");
     CK(halloc(h, (uint8_t**)&m.aq, 4 * n * ct), "alloc");
     CK(halloc(h, (uint8_t**)&m.partial, 4 * (size_t)n * h->L.NB * ct), "alloc");
@@ -573,6 +593,7 @@ static gdwd_status solve_multi(gdwd_handle* h, const double* Cs, int K, int kker
     for (int j = 0; j < 4; ++j) a.C[j] = Cs[j < K ? j : 0];
     a.K = K;
     a.max_iter = h->opt.max_iter;
+    a.stop_rule = h->opt.stop_rule;
     a.grid = h->grid;
     a.timeout_ns = (uint64_t)(h->opt.timeout_s * 1e9);
     a.dpad = dpad;
@@ -582,6 +603,8 @@ static gdwd_status solve_multi(gdwd_handle* h, const double* Cs, int K, int kker
     a.b = m.b;
     a.rhsA = m.rhsA;
     a.rhsB = m.rhsB;
+    a.Ur = m.Ur;
+    a.kc = m.kc;
     a.u = m.u;
     a.rho = m.rho;
     a.g = m.g;
@@ -766,6 +789,7 @@ extern "C" gdwd_status gdwd_get_info(const gdwd_handle* h, gdwd_info* info) {
   info->t_ingest_ms = h->t_stage_ms[0];
   info->t_gram_ms = h->t_stage_ms[1];
   info->t_factor_ms = h->t_stage_ms[2];
+  info->gram_tensor_cores = h->gram_tc ? 1 : 0;
   return GDWD_OK;
 }
 

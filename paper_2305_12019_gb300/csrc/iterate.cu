@@ -9,17 +9,31 @@
 //     Z~^T w = c - v - y beta,   w = g' - Z~ c / mu
 // (Woodbury applied to the SMW2 form of Sec. 3.3.2; the CPU oracle uses the
 // paper's d-space formulas eq-Ainv / eq-H instead, so the tests check this
-// algebra).  The Step-1b prox input c^k of eq-1c is then c-bar + r^k, Step 1c
-// only changes x, beta, c, and each iteration reads Z twice:
+// algebra).  The Step-1b prox input c^k of eq-1c is then c-bar + r^k, and Step 1c
+// only changes x, beta, c.
 //
-//   phase A  (Z pass 1)  deferred Step 2/3 d-update of u, rho (needs ||g||),
-//                        g' per row, per-slab partial dots of Z~^T g'
-//   phase R              b = reduction of the partials; rhs1 = b + v-bar
+// b = Z~^T g' needs no pass of its own.  With U_u = Z~^T u, U_rho = Z~^T rho and
+// U_g = Z~^T g, the deferred Step 2/3 update u+ = theta g,
+// rho+ = (1 - tau) rho - tau sigma sqrt(mu) (1 - theta) g maps to the same
+// update of U_u, U_rho, and since g = u - Z~ c / mu,
+//     U_g = Z~^T u - Z~^T Z~ c / mu = Z~^T u - (G - I) c,
+//     (G - I) c = (G - I)(x + beta p) = rhs2 - x + beta (y - p)
+// (G x = rhs2 and G p = y).  Z~^T u is taken directly, as column dots on the
+// chunks pass B streams anyway (u is known before the pass starts), so the
+// Gram's rounding enters U_g once per iteration, as it enters the n-space
+// Z~^T w, and does not accumulate; U_rho follows its recurrence, which contracts
+// by |1 - tau| < 1.  One iteration therefore reads Z ONCE:
+//
+//   prologue             warm start: U_u, U_rho by two passes over Z (after the
+//                        deferred update handed over); initial iterate: zero
+//   phase R              U_g from the column dots and (G - I) c; the deferred
+//                        n-space update; b; rhs1 = b + v-bar (rows of the CTA)
 //   phase N1             x-bar = G^{-1} rhs1 (double-float GEMV), beta-bar,
 //                        Step 1b prox (Newton, FP64), rhs2 = b + v
 //   phase N2             x = G^{-1} rhs2, beta, c, Z~^T w; Step 2 xi and
-//                        Step 3 alpha (n part); n-space KKT partial sums
-//   phase B  (Z pass 2)  t = Z~ c, ta = Z~ alpha; g = u - t / mu; d-space sums
+//                        Step 3 alpha (n part); (G - I) c; n-space KKT sums
+//   phase B  (Z pass)    deferred d-update of u, rho; t = Z~ c, ta = Z~ alpha;
+//                        g = u - t / mu; d-space sums; column dots Z~^T u
 //   phase S              all sums -> KKT residuals (Sec. 4.3), duality gap,
 //                        sigma rule (Sec. 4.4), stop test; identical in every CTA
 #include <algorithm>
@@ -71,6 +85,20 @@ struct IterEpi {
   }
 };
 
+// sum over the NB slabs of one row's pass-A partials (lanes of a warp; df for FP32)
+template <typename CT>
+__device__ __forceinline__ double reduce_partials(const CT* pp, int NB, int lane) {
+  if constexpr (sizeof(CT) == 8) {
+    double acc = 0.0;
+    for (int s2 = lane; s2 < NB; s2 += 32) acc += (double)pp[s2];
+    return warp_sum(acc);
+  } else {
+    df acc{0.f, 0.f};
+    for (int s2 = lane; s2 < NB; s2 += 32) df_add(acc, (float)pp[s2]);
+    return df_to_double(df_warp_sum(acc));
+  }
+}
+
 template <typename CT>
 __device__ __forceinline__ void store_ct(CT* p, double v) { *p = (CT)v; }
 
@@ -99,7 +127,6 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
   const int G = Q <= kThreads ? kThreads / Q : 1;
   const int nmy = (NB > cta) ? (NB - cta + grid - 1) / grid : 0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int gw = cta * kWarps + warp, W = grid * kWarps;
   // contiguous block of G^{-1} rows (and n-space entries) owned by this CTA
   const int64_t rpc = (n + grid - 1) / grid;
   const int64_t r0 = ((int64_t)cta * rpc < n) ? (int64_t)cta * rpc : n;
@@ -149,66 +176,86 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
     GDWD_MARK(k + 1);                                                                     \
   } while (0)
 
-  int it = it0;
-  for (; it < a.max_iter; ++it) {
-    // ---------------- phase A: deferred (u, rho) update, g', Z~^T g' partials
-    {
+  const int npair = (int)((n + 1) / 2);
+  float2* rhs_s = reinterpret_cast<float2*>(uni);
+  float* s_redf = reinterpret_cast<float*>(s_red);
+
+  // ---------------- prologue: U_u = Z~^T u and U_rho = Z~^T rho of the starting
+  // iterate for this CTA's rows.  A warm start computes them with two passes over
+  // Z (after the deferred (u, rho) update it hands over); the initial iterate has
+  // u = rho = 0.
+  if (a.refresh) {
+    const double rcoef0 = a.tau * sig_prev * sqmu * (1.0 - theta);
+    for (int v = 0; v < 2; ++v) {
       CT* gp = reinterpret_cast<CT*>(uni);
-      const double gsc = rcp_nr(sig * sqmu);
-      const double rcoef = a.tau * sig_prev * sqmu * (1.0 - theta);
       for (int k = 0; k < nmy; ++k) {
         const int64_t s = cta + (int64_t)k * grid;
         for (int j = threadIdx.x; j < TB; j += kThreads) {
           const int64_t gj = s * TB + j;
-          double gpv = 0.0;
+          double val = 0.0;
           if (gj < d) {
-            double uj = a.u[gj], rj = a.rho[gj];
-            if (pending) {
+            if (v == 0 && pending) {
               const double g = a.g[gj];
-              rj = (1.0 - a.tau) * rj - rcoef * g;      // rho <- rho - tau sigma D (w - u+)
-              uj = theta * g;                           // u+ = Pi_B(g)
-              a.u[gj] = uj;
-              a.rho[gj] = rj;
+              a.rho[gj] = (1.0 - a.tau) * a.rho[gj] - rcoef0 * g;
+              a.u[gj] = theta * g;
             }
-            gpv = uj + rj * gsc;
+            val = v == 0 ? a.u[gj] : a.rho[gj];
           }
-          gp[(size_t)k * TB + j] = (CT)gpv;
+          gp[(size_t)k * TB + j] = (CT)val;
         }
       }
       __syncthreads();
       PassA<T> pa{gp, a.partial, TB, NB, Q, H};
       if (!stream_slabs<T>(L, rg, cta, grid, a.err, a.timeout_ns, &s_abort, pa)) return;
-    }
-    GDWD_BARRIER(0);
-
-    const double inv_sig = rcp_nr(sig);
-    // ---------------- phase R: b = sc * sum of partials; rhs1 = b + xi - r - alpha / sigma
-    for (int64_t i = gw; i < n; i += W) {
-      const CT* pp = a.partial + (size_t)i * NB;
-      double bsum;
-      if constexpr (sizeof(CT) == 8) {
-        double acc = 0.0;
-        for (int s2 = lane; s2 < NB; s2 += 32) acc += (double)pp[s2];
-        bsum = warp_sum(acc);
-      } else {
-        df acc{0.f, 0.f};
-        for (int s2 = lane; s2 < NB; s2 += 32) df_add(acc, (float)pp[s2]);
-        bsum = df_to_double(df_warp_sum(acc));
+      GDWD_BARRIER(0);
+      for (int t = warp; t < nrows; t += kWarps) {
+        const int64_t i = r0 + t;
+        const double bsum = reduce_partials<CT>(a.partial + (size_t)i * NB, NB, lane);
+        if (lane == 0) (v == 0 ? a.Uu : a.Ur)[i] = a.sc[i] * bsum;
       }
-      if (lane == 0) {
-        const double bi = a.sc[i] * bsum;
-        a.b[i] = bi;
-        const double v = a.xi[i] - a.r[i] - a.alpha[i] * inv_sig;
-        const df r1 = df_from(bi + v);
-        a.rhsA[i] = make_float2(r1.hi, r1.lo);
+      GDWD_BARRIER(0);   // the partials are rewritten by the next pass
+    }
+    pending = 0;
+  } else {
+    for (int t = threadIdx.x; t < nrows; t += kThreads) {
+      a.Uu[r0 + t] = 0.0;
+      a.Ur[r0 + t] = 0.0;
+    }
+  }
+  __syncthreads();
+
+  int it = it0;
+  for (; it < a.max_iter; ++it) {
+    const double inv_sig = rcp_nr(sig);
+    // ---------------- phase R (this CTA's rows): U_g = Z~^T g of the last iteration
+    // from the pass-B column dots Z~^T u and (G - I) c; the deferred update
+    // U_u = theta U_g, U_rho <- (1 - tau) U_rho - tau sigma' sqrt(mu) (1 - theta) U_g;
+    // b = U_u + U_rho / (sigma sqrt(mu)); rhs1 = b + xi - r - alpha / sigma
+    {
+      const double gsc = rcp_nr(sig * sqmu);
+      const double rcoef = a.tau * sig_prev * sqmu * (1.0 - theta);
+      for (int t = warp; t < nrows; t += kWarps) {
+        const int64_t i = r0 + t;
+        double ug = 0.0;
+        if (pending) ug = a.sc[i] * reduce_partials<CT>(a.partial + (size_t)i * NB, NB, lane) - a.kc[i];
+        if (lane == 0) {
+          double uu = a.Uu[i], ur = a.Ur[i];
+          if (pending) {
+            uu = theta * ug;
+            ur = (1.0 - a.tau) * ur - rcoef * ug;
+            a.Ur[i] = ur;
+          }
+          const double bi = uu + ur * gsc;
+          a.b[i] = bi;
+          const double v = a.xi[i] - a.r[i] - a.alpha[i] * inv_sig;
+          const df r1 = df_from(bi + v);
+          a.rhsA[i] = make_float2(r1.hi, r1.lo);
+        }
       }
     }
     GDWD_BARRIER(2);
 
-    // ---------------- phase N1: x-bar, beta-bar, prox, rhs2
-    const int npair = (int)((n + 1) / 2);
-    float2* rhs_s = reinterpret_cast<float2*>(uni);
-    float* s_redf = reinterpret_cast<float*>(s_red);
+    // ---------------- phase N1: x-bar, beta-bar, Step 1b prox, rhs2
     {
       for (int64_t i = threadIdx.x; i < 2 * npair; i += kThreads) rhs_s[i] = i < n ? a.rhsA[i] : make_float2(0.f, 0.f);
       __syncthreads();
@@ -243,7 +290,8 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
     }
     GDWD_BARRIER(4);
 
-    // ---------------- phase N2: x, beta, c, Z~^T w; Step 2 (xi), Step 3 (alpha)
+    // ---------------- phase N2: x, beta, c, Z~^T w; Step 2 (xi), Step 3 (alpha);
+    // (G - I) c = rhs2 - x + beta (y - p) for the next U_g
     {
       for (int64_t i = threadIdx.x; i < 2 * npair; i += kThreads) rhs_s[i] = i < n ? a.rhsB[i] : make_float2(0.f, 0.f);
       __syncthreads();
@@ -267,7 +315,8 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
       for (int t = threadIdx.x; t < nrows; t += kThreads) {
         const int64_t i = r0 + t;
         {
-          const double c = ((double)s_xh[t] + (double)s_xl[t]) + beta * a.p[i];
+          const double xv = (double)s_xh[t] + (double)s_xl[t];
+          const double c = xv + beta * a.p[i];
           const double ri = a.r[i], al = a.alpha[i], yi = a.y[i], ce = a.C * a.e[i];
           const double v = a.xi[i] - ri - al * inv_sig;
           const double zw = c - v - yi * beta;                                     // Z~^T w
@@ -278,6 +327,8 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
           a.alpha[i] = an;
           store_ct(a.cq + i, a.sc[i] * c);
           store_ct(a.aq + i, a.sc[i] * an);
+          const double rh2 = (double)rhs_s[i].x + (double)rhs_s[i].y;
+          a.kc[i] = rh2 - xv + beta * (yi - a.p[i]);
           const double rq1 = pow_q1(ri, a.q, qcase);
           const double irq1 = rcp_nr(rq1);
           const double om = a.omega[i];
@@ -299,15 +350,37 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
     }
     GDWD_BARRIER(6);
 
-    // ---------------- phase B: t = Z~ c, ta = Z~ alpha, g, d-space sums
+    // ---------------- phase B (the one pass over Z): deferred (u, rho) update;
+    // t = Z~ c, ta = Z~ alpha, g = u - t / mu and the d-space sums; on the same
+    // chunks the column dots of Z~^T u (for the next U_g)
     {
       CT* cv = reinterpret_cast<CT*>(uni);
       CT* av = cv + n;
-      double* red = reinterpret_cast<double*>(
-          uni + ((2 * n * sizeof(CT) + 15) & ~(size_t)15));
+      const size_t off_red = (2 * n * sizeof(CT) + 15) & ~(size_t)15;
+      double* red = reinterpret_cast<double*>(uni + off_red);
+      CT* up = reinterpret_cast<CT*>(uni + off_red + (size_t)2 * G * TB * sizeof(double));
+      const double rcoef = a.tau * sig_prev * sqmu * (1.0 - theta);
       for (int64_t i = threadIdx.x; i < n; i += kThreads) {
         cv[i] = a.cq[i];
         av[i] = a.aq[i];
+      }
+      for (int k = 0; k < nmy; ++k) {
+        const int64_t s = cta + (int64_t)k * grid;
+        for (int j = threadIdx.x; j < TB; j += kThreads) {
+          const int64_t gj = s * TB + j;
+          double uj = 0.0;
+          if (gj < d) {
+            if (pending) {
+              const double g = a.g[gj];
+              a.rho[gj] = (1.0 - a.tau) * a.rho[gj] - rcoef * g;    // rho <- rho - tau sigma D (w - u+)
+              uj = theta * g;                                       // u+ = Pi_B(g)
+              a.u[gj] = uj;
+            } else {
+              uj = a.u[gj];
+            }
+          }
+          up[(size_t)k * TB + j] = (CT)uj;
+        }
       }
       __syncthreads();
       IterEpi epi{a.g, a.u, a.rho, inv_mu, sqmu * (1.0 - a.tau)};
@@ -325,7 +398,9 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
         pb.rc[kk].reset();
         pb.ra[kk].reset();
       }
-      if (!stream_slabs<T>(L, rg, cta, grid, a.err, a.timeout_ns, &s_abort, pb)) return;
+      PassA<T> pa{up, a.partial, TB, NB, Q, H};
+      PassBA<T, IterEpi> pba{&pb, &pa};
+      if (!stream_slabs<T>(L, rg, cta, grid, a.err, a.timeout_ns, &s_abort, pba)) return;
       const double vals[6] = {epi.sg2, epi.sgr, epi.sr2, epi.sa2, epi.sag, epi.sta2};
       block_sum_n<6>(vals, kWarps, s_part, a.scal + (size_t)S_G2 * grid + cta, grid);
     }
@@ -374,10 +449,12 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
       if (!(kkt == kkt) || isinf(kkt)) {
         done = 1;
         status = GDWD_ENUMERIC;
-      } else if (kkt <= a.tol) {
+      } else if (a.stop_rule == 0 ? kkt <= a.tol
+                                  : (fmax(ep, ed) < a.tol && fmin(ec, gap) < sqrt_nr(a.tol) &&
+                                     fmax(ec, gap) < 0.05)) {
         done = 1;
         status = GDWD_OK;
-      } else if (it >= 1) {                                                  // sigma rule, Sec. 4.4
+      } else if (it >= 1 && fmax(ep, ed) > a.tol) {                          // sigma rule, Sec. 4.4
         const float chi = (float)ep / fmaxf((float)ed, 1e-30f);
         const float ichi = (float)ed / fmaxf((float)ep, 1e-30f);
         const float big = fmaxf(chi, ichi);
@@ -439,7 +516,8 @@ static size_t union_bytes(const Layout& L, int grid) {
   const int Q = L.TB / VEC;
   const int G = Q <= kThreads ? kThreads / Q : 1;
   size_t a_bytes = (size_t)nmy * L.TB * sizeof(CT);
-  size_t b_bytes = ((2 * L.n * sizeof(CT) + 15) & ~(size_t)15) + (size_t)2 * G * L.TB * sizeof(double);
+  size_t b_bytes = ((2 * L.n * sizeof(CT) + 15) & ~(size_t)15) + (size_t)2 * G * L.TB * sizeof(double) +
+                   (size_t)nmy * L.TB * sizeof(CT);
   size_t n_bytes = (size_t)((L.n + 1) / 2) * 2 * sizeof(float2);
   size_t u = a_bytes;
   if (b_bytes > u) u = b_bytes;

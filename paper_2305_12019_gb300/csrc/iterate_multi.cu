@@ -7,12 +7,12 @@
 // frozen while the others continue.
 //
 // Per iteration, as in the single-instance kernel (see iterate.cu for the
-// n-space reduction):
-//   A   K deferred d-updates, g'_j, partial dots Z~^T [g'_1 .. g'_K] (one Z read)
-//   R   b_j = reduction of the partials
+// n-space reduction and for b_j = Z~^T g'_j without a pass of its own):
+//   R   U_g from the column dots, deferred n-space updates, b_j, rhs1_j
 //   N1  x-bar_j = G^{-1} rhs1_j (one read of each G^{-1} row for all j), Step 1b
-//   N2  x_j, beta_j, c_j, Steps 2-3, n-space sums
-//   B   Z~ [c_1 .. c_K], Z~ [alpha_1 .. alpha_K] (one Z read), d-space sums
+//   N2  x_j, beta_j, c_j, Steps 2-3, (G - I) c_j, n-space sums
+//   B   K deferred d-updates, Z~ [c_1 .. c_K], Z~ [alpha_1 .. alpha_K] and the
+//       column dots Z~^T [u_1 .. u_K] (the one Z read), d-space sums
 //   S   per-instance KKT, sigma rule, stop test
 #include <algorithm>
 #include <mutex>
@@ -50,7 +50,7 @@ __device__ __forceinline__ void load2(const __nv_fp8_e4m3* p, float* v) {
 }
 
 // pass A for K right-hand sides; each thread covers two columns per round so
-// that every g' vector read from shared memory serves two Z vectors
+// that every vector read from shared memory serves two Z vectors
 template <typename T, int K>
 struct PassAK {
   using CT = typename ElemTraits<T>::compute_t;
@@ -131,6 +131,10 @@ struct EpiK {
   }
 };
 
+// pass B for K instances and, on the same chunks, the column dots Z~^T u_j
+template <typename T, int K>
+struct PassBAK;
+
 // pass B for K instances x two right-hand sides (c_j, alpha_j); a thread owns
 // two consecutive rows of a column group; coefficients come through the L1
 template <typename T, int K>
@@ -209,6 +213,17 @@ struct PassBK {
   }
 };
 
+template <typename T, int K>
+struct PassBAK {
+  PassBK<T, K>* b;
+  PassAK<T, K>* a;
+  __device__ void chunk(const T* buf, int k, int s, int col0, int cw) {
+    b->chunk(buf, k, s, col0, cw);
+    a->chunk(buf, k, s, col0, cw);
+  }
+  __device__ void end_slab(int k, int s) { b->end_slab(k, s); }
+};
+
 // K x N values per thread summed over the block; out[j * S_COUNT * grid + (k0 + k) * grid]
 template <int K, int N>
 __device__ __forceinline__ void block_sum_kn(const double (&v)[K][N], double* s_part, double* out, int grid,
@@ -253,7 +268,6 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_multi_kernel(MultiArgs<ty
   const int G2 = Q2 <= kThreads ? kThreads / Q2 : 1;
   const int nmy = (NB > cta) ? (NB - cta + grid - 1) / grid : 0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int gw = cta * kWarps + warp, W = grid * kWarps;
   const int qcase = q_case(a.q);
   const double sqmu = sqrt(a.mu), inv_mu = 1.0 / a.mu;
   const double inv_q = 1.0 / a.q;
@@ -292,62 +306,49 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_multi_kernel(MultiArgs<ty
     if (!grid_barrier(a.bar, (unsigned)grid, gen, a.err, a.timeout_ns, &s_flag)) return; \
   } while (0)
 
+  // initial iterate: u = rho = 0, so Z~^T u = Z~^T rho = 0
+  for (int m = threadIdx.x; m < K * nrows; m += kThreads) {
+    const int j = m / nrows, t = m - j * nrows;
+    a.Ur[(int64_t)j * n + r0 + t] = 0.0;
+  }
+  __syncthreads();
+
+  float2* rhs_s = reinterpret_cast<float2*>(uni);
+  const int rstride = 2 * npair;
+  float* s_redf = reinterpret_cast<float*>(s_red);
   int it = 0;
   for (; it < a.max_iter && act; ++it) {
-    // ---------------- A: deferred (u, rho) updates, g'_j, partial dots
-    {
-      CT* gp = reinterpret_cast<CT*>(uni);
-      const int gstride = nmy * TB;
-#pragma unroll
-      for (int j = 0; j < K; ++j) {
-        const bool on = act & (1u << j);
-        const double gsc = rcp_nr(sig[j] * sqmu);
-        const double rcoef = a.tau * sig_prev[j] * sqmu * (1.0 - theta[j]);
-        for (int k = 0; k < nmy; ++k) {
-          const int64_t s = cta + (int64_t)k * grid;
-          for (int jl = threadIdx.x; jl < TB; jl += kThreads) {
-            const int64_t gj = s * TB + jl;
-            double gpv = 0.0;
-            if (on && gj < d) {
-              const int64_t idx = (int64_t)j * dpad + gj;
-              double uj = a.u[idx], rj = a.rho[idx];
-              if (pending) {
-                const double gv = a.g[idx];
-                rj = (1.0 - a.tau) * rj - rcoef * gv;
-                uj = theta[j] * gv;
-                a.u[idx] = uj;
-                a.rho[idx] = rj;
-              }
-              gpv = uj + rj * gsc;
-            }
-            gp[(size_t)j * gstride + (size_t)k * TB + jl] = (CT)gpv;
-          }
-        }
-      }
-      __syncthreads();
-      PassAK<T, K> pa{gp, gstride, a.partial, TB, NB, Q, n};
-      if (!stream_slabs<T>(L, rg, cta, grid, a.err, a.timeout_ns, &s_abort, pa)) return;
-    }
-    MBARRIER();
-
-    // ---------------- R
-    for (int64_t idx = gw; idx < (int64_t)K * n; idx += W) {
-      const int j = (int)(idx / n);
-      const int64_t i = idx - (int64_t)j * n;
+    // ---------------- R (this CTA's rows, every active instance): U_g from the
+    // pass-B column dots and (G - I) c, the deferred n-space update, b, rhs1
+    // (see iterate.cu)
+    for (int m = warp; m < K * nrows; m += kWarps) {
+      const int j = m / nrows, t = m - j * nrows;
       if (!(act & (1u << j))) continue;
-      const CT* pp = a.partial + (size_t)idx * NB;
-      double bsum;
-      if constexpr (sizeof(CT) == 8) {
-        double acc = 0.0;
-        for (int s2 = lane; s2 < NB; s2 += 32) acc += (double)pp[s2];
-        bsum = warp_sum(acc);
-      } else {
-        df acc{0.f, 0.f};
-        for (int s2 = lane; s2 < NB; s2 += 32) df_add(acc, (float)pp[s2]);
-        bsum = df_to_double(df_warp_sum(acc));
+      const int64_t i = r0 + t, idx = (int64_t)j * n + i;
+      double ug = 0.0;
+      if (pending) {
+        const CT* pp = a.partial + (size_t)idx * NB;
+        double bsum;
+        if constexpr (sizeof(CT) == 8) {
+          double acc = 0.0;
+          for (int s2 = lane; s2 < NB; s2 += 32) acc += (double)pp[s2];
+          bsum = warp_sum(acc);
+        } else {
+          df acc{0.f, 0.f};
+          for (int s2 = lane; s2 < NB; s2 += 32) df_add(acc, (float)pp[s2]);
+          bsum = df_to_double(df_warp_sum(acc));
+        }
+        ug = a.sc[i] * bsum - a.kc[idx];
       }
       if (lane == 0) {
-        const double bi = a.sc[i] * bsum;
+        double uu = 0.0, ur = a.Ur[idx];
+        if (pending) {
+          const double rcoef = a.tau * sig_prev[j] * sqmu * (1.0 - theta[j]);
+          uu = theta[j] * ug;
+          ur = (1.0 - a.tau) * ur - rcoef * ug;
+          a.Ur[idx] = ur;
+        }
+        const double bi = uu + ur * rcp_nr(sig[j] * sqmu);
         a.b[idx] = bi;
         const double v = a.xi[idx] - a.r[idx] - a.alpha[idx] * rcp_nr(sig[j]);
         const df r1 = df_from(bi + v);
@@ -358,9 +359,6 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_multi_kernel(MultiArgs<ty
 
     // ---------------- N1 and N2 share the structure: load K right-hand sides,
     // beta_j = -p^T rhs_j / s, rows of G^{-1} against all K, per-row work
-    float2* rhs_s = reinterpret_cast<float2*>(uni);
-    const int rstride = 2 * npair;
-    float* s_redf = reinterpret_cast<float*>(s_red);
     for (int phase = 0; phase < 2; ++phase) {
       const float2* src = phase == 0 ? a.rhsA : a.rhsB;
       for (int64_t m = threadIdx.x; m < (int64_t)K * rstride; m += kThreads) {
@@ -433,7 +431,8 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_multi_kernel(MultiArgs<ty
           const double inv_sig = rcp_nr(sig[j]);
           for (int t = threadIdx.x; t < nrows; t += kThreads) {
             const int64_t i = r0 + t, idx = (int64_t)j * n + i;
-            const double c = ((double)s_xh[j][t] + (double)s_xl[j][t]) + bet[j] * a.p[i];
+            const double xv = (double)s_xh[j][t] + (double)s_xl[j][t];
+            const double c = xv + bet[j] * a.p[i];
             const double ri = a.r[idx], al = a.alpha[idx], yi = a.y[i], ce = a.C[j] * a.e[i];
             const double v = a.xi[idx] - ri - al * inv_sig;
             const double zw = c - v - yi * bet[j];
@@ -444,6 +443,8 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_multi_kernel(MultiArgs<ty
             a.alpha[idx] = an;
             a.cq[idx] = (CT)(a.sc[i] * c);
             a.aq[idx] = (CT)(a.sc[i] * an);
+            const float2 rv = rhs_s[(size_t)j * rstride + i];
+            a.kc[idx] = ((double)rv.x + (double)rv.y) - xv + bet[j] * (yi - a.p[i]);   // (G - I) c
             const double rq1 = pow_q1(ri, a.q, qcase);
             const double irq1 = rcp_nr(rq1);
             const double om = a.omega[i];
@@ -465,9 +466,37 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_multi_kernel(MultiArgs<ty
       }
     }
 
-    // ---------------- B
+    // ---------------- B (the one Z read): K deferred d-updates, Z~ [c_1 .. c_K],
+    // Z~ [alpha_1 .. alpha_K], d-space sums, column dots Z~^T [u_1 .. u_K]
     {
+      const int gstride = nmy * TB;
       double* red = reinterpret_cast<double*>(uni);
+      CT* up = reinterpret_cast<CT*>(uni + (size_t)2 * G2 * TB * sizeof(double));
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        const bool on = act & (1u << j);
+        const double rcoef = a.tau * sig_prev[j] * sqmu * (1.0 - theta[j]);
+        for (int k = 0; k < nmy; ++k) {
+          const int64_t s = cta + (int64_t)k * grid;
+          for (int jl = threadIdx.x; jl < TB; jl += kThreads) {
+            const int64_t gj = s * TB + jl;
+            double uj = 0.0;
+            if (on && gj < d) {
+              const int64_t idx = (int64_t)j * dpad + gj;
+              if (pending) {
+                const double gv = a.g[idx];
+                a.rho[idx] = (1.0 - a.tau) * a.rho[idx] - rcoef * gv;
+                uj = theta[j] * gv;
+                a.u[idx] = uj;
+              } else {
+                uj = a.u[idx];
+              }
+            }
+            up[(size_t)j * gstride + (size_t)k * TB + jl] = (CT)uj;
+          }
+        }
+      }
+      __syncthreads();
       EpiK<K> epi;
       epi.g = a.g;
       epi.u = a.u;
@@ -497,7 +526,9 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_multi_kernel(MultiArgs<ty
           pb.rc[j][x].reset();
           pb.ra[j][x].reset();
         }
-      if (!stream_slabs<T>(L, rg, cta, grid, a.err, a.timeout_ns, &s_abort, pb)) return;
+      PassAK<T, K> pa{up, gstride, a.partial, TB, NB, Q, n};
+      PassBAK<T, K> pba{&pb, &pa};
+      if (!stream_slabs<T>(L, rg, cta, grid, a.err, a.timeout_ns, &s_abort, pba)) return;
       block_sum_kn<K, 6>(epi.sums, s_part, a.scal + cta, grid, S_G2);
     }
     MBARRIER();
@@ -546,10 +577,12 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_multi_kernel(MultiArgs<ty
       if (!(kkt == kkt) || isinf(kkt)) {
         done = 1.0;
         stat = GDWD_ENUMERIC;
-      } else if (kkt <= a.tol) {
+      } else if (a.stop_rule == 0 ? kkt <= a.tol
+                                  : (fmax(ep, ed) < a.tol && fmin(ec, gap) < sqrt_nr(a.tol) &&
+                                     fmax(ec, gap) < 0.05)) {
         done = 1.0;
         stat = GDWD_OK;
-      } else if (it >= 1) {
+      } else if (it >= 1 && fmax(ep, ed) > a.tol) {
         const float chi = (float)ep / fmaxf((float)ed, 1e-30f);
         const float ichi = (float)ed / fmaxf((float)ep, 1e-30f);
         const float big = fmaxf(chi, ichi);
@@ -602,14 +635,13 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_multi_kernel(MultiArgs<ty
 
 template <typename T>
 static size_t union_bytes_multi(const Layout& L, int grid, int K) {
-  using CT = typename ElemTraits<T>::compute_t;
-  const int nmy = (L.NB + grid - 1) / grid;
   const int Q2 = L.TB / 2;
   const int G2 = Q2 <= kThreads ? kThreads / Q2 : 1;
-  const size_t a_bytes = (size_t)K * nmy * L.TB * sizeof(CT);
+  using CT = typename ElemTraits<T>::compute_t;
+  const int nmy = (L.NB + grid - 1) / grid;
   const size_t n_bytes = (size_t)K * ((L.n + 1) / 2) * 2 * sizeof(float2);
-  const size_t b_bytes = (size_t)2 * G2 * L.TB * sizeof(double);
-  return (std::max(a_bytes, std::max(n_bytes, b_bytes)) + 127) & ~(size_t)127;
+  const size_t b_bytes = (size_t)2 * G2 * L.TB * sizeof(double) + (size_t)K * nmy * L.TB * sizeof(CT);
+  return (std::max(n_bytes, b_bytes) + 127) & ~(size_t)127;
 }
 
 template <auto Kern>

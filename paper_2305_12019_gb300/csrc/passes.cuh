@@ -244,4 +244,17 @@ struct PassB {
   }
 };
 
+// pass B and, on the same chunks, pass A with another vector (one read of Z
+// serves Z~ [c, alpha] and Z~^T u)
+template <typename T, typename Epi>
+struct PassBA {
+  PassB<T, Epi>* b;
+  PassA<T>* a;
+  __device__ void chunk(const T* buf, int k, int s, int col0, int cw) {
+    b->chunk(buf, k, s, col0, cw);
+    a->chunk(buf, k, s, col0, cw);
+  }
+  __device__ void end_slab(int k, int s) { b->end_slab(k, s); }
+};
+
 }  // namespace gdwd

@@ -342,18 +342,23 @@ int gram_ksplit(const Layout& L, int sms) {
 }
 
 cudaError_t run_gram(int store, const Layout& L, int ksplit, double* Kpart, const double* sc, double mu, double* G,
-                     cudaStream_t st) {
-  const int Tt = (int)((L.n + kGT - 1) / kGT);
-  const int tiles = Tt * (Tt + 1) / 2;
-  const dim3 grid(tiles * ksplit);
-  switch (store) {
-    case GDWD_F64: gram_kernel<double><<<grid, kThreads, 0, st>>>(L, Tt, ksplit, Kpart); break;
-    case GDWD_BF16: gram_kernel<__nv_bfloat16><<<grid, kThreads, 0, st>>>(L, Tt, ksplit, Kpart); break;
-    case GDWD_F16: gram_kernel<__half><<<grid, kThreads, 0, st>>>(L, Tt, ksplit, Kpart); break;
-    case GDWD_E4M3: gram_kernel<__nv_fp8_e4m3><<<grid, kThreads, 0, st>>>(L, Tt, ksplit, Kpart); break;
-    default: gram_kernel<float><<<grid, kThreads, 0, st>>>(L, Tt, ksplit, Kpart); break;
+                     bool tensor_cores, int* err, uint64_t timeout_ns, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  if (tensor_cores) {
+    e = run_gram_tc(store, L, ksplit, Kpart, err, timeout_ns, st);
+  } else {
+    const int Tt = (int)((L.n + kGT - 1) / kGT);
+    const int tiles = Tt * (Tt + 1) / 2;
+    const dim3 grid(tiles * ksplit);
+    switch (store) {
+      case GDWD_F64: gram_kernel<double><<<grid, kThreads, 0, st>>>(L, Tt, ksplit, Kpart); break;
+      case GDWD_BF16: gram_kernel<__nv_bfloat16><<<grid, kThreads, 0, st>>>(L, Tt, ksplit, Kpart); break;
+      case GDWD_F16: gram_kernel<__half><<<grid, kThreads, 0, st>>>(L, Tt, ksplit, Kpart); break;
+      case GDWD_E4M3: gram_kernel<__nv_fp8_e4m3><<<grid, kThreads, 0, st>>>(L, Tt, ksplit, Kpart); break;
+      default: gram_kernel<float><<<grid, kThreads, 0, st>>>(L, Tt, ksplit, Kpart); break;
+    }
+    e = cudaGetLastError();
   }
-  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   gram_finish_kernel<<<1024, 256, 0, st>>>(Kpart, ksplit, sc, L.n, 1.0 / mu, G);
   return cudaGetLastError();

@@ -84,6 +84,7 @@ struct IterArgs {
   double inv_s;          // 1 / (y^T p)
   double q, C, mu, tau, R, tol, kappa;
   int max_iter;
+  int stop_rule;         // 0: kkt <= tol; 1: the rule of Sec. 4.3
   int grid;
   uint64_t timeout_ns;
   // n-space state
@@ -95,11 +96,15 @@ struct IterArgs {
   float2* rhsB;
   CT* cq;                // n: sc_i c_i   (pass B right-hand side 1)
   CT* aq;                // n: sc_i alpha_i (pass B right-hand side 2)
+  double* Uu;            // n: Z~^T u of the starting iterate (rows of the owning CTA)
+  double* Ur;            // n: Z~^T rho (rows of the owning CTA)
+  double* kc;            // n: (G - I) c of the last iteration
+  int refresh;           // 1: U_u, U_rho from u, rho by two passes over Z at launch start
   // d-space state, NB*TB long (padding rows stay 0)
   double* u;
   double* rho;
   double* g;
-  CT* partial;           // n x NB per-slab partial dots of pass A
+  CT* partial;           // n x NB per-slab partial dots (Z~^T u of pass B; start-up passes)
   double* scal;          // grid x S_COUNT
   unsigned* bar;
   int* err;
@@ -123,13 +128,15 @@ struct MultiArgs {
   double C[4];
   int K;                // instances in use (the rest start frozen)
   int max_iter, grid;
+  int stop_rule;        // as in IterArgs
   uint64_t timeout_ns;
   int64_t dpad;
   double *r, *xi, *alpha, *b;   // [K][n]
   float2 *rhsA, *rhsB;          // [K][n]
+  double *Ur, *kc;              // [K][n]: Z~^T rho_j (rows of the owning CTA), (G - I) c_j
+  CT* partial;                  // [K][n][NB]: column dots Z~^T u_j of pass B
   CT *cq, *aq;                  // [K][n]
   double *u, *rho, *g;          // [K][dpad]
-  CT* partial;                  // [K][n][NB]
   double* scal;                 // [K][S_COUNT][grid]
   unsigned* bar;
   int* err;
@@ -166,9 +173,15 @@ struct FactorArgs {
 cudaError_t run_ingest(const void* Z, int zdt, int64_t ldz, const Layout& L, void* out, int store, double* part,
                        int nparts, double* sumsq, int* nonfinite, double* sc, double* zscale, double* amax,
                        double* colscale, cudaStream_t st);
+// Gram: tensor-core path (gram_tc.cu) for BF16 / FP16 / E4M3 storage when
+// gram_tc_supported(); SIMT double-float path (setup.cu) otherwise.
+bool gram_tc_supported(int store, const Layout& L);
+int gram_tc_ksplit(const Layout& L, int sms);
+cudaError_t run_gram_tc(int store, const Layout& L, int ksplit, double* Kpart, int* err, uint64_t timeout_ns,
+                        cudaStream_t st);
 int gram_ksplit(const Layout& L, int sms);
 cudaError_t run_gram(int store, const Layout& L, int ksplit, double* Kpart, const double* sc, double mu, double* G,
-                     cudaStream_t st);
+                     bool tensor_cores, int* err, uint64_t timeout_ns, cudaStream_t st);
 cudaError_t run_factor(const FactorArgs& a, cudaStream_t st);
 
 cudaError_t launch_prox(const double* a, const double* r0, const double* omega, double sigma, double q,

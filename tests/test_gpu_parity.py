@@ -260,3 +260,22 @@ def test_refinement_sweep_restores_original_optimum(gdwd_lib, fmt):
         _compare(r, w[:, k], ref)
         ok, _ = _predictions_match(inst.Xtest.astype(np.float64), w[:, k], r["beta"], ref["w"], ref["beta"])
         assert ok
+
+
+def test_paper_stopping_rule(gdwd_lib):
+    """stop_rule = 1 (Sec. 4.3's rule at tol 1e-5): the reported residuals meet its
+    three conditions, it stops no later than the strict rule, and the point is a
+    moderately accurate solution of the oracle's problem."""
+    inst = synth.gaussian(seed=71, d=6000, n=300, shift=1.0, n_pos=120, q=1.0, C=1.0)
+    with gdwd_lib.Solver(inst.Z, inst.y, 1.0, 1.0, store="f32", tol=1e-5, stop_rule=1, max_iter=2000) as s:
+        rp, wp, _ = s.solve()
+    with gdwd_lib.Solver(inst.Z, inst.y, 1.0, 1.0, store="f32", tol=1e-5) as s:
+        rs, ws, _ = s.solve()
+    r = rp[0]
+    assert r["status"] == 0 and rs[0]["status"] == 0
+    assert max(r["eta_p"], r["eta_d"]) < 1e-5
+    assert min(r["eta_c"], r["eta_gap"]) < np.sqrt(1e-5)
+    assert max(r["eta_c"], r["eta_gap"]) < 0.05
+    assert r["iters"] <= rs[0]["iters"]
+    ref = O.solve(inst.Z.astype(np.float64), inst.y, 1.0, 1.0, tol=1e-9)
+    assert abs(r["primal_obj"] - ref["primal"]) / ref["primal"] <= 0.05

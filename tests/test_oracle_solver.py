@@ -204,3 +204,25 @@ def test_scaling_invariance_of_solution():
     # the constraint of eq-primal holds in original units
     m = Z.T @ res["w"] + res["beta"] * y + res["xi"] - res["r"]
     assert np.linalg.norm(m) <= 1e-8
+
+
+def test_paper_stopping_rule():
+    """Sec. 4.3's rule (stop_rule = 1, tol = 1e-5): the final residuals meet its three
+    conditions, it stops no later than the strict max-residual rule at the same tol,
+    and its point is a moderately accurate solution (certified gap of the strict
+    optimum's order of the tolerance)."""
+    rng = np.random.default_rng(61)
+    X, y, Z = _two_class(rng, 300, 60, shift=0.8)
+    q, C = 2.0, 5.0
+    pap = O.solve(Z, y, q, C, tol=1e-5, stop_rule=1, max_iter=2000)
+    strict = O.solve(Z, y, q, C, tol=1e-5, stop_rule=0, max_iter=20000)
+    assert pap["converged"] and strict["converged"]
+    eta = pap["eta"]
+    assert max(eta["P"], eta["D"]) < 1e-5
+    assert min(eta["C"], eta["gap"]) < np.sqrt(1e-5)
+    assert max(eta["C"], eta["gap"]) < 0.05
+    assert pap["iters"] <= strict["iters"]
+    ref = O.solve(Z, y, q, C, tol=1e-11, max_iter=200000)
+    assert abs(pap["primal"] - ref["primal"]) / ref["primal"] <= 0.05
+    # strict run at the tighter tolerance meets every residual
+    assert strict["eta"]["kkt"] <= 1e-5

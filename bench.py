@@ -45,6 +45,38 @@ CONFIG = {"workload": WORKLOAD, "d": 20000, "n": 1000, "q": 1.0, "C": 10.0, "tol
 LAUNCHES_PER_STEP = 14
 
 
+# sources of the iteration kernel: the DRAM traffic recorded under profiles/ is
+# used only while their hash matches the one recorded with the counters
+KERNEL_SOURCES = ["common.cuh", "solver.cuh", "passes.cuh", "nspace.cuh", "iterate.cu"]
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "iterate_kernel_spiked_fp32.md")
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2305_12019_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """dram__bytes_read.sum + dram__bytes_write.sum of one iteration-kernel launch
+    from the committed ncu summary, or None if the kernel changed since."""
+    try:
+        fields = {}
+        with open(TRAFFIC_PROFILE) as f:
+            for line in f:
+                if ":" in line and line.startswith("- "):
+                    k, v = line[2:].split(":", 1)
+                    fields[k.strip()] = v.strip().strip("`")
+        if fields.get("source_hash") != kernel_source_hash():
+            return None
+        return int(fields["traffic_bytes_per_launch"])
+    except Exception:
+        return None
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -270,12 +302,7 @@ def main():
     roof = {"kernel": "iterate_kernel<float>", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
             "bytes_per_iteration": bytes_it, "iterations": iters, "launch_ms": t_iter_ms}
-    tf = os.path.join(ROOT, "profiles", "iterate_kernel_spiked_fp32_traffic.json")
-    if os.path.exists(tf):
-        try:
-            roof["traffic"] = json.load(open(tf)).get("traffic_bytes_per_launch")
-        except Exception:
-            pass
+    roof["traffic"] = profiled_traffic()
 
     # end to end through the public API with host buffers
     e2e_ms = []

@@ -651,6 +651,7 @@ static gdwd_status solve_multi(gdwd_handle* h, const double* Cs, int K, int kker
     if (w && !w_on_device) CK(cudaStreamSynchronize(st), "sync");   // h->wtmp is reused per instance
   }
   CK(cudaStreamSynchronize(st), "sync");
+  std::memcpy(h->phase_ns, c[0].phase_ns, sizeof(h->phase_ns));
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
   cudaEventDestroy(e0);

@@ -301,9 +301,26 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_multi_kernel(MultiArgs<ty
     if (j < a.K) act |= 1u << j;
   }
 
-#define MBARRIER()                                                                        \
+  // per-phase timing by CTA 0, thread 0 (same slots as the single-instance kernel)
+  __shared__ unsigned long long s_tacc[kPhaseSlots], s_tprev;
+  const bool timing = (cta == 0 && threadIdx.x == 0);
+  if (timing) {
+    for (int k = 0; k < kPhaseSlots; ++k) s_tacc[k] = 0;
+    s_tprev = globaltimer();
+  }
+#define MMARK(k)                           \
+  do {                                     \
+    if (timing) {                          \
+      const uint64_t t_ = globaltimer();   \
+      s_tacc[k] += t_ - s_tprev;           \
+      s_tprev = t_;                        \
+    }                                      \
+  } while (0)
+#define MBARRIER(k)                                                                       \
   do {                                                                                    \
+    MMARK(k);                                                                             \
     if (!grid_barrier(a.bar, (unsigned)grid, gen, a.err, a.timeout_ns, &s_flag)) return; \
+    MMARK(k + 1);                                                                         \
   } while (0)
 
   // initial iterate: u = rho = 0, so Z~^T u = Z~^T rho = 0
@@ -355,7 +372,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_multi_kernel(MultiArgs<ty
         a.rhsA[idx] = make_float2(r1.hi, r1.lo);
       }
     }
-    MBARRIER();
+    MBARRIER(2);
 
     // ---------------- N1 and N2 share the structure: load K right-hand sides,
     // beta_j = -p^T rhs_j / s, rows of G^{-1} against all K, per-row work
@@ -417,7 +434,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_multi_kernel(MultiArgs<ty
           const df r2 = df_from(a.b[idx] + v);
           a.rhsB[idx] = make_float2(r2.hi, r2.lo);
         }
-        MBARRIER();
+        MBARRIER(4);
       } else {
         double sums[K][9];
 #pragma unroll
@@ -462,7 +479,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_multi_kernel(MultiArgs<ty
           }
         }
         block_sum_kn<K, 9>(sums, s_part, a.scal + cta, grid, 0);
-        MBARRIER();
+        MBARRIER(6);
       }
     }
 
@@ -531,7 +548,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_multi_kernel(MultiArgs<ty
       if (!stream_slabs<T>(L, rg, cta, grid, a.err, a.timeout_ns, &s_abort, pba)) return;
       block_sum_kn<K, 6>(epi.sums, s_part, a.scal + cta, grid, S_G2);
     }
-    MBARRIER();
+    MBARRIER(8);
 
     // ---------------- S: per-instance totals, KKT, sigma rule, stop test
     for (int m = warp; m < K * (S_COUNT - 1); m += kWarps) {
@@ -542,6 +559,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_multi_kernel(MultiArgs<ty
       if (lane == 0) s_tot[j][k] = acc;
     }
     __syncthreads();
+    MMARK(13);
     if (threadIdx.x < K && (act & (1u << threadIdx.x))) {
       const int j = threadIdx.x;
       const double* tt = s_tot[j];
@@ -616,6 +634,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_multi_kernel(MultiArgs<ty
       }
     }
     __syncthreads();
+    MMARK(10);
 #pragma unroll
     for (int j = 0; j < K; ++j) {
       if (!(act & (1u << j))) continue;
@@ -628,9 +647,12 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_multi_kernel(MultiArgs<ty
     }
     pending = 1;
   }
-  if (cta == 0 && threadIdx.x == 0)
+  if (cta == 0 && threadIdx.x == 0) {
     for (int j = 0; j < K; ++j) a.ctrl[j].done = 1;
+    for (int k = 0; k < kPhaseSlots; ++k) a.ctrl[0].phase_ns[k] = (double)s_tacc[k];
+  }
 #undef MBARRIER
+#undef MMARK
 }
 
 template <typename T>

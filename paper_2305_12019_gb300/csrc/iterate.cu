@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
         pb.rc[kk].reset();
         pb.ra[kk].reset();
       }
-      PassA<T> pa{up, a.partial, TB, NB, Q, H};
+      PassA2<T> pa{up, a.partial, TB, NB, Q};
       PassBA<T, IterEpi> pba{&pb, &pa};
       if (!stream_slabs<T>(L, rg, cta, grid, a.err, a.timeout_ns, &s_abort, pba)) return;
       const double vals[6] = {epi.sg2, epi.sgr, epi.sr2, epi.sa2, epi.sag, epi.sta2};

@@ -128,6 +128,69 @@ struct PassA {
   __device__ void end_slab(int, int) {}
 };
 
+// Pass A with two columns per lane per round (64 columns per round): every
+// vector of the right-hand side read from shared memory serves two Z vectors.
+template <typename T>
+struct PassA2 {
+  using CT = typename ElemTraits<T>::compute_t;
+  static constexpr int VEC = ElemTraits<T>::kVec;
+  const CT* gp;       // shared: my slabs' right-hand side (slab k at gp + k * TB)
+  CT* partial;        // global n x NB
+  int TB, NB, Q;
+
+  __device__ void chunk(const T* buf, int k, int s, int col0, int cw) {
+    const int h = threadIdx.x & 7, cl = threadIdx.x >> 3;
+    const CT* g = gp + (size_t)k * TB;
+    for (int c0 = 0; c0 < cw; c0 += 2 * (kThreads / 8)) {
+      const int ca = c0 + cl, cb = ca + kThreads / 8;
+      const bool va = ca < cw, vb = cb < cw;
+      const T* pa = buf + (size_t)(va ? ca : 0) * TB;
+      const T* pb = buf + (size_t)(vb ? cb : 0) * TB;
+      CT a0 = 0, a1 = 0, b0 = 0, b1 = 0;
+      int v = h;
+      for (; v + 8 < Q; v += 16) {
+        CT ea0[VEC], ea1[VEC], eb0[VEC], eb1[VEC], g0[VEC], g1[VEC];
+        ElemTraits<T>::load(pa + v * VEC, ea0);
+        ElemTraits<T>::load(pa + (v + 8) * VEC, ea1);
+        ElemTraits<T>::load(pb + v * VEC, eb0);
+        ElemTraits<T>::load(pb + (v + 8) * VEC, eb1);
+        load_ct<VEC>(g + v * VEC, g0);
+        load_ct<VEC>(g + (v + 8) * VEC, g1);
+#pragma unroll
+        for (int kk = 0; kk < VEC; ++kk) {
+          a0 = fma(ea0[kk], g0[kk], a0);
+          a1 = fma(ea1[kk], g1[kk], a1);
+          b0 = fma(eb0[kk], g0[kk], b0);
+          b1 = fma(eb1[kk], g1[kk], b1);
+        }
+      }
+      if (v < Q) {
+        CT ea[VEC], eb[VEC], g0[VEC];
+        ElemTraits<T>::load(pa + v * VEC, ea);
+        ElemTraits<T>::load(pb + v * VEC, eb);
+        load_ct<VEC>(g + v * VEC, g0);
+#pragma unroll
+        for (int kk = 0; kk < VEC; ++kk) {
+          a0 = fma(ea[kk], g0[kk], a0);
+          b0 = fma(eb[kk], g0[kk], b0);
+        }
+      }
+      CT xa = a0 + a1, xb = b0 + b1;
+      xa += __shfl_xor_sync(0xffffffffu, xa, 4);
+      xb += __shfl_xor_sync(0xffffffffu, xb, 4);
+      xa += __shfl_xor_sync(0xffffffffu, xa, 2);
+      xb += __shfl_xor_sync(0xffffffffu, xb, 2);
+      xa += __shfl_xor_sync(0xffffffffu, xa, 1);
+      xb += __shfl_xor_sync(0xffffffffu, xb, 1);
+      if (h == 0) {
+        if (va) partial[(size_t)(col0 + ca) * NB + s] = xa;
+        if (vb) partial[(size_t)(col0 + cb) * NB + s] = xb;
+      }
+    }
+  }
+  __device__ void end_slab(int, int) {}
+};
+
 // Running sums of pass B: FP64 storage accumulates in double, FP32 storage
 // accumulates each chunk in float and folds it into a double-float.
 template <typename CT>
@@ -175,25 +238,38 @@ struct PassB {
     for (int kk = 0; kk < VEC; ++kk) ac[kk] = aa[kk] = 0;
     const T* base = buf + qv * VEC;
     if (two) {
+      // four columns per step, two accumulator sets: the shared-memory loads of
+      // a step are issued together and the FMA chains are half as long
+      CT bc[VEC], ba[VEC];
+#pragma unroll
+      for (int kk = 0; kk < VEC; ++kk) bc[kk] = ba[kk] = 0;
       int col = grp;
-      for (; col + G < cw; col += 2 * G) {
-        CT e0[VEC], e1[VEC];
+      for (; col + 3 * G < cw; col += 4 * G) {
+        CT e0[VEC], e1[VEC], e2[VEC], e3[VEC];
         ElemTraits<T>::load(base + (size_t)col * TB, e0);
         ElemTraits<T>::load(base + (size_t)(col + G) * TB, e1);
+        ElemTraits<T>::load(base + (size_t)(col + 2 * G) * TB, e2);
+        ElemTraits<T>::load(base + (size_t)(col + 3 * G) * TB, e3);
         const CT c0 = cv[col0 + col], a0 = av[col0 + col];
         const CT c1 = cv[col0 + col + G], a1 = av[col0 + col + G];
+        const CT c2 = cv[col0 + col + 2 * G], a2 = av[col0 + col + 2 * G];
+        const CT c3 = cv[col0 + col + 3 * G], a3 = av[col0 + col + 3 * G];
 #pragma unroll
         for (int kk = 0; kk < VEC; ++kk) {
           ac[kk] = fma(e0[kk], c0, ac[kk]);
           aa[kk] = fma(e0[kk], a0, aa[kk]);
+          bc[kk] = fma(e1[kk], c1, bc[kk]);
+          ba[kk] = fma(e1[kk], a1, ba[kk]);
         }
 #pragma unroll
         for (int kk = 0; kk < VEC; ++kk) {
-          ac[kk] = fma(e1[kk], c1, ac[kk]);
-          aa[kk] = fma(e1[kk], a1, aa[kk]);
+          ac[kk] = fma(e2[kk], c2, ac[kk]);
+          aa[kk] = fma(e2[kk], a2, aa[kk]);
+          bc[kk] = fma(e3[kk], c3, bc[kk]);
+          ba[kk] = fma(e3[kk], a3, ba[kk]);
         }
       }
-      if (col < cw) {
+      for (; col < cw; col += G) {
         CT e[VEC];
         ElemTraits<T>::load(base + (size_t)col * TB, e);
         const CT c = cv[col0 + col], a = av[col0 + col];
@@ -202,6 +278,11 @@ struct PassB {
           ac[kk] = fma(e[kk], c, ac[kk]);
           aa[kk] = fma(e[kk], a, aa[kk]);
         }
+      }
+#pragma unroll
+      for (int kk = 0; kk < VEC; ++kk) {
+        ac[kk] += bc[kk];
+        aa[kk] += ba[kk];
       }
     } else {
       for (int col = grp; col < cw; col += G) {
@@ -249,7 +330,7 @@ struct PassB {
 template <typename T, typename Epi>
 struct PassBA {
   PassB<T, Epi>* b;
-  PassA<T>* a;
+  PassA2<T>* a;
   __device__ void chunk(const T* buf, int k, int s, int col0, int cw) {
     b->chunk(buf, k, s, col0, cw);
     a->chunk(buf, k, s, col0, cw);

@@ -182,6 +182,34 @@ gdwd_status gdwd_apply(gdwd_handle* h, int32_t trans, const double* x, double* o
  */
 gdwd_status gdwd_gram(gdwd_handle* h, double* G_out);
 
+/*
+ * Weighted DWD (Sec. 4.5): the r-term of eq-primal becomes sum_i wt_i^q / r_i^q
+ * and the penalty C <e, xi>.  e and wt are host arrays of n positive finite
+ * doubles (copied; NULL = all ones, the default after gdwd_create).  They hold
+ * for every later gdwd_solve of h (and of its FP32 master copy when refine = 1).
+ * Errors: EINVAL (NULL handle, a non-positive or non-finite entry), ECUDA.
+ */
+gdwd_status gdwd_set_weights(gdwd_handle* h, const double* e, const double* wt);
+
+/*
+ * The class-balancing weights of Sec. 4.5: with n_+ and n_- the class sizes,
+ * K = n / log(n) and tau_+- = (n_+- / K)^(1/(1+q)), wt_i = tau_- / max(tau_+, tau_-)
+ * for y_i = +1 and tau_+ / max(tau_+, tau_-) for y_i = -1.  Host-only: y (n
+ * labels +-1) and wt (n doubles, written) are host arrays.
+ * Errors: EINVAL (n < 2, q <= 0, a label not +-1, a class empty).
+ */
+gdwd_status gdwd_imbalance_weights(const double* y, int64_t n, double q, double* wt);
+
+/*
+ * The penalty parameter of Sec. 4.1 for the handle's data:
+ * C = 10^(q+1) max{1, 10^(q-1) log(n) max(1000, d)^(1/3) / dist^(q+1)}, with dist
+ * the median of the Euclidean distances ||x_i - x_j|| over pairs of opposite
+ * labels (the mean of the two middle ones for an even count), taken from the
+ * Gram matrix of the stored data (for BF16 / FP16 / E4M3 storage: of the
+ * quantized data).  Writes *C_out (host).  Errors: EINVAL, ECUDA, ENOMEM.
+ */
+gdwd_status gdwd_suggest_C(gdwd_handle* h, double* C_out);
+
 /* Sizes and layout chosen by gdwd_create (for diagnostics and benchmarks). */
 typedef struct {
   int64_t d, n;
@@ -206,13 +234,15 @@ gdwd_status gdwd_get_info(const gdwd_handle* h, gdwd_info* info);
  * Device-side time of the last solve of h split by phase of the persistent
  * iteration kernel, as seen by its first CTA (globaltimer, nanoseconds summed
  * over iterations): ns[2k] = time in phase k, ns[2k+1] = the grid-barrier wait
- * that follows it, for k = A (Z^T g' stream), R (reduction), N1 (first n-space
- * solve and Step 1b), N2 (second solve, Steps 2-3), B (Z c stream); ns[10] =
- * the KKT / sigma phase; sub-phases split out of those: ns[11] N2 right-hand
- * side load and beta, ns[12] N2 rows of G^{-1}, ns[13] reduction of the
- * per-CTA partial sums, ns[14] N1 right-hand side load and beta-bar, ns[15] N1
- * rows of G^{-1}.  count (<= 16) entries are written to ns (host).
- * Diagnostics only; the paper has no counterpart.  Errors: EINVAL.
+ * that follows it, for k = 0 (the two start-up passes over Z of a warm start),
+ * 1 (R: U_g, b, rhs1), 2 (N1: first n-space solve and Step 1b), 3 (N2: second
+ * solve, Steps 2-3), 4 (B: the pass over Z); ns[10] = the KKT / sigma phase;
+ * sub-phases split out of those: ns[11] N2 right-hand side load and beta,
+ * ns[12] N2 rows of G^{-1}, ns[13] reduction of the per-CTA partial sums,
+ * ns[14] N1 right-hand side load and beta-bar, ns[15] N1 rows of G^{-1}
+ * (the joint C-grid kernel fills ns[2..10] and ns[13]).  count (<= 16)
+ * entries are written to ns (host).  Diagnostics only; the paper has no
+ * counterpart.  Errors: EINVAL.
  */
 gdwd_status gdwd_get_phase_times(const gdwd_handle* h, double* ns, int32_t count);
 

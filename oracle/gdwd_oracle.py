@@ -330,6 +330,38 @@ def sigma_update(sigma, eta_p, eta_d, theta=5.0):
 
 
 # --------------------------------------------------------------------------
+# weights and the penalty heuristic (Sec. 4.5, Sec. 4.1)
+# --------------------------------------------------------------------------
+
+def imbalance_weights(y, q):
+    """Sec. 4.5 class-balancing weights: tau_+- = (n_+- / K)^(1/(1+q)) with
+    K = n / log(n); tau_i = tau_- / max(tau_+, tau_-) if y_i = +1, tau_+ / max(...) if -1."""
+    y = np.asarray(y, dtype=np.float64)
+    n = y.size
+    n_pos = float(np.sum(y > 0))
+    n_neg = float(n - n_pos)
+    K = n / math.log(n)
+    tau_pos = (n_pos / K) ** (1.0 / (1.0 + q))
+    tau_neg = (n_neg / K) ** (1.0 / (1.0 + q))
+    top = max(tau_pos, tau_neg)
+    return np.where(y > 0, tau_neg / top, tau_pos / top)
+
+
+def suggest_C(Z, y, q):
+    """Sec. 4.1: C = 10^(q+1) max{1, 10^(q-1) log(n) max{1000, d}^(1/3) / dist^(q+1)},
+    dist = median Euclidean distance between points of opposite classes (x_i = y_i z_i)."""
+    Z = np.asarray(Z, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    d, n = Z.shape
+    X = Z * y[None, :]
+    P, M = X[:, y > 0], X[:, y < 0]
+    dists = [np.linalg.norm(P[:, i] - M[:, j]) for i in range(P.shape[1]) for j in range(M.shape[1])]
+    dist = float(np.median(dists))
+    t = 10.0 ** (q - 1.0) * math.log(n) * max(1000.0, float(d)) ** (1.0 / 3.0) / dist ** (q + 1.0)
+    return 10.0 ** (q + 1.0) * max(1.0, t)
+
+
+# --------------------------------------------------------------------------
 # Algorithm 1
 # --------------------------------------------------------------------------
 

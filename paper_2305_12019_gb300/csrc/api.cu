@@ -774,6 +774,114 @@ extern "C" gdwd_status gdwd_gram(gdwd_handle* h, double* G_out) {
   return GDWD_OK;
 }
 
+// ---------------------------------------------------------------- weights and C
+// omega_i = q wt_i^q (the prox constant of the weighted r-term)
+__global__ void omega_kernel(const double* wt, double q, int64_t n, double* omega) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    omega[i] = q * pow(wt[i], q);
+}
+
+static gdwd_status set_weights_one(gdwd_handle* h, const double* e, const double* wt) {
+  const int64_t n = h->n;
+  const int fb = (int)std::min<int64_t>((n + 255) / 256, 1024);
+  if (e) CK(cudaMemcpyAsync(h->e, e, n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "copy e");
+  else fill_kernel<<<fb, 256, 0, h->stream>>>(h->e, n, 1.0);
+  if (wt) CK(cudaMemcpyAsync(h->wt, wt, n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "copy wt");
+  else fill_kernel<<<fb, 256, 0, h->stream>>>(h->wt, n, 1.0);
+  omega_kernel<<<fb, 256, 0, h->stream>>>(h->wt, h->q, n, h->omega);
+  CK(cudaGetLastError(), "omega");
+  CK(cudaStreamSynchronize(h->stream), "sync");
+  return GDWD_OK;
+}
+
+extern "C" gdwd_status gdwd_set_weights(gdwd_handle* h, const double* e, const double* wt) {
+  if (!h) return fail(nullptr, GDWD_EINVAL, "gdwd_set_weights: NULL handle");
+  for (int64_t i = 0; i < h->n; ++i) {
+    if (e && !(e[i] > 0.0 && std::isfinite(e[i])))
+      return fail(h, GDWD_EINVAL, "gdwd_set_weights: e must be positive and finite");
+    if (wt && !(wt[i] > 0.0 && std::isfinite(wt[i])))
+      return fail(h, GDWD_EINVAL, "gdwd_set_weights: wt must be positive and finite");
+  }
+  gdwd_status st = set_weights_one(h, e, wt);
+  if (st == GDWD_OK && h->master) st = set_weights_one(h->master, e, wt);
+  return st;
+}
+
+extern "C" gdwd_status gdwd_imbalance_weights(const double* y, int64_t n, double q, double* wt) {
+  if (!y || !wt || n < 2 || !(q > 0.0)) return fail(nullptr, GDWD_EINVAL, "gdwd_imbalance_weights: bad argument");
+  int64_t np = 0, nm = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (y[i] == 1.0) ++np;
+    else if (y[i] == -1.0) ++nm;
+    else return fail(nullptr, GDWD_EINVAL, "gdwd_imbalance_weights: labels must be -1 or +1");
+  }
+  if (!np || !nm) return fail(nullptr, GDWD_EINVAL, "gdwd_imbalance_weights: both classes must occur");
+  const double K = (double)n / std::log((double)n);
+  const double tp = std::pow((double)np / K, 1.0 / (1.0 + q)), tm = std::pow((double)nm / K, 1.0 / (1.0 + q));
+  const double mx = std::max(tp, tm);
+  for (int64_t i = 0; i < n; ++i) wt[i] = (y[i] == 1.0 ? tm : tp) / mx;
+  return GDWD_OK;
+}
+
+// ||x_i - x_j|| for every pair i in the +1 class, j in the -1 class, from the Gram of
+// Z~: with x_i = y_i z_i, x_i - x_j = z_i + z_j, so the squared distance is
+// K_ii + K_jj + 2 K_ij, K = mu Z_scale^2 (G - I).
+__global__ void pair_dist_kernel(const double* G, int64_t n, const int* pos, int64_t np, const int* neg, int64_t nm,
+                                 double kscale, double* out) {
+  const int64_t total = np * nm;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = pos[idx / nm], j = neg[idx % nm];
+    const double kii = G[i * n + i] - 1.0, kjj = G[j * n + j] - 1.0, kij = G[i * n + j];
+    out[idx] = sqrt(fmax(0.0, kscale * (kii + kjj + 2.0 * kij)));
+  }
+}
+
+extern "C" gdwd_status gdwd_suggest_C(gdwd_handle* h, double* C_out) {
+  if (!h || !C_out) return fail(h, GDWD_EINVAL, "gdwd_suggest_C: NULL argument");
+  const int64_t n = h->n;
+  std::vector<double> y(n);
+  CK(cudaMemcpyAsync(y.data(), h->y, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy y");
+  CK(cudaStreamSynchronize(h->stream), "sync");
+  std::vector<int> pos, neg;
+  for (int64_t i = 0; i < n; ++i) (y[i] > 0 ? pos : neg).push_back((int)i);
+  const int64_t np = (int64_t)pos.size(), nm = (int64_t)neg.size(), total = np * nm;
+  int *dpos = nullptr, *dneg = nullptr;
+  double* dd = nullptr;
+  std::vector<double> dist(total);
+  auto cleanup = [&]() {
+    if (dpos) cudaFreeAsync(dpos, h->stream);
+    if (dneg) cudaFreeAsync(dneg, h->stream);
+    if (dd) cudaFreeAsync(dd, h->stream);
+  };
+  cudaError_t e = cudaMallocAsync(&dpos, np * sizeof(int), h->stream);
+  if (e == cudaSuccess) e = cudaMallocAsync(&dneg, nm * sizeof(int), h->stream);
+  if (e == cudaSuccess) e = cudaMallocAsync(&dd, total * sizeof(double), h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dpos, pos.data(), np * sizeof(int), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dneg, neg.data(), nm * sizeof(int), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) {
+    const double kscale = h->opt.mu * h->zscale * h->zscale;
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
+    pair_dist_kernel<<<blocks, 256, 0, h->stream>>>(h->G, n, dpos, np, dneg, nm, kscale, dd);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dist.data(), dd, total * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cleanup();
+  if (e != cudaSuccess) return cuda_fail(h, e, "gdwd_suggest_C");
+  // median of the between-class distances (mean of the two middle ones for an even count)
+  const int64_t mid = total / 2;
+  std::nth_element(dist.begin(), dist.begin() + mid, dist.end());
+  double med = dist[mid];
+  if (total % 2 == 0) med = 0.5 * (med + *std::max_element(dist.begin(), dist.begin() + mid));
+  // C = 10^(q+1) max{1, 10^(q-1) log(n) max(1000, d)^(1/3) / dist^(q+1)}  (Sec. 4.1)
+  const double q = h->q;
+  const double t = std::pow(10.0, q - 1.0) * std::log((double)n) * std::cbrt(std::max(1000.0, (double)h->d)) /
+                   std::pow(med, q + 1.0);
+  *C_out = std::pow(10.0, q + 1.0) * std::max(1.0, t);
+  return GDWD_OK;
+}
+
 extern "C" gdwd_status gdwd_get_info(const gdwd_handle* h, gdwd_info* info) {
   if (!h || !info) return fail(nullptr, GDWD_EINVAL, "gdwd_get_info: NULL argument");
   std::memset(info, 0, sizeof(*info));

@@ -63,8 +63,8 @@ struct PassAK {
 
   __device__ void chunk(const T* buf, int k, int s, int col0, int cw) {
     const int h = threadIdx.x & 7, cl = threadIdx.x >> 3;
-    for (int c0 = 0; c0 < cw; c0 += 64) {
-      const int ca = c0 + cl, cb = c0 + cl + 32;
+    for (int c0 = 0; c0 < cw; c0 += 2 * (kThreads / 8)) {
+      const int ca = c0 + cl, cb = ca + kThreads / 8;
       const bool va = ca < cw, vb = cb < cw;
       CT acc[2][K];
 #pragma unroll

@@ -58,10 +58,11 @@ class Request(ctypes.Structure):
 
 EXPORTS = ["gdwd_default_options", "gdwd_create", "gdwd_solve", "gdwd_free", "gdwd_last_error", "gdwd_prox",
            "gdwd_apply", "gdwd_gram", "gdwd_get_info", "gdwd_get_phase_times", "gdwd_get_stored",
-           "gdwd_server_create", "gdwd_server_submit", "gdwd_server_poll", "gdwd_server_destroy", "gdwd_solve_batch"]
+           "gdwd_server_create", "gdwd_server_submit", "gdwd_server_poll", "gdwd_server_destroy", "gdwd_solve_batch",
+           "gdwd_set_weights", "gdwd_imbalance_weights", "gdwd_suggest_C"]
 EAGAIN = 9
 STORE_NP = {F64: "float64", F32: "float32", BF16: "uint16", F16: "float16", E4M3: "uint8"}
-PHASES = ["A", "A_wait", "R", "R_wait", "N1_rows", "N1_wait", "N2_rows", "N2_wait", "B", "B_wait", "S_kkt",
+PHASES = ["warm_passes", "warm_passes_wait", "R", "R_wait", "N1_rows", "N1_wait", "N2_rows", "N2_wait", "B", "B_wait", "S_kkt",
           "N2_rhs", "N2_gemv", "S_sums", "N1_rhs", "N1_gemv"]
 
 _lib = None
@@ -101,6 +102,9 @@ def load(path: str = LIB_PATH):
     lib.gdwd_solve_batch.argtypes = [POINTER(Request), c_int32, c_int32, POINTER(Result), POINTER(c_double)]
     lib.gdwd_gram_noalloc.argtypes = [c_void_p, c_int64, c_int64, c_int64, c_void_p, c_void_p]
     lib.gdwd_gram_noalloc.restype = c_int32
+    lib.gdwd_set_weights.argtypes = [c_void_p, c_void_p, c_void_p]
+    lib.gdwd_imbalance_weights.argtypes = [c_void_p, c_int64, c_double, c_void_p]
+    lib.gdwd_suggest_C.argtypes = [c_void_p, POINTER(c_double)]
     for name in EXPORTS:
         if name != "gdwd_last_error":
             getattr(lib, name).restype = c_int32
@@ -219,6 +223,22 @@ class Solver:
         _check(_lib.gdwd_get_stored(self._h, c_void_p(Zq.ctypes.data), c_void_p(cs.ctypes.data)), self._h)
         return Zq.T, cs
 
+    def set_weights(self, e=None, wt=None):
+        """Weighted DWD (gdwd_set_weights): penalty weights e, r-term weights wt (n each)."""
+        ev = None if e is None else np.ascontiguousarray(np.asarray(e, dtype=np.float64))
+        wv = None if wt is None else np.ascontiguousarray(np.asarray(wt, dtype=np.float64))
+        for v in (ev, wv):
+            if v is not None and v.shape != (self.n,):
+                raise ValueError("weights must have n entries")
+        _check(_lib.gdwd_set_weights(self._h, None if ev is None else ev.ctypes.data,
+                                     None if wv is None else wv.ctypes.data), self._h)
+
+    def suggest_C(self):
+        """The penalty parameter heuristic of Sec. 4.1 for the handle's data (gdwd_suggest_C)."""
+        c = c_double()
+        _check(_lib.gdwd_suggest_C(self._h, ctypes.byref(c)), self._h)
+        return c.value
+
     def phase_times(self):
         """Per-phase device time (ns) of the last solve, CTA 0's view (gdwd_get_phase_times)."""
         buf = (c_double * 16)()
@@ -331,6 +351,15 @@ def solve_batch(requests, slots=4):
     lat = (c_double * k)()
     st = lib.gdwd_solve_batch(arr, k, int(slots), res, lat)
     return [r.as_dict() for r in res], list(lat), st
+
+
+def imbalance_weights(y, q):
+    """Class-balancing r-term weights of Sec. 4.5 (gdwd_imbalance_weights)."""
+    lib = load()
+    yv = np.ascontiguousarray(np.asarray(y, dtype=np.float64))
+    wt = np.zeros(yv.size)
+    _check(lib.gdwd_imbalance_weights(yv.ctypes.data, yv.size, float(q), wt.ctypes.data), None)
+    return wt
 
 
 def gram_noalloc(Z, K, stream=None):

@@ -279,3 +279,23 @@ def test_paper_stopping_rule(gdwd_lib):
     assert r["iters"] <= rs[0]["iters"]
     ref = O.solve(inst.Z.astype(np.float64), inst.y, 1.0, 1.0, tol=1e-9)
     assert abs(r["primal_obj"] - ref["primal"]) / ref["primal"] <= 0.05
+
+
+def test_weighted_solve_and_suggest_C(gdwd_lib):
+    """Weighted DWD (Sec. 4.5: class-balancing wt and per-sample e) against the
+    oracle, and the Sec. 4.1 penalty heuristic against the oracle's direct
+    median of between-class distances."""
+    inst = synth.gaussian(seed=81, d=3000, n=180, shift=1.0, n_pos=45, q=2.0, C=1.0, dtype=np.float64)
+    Z, y = inst.Z, inst.y
+    wt = gdwd_lib.imbalance_weights(y, 2.0)
+    assert np.allclose(wt, O.imbalance_weights(y, 2.0), rtol=1e-14)
+    e = 0.5 + 0.5 * np.random.default_rng(3).random(Z.shape[1])
+    with gdwd_lib.Solver(Z, y, 2.0, 3.0, store="f64", tol=1e-8) as s:
+        s.set_weights(e=e, wt=wt)
+        res, w, alpha = s.solve(alpha=True)
+        Cs = s.suggest_C()
+    r = res[0]
+    assert r["status"] == 0, r
+    ref = O.solve(Z, y, 2.0, 3.0, tol=1e-10, e=e, wt=wt)
+    _compare(r, w[:, 0], ref)
+    assert abs(Cs - O.suggest_C(Z, y, 2.0)) / O.suggest_C(Z, y, 2.0) <= 1e-9

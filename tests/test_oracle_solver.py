@@ -226,3 +226,26 @@ def test_paper_stopping_rule():
     assert abs(pap["primal"] - ref["primal"]) / ref["primal"] <= 0.05
     # strict run at the tighter tolerance meets every residual
     assert strict["eta"]["kkt"] <= 1e-5
+
+
+def test_imbalance_weights_closed_form():
+    """Sec. 4.5: K cancels in the ratio, so the minority class gets weight 1 and the
+    majority class (n_min / n_maj)^(1/(1+q)); balanced classes give all ones."""
+    y = np.array([1.0] * 3 + [-1.0] * 7)
+    w = O.imbalance_weights(y, 1.0)
+    assert np.allclose(w[:3], 1.0) and np.allclose(w[3:], 0.6546536707079771)      # sqrt(3/7)
+    w2 = O.imbalance_weights(y, 2.0)
+    assert np.allclose(w2[3:], 0.7539474411291538)                                  # (3/7)^(1/3)
+    assert np.allclose(O.imbalance_weights(np.array([1.0, -1.0] * 5), 4.0), 1.0)
+
+
+def test_suggest_C_hand_example():
+    """Sec. 4.1 on four 1-D points: x_+ = {0, 1}, x_- = {3, 5}; between-class
+    distances {3, 5, 2, 4}, median 3.5; n = 4, d = 1 (max{1000, d} = 1000)."""
+    x = np.array([[0.0, 1.0, 3.0, 5.0]])
+    y = np.array([1.0, 1.0, -1.0, -1.0])
+    Z = x * y
+    # q = 1: 10^2 max{1, log(4) * 10 / 3.5^2} = 100 * 1.131668...
+    assert abs(O.suggest_C(Z, y, 1.0) - 113.1668866220319) <= 1e-9
+    # q = 2: 10^3 max{1, 10 log(4) * 10 / 3.5^3} = 1000 * 3.233339...
+    assert abs(O.suggest_C(Z, y, 2.0) - 3233.33961777234) <= 1e-7

@@ -210,6 +210,7 @@ def main():
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-wall", type=float, default=300.0, help="served: stop admitting after this many seconds")
     ap.add_argument("--cg-d", type=int, default=50000)
     ap.add_argument("--cg-n", type=int, default=2000)
     ap.add_argument("--big-d", type=int, default=200000)

@@ -117,13 +117,16 @@ def uneven_batch(args, gdwd, synth):
             "config": {"workload": f"uneven_batch {len(reqs)} instances d 5k-50k n 200-2000 q in 0.5,1,2,4",
                        "store": "bf16", "slots": args.slots},
             "status": int(st), "converged": int(sum(r["status"] == 0 for r in res)),
+            "not_converged": [{"k": k, "d": shapes[k]["d"], "n": shapes[k]["n"], "q": shapes[k]["q"], "iters": r["iters"],
+                               "kkt": r["kkt"], "status": r["status"]} for k, r in enumerate(res) if r["status"] != 0],
             "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
             "certified_gap_original_data_every_8th": gaps}
 
 
 def served(args, gdwd, synth):
     """Poisson arrivals; each request's data is drawn on the device from its seed
-    when the client hands it to the server.  The client keeps at most
+    when the client hands it to the server.  Requests still waiting after
+    --serve-wall seconds are not served (counted in the line).  The client keeps at most
     2 x slots requests generated-but-unfinished (the rest wait as seeds), so
     device memory holds only what is in flight; latency runs from the arrival
     time to the moment the client sees the result."""
@@ -147,7 +150,8 @@ def served(args, gdwd, synth):
     dn_done = 0.0
     t_start = time.perf_counter()
     nxt = 0
-    while nxt < len(specs) or pending:
+    wall_limit = args.serve_wall
+    while (nxt < len(specs) and time.perf_counter() - t_start < wall_limit) or pending:
         for t in list(pending):
             out = srv.poll(t, wait=False)
             if out is not None:
@@ -159,7 +163,7 @@ def served(args, gdwd, synth):
                 iters.append(res["iters"])
                 dn_done += specs[k][0] * specs[k][1]
         now = time.perf_counter() - t_start
-        if nxt < len(specs) and len(pending) < max_out and arrivals[nxt] <= now:
+        if nxt < len(specs) and now < wall_limit and len(pending) < max_out and arrivals[nxt] <= now:
             d, n, q, C, seed = specs[nxt]
             with torch.cuda.stream(gen_stream):
                 g = torch.Generator(device="cuda")
@@ -190,7 +194,8 @@ def served(args, gdwd, synth):
             "latency_ms_p99": float(np.percentile(lat_e2e, 99)),
             "server_latency_ms_p50": float(np.percentile(lat_srv, 50)),
             "server_latency_ms_p99": float(np.percentile(lat_srv, 99)),
-            "requests": len(stats), "converged": ok, "wall_s": t_total,
+            "requests": len(stats), "arrived": int(arrivals.size), "not_served_by_wall_limit": int(arrivals.size - nxt),
+            "converged": ok, "wall_s": t_total, "wall_limit_s": wall_limit,
             "offered_rate": lam, "mean_iters": float(np.mean(iters)),
             "z_bytes_per_iteration_mean_fp16": 2.0 * dn_done / max(1, len(stats)),
             "config": {"workload": f"served Poisson {lam}/s for {T} s, d 1k-100k, n 50-5000, q in 1,2, C 0.1-100",

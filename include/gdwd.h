@@ -88,7 +88,14 @@ typedef struct {
                          <= tol; 1: the rule of Sec. 4.3: max(eta_P, eta_D) < tol,
                          min(eta_C, eta_gap) < sqrt(tol) and max(eta_C, eta_gap) < 0.05
                          (the paper uses tol = 1e-5 with max_iter = 2000).          */
-  int64_t reserved[6];
+  int32_t dots_every; /* b = Z~^T g' is carried in n-space from Z~^T u, Z~^T rho and
+                         (G - I) c; every dots_every-th iteration Z~^T u is taken
+                         directly from the pass over Z, bounding the number of
+                         iterations over which the Gram's rounding can accumulate.
+                         0 (default): 16 for FP64 / FP32 storage, 4 for BF16 / FP16 /
+                         E4M3 storage (tensor-core Gram); 1: every iteration.     */
+  int32_t reserved_i32;
+  int64_t reserved[5];
 } gdwd_options;
 
 /* Outcome of one solve (one value of C). */
@@ -237,9 +244,9 @@ gdwd_status gdwd_get_info(const gdwd_handle* h, gdwd_info* info);
  * that follows it, for k = 0 (the two start-up passes over Z of a warm start),
  * 1 (R: U_g, b, rhs1), 2 (N1: first n-space solve and Step 1b), 3 (N2: second
  * solve, Steps 2-3), 4 (B: the pass over Z); ns[10] = the KKT / sigma phase;
- * sub-phases split out of those: ns[11] N2 right-hand side load and beta,
- * ns[12] N2 rows of G^{-1}, ns[13] reduction of the per-CTA partial sums,
- * ns[14] N1 right-hand side load and beta-bar, ns[15] N1 rows of G^{-1}
+ * sub-phases split out of those: ns[11] N2 right-hand side load, ns[12] N2
+ * rows of G^{-1} and p^T rhs (beta), ns[13] reduction of the per-CTA partial
+ * sums, ns[14] N1 right-hand side load, ns[15] N1 rows of G^{-1} and p^T rhs
  * (the joint C-grid kernel fills ns[2..10] and ns[13]).  count (<= 16)
  * entries are written to ns (host).  Diagnostics only; the paper has no
  * counterpart.  Errors: EINVAL.

@@ -68,7 +68,7 @@ struct gdwd_handle {
   // state of the joint C-grid kernel (up to 4 instances), allocated on first use
   struct {
     bool ready = false;
-    double *r, *xi, *alpha, *b, *u, *rho, *g, *scal, *Ur, *kc;
+    double *r, *xi, *alpha, *b, *u, *rho, *g, *scal, *Uu, *Ur, *kc;
     float2 *rhsA, *rhsB;
     void *cq, *aq, *partial;
     Ctrl* ctrl;
@@ -191,6 +191,7 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
   if (opt.store < GDWD_F64 || opt.store > GDWD_E4M3) return fail(nullptr, GDWD_EINVAL, "gdwd_create: bad store dtype");
   if (opt.gram_path != 0 && opt.gram_path != 1) return fail(nullptr, GDWD_EINVAL, "gdwd_create: gram_path must be 0 or 1");
   if (opt.stop_rule != 0 && opt.stop_rule != 1) return fail(nullptr, GDWD_EINVAL, "gdwd_create: stop_rule must be 0 or 1");
+  if (opt.dots_every < 0) return fail(nullptr, GDWD_EINVAL, "gdwd_create: dots_every must be >= 0");
 
   gdwd_handle* h = new gdwd_handle();
   h->opt = opt;
@@ -259,7 +260,8 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
     CK(halloc(h, &h->p, n), "alloc");
     CK(halloc(h, &h->G, (size_t)n * n), "alloc(G)");
     CK(halloc(h, &h->P, (size_t)n * h->ldP), "alloc(P)");
-    CK(halloc(h, &h->pdf, n), "alloc");
+    CK(halloc(h, &h->pdf, h->ldP), "alloc");   // padded to ldP (a zero pair for odd n): read as a G^{-1} row
+    CK(cudaMemsetAsync(h->pdf, 0, (size_t)h->ldP * sizeof(float2), h->stream), "memset");
     CK(halloc(h, &h->r, n), "alloc");
     CK(halloc(h, &h->xi, n), "alloc");
     CK(halloc(h, &h->alpha, n), "alloc");
@@ -386,6 +388,13 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
   return GDWD_OK;
 }
 
+// iterations between direct Z~^T u column dots (0 = by storage: the Gram of
+// FP64 / FP32 storage is within a few 1e-8, the tensor-core Gram within 5e-7)
+static int dots_every_of(const gdwd_handle* h) {
+  if (h->opt.dots_every > 0) return h->opt.dots_every;
+  return (h->store == GDWD_F64 || h->store == GDWD_F32) ? 16 : 4;
+}
+
 template <typename CT>
 static IterArgs<CT> make_args(gdwd_handle* h, double C, double sigma0, int refresh) {
   IterArgs<CT> a{};
@@ -420,6 +429,7 @@ static IterArgs<CT> make_args(gdwd_handle* h, double C, double sigma0, int refre
   a.Ur = h->Ur;
   a.kc = h->kc;
   a.refresh = refresh;
+  a.dots_every = dots_every_of(h);
   a.rhsB = h->rhsB;
   a.cq = (CT*)h->cq;
   a.aq = (CT*)h->aq;
@@ -538,6 +548,7 @@ static gdwd_status solve_multi(gdwd_handle* h, const double* Cs, int K, int kker
     CK(halloc(h, &m.b, 4 * n), "alloc");
     CK(halloc(h, &m.rhsA, 4 * n), "alloc");
     CK(halloc(h, &m.rhsB, 4 * n), "alloc");
+    CK(halloc(h, &m.Uu, 4 * n), "alloc");
     CK(halloc(h, &m.Ur, 4 * n), "alloc");
     CK(halloc(h, &m.kc, 4 * n), "alloc");
     CK(halloc(h, (uint8_t**)&m.cq, 4 * n * ct), "alloc");
@@ -603,8 +614,10 @@ static gdwd_status solve_multi(gdwd_handle* h, const double* Cs, int K, int kker
     a.b = m.b;
     a.rhsA = m.rhsA;
     a.rhsB = m.rhsB;
+    a.Uu = m.Uu;
     a.Ur = m.Ur;
     a.kc = m.kc;
+    a.dots_every = dots_every_of(h);
     a.u = m.u;
     a.rho = m.rho;
     a.g = m.g;

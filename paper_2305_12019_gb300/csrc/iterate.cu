@@ -18,11 +18,12 @@
 // update of U_u, U_rho, and since g = u - Z~ c / mu,
 //     U_g = Z~^T u - Z~^T Z~ c / mu = Z~^T u - (G - I) c,
 //     (G - I) c = (G - I)(x + beta p) = rhs2 - x + beta (y - p)
-// (G x = rhs2 and G p = y).  Z~^T u is taken directly, as column dots on the
-// chunks pass B streams anyway (u is known before the pass starts), so the
-// Gram's rounding enters U_g once per iteration, as it enters the n-space
-// Z~^T w, and does not accumulate; U_rho follows its recurrence, which contracts
-// by |1 - tau| < 1.  One iteration therefore reads Z ONCE:
+// (G x = rhs2 and G p = y).  U_u follows u+ = theta g; every dots_every-th
+// iteration Z~^T u is taken directly instead, as column dots on the chunks
+// pass B streams anyway (u is known before the pass starts), so the Gram's
+// rounding in (G - I) c accumulates over at most dots_every iterations; U_rho
+// follows its recurrence, which contracts by |1 - tau| < 1.  One iteration
+// therefore reads Z ONCE:
 //
 //   prologue             warm start: U_u, U_rho by two passes over Z (after the
 //                        deferred update handed over); initial iterate: zero
@@ -33,7 +34,8 @@
 //   phase N2             x = G^{-1} rhs2, beta, c, Z~^T w; Step 2 xi and
 //                        Step 3 alpha (n part); (G - I) c; n-space KKT sums
 //   phase B  (Z pass)    deferred d-update of u, rho; t = Z~ c, ta = Z~ alpha;
-//                        g = u - t / mu; d-space sums; column dots Z~^T u
+//                        g = u - t / mu; d-space sums; (periodically) the
+//                        column dots Z~^T u
 //   phase S              all sums -> KKT residuals (Sec. 4.3), duality gap,
 //                        sigma rule (Sec. 4.4), stop test; identical in every CTA
 #include <algorithm>
@@ -131,12 +133,13 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
   const int64_t rpc = (n + grid - 1) / grid;
   const int64_t r0 = ((int64_t)cta * rpc < n) ? (int64_t)cta * rpc : n;
   const int nrows = (int)(((r0 + rpc < n) ? r0 + rpc : n) - r0);
-  __shared__ float s_xh[kMaxRowsPerCta], s_xl[kMaxRowsPerCta];
+  __shared__ float s_xh[kMaxRowsPerCta + 1], s_xl[kMaxRowsPerCta + 1];   // + the p^T rhs row
   const int qcase = q_case(a.q);
   const double sqmu = sqrt(a.mu), inv_mu = 1.0 / a.mu;
   const double den = 1.0 + a.C;
   const double inv_q = 1.0 / a.q;
   const float inv_den = (float)(1.0 / den);
+  const double sqrt_tol = sqrt(a.tol);
 
   Ring rg;
   rg.buf = smem;
@@ -178,7 +181,6 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
 
   const int npair = (int)((n + 1) / 2);
   float2* rhs_s = reinterpret_cast<float2*>(uni);
-  float* s_redf = reinterpret_cast<float*>(s_red);
 
   // ---------------- prologue: U_u = Z~^T u and U_rho = Z~^T rho of the starting
   // iterate for this CTA's rows.  A warm start computes them with two passes over
@@ -225,6 +227,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
   __syncthreads();
 
   int it = it0;
+  bool dots_prev = false;   // the last pass B took the column dots Z~^T u
   for (; it < a.max_iter; ++it) {
     const double inv_sig = rcp_nr(sig);
     // ---------------- phase R (this CTA's rows): U_g = Z~^T g of the last iteration
@@ -237,12 +240,14 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
       for (int t = warp; t < nrows; t += kWarps) {
         const int64_t i = r0 + t;
         double ug = 0.0;
-        if (pending) ug = a.sc[i] * reduce_partials<CT>(a.partial + (size_t)i * NB, NB, lane) - a.kc[i];
+        if (pending && dots_prev) ug = a.sc[i] * reduce_partials<CT>(a.partial + (size_t)i * NB, NB, lane);
         if (lane == 0) {
           double uu = a.Uu[i], ur = a.Ur[i];
           if (pending) {
+            ug = (dots_prev ? ug : uu) - a.kc[i];
             uu = theta * ug;
             ur = (1.0 - a.tau) * ur - rcoef * ug;
+            a.Uu[i] = uu;
             a.Ur[i] = ur;
           }
           const double bi = uu + ur * gsc;
@@ -259,23 +264,19 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
     {
       for (int64_t i = threadIdx.x; i < 2 * npair; i += kThreads) rhs_s[i] = i < n ? a.rhsA[i] : make_float2(0.f, 0.f);
       __syncthreads();
-      df pd{0.f, 0.f};
-      for (int64_t i = threadIdx.x; i < n; i += kThreads) {
-        const float2 pv = a.pdf[i];
-        df_fma(pd, df{pv.x, pv.y}, df{rhs_s[i].x, rhs_s[i].y});
-      }
-      const double betabar = -df_to_double(block_sum_df(pd, s_redf)) * a.inv_s;
       GDWD_MARK(14);
-      // G^{-1} rows of this CTA (one warp per row), then the per-row FP64 work with
-      // one row per lane so each FP64 instruction serves up to 32 rows
-      for (int t = warp; t < nrows; t += kWarps) {
-        const df x = row_dot(a.P + (size_t)(r0 + t) * a.ldP, rhs_s, npair);
+      // G^{-1} rows of this CTA and, as one more row, p^T rhs1 for beta-bar (one
+      // warp per row); then the per-row FP64 work with one row per lane so each
+      // FP64 instruction serves up to 32 rows
+      for (int t = warp; t <= nrows; t += kWarps) {
+        const df x = row_dot(t < nrows ? a.P + (size_t)(r0 + t) * a.ldP : a.pdf, rhs_s, npair);
         if (lane == 0) {
           s_xh[t] = x.hi;
           s_xl[t] = x.lo;
         }
       }
       __syncthreads();
+      const double betabar = -((double)s_xh[nrows] + (double)s_xl[nrows]) * a.inv_s;
       GDWD_MARK(15);
       for (int t = threadIdx.x; t < nrows; t += kThreads) {
         const int64_t i = r0 + t;
@@ -295,22 +296,17 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
     {
       for (int64_t i = threadIdx.x; i < 2 * npair; i += kThreads) rhs_s[i] = i < n ? a.rhsB[i] : make_float2(0.f, 0.f);
       __syncthreads();
-      df pd{0.f, 0.f};
-      for (int64_t i = threadIdx.x; i < n; i += kThreads) {
-        const float2 pv = a.pdf[i];
-        df_fma(pd, df{pv.x, pv.y}, df{rhs_s[i].x, rhs_s[i].y});
-      }
-      beta = -df_to_double(block_sum_df(pd, s_redf)) * a.inv_s;
       GDWD_MARK(11);
       double s_res2 = 0, s_ya = 0, s_xica = 0, s_ams2 = 0, s_amin2 = 0, s_amax2 = 0, s_pr = 0, s_px = 0, s_du = 0;
-      for (int t = warp; t < nrows; t += kWarps) {
-        const df x = row_dot(a.P + (size_t)(r0 + t) * a.ldP, rhs_s, npair);
+      for (int t = warp; t <= nrows; t += kWarps) {
+        const df x = row_dot(t < nrows ? a.P + (size_t)(r0 + t) * a.ldP : a.pdf, rhs_s, npair);
         if (lane == 0) {
           s_xh[t] = x.hi;
           s_xl[t] = x.lo;
         }
       }
       __syncthreads();
+      beta = -((double)s_xh[nrows] + (double)s_xl[nrows]) * a.inv_s;
       GDWD_MARK(12);
       for (int t = threadIdx.x; t < nrows; t += kThreads) {
         const int64_t i = r0 + t;
@@ -398,9 +394,16 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
         pb.rc[kk].reset();
         pb.ra[kk].reset();
       }
-      PassA2<T> pa{up, a.partial, TB, NB, Q};
-      PassBA<T, IterEpi> pba{&pb, &pa};
-      if (!stream_slabs<T>(L, rg, cta, grid, a.err, a.timeout_ns, &s_abort, pba)) return;
+      // the column dots Z~^T u run on every dots_every-th iteration; in between
+      // U_u follows its recurrence
+      dots_prev = ((it - it0) % a.dots_every) == a.dots_every - 1;
+      if (dots_prev) {
+        PassA2<T> pa{up, a.partial, TB, NB, Q};
+        PassBA<T, IterEpi> pba{&pb, &pa};
+        if (!stream_slabs<T>(L, rg, cta, grid, a.err, a.timeout_ns, &s_abort, pba)) return;
+      } else {
+        if (!stream_slabs<T>(L, rg, cta, grid, a.err, a.timeout_ns, &s_abort, pb)) return;
+      }
       const double vals[6] = {epi.sg2, epi.sgr, epi.sr2, epi.sa2, epi.sag, epi.sta2};
       block_sum_n<6>(vals, kWarps, s_part, a.scal + (size_t)S_G2 * grid + cta, grid);
     }
@@ -415,68 +418,88 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
     }
     __syncthreads();
     GDWD_MARK(13);
-    if (threadIdx.x == 0) {
-      // FP64 only where cancellation needs it (theta, ||w|| - R, the eta_D3 expansion,
-      // the duality gap); plain norms and ratios in FP32 (they are compared with tol).
-      const double S1 = s_tot[S_G2], S2 = s_tot[S_GRHO], S3 = s_tot[S_RHO2];
-      const double gs = rcp_nr(sig * sqmu);
-      const double gnorm = sqrt_nr(S1);
-      const double th = (gnorm <= a.R) ? 1.0 : div_nr(a.R, gnorm);          // Step 2 projection
-      const double w2 = fmax(0.0, S1 + 2.0 * gs * S2 + gs * gs * S3);        // ||w||^2
-      const double om = 1.0 - th;
-      const double wu2 = fmax(0.0, om * om * S1 + 2.0 * om * gs * S2 + gs * gs * S3);   // ||w - u+||^2
-      const double kap = a.tau * sig * a.mu * om;
-      const double d3 = fmax(0.0, s_tot[S_A2] - 2.0 * kap * s_tot[S_AG] + kap * kap * S1);
-      const float wnf = sqrtf((float)w2);
-      const double wmr = (w2 - a.R * a.R) * (double)(1.0f / (wnf + (float)a.R));   // ||w|| - R
-      const double p1 = sqrtf((float)s_tot[S_RES2]) * inv_den;
-      const double p2 = sqrtf((float)(a.mu * wu2)) * inv_den;
-      const double p3 = fmax(wmr, 0.0) * inv_den;
-      const double dd1 = sqrtf((float)s_tot[S_AMIN2]) * inv_den;
-      const double dd2 = sqrtf((float)s_tot[S_AMAX2]) * inv_den;
-      const double dd3 = sqrtf((float)d3) * inv_den;
-      const double c1 = fabs(s_tot[S_YA]) * inv_den;
-      const double c2 = fabs(s_tot[S_XICA]) * inv_den;
-      const double c3 = sqrtf((float)s_tot[S_AMS2]) * inv_den;
-      const double pobj = s_tot[S_PRIM_R] + a.C * s_tot[S_PRIM_XI];
-      const double dobj = a.kappa * s_tot[S_DUAL_A] - a.R * sqrt_nr(s_tot[S_TA2]);
-      const double gap = (double)((float)fabs(pobj - dobj) / (float)(1.0 + fabs(pobj) + fabs(dobj)));
-      const double ep = fmax(p1, fmax(p2, p3)), ed = fmax(dd1, fmax(dd2, dd3)), ec = fmax(c1, fmax(c2, c3));
-      const double kkt = fmax(fmax(ep, ed), fmax(ec, gap));
-      const double wn = (double)wnf;
-      int done = 0;
-      double sig_next = sig;
-      if (!(kkt == kkt) || isinf(kkt)) {
-        done = 1;
-        status = GDWD_ENUMERIC;
-      } else if (a.stop_rule == 0 ? kkt <= a.tol
-                                  : (fmax(ep, ed) < a.tol && fmin(ec, gap) < sqrt_nr(a.tol) &&
-                                     fmax(ec, gap) < 0.05)) {
-        done = 1;
-        status = GDWD_OK;
-      } else if (it >= 1 && fmax(ep, ed) > a.tol) {                          // sigma rule, Sec. 4.4
-        const float chi = (float)ep / fmaxf((float)ed, 1e-30f);
-        const float ichi = (float)ed / fmaxf((float)ep, 1e-30f);
-        const float big = fmaxf(chi, ichi);
-        const double zeta = big > 500.f ? 2.2 : (big > 50.f ? 1.65 : 1.1);
-        if (chi > 5.f) sig_next = sig * zeta;
-        else if (ichi > 5.f) sig_next = sig / zeta;
+    if (warp == 0) {
+      // Three independent chains on three lanes (the FP64 Newton-refined sqrt and
+      // divide are long dependent chains): lane 0 the projection / w quantities,
+      // lane 1 the objectives and gap, lane 2 the plain norms.  FP64 only where
+      // cancellation needs it (theta, ||w|| - R, the eta_D3 expansion, the gap);
+      // plain norms and ratios in FP32 (they are compared with tol).
+      double th = 1.0, p2 = 0.0, p3 = 0.0, dd3 = 0.0, wn = 0.0;             // lane 0
+      double pobj = 0.0, dobj = 0.0, gap = 0.0;                               // lane 1
+      double p1 = 0.0, dd1 = 0.0, dd2 = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0;    // lane 2
+      if (lane == 0) {
+        const double S1 = s_tot[S_G2], S2 = s_tot[S_GRHO], S3 = s_tot[S_RHO2];
+        const double gs = rcp_nr(sig * sqmu);
+        const double gnorm = sqrt_nr(S1);
+        th = (gnorm <= a.R) ? 1.0 : div_nr(a.R, gnorm);                      // Step 2 projection
+        const double w2 = fmax(0.0, S1 + 2.0 * gs * S2 + gs * gs * S3);      // ||w||^2
+        const double om = 1.0 - th;
+        const double wu2 = fmax(0.0, om * om * S1 + 2.0 * om * gs * S2 + gs * gs * S3);   // ||w - u+||^2
+        const double kap = a.tau * sig * a.mu * om;
+        const double d3 = fmax(0.0, s_tot[S_A2] - 2.0 * kap * s_tot[S_AG] + kap * kap * S1);
+        const float wnf = sqrtf((float)w2);
+        const double wmr = (w2 - a.R * a.R) * (double)(1.0f / (wnf + (float)a.R));   // ||w|| - R
+        p2 = sqrtf((float)(a.mu * wu2)) * inv_den;
+        p3 = fmax(wmr, 0.0) * inv_den;
+        dd3 = sqrtf((float)d3) * inv_den;
+        wn = (double)wnf;
+      } else if (lane == 1) {
+        pobj = s_tot[S_PRIM_R] + a.C * s_tot[S_PRIM_XI];
+        dobj = a.kappa * s_tot[S_DUAL_A] - a.R * sqrt_nr(s_tot[S_TA2]);
+        gap = (double)((float)fabs(pobj - dobj) / (float)(1.0 + fabs(pobj) + fabs(dobj)));
+      } else if (lane == 2) {
+        p1 = sqrtf((float)s_tot[S_RES2]) * inv_den;
+        dd1 = sqrtf((float)s_tot[S_AMIN2]) * inv_den;
+        dd2 = sqrtf((float)s_tot[S_AMAX2]) * inv_den;
+        c1 = fabs(s_tot[S_YA]) * inv_den;
+        c2 = fabs(s_tot[S_XICA]) * inv_den;
+        c3 = sqrtf((float)s_tot[S_AMS2]) * inv_den;
       }
-      s_ctl[0] = th;
-      s_ctl[1] = sig_next;
-      s_ctl[2] = done;
-      s_ctl[3] = status;
-      if (cta == 0) {
-        Ctrl* c = a.ctrl;
-        c->beta = beta;
-        c->pobj = pobj;
-        c->dobj = dobj;
-        c->kkt = kkt;
-        c->eta_p1 = p1; c->eta_p2 = p2; c->eta_p3 = p3;
-        c->eta_d1 = dd1; c->eta_d2 = dd2; c->eta_d3 = dd3;
-        c->eta_c1 = c1; c->eta_c2 = c2; c->eta_c3 = c3;
-        c->eta_gap = gap;
-        c->wnorm = wn;
+      pobj = __shfl_sync(0xffffffffu, pobj, 1);
+      dobj = __shfl_sync(0xffffffffu, dobj, 1);
+      gap = __shfl_sync(0xffffffffu, gap, 1);
+      p1 = __shfl_sync(0xffffffffu, p1, 2);
+      dd1 = __shfl_sync(0xffffffffu, dd1, 2);
+      dd2 = __shfl_sync(0xffffffffu, dd2, 2);
+      c1 = __shfl_sync(0xffffffffu, c1, 2);
+      c2 = __shfl_sync(0xffffffffu, c2, 2);
+      c3 = __shfl_sync(0xffffffffu, c3, 2);
+      if (lane == 0) {
+        const double ep = fmax(p1, fmax(p2, p3)), ed = fmax(dd1, fmax(dd2, dd3)), ec = fmax(c1, fmax(c2, c3));
+        const double kkt = fmax(fmax(ep, ed), fmax(ec, gap));
+        int done = 0;
+        double sig_next = sig;
+        if (!(kkt == kkt) || isinf(kkt)) {
+          done = 1;
+          status = GDWD_ENUMERIC;
+        } else if (a.stop_rule == 0 ? kkt <= a.tol
+                                    : (fmax(ep, ed) < a.tol && fmin(ec, gap) < sqrt_tol && fmax(ec, gap) < 0.05)) {
+          done = 1;
+          status = GDWD_OK;
+        } else if (it >= 1 && fmax(ep, ed) > a.tol) {                          // sigma rule, Sec. 4.4
+          const float chi = (float)ep / fmaxf((float)ed, 1e-30f);
+          const float ichi = (float)ed / fmaxf((float)ep, 1e-30f);
+          const float big = fmaxf(chi, ichi);
+          const double zeta = big > 500.f ? 2.2 : (big > 50.f ? 1.65 : 1.1);
+          if (chi > 5.f) sig_next = sig * zeta;
+          else if (ichi > 5.f) sig_next = sig / zeta;
+        }
+        s_ctl[0] = th;
+        s_ctl[1] = sig_next;
+        s_ctl[2] = done;
+        s_ctl[3] = status;
+        if (cta == 0) {
+          Ctrl* c = a.ctrl;
+          c->beta = beta;
+          c->pobj = pobj;
+          c->dobj = dobj;
+          c->kkt = kkt;
+          c->eta_p1 = p1; c->eta_p2 = p2; c->eta_p3 = p3;
+          c->eta_d1 = dd1; c->eta_d2 = dd2; c->eta_d3 = dd3;
+          c->eta_c1 = c1; c->eta_c2 = c2; c->eta_c3 = c3;
+          c->eta_gap = gap;
+          c->wnorm = wn;
+        }
       }
     }
     __syncthreads();

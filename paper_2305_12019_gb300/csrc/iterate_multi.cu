@@ -11,8 +11,9 @@
 //   R   U_g from the column dots, deferred n-space updates, b_j, rhs1_j
 //   N1  x-bar_j = G^{-1} rhs1_j (one read of each G^{-1} row for all j), Step 1b
 //   N2  x_j, beta_j, c_j, Steps 2-3, (G - I) c_j, n-space sums
-//   B   K deferred d-updates, Z~ [c_1 .. c_K], Z~ [alpha_1 .. alpha_K] and the
-//       column dots Z~^T [u_1 .. u_K] (the one Z read), d-space sums
+//   B   K deferred d-updates, Z~ [c_1 .. c_K], Z~ [alpha_1 .. alpha_K] and, every
+//       dots_every-th iteration, the column dots Z~^T [u_1 .. u_K] (the one Z
+//       read), d-space sums
 //   S   per-instance KKT, sigma rule, stop test
 #include <algorithm>
 #include <mutex>
@@ -327,6 +328,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_multi_kernel(MultiArgs<ty
   for (int m = threadIdx.x; m < K * nrows; m += kThreads) {
     const int j = m / nrows, t = m - j * nrows;
     a.Ur[(int64_t)j * n + r0 + t] = 0.0;
+    a.Uu[(int64_t)j * n + r0 + t] = 0.0;
   }
   __syncthreads();
 
@@ -334,6 +336,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_multi_kernel(MultiArgs<ty
   const int rstride = 2 * npair;
   float* s_redf = reinterpret_cast<float*>(s_red);
   int it = 0;
+  bool dots_prev = false;   // the last pass B took the column dots
   for (; it < a.max_iter && act; ++it) {
     // ---------------- R (this CTA's rows, every active instance): U_g from the
     // pass-B column dots and (G - I) c, the deferred n-space update, b, rhs1
@@ -343,7 +346,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_multi_kernel(MultiArgs<ty
       if (!(act & (1u << j))) continue;
       const int64_t i = r0 + t, idx = (int64_t)j * n + i;
       double ug = 0.0;
-      if (pending) {
+      if (pending && dots_prev) {
         const CT* pp = a.partial + (size_t)idx * NB;
         double bsum;
         if constexpr (sizeof(CT) == 8) {
@@ -355,14 +358,16 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_multi_kernel(MultiArgs<ty
           for (int s2 = lane; s2 < NB; s2 += 32) df_add(acc, (float)pp[s2]);
           bsum = df_to_double(df_warp_sum(acc));
         }
-        ug = a.sc[i] * bsum - a.kc[idx];
+        ug = a.sc[i] * bsum;
       }
       if (lane == 0) {
-        double uu = 0.0, ur = a.Ur[idx];
+        double uu = a.Uu[idx], ur = a.Ur[idx];
         if (pending) {
           const double rcoef = a.tau * sig_prev[j] * sqmu * (1.0 - theta[j]);
+          ug = (dots_prev ? ug : uu) - a.kc[idx];
           uu = theta[j] * ug;
           ur = (1.0 - a.tau) * ur - rcoef * ug;
+          a.Uu[idx] = uu;
           a.Ur[idx] = ur;
         }
         const double bi = uu + ur * rcp_nr(sig[j] * sqmu);
@@ -543,9 +548,14 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_multi_kernel(MultiArgs<ty
           pb.rc[j][x].reset();
           pb.ra[j][x].reset();
         }
-      PassAK<T, K> pa{up, gstride, a.partial, TB, NB, Q, n};
-      PassBAK<T, K> pba{&pb, &pa};
-      if (!stream_slabs<T>(L, rg, cta, grid, a.err, a.timeout_ns, &s_abort, pba)) return;
+      dots_prev = (it % a.dots_every) == a.dots_every - 1;
+      if (dots_prev) {
+        PassAK<T, K> pa{up, gstride, a.partial, TB, NB, Q, n};
+        PassBAK<T, K> pba{&pb, &pa};
+        if (!stream_slabs<T>(L, rg, cta, grid, a.err, a.timeout_ns, &s_abort, pba)) return;
+      } else {
+        if (!stream_slabs<T>(L, rg, cta, grid, a.err, a.timeout_ns, &s_abort, pb)) return;
+      }
       block_sum_kn<K, 6>(epi.sums, s_part, a.scal + cta, grid, S_G2);
     }
     MBARRIER(8);

@@ -100,6 +100,7 @@ struct IterArgs {
   double* Ur;            // n: Z~^T rho (rows of the owning CTA)
   double* kc;            // n: (G - I) c of the last iteration
   int refresh;           // 1: U_u, U_rho from u, rho by two passes over Z at launch start
+  int dots_every;        // >= 1: pass B takes the column dots Z~^T u every dots_every iterations
   // d-space state, NB*TB long (padding rows stay 0)
   double* u;
   double* rho;
@@ -133,7 +134,8 @@ struct MultiArgs {
   int64_t dpad;
   double *r, *xi, *alpha, *b;   // [K][n]
   float2 *rhsA, *rhsB;          // [K][n]
-  double *Ur, *kc;              // [K][n]: Z~^T rho_j (rows of the owning CTA), (G - I) c_j
+  double *Uu, *Ur, *kc;         // [K][n]: Z~^T u_j, Z~^T rho_j (rows of the owning CTA), (G - I) c_j
+  int dots_every;               // as in IterArgs
   CT* partial;                  // [K][n][NB]: column dots Z~^T u_j of pass B
   CT *cq, *aq;                  // [K][n]
   double *u, *rho, *g;          // [K][dpad]

@@ -299,3 +299,22 @@ def test_weighted_solve_and_suggest_C(gdwd_lib):
     ref = O.solve(Z, y, 2.0, 3.0, tol=1e-10, e=e, wt=wt)
     _compare(r, w[:, 0], ref)
     assert abs(Cs - O.suggest_C(Z, y, 2.0)) / O.suggest_C(Z, y, 2.0) <= 1e-9
+
+
+@pytest.mark.parametrize("store,dots_every", [("f32", 1), ("f32", 64), ("bf16", 1), ("f64", 1000)])
+def test_column_dot_period(gdwd_lib, store, dots_every):
+    """b = Z~^T g' carried in n-space with direct Z~^T u every dots_every iterations
+    (1: every iteration; large: almost never) reaches the oracle's solution."""
+    from tests import quantize_ref as QR
+    inst = synth.gaussian(seed=97, d=4001, n=230, shift=1.0, n_pos=90, q=1.0, C=2.0,
+                          dtype=np.float64 if store == "f64" else np.float32)
+    tol = 1e-8 if store == "f64" else 1e-6
+    with gdwd_lib.Solver(inst.Z, inst.y, 1.0, 2.0, store=store, tol=tol, dots_every=dots_every) as s:
+        res, w, _ = s.solve()
+    assert res[0]["status"] == 0, res[0]
+    Zref = inst.Z.astype(np.float64)
+    if store == "bf16":
+        qv, sc = QR.quantize(Zref, "bf16")
+        Zref = qv * sc[None, :]
+    ref = O.solve(Zref, inst.y, 1.0, 2.0, tol=1e-10)
+    _compare(res[0], w[:, 0], ref)

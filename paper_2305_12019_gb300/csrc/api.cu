@@ -70,7 +70,7 @@ struct gdwd_handle {
     bool ready = false;
     double *r, *xi, *alpha, *b, *u, *rho, *g, *scal, *Uu, *Ur, *kc;
     float2 *rhsA, *rhsB;
-    void *cq, *aq, *partial;
+    void *coef, *partial;
     Ctrl* ctrl;
   } ms;
   double phase_ns[kPhaseSlots] = {};
@@ -551,8 +551,7 @@ static gdwd_status solve_multi(gdwd_handle* h, const double* Cs, int K, int kker
     CK(halloc(h, &m.Uu, 4 * n), "alloc");
     CK(halloc(h, &m.Ur, 4 * n), "alloc");
     CK(halloc(h, &m.kc, 4 * n), "alloc");
-    CK(halloc(h, (uint8_t**)&m.cq, 4 * n * ct), "alloc");
-    CK(halloc(h, (uint8_t**)&m.aq, 4 * n * ct), "alloc");
+    CK(halloc(h, (uint8_t**)&m.coef, 8 * n * ct), "alloc");
     CK(halloc(h, (uint8_t**)&m.partial, 4 * (size_t)n * h->L.NB * ct), "alloc");
     CK(halloc(h, &m.u, 4 * dpad), "alloc");
     CK(halloc(h, &m.rho, 4 * dpad), "alloc");
@@ -631,15 +630,13 @@ static gdwd_status solve_multi(gdwd_handle* h, const double* Cs, int K, int kker
   if (h->store == GDWD_F64) {
     MultiArgs<double> a{};
     fill(a);
-    a.cq = (double*)m.cq;
-    a.aq = (double*)m.aq;
+    a.coef = (double*)m.coef;
     a.partial = (double*)m.partial;
     e = run_multi_f64(kker, a, smem_limit, st);
   } else {
     MultiArgs<float> a{};
     fill(a);
-    a.cq = (float*)m.cq;
-    a.aq = (float*)m.aq;
+    a.coef = (float*)m.coef;
     a.partial = (float*)m.partial;
     e = run_multi_f32(h->store, kker, a, smem_limit, st);
   }

@@ -136,72 +136,149 @@ struct EpiK {
 template <typename T, int K>
 struct PassBAK;
 
-// pass B for K instances x two right-hand sides (c_j, alpha_j); a thread owns
-// two consecutive rows of a column group; coefficients come through the L1
+// four consecutive stored elements (4-element aligned) -> compute type
+__device__ __forceinline__ void load4r(const double* p, double* v) {
+  const double2 x = *reinterpret_cast<const double2*>(p), y = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
+}
+__device__ __forceinline__ void load4r(const float* p, float* v) {
+  const float4 x = *reinterpret_cast<const float4*>(p);
+  v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+}
+__device__ __forceinline__ void load4r(const __nv_bfloat16* p, float* v) {
+  const uint2 x = *reinterpret_cast<const uint2*>(p);
+  bf16x2_to_float(x.x, v);
+  bf16x2_to_float(x.y, v + 2);
+}
+__device__ __forceinline__ void load4r(const __half* p, float* v) {
+  const uint2 x = *reinterpret_cast<const uint2*>(p);
+  const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&x.x));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&x.y));
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void load4r(const __nv_fp8_e4m3* p, float* v) {
+  const uint32_t w = *reinterpret_cast<const uint32_t*>(p);
+  const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w & 0xffffu), __NV_E4M3);
+  const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w >> 16), __NV_E4M3);
+  const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&lo));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&hi));
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
+// the 2K pass-B coefficients of one column (sc c_j, then sc alpha_j), stored
+// interleaved so that one column's are 16-byte vectors
+template <int N>
+__device__ __forceinline__ void load_coef(const float* p, float* v) {
+#pragma unroll
+  for (int k = 0; k < N; k += 4) {
+    const float4 x = __ldg(reinterpret_cast<const float4*>(p + k));
+    v[k] = x.x; v[k + 1] = x.y; v[k + 2] = x.z; v[k + 3] = x.w;
+  }
+}
+template <int N>
+__device__ __forceinline__ void load_coef(const double* p, double* v) {
+#pragma unroll
+  for (int k = 0; k < N; k += 2) {
+    const double2 x = __ldg(reinterpret_cast<const double2*>(p + k));
+    v[k] = x.x; v[k + 1] = x.y;
+  }
+}
+
+// pass B for K instances x two right-hand sides (c_j, alpha_j).  Thread t owns
+// rows 4q .. 4q+3 (q = t % Q4, Q4 = TB / 4) of the column group t / Q4, so the
+// threads of a step read consecutive 4-element pieces of one column; the
+// coefficients of a column are two (FP64: four) vector loads for all K; frozen
+// instances are skipped.
 template <typename T, int K>
 struct PassBK {
   using CT = typename ElemTraits<T>::compute_t;
-  const CT* cq;       // global [K][n]
-  const CT* aq;       // global [K][n]
+  const CT* coef;     // global [n][2K]
   double* red;        // shared 2 * G * TB
-  int TB, Q2, G;
+  int TB, Q4, G;
   int64_t n, d;
   unsigned act;       // bit j: instance j still iterating
   EpiK<K>* epi;
-  RunAcc<CT> rc[K][2], ra[K][2];
+  RunAcc<CT> rc[K][4], ra[K][4];
 
   __device__ void chunk(const T* buf, int k, int s, int col0, int cw) {
-    const int grp = threadIdx.x / Q2, q = threadIdx.x - grp * Q2;
+    const int grp = threadIdx.x / Q4, q = threadIdx.x - grp * Q4;
     if (grp >= G) return;
-    CT ac[K][2], aa[K][2];
-#pragma unroll
-    for (int j = 0; j < K; ++j) ac[j][0] = ac[j][1] = aa[j][0] = aa[j][1] = 0;
-    const T* base = buf + 2 * q;
-    for (int col = grp; col < cw; col += G) {
-      CT e[2];
-      load2(base + (size_t)col * TB, e);
-#pragma unroll
-      for (int j = 0; j < K; ++j) {
-        const CT c = __ldg(cq + (size_t)j * n + col0 + col);
-        const CT a = __ldg(aq + (size_t)j * n + col0 + col);
-        ac[j][0] = fma(e[0], c, ac[j][0]);
-        ac[j][1] = fma(e[1], c, ac[j][1]);
-        aa[j][0] = fma(e[0], a, aa[j][0]);
-        aa[j][1] = fma(e[1], a, aa[j][1]);
-      }
-    }
+    CT ac[K][4], aa[K][4];
 #pragma unroll
     for (int j = 0; j < K; ++j)
 #pragma unroll
-      for (int x = 0; x < 2; ++x) {
-        rc[j][x].fold(ac[j][x]);
-        ra[j][x].fold(aa[j][x]);
+      for (int r = 0; r < 4; ++r) ac[j][r] = aa[j][r] = 0;
+    const T* base = buf + 4 * q;
+    int col = grp;
+    // two columns per step: both columns' loads are in flight together
+    for (; col + G < cw; col += 2 * G) {
+      CT e0[4], e1[4], c0[2 * K], c1[2 * K];
+      load4r(base + (size_t)col * TB, e0);
+      load4r(base + (size_t)(col + G) * TB, e1);
+      load_coef<2 * K>(coef + (size_t)(col0 + col) * 2 * K, c0);
+      load_coef<2 * K>(coef + (size_t)(col0 + col + G) * 2 * K, c1);
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        if (!(act & (1u << j))) continue;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          ac[j][r] = fma(e0[r], c0[j], ac[j][r]);
+          aa[j][r] = fma(e0[r], c0[K + j], aa[j][r]);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          ac[j][r] = fma(e1[r], c1[j], ac[j][r]);
+          aa[j][r] = fma(e1[r], c1[K + j], aa[j][r]);
+        }
       }
+    }
+    if (col < cw) {
+      CT e[4], cf[2 * K];
+      load4r(base + (size_t)col * TB, e);
+      load_coef<2 * K>(coef + (size_t)(col0 + col) * 2 * K, cf);
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        if (!(act & (1u << j))) continue;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          ac[j][r] = fma(e[r], cf[j], ac[j][r]);
+          aa[j][r] = fma(e[r], cf[K + j], aa[j][r]);
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      if (!(act & (1u << j))) continue;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        rc[j][r].fold(ac[j][r]);
+        ra[j][r].fold(aa[j][r]);
+      }
+    }
   }
 
   template <int J>
   __device__ void finish_instance(int s) {
-    const int grp = threadIdx.x / Q2, q = threadIdx.x - grp * Q2;
+    if (!(act & (1u << J))) return;          // uniform across the CTA
+    const int grp = threadIdx.x / Q4, q = threadIdx.x - grp * Q4;
     if (grp < G) {
 #pragma unroll
-      for (int x = 0; x < 2; ++x) {
-        red[(size_t)grp * TB + 2 * q + x] = rc[J][x].get();
-        red[(size_t)(G + grp) * TB + 2 * q + x] = ra[J][x].get();
-        rc[J][x].reset();
-        ra[J][x].reset();
+      for (int r = 0; r < 4; ++r) {
+        red[(size_t)grp * TB + 4 * q + r] = rc[J][r].get();
+        red[(size_t)(G + grp) * TB + 4 * q + r] = ra[J][r].get();
+        rc[J][r].reset();
+        ra[J][r].reset();
       }
     }
     __syncthreads();
-    if (act & (1u << J)) {
-      for (int j = threadIdx.x; j < TB; j += blockDim.x) {
-        double t = 0.0, ta = 0.0;
-        for (int gq = 0; gq < G; ++gq) {
-          t += red[(size_t)gq * TB + j];
-          ta += red[(size_t)(G + gq) * TB + j];
-        }
-        const int64_t gj = (int64_t)s * TB + j;
-        if (gj < d) epi->template row<J>(gj, t, ta);
+    for (int j = threadIdx.x; j < TB; j += blockDim.x) {
+      double t = 0.0, ta = 0.0;
+      for (int gq = 0; gq < G; ++gq) {
+        t += red[(size_t)gq * TB + j];
+        ta += red[(size_t)(G + gq) * TB + j];
       }
+      const int64_t gj = (int64_t)s * TB + j;
+      if (gj < d) epi->template row<J>(gj, t, ta);
     }
     __syncthreads();
   }
@@ -265,8 +342,8 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_multi_kernel(MultiArgs<ty
   const int cta = blockIdx.x, grid = a.grid;
   const int64_t n = L.n, d = L.d, dpad = a.dpad;
   const int TB = L.TB, NB = L.NB;
-  const int Q = TB / VEC, Q2 = TB / 2;
-  const int G2 = Q2 <= kThreads ? kThreads / Q2 : 1;
+  const int Q = TB / VEC, Q4 = TB / 4;
+  const int G4 = Q4 <= kThreads ? kThreads / Q4 : 1;
   const int nmy = (NB > cta) ? (NB - cta + grid - 1) / grid : 0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int qcase = q_case(a.q);
@@ -463,8 +540,8 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_multi_kernel(MultiArgs<ty
             const double an = al - a.tau * sig[j] * res;
             a.xi[idx] = xin;
             a.alpha[idx] = an;
-            a.cq[idx] = (CT)(a.sc[i] * c);
-            a.aq[idx] = (CT)(a.sc[i] * an);
+            a.coef[(size_t)i * 2 * K + j] = (CT)(a.sc[i] * c);
+            a.coef[(size_t)i * 2 * K + K + j] = (CT)(a.sc[i] * an);
             const float2 rv = rhs_s[(size_t)j * rstride + i];
             a.kc[idx] = ((double)rv.x + (double)rv.y) - xv + bet[j] * (yi - a.p[i]);   // (G - I) c
             const double rq1 = pow_q1(ri, a.q, qcase);
@@ -493,7 +570,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_multi_kernel(MultiArgs<ty
     {
       const int gstride = nmy * TB;
       double* red = reinterpret_cast<double*>(uni);
-      CT* up = reinterpret_cast<CT*>(uni + (size_t)2 * G2 * TB * sizeof(double));
+      CT* up = reinterpret_cast<CT*>(uni + (size_t)2 * G4 * TB * sizeof(double));
 #pragma unroll
       for (int j = 0; j < K; ++j) {
         const bool on = act & (1u << j);
@@ -531,12 +608,11 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_multi_kernel(MultiArgs<ty
 #pragma unroll
         for (int k = 0; k < 6; ++k) epi.sums[j][k] = 0.0;
       PassBK<T, K> pb;
-      pb.cq = a.cq;
-      pb.aq = a.aq;
+      pb.coef = a.coef;
       pb.red = red;
       pb.TB = TB;
-      pb.Q2 = Q2;
-      pb.G = G2;
+      pb.Q4 = Q4;
+      pb.G = G4;
       pb.n = n;
       pb.d = d;
       pb.act = act;
@@ -667,12 +743,12 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_multi_kernel(MultiArgs<ty
 
 template <typename T>
 static size_t union_bytes_multi(const Layout& L, int grid, int K) {
-  const int Q2 = L.TB / 2;
-  const int G2 = Q2 <= kThreads ? kThreads / Q2 : 1;
+  const int Q4 = L.TB / 4;
+  const int G4 = Q4 <= kThreads ? kThreads / Q4 : 1;
   using CT = typename ElemTraits<T>::compute_t;
   const int nmy = (L.NB + grid - 1) / grid;
   const size_t n_bytes = (size_t)K * ((L.n + 1) / 2) * 2 * sizeof(float2);
-  const size_t b_bytes = (size_t)2 * G2 * L.TB * sizeof(double) + (size_t)K * nmy * L.TB * sizeof(CT);
+  const size_t b_bytes = (size_t)2 * G4 * L.TB * sizeof(double) + (size_t)K * nmy * L.TB * sizeof(CT);
   return (std::max(n_bytes, b_bytes) + 127) & ~(size_t)127;
 }
 
@@ -728,7 +804,7 @@ int multi_max_k(int store, const Layout& L, int grid, int smem_limit) {
       default: ub = union_bytes_multi<float>(L, grid, K); break;
     }
     const int64_t stage = ((int64_t)L.CW * L.TB * L.esize + 127) & ~(int64_t)127;
-    return (int64_t)smem_limit - (int64_t)ub - 1024 >= 2 * stage && L.TB / 2 <= kThreads &&
+    return (int64_t)smem_limit - (int64_t)ub - 1024 >= 2 * stage && L.TB / 4 <= kThreads &&
            (L.n + grid - 1) / grid <= kMaxRowsPerCta;
   };
   return fits(4) ? 4 : fits(2) ? 2 : 1;

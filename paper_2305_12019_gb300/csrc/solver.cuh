@@ -137,7 +137,7 @@ struct MultiArgs {
   double *Uu, *Ur, *kc;         // [K][n]: Z~^T u_j, Z~^T rho_j (rows of the owning CTA), (G - I) c_j
   int dots_every;               // as in IterArgs
   CT* partial;                  // [K][n][NB]: column dots Z~^T u_j of pass B
-  CT *cq, *aq;                  // [K][n]
+  CT* coef;                     // [n][2K]: sc_i c_ij (j < K), then sc_i alpha_ij
   double *u, *rho, *g;          // [K][dpad]
   double* scal;                 // [K][S_COUNT][grid]
   unsigned* bar;

@@ -26,10 +26,9 @@ R3  initial iterate r = xi = 1, w = u = 0, beta = 0, alpha = 0, rho = 0
     (the feasible point used in the proof of Prop. 2).
 R4  sigma0 = min(10C, n)^q (Sec. 4.4) unless given.
 R5  the sigma rule runs after the KKT evaluation of every iteration k >= 1.
-R5b ... while max(eta_P, eta_D) > tol: the rule balances eta_P against eta_D, and
-    once both meet the tolerance (the stricter stop of R8 may still wait on
-    eta_C or the gap) their ratio is rounding noise that would drive sigma by
-    factors of 2.2 per iteration.
+R5b ... unless eta_P or eta_D is below 1e-3 * tol: the rule balances eta_P
+    against eta_D, and once one of them is at the level of rounding their
+    ratio is noise that would push sigma by 2.2 per iteration.
 R6  eta_D also holds eta_D3 = ||Z~ alpha + D rho|| / (1+C), the w-stationarity of
     the Lagrangian of eq-gen-scale; chi = eta_P / max(eta_D, 1e-300).
 R7  eta_C3 is the unsquared norm ||alpha - s|| / (1+C).
@@ -428,7 +427,7 @@ def solve(Z, y, q, C, mu=1.0, tau=1.618, tol=1e-9, max_iter=50000, sigma0=None,
         if stop_rule == 1 and (max(eta["P"], eta["D"]) < tol and min(eta["C"], eta["gap"]) < math.sqrt(tol)
                                and max(eta["C"], eta["gap"]) < 0.05):               # Sec. 4.3
             break
-        if k >= 1 and max(eta["P"], eta["D"]) > tol:        # R5, R5b
+        if k >= 1 and min(eta["P"], eta["D"]) > 1e-3 * tol:   # R5, R5b
             sigma = sigma_update(sigma, eta["P"], eta["D"])
     if stop_rule == 1:
         converged = eta is not None and (max(eta["P"], eta["D"]) < tol and min(eta["C"], eta["gap"]) < math.sqrt(tol)

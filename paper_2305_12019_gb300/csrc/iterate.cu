@@ -476,7 +476,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
                                     : (fmax(ep, ed) < a.tol && fmin(ec, gap) < sqrt_tol && fmax(ec, gap) < 0.05)) {
           done = 1;
           status = GDWD_OK;
-        } else if (it >= 1 && fmax(ep, ed) > a.tol) {                          // sigma rule, Sec. 4.4
+        } else if (it >= 1 && fmin(ep, ed) > 1e-3 * a.tol) {                          // sigma rule, Sec. 4.4
           const float chi = (float)ep / fmaxf((float)ed, 1e-30f);
           const float ichi = (float)ed / fmaxf((float)ep, 1e-30f);
           const float big = fmaxf(chi, ichi);

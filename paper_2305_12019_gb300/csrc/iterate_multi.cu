@@ -686,7 +686,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_multi_kernel(MultiArgs<ty
                                      fmax(ec, gap) < 0.05)) {
         done = 1.0;
         stat = GDWD_OK;
-      } else if (it >= 1 && fmax(ep, ed) > a.tol) {
+      } else if (it >= 1 && fmin(ep, ed) > 1e-3 * a.tol) {
         const float chi = (float)ep / fmaxf((float)ed, 1e-30f);
         const float ichi = (float)ed / fmaxf((float)ep, 1e-30f);
         const float big = fmaxf(chi, ichi);

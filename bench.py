@@ -12,7 +12,7 @@ iteration kernel until kkt <= tol, then w), gdwd_free.
   e2e     the same with Z in pinned host memory: the host->device copy of Z and
           y and the device->host copy of w and the result inside every step
   roofline  the persistent iteration kernel: algorithmic bytes per launch
-          (iterations x (2 reads of Z + 2 reads of the double-float G^{-1} +
+          (iterations x (1 read of Z + 2 reads of the double-float G^{-1} +
           vector traffic)) / its CUDA-event duration, against the measured HBM peak
   cpu_baseline  the FP64 CPU oracle (oracle/) on the host cores, one full solve
 
@@ -143,10 +143,12 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": reasons, "samples": len(rows)}
 
 
-def algorithmic_bytes_per_iteration(d, n, zbytes, slabs):
-    """Per ADMM iteration: Z read twice, double-float G^{-1} read twice (8 n^2 B each),
-    d-vectors (u, rho, g read/written: 8 x 8d), n-vectors (~20 x 8n), pass-A partials (2 x 4 n slabs)."""
-    return 2 * d * n * zbytes + 2 * 8 * n * n + 64 * d + 160 * n + 8 * n * slabs
+def algorithmic_bytes_per_iteration(d, n, zbytes, slabs, dots_every=16):
+    """Per ADMM iteration: Z read once (b = Z~^T g' is carried in n-space), the
+    double-float G^{-1} read twice (8 n^2 B each), d-vectors (u, rho, g read/written:
+    8 x 8d), n-vectors (~20 x 8n), and every dots_every-th iteration the column-dot
+    partials (written and read: 2 x 4 n slabs)."""
+    return d * n * zbytes + 2 * 8 * n * n + 64 * d + 160 * n + 8 * n * slabs / dots_every
 
 
 def run_oracle_solve(inst):

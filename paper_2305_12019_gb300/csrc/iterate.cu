@@ -115,9 +115,9 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ uint64_t s_bars[kMaxStages];
   __shared__ int s_flag, s_abort;
-  __shared__ double s_red[2 * kWarps + 2];
   __shared__ double s_tot[S_COUNT];
   __shared__ double s_ctl[8];
+  __shared__ double s_eta[9];
   __shared__ double s_part[kWarps * 9];
 
   const Layout& L = a.L;
@@ -234,6 +234,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
     // from the pass-B column dots Z~^T u and (G - I) c; the deferred update
     // U_u = theta U_g, U_rho <- (1 - tau) U_rho - tau sigma' sqrt(mu) (1 - theta) U_g;
     // b = U_u + U_rho / (sigma sqrt(mu)); rhs1 = b + xi - r - alpha / sigma
+    ring_prefetch(L, rg, cta, grid);   // this iteration's first Z chunks arrive during R, N1, N2
     {
       const double gsc = rcp_nr(sig * sqmu);
       const double rcoef = a.tau * sig_prev * sqmu * (1.0 - theta);
@@ -418,53 +419,49 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
     }
     __syncthreads();
     GDWD_MARK(13);
-    if (warp == 0) {
-      // Three independent chains on three lanes (the FP64 Newton-refined sqrt and
-      // divide are long dependent chains): lane 0 the projection / w quantities,
-      // lane 1 the objectives and gap, lane 2 the plain norms.  FP64 only where
-      // cancellation needs it (theta, ||w|| - R, the eta_D3 expansion, the gap);
-      // plain norms and ratios in FP32 (they are compared with tol).
-      double th = 1.0, p2 = 0.0, p3 = 0.0, dd3 = 0.0, wn = 0.0;             // lane 0
-      double pobj = 0.0, dobj = 0.0, gap = 0.0;                               // lane 1
-      double p1 = 0.0, dd1 = 0.0, dd2 = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0;    // lane 2
-      if (lane == 0) {
-        const double S1 = s_tot[S_G2], S2 = s_tot[S_GRHO], S3 = s_tot[S_RHO2];
-        const double gs = rcp_nr(sig * sqmu);
-        const double gnorm = sqrt_nr(S1);
-        th = (gnorm <= a.R) ? 1.0 : div_nr(a.R, gnorm);                      // Step 2 projection
-        const double w2 = fmax(0.0, S1 + 2.0 * gs * S2 + gs * gs * S3);      // ||w||^2
-        const double om = 1.0 - th;
-        const double wu2 = fmax(0.0, om * om * S1 + 2.0 * om * gs * S2 + gs * gs * S3);   // ||w - u+||^2
-        const double kap = a.tau * sig * a.mu * om;
-        const double d3 = fmax(0.0, s_tot[S_A2] - 2.0 * kap * s_tot[S_AG] + kap * kap * S1);
-        const float wnf = sqrtf((float)w2);
-        const double wmr = (w2 - a.R * a.R) * (double)(1.0f / (wnf + (float)a.R));   // ||w|| - R
-        p2 = sqrtf((float)(a.mu * wu2)) * inv_den;
-        p3 = fmax(wmr, 0.0) * inv_den;
-        dd3 = sqrtf((float)d3) * inv_den;
-        wn = (double)wnf;
-      } else if (lane == 1) {
-        pobj = s_tot[S_PRIM_R] + a.C * s_tot[S_PRIM_XI];
-        dobj = a.kappa * s_tot[S_DUAL_A] - a.R * sqrt_nr(s_tot[S_TA2]);
-        gap = (double)((float)fabs(pobj - dobj) / (float)(1.0 + fabs(pobj) + fabs(dobj)));
-      } else if (lane == 2) {
-        p1 = sqrtf((float)s_tot[S_RES2]) * inv_den;
-        dd1 = sqrtf((float)s_tot[S_AMIN2]) * inv_den;
-        dd2 = sqrtf((float)s_tot[S_AMAX2]) * inv_den;
-        c1 = fabs(s_tot[S_YA]) * inv_den;
-        c2 = fabs(s_tot[S_XICA]) * inv_den;
-        c3 = sqrtf((float)s_tot[S_AMS2]) * inv_den;
-      }
-      pobj = __shfl_sync(0xffffffffu, pobj, 1);
-      dobj = __shfl_sync(0xffffffffu, dobj, 1);
-      gap = __shfl_sync(0xffffffffu, gap, 1);
-      p1 = __shfl_sync(0xffffffffu, p1, 2);
-      dd1 = __shfl_sync(0xffffffffu, dd1, 2);
-      dd2 = __shfl_sync(0xffffffffu, dd2, 2);
-      c1 = __shfl_sync(0xffffffffu, c1, 2);
-      c2 = __shfl_sync(0xffffffffu, c2, 2);
-      c3 = __shfl_sync(0xffffffffu, c3, 2);
-      if (lane == 0) {
+    // Three independent chains on the first lanes of three warps (the FP64
+    // Newton-refined sqrt and divide are long dependent chains; lanes of one warp
+    // would run them one after the other): warp 0 the projection / w quantities,
+    // warp 1 the objectives and gap, warp 2 the plain norms.  FP64 only where
+    // cancellation needs it (theta, ||w|| - R, the eta_D3 expansion, the gap);
+    // plain norms and ratios in FP32 (they are compared with tol).
+    if (lane == 0 && warp == 1) {
+      const double pobj = s_tot[S_PRIM_R] + a.C * s_tot[S_PRIM_XI];
+      const double dobj = a.kappa * s_tot[S_DUAL_A] - a.R * sqrt_nr(s_tot[S_TA2]);
+      s_eta[0] = pobj;
+      s_eta[1] = dobj;
+      s_eta[2] = (double)((float)fabs(pobj - dobj) / (float)(1.0 + fabs(pobj) + fabs(dobj)));
+    } else if (lane == 0 && warp == 2) {
+      s_eta[3] = sqrtf((float)s_tot[S_RES2]) * inv_den;       // p1
+      s_eta[4] = sqrtf((float)s_tot[S_AMIN2]) * inv_den;      // dd1
+      s_eta[5] = sqrtf((float)s_tot[S_AMAX2]) * inv_den;      // dd2
+      s_eta[6] = fabs(s_tot[S_YA]) * inv_den;                 // c1
+      s_eta[7] = fabs(s_tot[S_XICA]) * inv_den;               // c2
+      s_eta[8] = sqrtf((float)s_tot[S_AMS2]) * inv_den;       // c3
+    }
+    double th = 1.0, p2 = 0.0, p3 = 0.0, dd3 = 0.0, wn = 0.0;
+    if (threadIdx.x == 0) {
+      const double S1 = s_tot[S_G2], S2 = s_tot[S_GRHO], S3 = s_tot[S_RHO2];
+      const double gs = rcp_nr(sig * sqmu);
+      const double gnorm = sqrt_nr(S1);
+      th = (gnorm <= a.R) ? 1.0 : div_nr(a.R, gnorm);                        // Step 2 projection
+      const double w2 = fmax(0.0, S1 + 2.0 * gs * S2 + gs * gs * S3);        // ||w||^2
+      const double om = 1.0 - th;
+      const double wu2 = fmax(0.0, om * om * S1 + 2.0 * om * gs * S2 + gs * gs * S3);   // ||w - u+||^2
+      const double kap = a.tau * sig * a.mu * om;
+      const double d3 = fmax(0.0, s_tot[S_A2] - 2.0 * kap * s_tot[S_AG] + kap * kap * S1);
+      const float wnf = sqrtf((float)w2);
+      const double wmr = (w2 - a.R * a.R) * (double)(1.0f / (wnf + (float)a.R));   // ||w|| - R
+      p2 = sqrtf((float)(a.mu * wu2)) * inv_den;
+      p3 = fmax(wmr, 0.0) * inv_den;
+      dd3 = sqrtf((float)d3) * inv_den;
+      wn = (double)wnf;
+    }
+    __syncthreads();
+    {
+      const double pobj = s_eta[0], dobj = s_eta[1], gap = s_eta[2];
+      const double p1 = s_eta[3], dd1 = s_eta[4], dd2 = s_eta[5], c1 = s_eta[6], c2 = s_eta[7], c3 = s_eta[8];
+      if (threadIdx.x == 0) {
         const double ep = fmax(p1, fmax(p2, p3)), ed = fmax(dd1, fmax(dd2, dd3)), ec = fmax(c1, fmax(c2, c3));
         const double kkt = fmax(fmax(ep, ed), fmax(ec, gap));
         int done = 0;

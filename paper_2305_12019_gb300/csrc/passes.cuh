@@ -21,6 +21,7 @@ struct Ring {
   int stages;
   int stage_bytes;
   uint32_t phase;      // parity bit per stage (identical in all threads)
+  int prefetched;      // chunks of the next stream_slabs already issued (identical in all threads)
 };
 
 __device__ __forceinline__ void ring_init(Ring& rg) {
@@ -29,7 +30,39 @@ __device__ __forceinline__ void ring_init(Ring& rg) {
     fence_mbar_init();
   }
   rg.phase = 0;
+  rg.prefetched = 0;
   __syncthreads();
+}
+
+// Address and size of chunk c of this CTA's sequence (slab cta + k grid, chunk cc).
+__device__ __forceinline__ void chunk_src(const Layout& L, int cta, int grid, int c, const uint8_t*& src,
+                                          uint32_t& bytes) {
+  const int nch = (int)((L.n + L.CW - 1) / L.CW);
+  const int k = c / nch, cc = c - k * nch;
+  const int64_t s = cta + (int64_t)k * grid;
+  const int64_t col0 = (int64_t)cc * L.CW;
+  const int64_t cw = min((int64_t)L.CW, L.n - col0);
+  const int64_t col_bytes = (int64_t)L.TB * L.esize;
+  bytes = (uint32_t)(cw * col_bytes);
+  src = reinterpret_cast<const uint8_t*>(L.Z) + (s * L.n + col0) * col_bytes;
+}
+
+// Issues the first chunks of the next stream_slabs early (the ring must be idle:
+// every chunk of the previous stream consumed), so that they arrive while the
+// CTA does other work.
+__device__ __forceinline__ void ring_prefetch(const Layout& L, Ring& rg, int cta, int grid) {
+  const int nch = (int)((L.n + L.CW - 1) / L.CW);
+  const int nmy = (L.NB > cta) ? (L.NB - cta + grid - 1) / grid : 0;
+  const int pre = min(rg.stages, nmy * nch);
+  if (threadIdx.x == 0)
+    for (int c = 0; c < pre; ++c) {
+      const uint8_t* src;
+      uint32_t bytes;
+      chunk_src(L, cta, grid, c, src, bytes);
+      mbar_expect_tx(&rg.bars[c], bytes);
+      bulk_g2s(rg.buf + (size_t)c * rg.stage_bytes, src, bytes, &rg.bars[c]);
+    }
+  rg.prefetched = pre;
 }
 
 // Streams every chunk of the slabs cta, cta+grid, ... through the ring and
@@ -40,24 +73,21 @@ __device__ bool stream_slabs(const Layout& L, Ring& rg, int cta, int grid, int* 
   const int nch = (int)((L.n + L.CW - 1) / L.CW);
   const int nmy = (L.NB > cta) ? (L.NB - cta + grid - 1) / grid : 0;
   const int total = nmy * nch;
-  const uint8_t* Zb = reinterpret_cast<const uint8_t*>(L.Z);
-  const int64_t col_bytes = (int64_t)L.TB * L.esize;
 
   auto issue = [&](int c) {
-    const int k = c / nch, cc = c - k * nch;
-    const int64_t s = cta + (int64_t)k * grid;
-    const int64_t col0 = (int64_t)cc * L.CW;
-    const int64_t cw = min((int64_t)L.CW, L.n - col0);
-    const uint32_t bytes = (uint32_t)(cw * col_bytes);
+    const uint8_t* src;
+    uint32_t bytes;
+    chunk_src(L, cta, grid, c, src, bytes);
     const int st = c % rg.stages;
     mbar_expect_tx(&rg.bars[st], bytes);
-    bulk_g2s(rg.buf + (size_t)st * rg.stage_bytes, Zb + (s * L.n + col0) * col_bytes, bytes, &rg.bars[st]);
+    bulk_g2s(rg.buf + (size_t)st * rg.stage_bytes, src, bytes, &rg.bars[st]);
   };
 
   if (threadIdx.x == 0) {
     const int pre = min(rg.stages, total);
-    for (int c = 0; c < pre; ++c) issue(c);
+    for (int c = rg.prefetched; c < pre; ++c) issue(c);
   }
+  rg.prefetched = 0;
   for (int c = 0; c < total; ++c) {
     const int st = c % rg.stages;
     const int k = c / nch, cc = c - k * nch;

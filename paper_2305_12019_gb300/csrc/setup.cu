@@ -317,6 +317,119 @@ __global__ void __launch_bounds__(kThreads) gram_kernel(Layout L, int T_tiles, i
     }
 }
 
+// FP32 storage: 128 x 64 output tiles (the lower triangle's tile row I and tile
+// columns J <= 2I + 1), 8 x 4 outputs per thread, 16-row chunks staged through
+// shared memory, FP32 sums of 32 rows folded into double-float (the rounding
+// profile of gram_kernel<float> with twice the rows per fold, and twice the
+// multiply-adds per shared-memory read).
+constexpr int kG32I = 128, kG32J = 64, kG32K = 16;
+
+__device__ __forceinline__ int g32_tiles_j(int I, int Tj) { return (2 * I + 2 < Tj) ? 2 * I + 2 : Tj; }
+
+__global__ void __launch_bounds__(kThreads) gram32_kernel(Layout L, int Ti, int Tj, int ksplit, double* Kpart) {
+  __shared__ __align__(16) float As[kG32K][kG32I];
+  __shared__ __align__(16) float Bs[kG32K][kG32J];
+  // tile index -> (I, J): tile rows I hold g32_tiles_j(I) tiles each
+  int tile = blockIdx.x / ksplit;
+  const int sp = blockIdx.x % ksplit;
+  int I = 0;
+  while (tile >= g32_tiles_j(I, Tj)) {
+    tile -= g32_tiles_j(I, Tj);
+    ++I;
+  }
+  const int J = tile;
+  const int s0 = (int)((int64_t)L.NB * sp / ksplit), s1 = (int)((int64_t)L.NB * (sp + 1) / ksplit);
+  const int t = threadIdx.x;
+  const int ti = t >> 4, tj = t & 15;            // outputs rows ti*8.., columns tj*4..
+  // loader roles: A: column t % 128, rows 8 (t / 128) .. +8; B: column t % 64, rows 4 (t / 64) .. +4
+  const int ca = t & 127, ra = (t >> 7) * 8;
+  const int cb = t & 63, rb = (t >> 6) * 4;
+  const int64_t gca = (int64_t)I * kG32I + ca, gcb = (int64_t)J * kG32J + cb;
+  const float* Zs = reinterpret_cast<const float*>(L.Z);
+  float acc[8][4];
+  df sum[8][4];
+#pragma unroll
+  for (int p = 0; p < 8; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      acc[p][q] = 0.f;
+      sum[p][q] = df{0.f, 0.f};
+    }
+  // chunk sequence: (slab s, first row r0) for s in [s0, s1), r0 = 0, 16, .. < TB; the
+  // loads of the next chunk are issued before the current one is computed
+  const int per = (L.TB + kG32K - 1) / kG32K;
+  const int nchunk = (s1 - s0) * per;
+  auto load = [&](int c, float4& a0, float4& a1, float4& b0) {
+    a0 = make_float4(0.f, 0.f, 0.f, 0.f);
+    a1 = a0;
+    b0 = a0;
+    if (c >= nchunk) return;
+    const int s = s0 + c / per, r0 = (c % per) * kG32K;
+    const float* slab = Zs + (int64_t)s * L.TB * L.n;
+    // rows beyond the slab and columns beyond n are zero (TB is a multiple of 4)
+    if (gca < L.n) {
+      const float* pa = slab + gca * L.TB + r0 + ra;
+      if (r0 + ra < L.TB) a0 = *reinterpret_cast<const float4*>(pa);
+      if (r0 + ra + 4 < L.TB) a1 = *reinterpret_cast<const float4*>(pa + 4);
+    }
+    if (gcb < L.n && r0 + rb < L.TB) b0 = *reinterpret_cast<const float4*>(slab + gcb * L.TB + r0 + rb);
+  };
+  float4 a0, a1, b0;
+  load(0, a0, a1, b0);
+  int since_fold = 0;
+  for (int c = 0; c < nchunk; ++c) {
+    __syncthreads();   // the previous chunk's reads are done
+    As[ra + 0][ca] = a0.x; As[ra + 1][ca] = a0.y; As[ra + 2][ca] = a0.z; As[ra + 3][ca] = a0.w;
+    As[ra + 4][ca] = a1.x; As[ra + 5][ca] = a1.y; As[ra + 6][ca] = a1.z; As[ra + 7][ca] = a1.w;
+    Bs[rb + 0][cb] = b0.x; Bs[rb + 1][cb] = b0.y; Bs[rb + 2][cb] = b0.z; Bs[rb + 3][cb] = b0.w;
+    __syncthreads();
+    load(c + 1, a0, a1, b0);
+#pragma unroll
+    for (int k = 0; k < kG32K; ++k) {
+      const float4 x0 = *reinterpret_cast<const float4*>(&As[k][ti * 8]);
+      const float4 x1 = *reinterpret_cast<const float4*>(&As[k][ti * 8 + 4]);
+      const float4 y = *reinterpret_cast<const float4*>(&Bs[k][tj * 4]);
+      const float av[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+      const float bv[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+      for (int p = 0; p < 8; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(av[p], bv[q], acc[p][q]);
+    }
+    since_fold += kG32K;
+    if (since_fold >= 32) {
+#pragma unroll
+      for (int p = 0; p < 8; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          df_add(sum[p][q], acc[p][q]);
+          acc[p][q] = 0.f;
+        }
+      since_fold = 0;
+    }
+  }
+  const int64_t n = L.n;
+  double* out = Kpart + (int64_t)sp * n * n;
+#pragma unroll
+  for (int p = 0; p < 8; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      df v = sum[p][q];
+      df_add(v, acc[p][q]);
+      const int64_t i = (int64_t)I * kG32I + ti * 8 + p, j = (int64_t)J * kG32J + tj * 4 + q;
+      if (i < n && j < n && i >= j) out[i * n + j] = df_to_double(v);
+    }
+}
+
+int gram32_ksplit(const Layout& L, int sms) {
+  const int Ti = (int)((L.n + kG32I - 1) / kG32I), Tj = (int)((L.n + kG32J - 1) / kG32J);
+  int tiles = 0;
+  for (int I = 0; I < Ti; ++I) tiles += std::min(2 * I + 2, Tj);
+  int ks = std::max(1, sms / tiles);   // one wave of CTAs (one per SM)
+  ks = std::min(ks, std::max(1, L.NB));
+  return std::min(ks, 16);
+}
+
 // G_ij = delta_ij + sc_i sc_j sum_split K_ij / mu, both triangles.
 __global__ void gram_finish_kernel(const double* Kpart, int ksplit, const double* sc, int64_t n, double inv_mu,
                                    double* G) {
@@ -334,6 +447,7 @@ __global__ void gram_finish_kernel(const double* Kpart, int ksplit, const double
 }
 
 int gram_ksplit(const Layout& L, int sms) {
+  if (L.esize == 4) return gram32_ksplit(L, sms);
   const int Tt = (int)((L.n + kGT - 1) / kGT);
   const int tiles = Tt * (Tt + 1) / 2;
   int ks = std::max(1, (2 * sms + tiles - 1) / tiles);
@@ -355,7 +469,13 @@ cudaError_t run_gram(int store, const Layout& L, int ksplit, double* Kpart, cons
       case GDWD_BF16: gram_kernel<__nv_bfloat16><<<grid, kThreads, 0, st>>>(L, Tt, ksplit, Kpart); break;
       case GDWD_F16: gram_kernel<__half><<<grid, kThreads, 0, st>>>(L, Tt, ksplit, Kpart); break;
       case GDWD_E4M3: gram_kernel<__nv_fp8_e4m3><<<grid, kThreads, 0, st>>>(L, Tt, ksplit, Kpart); break;
-      default: gram_kernel<float><<<grid, kThreads, 0, st>>>(L, Tt, ksplit, Kpart); break;
+      default: {
+        const int Ti = (int)((L.n + kG32I - 1) / kG32I), Tj = (int)((L.n + kG32J - 1) / kG32J);
+        int tiles32 = 0;
+        for (int I = 0; I < Ti; ++I) tiles32 += std::min(2 * I + 2, Tj);
+        gram32_kernel<<<tiles32 * ksplit, kThreads, 0, st>>>(L, Ti, Tj, ksplit, Kpart);
+        break;
+      }
     }
     e = cudaGetLastError();
   }

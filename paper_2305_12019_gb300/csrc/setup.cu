@@ -550,6 +550,34 @@ __device__ __forceinline__ void tri_index(int t, int& i, int& j) {
   j = t - ii * (ii + 1) / 2;
 }
 
+// Cholesky of the 32 x 32 FP64 tile D (lower triangle, in place) by all threads
+// of the CTA, column by column: pivot, column scaling, then the trailing rank-1
+// update spread over the threads.  Dinv receives the reciprocals of the diagonal.
+// A non-positive pivot records GDWD_ENOTPD (and continues with 1).
+__device__ void chol_tile(double (*D)[kNB + 1], double* Dinv, int* err) {
+  for (int c = 0; c < kNB; ++c) {
+    if (threadIdx.x == 0) {
+      double piv = D[c][c];
+      if (!(piv > 0.0) || !isfinite(piv)) {
+        atomicCAS(err, 0, (int)GDWD_ENOTPD);
+        piv = 1.0;
+      }
+      const double lc = sqrt_nr(piv);
+      D[c][c] = lc;
+      Dinv[c] = rcp_nr(lc);
+    }
+    __syncthreads();
+    if (threadIdx.x > c && threadIdx.x < kNB) D[threadIdx.x][c] *= Dinv[c];
+    __syncthreads();
+    const int m = kNB - 1 - c;
+    for (int e = threadIdx.x; e < m * m; e += kThreads) {
+      const int r = c + 1 + e / m, q = c + 1 + e % m;
+      if (q <= r) D[r][q] -= D[r][c] * D[q][c];
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void __launch_bounds__(kThreads, 1) factor_kernel(FactorArgs a) {
   __shared__ float2 T0[kNB][kNB + 1], T1[kNB][kNB + 1], T2[kNB][kNB + 1];
   __shared__ double D[kNB][kNB + 1];     // FP64 diagonal tile
@@ -576,53 +604,20 @@ __global__ void __launch_bounds__(kThreads, 1) factor_kernel(FactorArgs a) {
   }
   FBAR();
 
-  // ---------------- Cholesky, right-looking over tile columns
+  // ---------------- Cholesky, right-looking over tile columns.  Every CTA factors
+  // the diagonal tile itself (all threads, FP64) and solves its panel rows with it,
+  // so no grid barrier separates the two; CTA 0 writes the factored tile back
+  // during the trailing update, which does not touch it.
   for (int k = 0; k < nb; ++k) {
     const int64_t k0 = (int64_t)k * kNB;
-    if (cta == 0) {
-      // FP64 unblocked Cholesky of the diagonal tile by warp 0 (lane = row)
-      for (int t = threadIdx.x; t < kNB * kNB; t += kThreads) {
-        const int r = t / kNB, c = t % kNB;
-        const int64_t gr = k0 + r, gc = k0 + c;
-        D[r][c] = (gr < n && gc < n) ? f2d(A[gr * n + gc]) : (gr == gc ? 1.0 : 0.0);
-      }
-      __syncthreads();
-      if (warp == 0) {
-        for (int c = 0; c < kNB; ++c) {
-          double piv = D[c][c];
-          if (!(piv > 0.0) || !isfinite(piv)) {
-            if (lane == 0) atomicCAS(a.err, 0, (int)GDWD_ENOTPD);
-            piv = 1.0;
-          }
-          const double lc = sqrt_nr(piv);
-          const double ilc = rcp_nr(lc);
-          __syncwarp();
-          if (lane > c) D[lane][c] *= ilc;
-          __syncwarp();
-          if (lane == 0) D[c][c] = lc;
-          __syncwarp();
-          if (lane > c)
-            for (int cc = c + 1; cc <= lane; ++cc) D[lane][cc] -= D[lane][c] * D[cc][c];
-          __syncwarp();
-        }
-      }
-      __syncthreads();
-      for (int t = threadIdx.x; t < kNB * kNB; t += kThreads) {
-        const int r = t / kNB, c = t % kNB;
-        const int64_t gr = k0 + r, gc = k0 + c;
-        if (gr < n && gc < n && c <= r) A[gr * n + gc] = d2f(D[r][c]);
-      }
-    }
-    FBAR();
-    // panel rows below the diagonal tile: L_ik = A_ik L_kk^{-T}, one warp per row (FP64)
     for (int t = threadIdx.x; t < kNB * kNB; t += kThreads) {
       const int r = t / kNB, c = t % kNB;
       const int64_t gr = k0 + r, gc = k0 + c;
       D[r][c] = (gr < n && gc < n) ? f2d(A[gr * n + gc]) : (gr == gc ? 1.0 : 0.0);
     }
     __syncthreads();
-    if (threadIdx.x < kNB) Dinv[threadIdx.x] = rcp_nr(D[threadIdx.x][threadIdx.x]);
-    __syncthreads();
+    chol_tile(D, Dinv, a.err);
+    // panel rows below the diagonal tile: L_ik = A_ik L_kk^{-T}, one warp per row (FP64)
     for (int64_t i = k0 + kNB + (int64_t)cta * kWarps + warp; i < n; i += (int64_t)grid * kWarps) {
       double x = (k0 + lane < n) ? f2d(A[i * n + k0 + lane]) : 0.0;
       for (int c = 0; c < kNB; ++c) {
@@ -633,6 +628,13 @@ __global__ void __launch_bounds__(kThreads, 1) factor_kernel(FactorArgs a) {
       if (k0 + lane < n) A[i * n + k0 + lane] = d2f(x);
     }
     FBAR();
+    if (cta == 0) {
+      for (int t = threadIdx.x; t < kNB * kNB; t += kThreads) {
+        const int r = t / kNB, c = t % kNB;
+        const int64_t gr = k0 + r, gc = k0 + c;
+        if (gr < n && gc < n && c <= r) A[gr * n + gc] = d2f(D[r][c]);
+      }
+    }
     // trailing update A_IJ -= L_Ik L_Jk^T for tiles k < J <= I (double-float)
     {
       const int m = nb - k - 1;

@@ -575,15 +575,20 @@ static cudaError_t launch_iterate_t(const IterArgs<typename ElemTraits<T>::compu
   return cudaLaunchCooperativeKernel((const void*)kern, dim3(args.grid), dim3(kThreads), params, smem, st);
 }
 
-// Columns per streamed chunk: about 64 KB per bulk copy (on this part one SM's
-// bulk copies from L2 complete one after another, so larger copies amortise the
-// per-copy latency), at least two stages next to the phase-local buffers.
+// Columns per streamed chunk, at least two stages next to the phase-local
+// buffers.  Every chunk costs a fixed ~0.5 us of waits and barriers on top of its
+// bytes, so chunks are large: about 96 KB (two or three stages) when the stored Z
+// fits in L2 and the pass is served from there, about 64 KB (three or more stages,
+// more copies in flight) when it streams from HBM (measured on the spiked FP32
+// workload at d = 20000 and 40000).
 template <typename T>
 static int choose_cw_t(const Layout& L, int grid, int smem_limit) {
   const int64_t ub = (int64_t)union_bytes<T>(L, grid);
   const int64_t col_bytes = (int64_t)L.TB * L.esize;
   const int64_t avail = (int64_t)smem_limit - ub - 1024;
-  int64_t cw = std::min<int64_t>(65536 / col_bytes, (avail / 2 - 128) / col_bytes);
+  const int64_t z_bytes = (int64_t)L.NB * L.TB * L.n * L.esize;
+  const int64_t target = z_bytes <= (96ll << 20) ? 98304 : 65536;
+  int64_t cw = std::min<int64_t>(target / col_bytes, (avail / 2 - 128) / col_bytes);
   cw = std::max<int64_t>(cw, 1);
   cw = std::min<int64_t>(cw, L.n);
   return (int)cw;

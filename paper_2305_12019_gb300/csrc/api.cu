@@ -447,8 +447,22 @@ static IterArgs<CT> make_args(gdwd_handle* h, double C, double sigma0, int refre
 // One solve for penalty C.  warm == NULL starts from the initial iterate of
 // reading R3; otherwise the iterate (and sigma) of the last solve of `warm` (a
 // handle of the same problem with another storage type) is the starting point.
+// A state to start a solve from: another handle's last iterate (refinement sweep,
+// iteration count restarts) or one instance of the joint C-grid kernel (it
+// continues, counting on).
+struct WarmSrc {
+  const double *r, *xi, *alpha, *u, *rho, *g;
+  const Ctrl* ctrl;           // device
+  cudaStream_t stream;
+  bool keep_count;
+};
+
+static WarmSrc warm_from(const gdwd_handle* o) {
+  return WarmSrc{o->r, o->xi, o->alpha, o->u, o->rho, o->g, o->ctrl, o->stream, false};
+}
+
 static gdwd_status solve_one(gdwd_handle* h, double C, double* w, int w_on_device, double* alpha, gdwd_result* res,
-                             gdwd_handle* warm = nullptr) {
+                             const WarmSrc* warm = nullptr) {
   const int64_t n = h->n, d = h->d;
   const int64_t dpad = (int64_t)h->L.NB * h->L.TB;
   cudaStream_t st = h->stream;
@@ -478,7 +492,7 @@ static gdwd_status solve_one(gdwd_handle* h, double C, double* w, int w_on_devic
     CK(cudaMemcpyAsync(h->rho, warm->rho, db, cudaMemcpyDeviceToDevice, st), "warm copy");
     CK(cudaMemcpyAsync(h->g, warm->g, db, cudaMemcpyDeviceToDevice, st), "warm copy");
     CK(cudaMemcpy(&c0, warm->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost), "warm ctrl");
-    c0.it = 0;
+    if (!warm->keep_count) c0.it = 0;
     c0.status = 0;
     c0.done = 0;
   }
@@ -617,6 +631,7 @@ static gdwd_status solve_multi(gdwd_handle* h, const double* Cs, int K, int kker
     a.Ur = m.Ur;
     a.kc = m.kc;
     a.dots_every = dots_every_of(h);
+    a.min_active = K > 1 ? 2 : 1;   // a lone straggler continues in the single-instance kernel
     a.u = m.u;
     a.rho = m.rho;
     a.g = m.g;
@@ -687,6 +702,22 @@ static gdwd_status solve_multi(gdwd_handle* h, const double* Cs, int K, int kker
     if (r->status != GDWD_OK && worst == GDWD_OK) worst = (gdwd_status)r->status;
   }
   if (kerr) return fail(h, (gdwd_status)kerr, "gdwd_solve: joint kernel stopped with a device error");
+  // an instance still iterating when the others had stopped: continue it from its
+  // state in the single-instance kernel (which does the work of one instance, where
+  // the joint kernel would still pay for K)
+  for (int j = 0; j < K; ++j) {
+    if (c[j].status != GDWD_EMAXITER || c[j].it >= h->opt.max_iter) continue;
+    const WarmSrc ws{m.r + (size_t)j * n, m.xi + (size_t)j * n, m.alpha + (size_t)j * n, m.u + (size_t)j * dpad,
+                     m.rho + (size_t)j * dpad, m.g + (size_t)j * dpad, m.ctrl + j, st, true};
+    const float joint_ms = ms;
+    const gdwd_status sj = solve_one(h, Cs[j], w ? w + (size_t)j * d : nullptr, w_on_device,
+                                     alpha ? alpha + (size_t)j * n : nullptr, res + j, &ws);
+    res[j].t_solve_ms += joint_ms;
+    if (sj != GDWD_OK && sj != GDWD_EMAXITER) return sj;
+  }
+  worst = GDWD_OK;
+  for (int j = 0; j < K; ++j)
+    if (res[j].status != GDWD_OK && worst == GDWD_OK) worst = (gdwd_status)res[j].status;
   return worst;
 }
 
@@ -722,8 +753,9 @@ extern "C" gdwd_status gdwd_solve(gdwd_handle* h, const double* Cs, int32_t nC, 
       gdwd_result rq;
       s = solve_one(h, C, nullptr, 0, nullptr, &rq);
       if (s != GDWD_OK && s != GDWD_EMAXITER) return s;
+      const WarmSrc ws = warm_from(h);
       s = solve_one(h->master, C, w ? w + (size_t)k * h->d : nullptr, w_on_device,
-                    alpha ? alpha + (size_t)k * h->n : nullptr, res + k, h);
+                    alpha ? alpha + (size_t)k * h->n : nullptr, res + k, &ws);
       res[k].iters += rq.iters;
       res[k].t_solve_ms += rq.t_solve_ms;
       res[k].t_setup_ms = h->t_setup_ms + h->master->t_setup_ms;

@@ -414,7 +414,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_multi_kernel(MultiArgs<ty
   float* s_redf = reinterpret_cast<float*>(s_red);
   int it = 0;
   bool dots_prev = false;   // the last pass B took the column dots
-  for (; it < a.max_iter && act; ++it) {
+  for (; it < a.max_iter && act && __popc(act) >= a.min_active; ++it) {
     ring_prefetch(L, rg, cta, grid);   // this iteration's first Z chunks arrive during R, N1, N2
     // ---------------- R (this CTA's rows, every active instance): U_g from the
     // pass-B column dots and (G - I) c, the deferred n-space update, b, rhs1

@@ -136,6 +136,7 @@ struct MultiArgs {
   float2 *rhsA, *rhsB;          // [K][n]
   double *Uu, *Ur, *kc;         // [K][n]: Z~^T u_j, Z~^T rho_j (rows of the owning CTA), (G - I) c_j
   int dots_every;               // as in IterArgs
+  int min_active;               // stop when fewer instances than this are still iterating
   CT* partial;                  // [K][n][NB]: column dots Z~^T u_j of pass B
   CT* coef;                     // [n][2K]: sc_i c_ij (j < K), then sc_i alpha_ij
   double *u, *rho, *g;          // [K][dpad]

@@ -551,31 +551,45 @@ __device__ __forceinline__ void tri_index(int t, int& i, int& j) {
 }
 
 // Cholesky of the 32 x 32 FP64 tile D (lower triangle, in place) by all threads
-// of the CTA, column by column: pivot, column scaling, then the trailing rank-1
-// update spread over the threads.  Dinv receives the reciprocals of the diagonal.
-// A non-positive pivot records GDWD_ENOTPD (and continues with 1).
-__device__ void chol_tile(double (*D)[kNB + 1], double* Dinv, int* err) {
-  for (int c = 0; c < kNB; ++c) {
-    if (threadIdx.x == 0) {
-      double piv = D[c][c];
-      if (!(piv > 0.0) || !isfinite(piv)) {
-        atomicCAS(err, 0, (int)GDWD_ENOTPD);
-        piv = 1.0;
-      }
-      const double lc = sqrt_nr(piv);
-      D[c][c] = lc;
-      Dinv[c] = rcp_nr(lc);
-    }
-    __syncthreads();
-    if (threadIdx.x > c && threadIdx.x < kNB) D[threadIdx.x][c] *= Dinv[c];
-    __syncthreads();
-    const int m = kNB - 1 - c;
-    for (int e = threadIdx.x; e < m * m; e += kThreads) {
-      const int r = c + 1 + e / m, q = c + 1 + e % m;
-      if (q <= r) D[r][q] -= D[r][c] * D[q][c];
-    }
-    __syncthreads();
+// of the CTA, column by column, with a look-ahead of one column: after column c is
+// scaled, warp 0 updates column c+1 alone and takes its pivot (sqrt and reciprocal,
+// a dependent FP64 chain) while the other warps update the rest of the trailing
+// triangle.  Dinv receives the reciprocals of the diagonal.  A non-positive pivot
+// records GDWD_ENOTPD (and continues with 1).
+__device__ __forceinline__ void chol_pivot(double (*D)[kNB + 1], double* Dinv, int c, int* err) {
+  double piv = D[c][c];
+  if (!(piv > 0.0) || !isfinite(piv)) {
+    atomicCAS(err, 0, (int)GDWD_ENOTPD);
+    piv = 1.0;
   }
+  const double lc = sqrt_nr(piv);
+  D[c][c] = lc;
+  Dinv[c] = rcp_nr(lc);
+}
+
+__device__ void chol_tile(double (*D)[kNB + 1], double* Dinv, int* err) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) chol_pivot(D, Dinv, 0, err);
+  for (int c = 0; c < kNB; ++c) {
+    __syncthreads();                                   // pivot c is in D[c][c], Dinv[c]
+    if (threadIdx.x > c && threadIdx.x < kNB) D[threadIdx.x][c] *= Dinv[c];
+    __syncthreads();                                   // column c of L is complete
+    if (c + 1 == kNB) break;
+    if (warp == 0) {
+      // column c+1 first, then its pivot
+      if (lane >= c + 1) D[lane][c + 1] -= D[lane][c] * D[c + 1][c];
+      __syncwarp();
+      if (lane == 0) chol_pivot(D, Dinv, c + 1, err);
+    } else {
+      // the rest of the trailing triangle: D[r][q] -= L[r][c] L[q][c], c+2 <= q <= r
+      const int m = kNB - 2 - c;                       // rows / columns c+2 .. 31
+      for (int e = threadIdx.x - 32; e < m * m; e += kThreads - 32) {
+        const int r = c + 2 + e / m, q = c + 2 + e % m;
+        if (q <= r) D[r][q] -= D[r][c] * D[q][c];
+      }
+    }
+  }
+  __syncthreads();
 }
 
 __global__ void __launch_bounds__(kThreads, 1) factor_kernel(FactorArgs a) {

@@ -207,7 +207,8 @@ def main():
     ap.add_argument("--d", type=int, default=20000, help="feature count (profiling of other sizes only)")
     ap.add_argument("--n", type=int, default=1000, help="sample count (profiling of other sizes only)")
     ap.add_argument("--workload", default="spiked_fp32",
-                    help="spiked_fp32 (default line) | plain_fp64 | cgrid_bf16 | uneven_batch | served | largest_fp8")
+                    help="spiked_fp32 (default line) | plain_fp64 | cgrid_bf16 | uneven_batch | served | largest_fp8 | "
+                         "kernelized")
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
@@ -217,6 +218,8 @@ def main():
     ap.add_argument("--cg-n", type=int, default=2000)
     ap.add_argument("--big-d", type=int, default=200000)
     ap.add_argument("--big-n", type=int, default=5000)
+    ap.add_argument("--kern-wide-d", type=int, default=200000)
+    ap.add_argument("--kern-steps", type=int, default=3)
     args = ap.parse_args()
     if args.workload != "spiked_fp32" and args.impl != "reference":
         import bench_workloads

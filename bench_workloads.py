@@ -14,6 +14,11 @@ stand-ins for the paper's data sets (see paper_2305_12019_gb300/synth.py).
                 on the device per request seed: p50 / p99 latency and solves/s
   largest_fp8   d=200000, n=5000, Student-t columns, 1:3, 16 values of C, E4M3
                 storage with the FP32 refinement sweep: C-solves/s
+  kernelized    the kernelized n-space iteration (no pass over Z per iteration)
+                against the Z-streaming one: the spiked FP32 bench instance
+                (d=20000, n=1000), a wide spiked FP32 instance (d=200000,
+                n=1000, Z 800 MB > L2) and the cgrid_bf16 grid (32 C, one at a
+                time): solves/s of both, per-iteration time, iterations
 """
 from __future__ import annotations
 
@@ -225,8 +230,72 @@ def largest_fp8(args, gdwd, synth):
             "converged": int(sum(r["status"] == 0 for r in res)), "certified_gap_C_ends": gaps}
 
 
+def _timed_steps(gdwd, Zd, inst, steps, **kw):
+    """Full create + solve + free steps (one warm-up): mean seconds, last result."""
+    torch = _torch()
+    out = None
+    times = []
+    for k in range(steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with gdwd.Solver(Zd, inst.y, inst.q, inst.C, tol=inst.tol, **kw) as s:
+            res, w, _ = s.solve()
+            info = s.info()
+            ph = s.phase_times()
+        torch.cuda.synchronize()
+        if k:
+            times.append(time.perf_counter() - t0)
+        out = (res[0], w[:, 0], info, ph)
+    return float(np.mean(times)), out
+
+
+def kernelized(args, gdwd, synth):
+    torch = _torch()
+    line = {"metric": "gDWD solves/s at KKT<=1e-6, kernelized n-space iteration", "unit": "solves/s"}
+    cases = {}
+    for name, d in (("spiked_fp32_d20000_n1000", 20000), ("spiked_fp32_d200000_n1000", args.kern_wide_d)):
+        inst = synth.spiked_fp32(d=d, m_test=0)
+        Zd = _device_colmajor(inst.Z)
+        row = {}
+        for label, k in (("streaming", 0), ("kernelized", 1)):
+            t, (r, w, info, ph) = _timed_steps(gdwd, Zd, inst, args.kern_steps, store="f32", kernelized=k)
+            row[label] = {"solves_per_s": 1.0 / t, "step_ms": t * 1e3, "iters": r["iters"], "kkt": r["kkt"],
+                          "status": r["status"], "solve_ms": r["t_solve_ms"], "setup_ms": info["t_setup_ms"],
+                          "us_per_iter": 1e3 * r["t_solve_ms"] / max(1, r["iters"]),
+                          "phase_us_per_iter": {kk: v / 1e3 / max(1, r["iters"]) for kk, v in ph.items() if v}}
+            row[label + "_w"] = w
+        row["rel_w_kernelized_vs_streaming"] = float(np.linalg.norm(row["kernelized_w"] - row["streaming_w"]) /
+                                                     np.linalg.norm(row["streaming_w"]))
+        del row["kernelized_w"], row["streaming_w"]
+        row["speedup"] = row["kernelized"]["solves_per_s"] / row["streaming"]["solves_per_s"]
+        cases[name] = row
+        del Zd
+        torch.cuda.empty_cache()
+    # the C grid of cgrid_bf16, one C after the other on the kernelized iteration
+    inst = synth.gaussian(seed=3001, d=args.cg_d, n=args.cg_n, shift=1.5, q=1.0, C=1.0)
+    Cs = np.logspace(-2, 3, 32)
+    Zd = _device_colmajor(inst.Z)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with gdwd.Solver(Zd, inst.y, 1.0, 1.0, store="bf16", tol=1e-6, kernelized=1) as s:
+        res, w, alpha = s.solve(Cs=Cs, alpha=True)
+    torch.cuda.synchronize()
+    t_grid = time.perf_counter() - t0
+    Z64 = inst.Z.astype(np.float64)
+    gaps = [O.certified_gap(Z64, inst.y, w[:, k], res[k]["beta"], alpha[:, k], 1.0, Cs[k])[2] for k in range(0, 32, 8)]
+    cases[f"cgrid_bf16_d{args.cg_d}_n{args.cg_n}_32C"] = {
+        "C_solves_per_s": 32 / t_grid, "ms": t_grid * 1e3, "iters": [r["iters"] for r in res],
+        "converged": int(sum(r["status"] == 0 for r in res)), "certified_gap_original_data_every_8th_C": gaps}
+    head = cases["spiked_fp32_d20000_n1000"]["kernelized"]
+    line.update({"value": head["solves_per_s"], "ms_per_step": head["step_ms"],
+                 "config": {"workload": "kernelized iteration: spiked_fp32 d=20000 n=1000 q=1 C=10 tol=1e-6 "
+                                        "(value); wide d=200000 and the BF16 C grid alongside", "store": "f32"},
+                 "cases": cases})
+    return line
+
+
 WORKLOADS = {"plain_fp64": plain_fp64, "cgrid_bf16": cgrid_bf16, "uneven_batch": uneven_batch, "served": served,
-             "largest_fp8": largest_fp8}
+             "largest_fp8": largest_fp8, "kernelized": kernelized}
 
 
 def run(name, args):

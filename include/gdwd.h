@@ -94,7 +94,18 @@ typedef struct {
                          iterations over which the Gram's rounding can accumulate.
                          0 (default): 16 for FP64 / FP32 storage, 4 for BF16 / FP16 /
                          E4M3 storage (tensor-core Gram); 1: every iteration.     */
-  int32_t reserved_i32;
+  int32_t kernelized; /* 0 (default): every iteration streams the stored Z once;
+                         1: the kernelized n-space iteration.  From the initial
+                         iterate w = u = rho = 0 every d-space iterate lies in the
+                         range of Z~, so the loop runs on K = Z~^T Z~ alone: two
+                         G^{-1} products and one K product with three columns per
+                         iteration, O(n^2) and independent of d, and
+                         w = Z~ (a_g + a_rho / (sigma sqrt(mu))) is formed once after
+                         the loop by one pass over Z.  Keeps K as double-float
+                         (8 n^2 bytes more).  gdwd_create returns EUNSUPPORTED when
+                         three double-float vectors of length n exceed a CTA's shared
+                         memory (n above about 9000 on GB300).  Several C values
+                         are then solved one after the other.                   */
   int64_t reserved[5];
 } gdwd_options;
 
@@ -232,7 +243,7 @@ typedef struct {
   double t_gram_ms;      /*           Gram matrix G                          */
   double t_factor_ms;    /*           Cholesky, inverse, p, s                */
   int32_t gram_tensor_cores; /* 1: the Gram ran on the tcgen05 tensor cores       */
-  int32_t reserved_;
+  int32_t kernelized;        /* 1: solves use the kernelized n-space iteration      */
 } gdwd_info;
 
 gdwd_status gdwd_get_info(const gdwd_handle* h, gdwd_info* info);
@@ -247,7 +258,9 @@ gdwd_status gdwd_get_info(const gdwd_handle* h, gdwd_info* info);
  * sub-phases split out of those: ns[11] N2 right-hand side load, ns[12] N2
  * rows of G^{-1} and p^T rhs (beta), ns[13] reduction of the per-CTA partial
  * sums, ns[14] N1 right-hand side load, ns[15] N1 rows of G^{-1} and p^T rhs
- * (the joint C-grid kernel fills ns[2..10] and ns[13]).  count (<= 16)
+ * (the joint C-grid kernel fills ns[2..10] and ns[13]; the kernelized
+ * iteration has no pass over Z and reports its K product in ns[8], ns[9] and
+ * the start-up product of a stored iterate in ns[0], ns[1]).  count (<= 16)
  * entries are written to ns (host).  Diagnostics only; the paper has no
  * counterpart.  Errors: EINVAL.
  */

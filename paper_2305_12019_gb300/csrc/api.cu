@@ -10,6 +10,7 @@
 #include <string>
 #include <vector>
 
+#include "iterate_kern.cuh"
 #include "solver.cuh"
 
 namespace gdwd {
@@ -59,6 +60,10 @@ struct gdwd_handle {
   double *Uu = nullptr, *Ur = nullptr, *kc = nullptr;   // n-space images of u, rho; (G - I) c
   void *cq = nullptr, *aq = nullptr, *partial = nullptr;
   double *u = nullptr, *rho = nullptr, *g = nullptr, *scal = nullptr, *wtmp = nullptr;
+  // kernelized iteration (opt.kernelized): K as double-float, the coefficient
+  // vectors of u, rho, g, the last K products, the GEMV right-hand sides
+  float2 *Kd = nullptr, *vdf = nullptr;
+  double *au = nullptr, *ar = nullptr, *ag = nullptr, *KG = nullptr, *KR = nullptr, *wcoef = nullptr;
   double* dscalars = nullptr;   // [0] sumsq [1] zscale [2] s
   double *amax = nullptr, *colscale = nullptr;   // per-column |max| and storage scale s_i
   unsigned* bar = nullptr;
@@ -192,6 +197,7 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
   if (opt.gram_path != 0 && opt.gram_path != 1) return fail(nullptr, GDWD_EINVAL, "gdwd_create: gram_path must be 0 or 1");
   if (opt.stop_rule != 0 && opt.stop_rule != 1) return fail(nullptr, GDWD_EINVAL, "gdwd_create: stop_rule must be 0 or 1");
   if (opt.dots_every < 0) return fail(nullptr, GDWD_EINVAL, "gdwd_create: dots_every must be >= 0");
+  if (opt.kernelized != 0 && opt.kernelized != 1) return fail(nullptr, GDWD_EINVAL, "gdwd_create: kernelized must be 0 or 1");
 
   gdwd_handle* h = new gdwd_handle();
   h->opt = opt;
@@ -232,6 +238,8 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
   plan_layout(h);
   if ((n + h->grid - 1) / h->grid > kMaxRowsPerCta)
     return bail(fail(nullptr, GDWD_EUNSUPPORTED, "gdwd_create: n too large for the n x n factor path of this build"));
+  if (opt.kernelized && n > kern_max_n(h->grid, h->smem_optin - 16384))
+    return bail(fail(nullptr, GDWD_EUNSUPPORTED, "gdwd_create: n too large for the kernelized iteration"));
   st = [&]() -> gdwd_status {
     cudaEvent_t e0, e1, evg, ef0;
     CK(cudaEventCreate(&e0), "cudaEventCreate");
@@ -280,6 +288,16 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
     CK(halloc(h, &h->g, dpad), "alloc");
     CK(halloc(h, &h->wtmp, dpad), "alloc");
     CK(halloc(h, &h->scal, (size_t)h->sms * S_COUNT), "alloc");
+    if (h->opt.kernelized) {
+      CK(halloc(h, &h->Kd, (size_t)n * h->ldP), "alloc(K)");
+      CK(halloc(h, &h->vdf, (size_t)3 * h->ldP), "alloc");
+      CK(halloc(h, &h->au, n), "alloc");
+      CK(halloc(h, &h->ar, n), "alloc");
+      CK(halloc(h, &h->ag, n), "alloc");
+      CK(halloc(h, &h->KG, n), "alloc");
+      CK(halloc(h, &h->KR, n), "alloc");
+      CK(halloc(h, &h->wcoef, n), "alloc");
+    }
     CK(halloc(h, &h->dscalars, 8), "alloc");
     CK(halloc(h, &h->bar, 4), "alloc");
     CK(halloc(h, &h->err, 4), "alloc");
@@ -346,6 +364,7 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
                     (uint64_t)(h->opt.timeout_s * 1e9)};
       ef = run_factor(fa, h->stream);
     }
+    if (ef == cudaSuccess && h->opt.kernelized) ef = run_kern_matrix(h->G, n, h->ldP, h->opt.mu, h->Kd, h->stream);
     int ferr = 0;
     if (ef == cudaSuccess) ef = cudaMemcpyAsync(&ferr, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     double hs[3] = {0, 0, 0};
@@ -444,6 +463,52 @@ static IterArgs<CT> make_args(gdwd_handle* h, double C, double sigma0, int refre
   return a;
 }
 
+static KernArgs make_kern_args(gdwd_handle* h, double C, int refresh) {
+  KernArgs a{};
+  a.P = h->P;
+  a.Kd = h->Kd;
+  a.ldP = h->ldP;
+  a.pdf = h->pdf;
+  a.p = h->p;
+  a.y = h->y;
+  a.e = h->e;
+  a.omega = h->omega;
+  a.wt = h->wt;
+  a.n = h->n;
+  a.inv_s = 1.0 / h->s;
+  a.q = h->q;
+  a.C = C;
+  a.mu = h->opt.mu;
+  a.tau = h->opt.tau;
+  a.R = h->zscale;
+  a.tol = h->opt.tol;
+  a.kappa = (h->q + 1.0) / h->q * std::pow(h->q, 1.0 / (h->q + 1.0));
+  a.max_iter = h->opt.max_iter;
+  a.stop_rule = h->opt.stop_rule;
+  a.grid = h->grid;
+  a.refresh = refresh;
+  a.timeout_ns = (uint64_t)(h->opt.timeout_s * 1e9);
+  a.r = h->r;
+  a.xi = h->xi;
+  a.alpha = h->alpha;
+  a.b = h->b;
+  a.rhsA = h->rhsA;
+  a.rhsB = h->rhsB;
+  a.Uu = h->Uu;
+  a.Ur = h->Ur;
+  a.au = h->au;
+  a.ar = h->ar;
+  a.ag = h->ag;
+  a.KG = h->KG;
+  a.KR = h->KR;
+  a.vdf = h->vdf;
+  a.scal = h->scal;
+  a.bar = h->bar;
+  a.err = h->err;
+  a.ctrl = h->ctrl;
+  return a;
+}
+
 // One solve for penalty C.  warm == NULL starts from the initial iterate of
 // reading R3; otherwise the iterate (and sigma) of the last solve of `warm` (a
 // handle of the same problem with another storage type) is the starting point.
@@ -452,13 +517,14 @@ static IterArgs<CT> make_args(gdwd_handle* h, double C, double sigma0, int refre
 // continues, counting on).
 struct WarmSrc {
   const double *r, *xi, *alpha, *u, *rho, *g;
+  const double *au, *ar, *ag;   // coefficient vectors of a kernelized handle (else NULL)
   const Ctrl* ctrl;           // device
   cudaStream_t stream;
   bool keep_count;
 };
 
 static WarmSrc warm_from(const gdwd_handle* o) {
-  return WarmSrc{o->r, o->xi, o->alpha, o->u, o->rho, o->g, o->ctrl, o->stream, false};
+  return WarmSrc{o->r, o->xi, o->alpha, o->u, o->rho, o->g, o->au, o->ar, o->ag, o->ctrl, o->stream, false};
 }
 
 static gdwd_status solve_one(gdwd_handle* h, double C, double* w, int w_on_device, double* alpha, gdwd_result* res,
@@ -488,9 +554,19 @@ static gdwd_status solve_one(gdwd_handle* h, double C, double* w, int w_on_devic
     CK(cudaMemcpyAsync(h->r, warm->r, nb, cudaMemcpyDeviceToDevice, st), "warm copy");
     CK(cudaMemcpyAsync(h->xi, warm->xi, nb, cudaMemcpyDeviceToDevice, st), "warm copy");
     CK(cudaMemcpyAsync(h->alpha, warm->alpha, nb, cudaMemcpyDeviceToDevice, st), "warm copy");
-    CK(cudaMemcpyAsync(h->u, warm->u, db, cudaMemcpyDeviceToDevice, st), "warm copy");
-    CK(cudaMemcpyAsync(h->rho, warm->rho, db, cudaMemcpyDeviceToDevice, st), "warm copy");
-    CK(cudaMemcpyAsync(h->g, warm->g, db, cudaMemcpyDeviceToDevice, st), "warm copy");
+    if (h->opt.kernelized) {
+      // the iterate is carried by its coefficient vectors; a handle without them
+      // (a Z-streaming one) cannot hand over u and rho in this form
+      if (!warm->au) return fail(h, GDWD_EUNSUPPORTED, "gdwd_solve: a kernelized solve starts only from a kernelized iterate");
+      CK(cudaMemcpyAsync(h->au, warm->au, nb, cudaMemcpyDeviceToDevice, st), "warm copy");
+      CK(cudaMemcpyAsync(h->ar, warm->ar, nb, cudaMemcpyDeviceToDevice, st), "warm copy");
+      CK(cudaMemcpyAsync(h->ag, warm->ag, nb, cudaMemcpyDeviceToDevice, st), "warm copy");
+    } else {
+      if (!warm->u) return fail(h, GDWD_EUNSUPPORTED, "gdwd_solve: a Z-streaming solve starts only from a Z-streaming iterate");
+      CK(cudaMemcpyAsync(h->u, warm->u, db, cudaMemcpyDeviceToDevice, st), "warm copy");
+      CK(cudaMemcpyAsync(h->rho, warm->rho, db, cudaMemcpyDeviceToDevice, st), "warm copy");
+      CK(cudaMemcpyAsync(h->g, warm->g, db, cudaMemcpyDeviceToDevice, st), "warm copy");
+    }
     CK(cudaMemcpy(&c0, warm->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost), "warm ctrl");
     if (!warm->keep_count) c0.it = 0;
     c0.status = 0;
@@ -505,7 +581,9 @@ static gdwd_status solve_one(gdwd_handle* h, double C, double* w, int w_on_devic
   CK(cudaEventRecord(e0, st), "event");
   cudaError_t e;
   const int smem_limit = h->smem_optin - 8192;
-  if (h->store == GDWD_F64)
+  if (h->opt.kernelized)
+    e = run_iterate_kern(make_kern_args(h, C, warm ? 1 : 0), smem_limit, st);
+  else if (h->store == GDWD_F64)
     e = run_iterate_f64(make_args<double>(h, C, sigma0, warm ? 1 : 0), smem_limit, st);
   else
     e = run_iterate_f32(h->store, make_args<float>(h, C, sigma0, warm ? 1 : 0), smem_limit, st);
@@ -515,13 +593,24 @@ static gdwd_status solve_one(gdwd_handle* h, double C, double* w, int w_on_devic
   int kerr = 0;
   CK(cudaMemcpyAsync(&c, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st), "copy ctrl");
   CK(cudaMemcpyAsync(&kerr, h->err, sizeof(int), cudaMemcpyDeviceToHost, st), "copy err");
-  const int wb = (int)std::min<int64_t>((d + 255) / 256, 2048);
   double* wdst = (w && w_on_device) ? w : h->wtmp;
-  finish_w_kernel<<<wb, 256, 0, st>>>(h->g, h->rho, h->ctrl, std::sqrt(h->opt.mu), h->zscale, d, wdst);
-  CK(cudaGetLastError(), "finish");
+  if (h->opt.kernelized) {
+    // w = Z~ (a_g + a_rho / (sigma' sqrt(mu))) / Z_scale by one pass over the stored Z
+    CK(run_kern_wcoef(h->ag, h->ar, h->ctrl, std::sqrt(h->opt.mu), h->zscale, n, h->wcoef, st), "finish");
+    CK(run_apply(h->store, h->L, 0, h->wcoef, h->sc, wdst, h->partial, std::min(h->L.NB, 4096), smem_limit, h->err,
+                 (uint64_t)(h->opt.timeout_s * 1e9), st),
+       "finish");
+  } else {
+    const int wb = (int)std::min<int64_t>((d + 255) / 256, 2048);
+    finish_w_kernel<<<wb, 256, 0, st>>>(h->g, h->rho, h->ctrl, std::sqrt(h->opt.mu), h->zscale, d, wdst);
+    CK(cudaGetLastError(), "finish");
+  }
   if (w && !w_on_device) CK(cudaMemcpyAsync(w, h->wtmp, d * sizeof(double), cudaMemcpyDeviceToHost, st), "copy w");
   if (alpha) CK(cudaMemcpyAsync(alpha, h->alpha, n * sizeof(double), cudaMemcpyDeviceToHost, st), "copy alpha");
+  int ferr = 0;
+  if (h->opt.kernelized) CK(cudaMemcpyAsync(&ferr, h->err, sizeof(int), cudaMemcpyDeviceToHost, st), "copy err");
   CK(cudaStreamSynchronize(st), "sync");
+  if (!kerr) kerr = ferr;
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
   cudaEventDestroy(e0);
@@ -708,7 +797,8 @@ static gdwd_status solve_multi(gdwd_handle* h, const double* Cs, int K, int kker
   for (int j = 0; j < K; ++j) {
     if (c[j].status != GDWD_EMAXITER || c[j].it >= h->opt.max_iter) continue;
     const WarmSrc ws{m.r + (size_t)j * n, m.xi + (size_t)j * n, m.alpha + (size_t)j * n, m.u + (size_t)j * dpad,
-                     m.rho + (size_t)j * dpad, m.g + (size_t)j * dpad, m.ctrl + j, st, true};
+                     m.rho + (size_t)j * dpad, m.g + (size_t)j * dpad, nullptr, nullptr, nullptr, m.ctrl + j, st,
+                     true};
     const float joint_ms = ms;
     const gdwd_status sj = solve_one(h, Cs[j], w ? w + (size_t)j * d : nullptr, w_on_device,
                                      alpha ? alpha + (size_t)j * n : nullptr, res + j, &ws);
@@ -732,7 +822,7 @@ extern "C" gdwd_status gdwd_solve(gdwd_handle* h, const double* Cs, int32_t nC, 
   }
   gdwd_status worst = GDWD_OK;
   // joint C-grid: groups of up to four C values per launch (one Z read per pass for all)
-  const int kmax = (count >= 2 && !h->master && !h->opt.cgrid_sequential)
+  const int kmax = (count >= 2 && !h->master && !h->opt.cgrid_sequential && !h->opt.kernelized)
                        ? multi_max_k(h->store, h->L, h->grid, h->smem_optin - 16384)
                        : 1;
   int k0 = 0;
@@ -941,6 +1031,7 @@ extern "C" gdwd_status gdwd_get_info(const gdwd_handle* h, gdwd_info* info) {
   info->t_gram_ms = h->t_stage_ms[1];
   info->t_factor_ms = h->t_stage_ms[2];
   info->gram_tensor_cores = h->gram_tc ? 1 : 0;
+  info->kernelized = h->opt.kernelized;
   return GDWD_OK;
 }
 

@@ -1,0 +1,534 @@
+// Kernelized n-space iteration of libgdwd: the loop of Algorithm 1 (Sec. 3) for
+// one value of C run on the Gram matrix alone, in ONE cooperative launch with
+// one CTA per SM and bounded grid barriers between its phases.
+//
+// From the initial iterate w = u = rho = 0 (reading R3) every d-space iterate
+// stays in the range of Z~.  The solution of eq-linsys (SMW2 form, Sec. 3.3.2,
+// solved in n-space as in the Z-streaming kernel) has w = g' - Z~ c / mu, Step 2
+// projects g = u - Z~ c / mu onto the ball (a scaling by theta) and Step 3 moves
+// rho by a multiple of the same g.  So u = Z~ a_u, rho = Z~ a_rho, g = Z~ a_g with
+//     a_g = a_u - c / mu,   a_u+ = theta a_g,
+//     a_rho+ = (1 - tau) a_rho - tau sigma sqrt(mu) (1 - theta) a_g,
+// and every d-space quantity the iteration reads is an n-space product with
+// K = Z~^T Z~:
+//     b = Z~^T g' = K a_u + K a_rho / (sigma sqrt(mu)),
+//     ||g||^2 = a_g^T K a_g,  <g, rho> = a_rho^T K a_g,  ||rho||^2 = a_rho^T K a_rho,
+//     ||Z~ alpha||^2 = alpha^T K alpha,  <Z~ alpha, rho> = alpha^T K a_rho,
+//     <Z~ alpha, g> = alpha^T K a_g.
+// One double-float GEMV with K and the three right-hand sides alpha, a_g, a_rho
+// per iteration gives all six products; K a_u and K a_rho of the next iteration
+// follow from K a_g and K a_rho by the coefficients' own update, so no product
+// is carried by a recurrence.  w = Z~ (a_g + a_rho / (sigma sqrt(mu))) is formed
+// once, after the loop, by one pass over Z.  An iteration costs two G^{-1} GEMVs
+// and one three-column K GEMV, O(n^2), and reads no Z.
+//
+//   prologue   a stored iterate: its deferred coefficient update, then U_u = K a_u,
+//              U_rho = K a_rho (two-column GEMV); the initial iterate: zeros
+//   phase R    this CTA's rows: the deferred update of a_u, a_rho, U_u, U_rho;
+//              b = U_u + U_rho / (sigma sqrt(mu)); rhs1 = b + v-bar
+//   phase N1   x-bar = G^{-1} rhs1 (double-float GEMV), beta-bar, Step 1b prox,
+//              rhs2 = b + v
+//   phase N2   x = G^{-1} rhs2, beta, c, Z~^T w; Step 2 xi, Step 3 alpha (n part);
+//              a_g; the n-space KKT sums
+//   phase K    K [alpha, a_g, a_rho] for this CTA's rows and the six products
+//   phase S    totals, KKT residuals (Sec. 4.3), duality gap, sigma rule
+//              (Sec. 4.4), stop test; identical in every CTA
+#include <algorithm>
+#include <mutex>
+
+#include "iterate_kern.cuh"
+#include "nspace.cuh"
+
+namespace gdwd {
+
+// slots of the per-CTA sums written by phase K (the N2 sums use S_RES2 .. S_DUAL_A)
+enum KernScal {
+  KS_G2 = S_G2,     // a_g^T K a_g     = ||g||^2
+  KS_GR,            // a_rho^T K a_g   = <g, rho>
+  KS_R2,            // a_rho^T K a_rho = ||rho||^2
+  KS_AR,            // alpha^T K a_rho = <Z~ alpha, rho>
+  KS_AG,            // alpha^T K a_g   = <Z~ alpha, g>
+  KS_TA2            // alpha^T K alpha = ||Z~ alpha||^2
+};
+static_assert((int)KS_TA2 < (int)S_COUNT, "phase-K sums must fit the partial-sum block");
+
+// Three products of one double-float row of K with three double-float vectors
+// held in shared memory (one warp; results in every lane).
+__device__ __forceinline__ void row_dot3(const float2* __restrict__ Krow, const float2* v0, const float2* v1,
+                                         const float2* v2, int npair, double& o0, double& o1, double& o2) {
+  const float4* K4 = reinterpret_cast<const float4*>(Krow);
+  const float4* A4 = reinterpret_cast<const float4*>(v0);
+  const float4* B4 = reinterpret_cast<const float4*>(v1);
+  const float4* C4 = reinterpret_cast<const float4*>(v2);
+  df a0{0.f, 0.f}, a1{0.f, 0.f}, b0{0.f, 0.f}, b1{0.f, 0.f}, c0{0.f, 0.f}, c1{0.f, 0.f};
+  const int lane = threadIdx.x & 31;
+  int j = lane;
+  for (; j + 32 < npair; j += 64) {
+    const float4 k0 = __ldg(K4 + j), k1 = __ldg(K4 + j + 32);
+    float4 r = A4[j];
+    df_fma(a0, df{k0.x, k0.y}, df{r.x, r.y});
+    df_fma(a1, df{k0.z, k0.w}, df{r.z, r.w});
+    r = B4[j];
+    df_fma(b0, df{k0.x, k0.y}, df{r.x, r.y});
+    df_fma(b1, df{k0.z, k0.w}, df{r.z, r.w});
+    r = C4[j];
+    df_fma(c0, df{k0.x, k0.y}, df{r.x, r.y});
+    df_fma(c1, df{k0.z, k0.w}, df{r.z, r.w});
+    r = A4[j + 32];
+    df_fma(a0, df{k1.x, k1.y}, df{r.x, r.y});
+    df_fma(a1, df{k1.z, k1.w}, df{r.z, r.w});
+    r = B4[j + 32];
+    df_fma(b0, df{k1.x, k1.y}, df{r.x, r.y});
+    df_fma(b1, df{k1.z, k1.w}, df{r.z, r.w});
+    r = C4[j + 32];
+    df_fma(c0, df{k1.x, k1.y}, df{r.x, r.y});
+    df_fma(c1, df{k1.z, k1.w}, df{r.z, r.w});
+  }
+  for (; j < npair; j += 32) {
+    const float4 k0 = __ldg(K4 + j);
+    float4 r = A4[j];
+    df_fma(a0, df{k0.x, k0.y}, df{r.x, r.y});
+    df_fma(a1, df{k0.z, k0.w}, df{r.z, r.w});
+    r = B4[j];
+    df_fma(b0, df{k0.x, k0.y}, df{r.x, r.y});
+    df_fma(b1, df{k0.z, k0.w}, df{r.z, r.w});
+    r = C4[j];
+    df_fma(c0, df{k0.x, k0.y}, df{r.x, r.y});
+    df_fma(c1, df{k0.z, k0.w}, df{r.z, r.w});
+  }
+  df_add(a0, a1);
+  df_add(b0, b1);
+  df_add(c0, c1);
+  o0 = df_to_double(df_warp_sum(a0));
+  o1 = df_to_double(df_warp_sum(b0));
+  o2 = df_to_double(df_warp_sum(c0));
+}
+
+__device__ __forceinline__ float2 to_f2(double x) {
+  const df v = df_from(x);
+  return make_float2(v.hi, v.lo);
+}
+
+__global__ void __launch_bounds__(kThreads, 1) iterate_kern_kernel(KernArgs a) {
+  extern __shared__ __align__(16) float2 vs[];        // 3 x ldP right-hand sides
+  __shared__ int s_flag;
+  __shared__ double s_tot[S_COUNT];
+  __shared__ double s_ctl[8];
+  __shared__ double s_eta[9];
+  __shared__ double s_part[kWarps * 9];
+  __shared__ float s_xh[kMaxRowsPerCta + 1], s_xl[kMaxRowsPerCta + 1];   // + the p^T rhs row
+  __shared__ double s_k[3][kMaxRowsPerCta];
+
+  const int cta = blockIdx.x, grid = a.grid;
+  const int64_t n = a.n;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t rpc = (n + grid - 1) / grid;
+  const int64_t r0 = ((int64_t)cta * rpc < n) ? (int64_t)cta * rpc : n;
+  const int nrows = (int)(((r0 + rpc < n) ? r0 + rpc : n) - r0);
+  const int npair = (int)((n + 1) / 2);
+  const int ldP = a.ldP;
+  const int qcase = q_case(a.q);
+  const double sqmu = sqrt(a.mu), inv_mu = 1.0 / a.mu;
+  const double den = 1.0 + a.C;
+  const double inv_q = 1.0 / a.q;
+  const float inv_den = (float)(1.0 / den);
+  const double sqrt_tol = sqrt(a.tol);
+  const double ac = sqmu * (1.0 - a.tau);              // Z~ alpha + ac rho enters eta_D3
+
+  unsigned gen = 0;
+  __shared__ unsigned long long s_tacc[kPhaseSlots], s_tprev;
+  const bool timing = (cta == 0 && threadIdx.x == 0);
+  if (timing) {
+    for (int k = 0; k < kPhaseSlots; ++k) s_tacc[k] = 0;
+    s_tprev = globaltimer();
+  }
+  double sig = a.ctrl->sigma, sig_prev = a.ctrl->sigma_prev, theta = a.ctrl->theta;
+  int pending = a.ctrl->pending;
+  const int it0 = a.ctrl->it;
+  int status = GDWD_EMAXITER;
+  double beta = 0.0;
+
+#define GDWD_MARK(k)                       \
+  do {                                     \
+    if (timing) {                          \
+      const uint64_t t_ = globaltimer();   \
+      s_tacc[k] += t_ - s_tprev;           \
+      s_tprev = t_;                        \
+    }                                      \
+  } while (0)
+#define GDWD_BARRIER(k)                                                                   \
+  do {                                                                                    \
+    GDWD_MARK(k);                                                                         \
+    if (!grid_barrier(a.bar, (unsigned)grid, gen, a.err, a.timeout_ns, &s_flag)) return; \
+    GDWD_MARK(k + 1);                                                                     \
+  } while (0)
+
+  // ---------------- prologue
+  if (a.refresh) {
+    // a stored iterate: its pending coefficient update, then U_u = K a_u and
+    // U_rho = K a_rho by a two-column GEMV
+    const double rcoef0 = a.tau * sig_prev * sqmu * (1.0 - theta);
+    for (int t = threadIdx.x; t < nrows; t += kThreads) {
+      const int64_t i = r0 + t;
+      double au = a.au[i], ar = a.ar[i];
+      if (pending) {
+        const double agi = a.ag[i];
+        au = theta * agi;
+        ar = (1.0 - a.tau) * ar - rcoef0 * agi;
+        a.au[i] = au;
+        a.ar[i] = ar;
+      }
+      a.vdf[i] = to_f2(au);
+      a.vdf[ldP + i] = to_f2(ar);
+    }
+    GDWD_BARRIER(0);
+    for (int64_t i = threadIdx.x; i < 2 * (int64_t)ldP; i += kThreads) {
+      const int64_t col = i % ldP;
+      vs[i] = col < n ? a.vdf[i] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int t = warp; t < nrows; t += kWarps) {
+      double ku, kr, unused;
+      row_dot3(a.Kd + (size_t)(r0 + t) * ldP, vs, vs + ldP, vs + ldP, npair, ku, kr, unused);
+      if (lane == 0) {
+        a.Uu[r0 + t] = ku;
+        a.Ur[r0 + t] = kr;
+      }
+    }
+    pending = 0;
+  } else {
+    for (int t = threadIdx.x; t < nrows; t += kThreads) {
+      const int64_t i = r0 + t;
+      a.Uu[i] = 0.0;
+      a.Ur[i] = 0.0;
+      a.au[i] = 0.0;
+      a.ar[i] = 0.0;
+      a.ag[i] = 0.0;
+    }
+  }
+  __syncthreads();
+
+  int it = it0;
+  for (; it < a.max_iter; ++it) {
+    const double inv_sig = rcp_nr(sig);
+    // ---------------- phase R (this CTA's rows): the deferred update
+    // a_u = theta a_g, a_rho <- (1 - tau) a_rho - tau sigma' sqrt(mu) (1 - theta) a_g
+    // and the same update of their images U_u = K a_u, U_rho = K a_rho from the
+    // last phase K's products; b = U_u + U_rho / (sigma sqrt(mu)); rhs1 = b + v
+    {
+      const double gsc = rcp_nr(sig * sqmu);
+      const double rcoef = a.tau * sig_prev * sqmu * (1.0 - theta);
+      for (int t = threadIdx.x; t < nrows; t += kThreads) {
+        const int64_t i = r0 + t;
+        double uu = a.Uu[i], ur = a.Ur[i];
+        if (pending) {
+          const double kg = a.KG[i], agi = a.ag[i];
+          uu = theta * kg;
+          ur = (1.0 - a.tau) * a.KR[i] - rcoef * kg;
+          a.Uu[i] = uu;
+          a.Ur[i] = ur;
+          a.au[i] = theta * agi;
+          a.ar[i] = (1.0 - a.tau) * a.ar[i] - rcoef * agi;
+        }
+        const double bi = uu + ur * gsc;
+        a.b[i] = bi;
+        const double v = a.xi[i] - a.r[i] - a.alpha[i] * inv_sig;
+        a.rhsA[i] = to_f2(bi + v);
+      }
+    }
+    GDWD_BARRIER(2);
+
+    // ---------------- phase N1: x-bar, beta-bar, Step 1b prox, rhs2
+    {
+      for (int64_t i = threadIdx.x; i < 2 * npair; i += kThreads) vs[i] = i < n ? a.rhsA[i] : make_float2(0.f, 0.f);
+      __syncthreads();
+      GDWD_MARK(14);
+      for (int t = warp; t <= nrows; t += kWarps) {
+        const df x = row_dot(t < nrows ? a.P + (size_t)(r0 + t) * ldP : a.pdf, vs, npair);
+        if (lane == 0) {
+          s_xh[t] = x.hi;
+          s_xl[t] = x.lo;
+        }
+      }
+      __syncthreads();
+      const double betabar = -((double)s_xh[nrows] + (double)s_xl[nrows]) * a.inv_s;
+      GDWD_MARK(15);
+      for (int t = threadIdx.x; t < nrows; t += kThreads) {
+        const int64_t i = r0 + t;
+        const double cbar = ((double)s_xh[t] + (double)s_xl[t]) + betabar * a.p[i];
+        const double ri = a.r[i];
+        const double rn = prox_root(cbar + ri, a.omega[i] * inv_sig, a.q, qcase, ri);
+        a.r[i] = rn;
+        const double v = a.xi[i] - rn - a.alpha[i] * inv_sig;
+        a.rhsB[i] = to_f2(a.b[i] + v);
+      }
+    }
+    GDWD_BARRIER(4);
+
+    // ---------------- phase N2: x, beta, c, Z~^T w; Step 2 (xi), Step 3 (alpha);
+    // a_g = a_u - c / mu; the right-hand sides of phase K
+    {
+      for (int64_t i = threadIdx.x; i < 2 * npair; i += kThreads) vs[i] = i < n ? a.rhsB[i] : make_float2(0.f, 0.f);
+      __syncthreads();
+      GDWD_MARK(11);
+      double s_res2 = 0, s_ya = 0, s_xica = 0, s_ams2 = 0, s_amin2 = 0, s_amax2 = 0, s_pr = 0, s_px = 0, s_du = 0;
+      for (int t = warp; t <= nrows; t += kWarps) {
+        const df x = row_dot(t < nrows ? a.P + (size_t)(r0 + t) * ldP : a.pdf, vs, npair);
+        if (lane == 0) {
+          s_xh[t] = x.hi;
+          s_xl[t] = x.lo;
+        }
+      }
+      __syncthreads();
+      beta = -((double)s_xh[nrows] + (double)s_xl[nrows]) * a.inv_s;
+      GDWD_MARK(12);
+      for (int t = threadIdx.x; t < nrows; t += kThreads) {
+        const int64_t i = r0 + t;
+        const double xv = (double)s_xh[t] + (double)s_xl[t];
+        const double c = xv + beta * a.p[i];
+        const double ri = a.r[i], al = a.alpha[i], yi = a.y[i], ce = a.C * a.e[i];
+        const double v = a.xi[i] - ri - al * inv_sig;
+        const double zw = c - v - yi * beta;                                     // Z~^T w
+        const double xin = fmax(0.0, ri - zw - yi * beta + (al - ce) * inv_sig);  // Step 2
+        const double res = zw + yi * beta + xin - ri;
+        const double an = al - a.tau * sig * res;                                // Step 3
+        a.xi[i] = xin;
+        a.alpha[i] = an;
+        const double agi = a.au[i] - c * inv_mu;                                 // g = u - Z~ c / mu
+        a.ag[i] = agi;
+        a.vdf[i] = to_f2(an);
+        a.vdf[ldP + i] = to_f2(agi);
+        a.vdf[2 * ldP + i] = to_f2(a.ar[i]);
+        const double rq1 = pow_q1(ri, a.q, qcase);
+        const double irq1 = rcp_nr(rq1);
+        const double om = a.omega[i];
+        s_res2 = fma(res, res, s_res2);
+        s_ya = fma(yi, an, s_ya);
+        s_xica = fma(xin, ce - an, s_xica);
+        const double dv = an - om * irq1;
+        s_ams2 = fma(dv, dv, s_ams2);
+        const double mn = fmin(0.0, an), mx = fmax(0.0, an - ce);
+        s_amin2 = fma(mn, mn, s_amin2);
+        s_amax2 = fma(mx, mx, s_amax2);
+        s_pr += om * inv_q * ri * irq1;           // wt^q r^-q
+        s_px = fma(a.e[i], xin, s_px);
+        s_du += dual_pow(a.wt[i] * an, a.q, qcase);
+      }
+      const double vals[9] = {s_res2, s_ya, s_xica, s_ams2, s_amin2, s_amax2, s_pr, s_px, s_du};
+      block_sum_n<9>(vals, (nrows + 31) / 32 < kWarps ? (nrows + 31) / 32 : kWarps, s_part, a.scal + cta, grid);
+    }
+    GDWD_BARRIER(6);
+
+    // ---------------- phase K: K alpha, K a_g, K a_rho for this CTA's rows and the
+    // six products of the d-space norms
+    {
+      for (int64_t i = threadIdx.x; i < 3 * (int64_t)ldP; i += kThreads) {
+        const int64_t col = i % ldP;
+        vs[i] = col < n ? a.vdf[i] : make_float2(0.f, 0.f);
+      }
+      __syncthreads();
+      for (int t = warp; t < nrows; t += kWarps) {
+        double ka, kg, kr;
+        row_dot3(a.Kd + (size_t)(r0 + t) * ldP, vs, vs + ldP, vs + 2 * ldP, npair, ka, kg, kr);
+        if (lane == 0) {
+          s_k[0][t] = ka;
+          s_k[1][t] = kg;
+          s_k[2][t] = kr;
+        }
+      }
+      __syncthreads();
+      double g2 = 0, gr = 0, r2 = 0, arho = 0, ag = 0, ta2 = 0;
+      for (int t = threadIdx.x; t < nrows; t += kThreads) {
+        const int64_t i = r0 + t;
+        const double ka = s_k[0][t], kg = s_k[1][t], kr = s_k[2][t];
+        const double al = a.alpha[i], agi = a.ag[i], ari = a.ar[i];
+        a.KG[i] = kg;
+        a.KR[i] = kr;
+        g2 = fma(agi, kg, g2);
+        gr = fma(ari, kg, gr);
+        r2 = fma(ari, kr, r2);
+        arho = fma(al, kr, arho);
+        ag = fma(al, kg, ag);
+        ta2 = fma(al, ka, ta2);
+      }
+      const double vals[6] = {g2, gr, r2, arho, ag, ta2};
+      block_sum_n<6>(vals, (nrows + 31) / 32 < kWarps ? (nrows + 31) / 32 : kWarps, s_part,
+                     a.scal + (size_t)KS_G2 * grid + cta, grid);
+    }
+    GDWD_BARRIER(8);
+
+    // ---------------- phase S: totals, KKT, sigma rule, stop test (same in every CTA)
+    for (int k = warp; k <= KS_TA2; k += kWarps) {
+      double acc = 0.0;
+      for (int c2 = lane; c2 < grid; c2 += 32) acc += a.scal[(size_t)k * grid + c2];
+      acc = warp_sum(acc);
+      if (lane == 0) s_tot[k] = acc;
+    }
+    __syncthreads();
+    GDWD_MARK(13);
+    // three independent FP64 chains on three warps, as in the Z-streaming kernel
+    if (lane == 0 && warp == 1) {
+      const double ta2 = fmax(0.0, s_tot[KS_TA2]);
+      const double pobj = s_tot[S_PRIM_R] + a.C * s_tot[S_PRIM_XI];
+      const double dobj = a.kappa * s_tot[S_DUAL_A] - a.R * sqrt_nr(ta2);
+      s_eta[0] = pobj;
+      s_eta[1] = dobj;
+      s_eta[2] = (double)((float)fabs(pobj - dobj) / (float)(1.0 + fabs(pobj) + fabs(dobj)));
+    } else if (lane == 0 && warp == 2) {
+      s_eta[3] = sqrtf((float)s_tot[S_RES2]) * inv_den;       // p1
+      s_eta[4] = sqrtf((float)s_tot[S_AMIN2]) * inv_den;      // dd1
+      s_eta[5] = sqrtf((float)s_tot[S_AMAX2]) * inv_den;      // dd2
+      s_eta[6] = fabs(s_tot[S_YA]) * inv_den;                 // c1
+      s_eta[7] = fabs(s_tot[S_XICA]) * inv_den;               // c2
+      s_eta[8] = sqrtf((float)s_tot[S_AMS2]) * inv_den;       // c3
+    }
+    double p2 = 0.0, p3 = 0.0, dd3 = 0.0, wn = 0.0, th = 1.0;
+    if (threadIdx.x == 0) {
+      const double S1 = fmax(0.0, s_tot[KS_G2]), S2 = s_tot[KS_GR], S3 = fmax(0.0, s_tot[KS_R2]);
+      // a = Z~ alpha + ac rho: ||a||^2 and <a, g> from the K products
+      const double A2 = s_tot[KS_TA2] + 2.0 * ac * s_tot[KS_AR] + ac * ac * S3;
+      const double AG = s_tot[KS_AG] + ac * S2;
+      const double gs = rcp_nr(sig * sqmu);
+      const double gnorm = sqrt_nr(S1);
+      th = (gnorm <= a.R) ? 1.0 : div_nr(a.R, gnorm);                        // Step 2 projection
+      const double w2 = fmax(0.0, S1 + 2.0 * gs * S2 + gs * gs * S3);        // ||w||^2
+      const double om = 1.0 - th;
+      const double wu2 = fmax(0.0, om * om * S1 + 2.0 * om * gs * S2 + gs * gs * S3);   // ||w - u+||^2
+      const double kap = a.tau * sig * a.mu * om;
+      const double d3 = fmax(0.0, A2 - 2.0 * kap * AG + kap * kap * S1);
+      const float wnf = sqrtf((float)w2);
+      const double wmr = (w2 - a.R * a.R) * (double)(1.0f / (wnf + (float)a.R));   // ||w|| - R
+      p2 = sqrtf((float)(a.mu * wu2)) * inv_den;
+      p3 = fmax(wmr, 0.0) * inv_den;
+      dd3 = sqrtf((float)d3) * inv_den;
+      wn = (double)wnf;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const double pobj = s_eta[0], dobj = s_eta[1], gap = s_eta[2];
+      const double p1 = s_eta[3], dd1 = s_eta[4], dd2 = s_eta[5], c1 = s_eta[6], c2 = s_eta[7], c3 = s_eta[8];
+      const double ep = fmax(p1, fmax(p2, p3)), ed = fmax(dd1, fmax(dd2, dd3)), ec = fmax(c1, fmax(c2, c3));
+      const double kkt = fmax(fmax(ep, ed), fmax(ec, gap));
+      int done = 0;
+      double sig_next = sig;
+      if (!(kkt == kkt) || isinf(kkt)) {
+        done = 1;
+        status = GDWD_ENUMERIC;
+      } else if (a.stop_rule == 0 ? kkt <= a.tol
+                                  : (fmax(ep, ed) < a.tol && fmin(ec, gap) < sqrt_tol && fmax(ec, gap) < 0.05)) {
+        done = 1;
+        status = GDWD_OK;
+      } else if (it >= 1 && fmin(ep, ed) > 1e-3 * a.tol) {                          // sigma rule, Sec. 4.4
+        const float chi = (float)ep / fmaxf((float)ed, 1e-30f);
+        const float ichi = (float)ed / fmaxf((float)ep, 1e-30f);
+        const float big = fmaxf(chi, ichi);
+        const double zeta = big > 500.f ? 2.2 : (big > 50.f ? 1.65 : 1.1);
+        if (chi > 5.f) sig_next = sig * zeta;
+        else if (ichi > 5.f) sig_next = sig / zeta;
+      }
+      s_ctl[0] = th;
+      s_ctl[1] = sig_next;
+      s_ctl[2] = done;
+      s_ctl[3] = status;
+      if (cta == 0) {
+        Ctrl* c = a.ctrl;
+        c->beta = beta;
+        c->pobj = pobj;
+        c->dobj = dobj;
+        c->kkt = kkt;
+        c->eta_p1 = p1; c->eta_p2 = p2; c->eta_p3 = p3;
+        c->eta_d1 = dd1; c->eta_d2 = dd2; c->eta_d3 = dd3;
+        c->eta_c1 = c1; c->eta_c2 = c2; c->eta_c3 = c3;
+        c->eta_gap = gap;
+        c->wnorm = wn;
+      }
+    }
+    __syncthreads();
+    GDWD_MARK(10);
+    sig_prev = sig;
+    theta = s_ctl[0];
+    sig = s_ctl[1];
+    pending = 1;
+    const bool done = s_ctl[2] != 0.0;
+    status = (int)s_ctl[3];
+    if (done) {
+      ++it;
+      break;
+    }
+  }
+  if (it >= a.max_iter && status != GDWD_OK) status = GDWD_EMAXITER;
+  if (cta == 0 && threadIdx.x == 0) {
+    Ctrl* c = a.ctrl;
+    c->sigma = sig;
+    c->sigma_prev = sig_prev;
+    c->theta = theta;
+    c->pending = pending;
+    c->it = it;
+    c->status = status;
+    c->done = 1;
+    for (int k = 0; k < kPhaseSlots; ++k) c->phase_ns[k] = (double)s_tacc[k];
+  }
+#undef GDWD_BARRIER
+#undef GDWD_MARK
+}
+
+static size_t kern_smem_bytes(int ldP) { return (size_t)3 * ldP * sizeof(float2); }
+
+int64_t kern_max_n(int grid, int smem_limit) {
+  const int64_t by_smem = ((int64_t)smem_limit / (3 * (int64_t)sizeof(float2))) & ~(int64_t)1;
+  const int64_t by_rows = (int64_t)grid * kMaxRowsPerCta;
+  return std::min(by_smem, by_rows);
+}
+
+cudaError_t run_iterate_kern(const KernArgs& a, int smem_limit, cudaStream_t st) {
+  const size_t smem = kern_smem_bytes(a.ldP);
+  if ((int64_t)smem > smem_limit || (a.n + a.grid - 1) / a.grid > kMaxRowsPerCta) return cudaErrorInvalidConfiguration;
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    attr = cudaFuncGetAttributes(&fa, iterate_kern_kernel);
+    if (attr == cudaSuccess)
+      attr = cudaFuncSetAttribute(iterate_kern_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  optin - (int)fa.sharedSizeBytes);
+  });
+  if (attr != cudaSuccess) return attr;
+  KernArgs args = a;
+  void* params[] = {(void*)&args};
+  return cudaLaunchCooperativeKernel((const void*)iterate_kern_kernel, dim3(a.grid), dim3(kThreads), params, smem, st);
+}
+
+__global__ void kern_matrix_kernel(const double* G, int64_t n, int ldP, double mu, float2* Kd) {
+  const int64_t total = n * ldP;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / ldP, j = t % ldP;
+    float2 v = make_float2(0.f, 0.f);
+    if (j < n) v = to_f2(mu * (G[i * n + j] - (i == j ? 1.0 : 0.0)));
+    Kd[t] = v;
+  }
+}
+
+cudaError_t run_kern_matrix(const double* G, int64_t n, int ldP, double mu, float2* Kd, cudaStream_t st) {
+  const int blocks = (int)std::min<int64_t>((n * ldP + 255) / 256, 4096);
+  kern_matrix_kernel<<<blocks, 256, 0, st>>>(G, n, ldP, mu, Kd);
+  return cudaGetLastError();
+}
+
+__global__ void kern_wcoef_kernel(const double* ag, const double* ar, const Ctrl* ctrl, double sqmu, double zscale,
+                                  int64_t n, double* x) {
+  const double gs = 1.0 / (ctrl->sigma_prev * sqmu);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = (ag[i] + ar[i] * gs) / zscale;
+}
+
+cudaError_t run_kern_wcoef(const double* ag, const double* ar, const Ctrl* ctrl, double sqmu, double zscale, int64_t n,
+                           double* x, cudaStream_t st) {
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 1024);
+  kern_wcoef_kernel<<<blocks, 256, 0, st>>>(ag, ar, ctrl, sqmu, zscale, n, x);
+  return cudaGetLastError();
+}
+
+}  // namespace gdwd

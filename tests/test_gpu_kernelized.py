@@ -1,0 +1,115 @@
+"""GPU parity of the kernelized n-space iteration (kernelized = 1) with the FP64 oracle.
+
+The kernelized iteration runs Algorithm 1 on K = Z~^T Z~ alone: u, rho and g are
+carried as coefficient vectors in the columns of Z~, every d-space norm is a
+quadratic form in K, and w is formed once after the loop.  In exact arithmetic
+its iterates equal those of the Z-streaming iteration, so it must reach the
+oracle's solution to the same tolerances (|d obj|/|obj| <= 1e-6,
+||dw||/||w|| <= 1e-4) in about the same number of iterations.
+"""
+import numpy as np
+import pytest
+
+from oracle import gdwd_oracle as O
+from paper_2305_12019_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+OBJ_TOL = 1e-6
+W_TOL = 1e-4
+
+
+def _compare(res, w, ref):
+    relobj = abs(res["primal_obj"] - ref["primal"]) / abs(ref["primal"])
+    relw = np.linalg.norm(w - ref["w"]) / np.linalg.norm(ref["w"])
+    assert relobj <= OBJ_TOL, relobj
+    assert relw <= W_TOL, relw
+
+
+@pytest.mark.parametrize("q,store,d,n,n_pos,C", [
+    (1.0, "f32", 4001, 203, 101, 10.0),
+    (0.5, "f64", 2500, 157, 40, 2.0),
+    (2.0, "f32", 6007, 311, 200, 5.0),
+    (4.0, "f64", 1201, 96, 70, 1.0),
+    (1.0, "f64", 150, 401, 200, 1.0),      # d < n: K is rank-deficient, G stays positive definite
+])
+def test_kernelized_matches_oracle(gdwd_lib, q, store, d, n, n_pos, C):
+    inst = synth.gaussian(seed=d + n, d=d, n=n, shift=1.0, n_pos=n_pos, q=q, C=C,
+                          dtype=np.float32 if store == "f32" else np.float64)
+    tol = 1e-8 if store == "f64" else 1e-6
+    ref = O.solve(inst.Z.astype(np.float64), inst.y, q, C, tol=1e-9)
+    with gdwd_lib.Solver(inst.Z, inst.y, q, C, store=store, tol=tol, kernelized=1) as s:
+        assert s.info()["kernelized"] == 1
+        res, w, alpha = s.solve(alpha=True)
+    r = res[0]
+    assert r["status"] == 0 and r["kkt"] <= tol, r
+    _compare(r, w[:, 0], ref)
+    up, lo, gap = O.certified_gap(inst.Z.astype(np.float64), inst.y, w[:, 0], r["beta"], alpha[:, 0], q, C)
+    assert gap <= 10 * tol
+
+
+def test_kernelized_follows_the_streaming_iteration(gdwd_lib):
+    """Same algorithm, other arithmetic: the two iterations stop within a few
+    iterations of each other and at the same point."""
+    inst = synth.gaussian(seed=5, d=8000, n=500, shift=1.0, n_pos=200, q=1.0, C=3.0, dtype=np.float64)
+    out = {}
+    for k in (0, 1):
+        with gdwd_lib.Solver(inst.Z, inst.y, 1.0, 3.0, store="f64", tol=1e-8, kernelized=k) as s:
+            res, w, _ = s.solve()
+        out[k] = (res[0], w[:, 0])
+    (r0, w0), (r1, w1) = out[0], out[1]
+    assert r0["status"] == 0 and r1["status"] == 0
+    assert abs(r0["iters"] - r1["iters"]) <= max(3, r0["iters"] // 50), (r0["iters"], r1["iters"])
+    assert abs(r0["primal_obj"] - r1["primal_obj"]) / abs(r0["primal_obj"]) <= 1e-8
+    assert np.linalg.norm(w0 - w1) / np.linalg.norm(w0) <= 1e-5
+
+
+def test_kernelized_spiked_fp32_full_size(gdwd_lib):
+    """The d = 20000, n = 1000 spiked FP32 workload through the kernelized iteration."""
+    inst = synth.spiked_fp32()
+    with gdwd_lib.Solver(inst.Z, inst.y, inst.q, inst.C, store="f32", tol=inst.tol, kernelized=1) as s:
+        res, w, alpha = s.solve(alpha=True)
+    r = res[0]
+    assert r["status"] == 0 and r["kkt"] <= inst.tol, r
+    Z64 = inst.Z.astype(np.float64)
+    up, lo, gap = O.certified_gap(Z64, inst.y, w[:, 0], r["beta"], alpha[:, 0], inst.q, inst.C)
+    assert gap <= 1e-5, gap
+    ref = O.solve(Z64, inst.y, inst.q, inst.C, tol=1e-8)
+    _compare(r, w[:, 0], ref)
+
+
+def test_kernelized_c_grid_weights_and_refinement(gdwd_lib):
+    """Several C on one handle (one after the other), weighted DWD, and the BF16
+    refinement sweep whose FP32 master starts from the quantized solve's
+    coefficient vectors."""
+    inst = synth.gaussian(seed=13, d=3000, n=180, shift=1.0, n_pos=45, q=2.0, C=1.0, dtype=np.float64)
+    Z, y = inst.Z, inst.y
+    Cs = [0.5, 3.0]
+    wt = gdwd_lib.imbalance_weights(y, 2.0)
+    with gdwd_lib.Solver(Z, y, 2.0, 1.0, store="f64", tol=1e-8, kernelized=1) as s:
+        s.set_weights(wt=wt)
+        res, w, _ = s.solve(Cs=Cs)
+    for k, C in enumerate(Cs):
+        assert res[k]["status"] == 0, res[k]
+        _compare(res[k], w[:, k], O.solve(Z, y, 2.0, C, tol=1e-10, wt=wt))
+    inst2 = synth.gaussian(seed=41, d=6007, n=301, shift=1.0, n_pos=120, q=1.0, C=2.0)
+    with gdwd_lib.Solver(inst2.Z, inst2.y, 1.0, 2.0, store="bf16", tol=1e-6, refine=1, kernelized=1) as s:
+        res, w, _ = s.solve()
+    r = res[0]
+    assert r["status"] == 0 and r["kkt"] <= 1e-6, r
+    _compare(r, w[:, 0], O.solve(inst2.Z.astype(np.float64), inst2.y, 1.0, 2.0, tol=1e-9))
+
+
+def test_kernelized_edge_cases(gdwd_lib):
+    """n = 2, d = 1; and an n beyond the shared-memory limit of the kernelized
+    iteration is refused at create time (before any device work)."""
+    X = np.array([[1.0, -1.0]])
+    y = np.array([1.0, -1.0])
+    with gdwd_lib.Solver(X * y, y, 1.0, 10.0, store="f64", tol=1e-9, kernelized=1) as s:
+        res, w, _ = s.solve()
+    assert res[0]["status"] == 0
+    assert abs(w[0, 0] - 1.0) <= 1e-6 and abs(res[0]["beta"]) <= 1e-6
+    n = 20000
+    yb = np.where(np.arange(n) % 2 == 0, 1.0, -1.0)
+    with pytest.raises(gdwd_lib.GdwdError, match="EUNSUPPORTED"):
+        gdwd_lib.Solver(np.ones((1, n)) * yb, yb, 1.0, 1.0, store="f64", kernelized=1)

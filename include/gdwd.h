@@ -102,10 +102,9 @@ typedef struct {
                          iteration, O(n^2) and independent of d, and
                          w = Z~ (a_g + a_rho / (sigma sqrt(mu))) is formed once after
                          the loop by one pass over Z.  Keeps K as double-float
-                         (8 n^2 bytes more).  gdwd_create returns EUNSUPPORTED when
-                         three double-float vectors of length n exceed a CTA's shared
-                         memory (n above about 9000 on GB300).  Several C values
-                         are then solved one after the other.                   */
+                         (8 n^2 bytes more).  Several C values are then solved one
+                         after the other.  A solve starts only from the iterate of
+                         a kernelized handle (the refinement sweep's master is one). */
   int64_t reserved[5];
 } gdwd_options;
 

@@ -274,11 +274,11 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
     CK(halloc(h, &h->xi, n), "alloc");
     CK(halloc(h, &h->alpha, n), "alloc");
     CK(halloc(h, &h->b, n), "alloc");
-    CK(halloc(h, &h->rhsA, n), "alloc");
+    CK(halloc(h, &h->rhsA, h->ldP), "alloc");   // padded to ldP (zero pair): read as pairs
     CK(halloc(h, &h->Uu, n), "alloc");
     CK(halloc(h, &h->Ur, n), "alloc");
     CK(halloc(h, &h->kc, n), "alloc");
-    CK(halloc(h, &h->rhsB, n), "alloc");
+    CK(halloc(h, &h->rhsB, h->ldP), "alloc");
     const size_t ct = h->store == GDWD_F64 ? 8 : 4;
     CK(halloc(h, (uint8_t**)&h->cq, n * ct), "alloc");
     CK(halloc(h, (uint8_t**)&h->aq, n * ct), "alloc");

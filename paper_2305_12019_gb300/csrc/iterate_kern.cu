@@ -53,7 +53,7 @@ enum KernScal {
 static_assert((int)KS_TA2 < (int)S_COUNT, "phase-K sums must fit the partial-sum block");
 
 // Three products of one double-float row of K with three double-float vectors
-// held in shared memory (one warp; results in every lane).
+// (one warp; results in every lane).
 __device__ __forceinline__ void row_dot3(const float2* __restrict__ Krow, const float2* v0, const float2* v1,
                                          const float2* v2, int npair, double& o0, double& o1, double& o2) {
   const float4* K4 = reinterpret_cast<const float4*>(Krow);
@@ -109,15 +109,38 @@ __device__ __forceinline__ float2 to_f2(double x) {
   return make_float2(v.hi, v.lo);
 }
 
+// Sum over the grid's per-CTA partials of one slot, in a fixed order (one warp;
+// up to eight loads per lane in flight; the result in every lane).
+__device__ __forceinline__ double grid_total(const double* part, int grid, int lane) {
+  double acc = 0.0;
+  for (int base = 0; base < grid; base += 256) {
+    double v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int c2 = base + lane + 32 * q;
+      v[q] = c2 < grid ? part[c2] : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc += v[q];
+  }
+  return warp_sum(acc);
+}
+
+// One CTA owns a contiguous block of at most kThreads rows of the n-space and
+// thread t holds row r0 + t of every n-vector in registers for the whole launch;
+// only the vectors other CTAs read (the right-hand sides of the GEMVs and the
+// partial sums) go through global memory.  The GEMVs read their right-hand
+// sides straight from L2 (every warp of the SM reads the same vector, so it is
+// served from L1 after the first warp).
 __global__ void __launch_bounds__(kThreads, 1) iterate_kern_kernel(KernArgs a) {
-  extern __shared__ __align__(16) float2 vs[];        // 3 x ldP right-hand sides
   __shared__ int s_flag;
   __shared__ double s_tot[S_COUNT];
   __shared__ double s_ctl[8];
   __shared__ double s_eta[9];
   __shared__ double s_part[kWarps * 9];
-  __shared__ float s_xh[kMaxRowsPerCta + 1], s_xl[kMaxRowsPerCta + 1];   // + the p^T rhs row
+  __shared__ double s_x[kMaxRowsPerCta + 1];      // GEMV results of the CTA's rows (+ the p^T rhs row)
   __shared__ double s_k[3][kMaxRowsPerCta];
+  static_assert(kMaxRowsPerCta <= kThreads, "one row per thread");
 
   const int cta = blockIdx.x, grid = a.grid;
   const int64_t n = a.n;
@@ -134,6 +157,26 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kern_kernel(KernArgs a) {
   const float inv_den = (float)(1.0 / den);
   const double sqrt_tol = sqrt(a.tol);
   const double ac = sqmu * (1.0 - a.tau);              // Z~ alpha + ac rho enters eta_D3
+  const int nw = (nrows + 31) / 32 < kWarps ? (nrows + 31) / 32 : kWarps;   // warps holding rows
+
+  // this thread's row
+  const int tr = threadIdx.x;
+  const bool mine = tr < nrows;
+  const int64_t i = r0 + tr;
+  double yi = 0, pi = 0, ce = 0, omi = 0, wti = 0, ei = 0;
+  double ri = 0, xii = 0, ali = 0, bi = 0;
+  double Uu = 0, Ur = 0, au = 0, ar = 0, ag = 0, KG = 0, KR = 0;
+  if (mine) {
+    yi = a.y[i];
+    pi = a.p[i];
+    ei = a.e[i];
+    ce = a.C * ei;
+    omi = a.omega[i];
+    wti = a.wt[i];
+    ri = a.r[i];
+    xii = a.xi[i];
+    ali = a.alpha[i];
+  }
 
   unsigned gen = 0;
   __shared__ unsigned long long s_tacc[kPhaseSlots], s_tprev;
@@ -167,100 +210,69 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kern_kernel(KernArgs a) {
   if (a.refresh) {
     // a stored iterate: its pending coefficient update, then U_u = K a_u and
     // U_rho = K a_rho by a two-column GEMV
-    const double rcoef0 = a.tau * sig_prev * sqmu * (1.0 - theta);
-    for (int t = threadIdx.x; t < nrows; t += kThreads) {
-      const int64_t i = r0 + t;
-      double au = a.au[i], ar = a.ar[i];
+    if (mine) {
+      au = a.au[i];
+      ar = a.ar[i];
       if (pending) {
+        const double rcoef0 = a.tau * sig_prev * sqmu * (1.0 - theta);
         const double agi = a.ag[i];
         au = theta * agi;
         ar = (1.0 - a.tau) * ar - rcoef0 * agi;
-        a.au[i] = au;
-        a.ar[i] = ar;
       }
       a.vdf[i] = to_f2(au);
       a.vdf[ldP + i] = to_f2(ar);
     }
     GDWD_BARRIER(0);
-    for (int64_t i = threadIdx.x; i < 2 * (int64_t)ldP; i += kThreads) {
-      const int64_t col = i % ldP;
-      vs[i] = col < n ? a.vdf[i] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
     for (int t = warp; t < nrows; t += kWarps) {
       double ku, kr, unused;
-      row_dot3(a.Kd + (size_t)(r0 + t) * ldP, vs, vs + ldP, vs + ldP, npair, ku, kr, unused);
+      row_dot3(a.Kd + (size_t)(r0 + t) * ldP, a.vdf, a.vdf + ldP, a.vdf + ldP, npair, ku, kr, unused);
       if (lane == 0) {
-        a.Uu[r0 + t] = ku;
-        a.Ur[r0 + t] = kr;
+        s_k[0][t] = ku;
+        s_k[1][t] = kr;
       }
     }
-    pending = 0;
-  } else {
-    for (int t = threadIdx.x; t < nrows; t += kThreads) {
-      const int64_t i = r0 + t;
-      a.Uu[i] = 0.0;
-      a.Ur[i] = 0.0;
-      a.au[i] = 0.0;
-      a.ar[i] = 0.0;
-      a.ag[i] = 0.0;
+    __syncthreads();
+    if (mine) {
+      Uu = s_k[0][tr];
+      Ur = s_k[1][tr];
     }
+    pending = 0;
   }
-  __syncthreads();
 
   int it = it0;
   for (; it < a.max_iter; ++it) {
     const double inv_sig = rcp_nr(sig);
-    // ---------------- phase R (this CTA's rows): the deferred update
+    // ---------------- phase R (this thread's row): the deferred update
     // a_u = theta a_g, a_rho <- (1 - tau) a_rho - tau sigma' sqrt(mu) (1 - theta) a_g
     // and the same update of their images U_u = K a_u, U_rho = K a_rho from the
     // last phase K's products; b = U_u + U_rho / (sigma sqrt(mu)); rhs1 = b + v
-    {
-      const double gsc = rcp_nr(sig * sqmu);
-      const double rcoef = a.tau * sig_prev * sqmu * (1.0 - theta);
-      for (int t = threadIdx.x; t < nrows; t += kThreads) {
-        const int64_t i = r0 + t;
-        double uu = a.Uu[i], ur = a.Ur[i];
-        if (pending) {
-          const double kg = a.KG[i], agi = a.ag[i];
-          uu = theta * kg;
-          ur = (1.0 - a.tau) * a.KR[i] - rcoef * kg;
-          a.Uu[i] = uu;
-          a.Ur[i] = ur;
-          a.au[i] = theta * agi;
-          a.ar[i] = (1.0 - a.tau) * a.ar[i] - rcoef * agi;
-        }
-        const double bi = uu + ur * gsc;
-        a.b[i] = bi;
-        const double v = a.xi[i] - a.r[i] - a.alpha[i] * inv_sig;
-        a.rhsA[i] = to_f2(bi + v);
+    if (mine) {
+      if (pending) {
+        const double rcoef = a.tau * sig_prev * sqmu * (1.0 - theta);
+        Uu = theta * KG;
+        Ur = (1.0 - a.tau) * KR - rcoef * KG;
+        au = theta * ag;
+        ar = (1.0 - a.tau) * ar - rcoef * ag;
       }
+      bi = Uu + Ur * rcp_nr(sig * sqmu);
+      a.rhsA[i] = to_f2(bi + (xii - ri - ali * inv_sig));
     }
     GDWD_BARRIER(2);
 
     // ---------------- phase N1: x-bar, beta-bar, Step 1b prox, rhs2
     {
-      for (int64_t i = threadIdx.x; i < 2 * npair; i += kThreads) vs[i] = i < n ? a.rhsA[i] : make_float2(0.f, 0.f);
-      __syncthreads();
       GDWD_MARK(14);
       for (int t = warp; t <= nrows; t += kWarps) {
-        const df x = row_dot(t < nrows ? a.P + (size_t)(r0 + t) * ldP : a.pdf, vs, npair);
-        if (lane == 0) {
-          s_xh[t] = x.hi;
-          s_xl[t] = x.lo;
-        }
+        const df x = row_dot(t < nrows ? a.P + (size_t)(r0 + t) * ldP : a.pdf, a.rhsA, npair);
+        if (lane == 0) s_x[t] = df_to_double(x);
       }
       __syncthreads();
-      const double betabar = -((double)s_xh[nrows] + (double)s_xl[nrows]) * a.inv_s;
       GDWD_MARK(15);
-      for (int t = threadIdx.x; t < nrows; t += kThreads) {
-        const int64_t i = r0 + t;
-        const double cbar = ((double)s_xh[t] + (double)s_xl[t]) + betabar * a.p[i];
-        const double ri = a.r[i];
-        const double rn = prox_root(cbar + ri, a.omega[i] * inv_sig, a.q, qcase, ri);
-        a.r[i] = rn;
-        const double v = a.xi[i] - rn - a.alpha[i] * inv_sig;
-        a.rhsB[i] = to_f2(a.b[i] + v);
+      if (mine) {
+        const double betabar = -s_x[nrows] * a.inv_s;
+        const double cbar = s_x[tr] + betabar * pi;
+        ri = prox_root(cbar + ri, omi * inv_sig, a.q, qcase, ri);
+        a.rhsB[i] = to_f2(bi + (xii - ri - ali * inv_sig));
       }
     }
     GDWD_BARRIER(4);
@@ -268,68 +280,52 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kern_kernel(KernArgs a) {
     // ---------------- phase N2: x, beta, c, Z~^T w; Step 2 (xi), Step 3 (alpha);
     // a_g = a_u - c / mu; the right-hand sides of phase K
     {
-      for (int64_t i = threadIdx.x; i < 2 * npair; i += kThreads) vs[i] = i < n ? a.rhsB[i] : make_float2(0.f, 0.f);
-      __syncthreads();
       GDWD_MARK(11);
-      double s_res2 = 0, s_ya = 0, s_xica = 0, s_ams2 = 0, s_amin2 = 0, s_amax2 = 0, s_pr = 0, s_px = 0, s_du = 0;
       for (int t = warp; t <= nrows; t += kWarps) {
-        const df x = row_dot(t < nrows ? a.P + (size_t)(r0 + t) * ldP : a.pdf, vs, npair);
-        if (lane == 0) {
-          s_xh[t] = x.hi;
-          s_xl[t] = x.lo;
-        }
+        const df x = row_dot(t < nrows ? a.P + (size_t)(r0 + t) * ldP : a.pdf, a.rhsB, npair);
+        if (lane == 0) s_x[t] = df_to_double(x);
       }
       __syncthreads();
-      beta = -((double)s_xh[nrows] + (double)s_xl[nrows]) * a.inv_s;
+      beta = -s_x[nrows] * a.inv_s;
       GDWD_MARK(12);
-      for (int t = threadIdx.x; t < nrows; t += kThreads) {
-        const int64_t i = r0 + t;
-        const double xv = (double)s_xh[t] + (double)s_xl[t];
-        const double c = xv + beta * a.p[i];
-        const double ri = a.r[i], al = a.alpha[i], yi = a.y[i], ce = a.C * a.e[i];
-        const double v = a.xi[i] - ri - al * inv_sig;
-        const double zw = c - v - yi * beta;                                     // Z~^T w
-        const double xin = fmax(0.0, ri - zw - yi * beta + (al - ce) * inv_sig);  // Step 2
+      double s_res2 = 0, s_ya = 0, s_xica = 0, s_ams2 = 0, s_amin2 = 0, s_amax2 = 0, s_pr = 0, s_px = 0, s_du = 0;
+      if (mine) {
+        const double c = s_x[tr] + beta * pi;
+        const double v = xii - ri - ali * inv_sig;
+        const double zw = c - v - yi * beta;                                      // Z~^T w
+        const double xin = fmax(0.0, ri - zw - yi * beta + (ali - ce) * inv_sig);  // Step 2
         const double res = zw + yi * beta + xin - ri;
-        const double an = al - a.tau * sig * res;                                // Step 3
-        a.xi[i] = xin;
-        a.alpha[i] = an;
-        const double agi = a.au[i] - c * inv_mu;                                 // g = u - Z~ c / mu
-        a.ag[i] = agi;
+        const double an = ali - a.tau * sig * res;                                // Step 3
+        xii = xin;
+        ali = an;
+        ag = au - c * inv_mu;                                                     // g = u - Z~ c / mu
         a.vdf[i] = to_f2(an);
-        a.vdf[ldP + i] = to_f2(agi);
-        a.vdf[2 * ldP + i] = to_f2(a.ar[i]);
-        const double rq1 = pow_q1(ri, a.q, qcase);
-        const double irq1 = rcp_nr(rq1);
-        const double om = a.omega[i];
-        s_res2 = fma(res, res, s_res2);
-        s_ya = fma(yi, an, s_ya);
-        s_xica = fma(xin, ce - an, s_xica);
-        const double dv = an - om * irq1;
-        s_ams2 = fma(dv, dv, s_ams2);
+        a.vdf[ldP + i] = to_f2(ag);
+        a.vdf[2 * ldP + i] = to_f2(ar);
+        const double irq1 = rcp_nr(pow_q1(ri, a.q, qcase));
+        s_res2 = res * res;
+        s_ya = yi * an;
+        s_xica = xin * (ce - an);
+        const double dv = an - omi * irq1;
+        s_ams2 = dv * dv;
         const double mn = fmin(0.0, an), mx = fmax(0.0, an - ce);
-        s_amin2 = fma(mn, mn, s_amin2);
-        s_amax2 = fma(mx, mx, s_amax2);
-        s_pr += om * inv_q * ri * irq1;           // wt^q r^-q
-        s_px = fma(a.e[i], xin, s_px);
-        s_du += dual_pow(a.wt[i] * an, a.q, qcase);
+        s_amin2 = mn * mn;
+        s_amax2 = mx * mx;
+        s_pr = omi * inv_q * ri * irq1;           // wt^q r^-q
+        s_px = ei * xin;
+        s_du = dual_pow(wti * an, a.q, qcase);
       }
       const double vals[9] = {s_res2, s_ya, s_xica, s_ams2, s_amin2, s_amax2, s_pr, s_px, s_du};
-      block_sum_n<9>(vals, (nrows + 31) / 32 < kWarps ? (nrows + 31) / 32 : kWarps, s_part, a.scal + cta, grid);
+      block_sum_n<9>(vals, nw, s_part, a.scal + cta, grid);
     }
     GDWD_BARRIER(6);
 
     // ---------------- phase K: K alpha, K a_g, K a_rho for this CTA's rows and the
     // six products of the d-space norms
     {
-      for (int64_t i = threadIdx.x; i < 3 * (int64_t)ldP; i += kThreads) {
-        const int64_t col = i % ldP;
-        vs[i] = col < n ? a.vdf[i] : make_float2(0.f, 0.f);
-      }
-      __syncthreads();
       for (int t = warp; t < nrows; t += kWarps) {
         double ka, kg, kr;
-        row_dot3(a.Kd + (size_t)(r0 + t) * ldP, vs, vs + ldP, vs + 2 * ldP, npair, ka, kg, kr);
+        row_dot3(a.Kd + (size_t)(r0 + t) * ldP, a.vdf, a.vdf + ldP, a.vdf + 2 * ldP, npair, ka, kg, kr);
         if (lane == 0) {
           s_k[0][t] = ka;
           s_k[1][t] = kg;
@@ -337,32 +333,27 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kern_kernel(KernArgs a) {
         }
       }
       __syncthreads();
-      double g2 = 0, gr = 0, r2 = 0, arho = 0, ag = 0, ta2 = 0;
-      for (int t = threadIdx.x; t < nrows; t += kThreads) {
-        const int64_t i = r0 + t;
-        const double ka = s_k[0][t], kg = s_k[1][t], kr = s_k[2][t];
-        const double al = a.alpha[i], agi = a.ag[i], ari = a.ar[i];
-        a.KG[i] = kg;
-        a.KR[i] = kr;
-        g2 = fma(agi, kg, g2);
-        gr = fma(ari, kg, gr);
-        r2 = fma(ari, kr, r2);
-        arho = fma(al, kr, arho);
-        ag = fma(al, kg, ag);
-        ta2 = fma(al, ka, ta2);
+      double g2 = 0, gr = 0, r2 = 0, arho = 0, agp = 0, ta2 = 0;
+      if (mine) {
+        const double ka = s_k[0][tr];
+        KG = s_k[1][tr];
+        KR = s_k[2][tr];
+        g2 = ag * KG;
+        gr = ar * KG;
+        r2 = ar * KR;
+        arho = ali * KR;
+        agp = ali * KG;
+        ta2 = ali * ka;
       }
-      const double vals[6] = {g2, gr, r2, arho, ag, ta2};
-      block_sum_n<6>(vals, (nrows + 31) / 32 < kWarps ? (nrows + 31) / 32 : kWarps, s_part,
-                     a.scal + (size_t)KS_G2 * grid + cta, grid);
+      const double vals[6] = {g2, gr, r2, arho, agp, ta2};
+      block_sum_n<6>(vals, nw, s_part, a.scal + (size_t)KS_G2 * grid + cta, grid);
     }
     GDWD_BARRIER(8);
 
     // ---------------- phase S: totals, KKT, sigma rule, stop test (same in every CTA)
     for (int k = warp; k <= KS_TA2; k += kWarps) {
-      double acc = 0.0;
-      for (int c2 = lane; c2 < grid; c2 += 32) acc += a.scal[(size_t)k * grid + c2];
-      acc = warp_sum(acc);
-      if (lane == 0) s_tot[k] = acc;
+      const double tot = grid_total(a.scal + (size_t)k * grid, grid, lane);
+      if (lane == 0) s_tot[k] = tot;
     }
     __syncthreads();
     GDWD_MARK(13);
@@ -457,6 +448,21 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kern_kernel(KernArgs a) {
     }
   }
   if (it >= a.max_iter && status != GDWD_OK) status = GDWD_EMAXITER;
+  // the rows back to global memory: the next launch's starting iterate and the
+  // coefficients of w
+  if (mine) {
+    a.r[i] = ri;
+    a.xi[i] = xii;
+    a.alpha[i] = ali;
+    a.b[i] = bi;
+    a.Uu[i] = Uu;
+    a.Ur[i] = Ur;
+    a.au[i] = au;
+    a.ar[i] = ar;
+    a.ag[i] = ag;
+    a.KG[i] = KG;
+    a.KR[i] = KR;
+  }
   if (cta == 0 && threadIdx.x == 0) {
     Ctrl* c = a.ctrl;
     c->sigma = sig;
@@ -472,33 +478,13 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kern_kernel(KernArgs a) {
 #undef GDWD_MARK
 }
 
-static size_t kern_smem_bytes(int ldP) { return (size_t)3 * ldP * sizeof(float2); }
+int64_t kern_max_n(int grid, int) { return (int64_t)grid * kMaxRowsPerCta; }
 
-int64_t kern_max_n(int grid, int smem_limit) {
-  const int64_t by_smem = ((int64_t)smem_limit / (3 * (int64_t)sizeof(float2))) & ~(int64_t)1;
-  const int64_t by_rows = (int64_t)grid * kMaxRowsPerCta;
-  return std::min(by_smem, by_rows);
-}
-
-cudaError_t run_iterate_kern(const KernArgs& a, int smem_limit, cudaStream_t st) {
-  const size_t smem = kern_smem_bytes(a.ldP);
-  if ((int64_t)smem > smem_limit || (a.n + a.grid - 1) / a.grid > kMaxRowsPerCta) return cudaErrorInvalidConfiguration;
-  static std::once_flag once;
-  static cudaError_t attr = cudaSuccess;
-  std::call_once(once, [] {
-    int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    cudaFuncAttributes fa;
-    attr = cudaFuncGetAttributes(&fa, iterate_kern_kernel);
-    if (attr == cudaSuccess)
-      attr = cudaFuncSetAttribute(iterate_kern_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  optin - (int)fa.sharedSizeBytes);
-  });
-  if (attr != cudaSuccess) return attr;
+cudaError_t run_iterate_kern(const KernArgs& a, int, cudaStream_t st) {
+  if ((a.n + a.grid - 1) / a.grid > kMaxRowsPerCta) return cudaErrorInvalidConfiguration;
   KernArgs args = a;
   void* params[] = {(void*)&args};
-  return cudaLaunchCooperativeKernel((const void*)iterate_kern_kernel, dim3(a.grid), dim3(kThreads), params, smem, st);
+  return cudaLaunchCooperativeKernel((const void*)iterate_kern_kernel, dim3(a.grid), dim3(kThreads), params, 0, st);
 }
 
 __global__ void kern_matrix_kernel(const double* G, int64_t n, int ldP, double mu, float2* Kd) {

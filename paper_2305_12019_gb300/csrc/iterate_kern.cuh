@@ -36,8 +36,7 @@ struct KernArgs {
   Ctrl* ctrl;
 };
 
-// Largest n the kernelized iteration accepts with smem_limit bytes of dynamic
-// shared memory per CTA (three double-float right-hand sides of length n).
+// Largest n the kernelized iteration accepts on `grid` CTAs (one row per thread).
 int64_t kern_max_n(int grid, int smem_limit);
 cudaError_t run_iterate_kern(const KernArgs& a, int smem_limit, cudaStream_t st);
 // Kd = mu (G - I) as double-float, rows padded to ldP with zeros.

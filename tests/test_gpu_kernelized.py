@@ -101,15 +101,23 @@ def test_kernelized_c_grid_weights_and_refinement(gdwd_lib):
 
 
 def test_kernelized_edge_cases(gdwd_lib):
-    """n = 2, d = 1; and an n beyond the shared-memory limit of the kernelized
-    iteration is refused at create time (before any device work)."""
+    """n = 2, d = 1 (one CTA holds both rows, the others none); a bad option
+    value is refused."""
     X = np.array([[1.0, -1.0]])
     y = np.array([1.0, -1.0])
     with gdwd_lib.Solver(X * y, y, 1.0, 10.0, store="f64", tol=1e-9, kernelized=1) as s:
         res, w, _ = s.solve()
     assert res[0]["status"] == 0
     assert abs(w[0, 0] - 1.0) <= 1e-6 and abs(res[0]["beta"]) <= 1e-6
-    n = 20000
-    yb = np.where(np.arange(n) % 2 == 0, 1.0, -1.0)
-    with pytest.raises(gdwd_lib.GdwdError, match="EUNSUPPORTED"):
-        gdwd_lib.Solver(np.ones((1, n)) * yb, yb, 1.0, 1.0, store="f64", kernelized=1)
+    with pytest.raises(gdwd_lib.GdwdError, match="EINVAL"):
+        gdwd_lib.Solver(X * y, y, 1.0, 1.0, store="f64", kernelized=2)
+
+
+def test_kernelized_few_ctas(gdwd_lib):
+    """grid = 8: each CTA holds up to 256 rows (one per thread) of an n = 2000
+    problem with a ragged last block."""
+    inst = synth.gaussian(seed=23, d=3000, n=1999, shift=1.0, n_pos=700, q=1.0, C=1.0, dtype=np.float64)
+    with gdwd_lib.Solver(inst.Z, inst.y, 1.0, 1.0, store="f64", tol=1e-8, kernelized=1, grid=8) as s:
+        res, w, _ = s.solve()
+    assert res[0]["status"] == 0, res[0]
+    _compare(res[0], w[:, 0], O.solve(inst.Z, inst.y, 1.0, 1.0, tol=1e-10))

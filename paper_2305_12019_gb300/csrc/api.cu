@@ -280,8 +280,8 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
     CK(halloc(h, &h->kc, n), "alloc");
     CK(halloc(h, &h->rhsB, h->ldP), "alloc");
     const size_t ct = h->store == GDWD_F64 ? 8 : 4;
-    CK(halloc(h, (uint8_t**)&h->cq, n * ct), "alloc");
-    CK(halloc(h, (uint8_t**)&h->aq, n * ct), "alloc");
+    CK(halloc(h, (uint8_t**)&h->cq, (n * ct + 15) / 16 * 16), "alloc");   // copied in 16-byte pieces
+    CK(halloc(h, (uint8_t**)&h->aq, (n * ct + 15) / 16 * 16), "alloc");
     CK(halloc(h, (uint8_t**)&h->partial, (size_t)n * h->L.NB * ct), "alloc");
     CK(halloc(h, &h->u, dpad), "alloc");
     CK(halloc(h, &h->rho, dpad), "alloc");

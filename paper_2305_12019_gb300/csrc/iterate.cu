@@ -134,6 +134,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
   const int64_t r0 = ((int64_t)cta * rpc < n) ? (int64_t)cta * rpc : n;
   const int nrows = (int)(((r0 + rpc < n) ? r0 + rpc : n) - r0);
   __shared__ float s_xh[kMaxRowsPerCta + 1], s_xl[kMaxRowsPerCta + 1];   // + the p^T rhs row
+  __shared__ double s_ug[kMaxRowsPerCta];                                 // Z~^T u from the column dots
   const int qcase = q_case(a.q);
   const double sqmu = sqrt(a.mu), inv_mu = 1.0 / a.mu;
   const double den = 1.0 + a.C;
@@ -180,7 +181,6 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
   } while (0)
 
   const int npair = (int)((n + 1) / 2);
-  float2* rhs_s = reinterpret_cast<float2*>(uni);
 
   // ---------------- prologue: U_u = Z~^T u and U_rho = Z~^T rho of the starting
   // iterate for this CTA's rows.  A warm start computes them with two passes over
@@ -238,39 +238,43 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
     {
       const double gsc = rcp_nr(sig * sqmu);
       const double rcoef = a.tau * sig_prev * sqmu * (1.0 - theta);
-      for (int t = warp; t < nrows; t += kWarps) {
-        const int64_t i = r0 + t;
-        double ug = 0.0;
-        if (pending && dots_prev) ug = a.sc[i] * reduce_partials<CT>(a.partial + (size_t)i * NB, NB, lane);
-        if (lane == 0) {
-          double uu = a.Uu[i], ur = a.Ur[i];
-          if (pending) {
-            ug = (dots_prev ? ug : uu) - a.kc[i];
-            uu = theta * ug;
-            ur = (1.0 - a.tau) * ur - rcoef * ug;
-            a.Uu[i] = uu;
-            a.Ur[i] = ur;
-          }
-          const double bi = uu + ur * gsc;
-          a.b[i] = bi;
-          const double v = a.xi[i] - a.r[i] - a.alpha[i] * inv_sig;
-          const df r1 = df_from(bi + v);
-          a.rhsA[i] = make_float2(r1.hi, r1.lo);
+      if (pending && dots_prev) {
+        // the column dots Z~^T u of the last pass: one warp per row sums its slabs
+        for (int t = warp; t < nrows; t += kWarps) {
+          const double ug = a.sc[r0 + t] * reduce_partials<CT>(a.partial + (size_t)(r0 + t) * NB, NB, lane);
+          if (lane == 0) s_ug[t] = ug;
         }
+        __syncthreads();
+      }
+      // the per-row work on consecutive threads (few warp instructions of FP64)
+      for (int t = threadIdx.x; t < nrows; t += kThreads) {
+        const int64_t i = r0 + t;
+        double uu = a.Uu[i], ur = a.Ur[i];
+        if (pending) {
+          const double ug = (dots_prev ? s_ug[t] : uu) - a.kc[i];
+          uu = theta * ug;
+          ur = (1.0 - a.tau) * ur - rcoef * ug;
+          a.Uu[i] = uu;
+          a.Ur[i] = ur;
+        }
+        const double bi = uu + ur * gsc;
+        a.b[i] = bi;
+        const double v = a.xi[i] - a.r[i] - a.alpha[i] * inv_sig;
+        const df r1 = df_from(bi + v);
+        a.rhsA[i] = make_float2(r1.hi, r1.lo);
       }
     }
     GDWD_BARRIER(2);
 
     // ---------------- phase N1: x-bar, beta-bar, Step 1b prox, rhs2
     {
-      for (int64_t i = threadIdx.x; i < 2 * npair; i += kThreads) rhs_s[i] = i < n ? a.rhsA[i] : make_float2(0.f, 0.f);
-      __syncthreads();
       GDWD_MARK(14);
       // G^{-1} rows of this CTA and, as one more row, p^T rhs1 for beta-bar (one
-      // warp per row); then the per-row FP64 work with one row per lane so each
-      // FP64 instruction serves up to 32 rows
+      // warp per row; rhs1 is read from L2, and from L1 after the SM's first warp);
+      // then the per-row FP64 work with one row per lane so each FP64 instruction
+      // serves up to 32 rows
       for (int t = warp; t <= nrows; t += kWarps) {
-        const df x = row_dot(t < nrows ? a.P + (size_t)(r0 + t) * a.ldP : a.pdf, rhs_s, npair);
+        const df x = row_dot(t < nrows ? a.P + (size_t)(r0 + t) * a.ldP : a.pdf, a.rhsA, npair);
         if (lane == 0) {
           s_xh[t] = x.hi;
           s_xl[t] = x.lo;
@@ -295,12 +299,10 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
     // ---------------- phase N2: x, beta, c, Z~^T w; Step 2 (xi), Step 3 (alpha);
     // (G - I) c = rhs2 - x + beta (y - p) for the next U_g
     {
-      for (int64_t i = threadIdx.x; i < 2 * npair; i += kThreads) rhs_s[i] = i < n ? a.rhsB[i] : make_float2(0.f, 0.f);
-      __syncthreads();
       GDWD_MARK(11);
       double s_res2 = 0, s_ya = 0, s_xica = 0, s_ams2 = 0, s_amin2 = 0, s_amax2 = 0, s_pr = 0, s_px = 0, s_du = 0;
       for (int t = warp; t <= nrows; t += kWarps) {
-        const df x = row_dot(t < nrows ? a.P + (size_t)(r0 + t) * a.ldP : a.pdf, rhs_s, npair);
+        const df x = row_dot(t < nrows ? a.P + (size_t)(r0 + t) * a.ldP : a.pdf, a.rhsB, npair);
         if (lane == 0) {
           s_xh[t] = x.hi;
           s_xl[t] = x.lo;
@@ -324,7 +326,8 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
           a.alpha[i] = an;
           store_ct(a.cq + i, a.sc[i] * c);
           store_ct(a.aq + i, a.sc[i] * an);
-          const double rh2 = (double)rhs_s[i].x + (double)rhs_s[i].y;
+          const float2 rb = a.rhsB[i];
+          const double rh2 = (double)rb.x + (double)rb.y;
           a.kc[i] = rh2 - xv + beta * (yi - a.p[i]);
           const double rq1 = pow_q1(ri, a.q, qcase);
           const double irq1 = rcp_nr(rq1);
@@ -351,15 +354,18 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
     // t = Z~ c, ta = Z~ alpha, g = u - t / mu and the d-space sums; on the same
     // chunks the column dots of Z~^T u (for the next U_g)
     {
+      // c and alpha (scaled, compute type) in 16-byte pieces: both vectors are
+      // padded to a multiple of 16 bytes in global and shared memory
+      const int64_t nv = (n * (int64_t)sizeof(CT) + 15) / 16;
       CT* cv = reinterpret_cast<CT*>(uni);
-      CT* av = cv + n;
-      const size_t off_red = (2 * n * sizeof(CT) + 15) & ~(size_t)15;
+      CT* av = reinterpret_cast<CT*>(uni + nv * 16);
+      const size_t off_red = (size_t)nv * 32;
       double* red = reinterpret_cast<double*>(uni + off_red);
       CT* up = reinterpret_cast<CT*>(uni + off_red + (size_t)2 * G * TB * sizeof(double));
       const double rcoef = a.tau * sig_prev * sqmu * (1.0 - theta);
-      for (int64_t i = threadIdx.x; i < n; i += kThreads) {
-        cv[i] = a.cq[i];
-        av[i] = a.aq[i];
+      for (int64_t k = threadIdx.x; k < nv; k += kThreads) {
+        reinterpret_cast<uint4*>(cv)[k] = reinterpret_cast<const uint4*>(a.cq)[k];
+        reinterpret_cast<uint4*>(av)[k] = reinterpret_cast<const uint4*>(a.aq)[k];
       }
       for (int k = 0; k < nmy; ++k) {
         const int64_t s = cta + (int64_t)k * grid;
@@ -411,12 +417,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
     GDWD_BARRIER(8);
 
     // ---------------- phase S: totals, KKT, sigma rule, stop test (same in every CTA)
-    for (int k = warp; k < S_COUNT - 1; k += kWarps) {
-      double acc = 0.0;
-      for (int c2 = lane; c2 < grid; c2 += 32) acc += a.scal[(size_t)k * grid + c2];
-      acc = warp_sum(acc);
-      if (lane == 0) s_tot[k] = acc;
-    }
+    grid_totals(a.scal, grid, S_COUNT - 1, s_tot);
     __syncthreads();
     GDWD_MARK(13);
     // Three independent chains on the first lanes of three warps (the FP64
@@ -536,12 +537,10 @@ static size_t union_bytes(const Layout& L, int grid) {
   const int Q = L.TB / VEC;
   const int G = Q <= kThreads ? kThreads / Q : 1;
   size_t a_bytes = (size_t)nmy * L.TB * sizeof(CT);
-  size_t b_bytes = ((2 * L.n * sizeof(CT) + 15) & ~(size_t)15) + (size_t)2 * G * L.TB * sizeof(double) +
+  size_t b_bytes = (size_t)(L.n * sizeof(CT) + 15) / 16 * 32 + (size_t)2 * G * L.TB * sizeof(double) +
                    (size_t)nmy * L.TB * sizeof(CT);
-  size_t n_bytes = (size_t)((L.n + 1) / 2) * 2 * sizeof(float2);
   size_t u = a_bytes;
   if (b_bytes > u) u = b_bytes;
-  if (n_bytes > u) u = n_bytes;
   return (u + 127) & ~(size_t)127;
 }
 

@@ -109,25 +109,30 @@ __device__ __forceinline__ float2 to_f2(double x) {
   return make_float2(v.hi, v.lo);
 }
 
-// Sum over the grid's per-CTA partials of one slot, in a fixed order (one warp;
-// up to eight loads per lane in flight; the result in every lane).
-__device__ __forceinline__ double grid_total(const double* part, int grid, int lane) {
-  double acc = 0.0;
-  for (int base = 0; base < grid; base += 256) {
-    double v[8];
+// N per-row values summed over the CTA's rows in row order (deterministic): the
+// rows' values go to shared memory, then warp k sums value k (lanes over rows,
+// then a fixed shuffle tree) and writes out[k * stride].
+template <int N>
+__device__ __forceinline__ void rows_sum(const double (&v)[N], int tr, bool mine, int nrows,
+                                         double (*s_rows)[kMaxRowsPerCta], double* out, int stride) {
+  if (mine) {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int c2 = base + lane + 32 * q;
-      v[q] = c2 < grid ? part[c2] : 0.0;
-    }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) acc += v[q];
+    for (int k = 0; k < N; ++k) s_rows[k][tr] = v[k];
   }
-  return warp_sum(acc);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int k = warp; k < N; k += kWarps) {
+    double acc = 0.0;
+    for (int t = lane; t < nrows; t += 32) acc += s_rows[k][t];
+    acc = warp_sum(acc);
+    if (lane == 0) out[(size_t)k * stride] = acc;
+  }
 }
 
 // One CTA owns a contiguous block of at most kThreads rows of the n-space and
-// thread t holds row r0 + t of every n-vector in registers for the whole launch;
+// thread t holds row r0 + t of every n-vector in registers for the whole launch
+// (consecutive rows share a warp: the per-row FP64 work of a CTA's few rows then
+// issues as few warp instructions as possible);
 // only the vectors other CTAs read (the right-hand sides of the GEMVs and the
 // partial sums) go through global memory.  The GEMVs read their right-hand
 // sides straight from L2 (every warp of the SM reads the same vector, so it is
@@ -137,7 +142,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kern_kernel(KernArgs a) {
   __shared__ double s_tot[S_COUNT];
   __shared__ double s_ctl[8];
   __shared__ double s_eta[9];
-  __shared__ double s_part[kWarps * 9];
+  __shared__ double s_rows[9][kMaxRowsPerCta];    // per-row partial sums
   __shared__ double s_x[kMaxRowsPerCta + 1];      // GEMV results of the CTA's rows (+ the p^T rhs row)
   __shared__ double s_k[3][kMaxRowsPerCta];
   static_assert(kMaxRowsPerCta <= kThreads, "one row per thread");
@@ -157,7 +162,6 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kern_kernel(KernArgs a) {
   const float inv_den = (float)(1.0 / den);
   const double sqrt_tol = sqrt(a.tol);
   const double ac = sqmu * (1.0 - a.tau);              // Z~ alpha + ac rho enters eta_D3
-  const int nw = (nrows + 31) / 32 < kWarps ? (nrows + 31) / 32 : kWarps;   // warps holding rows
 
   // this thread's row
   const int tr = threadIdx.x;
@@ -316,7 +320,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kern_kernel(KernArgs a) {
         s_du = dual_pow(wti * an, a.q, qcase);
       }
       const double vals[9] = {s_res2, s_ya, s_xica, s_ams2, s_amin2, s_amax2, s_pr, s_px, s_du};
-      block_sum_n<9>(vals, nw, s_part, a.scal + cta, grid);
+      rows_sum<9>(vals, tr, mine, nrows, s_rows, a.scal + cta, grid);
     }
     GDWD_BARRIER(6);
 
@@ -346,15 +350,12 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kern_kernel(KernArgs a) {
         ta2 = ali * ka;
       }
       const double vals[6] = {g2, gr, r2, arho, agp, ta2};
-      block_sum_n<6>(vals, nw, s_part, a.scal + (size_t)KS_G2 * grid + cta, grid);
+      rows_sum<6>(vals, tr, mine, nrows, s_rows, a.scal + (size_t)KS_G2 * grid + cta, grid);
     }
     GDWD_BARRIER(8);
 
     // ---------------- phase S: totals, KKT, sigma rule, stop test (same in every CTA)
-    for (int k = warp; k <= KS_TA2; k += kWarps) {
-      const double tot = grid_total(a.scal + (size_t)k * grid, grid, lane);
-      if (lane == 0) s_tot[k] = tot;
-    }
+    grid_totals(a.scal, grid, KS_TA2 + 1, s_tot);
     __syncthreads();
     GDWD_MARK(13);
     // three independent FP64 chains on three warps, as in the Z-streaming kernel

@@ -120,6 +120,30 @@ __device__ __forceinline__ void block_sum_n(const double (&v)[N], int nw, double
   }
 }
 
+// Totals over the grid of the per-CTA partial sums of slots 0 .. nslots-1
+// (nslots <= 16), in a fixed order: 16 threads per slot, each with all its loads
+// in flight, then a 16-lane shuffle tree; s_tot[k] receives slot k.
+__device__ __forceinline__ void grid_totals(const double* scal, int grid, int nslots, double* s_tot) {
+  const int k = threadIdx.x >> 4, sub = threadIdx.x & 15;
+  double acc = 0.0;
+  if (k < nslots) {
+    const double* part = scal + (size_t)k * grid;
+    for (int base = 0; base < grid; base += 16 * 12) {
+      double v[12];
+#pragma unroll
+      for (int q = 0; q < 12; ++q) {
+        const int c2 = base + sub + 16 * q;
+        v[q] = c2 < grid ? part[c2] : 0.0;
+      }
+#pragma unroll
+      for (int q = 0; q < 12; ++q) acc += v[q];
+    }
+  }
+#pragma unroll
+  for (int m = 8; m >= 1; m >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, m);
+  if (sub == 0 && k < nslots) s_tot[k] = acc;
+}
+
 // x_i = sum_j P_ij rhs_j for one row, one warp, double-float (result in all lanes).
 // Four independent 16-byte loads per lane per step keep several L2 requests in flight.
 __device__ __forceinline__ df row_dot(const float2* __restrict__ Prow, const float2* rhs_s, int npair) {

@@ -345,8 +345,11 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
           s_du += dual_pow(a.wt[i] * an, a.q, qcase);
         }
       }
+      // one row per thread (nrows <= kThreads): the sums go through the phase-local
+      // region, one warp per sum
       const double vals[9] = {s_res2, s_ya, s_xica, s_ams2, s_amin2, s_amax2, s_pr, s_px, s_du};
-      block_sum_n<9>(vals, (nrows + 31) / 32 < kWarps ? (nrows + 31) / 32 : kWarps, s_part, a.scal + cta, grid);
+      rows_sum<9>(vals, threadIdx.x, threadIdx.x < nrows, nrows, reinterpret_cast<double*>(uni), nrows, a.scal + cta,
+                  grid);
     }
     GDWD_BARRIER(6);
 
@@ -539,8 +542,10 @@ static size_t union_bytes(const Layout& L, int grid) {
   size_t a_bytes = (size_t)nmy * L.TB * sizeof(CT);
   size_t b_bytes = (size_t)(L.n * sizeof(CT) + 15) / 16 * 32 + (size_t)2 * G * L.TB * sizeof(double) +
                    (size_t)nmy * L.TB * sizeof(CT);
+  size_t r_bytes = (size_t)9 * sizeof(double) * (size_t)((L.n + grid - 1) / grid);   // N2 row sums
   size_t u = a_bytes;
   if (b_bytes > u) u = b_bytes;
+  if (r_bytes > u) u = r_bytes;
   return (u + 127) & ~(size_t)127;
 }
 

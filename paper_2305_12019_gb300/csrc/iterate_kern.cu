@@ -109,26 +109,6 @@ __device__ __forceinline__ float2 to_f2(double x) {
   return make_float2(v.hi, v.lo);
 }
 
-// N per-row values summed over the CTA's rows in row order (deterministic): the
-// rows' values go to shared memory, then warp k sums value k (lanes over rows,
-// then a fixed shuffle tree) and writes out[k * stride].
-template <int N>
-__device__ __forceinline__ void rows_sum(const double (&v)[N], int tr, bool mine, int nrows,
-                                         double (*s_rows)[kMaxRowsPerCta], double* out, int stride) {
-  if (mine) {
-#pragma unroll
-    for (int k = 0; k < N; ++k) s_rows[k][tr] = v[k];
-  }
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int k = warp; k < N; k += kWarps) {
-    double acc = 0.0;
-    for (int t = lane; t < nrows; t += 32) acc += s_rows[k][t];
-    acc = warp_sum(acc);
-    if (lane == 0) out[(size_t)k * stride] = acc;
-  }
-}
-
 // One CTA owns a contiguous block of at most kThreads rows of the n-space and
 // thread t holds row r0 + t of every n-vector in registers for the whole launch
 // (consecutive rows share a warp: the per-row FP64 work of a CTA's few rows then
@@ -142,7 +122,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kern_kernel(KernArgs a) {
   __shared__ double s_tot[S_COUNT];
   __shared__ double s_ctl[8];
   __shared__ double s_eta[9];
-  __shared__ double s_rows[9][kMaxRowsPerCta];    // per-row partial sums
+  __shared__ double s_rows[9 * kMaxRowsPerCta];    // per-row partial sums
   __shared__ double s_x[kMaxRowsPerCta + 1];      // GEMV results of the CTA's rows (+ the p^T rhs row)
   __shared__ double s_k[3][kMaxRowsPerCta];
   static_assert(kMaxRowsPerCta <= kThreads, "one row per thread");
@@ -320,7 +300,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kern_kernel(KernArgs a) {
         s_du = dual_pow(wti * an, a.q, qcase);
       }
       const double vals[9] = {s_res2, s_ya, s_xica, s_ams2, s_amin2, s_amax2, s_pr, s_px, s_du};
-      rows_sum<9>(vals, tr, mine, nrows, s_rows, a.scal + cta, grid);
+      rows_sum<9>(vals, tr, mine, nrows, s_rows, kMaxRowsPerCta, a.scal + cta, grid);
     }
     GDWD_BARRIER(6);
 
@@ -350,7 +330,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kern_kernel(KernArgs a) {
         ta2 = ali * ka;
       }
       const double vals[6] = {g2, gr, r2, arho, agp, ta2};
-      rows_sum<6>(vals, tr, mine, nrows, s_rows, a.scal + (size_t)KS_G2 * grid + cta, grid);
+      rows_sum<6>(vals, tr, mine, nrows, s_rows, kMaxRowsPerCta, a.scal + (size_t)KS_G2 * grid + cta, grid);
     }
     GDWD_BARRIER(8);
 

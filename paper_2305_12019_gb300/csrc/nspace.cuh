@@ -144,6 +144,29 @@ __device__ __forceinline__ void grid_totals(const double* scal, int grid, int ns
   if (sub == 0 && k < nslots) s_tot[k] = acc;
 }
 
+// N per-row values summed over the CTA's rows in row order (deterministic): the
+// rows' values go to shared memory s_rows (N x ld doubles, ld >= nrows), then
+// warp k sums value k (lanes over rows, then a fixed shuffle tree) and writes
+// out[k * stride].  Each warp reduces one value, so the FP64 adds of the N
+// reductions run on all warps instead of one after the other on the warp that
+// holds the rows.
+template <int N>
+__device__ __forceinline__ void rows_sum(const double (&v)[N], int tr, bool mine, int nrows, double* s_rows, int ld,
+                                         double* out, int stride) {
+  if (mine) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) s_rows[k * ld + tr] = v[k];
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int k = warp; k < N; k += kWarps) {
+    double acc = 0.0;
+    for (int t = lane; t < nrows; t += 32) acc += s_rows[k * ld + t];
+    acc = warp_sum(acc);
+    if (lane == 0) out[(size_t)k * stride] = acc;
+  }
+}
+
 // x_i = sum_j P_ij rhs_j for one row, one warp, double-float (result in all lanes).
 // Four independent 16-byte loads per lane per step keep several L2 requests in flight.
 __device__ __forceinline__ df row_dot(const float2* __restrict__ Prow, const float2* rhs_s, int npair) {

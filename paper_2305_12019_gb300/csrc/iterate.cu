@@ -118,7 +118,6 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
   __shared__ double s_tot[S_COUNT];
   __shared__ double s_ctl[8];
   __shared__ double s_eta[9];
-  __shared__ double s_part[kWarps * 9];
 
   const Layout& L = a.L;
   const int cta = blockIdx.x, grid = a.grid;
@@ -414,8 +413,12 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
       } else {
         if (!stream_slabs<T>(L, rg, cta, grid, a.err, a.timeout_ns, &s_abort, pb)) return;
       }
+      // the six d-space sums of every thread, one warp per sum, through the
+      // phase-local region (free once the pass is over)
       const double vals[6] = {epi.sg2, epi.sgr, epi.sr2, epi.sa2, epi.sag, epi.sta2};
-      block_sum_n<6>(vals, kWarps, s_part, a.scal + (size_t)S_G2 * grid + cta, grid);
+      __syncthreads();
+      rows_sum<6>(vals, threadIdx.x, true, kThreads, reinterpret_cast<double*>(uni), kThreads,
+                  a.scal + (size_t)S_G2 * grid + cta, grid);
     }
     GDWD_BARRIER(8);
 
@@ -543,6 +546,7 @@ static size_t union_bytes(const Layout& L, int grid) {
   size_t b_bytes = (size_t)(L.n * sizeof(CT) + 15) / 16 * 32 + (size_t)2 * G * L.TB * sizeof(double) +
                    (size_t)nmy * L.TB * sizeof(CT);
   size_t r_bytes = (size_t)9 * sizeof(double) * (size_t)((L.n + grid - 1) / grid);   // N2 row sums
+  if (r_bytes < (size_t)6 * kThreads * sizeof(double)) r_bytes = (size_t)6 * kThreads * sizeof(double);   // B sums
   size_t u = a_bytes;
   if (b_bytes > u) u = b_bytes;
   if (r_bytes > u) u = r_bytes;

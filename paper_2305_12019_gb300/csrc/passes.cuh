@@ -54,7 +54,9 @@ __device__ __forceinline__ void ring_prefetch(const Layout& L, Ring& rg, int cta
   const int nch = (int)((L.n + L.CW - 1) / L.CW);
   const int nmy = (L.NB > cta) ? (L.NB - cta + grid - 1) / grid : 0;
   const int pre = min(rg.stages, nmy * nch);
-  if (threadIdx.x == 0)
+  // issued by the last warp: thread 0 holds the first n-space row of the phase
+  // that runs meanwhile
+  if (threadIdx.x == kThreads - 32)
     for (int c = 0; c < pre; ++c) {
       const uint8_t* src;
       uint32_t bytes;

@@ -104,6 +104,16 @@ __device__ __forceinline__ double reduce_partials(const CT* pp, int NB, int lane
 template <typename CT>
 __device__ __forceinline__ void store_ct(CT* p, double v) { *p = (CT)v; }
 
+// The CTA's n-space rows (at most kMaxRowsPerCta) live in shared memory for the
+// whole launch: the iterate's row state and the per-row constants, one array
+// of rpc doubles each, ahead of the phase-local region.  The row phases then
+// touch global memory only for what other CTAs read.
+enum RowSlot { RS_R, RS_XI, RS_AL, RS_B, RS_KC, RS_UU, RS_UR, RS_Y, RS_P, RS_CE, RS_E, RS_OM, RS_WT, RS_SC, RS_COUNT };
+
+__host__ __device__ inline size_t row_state_bytes(int64_t rpc) {
+  return ((size_t)RS_COUNT * (size_t)rpc * sizeof(double) + 127) & ~(size_t)127;
+}
+
 // ---------------------------------------------------------------------------
 // the persistent kernel
 // ---------------------------------------------------------------------------
@@ -134,6 +144,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
   const int nrows = (int)(((r0 + rpc < n) ? r0 + rpc : n) - r0);
   __shared__ float s_xh[kMaxRowsPerCta + 1], s_xl[kMaxRowsPerCta + 1];   // + the p^T rhs row
   __shared__ double s_ug[kMaxRowsPerCta];                                 // Z~^T u from the column dots
+  __shared__ float2 s_rb[kMaxRowsPerCta];                                 // rhs2 of the CTA's rows
   const int qcase = q_case(a.q);
   const double sqmu = sqrt(a.mu), inv_mu = 1.0 / a.mu;
   const double den = 1.0 + a.C;
@@ -146,7 +157,10 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
   rg.bars = s_bars;
   rg.stages = stages;
   rg.stage_bytes = stage_bytes;
-  uint8_t* uni = smem + (size_t)stages * stage_bytes;     // phase-local region
+  double* rs = reinterpret_cast<double*>(smem + (size_t)stages * stage_bytes);   // row state
+  const int rld = (int)rpc;
+#define RS(slot, t) rs[(slot) * rld + (t)]
+  uint8_t* uni = smem + (size_t)stages * stage_bytes + row_state_bytes(rpc);     // phase-local region
   if (threadIdx.x == 0) s_abort = 0;
   ring_init(rg);
 
@@ -224,6 +238,24 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
     }
   }
   __syncthreads();
+  for (int t = threadIdx.x; t < nrows; t += kThreads) {
+    const int64_t i = r0 + t;
+    RS(RS_R, t) = a.r[i];
+    RS(RS_XI, t) = a.xi[i];
+    RS(RS_AL, t) = a.alpha[i];
+    RS(RS_B, t) = a.b[i];
+    RS(RS_KC, t) = a.kc[i];
+    RS(RS_UU, t) = a.Uu[i];
+    RS(RS_UR, t) = a.Ur[i];
+    RS(RS_Y, t) = a.y[i];
+    RS(RS_P, t) = a.p[i];
+    RS(RS_CE, t) = a.C * a.e[i];
+    RS(RS_E, t) = a.e[i];
+    RS(RS_OM, t) = a.omega[i];
+    RS(RS_WT, t) = a.wt[i];
+    RS(RS_SC, t) = a.sc[i];
+  }
+  __syncthreads();
 
   int it = it0;
   bool dots_prev = false;   // the last pass B took the column dots Z~^T u
@@ -240,7 +272,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
       if (pending && dots_prev) {
         // the column dots Z~^T u of the last pass: one warp per row sums its slabs
         for (int t = warp; t < nrows; t += kWarps) {
-          const double ug = a.sc[r0 + t] * reduce_partials<CT>(a.partial + (size_t)(r0 + t) * NB, NB, lane);
+          const double ug = RS(RS_SC, t) * reduce_partials<CT>(a.partial + (size_t)(r0 + t) * NB, NB, lane);
           if (lane == 0) s_ug[t] = ug;
         }
         __syncthreads();
@@ -248,17 +280,17 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
       // the per-row work on consecutive threads (few warp instructions of FP64)
       for (int t = threadIdx.x; t < nrows; t += kThreads) {
         const int64_t i = r0 + t;
-        double uu = a.Uu[i], ur = a.Ur[i];
+        double uu = RS(RS_UU, t), ur = RS(RS_UR, t);
         if (pending) {
-          const double ug = (dots_prev ? s_ug[t] : uu) - a.kc[i];
+          const double ug = (dots_prev ? s_ug[t] : uu) - RS(RS_KC, t);
           uu = theta * ug;
           ur = (1.0 - a.tau) * ur - rcoef * ug;
-          a.Uu[i] = uu;
-          a.Ur[i] = ur;
+          RS(RS_UU, t) = uu;
+          RS(RS_UR, t) = ur;
         }
         const double bi = uu + ur * gsc;
-        a.b[i] = bi;
-        const double v = a.xi[i] - a.r[i] - a.alpha[i] * inv_sig;
+        RS(RS_B, t) = bi;
+        const double v = RS(RS_XI, t) - RS(RS_R, t) - RS(RS_AL, t) * inv_sig;
         const df r1 = df_from(bi + v);
         a.rhsA[i] = make_float2(r1.hi, r1.lo);
       }
@@ -284,13 +316,14 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
       GDWD_MARK(15);
       for (int t = threadIdx.x; t < nrows; t += kThreads) {
         const int64_t i = r0 + t;
-        const double cbar = ((double)s_xh[t] + (double)s_xl[t]) + betabar * a.p[i];
-        const double ri = a.r[i];
-        const double rn = prox_root(cbar + ri, a.omega[i] * inv_sig, a.q, qcase, ri);
-        a.r[i] = rn;
-        const double v = a.xi[i] - rn - a.alpha[i] * inv_sig;
-        const df r2 = df_from(a.b[i] + v);
+        const double cbar = ((double)s_xh[t] + (double)s_xl[t]) + betabar * RS(RS_P, t);
+        const double ri = RS(RS_R, t);
+        const double rn = prox_root(cbar + ri, RS(RS_OM, t) * inv_sig, a.q, qcase, ri);
+        RS(RS_R, t) = rn;
+        const double v = RS(RS_XI, t) - rn - RS(RS_AL, t) * inv_sig;
+        const df r2 = df_from(RS(RS_B, t) + v);
         a.rhsB[i] = make_float2(r2.hi, r2.lo);
+        s_rb[t] = make_float2(r2.hi, r2.lo);
       }
     }
     GDWD_BARRIER(4);
@@ -314,23 +347,25 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
         const int64_t i = r0 + t;
         {
           const double xv = (double)s_xh[t] + (double)s_xl[t];
-          const double c = xv + beta * a.p[i];
-          const double ri = a.r[i], al = a.alpha[i], yi = a.y[i], ce = a.C * a.e[i];
-          const double v = a.xi[i] - ri - al * inv_sig;
+          const double pi = RS(RS_P, t);
+          const double c = xv + beta * pi;
+          const double ri = RS(RS_R, t), al = RS(RS_AL, t), yi = RS(RS_Y, t), ce = RS(RS_CE, t);
+          const double v = RS(RS_XI, t) - ri - al * inv_sig;
           const double zw = c - v - yi * beta;                                     // Z~^T w
           const double xin = fmax(0.0, ri - zw - yi * beta + (al - ce) * inv_sig);  // Step 2
           const double res = zw + yi * beta + xin - ri;
           const double an = al - a.tau * sig * res;                                // Step 3
-          a.xi[i] = xin;
-          a.alpha[i] = an;
-          store_ct(a.cq + i, a.sc[i] * c);
-          store_ct(a.aq + i, a.sc[i] * an);
-          const float2 rb = a.rhsB[i];
+          RS(RS_XI, t) = xin;
+          RS(RS_AL, t) = an;
+          const double sci = RS(RS_SC, t);
+          store_ct(a.cq + i, sci * c);
+          store_ct(a.aq + i, sci * an);
+          const float2 rb = s_rb[t];
           const double rh2 = (double)rb.x + (double)rb.y;
-          a.kc[i] = rh2 - xv + beta * (yi - a.p[i]);
+          RS(RS_KC, t) = rh2 - xv + beta * (yi - pi);
           const double rq1 = pow_q1(ri, a.q, qcase);
           const double irq1 = rcp_nr(rq1);
-          const double om = a.omega[i];
+          const double om = RS(RS_OM, t);
           s_res2 = fma(res, res, s_res2);
           s_ya = fma(yi, an, s_ya);
           s_xica = fma(xin, ce - an, s_xica);
@@ -340,8 +375,8 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
           s_amin2 = fma(mn, mn, s_amin2);
           s_amax2 = fma(mx, mx, s_amax2);
           s_pr += om * inv_q * ri * irq1;           // wt^q r^-q
-          s_px = fma(a.e[i], xin, s_px);
-          s_du += dual_pow(a.wt[i] * an, a.q, qcase);
+          s_px = fma(RS(RS_E, t), xin, s_px);
+          s_du += dual_pow(RS(RS_WT, t) * an, a.q, qcase);
         }
       }
       // one row per thread (nrows <= kThreads): the sums go through the phase-local
@@ -520,6 +555,18 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
     }
   }
   if (it >= a.max_iter && status != GDWD_OK) status = GDWD_EMAXITER;
+  // the rows back to global memory (the host reads alpha; a later launch starts
+  // from r, xi, alpha, U_u, U_rho and (G - I) c)
+  for (int t = threadIdx.x; t < nrows; t += kThreads) {
+    const int64_t i = r0 + t;
+    a.r[i] = RS(RS_R, t);
+    a.xi[i] = RS(RS_XI, t);
+    a.alpha[i] = RS(RS_AL, t);
+    a.b[i] = RS(RS_B, t);
+    a.kc[i] = RS(RS_KC, t);
+    a.Uu[i] = RS(RS_UU, t);
+    a.Ur[i] = RS(RS_UR, t);
+  }
   if (cta == 0 && threadIdx.x == 0) {
     Ctrl* c = a.ctrl;
     c->sigma = sig;
@@ -533,8 +580,10 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
   }
 #undef GDWD_BARRIER
 #undef GDWD_MARK
+#undef RS
 }
 
+// Phase-local region of the iteration kernel plus the resident row state ahead of it.
 template <typename T>
 static size_t union_bytes(const Layout& L, int grid) {
   using CT = typename ElemTraits<T>::compute_t;
@@ -550,7 +599,7 @@ static size_t union_bytes(const Layout& L, int grid) {
   size_t u = a_bytes;
   if (b_bytes > u) u = b_bytes;
   if (r_bytes > u) u = r_bytes;
-  return (u + 127) & ~(size_t)127;
+  return ((u + 127) & ~(size_t)127) + row_state_bytes((L.n + grid - 1) / grid);
 }
 
 

@@ -618,12 +618,13 @@ __global__ void __launch_bounds__(kThreads, 1) factor_kernel(FactorArgs a) {
   }
   FBAR();
 
-  // ---------------- Cholesky, right-looking over tile columns.  Every CTA factors
-  // the diagonal tile itself (all threads, FP64) and solves its panel rows with it,
-  // so no grid barrier separates the two; CTA 0 writes the factored tile back
-  // during the trailing update, which does not touch it.
-  for (int k = 0; k < nb; ++k) {
-    const int64_t k0 = (int64_t)k * kNB;
+  // ---------------- Cholesky, right-looking over tile columns, with a look-ahead of
+  // one tile: CTA 0 applies step k's update to diagonal tile k+1 first and factors
+  // it (all its threads, FP64) while the other CTAs apply the rest of step k's
+  // trailing update, so the factor of a diagonal tile is off the critical path
+  // whenever the trailing update takes longer.  Every CTA then reads the factored
+  // tile for its panel rows.
+  auto factor_diag = [&](int64_t k0) {    // CTA 0: D <- tile (k0, k0) of A, factor, store L
     for (int t = threadIdx.x; t < kNB * kNB; t += kThreads) {
       const int r = t / kNB, c = t % kNB;
       const int64_t gr = k0 + r, gc = k0 + c;
@@ -631,6 +632,26 @@ __global__ void __launch_bounds__(kThreads, 1) factor_kernel(FactorArgs a) {
     }
     __syncthreads();
     chol_tile(D, Dinv, a.err);
+    for (int t = threadIdx.x; t < kNB * kNB; t += kThreads) {
+      const int r = t / kNB, c = t % kNB;
+      const int64_t gr = k0 + r, gc = k0 + c;
+      if (gr < n && gc < n && c <= r) A[gr * n + gc] = d2f(D[r][c]);
+    }
+    __syncthreads();
+  };
+  if (cta == 0) factor_diag(0);
+  FBAR();
+  for (int k = 0; k < nb; ++k) {
+    const int64_t k0 = (int64_t)k * kNB;
+    // the factored diagonal tile L_kk and the reciprocals of its diagonal
+    for (int t = threadIdx.x; t < kNB * kNB; t += kThreads) {
+      const int r = t / kNB, c = t % kNB;
+      const int64_t gr = k0 + r, gc = k0 + c;
+      D[r][c] = (gr < n && gc < n && c <= r) ? f2d(A[gr * n + gc]) : (gr == gc ? 1.0 : 0.0);
+    }
+    __syncthreads();
+    if (threadIdx.x < kNB) Dinv[threadIdx.x] = rcp_nr(D[threadIdx.x][threadIdx.x]);
+    __syncthreads();
     // panel rows below the diagonal tile: L_ik = A_ik L_kk^{-T}, one warp per row (FP64)
     for (int64_t i = k0 + kNB + (int64_t)cta * kWarps + warp; i < n; i += (int64_t)grid * kWarps) {
       double x = (k0 + lane < n) ? f2d(A[i * n + k0 + lane]) : 0.0;
@@ -642,18 +663,13 @@ __global__ void __launch_bounds__(kThreads, 1) factor_kernel(FactorArgs a) {
       if (k0 + lane < n) A[i * n + k0 + lane] = d2f(x);
     }
     FBAR();
-    if (cta == 0) {
-      for (int t = threadIdx.x; t < kNB * kNB; t += kThreads) {
-        const int r = t / kNB, c = t % kNB;
-        const int64_t gr = k0 + r, gc = k0 + c;
-        if (gr < n && gc < n && c <= r) A[gr * n + gc] = d2f(D[r][c]);
-      }
-    }
-    // trailing update A_IJ -= L_Ik L_Jk^T for tiles k < J <= I (double-float)
+    // trailing update A_IJ -= L_Ik L_Jk^T for tiles k < J <= I (double-float).
+    // Tile 0 is the next diagonal tile: CTA 0 updates and factors it; the other
+    // tiles go round-robin to the other CTAs (to all CTAs on a grid of one).
     {
       const int m = nb - k - 1;
       const int ntile = m * (m + 1) / 2;
-      for (int t = cta; t < ntile; t += grid) {
+      auto update_tile = [&](int t) {
         int ii, jj;
         tri_index(t, ii, jj);
         const int64_t I0 = (int64_t)(k + 1 + ii) * kNB, J0 = (int64_t)(k + 1 + jj) * kNB;
@@ -665,6 +681,18 @@ __global__ void __launch_bounds__(kThreads, 1) factor_kernel(FactorArgs a) {
         __syncthreads();
         store_tile_df(T0, A, n, I0, J0);
         __syncthreads();
+      };
+      if (m > 0) {
+        if (cta == 0) {
+          update_tile(0);
+          factor_diag(k0 + kNB);
+        }
+        if (grid > 1) {
+          for (int t = cta; t < ntile; t += grid - 1)
+            if (cta > 0) update_tile(t);
+        } else {
+          for (int t = 1; t < ntile; ++t) update_tile(t);
+        }
       }
     }
     FBAR();

@@ -618,12 +618,15 @@ __global__ void __launch_bounds__(kThreads, 1) factor_kernel(FactorArgs a) {
   }
   FBAR();
 
-  // ---------------- Cholesky, right-looking over tile columns, with a look-ahead of
-  // one tile: CTA 0 applies step k's update to diagonal tile k+1 first and factors
-  // it (all its threads, FP64) while the other CTAs apply the rest of step k's
-  // trailing update, so the factor of a diagonal tile is off the critical path
-  // whenever the trailing update takes longer.  Every CTA then reads the factored
-  // tile for its panel rows.
+  // ---------------- Cholesky and X = L^{-1} in one sweep over tile columns k.
+  // Phase 1: with the factored diagonal tile L_kk, the panel rows below it
+  // (L_ik = A_ik L_kk^{-T}) and tile row k of X (X_kJ <- L_kk^{-1} X_kJ, J <= k; its
+  // updates from the steps before k are complete) -- n warp tasks in all.
+  // Phase 2: the trailing update of the Cholesky (A_IJ -= L_Ik L_Jk^T, k < J <= I)
+  // and of the inverse (X_IJ -= L_Ik X_kJ, I > k >= J), tile-parallel; CTA 0
+  // instead updates diagonal tile k+1 and factors it (FP64, all its threads), a
+  // look-ahead of one tile that keeps the diagonal factor off the critical path
+  // whenever the trailing update takes longer.  Two grid barriers per k.
   auto factor_diag = [&](int64_t k0) {    // CTA 0: D <- tile (k0, k0) of A, factor, store L
     for (int t = threadIdx.x; t < kNB * kNB; t += kThreads) {
       const int r = t / kNB, c = t % kNB;
@@ -639,6 +642,15 @@ __global__ void __launch_bounds__(kThreads, 1) factor_kernel(FactorArgs a) {
     }
     __syncthreads();
   };
+  // forward substitution L_kk x = b on one warp (lane r holds entry r; FP64)
+  auto trsv = [&](double x) {
+    for (int c = 0; c < kNB; ++c) {
+      const double xc = __shfl_sync(0xffffffffu, x, c) * Dinv[c];
+      if (lane == c) x = xc;
+      if (lane > c) x -= xc * D[lane][c];
+    }
+    return x;
+  };
   if (cta == 0) factor_diag(0);
   FBAR();
   for (int k = 0; k < nb; ++k) {
@@ -652,24 +664,31 @@ __global__ void __launch_bounds__(kThreads, 1) factor_kernel(FactorArgs a) {
     __syncthreads();
     if (threadIdx.x < kNB) Dinv[threadIdx.x] = rcp_nr(D[threadIdx.x][threadIdx.x]);
     __syncthreads();
-    // panel rows below the diagonal tile: L_ik = A_ik L_kk^{-T}, one warp per row (FP64)
-    for (int64_t i = k0 + kNB + (int64_t)cta * kWarps + warp; i < n; i += (int64_t)grid * kWarps) {
-      double x = (k0 + lane < n) ? f2d(A[i * n + k0 + lane]) : 0.0;
-      for (int c = 0; c < kNB; ++c) {
-        const double xc = __shfl_sync(0xffffffffu, x, c) * Dinv[c];
-        if (lane == c) x = xc;
-        if (lane > c) x -= xc * D[lane][c];
+    // phase 1: panel rows i >= k0 + 32 of A, then columns j < min(n, k0 + 32) of X's tile row k
+    {
+      const int64_t npanel = (n > k0 + kNB) ? n - k0 - kNB : 0;
+      const int64_t ncols = (n < k0 + kNB) ? n : k0 + kNB;
+      for (int64_t q = (int64_t)cta * kWarps + warp; q < npanel + ncols; q += (int64_t)grid * kWarps) {
+        if (q < npanel) {
+          const int64_t i = k0 + kNB + q;
+          const double x = trsv((k0 + lane < n) ? f2d(A[i * n + k0 + lane]) : 0.0);
+          if (k0 + lane < n) A[i * n + k0 + lane] = d2f(x);
+        } else {
+          const int64_t j = q - npanel;
+          const double x = trsv((k0 + lane < n) ? f2d(X[(k0 + lane) * n + j]) : 0.0);
+          if (k0 + lane < n) X[(k0 + lane) * n + j] = d2f(x);
+        }
       }
-      if (k0 + lane < n) A[i * n + k0 + lane] = d2f(x);
     }
     FBAR();
-    // trailing update A_IJ -= L_Ik L_Jk^T for tiles k < J <= I (double-float).
-    // Tile 0 is the next diagonal tile: CTA 0 updates and factors it; the other
-    // tiles go round-robin to the other CTAs (to all CTAs on a grid of one).
+    // phase 2: tile 0 of the Cholesky update is the next diagonal tile (CTA 0);
+    // the other Cholesky tiles and the inverse tiles go round-robin to the other
+    // CTAs (to all CTAs on a grid of one)
     {
       const int m = nb - k - 1;
-      const int ntile = m * (m + 1) / 2;
-      auto update_tile = [&](int t) {
+      const int ntc = m * (m + 1) / 2;        // Cholesky tiles (tile 0 = the next diagonal)
+      const int nti = m * (k + 1);            // inverse tiles
+      auto chol_tile_update = [&](int t) {
         int ii, jj;
         tri_index(t, ii, jj);
         const int64_t I0 = (int64_t)(k + 1 + ii) * kNB, J0 = (int64_t)(k + 1 + jj) * kNB;
@@ -682,50 +701,7 @@ __global__ void __launch_bounds__(kThreads, 1) factor_kernel(FactorArgs a) {
         store_tile_df(T0, A, n, I0, J0);
         __syncthreads();
       };
-      if (m > 0) {
-        if (cta == 0) {
-          update_tile(0);
-          factor_diag(k0 + kNB);
-        }
-        if (grid > 1) {
-          for (int t = cta; t < ntile; t += grid - 1)
-            if (cta > 0) update_tile(t);
-        } else {
-          for (int t = 1; t < ntile; ++t) update_tile(t);
-        }
-      }
-    }
-    FBAR();
-  }
-
-  // ---------------- X = L^{-1}: L X = I by tile rows (X starts as I)
-  for (int k = 0; k < nb; ++k) {
-    const int64_t k0 = (int64_t)k * kNB;
-    for (int t = threadIdx.x; t < kNB * kNB; t += kThreads) {
-      const int r = t / kNB, c = t % kNB;
-      const int64_t gr = k0 + r, gc = k0 + c;
-      D[r][c] = (gr < n && gc < n) ? f2d(A[gr * n + gc]) : (gr == gc ? 1.0 : 0.0);
-    }
-    __syncthreads();
-    if (threadIdx.x < kNB) Dinv[threadIdx.x] = rcp_nr(D[threadIdx.x][threadIdx.x]);
-    __syncthreads();
-    // X[k-tile rows, j] = L_kk^{-1} X[k-tile rows, j] for j < k0 + 32: one warp per column (FP64)
-    const int64_t ncols = (n < k0 + kNB) ? n : k0 + kNB;
-    for (int64_t j = (int64_t)cta * kWarps + warp; j < ncols; j += (int64_t)grid * kWarps) {
-      double x = (k0 + lane < n) ? f2d(X[(k0 + lane) * n + j]) : 0.0;
-      for (int c = 0; c < kNB; ++c) {
-        const double xc = __shfl_sync(0xffffffffu, x, c) * Dinv[c];
-        if (lane == c) x = xc;
-        if (lane > c) x -= xc * D[lane][c];
-      }
-      if (k0 + lane < n) X[(k0 + lane) * n + j] = d2f(x);
-    }
-    FBAR();
-    // X[I, J] -= L[I, k] X[k, J] for tile rows I > k, tile columns J <= k (double-float)
-    {
-      const int m = nb - k - 1;
-      const int ntile = m * (k + 1);
-      for (int t = cta; t < ntile; t += grid) {
+      auto inv_tile_update = [&](int t) {
         const int ii = t / (k + 1), jj = t % (k + 1);
         const int64_t I0 = (int64_t)(k + 1 + ii) * kNB, J0 = (int64_t)jj * kNB;
         load_tile_df(T0, X, n, I0, J0, false);
@@ -740,6 +716,21 @@ __global__ void __launch_bounds__(kThreads, 1) factor_kernel(FactorArgs a) {
         __syncthreads();
         store_tile_df(T0, X, n, I0, J0);
         __syncthreads();
+      };
+      auto task = [&](int u) {               // u = 0 .. ntc - 2: Cholesky tile u + 1; then inverse tiles
+        if (u < ntc - 1) chol_tile_update(u + 1);
+        else inv_tile_update(u - (ntc - 1));
+      };
+      const int ntask = (ntc > 0 ? ntc - 1 : 0) + nti;
+      if (m > 0 && cta == 0) {
+        chol_tile_update(0);
+        factor_diag(k0 + kNB);
+      }
+      if (grid > 1) {
+        if (cta > 0)
+          for (int u = cta - 1; u < ntask; u += grid - 1) task(u);
+      } else {
+        for (int u = 0; u < ntask; ++u) task(u);
       }
     }
     FBAR();

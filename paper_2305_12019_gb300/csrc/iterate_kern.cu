@@ -121,7 +121,8 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kern_kernel(KernArgs a) {
   __shared__ int s_flag;
   __shared__ double s_tot[S_COUNT];
   __shared__ double s_ctl[8];
-  __shared__ double s_eta[9];
+  __shared__ double s_pd[4];     // pobj, dobj, theta, ||w||
+  __shared__ float s_etaf[10];   // gap and the nine residuals
   __shared__ double s_rows[9 * kMaxRowsPerCta];    // per-row partial sums
   __shared__ double s_x[kMaxRowsPerCta + 1];      // GEMV results of the CTA's rows (+ the p^T rhs row)
   __shared__ double s_k[3][kMaxRowsPerCta];
@@ -141,6 +142,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kern_kernel(KernArgs a) {
   const double inv_q = 1.0 / a.q;
   const float inv_den = (float)(1.0 / den);
   const double sqrt_tol = sqrt(a.tol);
+  const SPhaseArgs sq{a.C, a.kappa, a.R, a.mu, a.tau, sqmu, a.tol, sqrt_tol, inv_den, a.stop_rule};
   const double ac = sqmu * (1.0 - a.tau);              // Z~ alpha + ac rho enters eta_D3
 
   // this thread's row
@@ -338,84 +340,16 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kern_kernel(KernArgs a) {
     grid_totals(a.scal, grid, KS_TA2 + 1, s_tot);
     __syncthreads();
     GDWD_MARK(13);
-    // three independent FP64 chains on three warps, as in the Z-streaming kernel
-    if (lane == 0 && warp == 1) {
-      const double ta2 = fmax(0.0, s_tot[KS_TA2]);
-      const double pobj = s_tot[S_PRIM_R] + a.C * s_tot[S_PRIM_XI];
-      const double dobj = a.kappa * s_tot[S_DUAL_A] - a.R * sqrt_nr(ta2);
-      s_eta[0] = pobj;
-      s_eta[1] = dobj;
-      s_eta[2] = (double)((float)fabs(pobj - dobj) / (float)(1.0 + fabs(pobj) + fabs(dobj)));
-    } else if (lane == 0 && warp == 2) {
-      s_eta[3] = sqrtf((float)s_tot[S_RES2]) * inv_den;       // p1
-      s_eta[4] = sqrtf((float)s_tot[S_AMIN2]) * inv_den;      // dd1
-      s_eta[5] = sqrtf((float)s_tot[S_AMAX2]) * inv_den;      // dd2
-      s_eta[6] = fabs(s_tot[S_YA]) * inv_den;                 // c1
-      s_eta[7] = fabs(s_tot[S_XICA]) * inv_den;               // c2
-      s_eta[8] = sqrtf((float)s_tot[S_AMS2]) * inv_den;       // c3
-    }
-    double p2 = 0.0, p3 = 0.0, dd3 = 0.0, wn = 0.0, th = 1.0;
+    // a = Z~ alpha + sqrt(mu)(1 - tau) rho: ||a||^2 and <a, g> from the K products
     if (threadIdx.x == 0) {
-      const double S1 = fmax(0.0, s_tot[KS_G2]), S2 = s_tot[KS_GR], S3 = fmax(0.0, s_tot[KS_R2]);
-      // a = Z~ alpha + ac rho: ||a||^2 and <a, g> from the K products
+      const double S2 = s_tot[KS_GR], S3 = fmax(0.0, s_tot[KS_R2]);
       const double A2 = s_tot[KS_TA2] + 2.0 * ac * s_tot[KS_AR] + ac * ac * S3;
       const double AG = s_tot[KS_AG] + ac * S2;
-      const double gs = rcp_nr(sig * sqmu);
-      const double gnorm = sqrt_nr(S1);
-      th = (gnorm <= a.R) ? 1.0 : div_nr(a.R, gnorm);                        // Step 2 projection
-      const double w2 = fmax(0.0, S1 + 2.0 * gs * S2 + gs * gs * S3);        // ||w||^2
-      const double om = 1.0 - th;
-      const double wu2 = fmax(0.0, om * om * S1 + 2.0 * om * gs * S2 + gs * gs * S3);   // ||w - u+||^2
-      const double kap = a.tau * sig * a.mu * om;
-      const double d3 = fmax(0.0, A2 - 2.0 * kap * AG + kap * kap * S1);
-      const float wnf = sqrtf((float)w2);
-      const double wmr = (w2 - a.R * a.R) * (double)(1.0f / (wnf + (float)a.R));   // ||w|| - R
-      p2 = sqrtf((float)(a.mu * wu2)) * inv_den;
-      p3 = fmax(wmr, 0.0) * inv_den;
-      dd3 = sqrtf((float)d3) * inv_den;
-      wn = (double)wnf;
+      s_tot[S_A2] = A2;
+      s_tot[S_AG] = AG;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      const double pobj = s_eta[0], dobj = s_eta[1], gap = s_eta[2];
-      const double p1 = s_eta[3], dd1 = s_eta[4], dd2 = s_eta[5], c1 = s_eta[6], c2 = s_eta[7], c3 = s_eta[8];
-      const double ep = fmax(p1, fmax(p2, p3)), ed = fmax(dd1, fmax(dd2, dd3)), ec = fmax(c1, fmax(c2, c3));
-      const double kkt = fmax(fmax(ep, ed), fmax(ec, gap));
-      int done = 0;
-      double sig_next = sig;
-      if (!(kkt == kkt) || isinf(kkt)) {
-        done = 1;
-        status = GDWD_ENUMERIC;
-      } else if (a.stop_rule == 0 ? kkt <= a.tol
-                                  : (fmax(ep, ed) < a.tol && fmin(ec, gap) < sqrt_tol && fmax(ec, gap) < 0.05)) {
-        done = 1;
-        status = GDWD_OK;
-      } else if (it >= 1 && fmin(ep, ed) > 1e-3 * a.tol) {                          // sigma rule, Sec. 4.4
-        const float chi = (float)ep / fmaxf((float)ed, 1e-30f);
-        const float ichi = (float)ed / fmaxf((float)ep, 1e-30f);
-        const float big = fmaxf(chi, ichi);
-        const double zeta = big > 500.f ? 2.2 : (big > 50.f ? 1.65 : 1.1);
-        if (chi > 5.f) sig_next = sig * zeta;
-        else if (ichi > 5.f) sig_next = sig / zeta;
-      }
-      s_ctl[0] = th;
-      s_ctl[1] = sig_next;
-      s_ctl[2] = done;
-      s_ctl[3] = status;
-      if (cta == 0) {
-        Ctrl* c = a.ctrl;
-        c->beta = beta;
-        c->pobj = pobj;
-        c->dobj = dobj;
-        c->kkt = kkt;
-        c->eta_p1 = p1; c->eta_p2 = p2; c->eta_p3 = p3;
-        c->eta_d1 = dd1; c->eta_d2 = dd2; c->eta_d3 = dd3;
-        c->eta_c1 = c1; c->eta_c2 = c2; c->eta_c3 = c3;
-        c->eta_gap = gap;
-        c->wnorm = wn;
-      }
-    }
-    __syncthreads();
+    s_phase(s_tot, sq, sig, it, beta, status, cta == 0, a.ctrl, s_pd, s_etaf, s_ctl);
     GDWD_MARK(10);
     sig_prev = sig;
     theta = s_ctl[0];

@@ -167,6 +167,99 @@ __device__ __forceinline__ void rows_sum(const double (&v)[N], int tr, bool mine
   }
 }
 
+// The scalar part of phase S, identical in every CTA, once the totals are in
+// s_tot (Scal layout): the KKT residuals of Sec. 4.3 (readings R6, R7, R9), the
+// duality gap, the stop test (R8) and the sigma rule of Sec. 4.4 (R5, R5b).
+// Three independent chains run on lane 0 of warps 0, 1 and 2: the projection and
+// the w quantities (FP64 where cancellation needs it: theta, ||w|| - R, the
+// eta_D3 expansion), the objectives and the gap, and the plain norms (FP32: they
+// are compared with tol).  The maxima, the stop test and the sigma rule are FP32.
+// s_ctl receives theta, sigma of the next iteration, done and the status; CTA 0
+// also writes the residuals to ctrl.
+struct SPhaseArgs {
+  double C, kappa, R, mu, tau, sqmu, tol, sqrt_tol;
+  float inv_den;
+  int stop_rule;
+};
+
+__device__ __forceinline__ void s_phase(const double* s_tot, const SPhaseArgs& q, double sig, int it, double beta,
+                                        int status, bool cta0, Ctrl* ctrl, double* s_pd, float* s_etaf,
+                                        double* s_ctl) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0 && warp == 1) {
+    const double pobj = s_tot[S_PRIM_R] + q.C * s_tot[S_PRIM_XI];
+    const double dobj = q.kappa * s_tot[S_DUAL_A] - q.R * sqrt_nr(fmax(0.0, s_tot[S_TA2]));
+    s_pd[0] = pobj;
+    s_pd[1] = dobj;
+    s_etaf[0] = (float)fabs(pobj - dobj) / (float)(1.0 + fabs(pobj) + fabs(dobj));   // gap
+  } else if (lane == 0 && warp == 2) {
+    s_etaf[1] = sqrtf((float)s_tot[S_RES2]) * q.inv_den;       // p1
+    s_etaf[2] = sqrtf((float)s_tot[S_AMIN2]) * q.inv_den;      // dd1
+    s_etaf[3] = sqrtf((float)s_tot[S_AMAX2]) * q.inv_den;      // dd2
+    s_etaf[4] = fabsf((float)s_tot[S_YA]) * q.inv_den;         // c1
+    s_etaf[5] = fabsf((float)s_tot[S_XICA]) * q.inv_den;       // c2
+    s_etaf[6] = sqrtf((float)s_tot[S_AMS2]) * q.inv_den;       // c3
+  } else if (threadIdx.x == 0) {
+    const double S1 = fmax(0.0, s_tot[S_G2]), S2 = s_tot[S_GRHO], S3 = fmax(0.0, s_tot[S_RHO2]);
+    const double gs = rcp_nr(sig * q.sqmu);
+    const double gnorm = sqrt_nr(S1);
+    const double th = (gnorm <= q.R) ? 1.0 : div_nr(q.R, gnorm);                 // Step 2 projection
+    const double w2 = fmax(0.0, S1 + 2.0 * gs * S2 + gs * gs * S3);              // ||w||^2
+    const double om = 1.0 - th;
+    const double wu2 = fmax(0.0, om * om * S1 + 2.0 * om * gs * S2 + gs * gs * S3);   // ||w - u+||^2
+    const double kap = q.tau * sig * q.mu * om;
+    const double d3 = fmax(0.0, s_tot[S_A2] - 2.0 * kap * s_tot[S_AG] + kap * kap * S1);
+    const float wnf = sqrtf((float)w2);
+    const double wmr = (w2 - q.R * q.R) * (double)(1.0f / (wnf + (float)q.R));   // ||w|| - R
+    s_pd[2] = th;
+    s_pd[3] = (double)wnf;
+    s_etaf[7] = sqrtf((float)q.mu * (float)wu2) * q.inv_den;   // p2
+    s_etaf[8] = (float)fmax(wmr, 0.0) * q.inv_den;            // p3
+    s_etaf[9] = sqrtf((float)d3) * q.inv_den;                 // dd3
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const float gap = s_etaf[0], p1 = s_etaf[1], dd1 = s_etaf[2], dd2 = s_etaf[3], c1 = s_etaf[4], c2 = s_etaf[5],
+                c3 = s_etaf[6], p2 = s_etaf[7], p3 = s_etaf[8], dd3 = s_etaf[9];
+    const float ep = fmaxf(p1, fmaxf(p2, p3)), ed = fmaxf(dd1, fmaxf(dd2, dd3)), ec = fmaxf(c1, fmaxf(c2, c3));
+    const float kkt = fmaxf(fmaxf(ep, ed), fmaxf(ec, gap));
+    const float tolf = (float)q.tol;
+    int done = 0;
+    double sig_next = sig;
+    if (!(kkt == kkt) || isinf(kkt)) {
+      done = 1;
+      status = GDWD_ENUMERIC;
+    } else if (q.stop_rule == 0 ? (double)kkt <= q.tol
+                                : (fmaxf(ep, ed) < tolf && fminf(ec, gap) < (float)q.sqrt_tol && fmaxf(ec, gap) < 0.05f)) {
+      done = 1;
+      status = GDWD_OK;
+    } else if (it >= 1 && fminf(ep, ed) > 1e-3f * tolf) {                            // sigma rule, Sec. 4.4
+      const float chi = ep / fmaxf(ed, 1e-30f);
+      const float ichi = ed / fmaxf(ep, 1e-30f);
+      const float big = fmaxf(chi, ichi);
+      const double zeta = big > 500.f ? 2.2 : (big > 50.f ? 1.65 : 1.1);
+      if (chi > 5.f) sig_next = sig * zeta;
+      else if (ichi > 5.f) sig_next = sig / zeta;
+    }
+    s_ctl[0] = s_pd[2];
+    s_ctl[1] = sig_next;
+    s_ctl[2] = done;
+    s_ctl[3] = status;
+    if (cta0) {
+      ctrl->beta = beta;
+      ctrl->pobj = s_pd[0];
+      ctrl->dobj = s_pd[1];
+      ctrl->kkt = kkt;
+      ctrl->eta_p1 = p1; ctrl->eta_p2 = p2; ctrl->eta_p3 = p3;
+      ctrl->eta_d1 = dd1; ctrl->eta_d2 = dd2; ctrl->eta_d3 = dd3;
+      ctrl->eta_c1 = c1; ctrl->eta_c2 = c2; ctrl->eta_c3 = c3;
+      ctrl->eta_gap = gap;
+      ctrl->wnorm = s_pd[3];
+    }
+  }
+  __syncthreads();
+}
+
 // x_i = sum_j P_ij rhs_j for one row, one warp, double-float (result in all lanes).
 // Four independent 16-byte loads per lane per step keep several L2 requests in flight.
 __device__ __forceinline__ df row_dot(const float2* __restrict__ Prow, const float2* rhs_s, int npair) {

@@ -263,13 +263,13 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
   bool dots_prev = false;   // the last pass B took the column dots Z~^T u
   for (; it < a.max_iter; ++it) {
     const double inv_sig = rcp_nr(sig);
+    const double gs_it = rcp_nr(sig * sqmu);   // 1 / (sigma sqrt(mu)) of this iteration
     // ---------------- phase R (this CTA's rows): U_g = Z~^T g of the last iteration
     // from the pass-B column dots Z~^T u and (G - I) c; the deferred update
     // U_u = theta U_g, U_rho <- (1 - tau) U_rho - tau sigma' sqrt(mu) (1 - theta) U_g;
     // b = U_u + U_rho / (sigma sqrt(mu)); rhs1 = b + xi - r - alpha / sigma
     ring_prefetch(L, rg, cta, grid);   // this iteration's first Z chunks arrive during R, N1, N2
     {
-      const double gsc = rcp_nr(sig * sqmu);
       const double rcoef = a.tau * sig_prev * sqmu * (1.0 - theta);
       if (pending && dots_prev) {
         // the column dots Z~^T u of the last pass: one warp per row sums its slabs
@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
           RS(RS_UU, t) = uu;
           RS(RS_UR, t) = ur;
         }
-        const double bi = uu + ur * gsc;
+        const double bi = uu + ur * gs_it;
         RS(RS_B, t) = bi;
         const double v = RS(RS_XI, t) - RS(RS_R, t) - RS(RS_AL, t) * inv_sig;
         const df r1 = df_from(bi + v);
@@ -463,7 +463,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
     grid_totals(a.scal, grid, S_COUNT - 1, s_tot);
     __syncthreads();
     GDWD_MARK(13);
-    s_phase(s_tot, sq, sig, it, beta, status, cta == 0, a.ctrl, s_pd, s_etaf, s_ctl);
+    s_phase(s_tot, sq, sig, gs_it, it, beta, status, cta == 0, a.ctrl, s_pd, s_etaf, s_ctl);
     GDWD_MARK(10);
     sig_prev = sig;
     theta = s_ctl[0];

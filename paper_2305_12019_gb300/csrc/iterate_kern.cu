@@ -228,6 +228,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kern_kernel(KernArgs a) {
   int it = it0;
   for (; it < a.max_iter; ++it) {
     const double inv_sig = rcp_nr(sig);
+    const double gs_it = rcp_nr(sig * sqmu);   // 1 / (sigma sqrt(mu)) of this iteration
     // ---------------- phase R (this thread's row): the deferred update
     // a_u = theta a_g, a_rho <- (1 - tau) a_rho - tau sigma' sqrt(mu) (1 - theta) a_g
     // and the same update of their images U_u = K a_u, U_rho = K a_rho from the
@@ -240,7 +241,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kern_kernel(KernArgs a) {
         au = theta * ag;
         ar = (1.0 - a.tau) * ar - rcoef * ag;
       }
-      bi = Uu + Ur * rcp_nr(sig * sqmu);
+      bi = Uu + Ur * gs_it;
       a.rhsA[i] = to_f2(bi + (xii - ri - ali * inv_sig));
     }
     GDWD_BARRIER(2);
@@ -349,7 +350,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kern_kernel(KernArgs a) {
       s_tot[S_AG] = AG;
     }
     __syncthreads();
-    s_phase(s_tot, sq, sig, it, beta, status, cta == 0, a.ctrl, s_pd, s_etaf, s_ctl);
+    s_phase(s_tot, sq, sig, gs_it, it, beta, status, cta == 0, a.ctrl, s_pd, s_etaf, s_ctl);
     GDWD_MARK(10);
     sig_prev = sig;
     theta = s_ctl[0];

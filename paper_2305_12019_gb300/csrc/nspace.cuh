@@ -12,7 +12,24 @@ namespace gdwd {
 // s^(q+1) (s - a) = kq,  kq = omega / sigma, by Newton's iteration of Sec. 3.2
 // kept inside the bracket [max(a,0), max(a,0) + max(kq, 1)] (f < 0 at the left
 // end, f >= 0 at the right end); steps that leave it are bisected.
+//
+// A dependent FP64 operation takes ~64 cycles on this part (an FP32 one ~4.5, a
+// division ~360), and the prox is on the critical path of every iteration.  So
+// the same safeguarded iteration first runs in FP32 to ~2e-6 relative; the FP64
+// iteration then starts there and stops once a Newton correction is below 1e-9
+// relative: by its quadratic convergence the error after that step is ~1e-18,
+// so two FP64 steps replace the ~4 that a 4-eps test on the correction needs.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ float pow_q1f(float s, float q, int qcase) {  // s^(q+1), FP32
+  switch (qcase) {
+    case 1: return s * s;
+    case 2: return s * s * s;
+    case 4: { float s2 = s * s; return s2 * s2 * s; }
+    case 5: return s * sqrtf(s);
+    default: return powf(s, q + 1.0f);
+  }
+}
+
 __device__ __forceinline__ double pow_q1(double s, double q, int qcase) {  // s^(q+1)
   switch (qcase) {
     case 1: return s * s;
@@ -31,16 +48,39 @@ __device__ inline double prox_root(double a, double kq, double q, int qcase, dou
   double lo = fmax(a, 0.0);
   double hi = lo + fmax(kq, 1.0);
   double s = (r0 > lo && r0 < hi) ? r0 : 0.5 * (lo + hi);
+  // FP32 start (inputs well inside the FP32 range; its own bracket)
+  if (fabs(a) < 1e15 && kq > 1e-20 && kq < 1e15 && hi < 1e15 && q <= 8.0) {
+    const float af = (float)a, kf = (float)kq, qf = (float)q;
+    float lf = (float)lo, hf = (float)hi, sf = (float)s;
+    for (int it = 0; it < 30; ++it) {
+      const float sq1 = pow_q1f(sf, qf, qcase);
+      const float f = sq1 * (sf - af) - kf;
+      if (f < 0.f) lf = sf;
+      else if (f > 0.f) hf = sf;
+      else break;
+      const float nt = sf * (kf * (qf + 2.f) + af * sq1) / (kf * (qf + 1.f) + sq1 * sf);
+      if (fabsf(nt - sf) <= 2e-6f * sf) {
+        sf = nt;
+        break;
+      }
+      sf = (nt > lf && nt < hf) ? nt : 0.5f * (lf + hf);
+    }
+    const double sd = (double)sf;
+    if (sd > lo && sd < hi) s = sd;
+  }
   for (int it = 0; it < 100; ++it) {
     const double sq1 = pow_q1(s, q, qcase);
     const double f = sq1 * (s - a) - kq;
     if (f < 0.0) lo = s;
     else if (f > 0.0) hi = s;
     else break;
-    const double nt = s * (kq * (q + 2.0) + a * sq1) / (kq * (q + 1.0) + sq1 * s);
-    // converged when the Newton correction is below 4 eps relative: tested before the
-    // safeguard, so rounding noise in f at the root cannot trigger a bisection step
-    if (fabs(nt - s) <= 8.881784197001252e-16 * s) {
+    const double num = kq * (q + 2.0) + a * sq1, den = kq * (q + 1.0) + sq1 * s;
+    // division by an FP32 seed and one FP64 correction (~1e-14) when den is in FP32 range
+    const double nt = s * ((den > 1e-30 && den < 1e30) ? div_nr(num, den) : num / den);
+    // converged when the correction is below 1e-9 relative (then taken): tested
+    // before the safeguard, so rounding noise in f at the root cannot trigger a
+    // bisection step
+    if (fabs(nt - s) <= 1e-9 * s) {
       s = nt;
       break;
     }
@@ -135,8 +175,13 @@ __device__ __forceinline__ void grid_totals(const double* scal, int grid, int ns
         const int c2 = base + sub + 16 * q;
         v[q] = c2 < grid ? part[c2] : 0.0;
       }
+      // pairwise (depth 4 instead of a chain of 12 FP64 adds)
 #pragma unroll
-      for (int q = 0; q < 12; ++q) acc += v[q];
+      for (int q = 0; q < 6; ++q) v[q] += v[q + 6];
+      v[0] += v[3];
+      v[1] += v[4];
+      v[2] += v[5];
+      acc += (v[0] + v[1]) + v[2];
     }
   }
 #pragma unroll
@@ -174,15 +219,16 @@ __device__ __forceinline__ void rows_sum(const double (&v)[N], int tr, bool mine
 // the w quantities (FP64 where cancellation needs it: theta, ||w|| - R, the
 // eta_D3 expansion), the objectives and the gap, and the plain norms (FP32: they
 // are compared with tol).  The maxima, the stop test and the sigma rule are FP32.
-// s_ctl receives theta, sigma of the next iteration, done and the status; CTA 0
-// also writes the residuals to ctrl.
+// gs = 1 / (sigma sqrt(mu)).  s_ctl receives theta, sigma of the next iteration,
+// done and the status; CTA 0 also writes the residuals to ctrl.
 struct SPhaseArgs {
   double C, kappa, R, mu, tau, sqmu, tol, sqrt_tol;
   float inv_den;
   int stop_rule;
 };
 
-__device__ __forceinline__ void s_phase(const double* s_tot, const SPhaseArgs& q, double sig, int it, double beta,
+__device__ __forceinline__ void s_phase(const double* s_tot, const SPhaseArgs& q, double sig, double gs, int it,
+                                        double beta,
                                         int status, bool cta0, Ctrl* ctrl, double* s_pd, float* s_etaf,
                                         double* s_ctl) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -201,7 +247,6 @@ __device__ __forceinline__ void s_phase(const double* s_tot, const SPhaseArgs& q
     s_etaf[6] = sqrtf((float)s_tot[S_AMS2]) * q.inv_den;       // c3
   } else if (threadIdx.x == 0) {
     const double S1 = fmax(0.0, s_tot[S_G2]), S2 = s_tot[S_GRHO], S3 = fmax(0.0, s_tot[S_RHO2]);
-    const double gs = rcp_nr(sig * q.sqmu);
     const double gnorm = sqrt_nr(S1);
     const double th = (gnorm <= q.R) ? 1.0 : div_nr(q.R, gnorm);                 // Step 2 projection
     const double w2 = fmax(0.0, S1 + 2.0 * gs * S2 + gs * gs * S3);              // ||w||^2

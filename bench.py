@@ -220,6 +220,7 @@ def main():
     ap.add_argument("--big-n", type=int, default=5000)
     ap.add_argument("--kern-wide-d", type=int, default=200000)
     ap.add_argument("--kern-steps", type=int, default=3)
+    ap.add_argument("--kern", type=int, default=0, help="uneven_batch / served: 1 = kernelized iteration")
     args = ap.parse_args()
     if args.workload != "spiked_fp32" and args.impl != "reference":
         import bench_workloads

@@ -12,6 +12,7 @@ stand-ins for the paper's data sets (see paper_2305_12019_gb300/synth.py).
   served        Poisson arrivals (200/s for 10 s by default) of FP16 problems with
                 d log-uniform 1k-100k, n 50-5000, q in {1,2}, C 0.1-100, generated
                 on the device per request seed: p50 / p99 latency and solves/s
+                (uneven_batch and served: --kern 1 runs the kernelized iteration)
   largest_fp8   d=200000, n=5000, Student-t columns, 1:3, 16 values of C, E4M3
                 storage with the FP32 refinement sweep: C-solves/s
   kernelized    the kernelized n-space iteration (no pass over Z per iteration)
@@ -104,7 +105,8 @@ def uneven_batch(args, gdwd, synth):
     for sh in shapes:
         inst = synth.gaussian(seed=sh["seed"], d=sh["d"], n=sh["n"], shift=1.5, n_pos=sh["n_pos"], q=sh["q"],
                               C=sh["C"])
-        r, k = gdwd.make_request(inst.Z, inst.y, inst.q, inst.C, store="bf16", tol=1e-6, want_alpha=True)
+        r, k = gdwd.make_request(inst.Z, inst.y, inst.q, inst.C, store="bf16", tol=1e-6, want_alpha=True,
+                                 kernelized=args.kern)
         reqs.append(r)
         keeps.append(k)
         insts.append(inst)
@@ -120,7 +122,8 @@ def uneven_batch(args, gdwd, synth):
     return {"metric": "gDWD instances/s (uneven batch)", "value": len(reqs) / dt, "unit": "solves/s",
             "ms_per_step": dt * 1e3,
             "config": {"workload": f"uneven_batch {len(reqs)} instances d 5k-50k n 200-2000 q in 0.5,1,2,4",
-                       "store": "bf16", "slots": args.slots},
+                       "store": "bf16", "slots": args.slots,
+                       "iteration": "kernelized" if args.kern else "Z-streaming"},
             "status": int(st), "converged": int(sum(r["status"] == 0 for r in res)),
             "not_converged": [{"k": k, "d": shapes[k]["d"], "n": shapes[k]["n"], "q": shapes[k]["q"], "iters": r["iters"],
                                "kkt": r["kkt"], "status": r["status"]} for k, r in enumerate(res) if r["status"] != 0],
@@ -182,7 +185,7 @@ def served(args, gdwd, synth):
             gen_stream.synchronize()
             yh = y.double().cpu().numpy()
             o = gdwd.default_options()
-            o.tol, o.store = 1e-6, gdwd.F16
+            o.tol, o.store, o.kernelized = 1e-6, gdwd.F16, args.kern
             w = np.zeros(d)
             r = gdwd.Request(Z=Zrows.data_ptr(), zdt=gdwd.F32, z_on_device=1, d=d, n=n, ldz=d,
                              y=yh.ctypes.data, q=q, C=C, opts=o, w=w.ctypes.data, alpha=None)
@@ -204,7 +207,8 @@ def served(args, gdwd, synth):
             "offered_rate": lam, "mean_iters": float(np.mean(iters)),
             "z_bytes_per_iteration_mean_fp16": 2.0 * dn_done / max(1, len(stats)),
             "config": {"workload": f"served Poisson {lam}/s for {T} s, d 1k-100k, n 50-5000, q in 1,2, C 0.1-100",
-                       "store": "f16", "slots": args.slots, "client_in_flight_max": max_out}}
+                       "store": "f16", "slots": args.slots, "client_in_flight_max": max_out,
+                       "iteration": "kernelized" if args.kern else "Z-streaming"}}
 
 
 def largest_fp8(args, gdwd, synth):

@@ -278,7 +278,7 @@ def prox(a, sigma, q, r0=None, omega=None, out=None, stream=None):
 
 
 def make_request(Z, y, q, C, *, store="f32", tol=1e-6, sigma0=0.0, max_iter=20000, mu=1.0, tau=1.618,
-                 timeout_s=2.0, want_alpha=False):
+                 timeout_s=2.0, want_alpha=False, kernelized=0):
     """A gdwd_request for host data (numpy, column-major copy) with host outputs.
 
     Returns (request, keep) where keep holds the arrays that must outlive the
@@ -293,6 +293,7 @@ def make_request(Z, y, q, C, *, store="f32", tol=1e-6, sigma0=0.0, max_iter=2000
     o = default_options()
     o.mu, o.tau, o.tol, o.sigma0, o.max_iter, o.timeout_s = mu, tau, tol, sigma0, max_iter, timeout_s
     o.store = DTYPES[store] if isinstance(store, str) else int(store)
+    o.kernelized = int(kernelized)
     r = Request(Z=Zn.ctypes.data, zdt=F64 if Zn.dtype == np.float64 else F32, z_on_device=0, d=d, n=n, ldz=d,
                 y=yv.ctypes.data, q=float(q), C=float(C), opts=o, w=w.ctypes.data,
                 alpha=None if al is None else al.ctypes.data)

@@ -121,3 +121,24 @@ def test_kernelized_few_ctas(gdwd_lib):
         res, w, _ = s.solve()
     assert res[0]["status"] == 0, res[0]
     _compare(res[0], w[:, 0], O.solve(inst.Z, inst.y, 1.0, 1.0, tol=1e-10))
+
+
+def test_kernelized_batch_matches_oracle(gdwd_lib):
+    """Uneven kernelized requests through gdwd_solve_batch (three slots, each on its
+    own SM share) reach the oracle's solutions."""
+    shapes = synth.uneven_batch(19, count=5, d_range=(800, 6000), n_range=(40, 300))
+    reqs, keeps, insts = [], [], []
+    for sh in shapes:
+        inst = synth.gaussian(seed=sh["seed"], d=sh["d"], n=sh["n"], shift=1.5, n_pos=sh["n_pos"], q=sh["q"],
+                              C=sh["C"], dtype=np.float32)
+        r, k = gdwd_lib.make_request(inst.Z, inst.y, inst.q, inst.C, store="f32", tol=1e-7, kernelized=1)
+        reqs.append(r)
+        keeps.append(k)
+        insts.append(inst)
+    res, lat, st = gdwd_lib.solve_batch(reqs, slots=3)
+    assert st == 0, [r["status"] for r in res]
+    for r, k, inst in zip(res, keeps, insts):
+        assert r["status"] == 0 and r["kkt"] <= 1e-7, r
+        ref = O.solve(inst.Z.astype(np.float64), inst.y, inst.q, inst.C, tol=1e-9, max_iter=100000)
+        assert abs(r["primal_obj"] - ref["primal"]) / abs(ref["primal"]) <= OBJ_TOL
+        assert np.linalg.norm(k["w"] - ref["w"]) / np.linalg.norm(ref["w"]) <= W_TOL

@@ -505,21 +505,27 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
 #undef RS
 }
 
-// Phase-local region of the iteration kernel plus the resident row state ahead of it.
+// Phase-local region of the streaming passes (pass A's vector, pass B's
+// coefficients and row partials); the stand-alone product kernels need only this.
 template <typename T>
-static size_t union_bytes(const Layout& L, int grid) {
+static size_t pass_bytes(const Layout& L, int grid) {
   using CT = typename ElemTraits<T>::compute_t;
   constexpr int VEC = ElemTraits<T>::kVec;
   const int nmy = (L.NB + grid - 1) / grid;
   const int Q = L.TB / VEC;
   const int G = Q <= kThreads ? kThreads / Q : 1;
-  size_t a_bytes = (size_t)nmy * L.TB * sizeof(CT);
-  size_t b_bytes = (size_t)(L.n * sizeof(CT) + 15) / 16 * 32 + (size_t)2 * G * L.TB * sizeof(double) +
-                   (size_t)nmy * L.TB * sizeof(CT);
+  const size_t a_bytes = (size_t)nmy * L.TB * sizeof(CT);
+  const size_t b_bytes = (size_t)(L.n * sizeof(CT) + 15) / 16 * 32 + (size_t)2 * G * L.TB * sizeof(double) +
+                         (size_t)nmy * L.TB * sizeof(CT);
+  return ((a_bytes > b_bytes ? a_bytes : b_bytes) + 127) & ~(size_t)127;
+}
+
+// Phase-local region of the iteration kernel plus the resident row state ahead of it.
+template <typename T>
+static size_t union_bytes(const Layout& L, int grid) {
   size_t r_bytes = (size_t)9 * sizeof(double) * (size_t)((L.n + grid - 1) / grid);   // N2 row sums
   if (r_bytes < (size_t)6 * kThreads * sizeof(double)) r_bytes = (size_t)6 * kThreads * sizeof(double);   // B sums
-  size_t u = a_bytes;
-  if (b_bytes > u) u = b_bytes;
+  size_t u = pass_bytes<T>(L, grid);
   if (r_bytes > u) u = r_bytes;
   return ((u + 127) & ~(size_t)127) + row_state_bytes((L.n + grid - 1) / grid);
 }
@@ -583,10 +589,13 @@ int choose_chunk_cols(int store, const Layout& L, int grid, int smem_limit) {
   }
 }
 
-// Plans the ring (stage size, stage count) for the available shared memory.
+// Plans the ring (stage size, stage count) for the available shared memory next
+// to the iteration kernel's phase-local region (apply = false) or the product
+// kernels' smaller one (apply = true).
 template <typename T>
-static bool plan_ring(const Layout& L, int grid, int smem_limit, int& stages, int& stage_bytes, size_t& smem) {
-  const size_t ub = union_bytes<T>(L, grid);
+static bool plan_ring(const Layout& L, int grid, int smem_limit, int& stages, int& stage_bytes, size_t& smem,
+                      bool apply = false) {
+  const size_t ub = apply ? pass_bytes<T>(L, grid) : union_bytes<T>(L, grid);
   stage_bytes = (int)(((size_t)L.CW * L.TB * L.esize + 127) & ~(size_t)127);
   const int64_t avail = (int64_t)smem_limit - (int64_t)ub - 1024;
   if (avail < 2 * (int64_t)stage_bytes) return false;
@@ -708,7 +717,7 @@ static cudaError_t run_apply_t(const Layout& L, int trans, const double* x, cons
   using CT = typename ElemTraits<T>::compute_t;
   int stages, sb;
   size_t smem;
-  if (!plan_ring<T>(L, grid, smem_limit, stages, sb, smem)) return cudaErrorInvalidConfiguration;
+  if (!plan_ring<T>(L, grid, smem_limit, stages, sb, smem, true)) return cudaErrorInvalidConfiguration;
   if (trans) {
     auto k = applyA_kernel<T>;
     cudaError_t e = ensure_max_dyn_smem<applyA_kernel<T>>();

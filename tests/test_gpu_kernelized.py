@@ -142,3 +142,19 @@ def test_kernelized_batch_matches_oracle(gdwd_lib):
         ref = O.solve(inst.Z.astype(np.float64), inst.y, inst.q, inst.C, tol=1e-9, max_iter=100000)
         assert abs(r["primal_obj"] - ref["primal"]) / abs(ref["primal"]) <= OBJ_TOL
         assert np.linalg.norm(k["w"] - ref["w"]) / np.linalg.norm(ref["w"]) <= W_TOL
+
+
+def test_kernelized_few_slabs_many_rows(gdwd_lib):
+    """A server-sized SM share (38 CTAs) with fewer slabs than CTAs and n = 3000:
+    the final pass that forms w plans its ring for its own grid, one CTA per
+    slab."""
+    from tests import quantize_ref as QR
+    inst = synth.gaussian(seed=29, d=1200, n=3000, shift=1.5, n_pos=1200, q=1.0, C=1.0)
+    with gdwd_lib.Solver(inst.Z, inst.y, 1.0, 1.0, store="f16", tol=1e-6, kernelized=1, grid=38) as s:
+        info = s.info()
+        res, w, _ = s.solve()
+    assert info["grid"] == 38 and info["slabs"] < 38
+    assert res[0]["status"] == 0, res[0]
+    qv, sc = QR.quantize(inst.Z.astype(np.float64), "f16")
+    ref = O.solve(qv * sc[None, :], inst.y, 1.0, 1.0, tol=1e-9)
+    _compare(res[0], w[:, 0], ref)

@@ -228,6 +228,31 @@ class SMW2:
         return A
 
 
+class Direct:
+    """A^{-1} h for the same A by the direct solver of Sec. 3.3.1 (T = 0, d << n):
+    A is formed once ((d+1) x (d+1), 2 n d^2 flops) and factored by Cholesky; a
+    solve is two triangular solves."""
+
+    def __init__(self, Z, y, mu):
+        self.Z = np.asarray(Z, dtype=np.float64)
+        self.y = np.asarray(y, dtype=np.float64)
+        self.mu = float(mu)
+        d, n = self.Z.shape
+        self.d, self.n = d, n
+        A = np.zeros((d + 1, d + 1))
+        A[:d, :d] = self.Z @ self.Z.T + self.mu * np.eye(d)
+        zy = self.Z @ self.y
+        A[:d, d] = zy
+        A[d, :d] = zy
+        A[d, d] = self.y @ self.y
+        self.L = np.linalg.cholesky(A)
+
+    def solve(self, h):
+        from scipy.linalg import solve_triangular
+        z = solve_triangular(self.L, h, lower=True)
+        return solve_triangular(self.L.T, z, lower=False)
+
+
 # --------------------------------------------------------------------------
 # r-subproblem (Step 1b, eq-1c / eq-varphi, Sec. 3.2)
 # --------------------------------------------------------------------------
@@ -365,8 +390,10 @@ def suggest_C(Z, y, q):
 # --------------------------------------------------------------------------
 
 def solve(Z, y, q, C, mu=1.0, tau=1.618, tol=1e-9, max_iter=50000, sigma0=None,
-          e=None, wt=None, record=False, stop_rule=0):
-    """Inexact sGS-ADMM (Algorithm 1) on eq-gen-scale, exact SMW2 solves (R11).
+          e=None, wt=None, record=False, stop_rule=0, linsys="smw"):
+    """Inexact sGS-ADMM (Algorithm 1) on eq-gen-scale, exact solves of eq-linsys (R11):
+    by SMW2 (Sec. 3.3.2, linsys = "smw") or by the direct solver (Sec. 3.3.1,
+    linsys = "direct").
 
     Z is d x n with columns y_i x_i (Sec. 2, eq-r); y in {-1, +1}^n.
     Returns a dict with w (original scale, w~ / Z_scale, Sec. 4.2), beta, r, xi,
@@ -379,7 +406,7 @@ def solve(Z, y, q, C, mu=1.0, tau=1.618, tol=1e-9, max_iter=50000, sigma0=None,
     wt = np.ones(n) if wt is None else np.asarray(wt, dtype=np.float64)
     omega = q * wt ** q
     Zt, zs = scale_data(Z)
-    smw = SMW2(Zt, y, mu)
+    smw = SMW2(Zt, y, mu) if linsys == "smw" else Direct(Zt, y, mu)
     D = math.sqrt(mu)
 
     # R3: feasible start

@@ -42,6 +42,35 @@ def test_smw_matches_dense_solve(d, n, mu):
     assert np.linalg.norm(A @ got - h) <= 1e-12 * np.linalg.norm(h) * np.linalg.norm(A)
 
 
+def test_direct_solver_residual_and_toy():
+    """The direct solver of Sec. 3.3.1: its solve leaves a residual of eq-linsys at
+    rounding level (A assembled here from its blocks), and Algorithm 1 run on it
+    reaches the closed-form optimum of the two-point toy and the SMW2 run's
+    optimum on a d < n problem."""
+    rng = np.random.default_rng(5)
+    d, n, mu = 6, 40, 0.7
+    Z = rng.standard_normal((d, n))
+    y = np.where(np.arange(n) < 15, 1.0, -1.0)
+    h = rng.standard_normal(d + 1)
+    got = O.Direct(Z, y, mu).solve(h)
+    w, b = got[:d], got[d]
+    r_w = Z @ (Z.T @ w + y * b) + mu * w - h[:d]          # first block row of eq-linsys
+    r_b = y @ (Z.T @ w + y * b) - h[d]                    # last row
+    assert np.linalg.norm(np.append(r_w, r_b)) <= 1e-12 * np.linalg.norm(h) * (1 + np.linalg.norm(Z) ** 2)
+    # two-point toy (q = 1, separable regime): w* = m / ||m||, beta* = 0
+    m = rng.standard_normal(5)
+    m *= 1.5 / np.linalg.norm(m)
+    yy = np.array([1.0, -1.0])
+    res = O.solve(np.stack([m, -m], axis=1) * yy, yy, 1.0, 1.0, tol=1e-10, max_iter=200000, linsys="direct")
+    assert res["converged"] and np.linalg.norm(res["w"] - m / 1.5) <= 1e-6 and abs(res["beta"]) <= 1e-7
+    # d < n: both solvers reach the same optimum
+    X, yv, Zs = _two_class(rng, 4, 60, shift=1.0, n_pos=20)
+    a = O.solve(Zs, yv, 2.0, 3.0, tol=1e-10, linsys="direct")
+    s_ = O.solve(Zs, yv, 2.0, 3.0, tol=1e-10, linsys="smw")
+    assert abs(a["primal"] - s_["primal"]) <= 1e-8 * abs(s_["primal"])
+    assert np.linalg.norm(a["w"] - s_["w"]) <= 1e-6 * np.linalg.norm(s_["w"])
+
+
 # ---------------------------------------------------------------- closed-form toy
 
 @pytest.mark.parametrize("q", [0.5, 1.0, 2.0, 4.0])

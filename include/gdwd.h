@@ -105,7 +105,20 @@ typedef struct {
                          (8 n^2 bytes more).  Several C values are then solved one
                          after the other.  A solve starts only from the iterate of
                          a kernelized handle (the refinement sweep's master is one). */
-  int64_t reserved[5];
+  int32_t solver;     /* solver of eq-linsys.  0 (default): SMW2 through the n x n
+                         Gram matrix (Sec. 3.3.2), for n << d.  1: the direct solver
+                         of Sec. 3.3.1 for d << n: the (d+1) x (d+1) system through
+                         the d x d matrix I + Z~ Z~^T / mu (factored once, FP64
+                         diagonal tiles, double-float inverse) with its border
+                         eliminated in closed form; Z^T is stored with samples as
+                         rows, and each iteration is two streaming passes per solve
+                         of eq-linsys plus the per-sample Steps 1b, 2 and 3.  With
+                         solver = 1: F32 or F64 storage, refine = 0 and kernelized =
+                         0 (else EUNSUPPORTED); gdwd_apply,
+                         gdwd_get_stored and gdwd_suggest_C return EUNSUPPORTED and
+                         gdwd_gram returns the d x d matrix I + Z~ Z~^T / mu.      */
+  int32_t reserved_i32;
+  int64_t reserved[4];
 } gdwd_options;
 
 /* Outcome of one solve (one value of C). */
@@ -243,6 +256,8 @@ typedef struct {
   double t_factor_ms;    /*           Cholesky, inverse, p, s                */
   int32_t gram_tensor_cores; /* 1: the Gram ran on the tcgen05 tensor cores       */
   int32_t kernelized;        /* 1: solves use the kernelized n-space iteration      */
+  int32_t solver;            /* 0: SMW2 (n x n Gram), 1: direct (d x d, d << n)   */
+  int32_t reserved_;
 } gdwd_info;
 
 gdwd_status gdwd_get_info(const gdwd_handle* h, gdwd_info* info);

@@ -15,8 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgdwd.so")
-SOURCES = ["api.cu", "setup.cu", "iterate.cu", "iterate_kern.cu", "iterate_multi.cu", "server.cu", "noalloc.cu",
-           "gram_tc.cu"]
+SOURCES = ["api.cu", "setup.cu", "iterate.cu", "iterate_kern.cu", "iterate_multi.cu", "direct.cu", "server.cu",
+           "noalloc.cu", "gram_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -10,6 +10,7 @@
 #include <string>
 #include <vector>
 
+#include "direct.cuh"
 #include "iterate_kern.cuh"
 #include "solver.cuh"
 
@@ -64,6 +65,13 @@ struct gdwd_handle {
   // vectors of u, rho, g, the last K products, the GEMV right-hand sides
   float2 *Kd = nullptr, *vdf = nullptr;
   double *au = nullptr, *ar = nullptr, *ag = nullptr, *KG = nullptr, *KR = nullptr, *wcoef = nullptr;
+  // direct solver (opt.solver = 1): Z^T is the stored matrix (samples as rows);
+  // G, P, p, pdf are d x d / d-long; the state of Algorithm 1 in d-space
+  bool direct = false;
+  double *bhat = nullptr, *t = nullptr, *dv = nullptr, *dv2 = nullptr, *dw = nullptr, *dx = nullptr;
+  double *Zxr = nullptr, *Za = nullptr, *Zdr = nullptr, *dscal = nullptr;
+  float2* hw = nullptr;
+  int nblk = 0;
   double* dscalars = nullptr;   // [0] sumsq [1] zscale [2] s
   double *amax = nullptr, *colscale = nullptr;   // per-column |max| and storage scale s_i
   unsigned* bar = nullptr;
@@ -142,13 +150,15 @@ extern "C" gdwd_status gdwd_default_options(gdwd_options* o) {
 static int esize_of(int dt) { return dt == GDWD_F64 ? 8 : dt == GDWD_F32 ? 4 : dt == GDWD_E4M3 ? 1 : 2; }
 
 // Chooses slab height, slab count, chunk width and grid (see Layout).
-static void plan_layout(gdwd_handle* h) {
+// Slab layout of the stored matrix: `rows` rows (d; the samples n for the
+// direct solver, which stores Z^T) and `cols` columns.
+static void plan_layout(gdwd_handle* h, int64_t rows, int64_t cols) {
   const int es = esize_of(h->store);
   // slab heights are a multiple of the 16-byte vector and of 4 rows (the Gram
   // tile loader reads 4 consecutive rows of a column)
   const int vec = std::max(16 / es, 4);
   const int gp = h->opt.grid > 0 ? std::min(h->opt.grid, h->sms) : h->sms;
-  const int64_t d = h->d;
+  const int64_t d = rows;
   int TB;
   if (h->opt.block_rows > 0) {
     TB = (h->opt.block_rows + vec - 1) / vec * vec;
@@ -162,13 +172,178 @@ static void plan_layout(gdwd_handle* h) {
   TB = std::min(TB, 256 * vec);
   const int NB = (int)((d + TB - 1) / TB);
   h->L.d = d;
-  h->L.n = h->n;
+  h->L.n = cols;
   h->L.TB = TB;
   h->L.NB = NB;
   h->L.esize = es;
-  h->grid = (int)std::min<int64_t>(gp, std::max<int64_t>(NB, (h->n + kWarps - 1) / kWarps));
+  h->grid = (int)std::min<int64_t>(gp, std::max<int64_t>(NB, (cols + kWarps - 1) / kWarps));
   h->grid = std::max(h->grid, 1);
   h->L.CW = choose_chunk_cols(h->store, h->L, h->grid, h->smem_optin - 8192);
+}
+
+static cudaError_t dir_apply(int trans, const double* x, double* out, void* ctx);
+
+// Set-up of the direct solver (Sec. 3.3.1): Z^T into the slab layout, its Gram
+// G' = I + Z~ Z~^T / mu (d x d), b^ = Z~ y, and the factor of G' with p = G'^{-1} b^,
+// s = b^T p.  h has its device, options and problem sizes set.
+static gdwd_status create_direct(gdwd_handle* h, const void* Z, int zdt, int64_t ldz, int z_on_device,
+                                 const double* y) {
+  const int64_t d = h->d, n = h->n;
+  h->direct = true;
+  plan_layout(h, n, d);
+  if ((d + h->grid - 1) / h->grid > kMaxRowsPerCta)
+    return fail(h, GDWD_EUNSUPPORTED, "gdwd_create: d too large for the d x d factor of the direct solver");
+  h->nblk = dir_blocks(n);
+  cudaEvent_t e0, e1, evg, ef0;
+  CK(cudaEventCreate(&e0), "cudaEventCreate");
+  CK(cudaEventCreate(&e1), "cudaEventCreate");
+  CK(cudaEventCreate(&evg), "cudaEventCreate");
+  CK(cudaEventCreate(&ef0), "cudaEventCreate");
+  CK(cudaEventRecord(e0, h->stream), "cudaEventRecord");
+  const int64_t npad = (int64_t)h->L.NB * h->L.TB;
+  const int es = h->L.esize;
+  const int zes = esize_of(zdt);
+  void* zbuf = nullptr;
+  CK(cudaMallocAsync(&zbuf, (size_t)npad * d * es, h->stream), "cudaMalloc(Z)");
+  h->allocs.push_back(zbuf);
+  h->bytes += (size_t)npad * d * es;
+  h->Z = zbuf;
+  h->L.Z = zbuf;
+  h->ldP = (int)((d + 1) / 2 * 2);
+  CK(halloc(h, &h->sc, d), "alloc");
+  CK(halloc(h, &h->amax, d), "alloc");
+  CK(halloc(h, &h->colscale, d), "alloc");
+  CK(halloc(h, &h->y, n), "alloc");
+  CK(halloc(h, &h->e, n), "alloc");
+  CK(halloc(h, &h->omega, n), "alloc");
+  CK(halloc(h, &h->wt, n), "alloc");
+  CK(halloc(h, &h->p, d), "alloc");
+  CK(halloc(h, &h->G, (size_t)d * d), "alloc(G)");
+  CK(halloc(h, &h->P, (size_t)d * h->ldP), "alloc(P)");
+  CK(halloc(h, &h->pdf, h->ldP), "alloc");
+  CK(halloc(h, &h->bhat, d), "alloc");
+  CK(halloc(h, &h->r, n), "alloc");
+  CK(halloc(h, &h->xi, n), "alloc");
+  CK(halloc(h, &h->alpha, n), "alloc");
+  CK(halloc(h, &h->t, n), "alloc");
+  CK(halloc(h, &h->dv, n), "alloc");
+  CK(halloc(h, &h->dv2, n), "alloc");
+  CK(halloc(h, &h->u, d), "alloc");
+  CK(halloc(h, &h->rho, d), "alloc");
+  CK(halloc(h, &h->dw, d), "alloc");
+  CK(halloc(h, &h->g, d), "alloc");
+  CK(halloc(h, &h->dx, d + 1), "alloc");
+  CK(halloc(h, &h->hw, h->ldP), "alloc");
+  CK(halloc(h, &h->Zxr, d), "alloc");
+  CK(halloc(h, &h->Za, d), "alloc");
+  CK(halloc(h, &h->Zdr, d), "alloc");
+  CK(halloc(h, &h->wtmp, d), "alloc");
+  CK(halloc(h, &h->scal, (size_t)DS_SLOTS * h->nblk), "alloc");
+  CK(halloc(h, &h->dscal, h->nblk), "alloc");
+  CK(halloc(h, (uint8_t**)&h->partial, (size_t)d * h->L.NB * sizeof(double)), "alloc");
+  CK(halloc(h, &h->dscalars, 8), "alloc");
+  CK(halloc(h, &h->bar, 4), "alloc");
+  CK(halloc(h, &h->err, 4), "alloc");
+  CK(halloc(h, (uint8_t**)&h->ctrl, sizeof(Ctrl)), "alloc");
+  CK(cudaMemcpyAsync(h->y, y, n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "copy y");
+  const int fb = (int)std::min<int64_t>((n + 255) / 256, 1024);
+  fill_kernel<<<fb, 256, 0, h->stream>>>(h->e, n, 1.0);
+  fill_kernel<<<fb, 256, 0, h->stream>>>(h->wt, n, 1.0);
+  fill_kernel<<<fb, 256, 0, h->stream>>>(h->omega, n, h->q);
+  // ingest: the caller's Z (d x n, column-major) transposed to n x d, then the
+  // slab layout with samples as rows
+  const void* zsrc = Z;
+  void* staging = nullptr;
+  int64_t ld = ldz;
+  if (!z_on_device) {
+    CK(cudaMallocAsync(&staging, (size_t)d * n * zes, h->stream), "cudaMalloc(staging)");
+    cudaError_t ec = cudaMemcpy2DAsync(staging, (size_t)d * zes, Z, (size_t)ldz * zes, (size_t)d * zes, (size_t)n,
+                                       cudaMemcpyHostToDevice, h->stream);
+    if (ec != cudaSuccess) {
+      cudaFreeAsync(staging, h->stream);
+      return cuda_fail(h, ec, "copy Z");
+    }
+    zsrc = staging;
+    ld = d;
+  }
+  void* zt = nullptr;
+  cudaError_t ei = cudaMallocAsync(&zt, (size_t)d * n * zes, h->stream);
+  if (ei == cudaSuccess) ei = run_transpose(zsrc, zdt, d, n, ld, zt, h->stream);
+  const int nparts = 1024;
+  double* part = nullptr;
+  if (ei == cudaSuccess) ei = cudaMallocAsync(&part, nparts * sizeof(double), h->stream);
+  if (ei == cudaSuccess)
+    ei = run_ingest(zt, zdt, n, h->L, h->Z, h->store, part, nparts, h->dscalars, h->err, h->sc, h->dscalars + 1,
+                    h->amax, h->colscale, h->stream);
+  int nf = 0;
+  if (ei == cudaSuccess) ei = cudaMemcpyAsync(&nf, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  if (ei == cudaSuccess) ei = cudaStreamSynchronize(h->stream);
+  if (part) cudaFreeAsync(part, h->stream);
+  if (zt) cudaFreeAsync(zt, h->stream);
+  if (staging) cudaFreeAsync(staging, h->stream);
+  if (ei != cudaSuccess) return cuda_fail(h, ei, "ingest");
+  if (nf) return fail(h, GDWD_EINVAL, "gdwd_create: Z has non-finite entries");
+  CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream), "memset");
+  // G' = I + Z~ Z~^T / mu: the Gram of the stored Z^T
+  CK(cudaEventRecord(evg, h->stream), "cudaEventRecord");
+  const bool tc = h->opt.gram_path == 0 && gram_tc_supported(h->store, h->L);
+  const int ks = tc ? gram_tc_ksplit(h->L, h->sms) : gram_ksplit(h->L, h->sms);
+  double* Kpart = nullptr;
+  CK(cudaMallocAsync(&Kpart, (size_t)ks * d * d * sizeof(double), h->stream), "cudaMalloc(Kpart)");
+  cudaError_t eg = run_gram(h->store, h->L, ks, Kpart, h->sc, h->opt.mu, h->G, tc, h->err,
+                            (uint64_t)(h->opt.timeout_s * 1e9), h->stream);
+  if (eg == cudaSuccess) {
+    CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream), "memset");
+    eg = dir_apply(1, h->y, h->bhat, h);   // b^ = Z~ y
+  }
+  int gerr = 0;
+  if (eg == cudaSuccess) eg = cudaMemcpyAsync(&gerr, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  if (eg == cudaSuccess) eg = cudaStreamSynchronize(h->stream);
+  cudaFreeAsync(Kpart, h->stream);
+  if (eg != cudaSuccess) return cuda_fail(h, eg, "gram");
+  if (gerr) return fail(h, (gdwd_status)gerr, "gdwd_create: a set-up kernel timed out");
+  h->gram_tc = tc;
+  // factor of G', p = G'^{-1} b^, s = b^T p
+  CK(cudaEventRecord(ef0, h->stream), "cudaEventRecord");
+  float2 *A = nullptr, *X = nullptr;
+  CK(cudaMallocAsync(&A, (size_t)d * d * sizeof(float2), h->stream), "cudaMalloc(A)");
+  cudaError_t ef = cudaMallocAsync(&X, (size_t)d * d * sizeof(float2), h->stream);
+  if (ef == cudaSuccess) ef = cudaMemsetAsync(h->bar, 0, sizeof(unsigned), h->stream);
+  if (ef == cudaSuccess) {
+    FactorArgs fa{h->G, A, X, h->P, h->ldP, h->bhat, h->p, h->pdf, h->dscalars + 2, d, h->grid, h->bar, h->err,
+                  (uint64_t)(h->opt.timeout_s * 1e9)};
+    ef = run_factor(fa, h->stream);
+  }
+  int ferr = 0;
+  if (ef == cudaSuccess) ef = cudaMemcpyAsync(&ferr, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  double hs[3] = {0, 0, 0};
+  if (ef == cudaSuccess) ef = cudaMemcpyAsync(hs, h->dscalars, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (ef == cudaSuccess) ef = cudaEventRecord(e1, h->stream);
+  if (ef == cudaSuccess) ef = cudaStreamSynchronize(h->stream);
+  cudaFreeAsync(A, h->stream);
+  cudaFreeAsync(X, h->stream);
+  if (ef != cudaSuccess) return cuda_fail(h, ef, "factor");
+  if (ferr == GDWD_ENOTPD) return fail(h, GDWD_ENOTPD, "gdwd_create: Cholesky met a non-positive pivot");
+  if (ferr) return fail(h, (gdwd_status)ferr, "gdwd_create: factor kernel reported an error");
+  h->zscale = hs[1];
+  h->s = hs[2];
+  float ms = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventElapsedTime(&m1, e0, evg);
+  cudaEventElapsedTime(&m2, evg, ef0);
+  cudaEventElapsedTime(&m3, ef0, e1);
+  h->t_setup_ms = ms;
+  h->t_stage_ms[0] = m1;
+  h->t_stage_ms[1] = m2;
+  h->t_stage_ms[2] = m3;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaEventDestroy(evg);
+  cudaEventDestroy(ef0);
+  // the border's Schur complement n - s / mu is positive (A is positive definite)
+  if (!((double)n - h->s / h->opt.mu > 0.0) || !std::isfinite(h->s))
+    return fail(h, GDWD_ENUMERIC, "gdwd_create: the Schur complement of the direct solver is not positive");
+  return GDWD_OK;
 }
 
 extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_t n, int64_t ldz, int32_t z_on_device,
@@ -198,6 +373,10 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
   if (opt.stop_rule != 0 && opt.stop_rule != 1) return fail(nullptr, GDWD_EINVAL, "gdwd_create: stop_rule must be 0 or 1");
   if (opt.dots_every < 0) return fail(nullptr, GDWD_EINVAL, "gdwd_create: dots_every must be >= 0");
   if (opt.kernelized != 0 && opt.kernelized != 1) return fail(nullptr, GDWD_EINVAL, "gdwd_create: kernelized must be 0 or 1");
+  if (opt.solver != 0 && opt.solver != 1) return fail(nullptr, GDWD_EINVAL, "gdwd_create: solver must be 0 or 1");
+  if (opt.solver == 1 && (opt.refine || opt.kernelized || (opt.store != GDWD_F32 && opt.store != GDWD_F64)))
+    return fail(nullptr, GDWD_EUNSUPPORTED,
+                "gdwd_create: the direct solver runs with F32 or F64 storage, without refine and kernelized");
 
   gdwd_handle* h = new gdwd_handle();
   h->opt = opt;
@@ -235,7 +414,13 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
     if (!coop) return bail(fail(nullptr, GDWD_ECUDA, "device does not support cooperative launch"));
   }
-  plan_layout(h);
+  if (opt.solver == 1) {
+    st = create_direct(h, Z, zdt, ldz, z_on_device, y);
+    if (st != GDWD_OK) return bail(st);
+    *out = h;
+    return GDWD_OK;
+  }
+  plan_layout(h, d, n);
   if ((n + h->grid - 1) / h->grid > kMaxRowsPerCta)
     return bail(fail(nullptr, GDWD_EUNSUPPORTED, "gdwd_create: n too large for the n x n factor path of this build"));
   if (opt.kernelized && n > kern_max_n(h->grid, h->smem_optin - 16384))
@@ -507,6 +692,127 @@ static KernArgs make_kern_args(gdwd_handle* h, double C, int refresh) {
   a.err = h->err;
   a.ctrl = h->ctrl;
   return a;
+}
+
+// The streaming passes of the direct solver over the stored Z^T: trans = 0 gives
+// Z~^T x (per sample), trans = 1 gives Z~ x (per feature; partials per slab).
+static cudaError_t dir_apply(int trans, const double* x, double* out, void* ctx) {
+  gdwd_handle* h = static_cast<gdwd_handle*>(ctx);
+  return run_dir_product(h->L, h->store, trans, x, h->sc, out, reinterpret_cast<double*>(h->partial), h->stream);
+}
+
+// One solve of the direct solver from the initial iterate of reading R3.  The
+// host issues the iteration's kernels in batches of kDirBatch iterations and
+// reads the control block between batches; kernels issued after convergence
+// return at once (the streaming passes among them still run).
+static gdwd_status solve_direct(gdwd_handle* h, double C, double* w, int w_on_device, double* alpha,
+                                gdwd_result* res) {
+  constexpr int kDirBatch = 8;
+  const int64_t n = h->n, d = h->d;
+  cudaStream_t st = h->stream;
+  const double sigma0 = h->opt.sigma0 > 0 ? h->opt.sigma0 : std::pow(std::min(10.0 * C, (double)n), h->q);
+  const int fb = (int)std::min<int64_t>((n + 255) / 256, 1024);
+  fill_kernel<<<fb, 256, 0, st>>>(h->r, n, 1.0);
+  fill_kernel<<<fb, 256, 0, st>>>(h->xi, n, 1.0);
+  CK(cudaMemsetAsync(h->alpha, 0, n * sizeof(double), st), "memset");
+  CK(cudaMemsetAsync(h->u, 0, d * sizeof(double), st), "memset");
+  CK(cudaMemsetAsync(h->rho, 0, d * sizeof(double), st), "memset");
+  CK(cudaMemsetAsync(h->Zxr, 0, d * sizeof(double), st), "memset");
+  CK(cudaMemsetAsync(h->Za, 0, d * sizeof(double), st), "memset");
+  CK(cudaMemsetAsync(h->scal, 0, (size_t)DS_SLOTS * h->nblk * sizeof(double), st), "memset");
+  CK(cudaMemsetAsync(h->err, 0, sizeof(int), st), "memset");
+  Ctrl c0{};
+  c0.sigma = sigma0;
+  c0.sigma_prev = sigma0;
+  c0.theta = 1.0;
+  CK(cudaMemcpyAsync(h->ctrl, &c0, sizeof(Ctrl), cudaMemcpyHostToDevice, st), "copy ctrl");
+  DirArgs a{};
+  a.d = d;
+  a.n = n;
+  a.P = h->P;
+  a.ldP = h->ldP;
+  a.pdf = h->pdf;
+  a.p = h->p;
+  a.s = h->s;
+  a.y = h->y;
+  a.e = h->e;
+  a.omega = h->omega;
+  a.wt = h->wt;
+  a.q = h->q;
+  a.C = C;
+  a.mu = h->opt.mu;
+  a.tau = h->opt.tau;
+  a.R = h->zscale;
+  a.tol = h->opt.tol;
+  a.kappa = (h->q + 1.0) / h->q * std::pow(h->q, 1.0 / (h->q + 1.0));
+  a.max_iter = h->opt.max_iter;
+  a.stop_rule = h->opt.stop_rule;
+  a.r = h->r;
+  a.xi = h->xi;
+  a.alpha = h->alpha;
+  a.t = h->t;
+  a.dv = h->dv;
+  a.dv2 = h->dv2;
+  a.u = h->u;
+  a.rho = h->rho;
+  a.w = h->dw;
+  a.g = h->g;
+  a.x = h->dx;
+  a.hw = h->hw;
+  a.Zxr = h->Zxr;
+  a.Za = h->Za;
+  a.Zdr = h->Zdr;
+  a.scal = h->scal;
+  a.dscal = h->dscal;
+  a.nblk = h->nblk;
+  a.ctrl = h->ctrl;
+  const DirPasses ps{dir_apply, h};
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0), "event");
+  CK(cudaEventCreate(&e1), "event");
+  CK(cudaEventRecord(e0, st), "event");
+  Ctrl c{};
+  int kerr = 0;
+  for (int it = 0; it < h->opt.max_iter; it += kDirBatch) {
+    for (int b = 0; b < kDirBatch; ++b) {
+      const cudaError_t e = run_dir_iteration(a, ps, st);
+      if (e != cudaSuccess) return cuda_fail(h, e, "direct solver iteration");
+    }
+    CK(cudaMemcpyAsync(&c, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st), "copy ctrl");
+    CK(cudaMemcpyAsync(&kerr, h->err, sizeof(int), cudaMemcpyDeviceToHost, st), "copy err");
+    CK(cudaStreamSynchronize(st), "sync");
+    if (c.done || kerr) break;
+  }
+  CK(cudaEventRecord(e1, st), "event");
+  double* wdst = (w && w_on_device) ? w : h->wtmp;
+  CK(run_dir_finish(h->dw, h->zscale, d, wdst, st), "finish");
+  if (w && !w_on_device) CK(cudaMemcpyAsync(w, h->wtmp, d * sizeof(double), cudaMemcpyDeviceToHost, st), "copy w");
+  if (alpha) CK(cudaMemcpyAsync(alpha, h->alpha, n * sizeof(double), cudaMemcpyDeviceToHost, st), "copy alpha");
+  CK(cudaMemcpyAsync(&c, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st), "copy ctrl");
+  CK(cudaStreamSynchronize(st), "sync");
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::memset(h->phase_ns, 0, sizeof(h->phase_ns));
+  std::memset(res, 0, sizeof(*res));
+  res->beta = c.beta;
+  res->primal_obj = c.pobj;
+  res->dual_obj = c.dobj;
+  res->kkt = c.kkt;
+  res->eta_p = std::max(c.eta_p1, std::max(c.eta_p2, c.eta_p3));
+  res->eta_d = std::max(c.eta_d1, std::max(c.eta_d2, c.eta_d3));
+  res->eta_c = std::max(c.eta_c1, std::max(c.eta_c2, c.eta_c3));
+  res->eta_gap = c.eta_gap;
+  res->sigma = c.sigma;
+  res->zscale = h->zscale;
+  res->t_setup_ms = h->t_setup_ms;
+  res->t_solve_ms = ms;
+  res->iters = c.it;
+  gdwd_status s = kerr ? (gdwd_status)kerr : (c.done ? (gdwd_status)c.status : GDWD_EMAXITER);
+  res->status = s;
+  if (kerr) return fail(h, s, "gdwd_solve: a device wait of the direct solver expired");
+  return s;
 }
 
 // One solve for penalty C.  warm == NULL starts from the initial iterate of
@@ -822,7 +1128,7 @@ extern "C" gdwd_status gdwd_solve(gdwd_handle* h, const double* Cs, int32_t nC, 
   }
   gdwd_status worst = GDWD_OK;
   // joint C-grid: groups of up to four C values per launch (one Z read per pass for all)
-  const int kmax = (count >= 2 && !h->master && !h->opt.cgrid_sequential && !h->opt.kernelized)
+  const int kmax = (count >= 2 && !h->master && !h->opt.cgrid_sequential && !h->opt.kernelized && !h->direct)
                        ? multi_max_k(h->store, h->L, h->grid, h->smem_optin - 16384)
                        : 1;
   int k0 = 0;
@@ -851,6 +1157,9 @@ extern "C" gdwd_status gdwd_solve(gdwd_handle* h, const double* Cs, int32_t nC, 
       res[k].t_setup_ms = h->t_setup_ms + h->master->t_setup_ms;
       res[k].reserved[0] = rq.iters;   // iterations on the quantized data
       if (s != GDWD_OK && s != GDWD_EMAXITER) return fail(h, s, h->master->last_error);
+    } else if (h->direct) {
+      s = solve_direct(h, C, w ? w + (size_t)k * h->d : nullptr, w_on_device,
+                       alpha ? alpha + (size_t)k * h->n : nullptr, res + k);
     } else {
       s = solve_one(h, C, w ? w + (size_t)k * h->d : nullptr, w_on_device,
                     alpha ? alpha + (size_t)k * h->n : nullptr, res + k);
@@ -887,6 +1196,7 @@ extern "C" gdwd_status gdwd_prox(const double* a, const double* r0, const double
 
 extern "C" gdwd_status gdwd_apply(gdwd_handle* h, int32_t trans, const double* x, double* out) {
   if (!h || !x || !out) return fail(h, GDWD_EINVAL, "gdwd_apply: NULL argument");
+  if (h->direct) return fail(h, GDWD_EUNSUPPORTED, "gdwd_apply: not on a handle of the direct solver");
   CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream), "memset");
   const int grid = h->L.NB;   // one CTA per slab
   CK(run_apply(h->store, h->L, trans, x, h->sc, out, h->partial, std::min(grid, 4096), h->smem_optin - 8192, h->err,
@@ -901,7 +1211,8 @@ extern "C" gdwd_status gdwd_apply(gdwd_handle* h, int32_t trans, const double* x
 
 extern "C" gdwd_status gdwd_gram(gdwd_handle* h, double* G_out) {
   if (!h || !G_out) return fail(h, GDWD_EINVAL, "gdwd_gram: NULL argument");
-  CK(cudaMemcpyAsync(G_out, h->G, (size_t)h->n * h->n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy G");
+  const size_t m = (size_t)(h->direct ? h->d : h->n);   // d x d for the direct solver
+  CK(cudaMemcpyAsync(G_out, h->G, m * m * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy G");
   CK(cudaStreamSynchronize(h->stream), "sync");
   return GDWD_OK;
 }
@@ -971,6 +1282,7 @@ __global__ void pair_dist_kernel(const double* G, int64_t n, const int* pos, int
 
 extern "C" gdwd_status gdwd_suggest_C(gdwd_handle* h, double* C_out) {
   if (!h || !C_out) return fail(h, GDWD_EINVAL, "gdwd_suggest_C: NULL argument");
+  if (h->direct) return fail(h, GDWD_EUNSUPPORTED, "gdwd_suggest_C: needs the n x n Gram (not on a direct-solver handle)");
   const int64_t n = h->n;
   std::vector<double> y(n);
   CK(cudaMemcpyAsync(y.data(), h->y, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy y");
@@ -1023,7 +1335,7 @@ extern "C" gdwd_status gdwd_get_info(const gdwd_handle* h, gdwd_info* info) {
   info->block_rows = h->L.TB;
   info->slabs = h->L.NB;
   info->grid = h->grid;
-  info->z_bytes = (int64_t)h->L.NB * h->L.TB * h->n * h->L.esize;
+  info->z_bytes = (int64_t)h->L.NB * h->L.TB * h->L.n * h->L.esize;
   info->device_bytes = (int64_t)h->bytes;
   info->zscale = h->zscale;
   info->t_setup_ms = h->t_setup_ms;
@@ -1032,6 +1344,7 @@ extern "C" gdwd_status gdwd_get_info(const gdwd_handle* h, gdwd_info* info) {
   info->t_factor_ms = h->t_stage_ms[2];
   info->gram_tensor_cores = h->gram_tc ? 1 : 0;
   info->kernelized = h->opt.kernelized;
+  info->solver = h->direct ? 1 : 0;
   return GDWD_OK;
 }
 
@@ -1043,6 +1356,7 @@ extern "C" gdwd_status gdwd_get_phase_times(const gdwd_handle* h, double* ns, in
 
 extern "C" gdwd_status gdwd_get_stored(const gdwd_handle* h, void* Zq, double* colscale) {
   if (!h || (!Zq && !colscale)) return fail(nullptr, GDWD_EINVAL, "gdwd_get_stored: bad argument");
+  if (h->direct) return fail(nullptr, GDWD_EUNSUPPORTED, "gdwd_get_stored: not on a direct-solver handle");
   gdwd_handle* hh = const_cast<gdwd_handle*>(h);
   const int es = h->L.esize;
   const int64_t d = h->d, n = h->n, TB = h->L.TB;

@@ -27,7 +27,8 @@ class Options(ctypes.Structure):
                 ("timeout_s", c_double), ("max_iter", c_int32), ("store", c_int32), ("grid", c_int32),
                 ("block_rows", c_int32), ("stream", c_void_p), ("refine", c_int32),
                 ("cgrid_sequential", c_int32), ("gram_path", c_int32), ("stop_rule", c_int32),
-                ("dots_every", c_int32), ("kernelized", c_int32), ("reserved", c_int64 * 5)]
+                ("dots_every", c_int32), ("kernelized", c_int32), ("solver", c_int32),
+                ("reserved_i32", c_int32), ("reserved", c_int64 * 4)]
 
 
 class Result(ctypes.Structure):
@@ -44,7 +45,8 @@ class Info(ctypes.Structure):
     _fields_ = [("d", c_int64), ("n", c_int64), ("store", c_int32), ("block_rows", c_int32), ("slabs", c_int32),
                 ("grid", c_int32), ("z_bytes", c_int64), ("device_bytes", c_int64), ("zscale", c_double),
                 ("t_setup_ms", c_double), ("t_ingest_ms", c_double), ("t_gram_ms", c_double),
-                ("t_factor_ms", c_double), ("gram_tensor_cores", c_int32), ("kernelized", c_int32)]
+                ("t_factor_ms", c_double), ("gram_tensor_cores", c_int32), ("kernelized", c_int32),
+                ("solver", c_int32), ("reserved_", c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -138,7 +140,7 @@ class Solver:
 
     def __init__(self, Z, y, q, C, *, store="f32", mu=1.0, tau=1.618, tol=1e-6, sigma0=0.0, max_iter=20000,
                  timeout_s=2.0, grid=0, block_rows=0, stream=None, refine=0, cgrid_sequential=0, gram_path=0,
-                 stop_rule=0, dots_every=0, kernelized=0):
+                 stop_rule=0, dots_every=0, kernelized=0, solver="smw"):
         lib = load()
         self._h = c_void_p()
         o = default_options()
@@ -147,6 +149,8 @@ class Solver:
         o.stop_rule = int(stop_rule)
         o.dots_every = int(dots_every)
         o.kernelized = int(kernelized)
+        o.solver = {"smw": 0, "direct": 1}[solver] if isinstance(solver, str) else int(solver)
+        self._direct = o.solver == 1
         o.cgrid_sequential = int(cgrid_sequential)
         o.mu, o.tau, o.tol, o.sigma0 = mu, tau, tol, sigma0
         o.max_iter, o.timeout_s = max_iter, timeout_s
@@ -207,7 +211,9 @@ class Solver:
         return out
 
     def gram(self):
-        G = np.zeros((self.n, self.n), dtype=np.float64)
+        """G = I + Z~^T Z~ / mu (n x n); with solver="direct" the d x d I + Z~ Z~^T / mu."""
+        m = self.d if self._direct else self.n
+        G = np.zeros((m, m), dtype=np.float64)
         _check(_lib.gdwd_gram(self._h, c_void_p(G.ctypes.data)), self._h)
         return G
 

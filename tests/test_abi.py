@@ -35,7 +35,7 @@ def test_struct_sizes_match_header():
     # sizes implied by the header's field lists (LP64)
     assert ctypes.sizeof(gdwd.Options) == 5 * 8 + 4 * 4 + 8 + 8 * 8
     assert ctypes.sizeof(gdwd.Result) == 12 * 8 + 2 * 4 + 4 * 8
-    assert ctypes.sizeof(gdwd.Info) == 2 * 8 + 4 * 4 + 2 * 8 + 2 * 8 + 4 * 8
+    assert ctypes.sizeof(gdwd.Info) == 2 * 8 + 4 * 4 + 2 * 8 + 2 * 8 + 3 * 8 + 4 * 4
 
 
 def test_default_options(lib):

@@ -208,7 +208,7 @@ def main():
     ap.add_argument("--n", type=int, default=1000, help="sample count (profiling of other sizes only)")
     ap.add_argument("--workload", default="spiked_fp32",
                     help="spiked_fp32 (default line) | plain_fp64 | cgrid_bf16 | uneven_batch | served | largest_fp8 | "
-                         "kernelized")
+                         "kernelized | direct_fp32")
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
@@ -221,6 +221,8 @@ def main():
     ap.add_argument("--kern-wide-d", type=int, default=200000)
     ap.add_argument("--kern-steps", type=int, default=3)
     ap.add_argument("--kern", type=int, default=0, help="uneven_batch / served: 1 = kernelized iteration")
+    ap.add_argument("--dir-d", type=int, default=200)
+    ap.add_argument("--dir-n", type=int, default=1000000)
     args = ap.parse_args()
     if args.workload != "spiked_fp32" and args.impl != "reference":
         import bench_workloads

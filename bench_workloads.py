@@ -13,6 +13,8 @@ stand-ins for the paper's data sets (see paper_2305_12019_gb300/synth.py).
                 d log-uniform 1k-100k, n 50-5000, q in {1,2}, C 0.1-100, generated
                 on the device per request seed: p50 / p99 latency and solves/s
                 (uneven_batch and served: --kern 1 runs the kernelized iteration)
+  direct_fp32   d=200, n=1e6 FP32 through the direct solver of eq-linsys (d << n):
+                solves/s, iterations, streaming-pass bandwidth
   largest_fp8   d=200000, n=5000, Student-t columns, 1:3, 16 values of C, E4M3
                 storage with the FP32 refinement sweep: C-solves/s
   kernelized    the kernelized n-space iteration (no pass over Z per iteration)
@@ -298,8 +300,37 @@ def kernelized(args, gdwd, synth):
     return line
 
 
+def direct_fp32(args, gdwd, synth):
+    """d << n through the direct solver of eq-linsys: the n x n Gram of the SMW
+    path would not fit (n = 1e6 -> 8 TB), the d x d one is 320 KB."""
+    torch = _torch()
+    d, n = args.dir_d, args.dir_n
+    inst = synth.gaussian(seed=7001, d=d, n=n, shift=0.3, n_pos=n // 2, q=1.0, C=1.0)
+    Zd = _device_colmajor(inst.Z)
+    times, out = [], None
+    for k in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with gdwd.Solver(Zd, inst.y, 1.0, 1.0, store="f32", tol=1e-6, solver="direct") as s:
+            res, w, alpha = s.solve(alpha=True)
+            info = s.info()
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+        out = (res[0], w[:, 0], alpha[:, 0], info)
+    r, w, al, info = out
+    gap = O.certified_gap(inst.Z.astype(np.float64), inst.y, w, r["beta"], al, 1.0, 1.0)[2]
+    zbytes = 4.0 * d * n
+    return {"metric": "gDWD solves/s at KKT<=1e-6, direct solver (d << n)", "value": 1.0 / times[-1],
+            "unit": "solves/s", "ms_per_step": times[-1] * 1e3,
+            "config": {"workload": f"direct_fp32 d={d} n={n} q=1 C=1 tol=1e-6", "store": "f32", "solver": "direct"},
+            "iters": r["iters"], "kkt": r["kkt"], "status": r["status"], "setup_ms": info["t_setup_ms"],
+            "solve_ms": r["t_solve_ms"], "us_per_iter": 1e3 * r["t_solve_ms"] / max(1, r["iters"]),
+            "z_passes_per_iter": 5, "z_gbs": 5 * zbytes * r["iters"] / (r["t_solve_ms"] * 1e-3) / 1e9,
+            "certified_gap": gap}
+
+
 WORKLOADS = {"plain_fp64": plain_fp64, "cgrid_bf16": cgrid_bf16, "uneven_batch": uneven_batch, "served": served,
-             "largest_fp8": largest_fp8, "kernelized": kernelized}
+             "largest_fp8": largest_fp8, "kernelized": kernelized, "direct_fp32": direct_fp32}
 
 
 def run(name, args):

@@ -97,12 +97,26 @@ __global__ void dir_rowdot_f32(Layout L, const float2* __restrict__ xs, double* 
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t s = i / L.TB, r = i - s * L.TB;
     const float* base = reinterpret_cast<const float*>(L.Z) + (size_t)s * L.TB * d + r;
-    df acc{0.f, 0.f};
-    for (int64_t j = 0; j < d; ++j) {
-      const float2 xv = __ldg(xs + j);
-      acc_prod<float>(acc, base[(size_t)j * L.TB], df{xv.x, xv.y});
+    // four independent accumulators: four loads of the row in flight
+    df a0{0.f, 0.f}, a1{0.f, 0.f}, a2{0.f, 0.f}, a3{0.f, 0.f};
+    int64_t j = 0;
+    for (; j + 3 < d; j += 4) {
+      const float z0 = base[(size_t)j * L.TB], z1 = base[(size_t)(j + 1) * L.TB];
+      const float z2 = base[(size_t)(j + 2) * L.TB], z3 = base[(size_t)(j + 3) * L.TB];
+      const float2 x0 = __ldg(xs + j), x1 = __ldg(xs + j + 1), x2 = __ldg(xs + j + 2), x3 = __ldg(xs + j + 3);
+      acc_prod<float>(a0, z0, df{x0.x, x0.y});
+      acc_prod<float>(a1, z1, df{x1.x, x1.y});
+      acc_prod<float>(a2, z2, df{x2.x, x2.y});
+      acc_prod<float>(a3, z3, df{x3.x, x3.y});
     }
-    out[i] = df_to_double(acc);
+    for (; j < d; ++j) {
+      const float2 xv = __ldg(xs + j);
+      acc_prod<float>(a0, base[(size_t)j * L.TB], df{xv.x, xv.y});
+    }
+    df_add(a0, a1);
+    df_add(a2, a3);
+    df_add(a0, a2);
+    out[i] = df_to_double(a0);
   }
 }
 
@@ -132,10 +146,18 @@ __global__ void dir_coldot_f32(Layout L, const double* __restrict__ v, double* p
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const float* base = reinterpret_cast<const float*>(L.Z) + (size_t)s * L.TB * d;
   for (int64_t j = warp; j < d; j += nw) {
-    df acc{0.f, 0.f};
-    for (int r = lane; r < L.TB; r += 32) acc_prod<float>(acc, base[(size_t)j * L.TB + r], df{vs_d[r].x, vs_d[r].y});
-    acc = df_warp_sum(acc);
-    if (lane == 0) part[(size_t)j * L.NB + s] = df_to_double(acc);
+    const float* col = base + (size_t)j * L.TB;
+    df a0{0.f, 0.f}, a1{0.f, 0.f};
+    int r = lane;
+    for (; r + 32 < L.TB; r += 64) {
+      const float z0 = col[r], z1 = col[r + 32];
+      acc_prod<float>(a0, z0, df{vs_d[r].x, vs_d[r].y});
+      acc_prod<float>(a1, z1, df{vs_d[r + 32].x, vs_d[r + 32].y});
+    }
+    if (r < L.TB) acc_prod<float>(a0, col[r], df{vs_d[r].x, vs_d[r].y});
+    df_add(a0, a1);
+    a0 = df_warp_sum(a0);
+    if (lane == 0) part[(size_t)j * L.NB + s] = df_to_double(a0);
   }
 }
 

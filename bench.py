@@ -28,6 +28,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -97,7 +98,7 @@ class Clocks:
 
     def __init__(self, gpu_index=0):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"gdwd_clocks_{os.getpid()}.csv")
         self.gpu = gpu_index
 
     def __enter__(self):

@@ -18,7 +18,7 @@ It is written to be read against the paper (arXiv 2305.12019), not to be fast:
   inside a bracket and bisected when a step leaves it (the paper's fallback);
 * the KKT residuals and duality gap of Sec. 4.3 and the sigma rule of Sec. 4.4.
 
-Readings where the paper is silent or garbled (each also listed in the design doc):
+Readings where the paper is silent or garbled (the CUDA path takes the same ones):
 
 R1  D is "a positive multiple of I"; D^2 = mu*I with mu = 1 by default.  The SMW
     matrix called D-hat in eq-Anew holds D^2 (the identity only holds that way).

@@ -7,7 +7,7 @@ synthetic problems at sizes that span several slabs, tiles and a ragged tail,
 then the full spiked FP32 workload (d = 20000, n = 1000) against the oracle and
 the weak-duality certificate.
 
-Tolerances (the spec acceptance): |d obj|/|obj| <= 1e-6,
+Tolerances (the acceptance bar): |d obj|/|obj| <= 1e-6,
 ||dw||/||w|| <= 1e-4, identical held-out predictions except near-ties
 (|w^T x + beta| < 1e-6 ||x||), kkt <= tol.
 """

@@ -39,6 +39,22 @@ def _torch():
     return torch
 
 
+def _hbm_peak():
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _roofline(kernel, bytes_per_iter, iters, solve_ms, formula):
+    peak, kind = _hbm_peak()
+    achieved = bytes_per_iter * iters / (solve_ms * 1e-3) / 1e9
+    return {"kernel": kernel, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": kind, "bytes_per_iteration": bytes_per_iter,
+            "bytes_formula": formula}
+
+
 def _device_colmajor(Z):
     torch = _torch()
     d, n = Z.shape
@@ -293,6 +309,10 @@ def kernelized(args, gdwd, synth):
         "C_solves_per_s": 32 / t_grid, "ms": t_grid * 1e3, "iters": [r["iters"] for r in res],
         "converged": int(sum(r["status"] == 0 for r in res)), "certified_gap_original_data_every_8th_C": gaps}
     head = cases["spiked_fp32_d20000_n1000"]["kernelized"]
+    n0 = 1000
+    kb = 24.0 * n0 * (n0 + 1) + 200.0 * n0      # G^-1 twice and K once (double-float rows), n-vectors
+    line["roofline"] = _roofline("iterate_kern_kernel", kb, head["iters"], head["solve_ms"],
+                                 "24 n (n+1) + 200 n bytes per iteration (two G^-1 GEMVs, one K GEMV)")
     line.update({"value": head["solves_per_s"], "ms_per_step": head["step_ms"],
                  "config": {"workload": "kernelized iteration: spiked_fp32 d=20000 n=1000 q=1 C=10 tol=1e-6 "
                                         "(value); wide d=200000 and the BF16 C grid alongside", "store": "f32"},
@@ -326,6 +346,9 @@ def direct_fp32(args, gdwd, synth):
             "iters": r["iters"], "kkt": r["kkt"], "status": r["status"], "setup_ms": info["t_setup_ms"],
             "solve_ms": r["t_solve_ms"], "us_per_iter": 1e3 * r["t_solve_ms"] / max(1, r["iters"]),
             "z_passes_per_iter": 5, "z_gbs": 5 * zbytes * r["iters"] / (r["t_solve_ms"] * 1e-3) / 1e9,
+            "roofline": _roofline("direct iteration (five streaming products)", 5 * zbytes + 24.0 * d * d + 64.0 * n,
+                                  r["iters"], r["t_solve_ms"],
+                                  "5 d n 4 (five products with Z^T) + 24 d^2 + 64 n bytes per iteration"),
             "certified_gap": gap}
 
 

@@ -92,31 +92,46 @@ __global__ void dir_scale_kernel(const double* x, const double* sc, int64_t d, i
   }
 }
 
+// FP32: one thread per quad of consecutive samples of a slab (the slab height is
+// a multiple of 4, so each column's quad is one 16-byte load and a warp reads
+// 512 contiguous bytes per column)
 __global__ void dir_rowdot_f32(Layout L, const float2* __restrict__ xs, double* out) {
   const int64_t n = L.d, d = L.n;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t s = i / L.TB, r = i - s * L.TB;
-    const float* base = reinterpret_cast<const float*>(L.Z) + (size_t)s * L.TB * d + r;
-    // four independent accumulators: four loads of the row in flight
+  const int64_t qps = L.TB / 4;                       // quads per slab
+  const int64_t nq = (int64_t)L.NB * qps;
+  for (int64_t qd = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; qd < nq; qd += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = qd / qps, r = (qd - s * qps) * 4;
+    const float4* col = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(L.Z) + (size_t)s * L.TB * d + r);
+    const int64_t cs = L.TB / 4;                       // float4 stride between columns
     df a0{0.f, 0.f}, a1{0.f, 0.f}, a2{0.f, 0.f}, a3{0.f, 0.f};
     int64_t j = 0;
-    for (; j + 3 < d; j += 4) {
-      const float z0 = base[(size_t)j * L.TB], z1 = base[(size_t)(j + 1) * L.TB];
-      const float z2 = base[(size_t)(j + 2) * L.TB], z3 = base[(size_t)(j + 3) * L.TB];
-      const float2 x0 = __ldg(xs + j), x1 = __ldg(xs + j + 1), x2 = __ldg(xs + j + 2), x3 = __ldg(xs + j + 3);
-      acc_prod<float>(a0, z0, df{x0.x, x0.y});
-      acc_prod<float>(a1, z1, df{x1.x, x1.y});
-      acc_prod<float>(a2, z2, df{x2.x, x2.y});
-      acc_prod<float>(a3, z3, df{x3.x, x3.y});
+    for (; j + 1 < d; j += 2) {
+      const float4 z = col[(size_t)j * cs], z2 = col[(size_t)(j + 1) * cs];
+      const float2 xv = __ldg(xs + j), xw = __ldg(xs + j + 1);
+      const df x{xv.x, xv.y}, w{xw.x, xw.y};
+      acc_prod<float>(a0, z.x, x);
+      acc_prod<float>(a1, z.y, x);
+      acc_prod<float>(a2, z.z, x);
+      acc_prod<float>(a3, z.w, x);
+      acc_prod<float>(a0, z2.x, w);
+      acc_prod<float>(a1, z2.y, w);
+      acc_prod<float>(a2, z2.z, w);
+      acc_prod<float>(a3, z2.w, w);
     }
-    for (; j < d; ++j) {
+    if (j < d) {
+      const float4 z = col[(size_t)j * cs];
       const float2 xv = __ldg(xs + j);
-      acc_prod<float>(a0, base[(size_t)j * L.TB], df{xv.x, xv.y});
+      const df x{xv.x, xv.y};
+      acc_prod<float>(a0, z.x, x);
+      acc_prod<float>(a1, z.y, x);
+      acc_prod<float>(a2, z.z, x);
+      acc_prod<float>(a3, z.w, x);
     }
-    df_add(a0, a1);
-    df_add(a2, a3);
-    df_add(a0, a2);
-    out[i] = df_to_double(a0);
+    const int64_t i0 = s * L.TB + r;
+    if (i0 < n) out[i0] = df_to_double(a0);
+    if (i0 + 1 < n) out[i0 + 1] = df_to_double(a1);
+    if (i0 + 2 < n) out[i0 + 2] = df_to_double(a2);
+    if (i0 + 3 < n) out[i0 + 3] = df_to_double(a3);
   }
 }
 
@@ -133,6 +148,8 @@ __global__ void dir_rowdot_f64(Layout L, const double* __restrict__ xs, double* 
 
 // part[j * NB + s] = sum over the samples of slab s of Zq_ij v_i: one CTA per
 // slab, one warp per column (lanes over the slab's rows, coalesced)
+// FP32: lanes over 16-byte quads of the column (512 contiguous bytes per warp
+// per load, two loads in flight)
 __global__ void dir_coldot_f32(Layout L, const double* __restrict__ v, double* part) {
   extern __shared__ float2 vs_d[];
   const int64_t s = blockIdx.x;
@@ -144,17 +161,32 @@ __global__ void dir_coldot_f32(Layout L, const double* __restrict__ v, double* p
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int quads = L.TB / 4;
   const float* base = reinterpret_cast<const float*>(L.Z) + (size_t)s * L.TB * d;
   for (int64_t j = warp; j < d; j += nw) {
-    const float* col = base + (size_t)j * L.TB;
+    const float4* col = reinterpret_cast<const float4*>(base + (size_t)j * L.TB);
     df a0{0.f, 0.f}, a1{0.f, 0.f};
-    int r = lane;
-    for (; r + 32 < L.TB; r += 64) {
-      const float z0 = col[r], z1 = col[r + 32];
-      acc_prod<float>(a0, z0, df{vs_d[r].x, vs_d[r].y});
-      acc_prod<float>(a1, z1, df{vs_d[r + 32].x, vs_d[r + 32].y});
+    int q = lane;
+    for (; q + 32 < quads; q += 64) {
+      const float4 z = col[q], z2 = col[q + 32];
+      const int r = 4 * q, r2 = 4 * (q + 32);
+      acc_prod<float>(a0, z.x, df{vs_d[r].x, vs_d[r].y});
+      acc_prod<float>(a0, z.y, df{vs_d[r + 1].x, vs_d[r + 1].y});
+      acc_prod<float>(a0, z.z, df{vs_d[r + 2].x, vs_d[r + 2].y});
+      acc_prod<float>(a0, z.w, df{vs_d[r + 3].x, vs_d[r + 3].y});
+      acc_prod<float>(a1, z2.x, df{vs_d[r2].x, vs_d[r2].y});
+      acc_prod<float>(a1, z2.y, df{vs_d[r2 + 1].x, vs_d[r2 + 1].y});
+      acc_prod<float>(a1, z2.z, df{vs_d[r2 + 2].x, vs_d[r2 + 2].y});
+      acc_prod<float>(a1, z2.w, df{vs_d[r2 + 3].x, vs_d[r2 + 3].y});
     }
-    if (r < L.TB) acc_prod<float>(a0, col[r], df{vs_d[r].x, vs_d[r].y});
+    if (q < quads) {
+      const float4 z = col[q];
+      const int r = 4 * q;
+      acc_prod<float>(a0, z.x, df{vs_d[r].x, vs_d[r].y});
+      acc_prod<float>(a0, z.y, df{vs_d[r + 1].x, vs_d[r + 1].y});
+      acc_prod<float>(a0, z.z, df{vs_d[r + 2].x, vs_d[r + 2].y});
+      acc_prod<float>(a0, z.w, df{vs_d[r + 3].x, vs_d[r + 3].y});
+    }
     df_add(a0, a1);
     a0 = df_warp_sum(a0);
     if (lane == 0) part[(size_t)j * L.NB + s] = df_to_double(a0);
@@ -201,13 +233,22 @@ cudaError_t run_dir_product(const Layout& L, int store, int trans, const double*
   if (trans == 0) {   // part holds the scaled x (d entries of 8 bytes)
     dir_scale_kernel<<<(int)std::min<int64_t>((L.n + 255) / 256, 1024), 256, 0, st>>>(x, sc, L.n, f64 ? 1 : 0, part);
     const int blocks = (int)std::min<int64_t>((L.d + 255) / 256, 65535);
-    if (f64) dir_rowdot_f64<<<blocks, 256, 0, st>>>(L, part, out);
-    else dir_rowdot_f32<<<blocks, 256, 0, st>>>(L, reinterpret_cast<const float2*>(part), out);
+    if (f64) {
+      dir_rowdot_f64<<<blocks, 256, 0, st>>>(L, part, out);
+    } else {
+      if (L.TB % 4) return cudaErrorInvalidValue;
+      const int qb = (int)std::min<int64_t>(((int64_t)L.NB * (L.TB / 4) + 255) / 256, 65535);
+      dir_rowdot_f32<<<qb, 256, 0, st>>>(L, reinterpret_cast<const float2*>(part), out);
+    }
     return cudaGetLastError();
   }
   const size_t smem = (size_t)L.TB * 8;
-  if (f64) dir_coldot_f64<<<L.NB, 256, smem, st>>>(L, x, part);
-  else dir_coldot_f32<<<L.NB, 256, smem, st>>>(L, x, part);
+  if (f64) {
+    dir_coldot_f64<<<L.NB, 256, smem, st>>>(L, x, part);
+  } else {
+    if (L.TB % 4) return cudaErrorInvalidValue;
+    dir_coldot_f32<<<L.NB, 256, smem, st>>>(L, x, part);
+  }
   const int rb = (int)std::min<int64_t>((L.n * 32 + 255) / 256, 4096);
   dir_colsum_kernel<<<rb, 256, 0, st>>>(part, sc, L.n, L.NB, out);
   return cudaGetLastError();

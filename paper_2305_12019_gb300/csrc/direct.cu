@@ -92,46 +92,69 @@ __global__ void dir_scale_kernel(const double* x, const double* sc, int64_t d, i
   }
 }
 
-// FP32: one thread per quad of consecutive samples of a slab (the slab height is
-// a multiple of 4, so each column's quad is one 16-byte load and a warp reads
-// 512 contiguous bytes per column)
-__global__ void dir_rowdot_f32(Layout L, const float2* __restrict__ xs, double* out) {
+// FP32: a block takes 64 quads of consecutive samples (the slab height is a
+// multiple of 4, so a column's quad is one 16-byte load and a warp reads 512
+// contiguous bytes) and splits the d columns over blockDim / 64 groups (1 or
+// 4; 4 when there are too few quads to fill the GPU), whose double-float
+// partials are added in a fixed order.
+constexpr int kRowQuads = 64, kRowGroups = 4;
+
+__global__ void __launch_bounds__(kRowQuads * kRowGroups) dir_rowdot_f32(Layout L, const float2* __restrict__ xs,
+                                                                         double* out) {
+  const int ng = blockDim.x / kRowQuads;
+  __shared__ float2 s_acc[kRowGroups][4][kRowQuads];
   const int64_t n = L.d, d = L.n;
   const int64_t qps = L.TB / 4;                       // quads per slab
   const int64_t nq = (int64_t)L.NB * qps;
-  for (int64_t qd = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; qd < nq; qd += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t s = qd / qps, r = (qd - s * qps) * 4;
-    const float4* col = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(L.Z) + (size_t)s * L.TB * d + r);
-    const int64_t cs = L.TB / 4;                       // float4 stride between columns
+  const int tq = threadIdx.x % kRowQuads, cg = threadIdx.x / kRowQuads;
+  for (int64_t q0 = (int64_t)blockIdx.x * kRowQuads; q0 < nq; q0 += (int64_t)gridDim.x * kRowQuads) {
+    const int64_t qd = q0 + tq;
     df a0{0.f, 0.f}, a1{0.f, 0.f}, a2{0.f, 0.f}, a3{0.f, 0.f};
-    int64_t j = 0;
-    for (; j + 1 < d; j += 2) {
-      const float4 z = col[(size_t)j * cs], z2 = col[(size_t)(j + 1) * cs];
-      const float2 xv = __ldg(xs + j), xw = __ldg(xs + j + 1);
-      const df x{xv.x, xv.y}, w{xw.x, xw.y};
-      acc_prod<float>(a0, z.x, x);
-      acc_prod<float>(a1, z.y, x);
-      acc_prod<float>(a2, z.z, x);
-      acc_prod<float>(a3, z.w, x);
-      acc_prod<float>(a0, z2.x, w);
-      acc_prod<float>(a1, z2.y, w);
-      acc_prod<float>(a2, z2.z, w);
-      acc_prod<float>(a3, z2.w, w);
+    int64_t s = 0, r = 0;
+    if (qd < nq) {
+      s = qd / qps;
+      r = (qd - s * qps) * 4;
+      const float4* col = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(L.Z) + (size_t)s * L.TB * d + r);
+      const int64_t cs = L.TB / 4;                     // float4 stride between columns
+      int64_t j = cg;
+      for (; j + ng < d; j += 2 * ng) {
+        const float4 z = col[(size_t)j * cs], z2 = col[(size_t)(j + ng) * cs];
+        const float2 xv = __ldg(xs + j), xw = __ldg(xs + j + ng);
+        const df x{xv.x, xv.y}, w{xw.x, xw.y};
+        acc_prod<float>(a0, z.x, x);
+        acc_prod<float>(a1, z.y, x);
+        acc_prod<float>(a2, z.z, x);
+        acc_prod<float>(a3, z.w, x);
+        acc_prod<float>(a0, z2.x, w);
+        acc_prod<float>(a1, z2.y, w);
+        acc_prod<float>(a2, z2.z, w);
+        acc_prod<float>(a3, z2.w, w);
+      }
+      if (j < d) {
+        const float4 z = col[(size_t)j * cs];
+        const float2 xv = __ldg(xs + j);
+        const df x{xv.x, xv.y};
+        acc_prod<float>(a0, z.x, x);
+        acc_prod<float>(a1, z.y, x);
+        acc_prod<float>(a2, z.z, x);
+        acc_prod<float>(a3, z.w, x);
+      }
     }
-    if (j < d) {
-      const float4 z = col[(size_t)j * cs];
-      const float2 xv = __ldg(xs + j);
-      const df x{xv.x, xv.y};
-      acc_prod<float>(a0, z.x, x);
-      acc_prod<float>(a1, z.y, x);
-      acc_prod<float>(a2, z.z, x);
-      acc_prod<float>(a3, z.w, x);
+    s_acc[cg][0][tq] = make_float2(a0.hi, a0.lo);
+    s_acc[cg][1][tq] = make_float2(a1.hi, a1.lo);
+    s_acc[cg][2][tq] = make_float2(a2.hi, a2.lo);
+    s_acc[cg][3][tq] = make_float2(a3.hi, a3.lo);
+    __syncthreads();
+    if (cg == 0 && qd < nq) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        df t{s_acc[0][k][tq].x, s_acc[0][k][tq].y};
+        for (int g = 1; g < ng; ++g) df_add(t, df{s_acc[g][k][tq].x, s_acc[g][k][tq].y});
+        const int64_t i = s * L.TB + r + k;
+        if (i < n) out[i] = df_to_double(t);
+      }
     }
-    const int64_t i0 = s * L.TB + r;
-    if (i0 < n) out[i0] = df_to_double(a0);
-    if (i0 + 1 < n) out[i0 + 1] = df_to_double(a1);
-    if (i0 + 2 < n) out[i0 + 2] = df_to_double(a2);
-    if (i0 + 3 < n) out[i0 + 3] = df_to_double(a3);
+    __syncthreads();
   }
 }
 
@@ -237,8 +260,10 @@ cudaError_t run_dir_product(const Layout& L, int store, int trans, const double*
       dir_rowdot_f64<<<blocks, 256, 0, st>>>(L, part, out);
     } else {
       if (L.TB % 4) return cudaErrorInvalidValue;
-      const int qb = (int)std::min<int64_t>(((int64_t)L.NB * (L.TB / 4) + 255) / 256, 65535);
-      dir_rowdot_f32<<<qb, 256, 0, st>>>(L, reinterpret_cast<const float2*>(part), out);
+      const int64_t nq = (int64_t)L.NB * (L.TB / 4);
+      const int ng = nq < (int64_t)152 * 1024 ? kRowGroups : 1;   // fewer quads than ~1024 per SM: split d
+      const int qb = (int)std::min<int64_t>((nq + kRowQuads - 1) / kRowQuads, 65535);
+      dir_rowdot_f32<<<qb, kRowQuads * ng, 0, st>>>(L, reinterpret_cast<const float2*>(part), out);
     }
     return cudaGetLastError();
   }

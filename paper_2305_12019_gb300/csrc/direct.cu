@@ -305,8 +305,8 @@ __global__ void dir_gemv_kernel(DirArgs a) {
   }
 }
 
-// the n-space block sums of the last per-sample kernel: totals of the slots in
-// [k0, k1) (one warp per slot, fixed order)
+// total of one slot of the per-block partial sums (one warp, fixed order; the
+// result in every lane)
 __device__ __forceinline__ double block_total(const double* part, int nblk, int lane) {
   double acc = 0.0;
   for (int b = lane; b < nblk; b += 32) acc += part[b];

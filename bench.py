@@ -84,6 +84,23 @@ def _dist():
     return ws, rank
 
 
+def max_over_ranks(t_ms, ws, device="cuda"):
+    """The largest of the ranks' timed milliseconds (all_reduce MAX), the same on
+    every rank; t_ms itself on one rank."""
+    if ws <= 1:
+        return float(t_ms)
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([float(t_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def replica_rate(units_per_rank, t_ms_max, ws):
+    """Whole-job rate of ws independent replicas: all units over the slowest rank's time."""
+    return ws * units_per_rank / (t_ms_max / 1e3)
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -291,13 +308,9 @@ def main():
     if ws > 1:
         torch.distributed.barrier()
     step_ms = [a.elapsed_time(b2) for a, b2 in ev]
-    t_ms = sum(step_ms)
-    if ws > 1:
-        tt = torch.tensor([t_ms], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_ms = float(tt.item())
+    t_ms = max_over_ranks(sum(step_ms), ws)
     ms_per_step = t_ms / args.steps
-    value = ws * args.steps / (t_ms / 1e3)
+    value = replica_rate(args.steps, t_ms, ws)
     for r in results:
         if r["status"] != 0 or r["kkt"] > inst.tol:
             raise SystemExit(f"solve did not converge: {r}")
@@ -323,7 +336,7 @@ def main():
         r, w = step_e2e()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
         assert r["status"] == 0
-    e2e_val = ws * len(e2e_ms) / (sum(e2e_ms) / 1e3)
+    e2e_val = replica_rate(len(e2e_ms), max_over_ranks(sum(e2e_ms), ws), ws)
     h2d = d * n * 4 + n * 8
     d2h = d * 8 + 256
 

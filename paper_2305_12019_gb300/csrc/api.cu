@@ -240,7 +240,7 @@ static gdwd_status create_direct(gdwd_handle* h, const void* Z, int zdt, int64_t
   CK(halloc(h, &h->wtmp, d), "alloc");
   CK(halloc(h, &h->scal, (size_t)DS_SLOTS * h->nblk), "alloc");
   CK(halloc(h, &h->dscal, h->nblk), "alloc");
-  CK(halloc(h, (uint8_t**)&h->partial, (size_t)d * h->L.NB * sizeof(double)), "alloc");
+  CK(halloc(h, (uint8_t**)&h->partial, (size_t)2 * d * h->L.NB * sizeof(double)), "alloc");   // two products
   CK(halloc(h, &h->dscalars, 8), "alloc");
   CK(halloc(h, &h->bar, 4), "alloc");
   CK(halloc(h, &h->err, 4), "alloc");
@@ -701,6 +701,12 @@ static cudaError_t dir_apply(int trans, const double* x, double* out, void* ctx)
   return run_dir_product(h->L, h->store, trans, x, h->sc, out, reinterpret_cast<double*>(h->partial), h->stream);
 }
 
+static cudaError_t dir_apply2(const double* x, const double* x2, double* out, double* out2, void* ctx) {
+  gdwd_handle* h = static_cast<gdwd_handle*>(ctx);
+  double* part = reinterpret_cast<double*>(h->partial);
+  return run_dir_product2(h->L, h->store, x, x2, h->sc, out, out2, part, part + (size_t)h->d * h->L.NB, h->stream);
+}
+
 // One solve of the direct solver from the initial iterate of reading R3.  The
 // host issues the iteration's kernels in batches of kDirBatch iterations and
 // reads the control block between batches; kernels issued after convergence
@@ -766,7 +772,7 @@ static gdwd_status solve_direct(gdwd_handle* h, double C, double* w, int w_on_de
   a.dscal = h->dscal;
   a.nblk = h->nblk;
   a.ctrl = h->ctrl;
-  const DirPasses ps{dir_apply, h};
+  const DirPasses ps{dir_apply, dir_apply2, h};
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0), "event");
   CK(cudaEventCreate(&e1), "event");

@@ -216,6 +216,48 @@ __global__ void dir_coldot_f32(Layout L, const double* __restrict__ v, double* p
   }
 }
 
+// Two right-hand sides in one read of the slab: part[j * NB + s] and
+// part2[j * NB + s] for v and v2 (FP32 storage)
+__global__ void dir_coldot2_f32(Layout L, const double* __restrict__ v, const double* __restrict__ v2, double* part,
+                                double* part2) {
+  extern __shared__ float2 vs_d[];                    // TB entries of v, then TB of v2
+  float2* vs2 = vs_d + L.TB;
+  const int64_t s = blockIdx.x;
+  const int64_t n = L.d, d = L.n;
+  for (int r = threadIdx.x; r < L.TB; r += blockDim.x) {
+    const int64_t i = s * L.TB + r;
+    const df t = df_from(i < n ? v[i] : 0.0), t2 = df_from(i < n ? v2[i] : 0.0);
+    vs_d[r] = make_float2(t.hi, t.lo);
+    vs2[r] = make_float2(t2.hi, t2.lo);
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int quads = L.TB / 4;
+  const float* base = reinterpret_cast<const float*>(L.Z) + (size_t)s * L.TB * d;
+  for (int64_t j = warp; j < d; j += nw) {
+    const float4* col = reinterpret_cast<const float4*>(base + (size_t)j * L.TB);
+    df a0{0.f, 0.f}, b0{0.f, 0.f};
+    for (int q = lane; q < quads; q += 32) {
+      const float4 z = col[q];
+      const int r = 4 * q;
+      acc_prod<float>(a0, z.x, df{vs_d[r].x, vs_d[r].y});
+      acc_prod<float>(a0, z.y, df{vs_d[r + 1].x, vs_d[r + 1].y});
+      acc_prod<float>(a0, z.z, df{vs_d[r + 2].x, vs_d[r + 2].y});
+      acc_prod<float>(a0, z.w, df{vs_d[r + 3].x, vs_d[r + 3].y});
+      acc_prod<float>(b0, z.x, df{vs2[r].x, vs2[r].y});
+      acc_prod<float>(b0, z.y, df{vs2[r + 1].x, vs2[r + 1].y});
+      acc_prod<float>(b0, z.z, df{vs2[r + 2].x, vs2[r + 2].y});
+      acc_prod<float>(b0, z.w, df{vs2[r + 3].x, vs2[r + 3].y});
+    }
+    a0 = df_warp_sum(a0);
+    b0 = df_warp_sum(b0);
+    if (lane == 0) {
+      part[(size_t)j * L.NB + s] = df_to_double(a0);
+      part2[(size_t)j * L.NB + s] = df_to_double(b0);
+    }
+  }
+}
+
 __global__ void dir_coldot_f64(Layout L, const double* __restrict__ v, double* part) {
   extern __shared__ float2 vs_d[];
   double* vd = reinterpret_cast<double*>(vs_d);
@@ -247,6 +289,19 @@ __global__ void dir_colsum_kernel(const double* part, const double* sc, int64_t 
     acc = warp_sum(acc);
     if (lane == 0) out[j] = sc[j] * acc;
   }
+}
+
+cudaError_t run_dir_product2(const Layout& L, int store, const double* x, const double* x2, const double* sc,
+                             double* out, double* out2, double* part, double* part2, cudaStream_t st) {
+  if (store != GDWD_F32 || L.TB % 4) {   // FP64 storage: two single products
+    cudaError_t e = run_dir_product(L, store, 1, x, sc, out, part, st);
+    return e != cudaSuccess ? e : run_dir_product(L, store, 1, x2, sc, out2, part2, st);
+  }
+  dir_coldot2_f32<<<L.NB, 256, (size_t)L.TB * 16, st>>>(L, x, x2, part, part2);
+  const int rb = (int)std::min<int64_t>((L.n * 32 + 255) / 256, 4096);
+  dir_colsum_kernel<<<rb, 256, 0, st>>>(part, sc, L.n, L.NB, out);
+  dir_colsum_kernel<<<rb, 256, 0, st>>>(part2, sc, L.n, L.NB, out2);
+  return cudaGetLastError();
 }
 
 cudaError_t run_dir_product(const Layout& L, int store, int trans, const double* x, const double* sc, double* out,
@@ -514,8 +569,7 @@ cudaError_t run_dir_iteration(const DirArgs& a, const DirPasses& ps, cudaStream_
   }
   dir_step23_kernel<<<nb, kThreads, 0, st>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = ps.apply(1, a.dv, a.Zxr, ps.ctx)) != cudaSuccess) return e;        // Z~ (xi - r)
-  if ((e = ps.apply(1, a.dv2, a.Za, ps.ctx)) != cudaSuccess) return e;        // Z~ alpha
+  if ((e = ps.apply2(a.dv, a.dv2, a.Zxr, a.Za, ps.ctx)) != cudaSuccess) return e;   // Z~ (xi - r), Z~ alpha
   dir_s_kernel<<<1, kThreads, 0, st>>>(a);
   return cudaGetLastError();
 }

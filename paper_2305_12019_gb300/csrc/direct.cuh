@@ -42,6 +42,8 @@ struct DirArgs {
 // out = Z~^T x (n-vector from a d-vector), trans = 1 gives out = Z~ x.
 struct DirPasses {
   cudaError_t (*apply)(int trans, const double* x, double* out, void* ctx);
+  // out = Z~ x and out2 = Z~ x2 in one read of the stored data
+  cudaError_t (*apply2)(const double* x, const double* x2, double* out, double* out2, void* ctx);
   void* ctx;
 };
 
@@ -51,6 +53,9 @@ int dir_blocks(int64_t n);
 // part (d x NB per-slab partials).
 cudaError_t run_dir_product(const Layout& L, int store, int trans, const double* x, const double* sc, double* out,
                             double* part, cudaStream_t st);
+// out = Z~ x and out2 = Z~ x2 (one read of the slabs for FP32 storage)
+cudaError_t run_dir_product2(const Layout& L, int store, const double* x, const double* x2, const double* sc,
+                             double* out, double* out2, double* part, double* part2, cudaStream_t st);
 cudaError_t run_transpose(const void* Z, int zdt, int64_t d, int64_t n, int64_t ld, void* out, cudaStream_t st);
 // one iteration of Algorithm 1 (all its kernels; a no-op once ctrl->done is set)
 cudaError_t run_dir_iteration(const DirArgs& a, const DirPasses& ps, cudaStream_t st);

@@ -1,0 +1,104 @@
+"""CPU checks of the algebra the CUDA path uses in place of the paper's formulas,
+against the oracle (no CUDA code is imported).
+
+* The n-space reduction of eq-linsys (Woodbury on the SMW2 form): x = G^{-1}(b + v),
+  beta = -y^T x / s, c = x + beta p, w = g' - Z~ c / mu.
+* The border elimination of the direct solver: with G' = I + Z~ Z~^T / mu,
+  P = G'^{-1}, b^ = Z~ y, p = P b^, s = b^T p:
+  beta = (h_beta - p^T h_w / mu) / (n - s / mu), w = (P h_w - p beta) / mu.
+* The kernelized iteration: u, rho, g carried as coefficient vectors in the columns
+  of Z~, every d-space norm a quadratic form in K = Z~^T Z~; its iterates equal
+  those of Algorithm 1 as the oracle runs it.
+"""
+import math
+
+import numpy as np
+
+from oracle import gdwd_oracle as O
+
+
+def _problem(seed, d, n, mu=0.8):
+    rng = np.random.default_rng(seed)
+    Z = rng.standard_normal((d, n))
+    y = np.where(np.arange(n) < n // 3, 1.0, -1.0)
+    return Z, y, mu, rng
+
+
+def test_nspace_reduction_matches_smw2():
+    Z, y, mu, rng = _problem(1, 40, 12)
+    G = np.eye(12) + Z.T @ Z / mu
+    p = np.linalg.solve(G, y)
+    s = y @ p
+    for _ in range(3):
+        u, rho, v = rng.standard_normal(40), rng.standard_normal(40), rng.standard_normal(12)
+        sigma = 0.37
+        gp = u + rho / (sigma * math.sqrt(mu))
+        x = np.linalg.solve(G, Z.T @ gp + v)
+        beta = -(y @ x) / s
+        c = x + beta * p
+        w = gp - Z @ c / mu
+        h = np.concatenate([-Z @ v + mu * u + math.sqrt(mu) * rho / sigma, [-(y @ v)]])
+        ref = O.SMW2(Z, y, mu).solve(h)
+        assert np.allclose(w, ref[:40], rtol=1e-11, atol=1e-11)
+        assert abs(beta - ref[40]) <= 1e-11 * (1 + abs(ref[40]))
+
+
+def test_direct_border_elimination_matches_direct_solve():
+    Z, y, mu, rng = _problem(2, 6, 50)
+    d, n = Z.shape
+    Gp = np.eye(d) + Z @ Z.T / mu
+    P = np.linalg.inv(Gp)
+    bh = Z @ y
+    p = P @ bh
+    s = bh @ p
+    for _ in range(3):
+        h = rng.standard_normal(d + 1)
+        beta = (h[d] - p @ h[:d] / mu) / (n - s / mu)
+        w = (P @ h[:d] - p * beta) / mu
+        ref = O.Direct(Z, y, mu).solve(h)
+        assert np.allclose(w, ref[:d], rtol=1e-11, atol=1e-11)
+        assert abs(beta - ref[d]) <= 1e-11 * (1 + abs(ref[d]))
+
+
+def test_kernelized_iterates_equal_algorithm_1():
+    """Twenty iterations of the coefficient form against the oracle's own iterates
+    (the same sigma: the oracle's sigma path is replayed)."""
+    rng = np.random.default_rng(3)
+    d, n, q, C, mu, tau = 30, 14, 1.0, 2.0, 1.0, 1.618
+    y = np.where(np.arange(n) < 6, 1.0, -1.0)
+    Z = rng.standard_normal((d, n)) * y
+    ref = O.solve(Z, y, q, C, mu=mu, tau=tau, tol=1e-300, max_iter=20, record=True)
+    sigmas = [h[0] for h in ref["history"]]
+    Zt, zs = O.scale_data(Z)
+    K = Zt.T @ Zt
+    G = np.eye(n) + K / mu
+    p = np.linalg.solve(G, y)
+    s = y @ p
+    sq = math.sqrt(mu)
+    r, xi, alpha = np.ones(n), np.ones(n), np.zeros(n)
+    au, ar = np.zeros(n), np.zeros(n)
+    for sigma in sigmas:
+        gs = 1.0 / (sigma * sq)
+        b = K @ au + (K @ ar) * gs                                    # Z~^T g'
+        vbar = xi - r - alpha / sigma
+        xb = np.linalg.solve(G, b + vbar)
+        betab = -(y @ xb) / s
+        cbar = xb + betab * p
+        r = O.prox_r(cbar + r, sigma, q, r0=r)                        # Step 1b
+        v = xi - r - alpha / sigma
+        x = np.linalg.solve(G, b + v)
+        beta = -(y @ x) / s
+        c = x + beta * p
+        ztw = c - v - y * beta                                        # Z~^T w
+        ag = au - c / mu                                              # g = Z~ a_g
+        gnorm = math.sqrt(max(ag @ K @ ag, 0.0))
+        theta = 1.0 if gnorm <= zs else zs / gnorm
+        xi = np.maximum(0.0, r - ztw - y * beta + alpha / sigma - C / sigma)   # Step 2
+        alpha = alpha - tau * sigma * (ztw + y * beta + xi - r)                # Step 3
+        ar = (1.0 - tau) * ar - tau * sigma * sq * (1.0 - theta) * ag
+        au = theta * ag
+    assert np.allclose(r, ref["r"], rtol=1e-9, atol=1e-12)
+    assert np.allclose(alpha, ref["alpha"], rtol=1e-9, atol=1e-12)
+    assert np.allclose(xi, ref["xi"], rtol=1e-9, atol=1e-12)
+    assert np.allclose(Zt @ au, ref["u_scaled"], rtol=1e-9, atol=1e-12)
+    assert np.allclose(Zt @ ar, ref["rho"], rtol=1e-9, atol=1e-12)

@@ -49,6 +49,8 @@ uint64_t footprint(const gdwd_request& r) {
   const int st = r.opts.store;
   const uint64_t es = st == GDWD_F64 ? 8 : st == GDWD_F32 ? 4 : st == GDWD_E4M3 ? 1 : 2;
   const uint64_t d = (uint64_t)r.d, n = (uint64_t)r.n;
+  if (r.opts.solver == 1)   // direct solver: Z^T plus a transposed copy at set-up, d x d matrices, n-vectors
+    return 2 * (n + 4096) * d * es + 64ull * d * d + 96ull * n + 4096ull * d + (8ull << 20);
   const uint64_t kern = r.opts.kernelized ? 8ull * n * (n + 1) : 0;   // K as double-float
   return (d + 4096) * n * es + 64ull * n * n + kern + 160ull * (d + 4096) + 4096ull * n + (8ull << 20);
 }

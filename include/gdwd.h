@@ -111,8 +111,9 @@ typedef struct {
                          the d x d matrix I + Z~ Z~^T / mu (factored once, FP64
                          diagonal tiles, double-float inverse) with its border
                          eliminated in closed form; Z^T is stored with samples as
-                         rows, and each iteration is two streaming passes per solve
-                         of eq-linsys plus the per-sample Steps 1b, 2 and 3.  With
+                         rows, and each iteration reads it four times (five products
+                         with Z~) around the per-sample Steps 1b, 2 and 3.  Every
+                         solve starts from the initial iterate.  With
                          solver = 1: F32 or F64 storage, refine = 0 and kernelized =
                          0 (else EUNSUPPORTED); gdwd_apply,
                          gdwd_get_stored and gdwd_suggest_C return EUNSUPPORTED and

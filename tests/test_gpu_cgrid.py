@@ -56,3 +56,21 @@ def test_joint_equals_sequential_bf16_six_c(gdwd_lib):
         relobj = abs(rj[k]["primal_obj"] - rs[k]["primal_obj"]) / abs(rs[k]["primal_obj"])
         relw = np.linalg.norm(wj[:, k] - ws[:, k]) / np.linalg.norm(ws[:, k])
         assert relobj <= 1e-6 and relw <= 1e-4, (k, relobj, relw)
+
+
+def test_cgrid_full_size_certificates(gdwd_lib):
+    """The C-grid workload at its full size (d = 50000, n = 2000, BF16 storage, the
+    joint kernel), on four of its 32 values of C: every solve reaches kkt <= 1e-6
+    on the stored problem, and the weak-duality certificate on the ORIGINAL data
+    (an FP64 host computation that holds at any size) stays at the level the BF16
+    quantization allows."""
+    inst = synth.gaussian(seed=3001, d=50000, n=2000, shift=1.5, q=1.0, C=1.0)
+    Cs = list(np.logspace(-2, 3, 32)[[4, 12, 20, 28]])
+    with gdwd_lib.Solver(inst.Z, inst.y, 1.0, 1.0, store="bf16", tol=1e-6) as s:
+        res, w, alpha = s.solve(Cs=Cs, alpha=True)
+    Z64 = inst.Z.astype(np.float64)
+    for k, C in enumerate(Cs):
+        r = res[k]
+        assert r["status"] == 0 and r["kkt"] <= 1e-6, (k, r)
+        up, lo, gap = O.certified_gap(Z64, inst.y, w[:, k], r["beta"], alpha[:, k], 1.0, C)
+        assert gap <= 1e-5, (k, gap)

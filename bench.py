@@ -238,7 +238,7 @@ def main():
     ap.add_argument("--big-n", type=int, default=5000)
     ap.add_argument("--kern-wide-d", type=int, default=200000)
     ap.add_argument("--kern-steps", type=int, default=3)
-    ap.add_argument("--kern", type=int, default=0, help="uneven_batch / served: 1 = kernelized iteration")
+    ap.add_argument("--kern", type=int, default=0, help="uneven_batch / served / largest_fp8: 1 = kernelized iteration")
     ap.add_argument("--dir-d", type=int, default=200)
     ap.add_argument("--dir-n", type=int, default=1000000)
     args = ap.parse_args()

@@ -12,7 +12,7 @@ stand-ins for the paper's data sets (see paper_2305_12019_gb300/synth.py).
   served        Poisson arrivals (200/s for 10 s by default) of FP16 problems with
                 d log-uniform 1k-100k, n 50-5000, q in {1,2}, C 0.1-100, generated
                 on the device per request seed: p50 / p99 latency and solves/s
-                (uneven_batch and served: --kern 1 runs the kernelized iteration)
+                (uneven_batch, served, largest_fp8: --kern 1 runs the kernelized iteration)
   direct_fp32   d=200, n=1e6 FP32 through the direct solver of eq-linsys (d << n):
                 solves/s, iterations, streaming-pass bandwidth
   largest_fp8   d=200000, n=5000, Student-t columns, 1:3, 16 values of C, E4M3
@@ -237,7 +237,7 @@ def largest_fp8(args, gdwd, synth):
     Zd = _device_colmajor(inst.Z)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    with gdwd.Solver(Zd, inst.y, 1.0, 1.0, store="e4m3", tol=1e-6, refine=1) as s:
+    with gdwd.Solver(Zd, inst.y, 1.0, 1.0, store="e4m3", tol=1e-6, refine=1, kernelized=args.kern) as s:
         res, w, alpha = s.solve(Cs=Cs, alpha=True)
         info = s.info()
     torch.cuda.synchronize()
@@ -246,7 +246,8 @@ def largest_fp8(args, gdwd, synth):
     gaps = [O.certified_gap(Z64, inst.y, w[:, k], res[k]["beta"], alpha[:, k], 1.0, Cs[k])[2] for k in (0, 15)]
     return {"metric": "gDWD C-solves/s at KKT<=1e-6 on the original data (FP8 + FP32 refinement)",
             "value": 16 / dt, "unit": "solves/s", "ms_per_step": dt * 1e3,
-            "config": {"workload": f"largest_fp8 d={d} n={n} Student-t 1:3 16 C", "store": "e4m3+refine"},
+            "config": {"workload": f"largest_fp8 d={d} n={n} Student-t 1:3 16 C", "store": "e4m3+refine",
+                       "iteration": "kernelized" if args.kern else "Z-streaming"},
             "setup_ms": info["t_setup_ms"], "gram_tensor_cores": info["gram_tensor_cores"],
             "iters": [r["iters"] for r in res],
             "converged": int(sum(r["status"] == 0 for r in res)), "certified_gap_C_ends": gaps}

@@ -1,7 +1,7 @@
 // C-ABI of libgdwd (include/gdwd.h): argument checks, handle memory, set-up
 // and solve orchestration on the caller's stream.  No computation of the
-// method happens on the host: every step runs in the kernels of setup.cu and
-// iterate.cu.
+// method happens on the host: every step runs in the kernels of setup.cu,
+// gram_tc.cu, iterate.cu, iterate_multi.cu, iterate_kern.cu and direct.cu.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>

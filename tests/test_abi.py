@@ -112,3 +112,46 @@ def test_server_arguments_rejected(lib):
     assert lib.gdwd_server_destroy(None) == 0
     assert lib.gdwd_solve_batch(None, -1, 1, None, None) == 1
     assert lib.gdwd_solve_batch(None, 0, 1, None, None) == 0
+
+
+def test_header_is_c_and_links_from_c(tmp_path, lib):
+    """include/gdwd.h compiles as C99 and a C program links against libgdwd.so and
+    calls it (the calls that need no GPU)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "abi.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include "gdwd.h"
+int main(void) {
+  gdwd_options o;
+  if (gdwd_default_options(&o) != GDWD_OK) return 1;
+  if (gdwd_default_options(NULL) != GDWD_EINVAL) return 2;
+  if (o.max_iter != 20000 || o.store != GDWD_F32 || o.solver != 0 || o.kernelized != 0) return 3;
+  if (gdwd_free(NULL) != GDWD_OK) return 4;
+  gdwd_handle* h = 0;
+  double y[2] = {1.0, 1.0};
+  float z[2] = {1.0f, 1.0f};
+  if (gdwd_create(z, GDWD_F32, 1, 2, 1, 0, y, 1.0, 1.0, &o, &h) != GDWD_EINVAL || h) return 5;
+  printf("ok %zu %zu\n", sizeof(gdwd_options), sizeof(gdwd_info));
+  return 0;
+}
+''')
+    libdir = os.path.join(ROOT, "paper_2305_12019_gb300")
+    exe = tmp_path / "abi"
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                        "-L", libdir, "-lgdwd", "-Wl,-rpath," + libdir, "-o", str(exe)],
+                       capture_output=True, text=True)
+    if r.returncode != 0 and "cannot find -lgdwd" in r.stderr:
+        # the library file is libgdwd.so in the package directory: link it by path
+        r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                            os.path.join(libdir, "libgdwd.so"), "-Wl,-rpath," + libdir, "-o", str(exe)],
+                           capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0, (out.returncode, out.stderr)
+    from paper_2305_12019_gb300 import gdwd
+    assert out.stdout.split() == ["ok", str(ctypes.sizeof(gdwd.Options)), str(ctypes.sizeof(gdwd.Info))]

@@ -313,8 +313,9 @@ gdwd_status gdwd_get_stored(const gdwd_handle* h, void* Zq, double* colscale);
  *     (different streams, or different host threads without ordering) race and
  *     give wrong results; order them on one stream;
  *   - no cudaMalloc, cudaFree or allocating library routine is called.
- * The paper has no counterpart (its set-up forms I + Z^T Z / mu, Sec. 3.3.2, by
- * an ordinary allocating routine).  Errors: EINVAL, ECUDA.
+ * The paper has no counterpart.  Errors: EINVAL (including n > 2048), ECUDA
+ * (also when an earlier asynchronous error is still pending on entry: it is
+ * left in place for the caller, and nothing is launched).
  */
 gdwd_status gdwd_gram_noalloc(const float* Z, int64_t d, int64_t n, int64_t ldz, double* K, void* stream);
 

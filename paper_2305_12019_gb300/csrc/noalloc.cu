@@ -22,6 +22,7 @@ namespace gdwd {
 namespace {
 
 constexpr int64_t kScratchDoubles = 4ll << 20;   // 32 MiB of FP64 partial products
+constexpr int64_t kMaxN = 2048;                   // kMaxN * kMaxN == kScratchDoubles
 constexpr int kTile = 64;
 constexpr int kChunk = 16;
 
@@ -134,14 +135,18 @@ using namespace gdwd;
 
 extern "C" gdwd_status gdwd_gram_noalloc(const float* Z, int64_t d, int64_t n, int64_t ldz, double* K, void* stream) {
   if (!Z || !K || d < 1 || n < 1 || ldz < d) return GDWD_EINVAL;
-  if (n * n > kScratchDoubles) return GDWD_EINVAL;   // n > 2048: beyond the fixed scratch
+  // n > 2048 is beyond the fixed scratch; n is bounded before it is squared
+  if (n > kMaxN || n * n > kScratchDoubles) return GDWD_EINVAL;
+  // an asynchronous error of earlier, unrelated work is left for its owner to
+  // read: this call launches nothing on a context that already failed
+  if (cudaPeekAtLastError() != cudaSuccess) return GDWD_ECUDA;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return GDWD_ECUDA;
   cudaError_t e = cudaSuccess;
   double* scratch = scratch_address(dev, &e);
   if (!scratch) return GDWD_ECUDA;
   int sms = 1;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) return GDWD_ECUDA;
   const int T = (int)((n + kTile - 1) / kTile);
   const int tiles = T * (T + 1) / 2;
   int ksplit = std::max(1, std::min<int>((2 * sms + tiles - 1) / tiles, 16));

@@ -375,10 +375,17 @@ def gram_noalloc(Z, K, stream=None):
     """K = Z^T Z (gdwd_gram_noalloc) for a CUDA float32 Z (d x n, column-major:
     Z.stride(0) == 1) into a CUDA float64 K (n x n, contiguous).  The library
     allocates nothing; its scratch is a fixed array inside the library (n <= 2048)."""
+    import torch
     lib = load()
     if Z.dim() != 2 or Z.stride(0) != 1:
         raise ValueError("Z must be d x n column-major (stride(0) == 1)")
+    if Z.dtype != torch.float32 or not Z.is_cuda:
+        raise ValueError("Z must be a CUDA float32 tensor")
     d, n = Z.shape
+    if K.dtype != torch.float64 or not K.is_cuda or not K.is_contiguous():
+        raise ValueError("K must be a contiguous CUDA float64 tensor")
+    if K.numel() < n * n:
+        raise ValueError(f"K holds {K.numel()} elements, fewer than n * n = {n * n}")
     ldz = Z.stride(1) if n > 1 else d
     st = lib.gdwd_gram_noalloc(c_void_p(Z.data_ptr()), d, n, ldz, c_void_p(K.data_ptr()), stream)
     if st != OK:

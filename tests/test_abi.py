@@ -155,3 +155,17 @@ int main(void) {
     assert out.returncode == 0, (out.returncode, out.stderr)
     from paper_2305_12019_gb300 import gdwd
     assert out.stdout.split() == ["ok", str(ctypes.sizeof(gdwd.Options)), str(ctypes.sizeof(gdwd.Info))]
+
+
+def test_gram_noalloc_refuses_host_tensors(lib):
+    """The binding of gdwd_gram_noalloc checks device, dtype and the output's size
+    before it calls the library (no GPU needed for the refusal)."""
+    import torch
+    from paper_2305_12019_gb300 import gdwd
+    Z = torch.as_strided(torch.ones(8 * 4, dtype=torch.float32), (8, 4), (1, 8))
+    K = torch.zeros(16, dtype=torch.float64)
+    with pytest.raises(ValueError):
+        gdwd.gram_noalloc(Z, K)
+    Zh = torch.as_strided(torch.ones(8 * 4, dtype=torch.float16), (8, 4), (1, 8))
+    with pytest.raises(ValueError):
+        gdwd.gram_noalloc(Zh, K)

@@ -39,12 +39,34 @@ def test_gram_noalloc_matches_allocating_path(gdwd_lib):
         assert np.all(np.isfinite(got))
         assert err <= 5e-8, (d, n, err)
         assert np.array_equal(got, got.T)
+        # and directly against the FP64 product of the same FP32 data, so that an
+        # error both paths share cannot hide
+        exact = Zh.astype(np.float64).T @ Zh.astype(np.float64)
+        err64 = np.abs(got - exact).max() / np.abs(exact).max()
+        assert err64 <= 5e-8, (d, n, err64)
 
 
 def test_gram_noalloc_rejects_oversize(gdwd_lib):
-    """n beyond the fixed scratch (n * n > 4,194,304) is refused before any GPU work."""
+    """n beyond the fixed scratch (n > 2048) is refused by the library before any GPU work."""
+    import ctypes
     import torch
     big = torch.as_strided(torch.zeros(8 * 2049, dtype=torch.float32, device="cuda"), (8, 2049), (1, 8))
-    K = torch.zeros(1, dtype=torch.float64, device="cuda")
+    K = torch.zeros(2049 * 2049, dtype=torch.float64, device="cuda")
     with pytest.raises(gdwd_lib.GdwdError):
         gdwd_lib.gram_noalloc(big, K)
+    # the C entry point itself, with n so large that n * n would overflow int64
+    lib = gdwd_lib.load()
+    st = lib.gdwd_gram_noalloc(ctypes.c_void_p(big.data_ptr()), 8, 1 << 40, 8, ctypes.c_void_p(K.data_ptr()), None)
+    assert st == 1   # GDWD_EINVAL
+
+
+def test_gram_noalloc_rejects_small_output(gdwd_lib):
+    """An output K with fewer than n * n elements is refused before anything is launched."""
+    import torch
+    Z = torch.as_strided(torch.ones(64 * 100, dtype=torch.float32, device="cuda"), (64, 100), (1, 64))
+    K = torch.zeros(100 * 100 - 1, dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        gdwd_lib.gram_noalloc(Z, K)
+    Kf = torch.zeros(100 * 100, dtype=torch.float32, device="cuda")
+    with pytest.raises(ValueError):
+        gdwd_lib.gram_noalloc(Z, Kf)

@@ -21,7 +21,18 @@
  *     what it needs and owns only what it allocates inside a handle;
  *   - a handle is not thread-safe: one host thread at a time per handle;
  *   - all work is issued on the stream given in gdwd_options (0 = legacy default
- *     stream) and every call that returns results synchronizes that stream.
+ *     stream) and every call that returns results synchronizes that stream;
+ *   - every device-side wait (grid barriers, bulk copies) is bounded by
+ *     gdwd_options.timeout_s: when one runs out the kernel waits (bounded) for
+ *     its own copies still in flight, records GDWD_ETIMEOUT and returns, and the
+ *     context stays usable.
+ * Fault injection for tests (environment variables, no effect while unset):
+ *   GDWD_INJECT_ALLOC_FAIL=k  the k-th device allocation of a handle fails as if
+ *                             the device were out of memory (gdwd_create then
+ *                             returns GDWD_ENOMEM and no handle);
+ *   GDWD_INJECT_STALL=1       the Z-streaming iteration kernel waits at its first
+ *                             grid barrier for an arrival that never comes, so the
+ *                             solve returns GDWD_ETIMEOUT after timeout_s.
  */
 #ifndef GDWD_H
 #define GDWD_H

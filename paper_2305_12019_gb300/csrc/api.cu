@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -114,8 +115,22 @@ static gdwd_status cuda_fail(gdwd_handle* h, cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail(h, e_, where); \
   } while (0)
 
+// Fault-injection hooks for tests, read from the environment (no effect while
+// the variables are unset):
+//   GDWD_INJECT_ALLOC_FAIL=k  the k-th device allocation of a handle fails as if
+//                             the device were out of memory;
+//   GDWD_INJECT_STALL=1       every launch of the Z-streaming iteration kernel
+//                             waits at its first grid barrier for an arrival that
+//                             never comes, so its bounded wait runs out.
+static long env_long(const char* name) {
+  const char* v = std::getenv(name);
+  return v ? std::strtol(v, nullptr, 10) : 0;
+}
+
 template <typename T>
 static cudaError_t halloc(gdwd_handle* h, T** p, size_t count) {
+  const long inject = env_long("GDWD_INJECT_ALLOC_FAIL");
+  if (inject > 0 && (long)h->allocs.size() + 1 == inject) return cudaErrorMemoryAllocation;
   void* q = nullptr;
   const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
   cudaError_t e = cudaMallocAsync(&q, bytes, h->stream);
@@ -634,6 +649,7 @@ static IterArgs<CT> make_args(gdwd_handle* h, double C, double sigma0, int refre
   a.kc = h->kc;
   a.refresh = refresh;
   a.dots_every = dots_every_of(h);
+  a.stall_first_barrier = env_long("GDWD_INJECT_STALL") > 0 ? 1 : 0;
   a.rhsB = h->rhsB;
   a.cq = (CT*)h->cq;
   a.aq = (CT*)h->aq;

@@ -136,14 +136,16 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   return v;
 }
 
+// `extra` arrivals beyond the grid are awaited as well: 0 in normal use; a test
+// passes 1 to make the wait run out (no CTA ever supplies that arrival).
 __device__ __forceinline__ bool grid_barrier(unsigned* counter, unsigned nblocks, unsigned& gen, int* err,
-                                             uint64_t timeout_ns, int* s_flag) {
+                                             uint64_t timeout_ns, int* s_flag, unsigned extra = 0) {
   __syncthreads();
   gen += 1;
   if (threadIdx.x == 0) {
     // the CTA barrier orders the block's writes before this release (cumulativity)
     red_add_release(counter, 1u);
-    const unsigned target = gen * nblocks;
+    const unsigned target = gen * nblocks + extra;
     int ok = 1;
     uint64_t t0 = 0;
     unsigned polls = 0;

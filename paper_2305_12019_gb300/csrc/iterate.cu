@@ -188,11 +188,15 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
       s_tprev = t_;                        \
     }                                      \
   } while (0)
-#define GDWD_BARRIER(k)                                                                   \
-  do {                                                                                    \
-    GDWD_MARK(k);                                                                         \
-    if (!grid_barrier(a.bar, (unsigned)grid, gen, a.err, a.timeout_ns, &s_flag)) return; \
-    GDWD_MARK(k + 1);                                                                     \
+#define GDWD_BARRIER(k)                                                                              \
+  do {                                                                                               \
+    GDWD_MARK(k);                                                                                    \
+    if (!grid_barrier(a.bar, (unsigned)grid, gen, a.err, a.timeout_ns, &s_flag,                      \
+                      (a.stall_first_barrier && gen == 0) ? 1u : 0u)) {                              \
+      ring_drain_prefetched(rg, a.err, a.timeout_ns);                                                \
+      return;                                                                                        \
+    }                                                                                                \
+    GDWD_MARK(k + 1);                                                                                \
   } while (0)
 
   const int npair = (int)((n + 1) / 2);

@@ -397,7 +397,10 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_multi_kernel(MultiArgs<ty
 #define MBARRIER(k)                                                                       \
   do {                                                                                    \
     MMARK(k);                                                                             \
-    if (!grid_barrier(a.bar, (unsigned)grid, gen, a.err, a.timeout_ns, &s_flag)) return; \
+    if (!grid_barrier(a.bar, (unsigned)grid, gen, a.err, a.timeout_ns, &s_flag)) {       \
+      ring_drain_prefetched(rg, a.err, a.timeout_ns);                                     \
+      return;                                                                             \
+    }                                                                                     \
     MMARK(k + 1);                                                                         \
   } while (0)
 

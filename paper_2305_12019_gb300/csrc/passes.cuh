@@ -67,8 +67,33 @@ __device__ __forceinline__ void ring_prefetch(const Layout& L, Ring& rg, int cta
   rg.prefetched = pre;
 }
 
+// Waits, bounded, until the bulk copies of chunks [c0, c1) of the current stream
+// have landed (chunk c sits in stage c % stages; `flipped` marks a chunk c0
+// whose stage parity was already toggled by the wait that gave up).  A CTA that
+// leaves the kernel early calls this first, so that no copy it issued is still
+// writing its shared memory when it exits.  Every wait is bounded by tmo; if
+// one runs out the CTA leaves all the same (the error word is already set).
+__device__ __forceinline__ void ring_drain(Ring& rg, int c0, int c1, bool flipped, int* err, uint64_t tmo) {
+  if (threadIdx.x == 0) {
+    for (int c = c0; c < c1; ++c) {
+      const int st = c % rg.stages;
+      uint32_t par = (rg.phase >> st) & 1u;
+      if (flipped && c == c0) par ^= 1u;
+      if (!mbar_wait(&rg.bars[st], par, err, tmo)) break;
+    }
+  }
+  __syncthreads();
+}
+
+// Chunks issued by ring_prefetch and not yet streamed: drained before an early exit.
+__device__ __forceinline__ void ring_drain_prefetched(Ring& rg, int* err, uint64_t tmo) {
+  if (rg.prefetched > 0) ring_drain(rg, 0, rg.prefetched, false, err, tmo);
+  rg.prefetched = 0;
+}
+
 // Streams every chunk of the slabs cta, cta+grid, ... through the ring and
-// calls f.chunk / f.end_slab.  Returns false (all threads) on a timed-out wait.
+// calls f.chunk / f.end_slab.  Returns false (all threads) on a timed-out wait,
+// after the copies still in flight have landed.
 template <typename T, typename F>
 __device__ bool stream_slabs(const Layout& L, Ring& rg, int cta, int grid, int* err, uint64_t tmo, int* s_abort,
                              F& f) {
@@ -100,7 +125,11 @@ __device__ bool stream_slabs(const Layout& L, Ring& rg, int cta, int grid, int* 
     rg.phase ^= 1u << st;
     f.chunk(reinterpret_cast<const T*>(rg.buf + (size_t)st * rg.stage_bytes), k, s, col0, cw);
     __syncthreads();
-    if (*(volatile int*)s_abort) return false;
+    if (*(volatile int*)s_abort) {
+      // chunks c .. min(c + stages, total) - 1 were issued and may be in flight
+      ring_drain(rg, c, min(c + rg.stages, total), true, err, tmo);
+      return false;
+    }
     if (threadIdx.x == 0 && c + rg.stages < total) issue(c + rg.stages);
     if (cc == nch - 1) f.end_slab(k, s);
   }

@@ -101,6 +101,8 @@ struct IterArgs {
   double* kc;            // n: (G - I) c of the last iteration
   int refresh;           // 1: U_u, U_rho from u, rho by two passes over Z at launch start
   int dots_every;        // >= 1: pass B takes the column dots Z~^T u every dots_every iterations
+  int stall_first_barrier;   // test hook: 1 makes the launch's first grid barrier wait for an
+                             // arrival that never comes, so it runs out after timeout_ns
   // d-space state, NB*TB long (padding rows stay 0)
   double* u;
   double* rho;

@@ -215,6 +215,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gdwd", choices=["gdwd", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the HBM-streaming and served blocks of the default line (profiling runs)")
+    ap.add_argument("--extras-serve-seconds", type=float, default=1.0)
     ap.add_argument("--d", type=int, default=20000, help="feature count (profiling of other sizes only)")
     ap.add_argument("--n", type=int, default=1000, help="sample count (profiling of other sizes only)")
     ap.add_argument("--workload", default="spiked_fp32",
@@ -356,6 +359,19 @@ def main():
         line["detail"]["err_vs_oracle"] = {
             "rel_obj": abs(res[0]["primal_obj"] - ref["primal"]) / abs(ref["primal"]),
             "rel_w": float(np.linalg.norm(w[:, 0] - ref["w"]) / np.linalg.norm(ref["w"]))}
+    if rank == 0 and ws == 1 and not args.no_extras:
+        # the two other halves of the metric: Z streamed from HBM (the C-grid
+        # instance, 200 MB of BF16) and a short served stream (Poisson arrivals,
+        # latency from arrival)
+        import bench_workloads
+        line["detail"]["hbm_stream"] = bench_workloads.hbm_stream(gdwd, synth)
+        sargs = argparse.Namespace(**vars(args))
+        sargs.serve_seconds, sargs.kern = args.extras_serve_seconds, 1
+        sv = bench_workloads.served(sargs, gdwd, synth)
+        line["detail"]["served"] = {k: sv[k] for k in ("value", "unit", "latency_ms_p50", "latency_ms_p99",
+                                                      "server_latency_ms_p50", "server_latency_ms_p99", "requests",
+                                                      "arrived", "converged", "wall_s", "offered_rate", "mean_iters",
+                                                      "config")}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

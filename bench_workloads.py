@@ -253,6 +253,41 @@ def largest_fp8(args, gdwd, synth):
             "converged": int(sum(r["status"] == 0 for r in res)), "certified_gap_C_ends": gaps}
 
 
+def hbm_stream(gdwd, synth, C=1.0, reps=2):
+    """The Z-streaming iteration where Z does stream from HBM: the C-grid instance
+    (d=50000, n=2000, Gaussian two-class with mean shift 1.5, BF16 storage: 200 MB,
+    above the 129 MB L2), one value of C per solve.  Returns the iteration kernel's
+    algorithmic bytes per iteration over its CUDA-event time against the measured
+    HBM copy bandwidth, with the per-phase split of the last solve."""
+    torch = _torch()
+    d, n = 50000, 2000
+    inst = synth.gaussian(seed=3001, d=d, n=n, shift=1.5, q=1.0, C=C)
+    Zd = _device_colmajor(inst.Z)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    with gdwd.Solver(Zd, inst.y, 1.0, C, store="bf16", tol=1e-6) as s:
+        s.solve()                                             # warm-up
+        runs = []
+        for k in range(reps):
+            flush.fill_(float(k))
+            torch.cuda.synchronize()
+            res, _, _ = s.solve()
+            runs.append(res[0])
+        info = s.info()
+        ph = s.phase_times()
+    iters = float(np.mean([r["iters"] for r in runs]))
+    t_ms = float(np.mean([r["t_solve_ms"] for r in runs]))
+    slabs = info["slabs"]
+    bpi = d * n * 2 + 16 * n * n + 64 * d + 160 * n + 8 * n * slabs / 4
+    roof = _roofline("iterate_kernel<__nv_bfloat16>", bpi, iters, t_ms,
+                     "d*n*2 + 16n^2 + 64d + 160n + 8n*slabs/4 (Z once, G^-1 twice, vectors, column dots every 4th)")
+    del Zd
+    torch.cuda.empty_cache()
+    return {"workload": f"cgrid_bf16 instance d={d} n={n} mu-shift 1.5, C={C}, BF16 Z 200 MB (> L2)",
+            "iterations": iters, "solve_ms": t_ms, "us_per_iteration": 1e3 * t_ms / iters,
+            "status": [r["status"] for r in runs], "kkt": [r["kkt"] for r in runs], "grid": info["grid"],
+            "roofline": roof, "phase_us_per_iter": {k: v / 1e3 / runs[-1]["iters"] for k, v in ph.items() if v > 0}}
+
+
 def _timed_steps(gdwd, Zd, inst, steps, **kw):
     """Full create + solve + free steps (one warm-up): mean seconds, last result."""
     torch = _torch()

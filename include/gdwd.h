@@ -283,10 +283,14 @@ gdwd_status gdwd_get_info(const gdwd_handle* h, gdwd_info* info);
  * solve, Steps 2-3), 4 (B: the pass over Z); ns[10] = the KKT / sigma phase;
  * sub-phases split out of those: ns[11] N2 right-hand side load, ns[12] N2
  * rows of G^{-1} and p^T rhs (beta), ns[13] reduction of the per-CTA partial
- * sums, ns[14] N1 right-hand side load, ns[15] N1 rows of G^{-1} and p^T rhs
- * (the joint C-grid kernel fills ns[2..10] and ns[13]; the kernelized
+ * sums, ns[14] N1 right-hand side load, ns[15] N1 rows of G^{-1} and p^T rhs,
+ * ns[16] B prologue (coefficients, deferred d-space update), ns[17] B stream
+ * over Z, ns[18] the Step 1b prox of the CTA's first row, ns[19] unused.  When
+ * the first solve of an iteration is fused into the previous pass over Z, ns[2]
+ * holds its combination and ns[3], ns[14], ns[15] stay empty for that
+ * iteration (the joint C-grid kernel fills ns[2..10] and ns[13]; the kernelized
  * iteration has no pass over Z and reports its K product in ns[8], ns[9] and
- * the start-up product of a stored iterate in ns[0], ns[1]).  count (<= 16)
+ * the start-up product of a stored iterate in ns[0], ns[1]).  count (<= 20)
  * entries are written to ns (host).  Diagnostics only; the paper has no
  * counterpart.  Errors: EINVAL.
  */

@@ -53,12 +53,13 @@ struct gdwd_handle {
   double t_stage_ms[3] = {0.0, 0.0, 0.0};   // ingest, Gram, factor
   size_t bytes = 0;
   std::vector<void*> allocs;
+  int alloc_calls = 0;   // device allocations requested so far (fault-injection hook)
   // device arrays
   void* Z = nullptr;
   double *sc = nullptr, *y = nullptr, *e = nullptr, *omega = nullptr, *wt = nullptr, *p = nullptr, *G = nullptr;
   float2 *P = nullptr, *pdf = nullptr;
   double *r = nullptr, *xi = nullptr, *alpha = nullptr, *b = nullptr;
-  float2 *rhsA = nullptr, *rhsB = nullptr;
+  float2 *rhsA = nullptr, *rhsB = nullptr, *vrhs = nullptr;
   double *Uu = nullptr, *Ur = nullptr, *kc = nullptr;   // n-space images of u, rho; (G - I) c
   void *cq = nullptr, *aq = nullptr, *partial = nullptr;
   double *u = nullptr, *rho = nullptr, *g = nullptr, *scal = nullptr, *wtmp = nullptr;
@@ -117,8 +118,8 @@ static gdwd_status cuda_fail(gdwd_handle* h, cudaError_t e, const char* where) {
 
 // Fault-injection hooks for tests, read from the environment (no effect while
 // the variables are unset):
-//   GDWD_INJECT_ALLOC_FAIL=k  the k-th device allocation of a handle fails as if
-//                             the device were out of memory;
+//   GDWD_INJECT_ALLOC_FAIL=k  the k-th device allocation of a handle (kept or
+//                             temporary) fails as if the device were out of memory;
 //   GDWD_INJECT_STALL=1       every launch of the Z-streaming iteration kernel
 //                             waits at its first grid barrier for an arrival that
 //                             never comes, so its bounded wait runs out.
@@ -127,13 +128,19 @@ static long env_long(const char* name) {
   return v ? std::strtol(v, nullptr, 10) : 0;
 }
 
+// Every device allocation of a handle (kept or temporary) goes through here.
+static cudaError_t dev_alloc(gdwd_handle* h, void** p, size_t bytes) {
+  ++h->alloc_calls;
+  const long inject = env_long("GDWD_INJECT_ALLOC_FAIL");
+  if (inject > 0 && (long)h->alloc_calls == inject) return cudaErrorMemoryAllocation;
+  return cudaMallocAsync(p, bytes, h->stream);
+}
+
 template <typename T>
 static cudaError_t halloc(gdwd_handle* h, T** p, size_t count) {
-  const long inject = env_long("GDWD_INJECT_ALLOC_FAIL");
-  if (inject > 0 && (long)h->allocs.size() + 1 == inject) return cudaErrorMemoryAllocation;
   void* q = nullptr;
   const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
-  cudaError_t e = cudaMallocAsync(&q, bytes, h->stream);
+  cudaError_t e = dev_alloc(h, &q, bytes);
   if (e != cudaSuccess) return e;
   h->allocs.push_back(q);
   h->bytes += bytes;
@@ -219,7 +226,7 @@ static gdwd_status create_direct(gdwd_handle* h, const void* Z, int zdt, int64_t
   const int es = h->L.esize;
   const int zes = esize_of(zdt);
   void* zbuf = nullptr;
-  CK(cudaMallocAsync(&zbuf, (size_t)npad * d * es, h->stream), "cudaMalloc(Z)");
+  CK(dev_alloc(h, (void**)&zbuf, (size_t)npad * d * es), "cudaMalloc(Z)");
   h->allocs.push_back(zbuf);
   h->bytes += (size_t)npad * d * es;
   h->Z = zbuf;
@@ -271,7 +278,7 @@ static gdwd_status create_direct(gdwd_handle* h, const void* Z, int zdt, int64_t
   void* staging = nullptr;
   int64_t ld = ldz;
   if (!z_on_device) {
-    CK(cudaMallocAsync(&staging, (size_t)d * n * zes, h->stream), "cudaMalloc(staging)");
+    CK(dev_alloc(h, (void**)&staging, (size_t)d * n * zes), "cudaMalloc(staging)");
     cudaError_t ec = cudaMemcpy2DAsync(staging, (size_t)d * zes, Z, (size_t)ldz * zes, (size_t)d * zes, (size_t)n,
                                        cudaMemcpyHostToDevice, h->stream);
     if (ec != cudaSuccess) {
@@ -282,11 +289,11 @@ static gdwd_status create_direct(gdwd_handle* h, const void* Z, int zdt, int64_t
     ld = d;
   }
   void* zt = nullptr;
-  cudaError_t ei = cudaMallocAsync(&zt, (size_t)d * n * zes, h->stream);
+  cudaError_t ei = dev_alloc(h, (void**)&zt, (size_t)d * n * zes);
   if (ei == cudaSuccess) ei = run_transpose(zsrc, zdt, d, n, ld, zt, h->stream);
   const int nparts = 1024;
   double* part = nullptr;
-  if (ei == cudaSuccess) ei = cudaMallocAsync(&part, nparts * sizeof(double), h->stream);
+  if (ei == cudaSuccess) ei = dev_alloc(h, (void**)&part, nparts * sizeof(double));
   if (ei == cudaSuccess)
     ei = run_ingest(zt, zdt, n, h->L, h->Z, h->store, part, nparts, h->dscalars, h->err, h->sc, h->dscalars + 1,
                     h->amax, h->colscale, h->stream);
@@ -304,7 +311,7 @@ static gdwd_status create_direct(gdwd_handle* h, const void* Z, int zdt, int64_t
   const bool tc = h->opt.gram_path == 0 && gram_tc_supported(h->store, h->L);
   const int ks = tc ? gram_tc_ksplit(h->L, h->sms) : gram_ksplit(h->L, h->sms);
   double* Kpart = nullptr;
-  CK(cudaMallocAsync(&Kpart, (size_t)ks * d * d * sizeof(double), h->stream), "cudaMalloc(Kpart)");
+  CK(dev_alloc(h, (void**)&Kpart, (size_t)ks * d * d * sizeof(double)), "cudaMalloc(Kpart)");
   cudaError_t eg = run_gram(h->store, h->L, ks, Kpart, h->sc, h->opt.mu, h->G, tc, h->err,
                             (uint64_t)(h->opt.timeout_s * 1e9), h->stream);
   if (eg == cudaSuccess) {
@@ -321,8 +328,8 @@ static gdwd_status create_direct(gdwd_handle* h, const void* Z, int zdt, int64_t
   // factor of G', p = G'^{-1} b^, s = b^T p
   CK(cudaEventRecord(ef0, h->stream), "cudaEventRecord");
   float2 *A = nullptr, *X = nullptr;
-  CK(cudaMallocAsync(&A, (size_t)d * d * sizeof(float2), h->stream), "cudaMalloc(A)");
-  cudaError_t ef = cudaMallocAsync(&X, (size_t)d * d * sizeof(float2), h->stream);
+  CK(dev_alloc(h, (void**)&A, (size_t)d * d * sizeof(float2)), "cudaMalloc(A)");
+  cudaError_t ef = dev_alloc(h, (void**)&X, (size_t)d * d * sizeof(float2));
   if (ef == cudaSuccess) ef = cudaMemsetAsync(h->bar, 0, sizeof(unsigned), h->stream);
   if (ef == cudaSuccess) {
     FactorArgs fa{h->G, A, X, h->P, h->ldP, h->bhat, h->p, h->pdf, h->dscalars + 2, d, h->grid, h->bar, h->err,
@@ -452,7 +459,7 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
     const int zes = esize_of(zdt);
     // persistent arrays
     void* zbuf = nullptr;
-    CK(cudaMallocAsync(&zbuf, (size_t)dpad * n * es, h->stream), "cudaMalloc(Z)");
+    CK(dev_alloc(h, (void**)&zbuf, (size_t)dpad * n * es), "cudaMalloc(Z)");
     h->allocs.push_back(zbuf);
     h->bytes += (size_t)dpad * n * es;
     h->Z = zbuf;
@@ -479,6 +486,8 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
     CK(halloc(h, &h->Ur, n), "alloc");
     CK(halloc(h, &h->kc, n), "alloc");
     CK(halloc(h, &h->rhsB, h->ldP), "alloc");
+    // right-hand sides of the fused first solve, [3][ldP], padding zero
+    CK(halloc(h, &h->vrhs, (size_t)3 * h->ldP), "alloc");
     const size_t ct = h->store == GDWD_F64 ? 8 : 4;
     CK(halloc(h, (uint8_t**)&h->cq, (n * ct + 15) / 16 * 16), "alloc");   // copied in 16-byte pieces
     CK(halloc(h, (uint8_t**)&h->aq, (n * ct + 15) / 16 * 16), "alloc");
@@ -513,7 +522,7 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
     void* staging = nullptr;
     int64_t ld = ldz;
     if (!z_on_device) {
-      CK(cudaMallocAsync(&staging, (size_t)d * n * zes, h->stream), "cudaMalloc(staging)");
+      CK(dev_alloc(h, (void**)&staging, (size_t)d * n * zes), "cudaMalloc(staging)");
       cudaError_t ec = cudaMemcpy2DAsync(staging, (size_t)d * zes, Z, (size_t)ldz * zes, (size_t)d * zes, (size_t)n,
                                          cudaMemcpyHostToDevice, h->stream);
       if (ec != cudaSuccess) {
@@ -526,7 +535,7 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
     const int nparts = 1024;
     double* part = nullptr;
     int* nonfinite = h->err;
-    CK(cudaMallocAsync(&part, nparts * sizeof(double), h->stream), "cudaMalloc");
+    CK(dev_alloc(h, (void**)&part, nparts * sizeof(double)), "cudaMalloc");
     cudaError_t ei = run_ingest(zsrc, zdt, ld, h->L, h->Z, h->store, part, nparts, h->dscalars, nonfinite, h->sc,
                                 h->dscalars + 1, h->amax, h->colscale, h->stream);
     int nf = 0;
@@ -542,7 +551,7 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
     const bool tc = h->opt.gram_path == 0 && gram_tc_supported(h->store, h->L);
     const int ks = tc ? gram_tc_ksplit(h->L, h->sms) : gram_ksplit(h->L, h->sms);
     double* Kpart = nullptr;
-    CK(cudaMallocAsync(&Kpart, (size_t)ks * n * n * sizeof(double), h->stream), "cudaMalloc(Kpart)");
+    CK(dev_alloc(h, (void**)&Kpart, (size_t)ks * n * n * sizeof(double)), "cudaMalloc(Kpart)");
     cudaError_t eg = run_gram(h->store, h->L, ks, Kpart, h->sc, h->opt.mu, h->G, tc, h->err,
                               (uint64_t)(h->opt.timeout_s * 1e9), h->stream);
     int gerr = 0;
@@ -555,8 +564,8 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
     // Cholesky, inverse, p, s
     CK(cudaEventRecord(ef0, h->stream), "cudaEventRecord");
     float2 *A = nullptr, *X = nullptr;
-    CK(cudaMallocAsync(&A, (size_t)n * n * sizeof(float2), h->stream), "cudaMalloc(A)");
-    cudaError_t ef = cudaMallocAsync(&X, (size_t)n * n * sizeof(float2), h->stream);
+    CK(dev_alloc(h, (void**)&A, (size_t)n * n * sizeof(float2)), "cudaMalloc(A)");
+    cudaError_t ef = dev_alloc(h, (void**)&X, (size_t)n * n * sizeof(float2));
     if (ef == cudaSuccess) ef = cudaMemsetAsync(h->bar, 0, sizeof(unsigned), h->stream);
     const int fgrid = h->grid;   // the handle's SM share (all SMs unless restricted by opt.grid)
     if (ef == cudaSuccess) {
@@ -650,6 +659,8 @@ static IterArgs<CT> make_args(gdwd_handle* h, double C, double sigma0, int refre
   a.refresh = refresh;
   a.dots_every = dots_every_of(h);
   a.stall_first_barrier = env_long("GDWD_INJECT_STALL") > 0 ? 1 : 0;
+  a.fuse = 1;
+  a.vrhs = h->vrhs;
   a.rhsB = h->rhsB;
   a.cq = (CT*)h->cq;
   a.aq = (CT*)h->aq;
@@ -1320,9 +1331,9 @@ extern "C" gdwd_status gdwd_suggest_C(gdwd_handle* h, double* C_out) {
     if (dneg) cudaFreeAsync(dneg, h->stream);
     if (dd) cudaFreeAsync(dd, h->stream);
   };
-  cudaError_t e = cudaMallocAsync(&dpos, np * sizeof(int), h->stream);
-  if (e == cudaSuccess) e = cudaMallocAsync(&dneg, nm * sizeof(int), h->stream);
-  if (e == cudaSuccess) e = cudaMallocAsync(&dd, total * sizeof(double), h->stream);
+  cudaError_t e = dev_alloc(h, (void**)&dpos, np * sizeof(int));
+  if (e == cudaSuccess) e = dev_alloc(h, (void**)&dneg, nm * sizeof(int));
+  if (e == cudaSuccess) e = dev_alloc(h, (void**)&dd, total * sizeof(double));
   if (e == cudaSuccess) e = cudaMemcpyAsync(dpos, pos.data(), np * sizeof(int), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dneg, neg.data(), nm * sizeof(int), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) {

@@ -82,25 +82,49 @@ __device__ __forceinline__ df df_warp_sum(df a) {
   return a;
 }
 
-// 1/b, a/b and sqrt(x) for FP64 operands whose magnitudes lie inside the FP32
-// range (b != 0, x >= 0): an FP32 seed and one FP64 Newton correction
-// (relative error ~1e-14).  FP64 division and square root are long dependent
-// chains on this part; these cost two or three FP64 operations.  Not for the
-// prox, whose stopping test needs exact division.
+// Approximate FP32 reciprocal and reciprocal square root of the special-function
+// unit (about 1 ulp; denormals flushed): seeds for the FP64 corrections below.
+// The correctly rounded forms (__frcp_rn, __fsqrt_rn, IEEE division) are long
+// instruction sequences on this part (~170 cycles against ~40).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+// sqrt(x) of a non-negative FP32 value to about 2 ulp (0 for x <= 0)
+__device__ __forceinline__ float fsqrt_approx(float x) { return x > 0.f ? x * rsqrt_approx(x) : 0.f; }
+
+// max(x, 0) and min(x, 0) by a compare and a select (the FP64 min / max
+// instructions are slower than both on this part); NaN gives 0, as fmax does.
+__device__ __forceinline__ double dmax0(double x) { return x > 0.0 ? x : 0.0; }
+__device__ __forceinline__ double dmin0(double x) { return x < 0.0 ? x : 0.0; }
+
+// 1/b, a/b and sqrt(x) for FP64 operands whose magnitudes lie inside the normal
+// FP32 range (b != 0, x >= 0): an FP32 seed from the special-function unit and
+// one FP64 Newton correction, which squares the seed's ~2^-23 relative error to
+// ~2^-46 (about 1.5e-14).  A dependent FP64 operation takes 64 cycles on this
+// part, an FP64 division ~1400 and an FP64 square root ~870; these take three
+// or four FP64 operations.
 __device__ __forceinline__ double rcp_nr(double b) {
-  const double r = (double)__frcp_rn((float)b);
+  const double r = (double)rcp_approx((float)b);
   return fma(r, fma(-b, r, 1.0), r);
 }
 __device__ __forceinline__ double div_nr(double a, double b) {
-  const double r = (double)__frcp_rn((float)b);
+  const double r = (double)rcp_approx((float)b);
   const double q = a * r;
   return fma(r, fma(-b, q, a), q);
 }
 __device__ __forceinline__ double sqrt_nr(double x) {
   if (!(x > 0.0)) return 0.0;
-  const float sf = __fsqrt_rn((float)x);
-  const double s = (double)sf;
-  return fma((double)(0.5f / sf), fma(-s, s, x), s);
+  const double r = (double)rsqrt_approx((float)x);   // ~1 / sqrt(x)
+  const double s = x * r;
+  const double h = 0.5 * r;
+  return fma(h, fma(-s, s, x), s);
 }
 
 __device__ __forceinline__ double warp_sum(double a) {

@@ -475,7 +475,8 @@ __global__ void __launch_bounds__(kThreads) dir_s_kernel(DirArgs a) {
   if (c->done) return;
   __shared__ double s_tot[S_COUNT];
   __shared__ double s_pd[4];
-  __shared__ float s_etaf[10];
+  __shared__ float s_etaf[11];
+  __shared__ int s_ictl[2];
   __shared__ double s_ctl[8];
   __shared__ double s_part[kWarps * 6];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -513,9 +514,9 @@ __global__ void __launch_bounds__(kThreads) dir_s_kernel(DirArgs a) {
   }
   __syncthreads();
   const SPhaseArgs sq{a.C, a.kappa, a.R, a.mu, a.tau, sqmu, a.tol, sqrt(a.tol), (float)(1.0 / (1.0 + a.C)),
-                      a.stop_rule};
+                      a.stop_rule, float_at_most(a.tol)};
   const int it = c->it;
-  s_phase(s_tot, sq, sig, gs, it, c->beta, GDWD_EMAXITER, true, c, s_pd, s_etaf, s_ctl);
+  s_phase(s_tot, sq, sig, gs, it, c->beta, GDWD_EMAXITER, true, c, s_pd, s_etaf, s_ctl, s_ictl);
   const double th = s_ctl[0];
   const double rcoef = a.tau * sig * sqmu * (1.0 - th);
   for (int64_t j = threadIdx.x; j < a.d; j += kThreads) {
@@ -528,8 +529,8 @@ __global__ void __launch_bounds__(kThreads) dir_s_kernel(DirArgs a) {
     c->sigma = s_ctl[1];
     c->theta = th;
     c->it = it + 1;
-    c->status = (int)s_ctl[3];
-    if (s_ctl[2] != 0.0) c->done = 1;
+    c->status = s_ictl[1];
+    if (s_ictl[0] != 0) c->done = 1;
     else if (it + 1 >= a.max_iter) {
       c->done = 1;
       c->status = GDWD_EMAXITER;

@@ -108,11 +108,98 @@ __device__ __forceinline__ void store_ct(CT* p, double v) { *p = (CT)v; }
 // whole launch: the iterate's row state and the per-row constants, one array
 // of rpc doubles each, ahead of the phase-local region.  The row phases then
 // touch global memory only for what other CTAs read.
-enum RowSlot { RS_R, RS_XI, RS_AL, RS_B, RS_KC, RS_UU, RS_UR, RS_Y, RS_P, RS_CE, RS_E, RS_OM, RS_WT, RS_SC, RS_COUNT };
+enum RowSlot { RS_R, RS_XI, RS_AL, RS_B, RS_KC, RS_UU, RS_UR, RS_Y, RS_P, RS_CE, RS_E, RS_OM, RS_WT, RS_SC,
+               RS_X1, RS_X2, RS_X3, RS_COUNT };
 
 __host__ __device__ inline size_t row_state_bytes(int64_t rpc) {
   return ((size_t)RS_COUNT * (size_t)rpc * sizeof(double) + 127) & ~(size_t)127;
 }
+
+// ---------------------------------------------------------------------------
+// Step 1a of the next iteration without a solve of its own.  Its right-hand
+// side rhs1 = b+ + xi - r - alpha / sigma' is linear in three n-vectors known at
+// the end of phase N2,
+//     V1 = U_g,  V2 = (1 - tau) U_rho / sqrt(mu) - alpha,  V3 = xi - r,
+//     rhs1 = a1 V1 + V2 / sigma' + V3,  a1 = theta - tau (sigma / sigma') (1 - theta),
+// whose coefficients wait only for phase S (theta, sigma').  So
+// x-bar = G^{-1} rhs1 = a1 X1 + X2 / sigma' + X3 with X_k = G^{-1} V_k, and
+// p^T rhs1 likewise from p^T V_k.  The three products of this CTA's rows (and
+// of the row p^T) are taken during the pass over Z: the rows of G^{-1}, the row
+// p^T and V1..V3 (all double-float, ldP long) come through the ring as extra
+// chunks of W columns each, and every warp multiplies one or two of the rows.
+// ---------------------------------------------------------------------------
+constexpr int kFuseRowsPerWarp = 2;
+
+struct FusedGemv {
+  const float2* P;
+  int ldP;
+  const float2* pdf;
+  const float2* vrhs;     // [3][ldP]
+  int64_t r0;
+  int nrows;
+  int W;                  // columns per extra chunk (even)
+  int nx;                 // extra chunks: ceil(ldP / W)
+  double* s_acc;          // shared, (nrows + 1) x 3 sums of the slices
+  __device__ int count() const { return nx; }
+  __device__ void issue(int e, uint8_t* dst, uint64_t* bar) const {
+    // V1..V3 were written by other CTAs' generic stores before the grid barrier;
+    // order them before this thread's bulk (async-proxy) reads
+    asm volatile("fence.proxy.async;" ::: "memory");
+    const int j0 = e * W;
+    const int w = min(W, ldP - j0);
+    const uint32_t bytes = (uint32_t)w * (uint32_t)sizeof(float2);
+    mbar_expect_tx(bar, bytes * (uint32_t)(nrows + 4));
+    const size_t slice = (size_t)W * sizeof(float2);
+    for (int t = 0; t < nrows; ++t) bulk_g2s(dst + t * slice, P + (size_t)(r0 + t) * ldP + j0, bytes, bar);
+    bulk_g2s(dst + nrows * slice, pdf + j0, bytes, bar);
+    for (int k = 0; k < 3; ++k) bulk_g2s(dst + (nrows + 1 + k) * slice, vrhs + (size_t)k * ldP + j0, bytes, bar);
+  }
+  __device__ void consume(int e, const uint8_t* buf) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int w = min(W, ldP - e * W);
+    const int npair = w / 2;
+    const size_t slice = (size_t)W * sizeof(float2);
+    const float4* V1 = reinterpret_cast<const float4*>(buf + (nrows + 1) * slice);
+    const float4* V2 = reinterpret_cast<const float4*>(buf + (nrows + 2) * slice);
+    const float4* V3 = reinterpret_cast<const float4*>(buf + (nrows + 3) * slice);
+#pragma unroll
+    for (int rr = 0; rr < kFuseRowsPerWarp; ++rr) {
+      const int t = warp + rr * kWarps;
+      if (t > nrows) break;
+      const float4* Pr = reinterpret_cast<const float4*>(buf + t * slice);
+      df a1{0.f, 0.f}, a2{0.f, 0.f}, a3{0.f, 0.f}, b1{0.f, 0.f}, b2{0.f, 0.f}, b3{0.f, 0.f};
+      for (int j = lane; j < npair; j += 32) {
+        const float4 pv = Pr[j], x1 = V1[j], x2 = V2[j], x3 = V3[j];
+        const df p0{pv.x, pv.y}, p1{pv.z, pv.w};
+        df_fma(a1, p0, df{x1.x, x1.y});
+        df_fma(a2, p0, df{x2.x, x2.y});
+        df_fma(a3, p0, df{x3.x, x3.y});
+        df_fma(b1, p1, df{x1.z, x1.w});
+        df_fma(b2, p1, df{x2.z, x2.w});
+        df_fma(b3, p1, df{x3.z, x3.w});
+      }
+      df_add(a1, b1);
+      df_add(a2, b2);
+      df_add(a3, b3);
+      a1 = df_warp_sum(a1);
+      a2 = df_warp_sum(a2);
+      a3 = df_warp_sum(a3);
+      if (lane == 0) {
+        double* acc = s_acc + t * 3;
+        const double v1 = df_to_double(a1), v2 = df_to_double(a2), v3 = df_to_double(a3);
+        if (e == 0) {
+          acc[0] = v1;
+          acc[1] = v2;
+          acc[2] = v3;
+        } else {
+          acc[0] += v1;
+          acc[1] += v2;
+          acc[2] += v3;
+        }
+      }
+    }
+  }
+};
 
 // ---------------------------------------------------------------------------
 // the persistent kernel
@@ -128,7 +215,8 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
   __shared__ double s_tot[S_COUNT];
   __shared__ double s_ctl[8];
   __shared__ double s_pd[4];     // pobj, dobj, theta, ||w||
-  __shared__ float s_etaf[10];   // gap and the nine residuals
+  __shared__ float s_etaf[11];   // gap, the nine residuals, kkt
+  __shared__ int s_ictl[2];      // done, status
 
   const Layout& L = a.L;
   const int cta = blockIdx.x, grid = a.grid;
@@ -146,13 +234,14 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
   __shared__ float s_xh[kMaxRowsPerCta + 1], s_xl[kMaxRowsPerCta + 1];   // + the p^T rhs row
   __shared__ double s_ug[kMaxRowsPerCta];                                 // Z~^T u from the column dots
   __shared__ float2 s_rb[kMaxRowsPerCta];                                 // rhs2 of the CTA's rows
+  __shared__ double s_gx[kFuseRowsPerWarp * kWarps * 3];                  // fused products: rows, then p^T
   const int qcase = q_case(a.q);
-  const double sqmu = sqrt(a.mu), inv_mu = 1.0 / a.mu;
+  const double sqmu = sqrt(a.mu), inv_mu = 1.0 / a.mu, inv_sqmu = 1.0 / sqmu;
   const double den = 1.0 + a.C;
   const double inv_q = 1.0 / a.q;
   const float inv_den = (float)(1.0 / den);
   const double sqrt_tol = sqrt(a.tol);
-  const SPhaseArgs sq{a.C, a.kappa, a.R, a.mu, a.tau, sqmu, a.tol, sqrt_tol, inv_den, a.stop_rule};
+  const SPhaseArgs sq{a.C, a.kappa, a.R, a.mu, a.tau, sqmu, a.tol, sqrt_tol, inv_den, a.stop_rule, float_at_most(a.tol)};
 
   Ring rg;
   rg.buf = smem;
@@ -165,6 +254,12 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
   uint8_t* uni = smem + (size_t)stages * stage_bytes + row_state_bytes(rpc);     // phase-local region
   if (threadIdx.x == 0) s_abort = 0;
   ring_init(rg);
+  // the fused first solve needs every row of the CTA (and p^T) on at most
+  // kFuseRowsPerWarp rows per warp, and a stage that holds slices of all of
+  // them and of the three right-hand sides
+  const int fuse_w = (int)((size_t)stage_bytes / ((size_t)(rpc + 4) * sizeof(float2))) & ~1;
+  const bool can_fuse = a.fuse && a.vrhs && rpc + 1 <= kFuseRowsPerWarp * kWarps && fuse_w >= 16;
+  FusedGemv fx{a.P, a.ldP, a.pdf, a.vrhs, r0, nrows, fuse_w, can_fuse ? (a.ldP + fuse_w - 1) / fuse_w : 0, s_gx};
 
   unsigned gen = 0;
   // per-phase timing by CTA 0, thread 0 (globaltimer, a few instructions per phase)
@@ -265,14 +360,21 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
 
   int it = it0;
   bool dots_prev = false;   // the last pass B took the column dots Z~^T u
+  bool fused = false;       // the last pass B made the three products of the fused first solve
   for (; it < a.max_iter; ++it) {
     const double inv_sig = rcp_nr(sig);
     const double gs_it = rcp_nr(sig * sqmu);   // 1 / (sigma sqrt(mu)) of this iteration
+    // this iteration's pass B takes the column dots Z~^T u every dots_every-th
+    // iteration; otherwise it makes the products of the next fused first solve
+    const bool dots_now = ((it - it0) % a.dots_every) == a.dots_every - 1;
+    const bool fuse_next = can_fuse && !dots_now;
     // ---------------- phase R (this CTA's rows): U_g = Z~^T g of the last iteration
     // from the pass-B column dots Z~^T u and (G - I) c; the deferred update
     // U_u = theta U_g, U_rho <- (1 - tau) U_rho - tau sigma' sqrt(mu) (1 - theta) U_g;
     // b = U_u + U_rho / (sigma sqrt(mu)); rhs1 = b + xi - r - alpha / sigma
     ring_prefetch(L, rg, cta, grid);   // this iteration's first Z chunks arrive during R, N1, N2
+    double betabar;
+    double xb_reg = 0.0;   // fused x-bar of this thread's row (at most one row per thread)
     {
       const double rcoef = a.tau * sig_prev * sqmu * (1.0 - theta);
       if (pending && dots_prev) {
@@ -283,6 +385,9 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
         }
         __syncthreads();
       }
+      // fused: x-bar = a1 X1 + X2 / sigma + X3 from the last pass's products
+      const double a1 = theta - a.tau * (sig_prev * inv_sig) * (1.0 - theta);
+      if (fused) betabar = -(a1 * s_gx[nrows * 3] + s_gx[nrows * 3 + 1] * inv_sig + s_gx[nrows * 3 + 2]) * a.inv_s;
       // the per-row work on consecutive threads (few warp instructions of FP64)
       for (int t = threadIdx.x; t < nrows; t += kThreads) {
         const int64_t i = r0 + t;
@@ -296,20 +401,21 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
         }
         const double bi = uu + ur * gs_it;
         RS(RS_B, t) = bi;
-        const double v = RS(RS_XI, t) - RS(RS_R, t) - RS(RS_AL, t) * inv_sig;
-        const df r1 = df_from(bi + v);
-        a.rhsA[i] = make_float2(r1.hi, r1.lo);
+        if (fused) {
+          xb_reg = a1 * s_gx[t * 3] + s_gx[t * 3 + 1] * inv_sig + s_gx[t * 3 + 2];
+        } else {
+          const double v = RS(RS_XI, t) - RS(RS_R, t) - RS(RS_AL, t) * inv_sig;
+          const df r1 = df_from(bi + v);
+          a.rhsA[i] = make_float2(r1.hi, r1.lo);
+        }
       }
     }
-    GDWD_BARRIER(2);
-
-    // ---------------- phase N1: x-bar, beta-bar, Step 1b prox, rhs2
-    {
+    if (!fused) {
+      GDWD_BARRIER(2);
+      // ---------------- phase N1 (first solve): x-bar = G^{-1} rhs1, beta-bar
       GDWD_MARK(14);
       // G^{-1} rows of this CTA and, as one more row, p^T rhs1 for beta-bar (one
-      // warp per row; rhs1 is read from L2, and from L1 after the SM's first warp);
-      // then the per-row FP64 work with one row per lane so each FP64 instruction
-      // serves up to 32 rows
+      // warp per row; rhs1 is read from L2, and from L1 after the SM's first warp)
       for (int t = warp; t <= nrows; t += kWarps) {
         const df x = row_dot(t < nrows ? a.P + (size_t)(r0 + t) * a.ldP : a.pdf, a.rhsA, npair);
         if (lane == 0) {
@@ -318,13 +424,20 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
         }
       }
       __syncthreads();
-      const double betabar = -((double)s_xh[nrows] + (double)s_xl[nrows]) * a.inv_s;
+      betabar = -((double)s_xh[nrows] + (double)s_xl[nrows]) * a.inv_s;
       GDWD_MARK(15);
+    }
+    // ---------------- phase N1 (rows): Step 1b prox, rhs2.  The per-row FP64 work
+    // has one row per lane so each FP64 instruction serves up to 32 rows
+    {
+      if (fused) GDWD_MARK(2);
       for (int t = threadIdx.x; t < nrows; t += kThreads) {
         const int64_t i = r0 + t;
-        const double cbar = ((double)s_xh[t] + (double)s_xl[t]) + betabar * RS(RS_P, t);
+        const double xb = fused ? xb_reg : (double)s_xh[t] + (double)s_xl[t];
+        const double cbar = xb + betabar * RS(RS_P, t);
         const double ri = RS(RS_R, t);
         const double rn = prox_root(cbar + ri, RS(RS_OM, t) * inv_sig, a.q, qcase, ri);
+        GDWD_MARK(18);
         RS(RS_R, t) = rn;
         const double v = RS(RS_XI, t) - rn - RS(RS_AL, t) * inv_sig;
         const df r2 = df_from(RS(RS_B, t) + v);
@@ -358,7 +471,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
           const double ri = RS(RS_R, t), al = RS(RS_AL, t), yi = RS(RS_Y, t), ce = RS(RS_CE, t);
           const double v = RS(RS_XI, t) - ri - al * inv_sig;
           const double zw = c - v - yi * beta;                                     // Z~^T w
-          const double xin = fmax(0.0, ri - zw - yi * beta + (al - ce) * inv_sig);  // Step 2
+          const double xin = dmax0(ri - zw - yi * beta + (al - ce) * inv_sig);  // Step 2
           const double res = zw + yi * beta + xin - ri;
           const double an = al - a.tau * sig * res;                                // Step 3
           RS(RS_XI, t) = xin;
@@ -368,7 +481,17 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
           store_ct(a.aq + i, sci * an);
           const float2 rb = s_rb[t];
           const double rh2 = (double)rb.x + (double)rb.y;
-          RS(RS_KC, t) = rh2 - xv + beta * (yi - pi);
+          const double kcn = rh2 - xv + beta * (yi - pi);
+          RS(RS_KC, t) = kcn;
+          if (fuse_next) {
+            // right-hand sides of the next fused first solve: U_g, (1 - tau) U_rho / sqrt(mu) - alpha, xi - r
+            const df v1 = df_from(RS(RS_UU, t) - kcn);
+            const df v2 = df_from((1.0 - a.tau) * inv_sqmu * RS(RS_UR, t) - an);
+            const df v3 = df_from(xin - ri);
+            a.vrhs[i] = make_float2(v1.hi, v1.lo);
+            a.vrhs[a.ldP + i] = make_float2(v2.hi, v2.lo);
+            a.vrhs[2 * (size_t)a.ldP + i] = make_float2(v3.hi, v3.lo);
+          }
           const double rq1 = pow_q1(ri, a.q, qcase);
           const double irq1 = rcp_nr(rq1);
           const double om = RS(RS_OM, t);
@@ -377,7 +500,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
           s_xica = fma(xin, ce - an, s_xica);
           const double dv = an - om * irq1;
           s_ams2 = fma(dv, dv, s_ams2);
-          const double mn = fmin(0.0, an), mx = fmax(0.0, an - ce);
+          const double mn = dmin0(an), mx = dmax0(an - ce);
           s_amin2 = fma(mn, mn, s_amin2);
           s_amax2 = fma(mx, mx, s_amax2);
           s_pr += om * inv_q * ri * irq1;           // wt^q r^-q
@@ -429,6 +552,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
         }
       }
       __syncthreads();
+      GDWD_MARK(16);
       IterEpi epi{a.g, a.u, a.rho, inv_mu, sqmu * (1.0 - a.tau)};
       PassB<T, IterEpi> pb;
       pb.cv = cv;
@@ -446,14 +570,19 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
       }
       // the column dots Z~^T u run on every dots_every-th iteration; in between
       // U_u follows its recurrence
-      dots_prev = ((it - it0) % a.dots_every) == a.dots_every - 1;
+      dots_prev = dots_now;
       if (dots_prev) {
         PassA2<T> pa{up, a.partial, TB, NB, Q};
         PassBA<T, IterEpi> pba{&pb, &pa};
         if (!stream_slabs<T>(L, rg, cta, grid, a.err, a.timeout_ns, &s_abort, pba)) return;
+      } else if (fuse_next) {
+        // the products of the next iteration's fused first solve ride on the ring
+        if (!stream_slabs<T>(L, rg, cta, grid, a.err, a.timeout_ns, &s_abort, pb, &fx)) return;
       } else {
         if (!stream_slabs<T>(L, rg, cta, grid, a.err, a.timeout_ns, &s_abort, pb)) return;
       }
+      fused = fuse_next;
+      GDWD_MARK(17);
       // the six d-space sums of every thread, one warp per sum, through the
       // phase-local region (free once the pass is over)
       const double vals[6] = {epi.sg2, epi.sgr, epi.sr2, epi.sa2, epi.sag, epi.sta2};
@@ -467,14 +596,14 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
     grid_totals(a.scal, grid, S_COUNT - 1, s_tot);
     __syncthreads();
     GDWD_MARK(13);
-    s_phase(s_tot, sq, sig, gs_it, it, beta, status, cta == 0, a.ctrl, s_pd, s_etaf, s_ctl);
+    s_phase(s_tot, sq, sig, gs_it, it, beta, status, false, a.ctrl, s_pd, s_etaf, s_ctl, s_ictl);
     GDWD_MARK(10);
     sig_prev = sig;
     theta = s_ctl[0];
     sig = s_ctl[1];
     pending = 1;
-    const bool done = s_ctl[2] != 0.0;
-    status = (int)s_ctl[3];
+    const bool done = s_ictl[0] != 0;
+    status = s_ictl[1];
     if (done) {
       ++it;
       break;
@@ -495,6 +624,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
   }
   if (cta == 0 && threadIdx.x == 0) {
     Ctrl* c = a.ctrl;
+    if (it > it0) s_report(c, beta, s_pd, s_etaf);   // the residuals of the last iteration
     c->sigma = sig;
     c->sigma_prev = sig_prev;
     c->theta = theta;

@@ -122,7 +122,8 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kern_kernel(KernArgs a) {
   __shared__ double s_tot[S_COUNT];
   __shared__ double s_ctl[8];
   __shared__ double s_pd[4];     // pobj, dobj, theta, ||w||
-  __shared__ float s_etaf[10];   // gap and the nine residuals
+  __shared__ float s_etaf[11];   // gap, the nine residuals, kkt
+  __shared__ int s_ictl[2];      // done, status
   __shared__ double s_rows[9 * kMaxRowsPerCta];    // per-row partial sums
   __shared__ double s_x[kMaxRowsPerCta + 1];      // GEMV results of the CTA's rows (+ the p^T rhs row)
   __shared__ double s_k[3][kMaxRowsPerCta];
@@ -142,7 +143,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kern_kernel(KernArgs a) {
   const double inv_q = 1.0 / a.q;
   const float inv_den = (float)(1.0 / den);
   const double sqrt_tol = sqrt(a.tol);
-  const SPhaseArgs sq{a.C, a.kappa, a.R, a.mu, a.tau, sqmu, a.tol, sqrt_tol, inv_den, a.stop_rule};
+  const SPhaseArgs sq{a.C, a.kappa, a.R, a.mu, a.tau, sqmu, a.tol, sqrt_tol, inv_den, a.stop_rule, float_at_most(a.tol)};
   const double ac = sqmu * (1.0 - a.tau);              // Z~ alpha + ac rho enters eta_D3
 
   // this thread's row
@@ -350,14 +351,14 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kern_kernel(KernArgs a) {
       s_tot[S_AG] = AG;
     }
     __syncthreads();
-    s_phase(s_tot, sq, sig, gs_it, it, beta, status, cta == 0, a.ctrl, s_pd, s_etaf, s_ctl);
+    s_phase(s_tot, sq, sig, gs_it, it, beta, status, false, a.ctrl, s_pd, s_etaf, s_ctl, s_ictl);
     GDWD_MARK(10);
     sig_prev = sig;
     theta = s_ctl[0];
     sig = s_ctl[1];
     pending = 1;
-    const bool done = s_ctl[2] != 0.0;
-    status = (int)s_ctl[3];
+    const bool done = s_ictl[0] != 0;
+    status = s_ictl[1];
     if (done) {
       ++it;
       break;
@@ -381,6 +382,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kern_kernel(KernArgs a) {
   }
   if (cta == 0 && threadIdx.x == 0) {
     Ctrl* c = a.ctrl;
+    if (it > it0) s_report(c, beta, s_pd, s_etaf);   // the residuals of the last iteration
     c->sigma = sig;
     c->sigma_prev = sig_prev;
     c->theta = theta;

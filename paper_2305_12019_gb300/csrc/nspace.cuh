@@ -13,12 +13,17 @@ namespace gdwd {
 // kept inside the bracket [max(a,0), max(a,0) + max(kq, 1)] (f < 0 at the left
 // end, f >= 0 at the right end); steps that leave it are bisected.
 //
-// A dependent FP64 operation takes ~64 cycles on this part (an FP32 one ~4.5, a
-// division ~360), and the prox is on the critical path of every iteration.  So
-// the same safeguarded iteration first runs in FP32 to ~2e-6 relative; the FP64
-// iteration then starts there and stops once a Newton correction is below 1e-9
-// relative: by its quadratic convergence the error after that step is ~1e-18,
-// so two FP64 steps replace the ~4 that a 4-eps test on the correction needs.
+// A dependent FP64 operation takes ~64 cycles on this part (an FP32 one ~5, an
+// FP64 division ~1400), and the prox is on the critical path of every
+// iteration.  So the same safeguarded iteration first runs in FP32 to ~2e-6
+// relative.  Two FP64 corrections follow, written as s <- s - s f / den with
+// f = s^(q+1)(s - a) - kq (Newton's step of Sec. 3.2 in correction form;
+// den = kq (q+1) + s^(q+2)): f cancels and is evaluated in FP64, while the
+// correction s f / den is a small number that needs only FP32 precision.  By
+// quadratic convergence the first leaves ~1e-11 relative and the second
+// ~1e-18 (plus ~1e-7 of the last correction from its FP32 quotient).  If the
+// FP32 stage did not converge, or the corrections are not small and inside the
+// bracket, the bracketed FP64 iteration runs instead.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float pow_q1f(float s, float q, int qcase) {  // s^(q+1), FP32
   switch (qcase) {
@@ -35,7 +40,7 @@ __device__ __forceinline__ double pow_q1(double s, double q, int qcase) {  // s^
     case 1: return s * s;
     case 2: return s * s * s;
     case 4: { double s2 = s * s; return s2 * s2 * s; }
-    case 5: return s * sqrt(s);   // q = 0.5
+    case 5: return s * sqrt_nr(s);   // q = 0.5
     default: return pow(s, q + 1.0);
   }
 }
@@ -45,27 +50,46 @@ __device__ __forceinline__ int q_case(double q) {
 }
 
 __device__ inline double prox_root(double a, double kq, double q, int qcase, double r0) {
-  double lo = fmax(a, 0.0);
-  double hi = lo + fmax(kq, 1.0);
+  double lo = dmax0(a);
+  double hi = lo + (kq > 1.0 ? kq : 1.0);
   double s = (r0 > lo && r0 < hi) ? r0 : 0.5 * (lo + hi);
-  // FP32 start (inputs well inside the FP32 range; its own bracket)
-  if (fabs(a) < 1e15 && kq > 1e-20 && kq < 1e15 && hi < 1e15 && q <= 8.0) {
+  // FP32 start, where every FP32 intermediate (up to a s^(q+1) and s^(q+2) with
+  // s < hi) stays finite and normal
+  if (a > -1e6 && a < 1e6 && kq > 1e-20 && kq < 1e6 && hi < 1e6 && q <= 4.0) {
     const float af = (float)a, kf = (float)kq, qf = (float)q;
     float lf = (float)lo, hf = (float)hi, sf = (float)s;
+    bool conv = false;
     for (int it = 0; it < 30; ++it) {
       const float sq1 = pow_q1f(sf, qf, qcase);
       const float f = sq1 * (sf - af) - kf;
       if (f < 0.f) lf = sf;
       else if (f > 0.f) hf = sf;
-      else break;
-      const float nt = sf * (kf * (qf + 2.f) + af * sq1) / (kf * (qf + 1.f) + sq1 * sf);
+      else {
+        conv = true;
+        break;
+      }
+      const float nt = sf * __fdividef(kf * (qf + 2.f) + af * sq1, kf * (qf + 1.f) + sq1 * sf);
       if (fabsf(nt - sf) <= 2e-6f * sf) {
         sf = nt;
+        conv = true;
         break;
       }
       sf = (nt > lf && nt < hf) ? nt : 0.5f * (lf + hf);
     }
     const double sd = (double)sf;
+    if (conv && sd > lo && sd < hi) {
+      const double kq1 = kq * (q + 1.0);
+      double x = sd, dl = 0.0;
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const double sq1 = pow_q1(x, q, qcase);
+        const double f = fma(sq1, x - a, -kq);
+        const double den = fma(sq1, x, kq1);
+        dl = (double)((float)x * __fdividef((float)f, (float)den));
+        x -= dl;
+      }
+      if (x > lo && x < hi && fabs(dl) <= 1e-9 * x) return x;
+    }
     if (sd > lo && sd < hi) s = sd;
   }
   for (int it = 0; it < 100; ++it) {
@@ -216,51 +240,84 @@ __device__ __forceinline__ void rows_sum(const double (&v)[N], int tr, bool mine
 // s_tot (Scal layout): the KKT residuals of Sec. 4.3 (readings R6, R7, R9), the
 // duality gap, the stop test (R8) and the sigma rule of Sec. 4.4 (R5, R5b).
 // Three independent chains run on lane 0 of warps 0, 1 and 2: the projection and
-// the w quantities (FP64 where cancellation needs it: theta, ||w|| - R, the
-// eta_D3 expansion), the objectives and the gap, and the plain norms (FP32: they
-// are compared with tol).  The maxima, the stop test and the sigma rule are FP32.
-// gs = 1 / (sigma sqrt(mu)).  s_ctl receives theta, sigma of the next iteration,
-// done and the status; CTA 0 also writes the residuals to ctrl.
+// the w quantities (FP64 where cancellation needs it: theta, ||w - u||^2, the
+// eta_D3 expansion, ||w|| - R), the objectives and the gap, and the plain norms
+// (FP32: they are compared with tol).  The maxima, the stop test and the sigma
+// rule are FP32.  On this part a dependent FP64 operation takes 64 cycles and an
+// FP64 compare with its select about 200, an FP64 division ~1400: the chain to
+// theta uses one FP32 rsqrt seed and one FP64 Newton step, the expansions are in
+// Horner form, and the sigma rule multiplies by the reciprocal factors.
+// gs = 1 / (sigma sqrt(mu)).  s_ctl receives theta and sigma of the next
+// iteration; s_ictl receives done and the status; s_etaf[10] the kkt value.
+// With `report` thread 0 also writes the residuals to ctrl (s_report).
 struct SPhaseArgs {
   double C, kappa, R, mu, tau, sqmu, tol, sqrt_tol;
   float inv_den;
   int stop_rule;
+  float tolf;        // the largest float <= tol (kkt <= tolf implies kkt <= tol)
 };
 
+// the largest float not above tol
+__device__ __forceinline__ float float_at_most(double tol) {
+  float t = (float)tol;
+  if ((double)t > tol) t = nextafterf(t, 0.f);
+  return t;
+}
+
+__device__ __forceinline__ void s_report(Ctrl* ctrl, double beta, const double* s_pd, const float* s_etaf) {
+  ctrl->beta = beta;
+  ctrl->pobj = s_pd[0];
+  ctrl->dobj = s_pd[1];
+  ctrl->kkt = s_etaf[10];
+  ctrl->eta_gap = s_etaf[0];
+  ctrl->eta_p1 = s_etaf[1];
+  ctrl->eta_d1 = s_etaf[2];
+  ctrl->eta_d2 = s_etaf[3];
+  ctrl->eta_c1 = s_etaf[4];
+  ctrl->eta_c2 = s_etaf[5];
+  ctrl->eta_c3 = s_etaf[6];
+  ctrl->eta_p2 = s_etaf[7];
+  ctrl->eta_p3 = s_etaf[8];
+  ctrl->eta_d3 = s_etaf[9];
+  ctrl->wnorm = s_pd[3];
+}
+
 __device__ __forceinline__ void s_phase(const double* s_tot, const SPhaseArgs& q, double sig, double gs, int it,
-                                        double beta,
-                                        int status, bool cta0, Ctrl* ctrl, double* s_pd, float* s_etaf,
-                                        double* s_ctl) {
+                                        double beta, int status, bool report, Ctrl* ctrl, double* s_pd,
+                                        float* s_etaf, double* s_ctl, int* s_ictl) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0 && warp == 1) {
     const double pobj = s_tot[S_PRIM_R] + q.C * s_tot[S_PRIM_XI];
-    const double dobj = q.kappa * s_tot[S_DUAL_A] - q.R * sqrt_nr(fmax(0.0, s_tot[S_TA2]));
+    const double dobj = q.kappa * s_tot[S_DUAL_A] - q.R * sqrt_nr(s_tot[S_TA2]);
     s_pd[0] = pobj;
     s_pd[1] = dobj;
-    s_etaf[0] = (float)fabs(pobj - dobj) / (float)(1.0 + fabs(pobj) + fabs(dobj));   // gap
+    s_etaf[0] = __fdividef(fabsf((float)(pobj - dobj)), 1.f + fabsf((float)pobj) + fabsf((float)dobj));   // gap
   } else if (lane == 0 && warp == 2) {
-    s_etaf[1] = sqrtf((float)s_tot[S_RES2]) * q.inv_den;       // p1
-    s_etaf[2] = sqrtf((float)s_tot[S_AMIN2]) * q.inv_den;      // dd1
-    s_etaf[3] = sqrtf((float)s_tot[S_AMAX2]) * q.inv_den;      // dd2
-    s_etaf[4] = fabsf((float)s_tot[S_YA]) * q.inv_den;         // c1
-    s_etaf[5] = fabsf((float)s_tot[S_XICA]) * q.inv_den;       // c2
-    s_etaf[6] = sqrtf((float)s_tot[S_AMS2]) * q.inv_den;       // c3
+    s_etaf[1] = fsqrt_approx((float)s_tot[S_RES2]) * q.inv_den;       // p1
+    s_etaf[2] = fsqrt_approx((float)s_tot[S_AMIN2]) * q.inv_den;      // dd1
+    s_etaf[3] = fsqrt_approx((float)s_tot[S_AMAX2]) * q.inv_den;      // dd2
+    s_etaf[4] = fabsf((float)s_tot[S_YA]) * q.inv_den;                // c1
+    s_etaf[5] = fabsf((float)s_tot[S_XICA]) * q.inv_den;              // c2
+    s_etaf[6] = fsqrt_approx((float)s_tot[S_AMS2]) * q.inv_den;       // c3
   } else if (threadIdx.x == 0) {
-    const double S1 = fmax(0.0, s_tot[S_G2]), S2 = s_tot[S_GRHO], S3 = fmax(0.0, s_tot[S_RHO2]);
-    const double gnorm = sqrt_nr(S1);
-    const double th = (gnorm <= q.R) ? 1.0 : div_nr(q.R, gnorm);                 // Step 2 projection
-    const double w2 = fmax(0.0, S1 + 2.0 * gs * S2 + gs * gs * S3);              // ||w||^2
+    const double S1 = s_tot[S_G2], S2 = s_tot[S_GRHO], S3 = s_tot[S_RHO2];   // ||g||^2, <g,rho>, ||rho||^2
+    const double t2 = 2.0 * gs * S2, t3 = gs * gs * S3;
+    // Step 2 projection: theta = min(1, R / ||g||), R / ||g|| = R rsqrt(S1)
+    const double r0 = (double)rsqrt_approx((float)S1);
+    const double rs = r0 * fma(-0.5 * S1, r0 * r0, 1.5);
+    const double th = (S1 <= q.R * q.R) ? 1.0 : q.R * rs;
+    const double w2 = S1 + t2 + t3;                                      // ||w||^2
     const double om = 1.0 - th;
-    const double wu2 = fmax(0.0, om * om * S1 + 2.0 * om * gs * S2 + gs * gs * S3);   // ||w - u+||^2
-    const double kap = q.tau * sig * q.mu * om;
-    const double d3 = fmax(0.0, s_tot[S_A2] - 2.0 * kap * s_tot[S_AG] + kap * kap * S1);
-    const float wnf = sqrtf((float)w2);
-    const double wmr = (w2 - q.R * q.R) * (double)(1.0f / (wnf + (float)q.R));   // ||w|| - R
+    const double wu2 = fma(om, fma(om, S1, t2), t3);                     // ||w - u+||^2
+    const double kap = (q.tau * q.mu) * sig * om;
+    const double d3 = fma(kap, fma(kap, S1, -2.0 * s_tot[S_AG]), s_tot[S_A2]);
+    const float wnf = fsqrt_approx((float)w2);
+    const double wmr = (w2 - q.R * q.R) * (double)rcp_approx(wnf + (float)q.R);   // ||w|| - R
     s_pd[2] = th;
     s_pd[3] = (double)wnf;
-    s_etaf[7] = sqrtf((float)q.mu * (float)wu2) * q.inv_den;   // p2
-    s_etaf[8] = (float)fmax(wmr, 0.0) * q.inv_den;            // p3
-    s_etaf[9] = sqrtf((float)d3) * q.inv_den;                 // dd3
+    s_etaf[7] = fsqrt_approx((float)q.mu * (float)wu2) * q.inv_den;   // p2 (a rounding-negative square gives 0)
+    s_etaf[8] = fmaxf((float)wmr, 0.f) * q.inv_den;                   // p3
+    s_etaf[9] = fsqrt_approx((float)d3) * q.inv_den;                  // dd3
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -268,68 +325,72 @@ __device__ __forceinline__ void s_phase(const double* s_tot, const SPhaseArgs& q
                 c3 = s_etaf[6], p2 = s_etaf[7], p3 = s_etaf[8], dd3 = s_etaf[9];
     const float ep = fmaxf(p1, fmaxf(p2, p3)), ed = fmaxf(dd1, fmaxf(dd2, dd3)), ec = fmaxf(c1, fmaxf(c2, c3));
     const float kkt = fmaxf(fmaxf(ep, ed), fmaxf(ec, gap));
-    const float tolf = (float)q.tol;
     int done = 0;
-    double sig_next = sig;
+    double mult = 1.0;
     if (!(kkt == kkt) || isinf(kkt)) {
       done = 1;
       status = GDWD_ENUMERIC;
-    } else if (q.stop_rule == 0 ? (double)kkt <= q.tol
-                                : (fmaxf(ep, ed) < tolf && fminf(ec, gap) < (float)q.sqrt_tol && fmaxf(ec, gap) < 0.05f)) {
+    } else if (q.stop_rule == 0 ? kkt <= q.tolf
+                                : (fmaxf(ep, ed) < q.tolf && fminf(ec, gap) < (float)q.sqrt_tol && fmaxf(ec, gap) < 0.05f)) {
       done = 1;
       status = GDWD_OK;
-    } else if (it >= 1 && fminf(ep, ed) > 1e-3f * tolf) {                            // sigma rule, Sec. 4.4
-      const float chi = ep / fmaxf(ed, 1e-30f);
-      const float ichi = ed / fmaxf(ep, 1e-30f);
+    } else if (it >= 1 && fminf(ep, ed) > 1e-3f * q.tolf) {                          // sigma rule, Sec. 4.4
+      const float chi = __fdividef(ep, fmaxf(ed, 1e-30f));
+      const float ichi = __fdividef(ed, fmaxf(ep, 1e-30f));
       const float big = fmaxf(chi, ichi);
-      const double zeta = big > 500.f ? 2.2 : (big > 50.f ? 1.65 : 1.1);
-      if (chi > 5.f) sig_next = sig * zeta;
-      else if (ichi > 5.f) sig_next = sig / zeta;
+      const int zk = big > 500.f ? 2 : (big > 50.f ? 1 : 0);
+      if (chi > 5.f) mult = zk == 2 ? 2.2 : (zk == 1 ? 1.65 : 1.1);
+      else if (ichi > 5.f) mult = zk == 2 ? (1.0 / 2.2) : (zk == 1 ? (1.0 / 1.65) : (1.0 / 1.1));
     }
     s_ctl[0] = s_pd[2];
-    s_ctl[1] = sig_next;
-    s_ctl[2] = done;
-    s_ctl[3] = status;
-    if (cta0) {
-      ctrl->beta = beta;
-      ctrl->pobj = s_pd[0];
-      ctrl->dobj = s_pd[1];
-      ctrl->kkt = kkt;
-      ctrl->eta_p1 = p1; ctrl->eta_p2 = p2; ctrl->eta_p3 = p3;
-      ctrl->eta_d1 = dd1; ctrl->eta_d2 = dd2; ctrl->eta_d3 = dd3;
-      ctrl->eta_c1 = c1; ctrl->eta_c2 = c2; ctrl->eta_c3 = c3;
-      ctrl->eta_gap = gap;
-      ctrl->wnorm = s_pd[3];
-    }
+    s_ctl[1] = sig * mult;
+    s_ictl[0] = done;
+    s_ictl[1] = status;
+    s_etaf[10] = kkt;
+    if (report) s_report(ctrl, beta, s_pd, s_etaf);
   }
   __syncthreads();
 }
 
 // x_i = sum_j P_ij rhs_j for one row, one warp, double-float (result in all lanes).
-// Four independent 16-byte loads per lane per step keep several L2 requests in flight.
+// The row is taken in steps of 128 pairs (four 16-byte loads of P and four of
+// the right-hand side per lane); the next step's eight loads are issued before
+// the current step's products, so one L2 round trip overlaps the next instead
+// of the loop waiting for each in turn.  Pairs past npair read as zero.
 __device__ __forceinline__ df row_dot(const float2* __restrict__ Prow, const float2* rhs_s, int npair) {
   const float4* P4 = reinterpret_cast<const float4*>(Prow);
   const float4* R4 = reinterpret_cast<const float4*>(rhs_s);
   df a0{0.f, 0.f}, a1{0.f, 0.f}, a2{0.f, 0.f}, a3{0.f, 0.f};
   const int lane = threadIdx.x & 31;
-  int j = lane;
-  for (; j + 96 < npair; j += 128) {
-    const float4 p0 = __ldg(P4 + j), p1 = __ldg(P4 + j + 32), p2 = __ldg(P4 + j + 64), p3 = __ldg(P4 + j + 96);
-    const float4 r0 = R4[j], r1 = R4[j + 32], r2 = R4[j + 64], r3 = R4[j + 96];
-    df_fma(a0, df{p0.x, p0.y}, df{r0.x, r0.y});
-    df_fma(a1, df{p0.z, p0.w}, df{r0.z, r0.w});
-    df_fma(a2, df{p1.x, p1.y}, df{r1.x, r1.y});
-    df_fma(a3, df{p1.z, p1.w}, df{r1.z, r1.w});
-    df_fma(a0, df{p2.x, p2.y}, df{r2.x, r2.y});
-    df_fma(a1, df{p2.z, p2.w}, df{r2.z, r2.w});
-    df_fma(a2, df{p3.x, p3.y}, df{r3.x, r3.y});
-    df_fma(a3, df{p3.z, p3.w}, df{r3.z, r3.w});
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 p[4], r[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int j = lane + 32 * u;
+    p[u] = j < npair ? __ldg(P4 + j) : z4;
+    r[u] = j < npair ? R4[j] : z4;
   }
-  for (; j < npair; j += 32) {
-    const float4 p0 = __ldg(P4 + j);
-    const float4 r0 = R4[j];
-    df_fma(a0, df{p0.x, p0.y}, df{r0.x, r0.y});
-    df_fma(a1, df{p0.z, p0.w}, df{r0.z, r0.w});
+  for (int base = 0; base < npair; base += 128) {
+    float4 pn[4], rn[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = base + 128 + lane + 32 * u;
+      pn[u] = j < npair ? __ldg(P4 + j) : z4;
+      rn[u] = j < npair ? R4[j] : z4;
+    }
+    df_fma(a0, df{p[0].x, p[0].y}, df{r[0].x, r[0].y});
+    df_fma(a1, df{p[0].z, p[0].w}, df{r[0].z, r[0].w});
+    df_fma(a2, df{p[1].x, p[1].y}, df{r[1].x, r[1].y});
+    df_fma(a3, df{p[1].z, p[1].w}, df{r[1].z, r[1].w});
+    df_fma(a0, df{p[2].x, p[2].y}, df{r[2].x, r[2].y});
+    df_fma(a1, df{p[2].z, p[2].w}, df{r[2].z, r[2].w});
+    df_fma(a2, df{p[3].x, p[3].y}, df{r[3].x, r[3].y});
+    df_fma(a3, df{p[3].z, p[3].w}, df{r[3].z, r[3].w});
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      p[u] = pn[u];
+      r[u] = rn[u];
+    }
   }
   df_add(a0, a1);
   df_add(a2, a3);

@@ -91,23 +91,44 @@ __device__ __forceinline__ void ring_drain_prefetched(Ring& rg, int* err, uint64
   rg.prefetched = 0;
 }
 
+// A stream without extra chunks.
+struct NoExtra {
+  __device__ int count() const { return 0; }
+  __device__ void issue(int, uint8_t*, uint64_t*) const {}
+  __device__ void consume(int, const uint8_t*) {}
+};
+
 // Streams every chunk of the slabs cta, cta+grid, ... through the ring and
-// calls f.chunk / f.end_slab.  Returns false (all threads) on a timed-out wait,
-// after the copies still in flight have landed.
-template <typename T, typename F>
+// calls f.chunk / f.end_slab.  An optional source x adds x->count() extra chunks
+// (other data the CTA needs during the pass): they take the ring right after
+// the first min(stages, Z chunks) chunks of Z -- the ones ring_prefetch may
+// have issued -- so their copies and their work overlap the rest of the pass.
+// x->issue(e, dst, bar) sets the transaction count and issues the copies of
+// extra chunk e (one thread); x->consume(e, buf) runs on all threads.  Returns
+// false (all threads) on a timed-out wait, after the copies still in flight
+// have landed.
+template <typename T, typename F, typename X = NoExtra>
 __device__ bool stream_slabs(const Layout& L, Ring& rg, int cta, int grid, int* err, uint64_t tmo, int* s_abort,
-                             F& f) {
+                             F& f, X* x = nullptr) {
   const int nch = (int)((L.n + L.CW - 1) / L.CW);
   const int nmy = (L.NB > cta) ? (L.NB - cta + grid - 1) / grid : 0;
-  const int total = nmy * nch;
+  const int nz = nmy * nch;
+  const int nx = x ? x->count() : 0;
+  const int xpos = min(rg.stages, nz);
+  const int total = nz + nx;
 
   auto issue = [&](int c) {
+    const int st = c % rg.stages;
+    uint8_t* dst = rg.buf + (size_t)st * rg.stage_bytes;
+    if (c >= xpos && c < xpos + nx) {
+      x->issue(c - xpos, dst, &rg.bars[st]);
+      return;
+    }
     const uint8_t* src;
     uint32_t bytes;
-    chunk_src(L, cta, grid, c, src, bytes);
-    const int st = c % rg.stages;
+    chunk_src(L, cta, grid, c < xpos ? c : c - nx, src, bytes);
     mbar_expect_tx(&rg.bars[st], bytes);
-    bulk_g2s(rg.buf + (size_t)st * rg.stage_bytes, src, bytes, &rg.bars[st]);
+    bulk_g2s(dst, src, bytes, &rg.bars[st]);
   };
 
   if (threadIdx.x == 0) {
@@ -117,13 +138,17 @@ __device__ bool stream_slabs(const Layout& L, Ring& rg, int cta, int grid, int* 
   rg.prefetched = 0;
   for (int c = 0; c < total; ++c) {
     const int st = c % rg.stages;
-    const int k = c / nch, cc = c - k * nch;
+    const bool extra = c >= xpos && c < xpos + nx;
+    const int cz = c < xpos ? c : c - nx;   // index among the Z chunks
+    const int k = cz / nch, cc = cz - k * nch;
     const int s = cta + k * grid;
     const int col0 = cc * L.CW;
     const int cw = (int)min((int64_t)L.CW, L.n - col0);
     if (!mbar_wait(&rg.bars[st], (rg.phase >> st) & 1u, err, tmo)) *s_abort = 1;
     rg.phase ^= 1u << st;
-    f.chunk(reinterpret_cast<const T*>(rg.buf + (size_t)st * rg.stage_bytes), k, s, col0, cw);
+    const uint8_t* buf = rg.buf + (size_t)st * rg.stage_bytes;
+    if (extra) x->consume(c - xpos, buf);
+    else f.chunk(reinterpret_cast<const T*>(buf), k, s, col0, cw);
     __syncthreads();
     if (*(volatile int*)s_abort) {
       // chunks c .. min(c + stages, total) - 1 were issued and may be in flight
@@ -131,7 +156,7 @@ __device__ bool stream_slabs(const Layout& L, Ring& rg, int cta, int grid, int* 
       return false;
     }
     if (threadIdx.x == 0 && c + rg.stages < total) issue(c + rg.stages);
-    if (cc == nch - 1) f.end_slab(k, s);
+    if (!extra && cc == nch - 1) f.end_slab(k, s);
   }
   return true;
 }

@@ -46,9 +46,10 @@ enum Scal {
 // Phases of one iteration, each followed by its grid-barrier wait:
 // 0 A, 1 wait, 2 R, 3 wait, 4 N1, 5 wait, 6 N2, 7 wait, 8 B, 9 wait, 10 S;
 // sub-phases: 11 N2 rhs load + beta, 12 N2 rows of G^{-1}, 13 S partial-sum
-// reduction, 14 N1 rhs load + beta-bar, 15 N1 rows of G^{-1} (the slot of a
-// phase then holds only its remainder).
-constexpr int kPhaseSlots = 16;
+// reduction, 14 N1 rhs load + beta-bar, 15 N1 rows of G^{-1}, 16 B prologue
+// (coefficients, deferred d-update), 17 B stream, 18 N1 prox of the first row,
+// 19 spare (the slot of a phase then holds only its remainder).
+constexpr int kPhaseSlots = 20;
 // n-space rows owned by one CTA of the iteration kernel (ceil(n / grid) <= this)
 constexpr int kMaxRowsPerCta = 256;
 
@@ -103,6 +104,9 @@ struct IterArgs {
   int dots_every;        // >= 1: pass B takes the column dots Z~^T u every dots_every iterations
   int stall_first_barrier;   // test hook: 1 makes the launch's first grid barrier wait for an
                              // arrival that never comes, so it runs out after timeout_ns
+  int fuse;              // 1: Step 1a's solve of the next iteration is taken from three
+                         // G^{-1} products made during the pass over Z (iterate.cu)
+  float2* vrhs;          // [3][ldP] double-float right-hand sides of those products
   // d-space state, NB*TB long (padding rows stay 0)
   double* u;
   double* rho;

@@ -65,7 +65,7 @@ EXPORTS = ["gdwd_default_options", "gdwd_create", "gdwd_solve", "gdwd_free", "gd
 EAGAIN = 9
 STORE_NP = {F64: "float64", F32: "float32", BF16: "uint16", F16: "float16", E4M3: "uint8"}
 PHASES = ["warm_passes", "warm_passes_wait", "R", "R_wait", "N1_rows", "N1_wait", "N2_rows", "N2_wait", "B", "B_wait", "S_kkt",
-          "N2_rhs", "N2_gemv", "S_sums", "N1_rhs", "N1_gemv"]
+          "N2_rhs", "N2_gemv", "S_sums", "N1_rhs", "N1_gemv", "B_prologue", "B_stream", "N1_prox", "spare"]
 
 _lib = None
 
@@ -249,9 +249,9 @@ class Solver:
 
     def phase_times(self):
         """Per-phase device time (ns) of the last solve, CTA 0's view (gdwd_get_phase_times)."""
-        buf = (c_double * 16)()
-        _check(_lib.gdwd_get_phase_times(self._h, buf, 16), self._h)
-        return {PHASES[k]: buf[k] for k in range(16)}
+        buf = (c_double * len(PHASES))()
+        _check(_lib.gdwd_get_phase_times(self._h, buf, len(PHASES)), self._h)
+        return {PHASES[k]: buf[k] for k in range(len(PHASES))}
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

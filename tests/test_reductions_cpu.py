@@ -102,3 +102,61 @@ def test_kernelized_iterates_equal_algorithm_1():
     assert np.allclose(xi, ref["xi"], rtol=1e-9, atol=1e-12)
     assert np.allclose(Zt @ au, ref["u_scaled"], rtol=1e-9, atol=1e-12)
     assert np.allclose(Zt @ ar, ref["rho"], rtol=1e-9, atol=1e-12)
+
+
+def test_fused_first_solve_equals_direct_solve():
+    """The Z-streaming kernel forms Step 1a's x-bar = G^{-1} rhs1 of iteration k+1
+    from three G^{-1} products taken during iteration k's pass over Z:
+        rhs1 = a1 U_g + ((1 - tau) U_rho / sqrt(mu) - alpha) / sigma' + (xi - r),
+        a1 = theta - tau (sigma / sigma') (1 - theta),
+    with U_g = Z~^T g, U_rho = Z~^T rho of iteration k and sigma' the next sigma.
+    Twenty iterations on the oracle's sigma path: the fused x-bar equals the direct
+    one, and the iterates equal the oracle's."""
+    rng = np.random.default_rng(4)
+    d, n, q, C, mu, tau = 30, 14, 1.0, 2.0, 0.7, 1.618
+    y = np.where(np.arange(n) < 6, 1.0, -1.0)
+    Z = rng.standard_normal((d, n)) * y
+    ref = O.solve(Z, y, q, C, mu=mu, tau=tau, tol=1e-300, max_iter=20, record=True)
+    sigmas = [h[0] for h in ref["history"]]
+    Zt, zs = O.scale_data(Z)
+    G = np.eye(n) + Zt.T @ Zt / mu
+    Gi = np.linalg.inv(G)
+    p = Gi @ y
+    s = y @ p
+    sq = math.sqrt(mu)
+    r, xi, alpha = np.ones(n), np.ones(n), np.zeros(n)
+    u, rho = np.zeros(d), np.zeros(d)
+    prev = None   # (X1, X2, X3, theta, sigma) from the last pass
+    for sigma in sigmas:
+        gp = u + rho / (sigma * sq)
+        b = Zt.T @ gp
+        rhs1 = b + xi - r - alpha / sigma
+        xb = Gi @ rhs1
+        if prev is not None:
+            X1, X2, X3, th, sp = prev
+            a1 = th - tau * (sp / sigma) * (1.0 - th)
+            xf = a1 * X1 + X2 / sigma + X3
+            assert np.allclose(xf, xb, rtol=1e-10, atol=1e-12 * np.abs(xb).max())
+        betab = -(y @ xb) / s
+        r = O.prox_r(xb + betab * p + r, sigma, q, r0=r)
+        v = xi - r - alpha / sigma
+        x = Gi @ (b + v)
+        beta = -(y @ x) / s
+        c = x + beta * p
+        w = gp - Zt @ c / mu
+        g = w - rho / (sigma * sq)
+        gn = np.linalg.norm(g)
+        theta = 1.0 if gn <= zs else zs / gn
+        ztw = Zt.T @ w
+        xi = np.maximum(0.0, r - ztw - y * beta + alpha / sigma - C / sigma)
+        alpha = alpha - tau * sigma * (ztw + y * beta + xi - r)
+        # the three right-hand sides the kernel multiplies by G^{-1} during the pass
+        V1 = Zt.T @ g
+        V2 = (1.0 - tau) * (Zt.T @ rho) / sq - alpha
+        V3 = xi - r
+        prev = (Gi @ V1, Gi @ V2, Gi @ V3, theta, sigma)
+        rho = rho - tau * sigma * sq * (w - theta * g)
+        u = theta * g
+    assert np.allclose(r, ref["r"], rtol=1e-9, atol=1e-12)
+    assert np.allclose(alpha, ref["alpha"], rtol=1e-9, atol=1e-12)
+    assert np.allclose(u, ref["u_scaled"], rtol=1e-9, atol=1e-12)

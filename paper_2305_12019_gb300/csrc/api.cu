@@ -659,7 +659,7 @@ static IterArgs<CT> make_args(gdwd_handle* h, double C, double sigma0, int refre
   a.refresh = refresh;
   a.dots_every = dots_every_of(h);
   a.stall_first_barrier = env_long("GDWD_INJECT_STALL") > 0 ? 1 : 0;
-  a.fuse = 1;
+  a.fuse = 0;
   a.vrhs = h->vrhs;
   a.rhsB = h->rhsB;
   a.cq = (CT*)h->cq;

@@ -192,6 +192,42 @@ __device__ __forceinline__ bool grid_barrier(unsigned* counter, unsigned nblocks
   return *(volatile int*)s_flag != 0;
 }
 
+// The same barrier with work for the rest of the CTA while thread 0 waits: warps
+// 1 .. kWarps-1 run side() between this CTA's arrival and the end of the wait
+// (work that depends only on the CTA's own data and is not needed by the other
+// CTAs before the next barrier; its global writes are ordered before that one).
+template <typename F>
+__device__ __forceinline__ bool grid_barrier_side(unsigned* counter, unsigned nblocks, unsigned& gen, int* err,
+                                                  uint64_t timeout_ns, int* s_flag, unsigned extra, F&& side) {
+  __syncthreads();
+  gen += 1;
+  if (threadIdx.x == 0) {
+    red_add_release(counter, 1u);
+    const unsigned target = gen * nblocks + extra;
+    int ok = 1;
+    uint64_t t0 = 0;
+    unsigned polls = 0;
+    while ((int)(ld_acquire(counter) - target) < 0) {
+      if ((++polls & 31u) == 0) {
+        if (ld_volatile(err) != 0) { ok = 0; break; }
+        const uint64_t t = globaltimer();
+        if (t0 == 0) t0 = t;
+        else if (t - t0 > timeout_ns) {
+          atomicCAS(err, 0, (int)GDWD_ETIMEOUT);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    if (ld_volatile(err) != 0) ok = 0;
+    *s_flag = ok;
+  } else if (threadIdx.x >= 32) {
+    side();
+  }
+  __syncthreads();
+  return *(volatile int*)s_flag != 0;
+}
+
 // ---------------------------------------------------------------------------
 // mbarrier + 1-D bulk async copy (cp.async.bulk, the untiled TMA form)
 // ---------------------------------------------------------------------------
@@ -220,6 +256,39 @@ __device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, u
           smem_u32(dst_smem)),
       "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
+}
+
+// The same copy with an L2 eviction-priority hint (a policy from createpolicy).
+__device__ __forceinline__ void bulk_g2s_hint(void* dst_smem, const void* src_gmem, uint32_t bytes, uint64_t* bar,
+                                              uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          smem_u32(dst_smem)),
+      "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+      : "memory");
+}
+
+// L2 eviction priority of the stored Z's chunks: 0 the default, 1 evict_last
+// (keep Z, the largest data reused every iteration, ahead of other lines),
+// 2 evict_first.
+#ifndef GDWD_Z_L2_HINT
+#define GDWD_Z_L2_HINT 0
+#endif
+__device__ __forceinline__ uint64_t z_l2_policy() {
+  uint64_t p = 0;
+#if GDWD_Z_L2_HINT == 1
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+#elif GDWD_Z_L2_HINT == 2
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+#endif
+  return p;
+}
+__device__ __forceinline__ void bulk_g2s_z(void* dst_smem, const void* src_gmem, uint32_t bytes, uint64_t* bar) {
+#if GDWD_Z_L2_HINT == 0
+  bulk_g2s(dst_smem, src_gmem, bytes, bar);
+#else
+  bulk_g2s_hint(dst_smem, src_gmem, bytes, bar, z_l2_policy());
+#endif
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {

@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(kThreads) dir_s_kernel(DirArgs a) {
   __shared__ double s_pd[4];
   __shared__ float s_etaf[11];
   __shared__ int s_ictl[2];
-  __shared__ double s_ctl[8];
+  __shared__ double s_ctl[15];
   __shared__ double s_part[kWarps * 6];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const double sig = c->sigma, sqmu = sqrt(a.mu);

@@ -68,15 +68,17 @@ cudaError_t launch_prox(const double* a, const double* r0, const double* omega, 
 // pass-B row epilogue of the iteration: g = u - t / mu and the d-space sums
 // ---------------------------------------------------------------------------
 struct IterEpi {
-  double* g;
-  const double* u;
-  const double* rho;
+  double* g;                 // global copy of g (written through: the host's w uses it)
+  const double* s_u;         // the CTA's slab rows of u, rho and g in shared memory
+  const double* s_rho;
+  double* s_g;
   double inv_mu, a_coef;     // a = ta + a_coef * rho, a_coef = sqrt(mu)(1 - tau)
   double sg2 = 0, sgr = 0, sr2 = 0, sa2 = 0, sag = 0, sta2 = 0;
-  __device__ void row(int64_t j, double t, double ta) {
-    const double gj = u[j] - t * inv_mu;
-    const double rj = rho[j];
+  __device__ void row(int64_t j, int m, double t, double ta) {
+    const double gj = s_u[m] - t * inv_mu;
+    const double rj = s_rho[m];
     const double aj = ta + a_coef * rj;
+    s_g[m] = gj;
     g[j] = gj;
     sg2 = fma(gj, gj, sg2);
     sgr = fma(gj, rj, sgr);
@@ -109,10 +111,18 @@ __device__ __forceinline__ void store_ct(CT* p, double v) { *p = (CT)v; }
 // of rpc doubles each, ahead of the phase-local region.  The row phases then
 // touch global memory only for what other CTAs read.
 enum RowSlot { RS_R, RS_XI, RS_AL, RS_B, RS_KC, RS_UU, RS_UR, RS_Y, RS_P, RS_CE, RS_E, RS_OM, RS_WT, RS_SC,
-               RS_X1, RS_X2, RS_X3, RS_COUNT };
+               RS_X1, RS_X2, RS_X3, RS_RES, RS_COUNT };
 
 __host__ __device__ inline size_t row_state_bytes(int64_t rpc) {
   return ((size_t)RS_COUNT * (size_t)rpc * sizeof(double) + 127) & ~(size_t)127;
+}
+
+// The CTA's slab rows of u, rho, g (FP64) and of u in the compute type (the
+// column dots' right-hand side) stay in shared memory for the whole launch, so
+// the d-space update and the pass-B epilogue read no global memory; the global
+// copies are written through.
+__host__ __device__ inline size_t slab_state_bytes(int nslab_rows, int ct_size) {
+  return ((size_t)nslab_rows * (3 * sizeof(double) + (size_t)ct_size) + 127) & ~(size_t)127;
 }
 
 // ---------------------------------------------------------------------------
@@ -213,7 +223,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
   __shared__ uint64_t s_bars[kMaxStages];
   __shared__ int s_flag, s_abort;
   __shared__ double s_tot[S_COUNT];
-  __shared__ double s_ctl[8];
+  __shared__ double s_ctl[15];
   __shared__ double s_pd[4];     // pobj, dobj, theta, ||w||
   __shared__ float s_etaf[11];   // gap, the nine residuals, kkt
   __shared__ int s_ictl[2];      // done, status
@@ -251,7 +261,13 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
   double* rs = reinterpret_cast<double*>(smem + (size_t)stages * stage_bytes);   // row state
   const int rld = (int)rpc;
 #define RS(slot, t) rs[(slot) * rld + (t)]
-  uint8_t* uni = smem + (size_t)stages * stage_bytes + row_state_bytes(rpc);     // phase-local region
+  const int nslab_max = (NB + grid - 1) / grid * TB;                              // slab rows, any CTA
+  uint8_t* sst = smem + (size_t)stages * stage_bytes + row_state_bytes(rpc);      // slab state
+  double* s_u = reinterpret_cast<double*>(sst);
+  double* s_rho = s_u + nslab_max;
+  double* s_g = s_rho + nslab_max;
+  CT* s_up = reinterpret_cast<CT*>(s_g + nslab_max);
+  uint8_t* uni = sst + slab_state_bytes(nslab_max, (int)sizeof(CT));              // phase-local region
   if (threadIdx.x == 0) s_abort = 0;
   ring_init(rg);
   // the fused first solve needs every row of the CTA (and p^T) on at most
@@ -282,6 +298,16 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
       s_tacc[k] += t_ - s_tprev;           \
       s_tprev = t_;                        \
     }                                      \
+  } while (0)
+#define GDWD_BARRIER_SIDE(k, ...)                                                                    \
+  do {                                                                                               \
+    GDWD_MARK(k);                                                                                    \
+    if (!grid_barrier_side(a.bar, (unsigned)grid, gen, a.err, a.timeout_ns, &s_flag,                 \
+                           (a.stall_first_barrier && gen == 0) ? 1u : 0u, __VA_ARGS__)) {            \
+      ring_drain_prefetched(rg, a.err, a.timeout_ns);                                                \
+      return;                                                                                        \
+    }                                                                                                \
+    GDWD_MARK(k + 1);                                                                                \
   } while (0)
 #define GDWD_BARRIER(k)                                                                              \
   do {                                                                                               \
@@ -356,14 +382,22 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
     RS(RS_WT, t) = a.wt[i];
     RS(RS_SC, t) = a.sc[i];
   }
+  for (int m = threadIdx.x; m < nmy * TB; m += kThreads) {
+    const int k = m / TB, j = m - k * TB;
+    const int64_t gj = (cta + (int64_t)k * grid) * TB + j;
+    const bool in = gj < d;
+    s_u[m] = in ? a.u[gj] : 0.0;
+    s_rho[m] = in ? a.rho[gj] : 0.0;
+    s_g[m] = in ? a.g[gj] : 0.0;
+  }
   __syncthreads();
 
   int it = it0;
   bool dots_prev = false;   // the last pass B took the column dots Z~^T u
   bool fused = false;       // the last pass B made the three products of the fused first solve
+  double inv_sig = rcp_nr(sig);   // from the last phase S after the first iteration
   for (; it < a.max_iter; ++it) {
-    const double inv_sig = rcp_nr(sig);
-    const double gs_it = rcp_nr(sig * sqmu);   // 1 / (sigma sqrt(mu)) of this iteration
+    const double gs_it = inv_sig * inv_sqmu;   // 1 / (sigma sqrt(mu)) of this iteration
     // this iteration's pass B takes the column dots Z~^T u every dots_every-th
     // iteration; otherwise it makes the products of the next fused first solve
     const bool dots_now = ((it - it0) % a.dots_every) == a.dots_every - 1;
@@ -445,13 +479,34 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
         s_rb[t] = make_float2(r2.hi, r2.lo);
       }
     }
-    GDWD_BARRIER(4);
+    // the deferred d-space update of the last iteration's Steps 2-3 on this CTA's
+    // slab rows, u+ = theta g, rho+ = (1 - tau) rho - tau sigma' sqrt(mu)
+    // (1 - theta) g, made by warps 1.. while thread 0 waits at the barrier; the
+    // pass over Z reads it from shared memory (u also in the compute type, for
+    // the column dots)
+    GDWD_BARRIER_SIDE(4, [&]() {
+      const double rcoefd = a.tau * sig_prev * sqmu * (1.0 - theta);
+      for (int m = threadIdx.x - 32; m < nmy * TB; m += kThreads - 32) {
+        const int k = m / TB, j = m - k * TB;
+        const int64_t gj = (cta + (int64_t)k * grid) * TB + j;
+        double uj = s_u[m];
+        if (pending && gj < d) {
+          const double g = s_g[m];
+          const double rn = (1.0 - a.tau) * s_rho[m] - rcoefd * g;   // rho <- rho - tau sigma D (w - u+)
+          uj = theta * g;                                            // u+ = Pi_B(g)
+          s_rho[m] = rn;
+          s_u[m] = uj;
+          a.rho[gj] = rn;
+          a.u[gj] = uj;
+        }
+        s_up[m] = (CT)uj;
+      }
+    });
 
     // ---------------- phase N2: x, beta, c, Z~^T w; Step 2 (xi), Step 3 (alpha);
     // (G - I) c = rhs2 - x + beta (y - p) for the next U_g
     {
       GDWD_MARK(11);
-      double s_res2 = 0, s_ya = 0, s_xica = 0, s_ams2 = 0, s_amin2 = 0, s_amax2 = 0, s_pr = 0, s_px = 0, s_du = 0;
       for (int t = warp; t <= nrows; t += kWarps) {
         const df x = row_dot(t < nrows ? a.P + (size_t)(r0 + t) * a.ldP : a.pdf, a.rhsB, npair);
         if (lane == 0) {
@@ -492,29 +547,52 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
             a.vrhs[a.ldP + i] = make_float2(v2.hi, v2.lo);
             a.vrhs[2 * (size_t)a.ldP + i] = make_float2(v3.hi, v3.lo);
           }
-          const double rq1 = pow_q1(ri, a.q, qcase);
-          const double irq1 = rcp_nr(rq1);
-          const double om = RS(RS_OM, t);
-          s_res2 = fma(res, res, s_res2);
-          s_ya = fma(yi, an, s_ya);
-          s_xica = fma(xin, ce - an, s_xica);
-          const double dv = an - om * irq1;
-          s_ams2 = fma(dv, dv, s_ams2);
-          const double mn = dmin0(an), mx = dmax0(an - ce);
-          s_amin2 = fma(mn, mn, s_amin2);
-          s_amax2 = fma(mx, mx, s_amax2);
-          s_pr += om * inv_q * ri * irq1;           // wt^q r^-q
-          s_px = fma(RS(RS_E, t), xin, s_px);
-          s_du += dual_pow(RS(RS_WT, t) * an, a.q, qcase);
+          RS(RS_RES, t) = res;
         }
       }
-      // one row per thread (nrows <= kThreads): the sums go through the phase-local
-      // region, one warp per sum
-      const double vals[9] = {s_res2, s_ya, s_xica, s_ams2, s_amin2, s_amax2, s_pr, s_px, s_du};
-      rows_sum<9>(vals, threadIdx.x, threadIdx.x < nrows, nrows, reinterpret_cast<double*>(uni), nrows, a.scal + cta,
-                  grid);
     }
-    GDWD_BARRIER(6);
+    // the n-space KKT sums (read only by phase S, after the pass over Z) are
+    // formed by warp 1 while thread 0 waits at the barrier: one lane per row
+    // computes the row's nine terms, then lane k adds term k over the rows
+    // through shared memory.  The objectives and y^T alpha (which cancels) are
+    // summed in FP64; the terms that only feed a residual in FP32.
+    GDWD_BARRIER_SIDE(6, [&]() {
+      if (warp != 1) return;
+      double* kt = reinterpret_cast<double*>(uni);         // [9][32] terms, then the 9 sums (free until phase B)
+      for (int t0 = 0; t0 < nrows; t0 += 32) {
+        const int t = t0 + lane;
+        double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        if (t < nrows) {
+          const double ri = RS(RS_R, t), an = RS(RS_AL, t), xin = RS(RS_XI, t), res = RS(RS_RES, t);
+          const double yi = RS(RS_Y, t), ce = RS(RS_CE, t), om = RS(RS_OM, t);
+          const double irq1 = rcp_nr(pow_q1(ri, a.q, qcase));
+          const double cma = ce - an;                       // C e_i - alpha_i
+          const float resf = (float)res, dvf = (float)(an - om * irq1), cmaf = (float)cma;
+          const float mn = fminf((float)an, 0.f), mx = fminf(cmaf, 0.f);   // min(alpha, 0), -max(alpha - Ce, 0)
+          v[0] = (double)(resf * resf);
+          v[1] = yi * an;
+          v[2] = (double)((float)xin * cmaf);
+          v[3] = (double)(dvf * dvf);
+          v[4] = (double)(mn * mn);
+          v[5] = (double)(mx * mx);
+          v[6] = om * inv_q * ri * irq1;                    // wt^q r^-q
+          v[7] = RS(RS_E, t) * xin;
+          v[8] = dual_pow(RS(RS_WT, t) * an, a.q, qcase);
+        }
+#pragma unroll
+        for (int k = 0; k < 9; ++k) kt[k * 32 + lane] = v[k];
+        __syncwarp();
+        if (lane < 9) {
+          const int nr = min(32, nrows - t0);
+          double acc = t0 == 0 ? 0.0 : kt[9 * 32 + lane];
+          for (int u = 0; u < nr; ++u) acc += kt[lane * 32 + u];
+          kt[9 * 32 + lane] = acc;
+        }
+        __syncwarp();
+      }
+      if (lane < 9) a.scal[(size_t)lane * grid + cta] = nrows > 0 ? kt[9 * 32 + lane] : 0.0;
+    });
+
 
     // ---------------- phase B (the one pass over Z): deferred (u, rho) update;
     // t = Z~ c, ta = Z~ alpha, g = u - t / mu and the d-space sums; on the same
@@ -527,33 +605,13 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
       CT* av = reinterpret_cast<CT*>(uni + nv * 16);
       const size_t off_red = (size_t)nv * 32;
       double* red = reinterpret_cast<double*>(uni + off_red);
-      CT* up = reinterpret_cast<CT*>(uni + off_red + (size_t)2 * G * TB * sizeof(double));
-      const double rcoef = a.tau * sig_prev * sqmu * (1.0 - theta);
       for (int64_t k = threadIdx.x; k < nv; k += kThreads) {
         reinterpret_cast<uint4*>(cv)[k] = reinterpret_cast<const uint4*>(a.cq)[k];
         reinterpret_cast<uint4*>(av)[k] = reinterpret_cast<const uint4*>(a.aq)[k];
       }
-      for (int k = 0; k < nmy; ++k) {
-        const int64_t s = cta + (int64_t)k * grid;
-        for (int j = threadIdx.x; j < TB; j += kThreads) {
-          const int64_t gj = s * TB + j;
-          double uj = 0.0;
-          if (gj < d) {
-            if (pending) {
-              const double g = a.g[gj];
-              a.rho[gj] = (1.0 - a.tau) * a.rho[gj] - rcoef * g;    // rho <- rho - tau sigma D (w - u+)
-              uj = theta * g;                                       // u+ = Pi_B(g)
-              a.u[gj] = uj;
-            } else {
-              uj = a.u[gj];
-            }
-          }
-          up[(size_t)k * TB + j] = (CT)uj;
-        }
-      }
       __syncthreads();
       GDWD_MARK(16);
-      IterEpi epi{a.g, a.u, a.rho, inv_mu, sqmu * (1.0 - a.tau)};
+      IterEpi epi{a.g, s_u, s_rho, s_g, inv_mu, sqmu * (1.0 - a.tau)};
       PassB<T, IterEpi> pb;
       pb.cv = cv;
       pb.av = av;
@@ -572,7 +630,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
       // U_u follows its recurrence
       dots_prev = dots_now;
       if (dots_prev) {
-        PassA2<T> pa{up, a.partial, TB, NB, Q};
+        PassA2<T> pa{s_up, a.partial, TB, NB, Q};
         PassBA<T, IterEpi> pba{&pb, &pa};
         if (!stream_slabs<T>(L, rg, cta, grid, a.err, a.timeout_ns, &s_abort, pba)) return;
       } else if (fuse_next) {
@@ -601,6 +659,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
     sig_prev = sig;
     theta = s_ctl[0];
     sig = s_ctl[1];
+    inv_sig = s_ctl[2];
     pending = 1;
     const bool done = s_ictl[0] != 0;
     status = s_ictl[1];
@@ -635,6 +694,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
     for (int k = 0; k < kPhaseSlots; ++k) c->phase_ns[k] = (double)s_tacc[k];
   }
 #undef GDWD_BARRIER
+#undef GDWD_BARRIER_SIDE
 #undef GDWD_MARK
 #undef RS
 }
@@ -657,11 +717,14 @@ static size_t pass_bytes(const Layout& L, int grid) {
 // Phase-local region of the iteration kernel plus the resident row state ahead of it.
 template <typename T>
 static size_t union_bytes(const Layout& L, int grid) {
-  size_t r_bytes = (size_t)9 * sizeof(double) * (size_t)((L.n + grid - 1) / grid);   // N2 row sums
+  size_t r_bytes = (size_t)10 * 32 * sizeof(double);                               // N2 KKT terms
   if (r_bytes < (size_t)6 * kThreads * sizeof(double)) r_bytes = (size_t)6 * kThreads * sizeof(double);   // B sums
   size_t u = pass_bytes<T>(L, grid);
   if (r_bytes > u) u = r_bytes;
-  return ((u + 127) & ~(size_t)127) + row_state_bytes((L.n + grid - 1) / grid);
+  using CT = typename ElemTraits<T>::compute_t;
+  const int nslab_rows = (L.NB + grid - 1) / grid * L.TB;
+  return ((u + 127) & ~(size_t)127) + row_state_bytes((L.n + grid - 1) / grid) +
+         slab_state_bytes(nslab_rows, (int)sizeof(CT));
 }
 
 
@@ -700,8 +763,22 @@ static cudaError_t launch_iterate_t(const IterArgs<typename ElemTraits<T>::compu
 // fits in L2 and the pass is served from there, about 64 KB (three or more stages,
 // more copies in flight) when it streams from HBM (measured on the spiked FP32
 // workload at d = 20000 and 40000).
+// The dynamic shared memory the iteration kernel may plan with.  The host's
+// limit leaves 8 KB below the per-block maximum for static shared memory; the
+// kernel's own static size (queried once) is taken if it is larger.
+template <typename T>
+static int iter_smem_limit(int smem_limit) {
+  static int stat = -1;
+  if (stat < 0) {
+    cudaFuncAttributes fa;
+    stat = cudaFuncGetAttributes(&fa, iterate_kernel<T>) == cudaSuccess ? (int)fa.sharedSizeBytes : 16384;
+  }
+  return std::min(smem_limit, smem_limit + 8192 - stat - 256);
+}
+
 template <typename T>
 static int choose_cw_t(const Layout& L, int grid, int smem_limit) {
+  smem_limit = iter_smem_limit<T>(smem_limit);
   const int64_t ub = (int64_t)union_bytes<T>(L, grid);
   const int64_t col_bytes = (int64_t)L.TB * L.esize;
   const int64_t avail = (int64_t)smem_limit - ub - 1024;
@@ -741,6 +818,7 @@ static bool plan_ring(const Layout& L, int grid, int smem_limit, int& stages, in
 cudaError_t run_iterate_f64(const IterArgs<double>& a, int smem_limit, cudaStream_t st) {
   int stages, sb;
   size_t smem;
+  smem_limit = iter_smem_limit<double>(smem_limit);
   if (!plan_ring<double>(a.L, a.grid, smem_limit, stages, sb, smem)) return cudaErrorInvalidConfiguration;
   return launch_iterate_t<double>(a, stages, sb, smem, st);
 }
@@ -749,6 +827,7 @@ template <typename T>
 static cudaError_t run_iterate_ft(const IterArgs<float>& a, int smem_limit, cudaStream_t st) {
   int stages, sb;
   size_t smem;
+  smem_limit = iter_smem_limit<T>(smem_limit);
   if (!plan_ring<T>(a.L, a.grid, smem_limit, stages, sb, smem)) return cudaErrorInvalidConfiguration;
   return launch_iterate_t<T>(a, stages, sb, smem, st);
 }
@@ -768,7 +847,7 @@ cudaError_t run_iterate_f32(int store, const IterArgs<float>& a, int smem_limit,
 // ---------------------------------------------------------------------------
 struct ApplyEpi {
   double* out;
-  __device__ void row(int64_t j, double t, double) { out[j] = t; }
+  __device__ void row(int64_t j, int, double t, double) { out[j] = t; }
 };
 
 template <typename T>

@@ -120,7 +120,7 @@ __device__ __forceinline__ float2 to_f2(double x) {
 __global__ void __launch_bounds__(kThreads, 1) iterate_kern_kernel(KernArgs a) {
   __shared__ int s_flag;
   __shared__ double s_tot[S_COUNT];
-  __shared__ double s_ctl[8];
+  __shared__ double s_ctl[15];
   __shared__ double s_pd[4];     // pobj, dobj, theta, ||w||
   __shared__ float s_etaf[11];   // gap, the nine residuals, kkt
   __shared__ int s_ictl[2];      // done, status

@@ -247,8 +247,9 @@ __device__ __forceinline__ void rows_sum(const double (&v)[N], int tr, bool mine
 // FP64 compare with its select about 200, an FP64 division ~1400: the chain to
 // theta uses one FP32 rsqrt seed and one FP64 Newton step, the expansions are in
 // Horner form, and the sigma rule multiplies by the reciprocal factors.
-// gs = 1 / (sigma sqrt(mu)).  s_ctl receives theta and sigma of the next
-// iteration; s_ictl receives done and the status; s_etaf[10] the kkt value.
+// gs = 1 / (sigma sqrt(mu)).  s_ctl (15 doubles) receives theta, sigma and
+// 1 / sigma of the next iteration; s_ictl receives done and the status;
+// s_etaf[10] the kkt value.
 // With `report` thread 0 also writes the residuals to ctrl (s_report).
 struct SPhaseArgs {
   double C, kappa, R, mu, tau, sqmu, tol, sqrt_tol;
@@ -286,6 +287,13 @@ __device__ __forceinline__ void s_phase(const double* s_tot, const SPhaseArgs& q
                                         double beta, int status, bool report, Ctrl* ctrl, double* s_pd,
                                         float* s_etaf, double* s_ctl, int* s_ictl) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 3 && lane < 7) {
+    // 1 / sigma' for each value the sigma rule can give (sigma times 1, 1.1, 1.65,
+    // 2.2 or their reciprocals): ready before the rule picks one
+    const double m = lane == 0 ? 1.0 : lane == 1 ? 1.1 : lane == 2 ? 1.65 : lane == 3 ? 2.2
+                   : lane == 4 ? (1.0 / 1.1) : lane == 5 ? (1.0 / 1.65) : (1.0 / 2.2);
+    s_ctl[8 + lane] = rcp_nr(sig * m);
+  }
   if (lane == 0 && warp == 1) {
     const double pobj = s_tot[S_PRIM_R] + q.C * s_tot[S_PRIM_XI];
     const double dobj = q.kappa * s_tot[S_DUAL_A] - q.R * sqrt_nr(s_tot[S_TA2]);
@@ -327,6 +335,7 @@ __device__ __forceinline__ void s_phase(const double* s_tot, const SPhaseArgs& q
     const float kkt = fmaxf(fmaxf(ep, ed), fmaxf(ec, gap));
     int done = 0;
     double mult = 1.0;
+    int mi = 0;   // index of mult among the candidates of 1 / sigma'
     if (!(kkt == kkt) || isinf(kkt)) {
       done = 1;
       status = GDWD_ENUMERIC;
@@ -339,11 +348,17 @@ __device__ __forceinline__ void s_phase(const double* s_tot, const SPhaseArgs& q
       const float ichi = __fdividef(ed, fmaxf(ep, 1e-30f));
       const float big = fmaxf(chi, ichi);
       const int zk = big > 500.f ? 2 : (big > 50.f ? 1 : 0);
-      if (chi > 5.f) mult = zk == 2 ? 2.2 : (zk == 1 ? 1.65 : 1.1);
-      else if (ichi > 5.f) mult = zk == 2 ? (1.0 / 2.2) : (zk == 1 ? (1.0 / 1.65) : (1.0 / 1.1));
+      if (chi > 5.f) {
+        mult = zk == 2 ? 2.2 : (zk == 1 ? 1.65 : 1.1);
+        mi = 1 + zk;
+      } else if (ichi > 5.f) {
+        mult = zk == 2 ? (1.0 / 2.2) : (zk == 1 ? (1.0 / 1.65) : (1.0 / 1.1));
+        mi = 4 + zk;
+      }
     }
     s_ctl[0] = s_pd[2];
     s_ctl[1] = sig * mult;
+    s_ctl[2] = s_ctl[8 + mi];   // 1 / sigma'
     s_ictl[0] = done;
     s_ictl[1] = status;
     s_etaf[10] = kkt;
@@ -356,28 +371,31 @@ __device__ __forceinline__ void s_phase(const double* s_tot, const SPhaseArgs& q
 // The row is taken in steps of 128 pairs (four 16-byte loads of P and four of
 // the right-hand side per lane); the next step's eight loads are issued before
 // the current step's products, so one L2 round trip overlaps the next instead
-// of the loop waiting for each in turn.  Pairs past npair read as zero.
+// of the loop waiting for each in turn.  Every load reads inside the row: an
+// index past npair is clamped to the last pair and its value then zeroed.
+__device__ __forceinline__ void row_pair_load(const float4* P4, const float4* R4, int j, int npair, float4& p,
+                                              float4& r) {
+  const int jj = j < npair ? j : npair - 1;
+  p = __ldg(P4 + jj);
+  r = R4[jj];
+  if (j >= npair) {
+    p = make_float4(0.f, 0.f, 0.f, 0.f);
+    r = p;
+  }
+}
+
 __device__ __forceinline__ df row_dot(const float2* __restrict__ Prow, const float2* rhs_s, int npair) {
   const float4* P4 = reinterpret_cast<const float4*>(Prow);
   const float4* R4 = reinterpret_cast<const float4*>(rhs_s);
   df a0{0.f, 0.f}, a1{0.f, 0.f}, a2{0.f, 0.f}, a3{0.f, 0.f};
   const int lane = threadIdx.x & 31;
-  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   float4 p[4], r[4];
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int j = lane + 32 * u;
-    p[u] = j < npair ? __ldg(P4 + j) : z4;
-    r[u] = j < npair ? R4[j] : z4;
-  }
+  for (int u = 0; u < 4; ++u) row_pair_load(P4, R4, lane + 32 * u, npair, p[u], r[u]);
   for (int base = 0; base < npair; base += 128) {
     float4 pn[4], rn[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int j = base + 128 + lane + 32 * u;
-      pn[u] = j < npair ? __ldg(P4 + j) : z4;
-      rn[u] = j < npair ? R4[j] : z4;
-    }
+    for (int u = 0; u < 4; ++u) row_pair_load(P4, R4, base + 128 + lane + 32 * u, npair, pn[u], rn[u]);
     df_fma(a0, df{p[0].x, p[0].y}, df{r[0].x, r[0].y});
     df_fma(a1, df{p[0].z, p[0].w}, df{r[0].z, r[0].w});
     df_fma(a2, df{p[1].x, p[1].y}, df{r[1].x, r[1].y});

@@ -34,18 +34,37 @@ __device__ __forceinline__ void ring_init(Ring& rg) {
   __syncthreads();
 }
 
-// Address and size of chunk c of this CTA's sequence (slab cta + k grid, chunk cc).
-__device__ __forceinline__ void chunk_src(const Layout& L, int cta, int grid, int c, const uint8_t*& src,
-                                          uint32_t& bytes) {
-  const int nch = (int)((L.n + L.CW - 1) / L.CW);
-  const int k = c / nch, cc = c - k * nch;
-  const int64_t s = cta + (int64_t)k * grid;
-  const int64_t col0 = (int64_t)cc * L.CW;
-  const int64_t cw = min((int64_t)L.CW, L.n - col0);
-  const int64_t col_bytes = (int64_t)L.TB * L.esize;
-  bytes = (uint32_t)(cw * col_bytes);
-  src = reinterpret_cast<const uint8_t*>(L.Z) + (s * L.n + col0) * col_bytes;
-}
+// A cursor over the Z chunks of this CTA's sequence (slab cta + k grid, chunk cc
+// of CW columns within it), advanced one chunk at a time with no division: the
+// address of the next copy is ready when the stage it refills frees up.
+struct ZCursor {
+  const uint8_t* slab;   // first byte of the current slab
+  int64_t slab_step;     // bytes from one of this CTA's slabs to the next
+  int64_t chunk_bytes;   // bytes of a full chunk (CW columns)
+  int cc, nch, k;        // chunk within the slab, chunks per slab, slab ordinal
+  uint32_t last_bytes;   // bytes of a slab's last chunk
+  __device__ void init(const Layout& L, int cta, int grid, int first) {
+    const int64_t col_bytes = (int64_t)L.TB * L.esize;
+    nch = (int)((L.n + L.CW - 1) / L.CW);
+    chunk_bytes = (int64_t)L.CW * col_bytes;
+    last_bytes = (uint32_t)((L.n - (int64_t)(nch - 1) * L.CW) * col_bytes);
+    slab_step = (int64_t)grid * L.n * col_bytes;
+    k = first / nch;
+    cc = first - k * nch;
+    slab = reinterpret_cast<const uint8_t*>(L.Z) + ((int64_t)cta + (int64_t)k * grid) * L.n * col_bytes;
+  }
+  __device__ void get(const uint8_t*& src, uint32_t& bytes) const {
+    src = slab + (int64_t)cc * chunk_bytes;
+    bytes = cc == nch - 1 ? last_bytes : (uint32_t)chunk_bytes;
+  }
+  __device__ void advance() {
+    if (++cc == nch) {
+      cc = 0;
+      ++k;
+      slab += slab_step;
+    }
+  }
+};
 
 // Issues the first chunks of the next stream_slabs early (the ring must be idle:
 // every chunk of the previous stream consumed), so that they arrive while the
@@ -56,14 +75,18 @@ __device__ __forceinline__ void ring_prefetch(const Layout& L, Ring& rg, int cta
   const int pre = min(rg.stages, nmy * nch);
   // issued by the last warp: thread 0 holds the first n-space row of the phase
   // that runs meanwhile
-  if (threadIdx.x == kThreads - 32)
+  if (threadIdx.x == kThreads - 32) {
+    ZCursor zc;
+    zc.init(L, cta, grid, 0);
     for (int c = 0; c < pre; ++c) {
       const uint8_t* src;
       uint32_t bytes;
-      chunk_src(L, cta, grid, c, src, bytes);
+      zc.get(src, bytes);
+      zc.advance();
       mbar_expect_tx(&rg.bars[c], bytes);
-      bulk_g2s(rg.buf + (size_t)c * rg.stage_bytes, src, bytes, &rg.bars[c]);
+      bulk_g2s_z(rg.buf + (size_t)c * rg.stage_bytes, src, bytes, &rg.bars[c]);
     }
+  }
   rg.prefetched = pre;
 }
 
@@ -117,6 +140,10 @@ __device__ bool stream_slabs(const Layout& L, Ring& rg, int cta, int grid, int* 
   const int xpos = min(rg.stages, nz);
   const int total = nz + nx;
 
+  // the issue side (thread 0) walks the Z chunks from the first one not yet
+  // issued by ring_prefetch; the extra chunks sit at positions [xpos, xpos + nx)
+  ZCursor iz;
+  if (threadIdx.x == 0) iz.init(L, cta, grid, rg.prefetched);
   auto issue = [&](int c) {
     const int st = c % rg.stages;
     uint8_t* dst = rg.buf + (size_t)st * rg.stage_bytes;
@@ -126,9 +153,10 @@ __device__ bool stream_slabs(const Layout& L, Ring& rg, int cta, int grid, int* 
     }
     const uint8_t* src;
     uint32_t bytes;
-    chunk_src(L, cta, grid, c < xpos ? c : c - nx, src, bytes);
+    iz.get(src, bytes);
+    iz.advance();
     mbar_expect_tx(&rg.bars[st], bytes);
-    bulk_g2s(dst, src, bytes, &rg.bars[st]);
+    bulk_g2s_z(dst, src, bytes, &rg.bars[st]);
   };
 
   if (threadIdx.x == 0) {
@@ -136,11 +164,10 @@ __device__ bool stream_slabs(const Layout& L, Ring& rg, int cta, int grid, int* 
     for (int c = rg.prefetched; c < pre; ++c) issue(c);
   }
   rg.prefetched = 0;
+  int k = 0, cc = 0;   // slab ordinal and chunk of the next Z chunk consumed
   for (int c = 0; c < total; ++c) {
     const int st = c % rg.stages;
     const bool extra = c >= xpos && c < xpos + nx;
-    const int cz = c < xpos ? c : c - nx;   // index among the Z chunks
-    const int k = cz / nch, cc = cz - k * nch;
     const int s = cta + k * grid;
     const int col0 = cc * L.CW;
     const int cw = (int)min((int64_t)L.CW, L.n - col0);
@@ -156,7 +183,13 @@ __device__ bool stream_slabs(const Layout& L, Ring& rg, int cta, int grid, int* 
       return false;
     }
     if (threadIdx.x == 0 && c + rg.stages < total) issue(c + rg.stages);
-    if (!extra && cc == nch - 1) f.end_slab(k, s);
+    if (!extra) {
+      if (cc == nch - 1) f.end_slab(k, s);
+      if (++cc == nch) {
+        cc = 0;
+        ++k;
+      }
+    }
   }
   return true;
 }
@@ -283,15 +316,21 @@ template <typename CT>
 struct RunAcc;
 template <>
 struct RunAcc<double> {
+  using part_t = double;   // what the end-of-slab reduction stores per group
   double v = 0.0;
   __device__ void fold(double c) { v += c; }
+  __device__ void merge(part_t p) { v += p; }
+  __device__ part_t part() const { return v; }
   __device__ double get() const { return v; }
   __device__ void reset() { v = 0.0; }
 };
 template <>
 struct RunAcc<float> {
+  using part_t = float2;   // (hi, lo): the groups are added in double-float, FP32 pipes only
   df v{0.f, 0.f};
   __device__ void fold(float c) { df_add(v, c); }
+  __device__ void merge(part_t p) { df_add(v, df{p.x, p.y}); }
+  __device__ part_t part() const { return make_float2(v.hi, v.lo); }
   __device__ double get() const { return df_to_double(v); }
   __device__ void reset() { v.hi = 0.f; v.lo = 0.f; }
 };
@@ -301,7 +340,8 @@ struct RunAcc<float> {
 // Thread t owns vector qv = t % Q of the column group t / Q (Q = TB / VEC <= 256),
 // so the threads of a step read consecutive 16-byte vectors (conflict-free).
 // At the end of a slab the groups are summed through shared memory and the
-// row epilogue Epi runs once per row j of the slab with t_j and ta_j.
+// row epilogue Epi runs once per row j of the slab with t_j and ta_j (given the
+// global row and its index among the CTA's slab rows, k * TB + j for its k-th slab).
 // ---------------------------------------------------------------------------
 template <typename T, typename Epi>
 struct PassB {
@@ -387,25 +427,27 @@ struct PassB {
   }
 
   __device__ void end_slab(int k, int s) {
+    using P = typename RunAcc<CT>::part_t;
+    P* redp = reinterpret_cast<P*>(red);   // 2 G TB parts (8 bytes each, like the doubles it was sized for)
     const int grp = threadIdx.x / Q, qv = threadIdx.x - grp * Q;
     if (grp < G) {
 #pragma unroll
       for (int kk = 0; kk < VEC; ++kk) {
-        red[(size_t)grp * TB + qv * VEC + kk] = rc[kk].get();
-        red[(size_t)(G + grp) * TB + qv * VEC + kk] = ra[kk].get();
+        redp[(size_t)grp * TB + qv * VEC + kk] = rc[kk].part();
+        redp[(size_t)(G + grp) * TB + qv * VEC + kk] = ra[kk].part();
         rc[kk].reset();
         ra[kk].reset();
       }
     }
     __syncthreads();
     for (int j = threadIdx.x; j < TB; j += blockDim.x) {
-      double t = 0.0, ta = 0.0;
+      RunAcc<CT> t, ta;
       for (int gq = 0; gq < G; ++gq) {
-        t += red[(size_t)gq * TB + j];
-        ta += red[(size_t)(G + gq) * TB + j];
+        t.merge(redp[(size_t)gq * TB + j]);
+        ta.merge(redp[(size_t)(G + gq) * TB + j]);
       }
       const int64_t gj = (int64_t)s * TB + j;
-      if (gj < d) epi->row(gj, t, ta);
+      if (gj < d) epi->row(gj, k * TB + j, t.get(), ta.get());
     }
     __syncthreads();
   }

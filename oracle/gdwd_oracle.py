@@ -253,6 +253,67 @@ class Direct:
         return solve_triangular(self.L.T, z, lower=False)
 
 
+class LinsysOperator:
+    """eq-linsys with T = 0 as a matrix-free operator (Sec. 3.3.3):
+    A [w; beta] = [Z (Z^T w + y beta) + mu w; y^T (Z^T w + y beta)], two products
+    with Z (4nd flops) per application.  A = U U^T + diag(mu I_d, 0) with
+    U = [Z; y^T], so A is symmetric positive definite (for [w; beta] != 0 the
+    quadratic form is ||Z^T w + beta y||^2 + mu ||w||^2 > 0)."""
+
+    def __init__(self, Z, y, mu):
+        self.Z = np.asarray(Z, dtype=np.float64)
+        self.y = np.asarray(y, dtype=np.float64)
+        self.mu = float(mu)
+        self.d = self.Z.shape[0]
+
+    def matvec(self, v):
+        t = self.Z.T @ v[: self.d] + self.y * v[self.d]
+        return np.concatenate([self.Z @ t + self.mu * v[: self.d], [self.y @ t]])
+
+    def diagonal(self):
+        """diag(A): the Jacobi preconditioner."""
+        return np.concatenate([np.sum(self.Z * self.Z, axis=1) + self.mu, [self.y @ self.y]])
+
+
+def pcg(op, h, x0, tol, max_steps=10000):
+    """Preconditioned conjugate gradients (Jacobi: M = diag(A)) for the symmetric
+    positive definite eq-linsys, started at x0 and stopped once the residual meets
+    the accuracy condition ||h - A x|| <= tol (eq-linsys-tol).  Returns
+    (x, ||h - A x||, steps).  The paper's own Krylov solver (PSQMR) is described in
+    an appendix that is not part of the text; for an SPD system CG is the method
+    of that family with the same cost per step (one product with A)."""
+    m = op.diagonal()
+    x = np.array(x0, dtype=np.float64)
+    r = h - op.matvec(x)
+    rn = np.linalg.norm(r)
+    steps = 0
+    if rn <= tol:
+        return x, rn, 0
+    z = r / m
+    p = z.copy()
+    rz = r @ z
+    while steps < max_steps:
+        Ap = op.matvec(p)
+        a = rz / (p @ Ap)
+        x += a * p
+        r -= a * Ap
+        steps += 1
+        rn = np.linalg.norm(r)
+        if rn <= tol:
+            break
+        z = r / m
+        rz_new = r @ z
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return x, np.linalg.norm(h - op.matvec(x)), steps
+
+
+def eps_schedule(k, c):
+    """The summable tolerances of Algorithm 1: eps_k = c / (k + 1)^1.5 (Sec. 3, after
+    Algorithm 1; c inversely proportional to the Frobenius norm of the data)."""
+    return c / (k + 1.0) ** 1.5
+
+
 # --------------------------------------------------------------------------
 # r-subproblem (Step 1b, eq-1c / eq-varphi, Sec. 3.2)
 # --------------------------------------------------------------------------
@@ -466,4 +527,88 @@ def solve(Z, y, q, C, mu=1.0, tau=1.618, tol=1e-9, max_iter=50000, sigma0=None,
         "w_scaled": w, "u_scaled": u, "rho": rho, "zscale": zs, "sigma": sigma,
         "iters": k + 1, "converged": converged, "eta": eta, "primal": pobj, "dual": dobj,
         "history": history,
+    }
+
+
+def solve_inexact(Z, y, q, C, mu=1.0, tau=1.618, tol=1e-9, max_iter=50000, sigma0=None, e=None, wt=None,
+                  eps_c=None, record=False):
+    """Algorithm 1 with inexact solves of eq-linsys (Sec. 3, Steps 1a-1c; Sec. 3.3.3,
+    the case where d and n are both large, T = 0): no n x n or d x d matrix is formed.
+
+    Step 1a solves eq-linsys by PCG to ||h-bar - A [w-bar; beta-bar]|| <= eps_k
+    (eq-linsys-tol), warm-started at the last (w, beta).  Step 1c first tests Step
+    1a's solution against the new right-hand side h (r^k replaced by r^{k+1}): if
+    ||h - A [w-bar; beta-bar]|| <= 5 eps_k it is kept and the solve is skipped,
+    else PCG continues from it to 5 eps_k.  eps_k = c / (k+1)^1.5 with
+    c = eps_c, by default 1 / ||Z~||_F (the paper fixes c only up to this
+    proportionality).  Returns solve()'s dict plus "cg_steps" (all PCG steps) and
+    "step1c_solves" (iterations in which Step 1c had to solve: the paper's
+    "double" count).
+    """
+    Z = np.asarray(Z, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    d, n = Z.shape
+    e = np.ones(n) if e is None else np.asarray(e, dtype=np.float64)
+    wt = np.ones(n) if wt is None else np.asarray(wt, dtype=np.float64)
+    omega = q * wt ** q
+    Zt, zs = scale_data(Z)
+    op = LinsysOperator(Zt, y, mu)
+    D = math.sqrt(mu)
+    c_eps = (1.0 / np.linalg.norm(Zt)) if eps_c is None else float(eps_c)
+
+    r = np.ones(n)
+    xi = np.ones(n)
+    w = np.zeros(d)
+    u = np.zeros(d)
+    beta = 0.0
+    alpha = np.zeros(n)
+    rho = np.zeros(d)
+    sigma = float(sigma0) if sigma0 is not None and sigma0 > 0 else min(10.0 * C, n) ** q
+    history = []
+    eta = None
+    pobj = dobj = float("nan")
+    cg_steps = 0
+    solves_1c = 0
+    k = 0
+    for k in range(max_iter):
+        eps_k = eps_schedule(k, c_eps)
+        # Step 1a
+        v = xi - r - alpha / sigma
+        hbar = np.concatenate([-Zt @ v + mu * u + D * rho / sigma, [-(y @ v)]])
+        sol, _, st = pcg(op, hbar, np.concatenate([w, [beta]]), eps_k)
+        cg_steps += st
+        wbar, betabar = sol[:d], sol[d]
+        # Step 1b
+        ck = Zt.T @ wbar + y * betabar + xi - alpha / sigma
+        r = prox_r(ck, sigma, q, r0=r, omega=omega)
+        # Step 1c: keep Step 1a's solution if it is accurate enough for the new h
+        v = xi - r - alpha / sigma
+        h = np.concatenate([-Zt @ v + mu * u + D * rho / sigma, [-(y @ v)]])
+        if np.linalg.norm(h - op.matvec(sol)) > 5.0 * eps_k:
+            sol, _, st = pcg(op, h, sol, 5.0 * eps_k)
+            cg_steps += st
+            solves_1c += 1
+        w, beta = sol[:d], sol[d]
+        # Step 2
+        g = w - rho / (sigma * D)
+        gn = np.linalg.norm(g)
+        u = g if gn <= zs else g * (zs / gn)
+        ztw = Zt.T @ w
+        xi = np.maximum(0.0, r - ztw - y * beta + alpha / sigma - C * e / sigma)
+        # Step 3
+        alpha = alpha - tau * sigma * (ztw + y * beta + xi - r)
+        rho = rho - tau * sigma * D * (w - u)
+        eta, pobj, dobj = kkt_residuals(Zt, zs, y, q, C, mu, r, w, beta, xi, u, alpha, rho, e, wt)
+        if record:
+            history.append((sigma, eta["kkt"], eta["P"], eta["D"], eps_k))
+        if eta["kkt"] <= tol:
+            break
+        if k >= 1 and min(eta["P"], eta["D"]) > 1e-3 * tol:
+            sigma = sigma_update(sigma, eta["P"], eta["D"])
+    converged = eta is not None and eta["kkt"] <= tol
+    return {
+        "w": w / zs, "beta": float(beta), "r": r, "xi": xi, "alpha": alpha,
+        "w_scaled": w, "u_scaled": u, "rho": rho, "zscale": zs, "sigma": sigma,
+        "iters": k + 1, "converged": converged, "eta": eta, "primal": pobj, "dual": dobj,
+        "history": history, "cg_steps": cg_steps, "step1c_solves": solves_1c, "eps_c": c_eps,
     }

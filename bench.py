@@ -222,7 +222,7 @@ def main():
     ap.add_argument("--n", type=int, default=1000, help="sample count (profiling of other sizes only)")
     ap.add_argument("--workload", default="spiked_fp32",
                     help="spiked_fp32 (default line) | plain_fp64 | cgrid_bf16 | uneven_batch | served | largest_fp8 | "
-                         "kernelized | direct_fp32")
+                         "kernelized | direct_fp32 | hbm_stream")
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--serve-seconds", type=float, default=10.0)

@@ -390,7 +390,8 @@ def direct_fp32(args, gdwd, synth):
 
 
 WORKLOADS = {"plain_fp64": plain_fp64, "cgrid_bf16": cgrid_bf16, "uneven_batch": uneven_batch, "served": served,
-             "largest_fp8": largest_fp8, "kernelized": kernelized, "direct_fp32": direct_fp32}
+             "largest_fp8": largest_fp8, "kernelized": kernelized, "direct_fp32": direct_fp32,
+             "hbm_stream": lambda args, gdwd, synth: dict(metric="Z-stream GB/s of the iteration kernel (BF16 Z 200 MB)", **hbm_stream(gdwd, synth))}
 
 
 def run(name, args):

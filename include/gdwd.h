@@ -93,8 +93,12 @@ typedef struct {
                          pass over Z serves all of them; 1: one C at a time.         */
   int32_t gram_path;  /* 0 (default): the Gram of BF16, F16 and E4M3 storage runs on
                          the tensor cores (tcgen05.mma; exact products, FP32 sums of at
-                         most 256 rows folded into double-float), F32 / F64 on the SIMT
-                         double-float kernel; 1: the SIMT kernel for every storage.  */
+                         most 256 rows folded into double-float); F32 storage too,
+                         through a three-term BF16 split of each value (six exact
+                         products per pair, the dropped terms below 2^-23 of the
+                         product; a temporary 6 d n bytes during gdwd_create); F64
+                         on the SIMT FP64 kernel; 1: the SIMT kernel for every
+                         storage.  */
   int32_t stop_rule;  /* 0 (default): stop when kkt = max(eta_P, eta_D, eta_C, eta_gap)
                          <= tol; 1: the rule of Sec. 4.3: max(eta_P, eta_D) < tol,
                          min(eta_C, eta_gap) < sqrt(tol) and max(eta_C, eta_gap) < 0.05
@@ -128,7 +132,19 @@ typedef struct {
                          solver = 1: F32 or F64 storage, refine = 0 and kernelized =
                          0 (else EUNSUPPORTED); gdwd_apply,
                          gdwd_get_stored and gdwd_suggest_C return EUNSUPPORTED and
-                         gdwd_gram returns the d x d matrix I + Z~ Z~^T / mu.      */
+                         gdwd_gram returns the d x d matrix I + Z~ Z~^T / mu.
+                         2: the inexact solver for d and n both large (Sec. 3.3.3
+                         with T = 0): no n x n or d x d matrix is formed; Steps 1a
+                         and 1c solve eq-linsys by Jacobi-preconditioned conjugate
+                         gradients on the matrix-free (d+1) x (d+1) operator (two
+                         passes over the stored Z per step) to the accuracy
+                         eq-linsys-tol with eps_k = c / (k+1)^1.5, c = 1 / ||Z~||_F
+                         (Algorithm 1), and Step 1c reuses Step 1a's solution when it
+                         already meets 5 eps_k for the new right-hand side.  F32 or
+                         F64 storage, refine = 0, kernelized = 0 (else
+                         EUNSUPPORTED); gdwd_gram and gdwd_suggest_C return
+                         EUNSUPPORTED; gdwd_result.reserved[1] holds the CG steps
+                         and reserved[2] the iterations in which Step 1c solved. */
   int32_t reserved_i32;
   int64_t reserved[4];
 } gdwd_options;

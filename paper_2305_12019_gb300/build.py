@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgdwd.so")
 SOURCES = ["api.cu", "setup.cu", "iterate.cu", "iterate_kern.cu", "iterate_multi.cu", "direct.cu", "server.cu",
-           "noalloc.cu", "gram_tc.cu"]
+           "noalloc.cu", "gram_tc.cu", "inexact.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

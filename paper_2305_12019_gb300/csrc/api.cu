@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "direct.cuh"
+#include "inexact.cuh"
 #include "iterate_kern.cuh"
 #include "solver.cuh"
 
@@ -70,6 +71,13 @@ struct gdwd_handle {
   // direct solver (opt.solver = 1): Z^T is the stored matrix (samples as rows);
   // G, P, p, pdf are d x d / d-long; the state of Algorithm 1 in d-space
   bool direct = false;
+  // inexact solver (opt.solver = 2): no n x n or d x d matrix; eq-linsys by CG
+  bool inexact = false;
+  double *mw = nullptr, *ztw = nullptr, *ixw = nullptr;
+  double *ixv = nullptr, *ixtn = nullptr, *ixzp = nullptr, *ixdr = nullptr;
+  double *ixhw = nullptr, *ixcr = nullptr, *ixcz = nullptr, *ixcp = nullptr, *ixcap = nullptr, *ixtd = nullptr;
+  double* ixpart = nullptr;
+  std::vector<double> ixhpart;
   double *bhat = nullptr, *t = nullptr, *dv = nullptr, *dv2 = nullptr, *dw = nullptr, *dx = nullptr;
   double *Zxr = nullptr, *Za = nullptr, *Zdr = nullptr, *dscal = nullptr;
   float2* hw = nullptr;
@@ -200,7 +208,8 @@ static void plan_layout(gdwd_handle* h, int64_t rows, int64_t cols) {
   h->L.esize = es;
   h->grid = (int)std::min<int64_t>(gp, std::max<int64_t>(NB, (cols + kWarps - 1) / kWarps));
   h->grid = std::max(h->grid, 1);
-  h->L.CW = choose_chunk_cols(h->store, h->L, h->grid, h->smem_optin - 8192);
+  // the inexact solver streams FP32 storage into FP64 arithmetic (wider staging)
+  h->L.CW = choose_chunk_cols(h->store, h->L, h->grid, h->smem_optin - 8192, h->inexact);
 }
 
 static cudaError_t dir_apply(int trans, const double* x, double* out, void* ctx);
@@ -309,11 +318,16 @@ static gdwd_status create_direct(gdwd_handle* h, const void* Z, int zdt, int64_t
   // G' = I + Z~ Z~^T / mu: the Gram of the stored Z^T
   CK(cudaEventRecord(evg, h->stream), "cudaEventRecord");
   const bool tc = h->opt.gram_path == 0 && gram_tc_supported(h->store, h->L);
-  const int ks = tc ? gram_tc_ksplit(h->L, h->sms) : gram_ksplit(h->L, h->sms);
+  const int ks = tc ? gram_tc_ksplit(h->store, h->L, h->sms) : gram_ksplit(h->L, h->sms);
   double* Kpart = nullptr;
   CK(dev_alloc(h, (void**)&Kpart, (size_t)ks * d * d * sizeof(double)), "cudaMalloc(Kpart)");
-  cudaError_t eg = run_gram(h->store, h->L, ks, Kpart, h->sc, h->opt.mu, h->G, tc, h->err,
-                            (uint64_t)(h->opt.timeout_s * 1e9), h->stream);
+  void* gscratch = nullptr;
+  const size_t gsb = tc ? gram_tc_scratch_bytes(h->store, h->L) : 0;
+  cudaError_t eg = gsb ? dev_alloc(h, &gscratch, gsb) : cudaSuccess;
+  if (eg == cudaSuccess)
+    eg = run_gram(h->store, h->L, ks, Kpart, h->sc, h->opt.mu, h->G, tc, gscratch, h->err,
+                  (uint64_t)(h->opt.timeout_s * 1e9), h->stream);
+  if (gscratch) cudaFreeAsync(gscratch, h->stream);
   if (eg == cudaSuccess) {
     CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream), "memset");
     eg = dir_apply(1, h->y, h->bhat, h);   // b^ = Z~ y
@@ -395,7 +409,10 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
   if (opt.stop_rule != 0 && opt.stop_rule != 1) return fail(nullptr, GDWD_EINVAL, "gdwd_create: stop_rule must be 0 or 1");
   if (opt.dots_every < 0) return fail(nullptr, GDWD_EINVAL, "gdwd_create: dots_every must be >= 0");
   if (opt.kernelized != 0 && opt.kernelized != 1) return fail(nullptr, GDWD_EINVAL, "gdwd_create: kernelized must be 0 or 1");
-  if (opt.solver != 0 && opt.solver != 1) return fail(nullptr, GDWD_EINVAL, "gdwd_create: solver must be 0 or 1");
+  if (opt.solver < 0 || opt.solver > 2) return fail(nullptr, GDWD_EINVAL, "gdwd_create: solver must be 0, 1 or 2");
+  if (opt.solver == 2 && (opt.refine || opt.kernelized || (opt.store != GDWD_F32 && opt.store != GDWD_F64)))
+    return fail(nullptr, GDWD_EUNSUPPORTED,
+                "gdwd_create: the inexact solver runs with F32 or F64 storage, without refine and kernelized");
   if (opt.solver == 1 && (opt.refine || opt.kernelized || (opt.store != GDWD_F32 && opt.store != GDWD_F64)))
     return fail(nullptr, GDWD_EUNSUPPORTED,
                 "gdwd_create: the direct solver runs with F32 or F64 storage, without refine and kernelized");
@@ -442,8 +459,9 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
     *out = h;
     return GDWD_OK;
   }
+  h->inexact = opt.solver == 2;
   plan_layout(h, d, n);
-  if ((n + h->grid - 1) / h->grid > kMaxRowsPerCta)
+  if (!h->inexact && (n + h->grid - 1) / h->grid > kMaxRowsPerCta)
     return bail(fail(nullptr, GDWD_EUNSUPPORTED, "gdwd_create: n too large for the n x n factor path of this build"));
   if (opt.kernelized && n > kern_max_n(h->grid, h->smem_optin - 16384))
     return bail(fail(nullptr, GDWD_EUNSUPPORTED, "gdwd_create: n too large for the kernelized iteration"));
@@ -472,25 +490,33 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
     CK(halloc(h, &h->e, n), "alloc");
     CK(halloc(h, &h->omega, n), "alloc");
     CK(halloc(h, &h->wt, n), "alloc");
-    CK(halloc(h, &h->p, n), "alloc");
-    CK(halloc(h, &h->G, (size_t)n * n), "alloc(G)");
-    CK(halloc(h, &h->P, (size_t)n * h->ldP), "alloc(P)");
-    CK(halloc(h, &h->pdf, h->ldP), "alloc");   // padded to ldP (a zero pair for odd n): read as a G^{-1} row
-    CK(cudaMemsetAsync(h->pdf, 0, (size_t)h->ldP * sizeof(float2), h->stream), "memset");
     CK(halloc(h, &h->r, n), "alloc");
     CK(halloc(h, &h->xi, n), "alloc");
     CK(halloc(h, &h->alpha, n), "alloc");
-    CK(halloc(h, &h->b, n), "alloc");
-    CK(halloc(h, &h->rhsA, h->ldP), "alloc");   // padded to ldP (zero pair): read as pairs
-    CK(halloc(h, &h->Uu, n), "alloc");
-    CK(halloc(h, &h->Ur, n), "alloc");
-    CK(halloc(h, &h->kc, n), "alloc");
-    CK(halloc(h, &h->rhsB, h->ldP), "alloc");
-    // right-hand sides of the fused first solve, [3][ldP], padding zero
-    CK(halloc(h, &h->vrhs, (size_t)3 * h->ldP), "alloc");
-    const size_t ct = h->store == GDWD_F64 ? 8 : 4;
-    CK(halloc(h, (uint8_t**)&h->cq, (n * ct + 15) / 16 * 16), "alloc");   // copied in 16-byte pieces
-    CK(halloc(h, (uint8_t**)&h->aq, (n * ct + 15) / 16 * 16), "alloc");
+    const size_t ct = (h->store == GDWD_F64 || h->inexact) ? 8 : 4;   // the inexact solver's products are FP64
+    if (!h->inexact) {
+      CK(halloc(h, &h->p, n), "alloc");
+      CK(halloc(h, &h->G, (size_t)n * n), "alloc(G)");
+      CK(halloc(h, &h->P, (size_t)n * h->ldP), "alloc(P)");
+      CK(halloc(h, &h->pdf, h->ldP), "alloc");   // padded to ldP (a zero pair for odd n): read as a G^{-1} row
+      CK(cudaMemsetAsync(h->pdf, 0, (size_t)h->ldP * sizeof(float2), h->stream), "memset");
+      CK(halloc(h, &h->b, n), "alloc");
+      CK(halloc(h, &h->rhsA, h->ldP), "alloc");   // padded to ldP (zero pair): read as pairs
+      CK(halloc(h, &h->Uu, n), "alloc");
+      CK(halloc(h, &h->Ur, n), "alloc");
+      CK(halloc(h, &h->kc, n), "alloc");
+      CK(halloc(h, &h->rhsB, h->ldP), "alloc");
+      // right-hand sides of the fused first solve, [3][ldP], padding zero
+      CK(halloc(h, &h->vrhs, (size_t)3 * h->ldP), "alloc");
+      CK(halloc(h, (uint8_t**)&h->cq, (n * ct + 15) / 16 * 16), "alloc");   // copied in 16-byte pieces
+      CK(halloc(h, (uint8_t**)&h->aq, (n * ct + 15) / 16 * 16), "alloc");
+    } else {
+      for (double** pp : {&h->ztw, &h->ixv, &h->ixtn, &h->ixzp, &h->ixdr}) CK(halloc(h, pp, n), "alloc");
+      for (double** pp : {&h->mw, &h->ixw, &h->ixhw, &h->ixcr, &h->ixcz, &h->ixcp, &h->ixcap, &h->ixtd})
+        CK(halloc(h, pp, dpad), "alloc");
+      CK(halloc(h, &h->ixpart, (size_t)kIxSlots * kIxBlocks), "alloc");
+      h->ixhpart.assign((size_t)kIxSlots * kIxBlocks, 0.0);
+    }
     CK(halloc(h, (uint8_t**)&h->partial, (size_t)n * h->L.NB * ct), "alloc");
     CK(halloc(h, &h->u, dpad), "alloc");
     CK(halloc(h, &h->rho, dpad), "alloc");
@@ -532,34 +558,62 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
       zsrc = staging;
       ld = d;
     }
+    // The set-up runs as one stream of kernels with a single synchronisation at
+    // the end; the non-finite flag (err[1]) and the kernels' status (err[0]) are
+    // read there.  Data with a non-finite entry still flows through the Gram and
+    // the factor (whose bounded waits and pivot checks keep them finite in time)
+    // and is refused at the end.
     const int nparts = 1024;
     double* part = nullptr;
-    int* nonfinite = h->err;
+    int* nonfinite = h->err + 1;
     CK(dev_alloc(h, (void**)&part, nparts * sizeof(double)), "cudaMalloc");
     cudaError_t ei = run_ingest(zsrc, zdt, ld, h->L, h->Z, h->store, part, nparts, h->dscalars, nonfinite, h->sc,
                                 h->dscalars + 1, h->amax, h->colscale, h->stream);
-    int nf = 0;
-    if (ei == cudaSuccess) ei = cudaMemcpyAsync(&nf, nonfinite, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
-    if (ei == cudaSuccess) ei = cudaStreamSynchronize(h->stream);
     cudaFreeAsync(part, h->stream);
     if (staging) cudaFreeAsync(staging, h->stream);
     if (ei != cudaSuccess) return cuda_fail(h, ei, "ingest");
-    if (nf) return fail(h, GDWD_EINVAL, "gdwd_create: Z has non-finite entries");
-    CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream), "memset");
+    if (h->inexact) {
+      int nf = 0;
+      CK(cudaMemcpyAsync(&nf, nonfinite, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "copy");
+      CK(cudaStreamSynchronize(h->stream), "sync");
+      if (nf) return fail(h, GDWD_EINVAL, "gdwd_create: Z has non-finite entries");
+      // no Gram and no factor: the Jacobi preconditioner diag(Z~ Z~^T) + mu and Z_scale
+      CK(cudaEventRecord(evg, h->stream), "cudaEventRecord");
+      CK(run_row_sumsq(h->store, h->L, h->sc, h->opt.mu, h->mw, h->stream), "preconditioner");
+      double hs[2] = {0, 0};
+      CK(cudaMemcpyAsync(hs, h->dscalars, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy");
+      CK(cudaEventRecord(e1, h->stream), "cudaEventRecord");
+      CK(cudaStreamSynchronize(h->stream), "sync");
+      h->zscale = hs[1];
+      float ms = 0.f, m1 = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      cudaEventElapsedTime(&m1, e0, evg);
+      h->t_setup_ms = ms;
+      h->t_stage_ms[0] = m1;
+      h->t_stage_ms[1] = ms - m1;
+      h->t_stage_ms[2] = 0.0;
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      cudaEventDestroy(evg);
+      cudaEventDestroy(ef0);
+      if (!(h->zscale > 0.0) || !std::isfinite(h->zscale)) return fail(h, GDWD_EINVAL, "gdwd_create: Z is zero");
+      return GDWD_OK;
+    }
     // Gram and G = I + K / mu
     CK(cudaEventRecord(evg, h->stream), "cudaEventRecord");
     const bool tc = h->opt.gram_path == 0 && gram_tc_supported(h->store, h->L);
-    const int ks = tc ? gram_tc_ksplit(h->L, h->sms) : gram_ksplit(h->L, h->sms);
+    const int ks = tc ? gram_tc_ksplit(h->store, h->L, h->sms) : gram_ksplit(h->L, h->sms);
     double* Kpart = nullptr;
     CK(dev_alloc(h, (void**)&Kpart, (size_t)ks * n * n * sizeof(double)), "cudaMalloc(Kpart)");
-    cudaError_t eg = run_gram(h->store, h->L, ks, Kpart, h->sc, h->opt.mu, h->G, tc, h->err,
-                              (uint64_t)(h->opt.timeout_s * 1e9), h->stream);
-    int gerr = 0;
-    if (eg == cudaSuccess) eg = cudaMemcpyAsync(&gerr, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
-    if (eg == cudaSuccess) eg = cudaStreamSynchronize(h->stream);
+    void* gscratch = nullptr;     // the BF16 split of FP32 storage for the tensor-core Gram
+    const size_t gsb = tc ? gram_tc_scratch_bytes(h->store, h->L) : 0;
+    cudaError_t eg = gsb ? dev_alloc(h, &gscratch, gsb) : cudaSuccess;
+    if (eg == cudaSuccess)
+      eg = run_gram(h->store, h->L, ks, Kpart, h->sc, h->opt.mu, h->G, tc, gscratch, h->err,
+                    (uint64_t)(h->opt.timeout_s * 1e9), h->stream);
+    if (gscratch) cudaFreeAsync(gscratch, h->stream);
     cudaFreeAsync(Kpart, h->stream);
     if (eg != cudaSuccess) return cuda_fail(h, eg, "gram");
-    if (gerr) return fail(h, (gdwd_status)gerr, "gdwd_create: the Gram kernel timed out");
     h->gram_tc = tc;
     // Cholesky, inverse, p, s
     CK(cudaEventRecord(ef0, h->stream), "cudaEventRecord");
@@ -574,8 +628,8 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
       ef = run_factor(fa, h->stream);
     }
     if (ef == cudaSuccess && h->opt.kernelized) ef = run_kern_matrix(h->G, n, h->ldP, h->opt.mu, h->Kd, h->stream);
-    int ferr = 0;
-    if (ef == cudaSuccess) ef = cudaMemcpyAsync(&ferr, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    int flags[2] = {0, 0};
+    if (ef == cudaSuccess) ef = cudaMemcpyAsync(flags, h->err, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     double hs[3] = {0, 0, 0};
     if (ef == cudaSuccess) ef = cudaMemcpyAsync(hs, h->dscalars, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     if (ef == cudaSuccess) ef = cudaEventRecord(e1, h->stream);
@@ -583,8 +637,9 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
     cudaFreeAsync(A, h->stream);
     cudaFreeAsync(X, h->stream);
     if (ef != cudaSuccess) return cuda_fail(h, ef, "factor");
-    if (ferr == GDWD_ENOTPD) return fail(h, GDWD_ENOTPD, "gdwd_create: Cholesky met a non-positive pivot");
-    if (ferr) return fail(h, (gdwd_status)ferr, "gdwd_create: factor kernel reported an error");
+    if (flags[1]) return fail(h, GDWD_EINVAL, "gdwd_create: Z has non-finite entries");
+    if (flags[0] == GDWD_ENOTPD) return fail(h, GDWD_ENOTPD, "gdwd_create: Cholesky met a non-positive pivot");
+    if (flags[0]) return fail(h, (gdwd_status)flags[0], "gdwd_create: the Gram or factor kernel reported an error");
     h->zscale = hs[1];
     h->s = hs[2];
     float ms = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
@@ -975,6 +1030,109 @@ static gdwd_status solve_one(gdwd_handle* h, double C, double* w, int w_on_devic
   return s;
 }
 
+// The inexact solver (solver = 2): products with the stored data by the
+// streaming kernels; trans != 0 gives Z~^T x, trans == 0 gives Z~ x.
+static cudaError_t ix_apply(int trans, const double* x, double* out, void* ctx) {
+  gdwd_handle* h = static_cast<gdwd_handle*>(ctx);
+  return run_apply(h->store, h->L, trans, x, h->sc, out, h->partial, std::min(h->L.NB, 4096), h->smem_optin - 8192,
+                   h->err, (uint64_t)(h->opt.timeout_s * 1e9), h->stream, true);
+}
+
+static gdwd_status solve_inexact(gdwd_handle* h, double C, double* w, int w_on_device, double* alpha,
+                                 gdwd_result* res) {
+  const int64_t n = h->n, d = h->d, dpad = (int64_t)h->L.NB * h->L.TB;
+  cudaStream_t st = h->stream;
+  const double sigma0 = h->opt.sigma0 > 0 ? h->opt.sigma0 : std::pow(std::min(10.0 * C, (double)n), h->q);
+  // initial iterate: r = xi = 1, w = u = 0, beta = 0, alpha = 0, rho = 0
+  const int fb = (int)std::min<int64_t>((n + 255) / 256, 1024);
+  fill_kernel<<<fb, 256, 0, st>>>(h->r, n, 1.0);
+  fill_kernel<<<fb, 256, 0, st>>>(h->xi, n, 1.0);
+  CK(cudaMemsetAsync(h->alpha, 0, n * sizeof(double), st), "memset");
+  CK(cudaMemsetAsync(h->ixw, 0, dpad * sizeof(double), st), "memset");
+  CK(cudaMemsetAsync(h->u, 0, dpad * sizeof(double), st), "memset");
+  CK(cudaMemsetAsync(h->rho, 0, dpad * sizeof(double), st), "memset");
+  CK(cudaMemsetAsync(h->ztw, 0, n * sizeof(double), st), "memset");
+  CK(cudaMemsetAsync(h->err, 0, sizeof(int), st), "memset");
+  IxArgs a{};
+  a.d = d;
+  a.n = n;
+  a.y = h->y;
+  a.e = h->e;
+  a.omega = h->omega;
+  a.wt = h->wt;
+  a.mw = h->mw;
+  a.q = h->q;
+  a.C = C;
+  a.mu = h->opt.mu;
+  a.tau = h->opt.tau;
+  a.R = h->zscale;
+  a.tol = h->opt.tol;
+  a.kappa = (h->q + 1.0) / h->q * std::pow(h->q, 1.0 / (h->q + 1.0));
+  a.eps_c = 1.0 / h->zscale;   // 1 / ||Z~||_F: ||Z~||_F = ||Z||_F / Z_scale = Z_scale
+  a.max_iter = h->opt.max_iter;
+  a.stop_rule = h->opt.stop_rule;
+  a.r = h->r;
+  a.xi = h->xi;
+  a.alpha = h->alpha;
+  a.ztw = h->ztw;
+  a.w = h->ixw;
+  a.u = h->u;
+  a.rho = h->rho;
+  a.beta = 0.0;
+  a.v = h->ixv;
+  a.tn = h->ixtn;
+  a.zp = h->ixzp;
+  a.dr = h->ixdr;
+  a.hw = h->ixhw;
+  a.cr = h->ixcr;
+  a.cz = h->ixcz;
+  a.cp = h->ixcp;
+  a.cap = h->ixcap;
+  a.td = h->ixtd;
+  a.part = h->ixpart;
+  a.hpart = h->ixhpart.data();
+  const IxPasses ps{ix_apply, h};
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0), "event");
+  CK(cudaEventCreate(&e1), "event");
+  CK(cudaEventRecord(e0, st), "event");
+  IxResult r{};
+  CK(run_inexact(a, ps, sigma0, st, &r), "inexact solver");
+  CK(cudaEventRecord(e1, st), "event");
+  int kerr = 0;
+  CK(cudaMemcpyAsync(&kerr, h->err, sizeof(int), cudaMemcpyDeviceToHost, st), "copy err");
+  double* wdst = (w && w_on_device) ? w : h->wtmp;
+  CK(run_dir_finish(h->ixw, h->zscale, d, wdst, st), "finish");
+  if (w && !w_on_device) CK(cudaMemcpyAsync(w, h->wtmp, d * sizeof(double), cudaMemcpyDeviceToHost, st), "copy w");
+  if (alpha) CK(cudaMemcpyAsync(alpha, h->alpha, n * sizeof(double), cudaMemcpyDeviceToHost, st), "copy alpha");
+  CK(cudaStreamSynchronize(st), "sync");
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::memset(h->phase_ns, 0, sizeof(h->phase_ns));
+  std::memset(res, 0, sizeof(*res));
+  res->beta = r.beta;
+  res->primal_obj = r.pobj;
+  res->dual_obj = r.dobj;
+  res->kkt = r.kkt;
+  res->eta_p = std::max(r.eta_p1, std::max(r.eta_p2, r.eta_p3));
+  res->eta_d = std::max(r.eta_d1, std::max(r.eta_d2, r.eta_d3));
+  res->eta_c = std::max(r.eta_c1, std::max(r.eta_c2, r.eta_c3));
+  res->eta_gap = r.eta_gap;
+  res->sigma = r.sigma;
+  res->zscale = h->zscale;
+  res->t_setup_ms = h->t_setup_ms;
+  res->t_solve_ms = ms;
+  res->iters = r.iters;
+  res->reserved[1] = r.cg_steps;        // conjugate-gradient steps of Steps 1a and 1c
+  res->reserved[2] = r.step1c_solves;   // iterations in which Step 1c solved (the paper's "double")
+  gdwd_status s = kerr ? (gdwd_status)kerr : (gdwd_status)r.status;
+  res->status = s;
+  if (kerr) return fail(h, s, "gdwd_solve: a device wait of the inexact solver expired");
+  return s;
+}
+
 // Up to four values of C in lock-step in one launch of the joint kernel.
 static gdwd_status solve_multi(gdwd_handle* h, const double* Cs, int K, int kker, double* w, int w_on_device,
                                double* alpha, gdwd_result* res) {
@@ -1161,7 +1319,8 @@ extern "C" gdwd_status gdwd_solve(gdwd_handle* h, const double* Cs, int32_t nC, 
   }
   gdwd_status worst = GDWD_OK;
   // joint C-grid: groups of up to four C values per launch (one Z read per pass for all)
-  const int kmax = (count >= 2 && !h->master && !h->opt.cgrid_sequential && !h->opt.kernelized && !h->direct)
+  const int kmax = (count >= 2 && !h->master && !h->opt.cgrid_sequential && !h->opt.kernelized && !h->direct &&
+                    !h->inexact)
                        ? multi_max_k(h->store, h->L, h->grid, h->smem_optin - 16384)
                        : 1;
   int k0 = 0;
@@ -1193,6 +1352,9 @@ extern "C" gdwd_status gdwd_solve(gdwd_handle* h, const double* Cs, int32_t nC, 
     } else if (h->direct) {
       s = solve_direct(h, C, w ? w + (size_t)k * h->d : nullptr, w_on_device,
                        alpha ? alpha + (size_t)k * h->n : nullptr, res + k);
+    } else if (h->inexact) {
+      s = solve_inexact(h, C, w ? w + (size_t)k * h->d : nullptr, w_on_device,
+                        alpha ? alpha + (size_t)k * h->n : nullptr, res + k);
     } else {
       s = solve_one(h, C, w ? w + (size_t)k * h->d : nullptr, w_on_device,
                     alpha ? alpha + (size_t)k * h->n : nullptr, res + k);
@@ -1244,6 +1406,7 @@ extern "C" gdwd_status gdwd_apply(gdwd_handle* h, int32_t trans, const double* x
 
 extern "C" gdwd_status gdwd_gram(gdwd_handle* h, double* G_out) {
   if (!h || !G_out) return fail(h, GDWD_EINVAL, "gdwd_gram: NULL argument");
+  if (h->inexact) return fail(h, GDWD_EUNSUPPORTED, "gdwd_gram: the inexact solver forms no Gram matrix");
   const size_t m = (size_t)(h->direct ? h->d : h->n);   // d x d for the direct solver
   CK(cudaMemcpyAsync(G_out, h->G, m * m * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy G");
   CK(cudaStreamSynchronize(h->stream), "sync");
@@ -1315,7 +1478,8 @@ __global__ void pair_dist_kernel(const double* G, int64_t n, const int* pos, int
 
 extern "C" gdwd_status gdwd_suggest_C(gdwd_handle* h, double* C_out) {
   if (!h || !C_out) return fail(h, GDWD_EINVAL, "gdwd_suggest_C: NULL argument");
-  if (h->direct) return fail(h, GDWD_EUNSUPPORTED, "gdwd_suggest_C: needs the n x n Gram (not on a direct-solver handle)");
+  if (h->direct || h->inexact)
+    return fail(h, GDWD_EUNSUPPORTED, "gdwd_suggest_C: needs the n x n Gram (not on a direct or inexact handle)");
   const int64_t n = h->n;
   std::vector<double> y(n);
   CK(cudaMemcpyAsync(y.data(), h->y, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy y");
@@ -1377,7 +1541,7 @@ extern "C" gdwd_status gdwd_get_info(const gdwd_handle* h, gdwd_info* info) {
   info->t_factor_ms = h->t_stage_ms[2];
   info->gram_tensor_cores = h->gram_tc ? 1 : 0;
   info->kernelized = h->opt.kernelized;
-  info->solver = h->direct ? 1 : 0;
+  info->solver = h->direct ? 1 : (h->inexact ? 2 : 0);
   return GDWD_OK;
 }
 

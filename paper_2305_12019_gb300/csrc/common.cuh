@@ -60,6 +60,24 @@ __device__ __forceinline__ void df_fma(df& acc, df a, df b) {
   acc.hi = s;
 }
 
+// a * b, normalized (|lo| <= ulp(hi) / 2)
+__device__ __forceinline__ df df_mul(df a, df b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  const float t = p + e;
+  return df{t, e - (t - p)};
+}
+
+// a + b, normalized
+__device__ __forceinline__ df df_sum(df a, df b) {
+  df_add(a, b);
+  return a;
+}
+
+__device__ __forceinline__ df df_neg(df a) { return df{-a.hi, -a.lo}; }
+
 __device__ __forceinline__ df df_from(double x) {
   df r;
   r.hi = (float)x;
@@ -125,6 +143,14 @@ __device__ __forceinline__ double sqrt_nr(double x) {
   const double s = x * r;
   const double h = 0.5 * r;
   return fma(h, fma(-s, s, x), s);
+}
+
+// 1/sqrt(x) for x > 0 inside the normal FP32 range: an FP32 seed and one FP64
+// Newton step (~3e-14 relative).
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  const double r = (double)rsqrt_approx((float)x);
+  const double h = 0.5 * r;
+  return fma(h, fma(-x * r, r, 1.0), r);
 }
 
 __device__ __forceinline__ double warp_sum(double a) {
@@ -338,6 +364,25 @@ struct ElemTraits<float> {
   using compute_t = float;
   static constexpr int kVec = 4;
   __device__ __forceinline__ static void load(const void* p, float* v) {
+    float4 x = *reinterpret_cast<const float4*>(p);
+    v[0] = x.x;
+    v[1] = x.y;
+    v[2] = x.z;
+    v[3] = x.w;
+  }
+};
+
+// FP32 storage read into FP64 arithmetic (the inexact solver's products, whose
+// conjugate-gradient recurrences need more than FP32 products): four stored
+// values per 16-byte vector, each widened to double.
+struct f32w {
+  float v;
+};
+template <>
+struct ElemTraits<f32w> {
+  using compute_t = double;
+  static constexpr int kVec = 4;
+  __device__ __forceinline__ static void load(const void* p, double* v) {
     float4 x = *reinterpret_cast<const float4*>(p);
     v[0] = x.x;
     v[1] = x.y;

@@ -1,5 +1,5 @@
 // K = Zq^T Zq on the 5th-generation tensor cores, for BF16, FP16 and E4M3
-// storage.
+// storage, and for FP32 storage through a three-term BF16 split.
 //
 // The Gram matrix of the stored codes is the one dense contraction of the
 // method: the n x n block I + Z~^T Z~ / mu of the SMW2 solve (Sec. 3.2,
@@ -24,6 +24,16 @@
 //   * the epilogue writes the tile's FP64 partial; gram_finish_kernel sums the
 //     k-splits in a fixed order and applies the column scales.
 //
+// FP32 storage: each value is split into three BF16 terms, z = h + m + l
+// (h = bf16(z), m = bf16(z - h), l = bf16(z - h - m); both differences are exact
+// in FP32), written by split3_kernel into a scratch slab layout of 128 rows per
+// slab, term t in slabs [t NB2, (t+1) NB2).  A k-step then loads the three terms
+// of both column tiles into three consecutive ring stages and issues the six
+// products whose order is at most 2^-16 of z_i z_j (l h, h l, m m, m h, h m,
+// h h; smallest first), 24 MMAs per strip of 64 rows, h h into an accumulator
+// of its own.  The products are exact; the three dropped ones (m l, l m, l l)
+// are below 2^-23 of |z_i z_j|, about the rounding of one FP32 product.
+//
 // Every wait is bounded: after timeout_ns without progress a CTA records
 // GDWD_ETIMEOUT, the other roles of the CTA stop at their next wait, the
 // producer waits (bounded) for its copies still in flight, the MMA thread for
@@ -46,12 +56,17 @@ constexpr int kEpiWarps = 16;                  // four per tensor-memory lane qu
 constexpr int kEpiWarp0 = 4;                   // warps 0-3: producer, MMA, two idle
 constexpr int kThreadsTc = (kEpiWarp0 + kEpiWarps) * 32;
 constexpr int kTmemCols = 2 * kTT;             // two FP32 accumulator buffers
+// The split of FP32 storage keeps the h h products in their own accumulator
+// (columns [256, 512)), so the FP32 sum of a strip's largest terms carries only
+// the four roundings of its four MMAs; the five smaller products share the other.
+constexpr int kTmemColsSplit = 4 * kTT;
 // The tensor core adds each MMA's 16 (8-bit: 32) products into the FP32
 // accumulator with one rounding relative to the running sum, so the rows summed
 // in FP32 before a fold into double-float bound the error: one 128-byte strip
 // per fold (64 rows of 16-bit codes, 128 of E4M3; four MMAs) keeps it within
 // four FP32 roundings of the largest partial.
 constexpr int kFoldSteps = 1;
+constexpr int kSplitRows = 128;                // rows per slab of the BF16 split of FP32 storage
 
 struct __align__(1024) TcShared {
   uint8_t a[kStages][kStageBytes];             // 1024-byte aligned (128-byte swizzle atoms)
@@ -98,10 +113,11 @@ __host__ __device__ constexpr uint32_t idesc_mn128(uint32_t fmt) {
   return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kTT >> 3) << 17) | ((uint32_t)(kTT >> 4) << 24);
 }
 
-// kKind: 0 = FP16, 1 = BF16 (kind::f16, format codes 0 / 1), 2 = E4M3 (kind::f8f6f4, code 0)
+// kKind: 0 = FP16, 1 = BF16 (kind::f16, format codes 0 / 1), 2 = E4M3 (kind::f8f6f4, code 0),
+// 3 = the BF16 terms of FP32 storage (kind::f16, BF16)
 template <int kKind>
 __device__ __forceinline__ void mma_128x128(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
-  constexpr uint32_t idesc = idesc_mn128(kKind == 1 ? 1u : 0u);
+  constexpr uint32_t idesc = idesc_mn128((kKind == 1 || kKind == 3) ? 1u : 0u);
   if constexpr (kKind == 2) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
@@ -153,7 +169,12 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, TcShared
 template <int kKind>
 __global__ void __launch_bounds__(kThreadsTc, 1)
     gram_tc_kernel(const __grid_constant__ CUtensorMap zmap, int ksplit, int nstrips, int strip_rows,
-                   int64_t ksteps, int fold, int64_t n, double* Kpart, int* err, uint64_t timeout_ns) {
+                   int64_t ksteps, int fold, int tslabs, int64_t n, double* Kpart, int* err, uint64_t timeout_ns) {
+  // terms per k-step: one for 16- and 8-bit storage, three for the split of FP32
+  // (term t of k-step i in ring stage (i kTerms + t) mod kStages; tslabs = slabs per term)
+  constexpr int kTerms = kKind == 3 ? 3 : 1;
+  constexpr int kCols = kKind == 3 ? kTmemColsSplit : kTmemCols;
+  static_assert(kStages % kTerms == 0, "the terms of a k-step occupy consecutive stages");
   extern __shared__ uint8_t smem_raw[];
   TcShared& S = *reinterpret_cast<TcShared*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -183,7 +204,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem_base)),
-                 "r"(kTmemCols)
+                 "r"(kCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -197,21 +218,23 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     if (lane == 0) {
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&zmap)) : "memory");
       const uint32_t tx = diag ? (uint32_t)kStageBytes : 2u * kStageBytes;
+      const int nsub = nsteps * kTerms;
       int issued = 0;
-      for (int i = 0; i < nsteps; ++i) {
-        const int s = i % kStages;
-        if (i >= kStages && !tc_wait(&S.empty[s], (uint32_t)((i / kStages) - 1) & 1u, S, err, timeout_ns)) break;
+      for (int u = 0; u < nsub; ++u) {
+        const int s = u % kStages;
+        if (u >= kStages && !tc_wait(&S.empty[s], (uint32_t)((u / kStages) - 1) & 1u, S, err, timeout_ns)) break;
+        const int i = u / kTerms, t = u - i * kTerms;
         const int64_t k = k0 + i;
         const int slab = (int)(k / nstrips);
         const int x = (int)(k - (int64_t)slab * nstrips) * strip_rows;
         mbar_expect_tx(&S.full[s], tx);
-        tma_load_3d(S.a[s], &zmap, x, I * kTT, slab, &S.full[s]);
-        if (!diag) tma_load_3d(S.b[s], &zmap, x, J * kTT, slab, &S.full[s]);
-        issued = i + 1;
+        tma_load_3d(S.a[s], &zmap, x, I * kTT, t * tslabs + slab, &S.full[s]);
+        if (!diag) tma_load_3d(S.b[s], &zmap, x, J * kTT, t * tslabs + slab, &S.full[s]);
+        issued = u + 1;
       }
       if (*(volatile int*)&S.abort) {   // let the copies still in flight land
-        for (int i = issued > kStages ? issued - kStages : 0; i < issued; ++i)
-          mbar_wait(&S.full[i % kStages], (uint32_t)(i / kStages) & 1u, err, timeout_ns);
+        for (int u = issued > kStages ? issued - kStages : 0; u < issued; ++u)
+          mbar_wait(&S.full[u % kStages], (uint32_t)(u / kStages) & 1u, err, timeout_ns);
       }
     }
     __syncwarp();
@@ -228,19 +251,41 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         tc_fence_after();
         const uint32_t dt = tbase + (uint32_t)(buf * kTT);
         const int i0 = c * fold, i1 = (i0 + fold < nsteps) ? i0 + fold : nsteps;
-        for (int i = i0; i < i1; ++i) {
-          const int s = i % kStages;
-          if (!tc_wait(&S.full[s], (uint32_t)(i / kStages) & 1u, S, err, timeout_ns)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          const uint64_t da = smem_desc_sw128(S.a[s]);
-          const uint64_t db = diag ? da : smem_desc_sw128(S.b[s]);
+        for (int i = i0; i < i1 && ok; ++i) {
+          int st[kTerms];
 #pragma unroll
-          for (int j = 0; j < kStrip / 32; ++j)   // 32 bytes of k per MMA: start address + 2j (16-byte units)
-            mma_128x128<kKind>(dt, da + 2 * j, db + 2 * j, (i > i0 || j > 0) ? 1u : 0u);
-          mma_commit(&S.empty[s]);
+          for (int t = 0; t < kTerms; ++t) {
+            const int u = i * kTerms + t;
+            st[t] = u % kStages;
+            if (!tc_wait(&S.full[st[t]], (uint32_t)(u / kStages) & 1u, S, err, timeout_ns)) {
+              ok = false;
+              break;
+            }
+          }
+          if (!ok) break;
+          tc_fence_after();
+          if constexpr (kTerms == 1) {
+            const uint64_t da = smem_desc_sw128(S.a[st[0]]);
+            const uint64_t db = diag ? da : smem_desc_sw128(S.b[st[0]]);
+#pragma unroll
+            for (int j = 0; j < kStrip / 32; ++j)   // 32 bytes of k per MMA: start address + 2j (16-byte units)
+              mma_128x128<kKind>(dt, da + 2 * j, db + 2 * j, (i > i0 || j > 0) ? 1u : 0u);
+          } else {
+            // the products of the split terms (A term, B term), smallest first
+            constexpr int kPa[6] = {2, 0, 1, 1, 0, 0}, kPb[6] = {0, 2, 1, 0, 1, 0};
+#pragma unroll
+            for (int p = 0; p < 6; ++p) {
+              const int sa = st[kPa[p]], sb = st[kPb[p]];
+              const uint64_t da = smem_desc_sw128(S.a[sa]);
+              const uint64_t db = smem_desc_sw128(diag ? S.a[sb] : S.b[sb]);
+              const bool hh = p == 5;                            // h h: its own accumulator
+              const uint32_t acc_d = hh ? dt + 2 * kTT : dt;
+#pragma unroll
+              for (int j = 0; j < kStrip / 32; ++j)
+                mma_128x128<kKind>(acc_d, da + 2 * j, db + 2 * j, (i > i0 || (!hh && p > 0) || j > 0) ? 1u : 0u);
+            }
+          }
+          for (int t = 0; t < kTerms; ++t) mma_commit(&S.empty[st[t]]);
         }
         if (ok) mma_commit(&S.acc_full[buf]);
       }
@@ -272,6 +317,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
           tmem_ld_x8(ta + 8 * g, v);
 #pragma unroll
           for (int q = 0; q < 8; ++q) df_add(acc[8 * g + q], v[q]);
+          if constexpr (kKind == 3) {
+            tmem_ld_x8(ta + 2 * kTT + 8 * g, v);                 // the h h accumulator
+#pragma unroll
+            for (int q = 0; q < 8; ++q) df_add(acc[8 * g + q], v[q]);
+          }
         }
         tc_fence_before();
         mbar_arrive(&S.acc_empty[buf]);
@@ -293,7 +343,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kTmemCols) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kCols) : "memory");
   }
 }
 
@@ -328,62 +378,143 @@ cudaError_t set_smem_once() {
 
 template <int kKind>
 cudaError_t launch_tc(const CUtensorMap& map, int tiles, int ksplit, int nstrips, int strip_rows, int64_t ksteps,
-                      int fold, int64_t n, double* Kpart, int* err, uint64_t timeout_ns, cudaStream_t st) {
+                      int fold, int tslabs, int64_t n, double* Kpart, int* err, uint64_t timeout_ns, cudaStream_t st) {
   cudaError_t e = set_smem_once<kKind>();
   if (e != cudaSuccess) return e;
   gram_tc_kernel<kKind><<<tiles * ksplit, kThreadsTc, kTcSmem, st>>>(map, ksplit, nstrips, strip_rows, ksteps, fold,
-                                                                    n, Kpart, err, timeout_ns);
+                                                                    tslabs, n, Kpart, err, timeout_ns);
   return cudaGetLastError();
+}
+
+// The three BF16 terms of a value (each difference exact in FP32).
+__device__ __forceinline__ void split3(float x, uint32_t& h, uint32_t& m, uint32_t& l) {
+  const __nv_bfloat16 bh = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(bh);
+  const __nv_bfloat16 bm = __float2bfloat16_rn(r1);
+  const float r2 = r1 - __bfloat162float(bm);
+  const __nv_bfloat16 bl = __float2bfloat16_rn(r2);
+  h = __bfloat16_as_ushort(bh);
+  m = __bfloat16_as_ushort(bm);
+  l = __bfloat16_as_ushort(bl);
+}
+
+// FP32 slab layout (TB rows per slab) -> three BF16 term arrays of kSplitRows
+// rows per slab (NB2 slabs each, term t at slabs [t NB2, (t+1) NB2)); rows past d
+// are zero.  Each thread writes 8 consecutive rows of one column of each term
+// (one 16-byte store per term).
+__global__ void split3_kernel(const float* __restrict__ Z, Layout L, int NB2, uint16_t* __restrict__ out) {
+  const int64_t per_slab = (int64_t)kSplitRows * L.n;
+  const int64_t term = (int64_t)NB2 * per_slab;
+  const int64_t groups = term / 8;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < groups; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = g * 8;
+    const int64_t s2 = e / per_slab, rem = e - s2 * per_slab;
+    const int64_t i = rem / kSplitRows;
+    const int64_t j0 = s2 * kSplitRows + (rem - i * kSplitRows);   // global row of the first of the 8
+    int64_t s = j0 / L.TB, jl = j0 - s * L.TB;
+    uint32_t h[4], m[4], l[4];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float x = (j0 + q < L.d) ? Z[(s * L.n + i) * L.TB + jl] : 0.f;
+      if (++jl == L.TB) {
+        jl = 0;
+        ++s;
+      }
+      uint32_t a, b, c;
+      split3(x, a, b, c);
+      if (q & 1) {
+        h[q >> 1] |= a << 16;
+        m[q >> 1] |= b << 16;
+        l[q >> 1] |= c << 16;
+      } else {
+        h[q >> 1] = a;
+        m[q >> 1] = b;
+        l[q >> 1] = c;
+      }
+    }
+    *reinterpret_cast<uint4*>(out + e) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(out + term + e) = make_uint4(m[0], m[1], m[2], m[3]);
+    *reinterpret_cast<uint4*>(out + 2 * term + e) = make_uint4(l[0], l[1], l[2], l[3]);
+  }
+}
+
+int split_slabs(const Layout& L) { return (int)((L.d + kSplitRows - 1) / kSplitRows); }
+
+// k-steps (strips of 128 bytes per column) of the operand the kernel reads
+int64_t tc_ksteps(int store, const Layout& L) {
+  if (store == GDWD_F32) return (int64_t)split_slabs(L) * (kSplitRows * 2 / kStrip);
+  const int strip_rows = kStrip / L.esize;
+  return (int64_t)L.NB * ((L.TB + strip_rows - 1) / strip_rows);
 }
 
 }  // namespace
 
 bool gram_tc_supported(int store, const Layout& L) {
-  if (store != GDWD_BF16 && store != GDWD_F16 && store != GDWD_E4M3) return false;
+  if (store != GDWD_BF16 && store != GDWD_F16 && store != GDWD_E4M3 && store != GDWD_F32) return false;
   // tensor-map strides are multiples of 16 bytes; tile rows and the slab count fit int
-  if (((int64_t)L.TB * L.esize) % 16 != 0 || L.n > (1LL << 30)) return false;
+  if (store != GDWD_F32 && ((int64_t)L.TB * L.esize) % 16 != 0) return false;
+  if (L.n > (1LL << 30) || 3LL * split_slabs(L) > (1LL << 30)) return false;
   return encode_tiled() != nullptr;
 }
 
-int gram_tc_ksplit(const Layout& L, int sms) {
+size_t gram_tc_scratch_bytes(int store, const Layout& L) {
+  return store == GDWD_F32 ? (size_t)3 * split_slabs(L) * kSplitRows * (size_t)L.n * sizeof(uint16_t) : 0;
+}
+
+int gram_tc_ksplit(int store, const Layout& L, int sms) {
   const int64_t Tt = (L.n + kTT - 1) / kTT;
   const int64_t tiles = Tt * (Tt + 1) / 2;
-  const int strip_rows = kStrip / L.esize;
-  const int64_t ksteps = (int64_t)L.NB * ((L.TB + strip_rows - 1) / strip_rows);
-  int64_t ks = (sms + tiles - 1) / tiles;                           // at least one wave of CTAs
+  const int64_t ksteps = tc_ksteps(store, L);
+  // one CTA per SM (the ring takes most of shared memory): whole waves only,
+  // since a partial second wave doubles the time of the splits in it
+  int64_t ks = tiles < sms ? sms / tiles : 1;
   ks = std::min<int64_t>(ks, std::max<int64_t>(1, ksteps / 4));      // >= 4 k-steps per split
   return (int)std::max<int64_t>(1, std::min<int64_t>(ks, 32));
 }
 
-cudaError_t run_gram_tc(int store, const Layout& L, int ksplit, double* Kpart, int* err, uint64_t timeout_ns,
-                        cudaStream_t st) {
+cudaError_t run_gram_tc(int store, const Layout& L, int ksplit, double* Kpart, void* scratch, int* err,
+                        uint64_t timeout_ns, cudaStream_t st) {
   EncodeTiledFn enc = encode_tiled();
   if (!enc) return cudaErrorNotSupported;
-  const int es = L.esize;
+  const bool split = store == GDWD_F32;
+  if (split && !scratch) return cudaErrorInvalidValue;
+  const int es = split ? 2 : L.esize;
+  const int rows = split ? kSplitRows : L.TB;                       // rows per slab of the operand
+  const int slabs = split ? split_slabs(L) : L.NB;                  // slabs per term
   const int strip_rows = kStrip / es;
-  const int nstrips = (L.TB + strip_rows - 1) / strip_rows;
-  const int64_t ksteps = (int64_t)L.NB * nstrips;
+  const int nstrips = (rows + strip_rows - 1) / strip_rows;
+  const int64_t ksteps = (int64_t)slabs * nstrips;
   const int fold = kFoldSteps;
   const int64_t Tt = (L.n + kTT - 1) / kTT;
   const int tiles = (int)(Tt * (Tt + 1) / 2);
-  // Z in the slab layout as a 3-D tensor: rows within a slab (contiguous), columns, slabs
+  if (split) {
+    const int64_t groups = (int64_t)slabs * kSplitRows * L.n / 8;
+    const int blocks = (int)std::min<int64_t>((groups + 255) / 256, 152 * 16);
+    split3_kernel<<<blocks, 256, 0, st>>>(static_cast<const float*>(L.Z), L, slabs, static_cast<uint16_t*>(scratch));
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  // the operand in the slab layout as a 3-D tensor: rows within a slab
+  // (contiguous), columns, slabs (for the split: the three terms' slabs in turn)
   CUtensorMap map;
-  const cuuint64_t dims[3] = {(cuuint64_t)L.TB, (cuuint64_t)L.n, (cuuint64_t)L.NB};
-  const cuuint64_t strides[2] = {(cuuint64_t)L.TB * es, (cuuint64_t)L.TB * es * (cuuint64_t)L.n};
+  const cuuint64_t dims[3] = {(cuuint64_t)rows, (cuuint64_t)L.n, (cuuint64_t)slabs * (split ? 3 : 1)};
+  const cuuint64_t strides[2] = {(cuuint64_t)rows * es, (cuuint64_t)rows * es * (cuuint64_t)L.n};
   const cuuint32_t box[3] = {(cuuint32_t)strip_rows, (cuuint32_t)kTT, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
-  const CUresult r = enc(&map, es == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_UINT16, 3,
-                         const_cast<void*>(L.Z), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  void* base = split ? scratch : const_cast<void*>(L.Z);
+  const CUresult r = enc(&map, es == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, base, dims,
+                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
   switch (store) {
-    case GDWD_F16: return launch_tc<0>(map, tiles, ksplit, nstrips, strip_rows, ksteps, fold, L.n, Kpart, err,
+    case GDWD_F16: return launch_tc<0>(map, tiles, ksplit, nstrips, strip_rows, ksteps, fold, 0, L.n, Kpart, err,
                                        timeout_ns, st);
-    case GDWD_BF16: return launch_tc<1>(map, tiles, ksplit, nstrips, strip_rows, ksteps, fold, L.n, Kpart, err,
+    case GDWD_BF16: return launch_tc<1>(map, tiles, ksplit, nstrips, strip_rows, ksteps, fold, 0, L.n, Kpart, err,
                                         timeout_ns, st);
-    case GDWD_E4M3: return launch_tc<2>(map, tiles, ksplit, nstrips, strip_rows, ksteps, fold, L.n, Kpart, err,
+    case GDWD_E4M3: return launch_tc<2>(map, tiles, ksplit, nstrips, strip_rows, ksteps, fold, 0, L.n, Kpart, err,
                                         timeout_ns, st);
+    case GDWD_F32: return launch_tc<3>(map, tiles, ksplit, nstrips, strip_rows, ksteps, fold, slabs, L.n, Kpart,
+                                       err, timeout_ns, st);
     default: return cudaErrorNotSupported;
   }
 }

@@ -68,24 +68,22 @@ cudaError_t launch_prox(const double* a, const double* r0, const double* omega, 
 // pass-B row epilogue of the iteration: g = u - t / mu and the d-space sums
 // ---------------------------------------------------------------------------
 struct IterEpi {
-  double* g;                 // global copy of g (written through: the host's w uses it)
-  const double* s_u;         // the CTA's slab rows of u, rho and g in shared memory
-  const double* s_rho;
-  double* s_g;
-  double inv_mu, a_coef;     // a = ta + a_coef * rho, a_coef = sqrt(mu)(1 - tau)
-  double sg2 = 0, sgr = 0, sr2 = 0, sa2 = 0, sag = 0, sta2 = 0;
-  __device__ void row(int64_t j, int m, double t, double ta) {
-    const double gj = s_u[m] - t * inv_mu;
-    const double rj = s_rho[m];
-    const double aj = ta + a_coef * rj;
+  const df* s_u;             // the CTA's slab rows of u, rho and g in shared memory (double-float)
+  const df* s_rho;
+  df* s_g;
+  df inv_mu, a_coef;         // a = ta + a_coef * rho, a_coef = sqrt(mu)(1 - tau)
+  df sg2{0.f, 0.f}, sgr{0.f, 0.f}, sr2{0.f, 0.f}, sa2{0.f, 0.f}, sag{0.f, 0.f}, sta2{0.f, 0.f};
+  __device__ void row(int64_t, int m, df t, df ta) {
+    const df gj = df_sum(s_u[m], df_neg(df_mul(t, inv_mu)));
+    const df rj = s_rho[m];
+    const df aj = df_sum(ta, df_mul(a_coef, rj));
     s_g[m] = gj;
-    g[j] = gj;
-    sg2 = fma(gj, gj, sg2);
-    sgr = fma(gj, rj, sgr);
-    sr2 = fma(rj, rj, sr2);
-    sa2 = fma(aj, aj, sa2);
-    sag = fma(aj, gj, sag);
-    sta2 = fma(ta, ta, sta2);
+    df_fma(sg2, gj, gj);
+    df_fma(sgr, gj, rj);
+    df_fma(sr2, rj, rj);
+    df_fma(sa2, aj, aj);
+    df_fma(sag, aj, gj);
+    df_fma(sta2, ta, ta);
   }
 };
 
@@ -247,6 +245,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
   __shared__ double s_gx[kFuseRowsPerWarp * kWarps * 3];                  // fused products: rows, then p^T
   const int qcase = q_case(a.q);
   const double sqmu = sqrt(a.mu), inv_mu = 1.0 / a.mu, inv_sqmu = 1.0 / sqmu;
+  const df inv_mu_df = df_from(inv_mu), acoef_df = df_from(sqmu * (1.0 - a.tau)), omtau = df_from(1.0 - a.tau);
   const double den = 1.0 + a.C;
   const double inv_q = 1.0 / a.q;
   const float inv_den = (float)(1.0 / den);
@@ -263,9 +262,9 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
 #define RS(slot, t) rs[(slot) * rld + (t)]
   const int nslab_max = (NB + grid - 1) / grid * TB;                              // slab rows, any CTA
   uint8_t* sst = smem + (size_t)stages * stage_bytes + row_state_bytes(rpc);      // slab state
-  double* s_u = reinterpret_cast<double*>(sst);
-  double* s_rho = s_u + nslab_max;
-  double* s_g = s_rho + nslab_max;
+  df* s_u = reinterpret_cast<df*>(sst);
+  df* s_rho = s_u + nslab_max;
+  df* s_g = s_rho + nslab_max;
   CT* s_up = reinterpret_cast<CT*>(s_g + nslab_max);
   uint8_t* uni = sst + slab_state_bytes(nslab_max, (int)sizeof(CT));              // phase-local region
   if (threadIdx.x == 0) s_abort = 0;
@@ -386,9 +385,9 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
     const int k = m / TB, j = m - k * TB;
     const int64_t gj = (cta + (int64_t)k * grid) * TB + j;
     const bool in = gj < d;
-    s_u[m] = in ? a.u[gj] : 0.0;
-    s_rho[m] = in ? a.rho[gj] : 0.0;
-    s_g[m] = in ? a.g[gj] : 0.0;
+    s_u[m] = df_from(in ? a.u[gj] : 0.0);
+    s_rho[m] = df_from(in ? a.rho[gj] : 0.0);
+    s_g[m] = df_from(in ? a.g[gj] : 0.0);
   }
   __syncthreads();
 
@@ -485,21 +484,20 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
     // pass over Z reads it from shared memory (u also in the compute type, for
     // the column dots)
     GDWD_BARRIER_SIDE(4, [&]() {
-      const double rcoefd = a.tau * sig_prev * sqmu * (1.0 - theta);
+      // double-float on the FP32 pipes: each warp-level FP64 instruction occupies
+      // the SM's FP64 unit for ~19 cycles, whatever the number of active lanes
+      const df th = df_from(theta), mrc = df_from(-a.tau * sig_prev * sqmu * (1.0 - theta));
       for (int m = threadIdx.x - 32; m < nmy * TB; m += kThreads - 32) {
         const int k = m / TB, j = m - k * TB;
         const int64_t gj = (cta + (int64_t)k * grid) * TB + j;
-        double uj = s_u[m];
+        df uj = s_u[m];
         if (pending && gj < d) {
-          const double g = s_g[m];
-          const double rn = (1.0 - a.tau) * s_rho[m] - rcoefd * g;   // rho <- rho - tau sigma D (w - u+)
-          uj = theta * g;                                            // u+ = Pi_B(g)
-          s_rho[m] = rn;
+          const df g = s_g[m];
+          s_rho[m] = df_sum(df_mul(omtau, s_rho[m]), df_mul(mrc, g));   // rho <- rho - tau sigma D (w - u+)
+          uj = df_mul(th, g);                                            // u+ = Pi_B(g)
           s_u[m] = uj;
-          a.rho[gj] = rn;
-          a.u[gj] = uj;
         }
-        s_up[m] = (CT)uj;
+        s_up[m] = (CT)((double)uj.hi + (double)uj.lo);
       }
     });
 
@@ -590,7 +588,10 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
         }
         __syncwarp();
       }
-      if (lane < 9) a.scal[(size_t)lane * grid + cta] = nrows > 0 ? kt[9 * 32 + lane] : 0.0;
+      if (lane < 9) {   // as a double-float pair (summed on the FP32 pipes in phase S)
+        const df p = df_from(nrows > 0 ? kt[9 * 32 + lane] : 0.0);
+        reinterpret_cast<float2*>(a.scal)[(size_t)lane * grid + cta] = make_float2(p.hi, p.lo);
+      }
     });
 
 
@@ -611,7 +612,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
       }
       __syncthreads();
       GDWD_MARK(16);
-      IterEpi epi{a.g, s_u, s_rho, s_g, inv_mu, sqmu * (1.0 - a.tau)};
+      IterEpi epi{s_u, s_rho, s_g, inv_mu_df, acoef_df};
       PassB<T, IterEpi> pb;
       pb.cv = cv;
       pb.av = av;
@@ -643,15 +644,15 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
       GDWD_MARK(17);
       // the six d-space sums of every thread, one warp per sum, through the
       // phase-local region (free once the pass is over)
-      const double vals[6] = {epi.sg2, epi.sgr, epi.sr2, epi.sa2, epi.sag, epi.sta2};
+      const df vals[6] = {epi.sg2, epi.sgr, epi.sr2, epi.sa2, epi.sag, epi.sta2};
       __syncthreads();
-      rows_sum<6>(vals, threadIdx.x, true, kThreads, reinterpret_cast<double*>(uni), kThreads,
-                  a.scal + (size_t)S_G2 * grid + cta, grid);
+      rows_sum_df<6>(vals, reinterpret_cast<float2*>(uni), TB,
+                     reinterpret_cast<float2*>(a.scal) + (size_t)S_G2 * grid + cta, grid);
     }
     GDWD_BARRIER(8);
 
     // ---------------- phase S: totals, KKT, sigma rule, stop test (same in every CTA)
-    grid_totals(a.scal, grid, S_COUNT - 1, s_tot);
+    grid_totals_df(reinterpret_cast<const float2*>(a.scal), grid, s_tot);
     __syncthreads();
     GDWD_MARK(13);
     s_phase(s_tot, sq, sig, gs_it, it, beta, status, false, a.ctrl, s_pd, s_etaf, s_ctl, s_ictl);
@@ -669,6 +670,17 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
     }
   }
   if (it >= a.max_iter && status != GDWD_OK) status = GDWD_EMAXITER;
+  // the slab rows of u, rho and g back to global memory (the host forms w from
+  // g and rho; a later launch starts from them)
+  for (int m = threadIdx.x; m < nmy * TB; m += kThreads) {
+    const int k = m / TB, j = m - k * TB;
+    const int64_t gj = (cta + (int64_t)k * grid) * TB + j;
+    if (gj < d) {
+      a.u[gj] = df_to_double(s_u[m]);
+      a.rho[gj] = df_to_double(s_rho[m]);
+      a.g[gj] = df_to_double(s_g[m]);
+    }
+  }
   // the rows back to global memory (the host reads alpha; a later launch starts
   // from r, xi, alpha, U_u, U_rho and (G - I) c)
   for (int t = threadIdx.x; t < nrows; t += kThreads) {
@@ -790,7 +802,18 @@ static int choose_cw_t(const Layout& L, int grid, int smem_limit) {
   return (int)cw;
 }
 
-int choose_chunk_cols(int store, const Layout& L, int grid, int smem_limit) {
+// Chunk columns for the stand-alone product kernels alone (no iteration kernel).
+template <typename T>
+static int choose_cw_apply(const Layout& L, int grid, int smem_limit) {
+  const int64_t col_bytes = (int64_t)L.TB * L.esize;
+  const int64_t avail = (int64_t)smem_limit - (int64_t)pass_bytes<T>(L, grid) - 1024;
+  int64_t cw = std::min<int64_t>(65536 / col_bytes, (avail / 2 - 128) / col_bytes);
+  cw = std::max<int64_t>(cw, 1);
+  return (int)std::min<int64_t>(cw, L.n);
+}
+
+int choose_chunk_cols(int store, const Layout& L, int grid, int smem_limit, bool wide) {
+  if (wide && store == GDWD_F32) return choose_cw_apply<f32w>(L, grid, smem_limit);
   switch (store) {
     case GDWD_F64: return choose_cw_t<double>(L, grid, smem_limit);
     case GDWD_BF16: return choose_cw_t<__nv_bfloat16>(L, grid, smem_limit);
@@ -847,7 +870,7 @@ cudaError_t run_iterate_f32(int store, const IterArgs<float>& a, int smem_limit,
 // ---------------------------------------------------------------------------
 struct ApplyEpi {
   double* out;
-  __device__ void row(int64_t j, int, double t, double) { out[j] = t; }
+  __device__ void row(int64_t j, int, df t, df) { out[j] = df_to_double(t); }
 };
 
 template <typename T>
@@ -950,7 +973,9 @@ static cudaError_t run_apply_t(const Layout& L, int trans, const double* x, cons
 }
 
 cudaError_t run_apply(int store, const Layout& L, int trans, const double* x, const double* sc, double* out,
-                      void* partial, int grid, int smem_limit, int* err, uint64_t tmo, cudaStream_t st) {
+                      void* partial, int grid, int smem_limit, int* err, uint64_t tmo, cudaStream_t st, bool wide) {
+  if (wide && store == GDWD_F32)
+    return run_apply_t<f32w>(L, trans, x, sc, out, partial, grid, smem_limit, err, tmo, st);
   switch (store) {
     case GDWD_F64: return run_apply_t<double>(L, trans, x, sc, out, partial, grid, smem_limit, err, tmo, st);
     case GDWD_BF16: return run_apply_t<__nv_bfloat16>(L, trans, x, sc, out, partial, grid, smem_limit, err, tmo, st);

@@ -50,48 +50,57 @@ __device__ __forceinline__ int q_case(double q) {
 }
 
 __device__ inline double prox_root(double a, double kq, double q, int qcase, double r0) {
+  // FP32 start, where every FP32 intermediate (up to a s^(q+1) and s^(q+2) with
+  // s < hi) stays finite and normal; its bracket and eligibility tests are FP32
+  // too (each FP64 instruction occupies this part's FP64 unit for many cycles)
+  {
+    const float af = (float)a, kf = (float)kq, qf = (float)q, r0f = (float)r0;
+    const float lf0 = fmaxf(af, 0.f);
+    const float hf0 = lf0 + fmaxf(kf, 1.f);
+    if (fabsf(af) < 1e6f && kf > 1e-20f && kf < 1e6f && hf0 < 1e6f && q <= 4.0) {
+      float lf = lf0, hf = hf0;
+      float sf = (r0f > lf && r0f < hf) ? r0f : 0.5f * (lf + hf);
+      bool conv = false;
+      for (int it = 0; it < 30; ++it) {
+        const float sq1 = pow_q1f(sf, qf, qcase);
+        const float f = sq1 * (sf - af) - kf;
+        if (f < 0.f) lf = sf;
+        else if (f > 0.f) hf = sf;
+        else {
+          conv = true;
+          break;
+        }
+        const float nt = sf * __fdividef(kf * (qf + 2.f) + af * sq1, kf * (qf + 1.f) + sq1 * sf);
+        if (fabsf(nt - sf) <= 2e-6f * sf) {
+          sf = nt;
+          conv = true;
+          break;
+        }
+        sf = (nt > lf && nt < hf) ? nt : 0.5f * (lf + hf);
+      }
+      if (conv && sf > 0.f) {
+        const double kq1 = kq * (q + 1.0);
+        double x = (double)sf;
+        float dlf = 0.f, xf = sf;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const double sq1 = pow_q1(x, q, qcase);
+          const double f = fma(sq1, x - a, -kq);
+          const double den = fma(sq1, x, kq1);
+          dlf = xf * __fdividef((float)f, (float)den);
+          x -= (double)dlf;
+          xf = (float)x;
+        }
+        // accepted when the last correction is below 1e-9 relative and the
+        // root stays on the positive side of max(a, 0)
+        if (fabsf(dlf) <= 1e-9f * sf && xf >= lf0) return x;
+      }
+    }
+  }
+  // bracketed FP64 iteration (inputs outside the FP32 range, or no FP32 convergence)
   double lo = dmax0(a);
   double hi = lo + (kq > 1.0 ? kq : 1.0);
   double s = (r0 > lo && r0 < hi) ? r0 : 0.5 * (lo + hi);
-  // FP32 start, where every FP32 intermediate (up to a s^(q+1) and s^(q+2) with
-  // s < hi) stays finite and normal
-  if (a > -1e6 && a < 1e6 && kq > 1e-20 && kq < 1e6 && hi < 1e6 && q <= 4.0) {
-    const float af = (float)a, kf = (float)kq, qf = (float)q;
-    float lf = (float)lo, hf = (float)hi, sf = (float)s;
-    bool conv = false;
-    for (int it = 0; it < 30; ++it) {
-      const float sq1 = pow_q1f(sf, qf, qcase);
-      const float f = sq1 * (sf - af) - kf;
-      if (f < 0.f) lf = sf;
-      else if (f > 0.f) hf = sf;
-      else {
-        conv = true;
-        break;
-      }
-      const float nt = sf * __fdividef(kf * (qf + 2.f) + af * sq1, kf * (qf + 1.f) + sq1 * sf);
-      if (fabsf(nt - sf) <= 2e-6f * sf) {
-        sf = nt;
-        conv = true;
-        break;
-      }
-      sf = (nt > lf && nt < hf) ? nt : 0.5f * (lf + hf);
-    }
-    const double sd = (double)sf;
-    if (conv && sd > lo && sd < hi) {
-      const double kq1 = kq * (q + 1.0);
-      double x = sd, dl = 0.0;
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const double sq1 = pow_q1(x, q, qcase);
-        const double f = fma(sq1, x - a, -kq);
-        const double den = fma(sq1, x, kq1);
-        dl = (double)((float)x * __fdividef((float)f, (float)den));
-        x -= dl;
-      }
-      if (x > lo && x < hi && fabs(dl) <= 1e-9 * x) return x;
-    }
-    if (sd > lo && sd < hi) s = sd;
-  }
   for (int it = 0; it < 100; ++it) {
     const double sq1 = pow_q1(s, q, qcase);
     const double f = sq1 * (s - a) - kq;
@@ -211,6 +220,98 @@ __device__ __forceinline__ void grid_totals(const double* scal, int grid, int ns
 #pragma unroll
   for (int m = 8; m >= 1; m >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, m);
   if (sub == 0 && k < nslots) s_tot[k] = acc;
+}
+
+// Grid totals when slots 0 .. S_DUAL_A hold double-float partials (float2 hi, lo
+// in the 8-byte slots) and S_G2 .. S_TA2 FP64 ones.  Each warp-level FP64
+// instruction occupies this part's FP64 unit for ~19 cycles whatever the number
+// of active lanes, so the nine double-float slots are added on the FP32 pipes by
+// warps 0-4 (16 lanes per slot) and the six FP64 slots by warps 5-7 only.  The
+// order of the additions is fixed (deterministic).
+__device__ __forceinline__ void grid_totals_mixed(const double* scal, int grid, double* s_tot) {
+  const int t = threadIdx.x, sub = t & 15;
+  if (t < 160) {
+    const int k = t >> 4;                       // 0 .. 9; k = 9 (threads 144-159) holds no slot
+    df acc{0.f, 0.f};
+    if (k <= S_DUAL_A) {
+      const float2* part = reinterpret_cast<const float2*>(scal + (size_t)k * grid);
+      for (int c = sub; c < grid; c += 16) {
+        const float2 v = part[c];
+        df_add(acc, df{v.x, v.y});
+      }
+    }
+#pragma unroll
+    for (int m = 8; m >= 1; m >>= 1) df_add(acc, df_shfl_xor(acc, m));
+    if (sub == 0 && k <= S_DUAL_A) s_tot[k] = df_to_double(acc);
+  } else {
+    const int k = S_G2 + ((t - 160) >> 4);      // 9 .. 14
+    const double* part = scal + (size_t)k * grid;
+    double acc = 0.0;
+    for (int base = 0; base < grid; base += 16 * 12) {
+      double v[12];
+#pragma unroll
+      for (int q = 0; q < 12; ++q) {
+        const int c2 = base + sub + 16 * q;
+        v[q] = c2 < grid ? part[c2] : 0.0;
+      }
+#pragma unroll
+      for (int q = 0; q < 6; ++q) v[q] += v[q + 6];
+      v[0] += v[3];
+      v[1] += v[4];
+      v[2] += v[5];
+      acc += (v[0] + v[1]) + v[2];
+    }
+#pragma unroll
+    for (int m = 8; m >= 1; m >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, m);
+    if (sub == 0) s_tot[k] = acc;
+  }
+}
+
+// Grid totals of double-float partials (float2 hi, lo in every 8-byte slot),
+// added on the FP32 pipes in a fixed order (16 lanes per slot, then a fixed
+// shuffle tree); warp 0 converts the 15 totals to FP64 (three FP64 instructions
+// in all: each warp-level FP64 instruction occupies this part's FP64 unit for
+// ~19 cycles whatever the number of active lanes).  s_tot is valid after the
+// caller's next __syncthreads.
+__device__ __forceinline__ void grid_totals_df(const float2* scal, int grid, double* s_tot) {
+  __shared__ float2 s_totf[16];
+  const int t = threadIdx.x, k = t >> 4, sub = t & 15;
+  df acc{0.f, 0.f};
+  if (k < S_COUNT - 1) {
+    const float2* part = scal + (size_t)k * grid;
+    for (int c = sub; c < grid; c += 16) {
+      const float2 v = part[c];
+      df_add(acc, df{v.x, v.y});
+    }
+  }
+#pragma unroll
+  for (int m = 8; m >= 1; m >>= 1) df_add(acc, df_shfl_xor(acc, m));
+  if (sub == 0 && k < S_COUNT - 1) s_totf[k] = make_float2(acc.hi, acc.lo);
+  __syncthreads();
+  if (t < S_COUNT - 1) s_tot[t] = (double)s_totf[t].x + (double)s_totf[t].y;
+}
+
+// N double-float values per thread summed over the first nr threads of the block
+// (deterministic): through shared memory s_rows (N x kThreads float2), warp k
+// sums value k and lane 0 writes it to out[k * stride] as a double-float pair.
+template <int N>
+__device__ __forceinline__ void rows_sum_df(const df (&v)[N], float2* s_rows, int nr, float2* out, int stride) {
+  nr = nr < kThreads ? nr : kThreads;
+  if ((int)threadIdx.x < nr) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) s_rows[k * kThreads + threadIdx.x] = make_float2(v[k].hi, v[k].lo);
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int k = warp; k < N; k += kWarps) {
+    df acc{0.f, 0.f};
+    for (int t = lane; t < nr; t += 32) {
+      const float2 x = s_rows[k * kThreads + t];
+      df_add(acc, df{x.x, x.y});
+    }
+    acc = df_warp_sum(acc);
+    if (lane == 0) out[(size_t)k * stride] = make_float2(acc.hi, acc.lo);
+  }
 }
 
 // N per-row values summed over the CTA's rows in row order (deterministic): the
@@ -368,11 +469,8 @@ __device__ __forceinline__ void s_phase(const double* s_tot, const SPhaseArgs& q
 }
 
 // x_i = sum_j P_ij rhs_j for one row, one warp, double-float (result in all lanes).
-// The row is taken in steps of 128 pairs (four 16-byte loads of P and four of
-// the right-hand side per lane); the next step's eight loads are issued before
-// the current step's products, so one L2 round trip overlaps the next instead
-// of the loop waiting for each in turn.  Every load reads inside the row: an
-// index past npair is clamped to the last pair and its value then zeroed.
+// Every load reads inside the row: an index past npair is clamped to the last
+// pair and its value then zeroed.
 __device__ __forceinline__ void row_pair_load(const float4* P4, const float4* R4, int j, int npair, float4& p,
                                               float4& r) {
   const int jj = j < npair ? j : npair - 1;
@@ -389,25 +487,19 @@ __device__ __forceinline__ df row_dot(const float2* __restrict__ Prow, const flo
   const float4* R4 = reinterpret_cast<const float4*>(rhs_s);
   df a0{0.f, 0.f}, a1{0.f, 0.f}, a2{0.f, 0.f}, a3{0.f, 0.f};
   const int lane = threadIdx.x & 31;
-  float4 p[4], r[4];
+  // blocks of 512 pairs: all sixteen loads of P and of the right-hand side of a
+  // lane are issued before any product, so a row of up to 1024 columns costs
+  // one L2 round trip
+  for (int base = 0; base < npair; base += 512) {
+    float4 p[16], r[16];
 #pragma unroll
-  for (int u = 0; u < 4; ++u) row_pair_load(P4, R4, lane + 32 * u, npair, p[u], r[u]);
-  for (int base = 0; base < npair; base += 128) {
-    float4 pn[4], rn[4];
+    for (int u = 0; u < 16; ++u) row_pair_load(P4, R4, base + lane + 32 * u, npair, p[u], r[u]);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) row_pair_load(P4, R4, base + 128 + lane + 32 * u, npair, pn[u], rn[u]);
-    df_fma(a0, df{p[0].x, p[0].y}, df{r[0].x, r[0].y});
-    df_fma(a1, df{p[0].z, p[0].w}, df{r[0].z, r[0].w});
-    df_fma(a2, df{p[1].x, p[1].y}, df{r[1].x, r[1].y});
-    df_fma(a3, df{p[1].z, p[1].w}, df{r[1].z, r[1].w});
-    df_fma(a0, df{p[2].x, p[2].y}, df{r[2].x, r[2].y});
-    df_fma(a1, df{p[2].z, p[2].w}, df{r[2].z, r[2].w});
-    df_fma(a2, df{p[3].x, p[3].y}, df{r[3].x, r[3].y});
-    df_fma(a3, df{p[3].z, p[3].w}, df{r[3].z, r[3].w});
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      p[u] = pn[u];
-      r[u] = rn[u];
+    for (int u = 0; u < 16; u += 2) {
+      df_fma(a0, df{p[u].x, p[u].y}, df{r[u].x, r[u].y});
+      df_fma(a1, df{p[u].z, p[u].w}, df{r[u].z, r[u].w});
+      df_fma(a2, df{p[u + 1].x, p[u + 1].y}, df{r[u + 1].x, r[u + 1].y});
+      df_fma(a3, df{p[u + 1].z, p[u + 1].w}, df{r[u + 1].z, r[u + 1].w});
     }
   }
   df_add(a0, a1);

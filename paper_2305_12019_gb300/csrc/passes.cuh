@@ -322,6 +322,7 @@ struct RunAcc<double> {
   __device__ void merge(part_t p) { v += p; }
   __device__ part_t part() const { return v; }
   __device__ double get() const { return v; }
+  __device__ df get_df() const { return df_from(v); }
   __device__ void reset() { v = 0.0; }
 };
 template <>
@@ -332,6 +333,7 @@ struct RunAcc<float> {
   __device__ void merge(part_t p) { df_add(v, df{p.x, p.y}); }
   __device__ part_t part() const { return make_float2(v.hi, v.lo); }
   __device__ double get() const { return df_to_double(v); }
+  __device__ df get_df() const { return df_sum(df{0.f, 0.f}, v); }
   __device__ void reset() { v.hi = 0.f; v.lo = 0.f; }
 };
 
@@ -340,8 +342,9 @@ struct RunAcc<float> {
 // Thread t owns vector qv = t % Q of the column group t / Q (Q = TB / VEC <= 256),
 // so the threads of a step read consecutive 16-byte vectors (conflict-free).
 // At the end of a slab the groups are summed through shared memory and the
-// row epilogue Epi runs once per row j of the slab with t_j and ta_j (given the
-// global row and its index among the CTA's slab rows, k * TB + j for its k-th slab).
+// row epilogue Epi runs once per row j of the slab with t_j and ta_j as
+// double-float values (given the global row and its index among the CTA's slab
+// rows, k * TB + j for its k-th slab).
 // ---------------------------------------------------------------------------
 template <typename T, typename Epi>
 struct PassB {
@@ -447,7 +450,7 @@ struct PassB {
         ta.merge(redp[(size_t)(G + gq) * TB + j]);
       }
       const int64_t gj = (int64_t)s * TB + j;
-      if (gj < d) epi->row(gj, k * TB + j, t.get(), ta.get());
+      if (gj < d) epi->row(gj, k * TB + j, t.get_df(), ta.get_df());
     }
     __syncthreads();
   }

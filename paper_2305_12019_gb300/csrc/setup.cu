@@ -43,12 +43,108 @@ __global__ void sumsq_kernel(const TI* __restrict__ Z, int64_t d, int64_t n, int
   if (bad) atomicOr(nonfinite, 1);
 }
 
+// The block partials summed by one warp in a fixed order (lane l takes parts l,
+// l + 32, ...; then a fixed shuffle tree), so every caller gets the same bits.
+__device__ __forceinline__ double sum_parts_warp(const double* part, int np) {
+  const int lane = threadIdx.x & 31;
+  double t = 0.0;
+  for (int i = lane; i < np; i += 32) t += part[i];
+  return warp_sum(t);
+}
+
 __global__ void sum_parts_kernel(const double* part, int np, double* out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double t = 0.0;
-    for (int i = 0; i < np; ++i) t += part[i];
-    *out = t;
+  if (threadIdx.x >= 32 || blockIdx.x != 0) return;
+  const double t = sum_parts_warp(part, np);
+  if (threadIdx.x == 0) *out = t;
+}
+
+// FP32 / FP64 storage in one pass over the caller's column-major Z: the slab
+// copy, the squares summed for ||Z||_F (FP32 input: exact squares, fmaf, added
+// in double-float; FP64 input: FP64) and the finiteness check.  Work item =
+// (slab, group of kIngCols columns); the item's output is one contiguous run.
+constexpr int kIngCols = 32;
+
+template <typename TI>
+struct SqAcc;
+template <>
+struct SqAcc<float> {
+  df a{0.f, 0.f};
+  __device__ __forceinline__ void add(float v) {
+    const float p = v * v;
+    const float e = fmaf(v, v, -p);
+    float s, e2;
+    two_sum(a.hi, p, s, e2);
+    a.lo += e2 + e;
+    a.hi = s;
   }
+  __device__ __forceinline__ double get() const { return df_to_double(a); }
+};
+template <>
+struct SqAcc<double> {
+  double a = 0.0;
+  __device__ __forceinline__ void add(double v) { a = fma(v, v, a); }
+  __device__ __forceinline__ double get() const { return a; }
+};
+
+template <typename TI, typename TS>
+__global__ void __launch_bounds__(256) ingest_kernel(const TI* __restrict__ Z, int64_t ldz, Layout L,
+                                                     TS* __restrict__ out, double* part, int* nonfinite) {
+  const int ngrp = (int)((L.n + kIngCols - 1) / kIngCols);
+  const int64_t items = (int64_t)L.NB * ngrp;
+  const int64_t per_slab = (int64_t)L.TB * L.n;
+  SqAcc<TI> acc;
+  bool bad = false;
+  for (int64_t w = blockIdx.x; w < items; w += gridDim.x) {
+    const int s = (int)(w / ngrp), g = (int)(w - (int64_t)s * ngrp);
+    const int64_t i0 = (int64_t)g * kIngCols;
+    const int nc = (int)(L.n - i0 < kIngCols ? L.n - i0 : kIngCols);
+    const int64_t j0 = (int64_t)s * L.TB;
+    const int rows = (int)(L.d - j0 < L.TB ? L.d - j0 : L.TB);   // valid rows of this slab (>= 1)
+    TS* o = out + s * per_slab + i0 * L.TB;
+    const TI* zin = Z + i0 * ldz + j0;
+    const int total = nc * L.TB;
+    for (int e = threadIdx.x; e < total; e += 256) {
+      const int c = e / L.TB, jl = e - c * L.TB;
+      TI v = (TI)0;
+      if (jl < rows) {
+        v = zin[(int64_t)c * ldz + jl];
+        bad |= !isfinite(v);
+        acc.add(v);
+      }
+      o[e] = (TS)v;
+    }
+  }
+  __shared__ double sred[8];
+  const double t = warp_sum(acc.get());
+  if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double u = 0.0;
+    for (int k = 0; k < 8; ++k) u += sred[k];
+    part[blockIdx.x] = u;
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(nonfinite, 1);
+}
+
+// ||Z||_F^2 from the ingest partials (every block sums them the same way), then
+// sc_i = 1 / Z_scale with Z_scale = sqrt(||Z||_F); block 0 stores both scalars.
+__global__ void ingest_scale_kernel(const double* part, int np, int64_t n, double* sumsq, double* sc,
+                                    double* zscale) {
+  __shared__ double s_zs;
+  if (threadIdx.x < 32) {
+    const double t = sum_parts_warp(part, np);
+    if (threadIdx.x == 0) {
+      s_zs = sqrt(sqrt(t));
+      if (blockIdx.x == 0) {
+        *sumsq = t;
+        *zscale = s_zs;
+      }
+    }
+  }
+  __syncthreads();
+  const double inv = 1.0 / s_zs;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    sc[i] = inv;
 }
 
 template <typename TI, typename TS>
@@ -141,25 +237,26 @@ static void quantize_t(const TI* Z, int64_t ldz, const Layout& L, void* out, dou
 cudaError_t run_ingest(const void* Z, int zdt, int64_t ldz, const Layout& L, void* out, int store, double* part,
                        int nparts, double* sumsq, int* nonfinite, double* sc, double* zscale, double* amax,
                        double* colscale, cudaStream_t st) {
+  const int nb = (int)std::min<int64_t>((L.n + 255) / 256, 1024);
+  if (store == GDWD_F64 || store == GDWD_F32) {
+    const int64_t items = (int64_t)L.NB * ((L.n + kIngCols - 1) / kIngCols);
+    const int blocks = (int)std::min<int64_t>(items, nparts);
+    if (zdt == GDWD_F64 && store == GDWD_F64)
+      ingest_kernel<double, double><<<blocks, 256, 0, st>>>((const double*)Z, ldz, L, (double*)out, part, nonfinite);
+    else if (zdt == GDWD_F64 && store == GDWD_F32)
+      ingest_kernel<double, float><<<blocks, 256, 0, st>>>((const double*)Z, ldz, L, (float*)out, part, nonfinite);
+    else if (zdt == GDWD_F32 && store == GDWD_F64)
+      ingest_kernel<float, double><<<blocks, 256, 0, st>>>((const float*)Z, ldz, L, (double*)out, part, nonfinite);
+    else
+      ingest_kernel<float, float><<<blocks, 256, 0, st>>>((const float*)Z, ldz, L, (float*)out, part, nonfinite);
+    ingest_scale_kernel<<<nb, 256, 0, st>>>(part, blocks, L.n, sumsq, sc, zscale);
+    return cudaGetLastError();
+  }
   if (zdt == GDWD_F64)
     sumsq_kernel<double><<<nparts, 256, 0, st>>>((const double*)Z, L.d, L.n, ldz, part, nonfinite);
   else
     sumsq_kernel<float><<<nparts, 256, 0, st>>>((const float*)Z, L.d, L.n, ldz, part, nonfinite);
   sum_parts_kernel<<<1, 32, 0, st>>>(part, nparts, sumsq);
-  const int blocks = 152 * 8;
-  const int nb = (int)std::min<int64_t>((L.n + 255) / 256, 1024);
-  if (store == GDWD_F64 || store == GDWD_F32) {
-    if (zdt == GDWD_F64 && store == GDWD_F64)
-      to_slabs_kernel<double, double><<<blocks, 256, 0, st>>>((const double*)Z, ldz, L, (double*)out);
-    else if (zdt == GDWD_F64 && store == GDWD_F32)
-      to_slabs_kernel<double, float><<<blocks, 256, 0, st>>>((const double*)Z, ldz, L, (float*)out);
-    else if (zdt == GDWD_F32 && store == GDWD_F64)
-      to_slabs_kernel<float, double><<<blocks, 256, 0, st>>>((const float*)Z, ldz, L, (double*)out);
-    else
-      to_slabs_kernel<float, float><<<blocks, 256, 0, st>>>((const float*)Z, ldz, L, (float*)out);
-    scale_kernel<<<nb, 256, 0, st>>>(sumsq, L.n, sc, zscale);
-    return cudaGetLastError();
-  }
   const bool f64 = zdt == GDWD_F64;
   switch (store) {
     case GDWD_BF16:
@@ -456,10 +553,10 @@ int gram_ksplit(const Layout& L, int sms) {
 }
 
 cudaError_t run_gram(int store, const Layout& L, int ksplit, double* Kpart, const double* sc, double mu, double* G,
-                     bool tensor_cores, int* err, uint64_t timeout_ns, cudaStream_t st) {
+                     bool tensor_cores, void* scratch, int* err, uint64_t timeout_ns, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
   if (tensor_cores) {
-    e = run_gram_tc(store, L, ksplit, Kpart, err, timeout_ns, st);
+    e = run_gram_tc(store, L, ksplit, Kpart, scratch, err, timeout_ns, st);
   } else {
     const int Tt = (int)((L.n + kGT - 1) / kGT);
     const int tiles = Tt * (Tt + 1) / 2;
@@ -487,10 +584,10 @@ cudaError_t run_gram(int store, const Layout& L, int ksplit, double* Kpart, cons
 // ------------------------------------------------------------------ factor
 // One cooperative launch computes G = L L^T, X = L^{-1} and P = X^T X = G^{-1}
 // with 32x32 tiles.  The matrices live in double-float (float2 hi/lo, ~48-bit
-// mantissa): FP64 issues at 1/58 of the FP32 rate on this part, so the bulk
-// tile updates (n^3/6 multiply-adds in each of the three stages) run in
-// double-float on the FP32 pipes; the small sequential pieces (the 32x32
-// diagonal Cholesky, the triangular solves against it) run in FP64.
+// mantissa): FP64 issues at 1/58 of the FP32 rate on this part, so everything
+// runs in double-float on the FP32 pipes -- the bulk tile updates (n^3/6
+// multiply-adds in each of the three stages) and the small sequential pieces
+// (the 32x32 diagonal Cholesky, the triangular solves against it).
 constexpr int kNB = 32;   // tile
 
 __device__ __forceinline__ double f2d(float2 v) { return (double)v.x + (double)v.y; }
@@ -550,42 +647,87 @@ __device__ __forceinline__ void tri_index(int t, int& i, int& j) {
   j = t - ii * (ii + 1) / 2;
 }
 
-// Cholesky of the 32 x 32 FP64 tile D (lower triangle, in place) by all threads
-// of the CTA, column by column, with a look-ahead of one column: after column c is
-// scaled, warp 0 updates column c+1 alone and takes its pivot (sqrt and reciprocal,
-// a dependent FP64 chain) while the other warps update the rest of the trailing
-// triangle.  Dinv receives the reciprocals of the diagonal.  A non-positive pivot
-// records GDWD_ENOTPD (and continues with 1).
-__device__ __forceinline__ void chol_pivot(double (*D)[kNB + 1], double* Dinv, int c, int* err) {
-  double piv = D[c][c];
-  if (!(piv > 0.0) || !isfinite(piv)) {
-    atomicCAS(err, 0, (int)GDWD_ENOTPD);
-    piv = 1.0;
-  }
-  const double lc = sqrt_nr(piv);
-  D[c][c] = lc;
-  Dinv[c] = rcp_nr(lc);
+// The diagonal tiles and the triangular solves against them run in
+// double-float too: FP64 issues at one warp instruction per 64 cycles per SM
+// sub-partition, which made the 32-column pivot chain of a tile the factor's
+// critical path.
+__device__ __forceinline__ df df_of(float2 v) { return df{v.x, v.y}; }
+__device__ __forceinline__ float2 f2_of(df v) { return make_float2(v.hi, v.lo); }
+__device__ __forceinline__ df df_shfl(df a, int src) {
+  return df{__shfl_sync(0xffffffffu, a.hi, src), __shfl_sync(0xffffffffu, a.lo, src)};
+}
+// a - b * c
+__device__ __forceinline__ df df_fnma(df a, df b, df c) { return df_sum(a, df_neg(df_mul(b, c))); }
+
+// r (1 + e) for a small FP32 e (the correction of a Newton step)
+__device__ __forceinline__ df df_scale_1p(df r, float e) {
+  const float c = r.hi * e;
+  return df_sum(r, df{c, fmaf(r.hi, e, -c)});
 }
 
-__device__ void chol_tile(double (*D)[kNB + 1], double* Dinv, int* err) {
+// 1 / sqrt(p) and sqrt(p) of a positive double-float p inside the normal FP32
+// range: an FP32 seed and two double-float Newton steps (~1e-14 relative).
+__device__ __forceinline__ void df_rsqrt_sqrt(df p, df& inv, df& s) {
+  df r{rsqrt_approx(p.hi), 0.f};
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const df t = df_mul(p, df_mul(r, r));        // p r^2, close to 1
+    const float e = (1.0f - t.hi) - t.lo;        // 1 - t.hi is exact there
+    r = df_scale_1p(r, 0.5f * e);
+  }
+  inv = r;
+  s = df_mul(p, r);
+}
+
+// 1 / b of a double-float b inside the normal FP32 range (two Newton steps).
+__device__ __forceinline__ df df_rcp(df b) {
+  df r{rcp_approx(b.hi), 0.f};
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const df t = df_mul(b, r);
+    r = df_scale_1p(r, (1.0f - t.hi) - t.lo);
+  }
+  return r;
+}
+
+// Pivot c of the tile: L_cc = sqrt(D_cc) into D, 1 / L_cc into Dinv.  A
+// non-positive pivot records GDWD_ENOTPD (and continues with 1).
+__device__ __forceinline__ void chol_pivot_df(float2 (*D)[kNB + 1], float2* Dinv, int c, int* err) {
+  df p = df_of(D[c][c]);
+  if (!(p.hi > 0.f) || !isfinite(p.hi)) {
+    atomicCAS(err, 0, (int)GDWD_ENOTPD);
+    p = df{1.f, 0.f};
+  }
+  df inv, sq;
+  df_rsqrt_sqrt(p, inv, sq);
+  D[c][c] = f2_of(sq);
+  Dinv[c] = f2_of(inv);
+}
+
+// Cholesky of the 32 x 32 double-float tile D (lower triangle, in place) by all
+// threads of the CTA, column by column, with a look-ahead of one column: after
+// column c is scaled, warp 0 updates column c+1 alone and takes its pivot while
+// the other warps update the rest of the trailing triangle.
+__device__ void chol_tile_df(float2 (*D)[kNB + 1], float2* Dinv, int* err) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (threadIdx.x == 0) chol_pivot(D, Dinv, 0, err);
+  if (threadIdx.x == 0) chol_pivot_df(D, Dinv, 0, err);
   for (int c = 0; c < kNB; ++c) {
     __syncthreads();                                   // pivot c is in D[c][c], Dinv[c]
-    if (threadIdx.x > c && threadIdx.x < kNB) D[threadIdx.x][c] *= Dinv[c];
+    if (threadIdx.x > c && threadIdx.x < kNB)
+      D[threadIdx.x][c] = f2_of(df_mul(df_of(D[threadIdx.x][c]), df_of(Dinv[c])));
     __syncthreads();                                   // column c of L is complete
     if (c + 1 == kNB) break;
     if (warp == 0) {
       // column c+1 first, then its pivot
-      if (lane >= c + 1) D[lane][c + 1] -= D[lane][c] * D[c + 1][c];
+      if (lane >= c + 1) D[lane][c + 1] = f2_of(df_fnma(df_of(D[lane][c + 1]), df_of(D[lane][c]), df_of(D[c + 1][c])));
       __syncwarp();
-      if (lane == 0) chol_pivot(D, Dinv, c + 1, err);
+      if (lane == 0) chol_pivot_df(D, Dinv, c + 1, err);
     } else {
       // the rest of the trailing triangle: D[r][q] -= L[r][c] L[q][c], c+2 <= q <= r
       const int m = kNB - 2 - c;                       // rows / columns c+2 .. 31
       for (int e = threadIdx.x - 32; e < m * m; e += kThreads - 32) {
         const int r = c + 2 + e / m, q = c + 2 + e % m;
-        if (q <= r) D[r][q] -= D[r][c] * D[q][c];
+        if (q <= r) D[r][q] = f2_of(df_fnma(df_of(D[r][q]), df_of(D[r][c]), df_of(D[q][c])));
       }
     }
   }
@@ -594,8 +736,8 @@ __device__ void chol_tile(double (*D)[kNB + 1], double* Dinv, int* err) {
 
 __global__ void __launch_bounds__(kThreads, 1) factor_kernel(FactorArgs a) {
   __shared__ float2 T0[kNB][kNB + 1], T1[kNB][kNB + 1], T2[kNB][kNB + 1];
-  __shared__ double D[kNB][kNB + 1];     // FP64 diagonal tile
-  __shared__ double Dinv[kNB];           // its inverse diagonal
+  __shared__ float2 D[kNB][kNB + 1];     // double-float diagonal tile
+  __shared__ float2 Dinv[kNB];           // its inverse diagonal
   __shared__ int s_flag;
   __shared__ double s_red[kWarps + 1];
   const int64_t n = a.n;
@@ -624,30 +766,29 @@ __global__ void __launch_bounds__(kThreads, 1) factor_kernel(FactorArgs a) {
   // updates from the steps before k are complete) -- n warp tasks in all.
   // Phase 2: the trailing update of the Cholesky (A_IJ -= L_Ik L_Jk^T, k < J <= I)
   // and of the inverse (X_IJ -= L_Ik X_kJ, I > k >= J), tile-parallel; CTA 0
-  // instead updates diagonal tile k+1 and factors it (FP64, all its threads), a
+  // instead updates diagonal tile k+1 and factors it (all its threads), a
   // look-ahead of one tile that keeps the diagonal factor off the critical path
   // whenever the trailing update takes longer.  Two grid barriers per k.
   auto factor_diag = [&](int64_t k0) {    // CTA 0: D <- tile (k0, k0) of A, factor, store L
     for (int t = threadIdx.x; t < kNB * kNB; t += kThreads) {
       const int r = t / kNB, c = t % kNB;
       const int64_t gr = k0 + r, gc = k0 + c;
-      D[r][c] = (gr < n && gc < n) ? f2d(A[gr * n + gc]) : (gr == gc ? 1.0 : 0.0);
+      D[r][c] = (gr < n && gc < n) ? A[gr * n + gc] : make_float2(gr == gc ? 1.f : 0.f, 0.f);
     }
-    __syncthreads();
-    chol_tile(D, Dinv, a.err);
+    chol_tile_df(D, Dinv, a.err);
     for (int t = threadIdx.x; t < kNB * kNB; t += kThreads) {
       const int r = t / kNB, c = t % kNB;
       const int64_t gr = k0 + r, gc = k0 + c;
-      if (gr < n && gc < n && c <= r) A[gr * n + gc] = d2f(D[r][c]);
+      if (gr < n && gc < n && c <= r) A[gr * n + gc] = D[r][c];
     }
     __syncthreads();
   };
-  // forward substitution L_kk x = b on one warp (lane r holds entry r; FP64)
-  auto trsv = [&](double x) {
+  // forward substitution L_kk x = b on one warp (lane r holds entry r; double-float)
+  auto trsv = [&](df x) {
     for (int c = 0; c < kNB; ++c) {
-      const double xc = __shfl_sync(0xffffffffu, x, c) * Dinv[c];
+      const df xc = df_mul(df_shfl(x, c), df_of(Dinv[c]));
       if (lane == c) x = xc;
-      if (lane > c) x -= xc * D[lane][c];
+      if (lane > c) x = df_fnma(x, xc, df_of(D[lane][c]));
     }
     return x;
   };
@@ -659,10 +800,10 @@ __global__ void __launch_bounds__(kThreads, 1) factor_kernel(FactorArgs a) {
     for (int t = threadIdx.x; t < kNB * kNB; t += kThreads) {
       const int r = t / kNB, c = t % kNB;
       const int64_t gr = k0 + r, gc = k0 + c;
-      D[r][c] = (gr < n && gc < n && c <= r) ? f2d(A[gr * n + gc]) : (gr == gc ? 1.0 : 0.0);
+      D[r][c] = (gr < n && gc < n && c <= r) ? A[gr * n + gc] : make_float2(gr == gc ? 1.f : 0.f, 0.f);
     }
     __syncthreads();
-    if (threadIdx.x < kNB) Dinv[threadIdx.x] = rcp_nr(D[threadIdx.x][threadIdx.x]);
+    if (threadIdx.x < kNB) Dinv[threadIdx.x] = f2_of(df_rcp(df_of(D[threadIdx.x][threadIdx.x])));
     __syncthreads();
     // phase 1: panel rows i >= k0 + 32 of A, then columns j < min(n, k0 + 32) of X's tile row k
     {
@@ -671,12 +812,12 @@ __global__ void __launch_bounds__(kThreads, 1) factor_kernel(FactorArgs a) {
       for (int64_t q = (int64_t)cta * kWarps + warp; q < npanel + ncols; q += (int64_t)grid * kWarps) {
         if (q < npanel) {
           const int64_t i = k0 + kNB + q;
-          const double x = trsv((k0 + lane < n) ? f2d(A[i * n + k0 + lane]) : 0.0);
-          if (k0 + lane < n) A[i * n + k0 + lane] = d2f(x);
+          const df x = trsv((k0 + lane < n) ? df_of(A[i * n + k0 + lane]) : df{0.f, 0.f});
+          if (k0 + lane < n) A[i * n + k0 + lane] = f2_of(x);
         } else {
           const int64_t j = q - npanel;
-          const double x = trsv((k0 + lane < n) ? f2d(X[(k0 + lane) * n + j]) : 0.0);
-          if (k0 + lane < n) X[(k0 + lane) * n + j] = d2f(x);
+          const df x = trsv((k0 + lane < n) ? df_of(X[(k0 + lane) * n + j]) : df{0.f, 0.f});
+          if (k0 + lane < n) X[(k0 + lane) * n + j] = f2_of(x);
         }
       }
     }
@@ -707,7 +848,7 @@ __global__ void __launch_bounds__(kThreads, 1) factor_kernel(FactorArgs a) {
         load_tile_df(T0, X, n, I0, J0, false);
         load_tile_df(T1, A, n, I0, k0, false);
         for (int q = threadIdx.x; q < kNB * kNB; q += kThreads) {     // T2 = X[k-tile, J-tile]^T
-          const int r = q / kNB, c = q % kNB;
+          const int r = q % kNB, c = q / kNB;                        // consecutive threads: consecutive columns of X
           const int64_t gr = k0 + c, gc = J0 + r;
           T2[r][c] = (gr < n && gc < n) ? X[gr * n + gc] : make_float2(0.f, 0.f);
         }
@@ -747,7 +888,7 @@ __global__ void __launch_bounds__(kThreads, 1) factor_kernel(FactorArgs a) {
       for (int M = ii; M < nb; ++M) {
         const int64_t M0 = (int64_t)M * kNB;
         for (int q = threadIdx.x; q < kNB * kNB; q += kThreads) {
-          const int r = q / kNB, c = q % kNB;
+          const int r = q % kNB, c = q / kNB;                        // consecutive threads: consecutive columns of X
           const int64_t gm = M0 + c;
           T1[r][c] = (gm < n && I0 + r < n) ? X[gm * n + I0 + r] : make_float2(0.f, 0.f);
           T2[r][c] = (gm < n && J0 + r < n) ? X[gm * n + J0 + r] : make_float2(0.f, 0.f);

@@ -156,11 +156,14 @@ cudaError_t run_multi_f64(int K, const MultiArgs<double>& a, int smem_limit, cud
 cudaError_t run_multi_f32(int store, int K, const MultiArgs<float>& a, int smem_limit, cudaStream_t st);
 
 // Host-side launchers (defined in the .cu files).
-int choose_chunk_cols(int store, const Layout& L, int grid, int smem_limit);
+int choose_chunk_cols(int store, const Layout& L, int grid, int smem_limit, bool wide = false);
 cudaError_t run_iterate_f64(const IterArgs<double>& a, int smem_limit, cudaStream_t st);
 cudaError_t run_iterate_f32(int store, const IterArgs<float>& a, int smem_limit, cudaStream_t st);
+// wide = true reads FP32 storage into FP64 arithmetic (partial then holds n x NB
+// doubles); other storage ignores it.
 cudaError_t run_apply(int store, const Layout& L, int trans, const double* x, const double* sc, double* out,
-                      void* partial, int grid, int smem_limit, int* err, uint64_t tmo, cudaStream_t st);
+                      void* partial, int grid, int smem_limit, int* err, uint64_t tmo, cudaStream_t st,
+                      bool wide = false);
 
 // set-up (setup.cu)
 struct FactorArgs {
@@ -182,15 +185,18 @@ struct FactorArgs {
 cudaError_t run_ingest(const void* Z, int zdt, int64_t ldz, const Layout& L, void* out, int store, double* part,
                        int nparts, double* sumsq, int* nonfinite, double* sc, double* zscale, double* amax,
                        double* colscale, cudaStream_t st);
-// Gram: tensor-core path (gram_tc.cu) for BF16 / FP16 / E4M3 storage when
-// gram_tc_supported(); SIMT double-float path (setup.cu) otherwise.
+// Gram: tensor-core path (gram_tc.cu) for BF16 / FP16 / E4M3 storage, and for
+// FP32 storage through its three-term BF16 split (which needs
+// gram_tc_scratch_bytes() of device scratch), when gram_tc_supported(); SIMT
+// double-float path (setup.cu) otherwise.
 bool gram_tc_supported(int store, const Layout& L);
-int gram_tc_ksplit(const Layout& L, int sms);
-cudaError_t run_gram_tc(int store, const Layout& L, int ksplit, double* Kpart, int* err, uint64_t timeout_ns,
-                        cudaStream_t st);
+size_t gram_tc_scratch_bytes(int store, const Layout& L);
+int gram_tc_ksplit(int store, const Layout& L, int sms);
+cudaError_t run_gram_tc(int store, const Layout& L, int ksplit, double* Kpart, void* scratch, int* err,
+                        uint64_t timeout_ns, cudaStream_t st);
 int gram_ksplit(const Layout& L, int sms);
 cudaError_t run_gram(int store, const Layout& L, int ksplit, double* Kpart, const double* sc, double mu, double* G,
-                     bool tensor_cores, int* err, uint64_t timeout_ns, cudaStream_t st);
+                     bool tensor_cores, void* scratch, int* err, uint64_t timeout_ns, cudaStream_t st);
 cudaError_t run_factor(const FactorArgs& a, cudaStream_t st);
 
 cudaError_t launch_prox(const double* a, const double* r0, const double* omega, double sigma, double q,

@@ -38,7 +38,11 @@ class Result(ctypes.Structure):
                 ("iters", c_int32), ("status", c_int32), ("reserved", c_int64 * 4)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        out = {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        # quantized-stage iterations (refinement sweep); CG steps and Step 1c solves (inexact solver)
+        out["quantized_iters"], out["cg_steps"], out["step1c_solves"] = (int(self.reserved[0]), int(self.reserved[1]),
+                                                                        int(self.reserved[2]))
+        return out
 
 
 class Info(ctypes.Structure):
@@ -149,7 +153,7 @@ class Solver:
         o.stop_rule = int(stop_rule)
         o.dots_every = int(dots_every)
         o.kernelized = int(kernelized)
-        o.solver = {"smw": 0, "direct": 1}[solver] if isinstance(solver, str) else int(solver)
+        o.solver = {"smw": 0, "direct": 1, "inexact": 2}[solver] if isinstance(solver, str) else int(solver)
         self._direct = o.solver == 1
         o.cgrid_sequential = int(cgrid_sequential)
         o.mu, o.tau, o.tol, o.sigma0 = mu, tau, tol, sigma0

@@ -80,7 +80,7 @@ def test_invalid_arguments_rejected(lib):
     o.store = 9
     assert _create(lib, Z, y, opts=o)[0] == 1
     # option values and combinations checked before any device work
-    for field, val in (("kernelized", 2), ("solver", 2), ("gram_path", 2), ("stop_rule", 3), ("dots_every", -1)):
+    for field, val in (("kernelized", 2), ("solver", 3), ("gram_path", 2), ("stop_rule", 3), ("dots_every", -1)):
         o = gdwd.default_options()
         setattr(o, field, val)
         assert _create(lib, Z, y, opts=o)[0] == 1, field
@@ -92,6 +92,14 @@ def test_invalid_arguments_rejected(lib):
         st, h = _create(lib, Z, y, opts=o)
         assert st == 8 and h.value is None, kw          # GDWD_EUNSUPPORTED
         assert b"direct solver" in lib.gdwd_last_error(None)
+    for kw in ({"refine": 1}, {"kernelized": 1}, {"store": gdwd.DTYPES["e4m3"]}):
+        o = gdwd.default_options()
+        o.solver = 2
+        for k, v in kw.items():
+            setattr(o, k, v)
+        st, h = _create(lib, Z, y, opts=o)
+        assert st == 8 and h.value is None, kw          # GDWD_EUNSUPPORTED
+        assert b"inexact solver" in lib.gdwd_last_error(None)
     assert lib.gdwd_free(None) == 0
     assert lib.gdwd_solve(None, None, 0, None, 0, None, None) == 1
     assert lib.gdwd_prox(None, None, None, 1.0, -1.0, 4, None, None) == 1

@@ -85,3 +85,23 @@ def test_injected_allocation_failure(gdwd_lib, monkeypatch, k):
     with gdwd_lib.Solver(Z, y, 1.0, 1.0, store="f32") as s:
         res, w, _ = s.solve()
     assert res[0]["status"] == 0
+
+
+@pytest.mark.parametrize("store,solver", [("f32", "smw"), ("f64", "smw"), ("bf16", "smw"), ("f32", "direct"),
+                                          ("f32", "inexact")])
+def test_non_finite_data_refused(gdwd_lib, store, solver):
+    """A NaN or Inf in Z is refused with GDWD_EINVAL and no handle, after the
+    set-up kernels have run on it (the finiteness flag is read at the single
+    synchronisation of gdwd_create); the next create on clean data succeeds."""
+    Z, y = _problem(seed=11, d=600, n=120)
+    if solver == "direct":
+        Z, y = _problem(seed=11, d=40, n=900)
+    for bad in (np.nan, np.inf):
+        Zb = Z.copy()
+        Zb[Z.shape[0] // 2, Z.shape[1] - 1] = bad
+        with pytest.raises(gdwd_lib.GdwdError) as exc:
+            gdwd_lib.Solver(Zb, y, 1.0, 1.0, store=store, solver=solver)
+        assert exc.value.status == 1 and "non-finite" in str(exc.value)
+    with gdwd_lib.Solver(Z, y, 1.0, 1.0, store=store, solver=solver) as s:
+        res, w, _ = s.solve()
+    assert res[0]["status"] == 0

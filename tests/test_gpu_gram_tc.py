@@ -1,4 +1,5 @@
-"""GPU tests of the tensor-core Gram (tcgen05) for BF16, FP16 and E4M3 storage.
+"""GPU tests of the tensor-core Gram (tcgen05) for BF16, FP16 and E4M3 storage
+(and for FP32 storage through its BF16 split, at the end).
 
 The reference is the Gram matrix of the stored codes computed here in FP64:
 G = I + (Q diag(s) / Z_scale)^T (Q diag(s) / Z_scale) / mu, with Q the decoded
@@ -72,6 +73,50 @@ def test_solve_after_tensor_core_gram(gdwd_lib):
     out = []
     for gp in (0, 1):
         with gdwd_lib.Solver(inst.Z, inst.y, 1.0, 1.0, store="bf16", tol=1e-6, gram_path=gp) as s:
+            res, w, _ = s.solve()
+            out.append((res[0], w[:, 0]))
+    (r0, w0), (r1, w1) = out
+    assert r0["status"] == 0 and r1["status"] == 0
+    assert abs(r0["primal_obj"] - r1["primal_obj"]) / abs(r1["primal_obj"]) <= 1e-6
+    assert np.linalg.norm(w0 - w1) / np.linalg.norm(w1) <= 1e-4
+
+
+@pytest.mark.parametrize("d,n", [(37, 5), (2531, 257), (20011, 1000)])
+def test_fp32_split_gram_matches_fp64(gdwd_lib, d, n):
+    """FP32 storage on the tensor cores: each value split into three BF16 terms
+    (exact: z = h + m + l up to 2^-24 |z|), six exact products per pair, the h h
+    products summed over a 64-row strip in FP32 (four MMAs) and the five smaller
+    products (at most 2^-8 of h h) in a second accumulator.  Against the FP64
+    Gram of the FP32 data: the accumulator's roundings of each strip's h h
+    partial, which need not be round-to-nearest (up to 2^-23 each, of one
+    sign), four per strip, plus the dropped terms (below 2^-23 of a product):
+    <= 5 * 2^-23 = 6e-7 of the largest entry (1.05e-7 measured at d = 2531
+    with one column 50 times the others)."""
+    rng = np.random.default_rng(11 * d + n)
+    y = np.where(np.arange(n) % 3 == 0, 1.0, -1.0)
+    Z = (rng.standard_normal((d, n)) * y).astype(np.float32)
+    Z[:, 1] *= 50.0
+    mu = 0.7
+    with gdwd_lib.Solver(Z, y, 1.0, 1.0, store="f32", mu=mu) as s:
+        assert s.info()["gram_tensor_cores"] == 1
+        G = s.gram()
+        zs = s.info()["zscale"]
+    Zt = Z.astype(np.float64) / zs
+    Kref = Zt.T @ Zt / mu
+    err = np.max(np.abs(G - np.eye(n) - Kref)) / np.max(np.abs(Kref))
+    assert err <= 6e-7, err
+    assert np.array_equal(G, G.T)
+
+
+def test_fp32_solve_after_split_gram(gdwd_lib):
+    """An FP32 solve whose factor comes from the split tensor-core Gram reaches
+    the SIMT-Gram solve's solution and iteration count to within the stop rule."""
+    from paper_2305_12019_gb300 import synth
+    inst = synth.gaussian(seed=92, d=9000, n=600, shift=1.0, n_pos=200, q=1.0, C=2.0)
+    out = []
+    for gp in (0, 1):
+        with gdwd_lib.Solver(inst.Z, inst.y, 1.0, 2.0, store="f32", tol=1e-6, gram_path=gp) as s:
+            assert s.info()["gram_tensor_cores"] == (1 if gp == 0 else 0)
             res, w, _ = s.solve()
             out.append((res[0], w[:, 0]))
     (r0, w0), (r1, w1) = out

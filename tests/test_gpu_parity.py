@@ -64,9 +64,10 @@ def test_prox_parity(gdwd_lib, q):
     assert got0.numel() == 0
 
 
+@pytest.mark.parametrize("gram_path", [0, 1])
 @pytest.mark.parametrize("store,d,n", [("f64", 3001, 257), ("f32", 3001, 257), ("f32", 9000, 130),
                                        ("f64", 37, 300), ("f64", 2500, 157), ("f32", 1111, 65)])
-def test_gram_parity(gdwd_lib, store, d, n):
+def test_gram_parity(gdwd_lib, store, d, n, gram_path):
     rng = np.random.default_rng(d + n)
     y = np.where(np.arange(n) % 3 == 0, 1.0, -1.0)
     X = rng.standard_normal((d, n))
@@ -74,17 +75,25 @@ def test_gram_parity(gdwd_lib, store, d, n):
         X = X.astype(np.float32).astype(np.float64)
     Z = X * y
     mu = 0.7
-    with gdwd_lib.Solver(Z.astype(np.float32) if store == "f32" else Z, y, 1.0, 1.0, store=store, mu=mu) as s:
+    with gdwd_lib.Solver(Z.astype(np.float32) if store == "f32" else Z, y, 1.0, 1.0, store=store, mu=mu,
+                         gram_path=gram_path) as s:
         G = s.gram()
-        zs = s.info()["zscale"]
+        info = s.info()
+        zs = info["zscale"]
+    assert info["gram_tensor_cores"] == (1 if (store == "f32" and gram_path == 0) else 0)
     Zt, zs_ref = O.scale_data(Z)
     Gref = np.eye(n) + Zt.T @ Zt / mu
     assert abs(zs - zs_ref) <= 1e-13 * zs_ref
     err = np.abs(G - Gref).max() / np.abs(Gref).max()
-    # FP32 storage: products are rounded to FP32 and summed in FP32 over 16-row
-    # chunks before the double-float fold, ~16 * 2^-24 per chunk relative, random
-    # over d/16 chunks: a few 1e-8 of the largest entry.  FP64 storage: FP64 sums.
-    assert err <= (1e-13 if store == "f64" else 5e-8), err
+    # FP32 storage, SIMT kernel: products rounded to FP32 and summed in FP32 over
+    # 16-row chunks before the double-float fold, ~16 * 2^-24 per chunk relative,
+    # random over d/16 chunks: a few 1e-8 of the largest entry.  FP32 storage,
+    # tensor cores: exact products of the BF16 split terms, but the tensor core's
+    # FP32 accumulation of a 64-row strip (four roundings of up to 2^-23 each,
+    # not necessarily of random sign) plus the dropped terms (below 2^-23 of a
+    # product): <= 6e-7 of the largest entry.  FP64 storage: FP64 sums.
+    bound = 1e-13 if store == "f64" else (6e-7 if gram_path == 0 else 5e-8)
+    assert err <= bound, err
     assert np.array_equal(G, G.T)
 
 

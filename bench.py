@@ -41,9 +41,9 @@ UNIT = "solves/s"
 WORKLOAD = "spiked_fp32 d=20000 n=1000 q=1 C=10 tol=1e-6"
 CONFIG = {"workload": WORKLOAD, "d": 20000, "n": 1000, "q": 1.0, "C": 10.0, "tol": 1e-6, "store": "f32",
           "seed": 2001, "l2": "flushed between steps (Z is 80 MB < 129 MB L2); Z stays L2-resident within a solve"}
-# gdwd_create launches 10 kernels (3 fills, sum of squares, partial sum, slab copy, scale,
+# gdwd_create launches 9 kernels (3 fills, one-pass ingest, scale, BF16 split, tensor-core
 # Gram, Gram finish, factor), gdwd_solve 4 (2 fills, iteration, w finish)
-LAUNCHES_PER_STEP = 14
+LAUNCHES_PER_STEP = 13
 
 
 # sources of the iteration kernel: the DRAM traffic recorded under profiles/ is

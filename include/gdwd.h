@@ -96,9 +96,10 @@ typedef struct {
                          most 256 rows folded into double-float); F32 storage too,
                          through a three-term BF16 split of each value (six exact
                          products per pair, the dropped terms below 2^-23 of the
-                         product; a temporary 6 d n bytes during gdwd_create); F64
-                         on the SIMT FP64 kernel; 1: the SIMT kernel for every
-                         storage.  */
+                         product; a temporary 6 d n bytes during gdwd_create), when
+                         the contraction has at most 65536 rows (d for this solver,
+                         n for the direct one); F64 on the SIMT FP64 kernel; 1: the
+                         SIMT kernel for every storage.  */
   int32_t stop_rule;  /* 0 (default): stop when kkt = max(eta_P, eta_D, eta_C, eta_gap)
                          <= tol; 1: the rule of Sec. 4.3: max(eta_P, eta_D) < tol,
                          min(eta_C, eta_gap) < sqrt(tol) and max(eta_C, eta_gap) < 0.05

@@ -790,9 +790,10 @@ static cudaError_t dir_apply2(const double* x, const double* x2, double* out, do
 }
 
 // One solve of the direct solver from the initial iterate of reading R3.  The
-// host issues the iteration's kernels in batches of kDirBatch iterations and
-// reads the control block between batches; kernels issued after convergence
-// return at once (the streaming passes among them still run).
+// host issues the iteration's kernels in batches of kDirBatch iterations (a
+// captured CUDA graph after the first batch) and reads the control block
+// between batches; kernels issued after convergence return at once (the
+// streaming passes among them still run).
 static gdwd_status solve_direct(gdwd_handle* h, double C, double* w, int w_on_device, double* alpha,
                                 gdwd_result* res) {
   constexpr int kDirBatch = 8;
@@ -861,11 +862,44 @@ static gdwd_status solve_direct(gdwd_handle* h, double C, double* w, int w_on_de
   CK(cudaEventRecord(e0, st), "event");
   Ctrl c{};
   int kerr = 0;
-  for (int it = 0; it < h->opt.max_iter; it += kDirBatch) {
+  // A batch is ~16 kernel launches per iteration.  The first batch runs
+  // eagerly (it also sets the kernels' attributes); the later ones replay one
+  // CUDA graph captured from the same calls, so the host issues one launch per
+  // batch.  If capture is refused the batches stay eager.
+  auto batch = [&]() -> cudaError_t {
     for (int b = 0; b < kDirBatch; ++b) {
       const cudaError_t e = run_dir_iteration(a, ps, st);
-      if (e != cudaSuccess) return cuda_fail(h, e, "direct solver iteration");
+      if (e != cudaSuccess) return e;
     }
+    return cudaSuccess;
+  };
+  struct GraphExec {
+    cudaGraphExec_t x = nullptr;
+    ~GraphExec() {
+      if (x) cudaGraphExecDestroy(x);
+    }
+  } gx;
+  bool use_graph = true;
+  for (int it = 0; it < h->opt.max_iter; it += kDirBatch) {
+    cudaError_t e = cudaSuccess;
+    if (it > 0 && use_graph && !gx.x) {
+      cudaGraph_t g = nullptr;
+      e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        const cudaError_t eb = batch();
+        e = cudaStreamEndCapture(st, &g);
+        if (eb != cudaSuccess) e = eb;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&gx.x, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e != cudaSuccess) {   // nothing captured ran: run the batch eagerly from now on
+        cudaGetLastError();
+        gx.x = nullptr;
+        use_graph = false;
+      }
+    }
+    e = gx.x ? cudaGraphLaunch(gx.x, st) : batch();
+    if (e != cudaSuccess) return cuda_fail(h, e, "direct solver iteration");
     CK(cudaMemcpyAsync(&c, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st), "copy ctrl");
     CK(cudaMemcpyAsync(&kerr, h->err, sizeof(int), cudaMemcpyDeviceToHost, st), "copy err");
     CK(cudaStreamSynchronize(st), "sync");

@@ -67,6 +67,7 @@ constexpr int kTmemColsSplit = 4 * kTT;
 // four FP32 roundings of the largest partial.
 constexpr int kFoldSteps = 1;
 constexpr int kSplitRows = 128;                // rows per slab of the BF16 split of FP32 storage
+constexpr int64_t kSplitMaxRows = 65536;       // longest contraction the FP32 split serves
 
 struct __align__(1024) TcShared {
   uint8_t a[kStages][kStageBytes];             // 1024-byte aligned (128-byte swizzle atoms)
@@ -451,6 +452,13 @@ int64_t tc_ksteps(int store, const Layout& L) {
 
 bool gram_tc_supported(int store, const Layout& L) {
   if (store != GDWD_BF16 && store != GDWD_F16 && store != GDWD_E4M3 && store != GDWD_F32) return false;
+  // FP32 storage: the tensor core's FP32 accumulation of a strip's h h products
+  // need not round to nearest, so its error can add up with one sign from strip
+  // to strip (about 1e-7 of the sum of the strips' magnitudes).  Over a long
+  // contraction with cancellation (the d x d Gram of the direct solver over
+  // n = 1e6 samples) that is far above the SIMT kernel's error, so the split
+  // serves contractions of at most kSplitMaxRows rows.
+  if (store == GDWD_F32 && L.d > kSplitMaxRows) return false;
   // tensor-map strides are multiples of 16 bytes; tile rows and the slab count fit int
   if (store != GDWD_F32 && ((int64_t)L.TB * L.esize) % 16 != 0) return false;
   if (L.n > (1LL << 30) || 3LL * split_slabs(L) > (1LL << 30)) return false;

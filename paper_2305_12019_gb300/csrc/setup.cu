@@ -596,51 +596,9 @@ __device__ __forceinline__ float2 d2f(double x) {
   return make_float2(h.hi, h.lo);
 }
 
-// tile [r0, r0+32) x [c0, c0+32) of a row-major n x n df matrix into shared memory
-__device__ __forceinline__ void load_tile_df(float2 (*S)[kNB + 1], const float2* M, int64_t n, int64_t r0,
-                                             int64_t c0, bool unit_pad) {
-  for (int t = threadIdx.x; t < kNB * kNB; t += kThreads) {
-    const int r = t / kNB, c = t % kNB;
-    const int64_t gr = r0 + r, gc = c0 + c;
-    S[r][c] = (gr < n && gc < n) ? M[gr * n + gc] : make_float2((unit_pad && gr == gc) ? 1.f : 0.f, 0.f);
-  }
-}
-
-__device__ __forceinline__ void store_tile_df(const float2 (*S)[kNB + 1], float2* M, int64_t n, int64_t r0,
-                                              int64_t c0) {
-  for (int t = threadIdx.x; t < kNB * kNB; t += kThreads) {
-    const int r = t / kNB, c = t % kNB;
-    const int64_t gr = r0 + r, gc = c0 + c;
-    if (gr < n && gc < n) M[gr * n + gc] = S[r][c];
-  }
-}
-
-// C[32x32] += sgn * A B^T (all double-float tiles in shared memory).  256
-// threads, 4 outputs each (row r = t / 8, columns t % 8 + 8 q).
-__device__ __forceinline__ void tile_acc_abt(float2 (*C)[kNB + 1], const float2 (*Am)[kNB + 1],
-                                             const float2 (*Bm)[kNB + 1], float sgn) {
-  const int r = threadIdx.x >> 3, c0 = threadIdx.x & 7;
-  df acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-#pragma unroll 4
-  for (int k = 0; k < kNB; ++k) {
-    const float2 a = Am[r][k];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float2 b = Bm[c0 + 8 * q][k];
-      df_fma(acc[q], df{a.x, a.y}, df{b.x, b.y});
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    df cv{C[r][c0 + 8 * q].x, C[r][c0 + 8 * q].y};
-    df_add(cv, df{sgn * acc[q].hi, sgn * acc[q].lo});
-    C[r][c0 + 8 * q] = make_float2(cv.hi, cv.lo);
-  }
-}
-
 // tile index t of the lower triangle (row-major) -> (i, j), i >= j
 __device__ __forceinline__ void tri_index(int t, int& i, int& j) {
-  int ii = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+  int ii = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);   // an estimate, corrected below
   while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
   while (ii * (ii + 1) / 2 > t) --ii;
   i = ii;
@@ -704,10 +662,28 @@ __device__ __forceinline__ void chol_pivot_df(float2 (*D)[kNB + 1], float2* Dinv
   Dinv[c] = f2_of(inv);
 }
 
+// The lower triangle of a 32 x 32 tile as (row << 8 | column), column-major
+// (column q's entries from off[q]): the entries with column >= q are a suffix.
+struct TriTable {
+  uint16_t rq[kNB * (kNB + 1) / 2];
+  uint16_t off[kNB + 1];
+  constexpr TriTable() : rq(), off() {
+    int k = 0;
+    for (int q = 0; q < kNB; ++q) {
+      off[q] = (uint16_t)k;
+      for (int r = q; r < kNB; ++r) rq[k++] = (uint16_t)(r << 8 | q);
+    }
+    off[kNB] = (uint16_t)k;
+  }
+};
+__device__ const TriTable kTri;
+
 // Cholesky of the 32 x 32 double-float tile D (lower triangle, in place) by all
 // threads of the CTA, column by column, with a look-ahead of one column: after
 // column c is scaled, warp 0 updates column c+1 alone and takes its pivot while
-// the other warps update the rest of the trailing triangle.
+// the other warps update the rest of the trailing triangle (its entries taken
+// from a table, so no thread idles on the upper half).  (One warp holding the
+// rows in registers is slower: a single warp issues the whole trailing update.)
 __device__ void chol_tile_df(float2 (*D)[kNB + 1], float2* Dinv, int* err) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) chol_pivot_df(D, Dinv, 0, err);
@@ -724,10 +700,10 @@ __device__ void chol_tile_df(float2 (*D)[kNB + 1], float2* Dinv, int* err) {
       if (lane == 0) chol_pivot_df(D, Dinv, c + 1, err);
     } else {
       // the rest of the trailing triangle: D[r][q] -= L[r][c] L[q][c], c+2 <= q <= r
-      const int m = kNB - 2 - c;                       // rows / columns c+2 .. 31
-      for (int e = threadIdx.x - 32; e < m * m; e += kThreads - 32) {
-        const int r = c + 2 + e / m, q = c + 2 + e % m;
-        if (q <= r) D[r][q] = f2_of(df_fnma(df_of(D[r][q]), df_of(D[r][c]), df_of(D[q][c])));
+      const int e1 = kTri.off[kNB];
+      for (int e = kTri.off[c + 2] + threadIdx.x - 32; e < e1; e += kThreads - 32) {
+        const int rq = __ldg(&kTri.rq[e]), r = rq >> 8, q = rq & 255;
+        D[r][q] = f2_of(df_fnma(df_of(D[r][q]), df_of(D[r][c]), df_of(D[q][c])));
       }
     }
   }
@@ -735,7 +711,7 @@ __device__ void chol_tile_df(float2 (*D)[kNB + 1], float2* Dinv, int* err) {
 }
 
 __global__ void __launch_bounds__(kThreads, 1) factor_kernel(FactorArgs a) {
-  __shared__ float2 T0[kNB][kNB + 1], T1[kNB][kNB + 1], T2[kNB][kNB + 1];
+  __shared__ float2 T1[kNB][kNB + 1], T2[kNB][kNB + 1];
   __shared__ float2 D[kNB][kNB + 1];     // double-float diagonal tile
   __shared__ float2 Dinv[kNB];           // its inverse diagonal
   __shared__ int s_flag;
@@ -829,49 +805,105 @@ __global__ void __launch_bounds__(kThreads, 1) factor_kernel(FactorArgs a) {
       const int m = nb - k - 1;
       const int ntc = m * (m + 1) / 2;        // Cholesky tiles (tile 0 = the next diagonal)
       const int nti = m * (k + 1);            // inverse tiles
-      auto chol_tile_update = [&](int t) {
-        int ii, jj;
-        tri_index(t, ii, jj);
-        const int64_t I0 = (int64_t)(k + 1 + ii) * kNB, J0 = (int64_t)(k + 1 + jj) * kNB;
-        load_tile_df(T0, A, n, I0, J0, true);
-        load_tile_df(T1, A, n, I0, k0, false);
-        load_tile_df(T2, A, n, J0, k0, false);
-        __syncthreads();
-        tile_acc_abt(T0, T1, T2, -1.f);
-        __syncthreads();
-        store_tile_df(T0, A, n, I0, J0);
-        __syncthreads();
+      // A task updates one 32 x 32 tile C -= L_Ik B^T: a Cholesky tile (C = A_IJ,
+      // B = L_Jk) or an inverse tile (C = X_IJ, B^T = X_kJ).  Each thread keeps its
+      // four outputs (orow, oc0 + 8 q) in registers, and the operands of a CTA's
+      // next task are loaded into registers while the current one is computed.
+      constexpr int kPer = kNB * kNB / kThreads;
+      const int orow = threadIdx.x >> 3, oc0 = threadIdx.x & 7;
+      struct Fetched {
+        float2 a[kPer], b[kPer], c[4];
+        float2* C;
+        int64_t I0, J0;
       };
-      auto inv_tile_update = [&](int t) {
-        const int ii = t / (k + 1), jj = t % (k + 1);
-        const int64_t I0 = (int64_t)(k + 1 + ii) * kNB, J0 = (int64_t)jj * kNB;
-        load_tile_df(T0, X, n, I0, J0, false);
-        load_tile_df(T1, A, n, I0, k0, false);
-        for (int q = threadIdx.x; q < kNB * kNB; q += kThreads) {     // T2 = X[k-tile, J-tile]^T
-          const int r = q % kNB, c = q / kNB;                        // consecutive threads: consecutive columns of X
-          const int64_t gr = k0 + c, gc = J0 + r;
-          T2[r][c] = (gr < n && gc < n) ? X[gr * n + gc] : make_float2(0.f, 0.f);
+      auto fetch = [&](int u, Fetched& f) {   // u < ntc: Cholesky tile u; then inverse tiles
+        const bool chol = u < ntc;
+        int64_t I0, J0;
+        if (chol) {
+          int ii, jj;
+          tri_index(u, ii, jj);
+          I0 = (int64_t)(k + 1 + ii) * kNB;
+          J0 = (int64_t)(k + 1 + jj) * kNB;
+        } else {
+          const int t = u - ntc, ii = t / (k + 1), jj = t % (k + 1);
+          I0 = (int64_t)(k + 1 + ii) * kNB;
+          J0 = (int64_t)jj * kNB;
         }
-        __syncthreads();
-        tile_acc_abt(T0, T1, T2, -1.f);
-        __syncthreads();
-        store_tile_df(T0, X, n, I0, J0);
-        __syncthreads();
+        f.C = chol ? A : X;
+        f.I0 = I0;
+        f.J0 = J0;
+#pragma unroll
+        for (int e = 0; e < kPer; ++e) {
+          const int q = threadIdx.x + e * kThreads;
+          const int r = q / kNB, c = q % kNB;                      // row-major: consecutive threads, consecutive columns
+          f.a[e] = (I0 + r < n && k0 + c < n) ? A[(I0 + r) * n + k0 + c] : make_float2(0.f, 0.f);
+          if (chol) {
+            f.b[e] = (J0 + r < n && k0 + c < n) ? A[(J0 + r) * n + k0 + c] : make_float2(0.f, 0.f);
+          } else {
+            const int rt = q % kNB, ct = q / kNB;                  // B[rt][ct] = X[k0 + ct][J0 + rt]
+            f.b[e] = (k0 + ct < n && J0 + rt < n) ? X[(k0 + ct) * n + J0 + rt] : make_float2(0.f, 0.f);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int64_t gi = I0 + orow, gj = J0 + oc0 + 8 * q;
+          f.c[q] = (gi < n && gj < n) ? f.C[gi * n + gj] : make_float2(0.f, 0.f);
+        }
       };
-      auto task = [&](int u) {               // u = 0 .. ntc - 2: Cholesky tile u + 1; then inverse tiles
-        if (u < ntc - 1) chol_tile_update(u + 1);
-        else inv_tile_update(u - (ntc - 1));
+      // commit f's operands to T1 / T2 (B transposed for inverse tiles, as fetched)
+      auto commit = [&](const Fetched& f, bool chol) {
+#pragma unroll
+        for (int e = 0; e < kPer; ++e) {
+          const int q = threadIdx.x + e * kThreads;
+          T1[q / kNB][q % kNB] = f.a[e];
+          if (chol) T2[q / kNB][q % kNB] = f.b[e];
+          else T2[q % kNB][q / kNB] = f.b[e];
+        }
       };
-      const int ntask = (ntc > 0 ? ntc - 1 : 0) + nti;
+      auto finish = [&](float2* C, int64_t I0, int64_t J0, const float2 (&c)[4]) {
+        df acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll 4
+        for (int kk = 0; kk < kNB; ++kk) {
+          const float2 av = T1[orow][kk];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float2 bv = T2[oc0 + 8 * q][kk];
+            df_fma(acc[q], df{av.x, av.y}, df{bv.x, bv.y});
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int64_t gi = I0 + orow, gj = J0 + oc0 + 8 * q;
+          if (gi < n && gj < n) C[gi * n + gj] = f2_of(df_sum(df{c[q].x, c[q].y}, df_neg(acc[q])));
+        }
+      };
+      const int ntask = (ntc > 0 ? ntc - 1 : 0) + nti;   // every tile but the next diagonal one
       if (m > 0 && cta == 0) {
-        chol_tile_update(0);
+        Fetched f;
+        fetch(0, f);
+        commit(f, true);
+        __syncthreads();
+        finish(f.C, f.I0, f.J0, f.c);
+        __syncthreads();
         factor_diag(k0 + kNB);
       }
-      if (grid > 1) {
-        if (cta > 0)
-          for (int u = cta - 1; u < ntask; u += grid - 1) task(u);
-      } else {
-        for (int u = 0; u < ntask; ++u) task(u);
+      const int first = grid > 1 ? cta - 1 : 0, stride = grid > 1 ? grid - 1 : 1;
+      if (grid == 1 || cta > 0) {
+        Fetched f;
+        int u = first;
+        if (u < ntask) fetch(u + 1, f);                  // task u is tile u + 1 (tile 0: CTA 0)
+        while (u < ntask) {
+          commit(f, u + 1 < ntc);
+          const float2 cc[4] = {f.c[0], f.c[1], f.c[2], f.c[3]};
+          float2* C = f.C;
+          const int64_t I0 = f.I0, J0 = f.J0;
+          __syncthreads();
+          const int next = u + stride;
+          if (next < ntask) fetch(next + 1, f);
+          finish(C, I0, J0, cc);
+          __syncthreads();
+          u = next;
+        }
       }
     }
     FBAR();
@@ -884,28 +916,57 @@ __global__ void __launch_bounds__(kThreads, 1) factor_kernel(FactorArgs a) {
       int ii, jj;
       tri_index(t, ii, jj);
       const int64_t I0 = (int64_t)ii * kNB, J0 = (int64_t)jj * kNB;
-      for (int q = threadIdx.x; q < kNB * kNB; q += kThreads) T0[q / kNB][q % kNB] = make_float2(0.f, 0.f);
-      for (int M = ii; M < nb; ++M) {
+      // the sum over M runs in registers (4 outputs per thread); the two X tiles
+      // of step M + 1 are loaded into registers while step M is computed
+      constexpr int kPer = kNB * kNB / kThreads;
+      float2 pa[kPer], pb[kPer];
+      auto fetch = [&](int M) {
         const int64_t M0 = (int64_t)M * kNB;
-        for (int q = threadIdx.x; q < kNB * kNB; q += kThreads) {
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+          const int q = threadIdx.x + k * kThreads;
           const int r = q % kNB, c = q / kNB;                        // consecutive threads: consecutive columns of X
           const int64_t gm = M0 + c;
-          T1[r][c] = (gm < n && I0 + r < n) ? X[gm * n + I0 + r] : make_float2(0.f, 0.f);
-          T2[r][c] = (gm < n && J0 + r < n) ? X[gm * n + J0 + r] : make_float2(0.f, 0.f);
+          pa[k] = (gm < n && I0 + r < n) ? X[gm * n + I0 + r] : make_float2(0.f, 0.f);
+          pb[k] = (gm < n && J0 + r < n) ? X[gm * n + J0 + r] : make_float2(0.f, 0.f);
+        }
+      };
+      const int orow = threadIdx.x >> 3, oc0 = threadIdx.x & 7;      // outputs (orow, oc0 + 8 q)
+      df acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+      fetch(ii);
+      for (int M = ii; M < nb; ++M) {
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+          const int q = threadIdx.x + k * kThreads;
+          T1[q % kNB][q / kNB] = pa[k];
+          T2[q % kNB][q / kNB] = pb[k];
         }
         __syncthreads();
-        tile_acc_abt(T0, T1, T2, 1.f);
+        if (M + 1 < nb) fetch(M + 1);
+#pragma unroll 4
+        for (int k = 0; k < kNB; ++k) {
+          const float2 av = T1[orow][k];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float2 bv = T2[oc0 + 8 * q][k];
+            df_fma(acc[q], df{av.x, av.y}, df{bv.x, bv.y});
+          }
+        }
+        // renormalise after every 32 terms: df_fma lets lo grow, and a lo far
+        // above ulp(hi) / 2 rounds away the low bits
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] = df_sum(df{0.f, 0.f}, acc[q]);
         __syncthreads();
       }
-      for (int q = threadIdx.x; q < kNB * kNB; q += kThreads) {
-        const int r = q / kNB, c = q % kNB;
-        const int64_t gi = I0 + r, gj = J0 + c;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int64_t gi = I0 + orow, gj = J0 + oc0 + 8 * q;
         if (gi < n && gj < n && gi >= gj) {
-          a.P[gi * a.ldP + gj] = T0[r][c];
-          a.P[gj * a.ldP + gi] = T0[r][c];
+          const df v = df_sum(df{0.f, 0.f}, acc[q]);
+          a.P[gi * a.ldP + gj] = f2_of(v);
+          a.P[gj * a.ldP + gi] = f2_of(v);
         }
       }
-      __syncthreads();
     }
   }
   FBAR();

@@ -6,8 +6,9 @@
   the FP64 oracle on the dequantized data (objective, w, held-out predictions).
 * Served stream (Poisson arrivals, d 1k-100k, n 50-5000, q in {1, 2}, C
   0.1-100, FP16 storage, data drawn on the device from each request's seed): a
-  seeded sample of the stream's requests, regenerated the same way, submitted
-  to one server together, each against the oracle on its dequantized data.
+  seeded sample of the stream's requests (d n <= 4e6, so the oracle finishes),
+  regenerated the same way, submitted to one server together, each against the
+  oracle on its dequantized data.
 * Largest instance (d = 200000, n = 5000, Student-t columns, classes 1:3, E4M3
   storage with the FP32 refinement sweep, 16 values of C): the weak-duality
   certificate on the ORIGINAL data for every C; and the same recipe at d = 4000,
@@ -61,8 +62,9 @@ def _oracle_job(job):
     if job.get("fmt"):
         qv, sc = QR.quantize(Z, job["fmt"])
         Z = qv * sc[None, :]
-    r = O.solve(Z, y, job["q"], job["C"], tol=job.get("tol", 1e-7), max_iter=job.get("max_iter", 50000))
-    return {"primal": r["primal"], "w": r["w"], "beta": r["beta"], "iters": r["iters"], "converged": r["converged"]}
+    r = O.solve(Z, y, job["q"], job["C"], tol=job.get("tol", 1e-7), max_iter=job.get("max_iter", 60000))
+    return {"primal": r["primal"], "w": r["w"], "beta": r["beta"], "iters": r["iters"], "converged": r["converged"],
+            "kkt": r["eta"]["kkt"]}
 
 
 class _Pool:
@@ -99,7 +101,10 @@ def _predictions_match(Xt, w_gpu, b_gpu, w_ref, b_ref):
 
 def _check(res, w, ref, q, Xt=None):
     assert res["status"] == 0 and res["kkt"] <= 1e-6, res
-    assert ref["converged"]
+    # the reference is solved to 1e-7; where the FP64 iteration needs more than
+    # its iteration limit for that (large C), it must at least be 5x tighter
+    # than the GPU's stop
+    assert ref["converged"] or ref["kkt"] <= 2e-7, ref["kkt"]
     relobj = abs(res["primal_obj"] - ref["primal"]) / (1.0 + abs(ref["primal"]))
     relw = np.linalg.norm(w - ref["w"]) / np.linalg.norm(ref["w"])
     assert relobj <= OBJ_TOL, relobj
@@ -168,7 +173,7 @@ def _served_data(d, n, seed):
 
 def test_served_requests_against_oracle(gdwd_lib):
     specs = _served_specs()
-    small = [s for s in specs if s[0] * s[1] <= 1e7]          # oracle cost bound
+    small = [s for s in specs if s[0] * s[1] <= 4e6]          # oracle cost bound
     rng = np.random.default_rng(77)
     sample = [small[i] for i in sorted(rng.choice(len(small), size=6, replace=False))]
     datas = [_served_data(d, n, seed) for d, n, q, C, seed in sample]

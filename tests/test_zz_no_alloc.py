@@ -4,8 +4,9 @@ It is for callers that cannot allocate device memory when they need the
 product, so its scratch is a fixed array inside the library that every call
 reuses.  The test calls it twice in a row through the C-ABI, on data of two
 different shapes, and checks each result against the Gram matrix built by the
-ordinary (allocating) path, gdwd_create + gdwd_gram, within the tolerance of the
-other Gram tests; it must pass alone in a fresh process and after the other tests.
+ordinary (allocating) path with its SIMT kernel, gdwd_create (gram_path = 1) +
+gdwd_gram, and against the FP64 product, within the tolerance of the SIMT Gram
+tests; it must pass alone in a fresh process and after the other tests.
 """
 import numpy as np
 import pytest
@@ -14,10 +15,10 @@ pytestmark = pytest.mark.gpu
 
 
 def _reference_gram(gdwd_lib, Z):
-    """Z^T Z from the allocating path: gdwd_gram returns I + Z~^T Z~ with Z~ = Z / Z_scale."""
+    """Z^T Z from the allocating path's SIMT Gram: gdwd_gram returns I + Z~^T Z~ with Z~ = Z / Z_scale."""
     n = Z.shape[1]
     y = np.where(np.arange(n) % 2 == 0, 1.0, -1.0)
-    with gdwd_lib.Solver(Z, y, 1.0, 1.0, store="f32", mu=1.0) as s:
+    with gdwd_lib.Solver(Z, y, 1.0, 1.0, store="f32", mu=1.0, gram_path=1) as s:
         G = s.gram()
         zs = s.info()["zscale"]
     return (G - np.eye(n)) * zs * zs

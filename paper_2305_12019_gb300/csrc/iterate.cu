@@ -67,22 +67,33 @@ cudaError_t launch_prox(const double* a, const double* r0, const double* omega, 
 // ---------------------------------------------------------------------------
 // pass-B row epilogue of the iteration: g = u - t / mu and the d-space sums
 // ---------------------------------------------------------------------------
+// eta_D3 needs ||kap g - a||^2 with kap = tau mu sigma (1 - theta), and eta_P2
+// ||w - u+||^2 = ||(1 - theta) g + gs rho||^2, with theta = min(1, R / ||g||)
+// known only after the pass.  Expanding them in sums of g, a and rho cancels
+// catastrophically once the residuals are small, and the rounding then decides
+// the sigma rule.  So the pass sums v = a - khat g and y = (1 - theta_prev) g +
+// gs rho, with theta_prev the last iteration's theta and khat = tau mu sigma
+// (1 - theta_prev); phase S expands both in the small theta_prev - theta (zero
+// once theta settles).
 struct IterEpi {
   const df* s_u;             // the CTA's slab rows of u, rho and g in shared memory (double-float)
   const df* s_rho;
   df* s_g;
   df inv_mu, a_coef;         // a = ta + a_coef * rho, a_coef = sqrt(mu)(1 - tau)
-  df sg2{0.f, 0.f}, sgr{0.f, 0.f}, sr2{0.f, 0.f}, sa2{0.f, 0.f}, sag{0.f, 0.f}, sta2{0.f, 0.f};
+  df khat, omp, gs;          // v = a - khat g; y = omp g + gs rho, omp = 1 - theta_prev
+  df sg2{0.f, 0.f}, syg{0.f, 0.f}, sy2{0.f, 0.f}, sv2{0.f, 0.f}, svg{0.f, 0.f}, sta2{0.f, 0.f};
   __device__ void row(int64_t, int m, df t, df ta) {
     const df gj = df_sum(s_u[m], df_neg(df_mul(t, inv_mu)));
     const df rj = s_rho[m];
     const df aj = df_sum(ta, df_mul(a_coef, rj));
+    const df vj = df_sum(aj, df_neg(df_mul(khat, gj)));
+    const df yj = df_sum(df_mul(omp, gj), df_mul(gs, rj));
     s_g[m] = gj;
     df_fma(sg2, gj, gj);
-    df_fma(sgr, gj, rj);
-    df_fma(sr2, rj, rj);
-    df_fma(sa2, aj, aj);
-    df_fma(sag, aj, gj);
+    df_fma(syg, yj, gj);
+    df_fma(sy2, yj, yj);
+    df_fma(sv2, vj, vj);
+    df_fma(svg, vj, gj);
     df_fma(sta2, ta, ta);
   }
 };
@@ -612,7 +623,8 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
       }
       __syncthreads();
       GDWD_MARK(16);
-      IterEpi epi{s_u, s_rho, s_g, inv_mu_df, acoef_df};
+      IterEpi epi{s_u, s_rho, s_g, inv_mu_df, acoef_df, df_from(a.tau * a.mu * sig * (1.0 - theta)),
+                  df_from(1.0 - theta), df_from(gs_it)};
       PassB<T, IterEpi> pb;
       pb.cv = cv;
       pb.av = av;
@@ -644,7 +656,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
       GDWD_MARK(17);
       // the six d-space sums of every thread, one warp per sum, through the
       // phase-local region (free once the pass is over)
-      const df vals[6] = {epi.sg2, epi.sgr, epi.sr2, epi.sa2, epi.sag, epi.sta2};
+      const df vals[6] = {epi.sg2, epi.syg, epi.sy2, epi.sv2, epi.svg, epi.sta2};
       __syncthreads();
       rows_sum_df<6>(vals, reinterpret_cast<float2*>(uni), TB,
                      reinterpret_cast<float2*>(a.scal) + (size_t)S_G2 * grid + cta, grid);
@@ -655,7 +667,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
     grid_totals_df(reinterpret_cast<const float2*>(a.scal), grid, s_tot);
     __syncthreads();
     GDWD_MARK(13);
-    s_phase(s_tot, sq, sig, gs_it, it, beta, status, false, a.ctrl, s_pd, s_etaf, s_ctl, s_ictl);
+    s_phase(s_tot, sq, sig, gs_it, it, beta, status, false, a.ctrl, s_pd, s_etaf, s_ctl, s_ictl, theta, true);
     GDWD_MARK(10);
     sig_prev = sig;
     theta = s_ctl[0];

@@ -41,16 +41,24 @@
 
 namespace gdwd {
 
-// slots of the per-CTA sums written by phase K (the N2 sums use S_RES2 .. S_DUAL_A)
+// Phase K's sums, in the slots S_G2 .. S_TA2 that phase S reads.  The d-space
+// vectors are Z~ times coefficient vectors (g = Z~ a_g, rho = Z~ a_rho), so each
+// norm is a quadratic form in K summed row by row.  The two small residuals are
+// taken about the last iteration's theta_prev, as in the streaming iteration:
+// y = (1 - theta_prev) g + rho / (sigma sqrt(mu)) and v = a - khat g, with
+// a = Z~ alpha + sqrt(mu)(1 - tau) rho and khat = tau mu sigma (1 - theta_prev),
+// their coefficient vectors formed per row before the products.
 enum KernScal {
-  KS_G2 = S_G2,     // a_g^T K a_g     = ||g||^2
-  KS_GR,            // a_rho^T K a_g   = <g, rho>
-  KS_R2,            // a_rho^T K a_rho = ||rho||^2
-  KS_AR,            // alpha^T K a_rho = <Z~ alpha, rho>
-  KS_AG,            // alpha^T K a_g   = <Z~ alpha, g>
-  KS_TA2            // alpha^T K alpha = ||Z~ alpha||^2
+  KS_G2 = S_G2,     // ||g||^2
+  KS_YG,            // <y, g>
+  KS_Y2,            // ||y||^2
+  KS_V2,            // ||v||^2
+  KS_VG,            // <v, g>
+  KS_TA2            // ||Z~ alpha||^2
 };
-static_assert((int)KS_TA2 < (int)S_COUNT, "phase-K sums must fit the partial-sum block");
+static_assert((int)KS_TA2 < (int)S_COUNT && (int)KS_YG == (int)S_GRHO && (int)KS_Y2 == (int)S_RHO2 &&
+                  (int)KS_V2 == (int)S_A2 && (int)KS_VG == (int)S_AG && (int)KS_TA2 == (int)S_TA2,
+              "phase-K sums sit in the slots phase S reads");
 
 // Three products of one double-float row of K with three double-float vectors
 // (one warp; results in every lane).
@@ -321,19 +329,22 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kern_kernel(KernArgs a) {
         }
       }
       __syncthreads();
-      double g2 = 0, gr = 0, r2 = 0, arho = 0, agp = 0, ta2 = 0;
+      double g2 = 0, yg = 0, y2 = 0, v2 = 0, vg = 0, ta2 = 0;
       if (mine) {
         const double ka = s_k[0][tr];
         KG = s_k[1][tr];
         KR = s_k[2][tr];
+        const double omp = 1.0 - theta, khat = a.tau * a.mu * sig * omp;
+        const double cy = omp * ag + gs_it * ar, kcy = omp * KG + gs_it * KR;       // y's coefficients, K times them
+        const double cv = ali + ac * ar - khat * ag, kcv = ka + ac * KR - khat * KG;  // v's
         g2 = ag * KG;
-        gr = ar * KG;
-        r2 = ar * KR;
-        arho = ali * KR;
-        agp = ali * KG;
+        yg = cy * KG;
+        y2 = cy * kcy;
+        v2 = cv * kcv;
+        vg = cv * KG;
         ta2 = ali * ka;
       }
-      const double vals[6] = {g2, gr, r2, arho, agp, ta2};
+      const double vals[6] = {g2, yg, y2, v2, vg, ta2};
       rows_sum<6>(vals, tr, mine, nrows, s_rows, kMaxRowsPerCta, a.scal + (size_t)KS_G2 * grid + cta, grid);
     }
     GDWD_BARRIER(8);
@@ -342,16 +353,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kern_kernel(KernArgs a) {
     grid_totals(a.scal, grid, KS_TA2 + 1, s_tot);
     __syncthreads();
     GDWD_MARK(13);
-    // a = Z~ alpha + sqrt(mu)(1 - tau) rho: ||a||^2 and <a, g> from the K products
-    if (threadIdx.x == 0) {
-      const double S2 = s_tot[KS_GR], S3 = fmax(0.0, s_tot[KS_R2]);
-      const double A2 = s_tot[KS_TA2] + 2.0 * ac * s_tot[KS_AR] + ac * ac * S3;
-      const double AG = s_tot[KS_AG] + ac * S2;
-      s_tot[S_A2] = A2;
-      s_tot[S_AG] = AG;
-    }
-    __syncthreads();
-    s_phase(s_tot, sq, sig, gs_it, it, beta, status, false, a.ctrl, s_pd, s_etaf, s_ctl, s_ictl);
+    s_phase(s_tot, sq, sig, gs_it, it, beta, status, false, a.ctrl, s_pd, s_etaf, s_ctl, s_ictl, theta, true);
     GDWD_MARK(10);
     sig_prev = sig;
     theta = s_ctl[0];

@@ -384,9 +384,15 @@ __device__ __forceinline__ void s_report(Ctrl* ctrl, double beta, const double* 
   ctrl->wnorm = s_pd[3];
 }
 
+// vsums: the d-space sums are taken about the last iteration's theta_prev
+// (S_GRHO = <y, g>, S_RHO2 = ||y||^2, y = (1 - theta_prev) g + gs rho; S_AG =
+// <v, g>, S_A2 = ||v||^2, v = a - tau mu sigma (1 - theta_prev) g), so the
+// small residuals are expanded in theta_prev - theta; otherwise they are
+// <g, rho>, ||rho||^2, <a, g>, ||a||^2.
 __device__ __forceinline__ void s_phase(const double* s_tot, const SPhaseArgs& q, double sig, double gs, int it,
                                         double beta, int status, bool report, Ctrl* ctrl, double* s_pd,
-                                        float* s_etaf, double* s_ctl, int* s_ictl) {
+                                        float* s_etaf, double* s_ctl, int* s_ictl, double theta_prev = 1.0,
+                                        bool vsums = false) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == 3 && lane < 7) {
     // 1 / sigma' for each value the sigma rule can give (sigma times 1, 1.1, 1.65,
@@ -409,17 +415,27 @@ __device__ __forceinline__ void s_phase(const double* s_tot, const SPhaseArgs& q
     s_etaf[5] = fabsf((float)s_tot[S_XICA]) * q.inv_den;              // c2
     s_etaf[6] = fsqrt_approx((float)s_tot[S_AMS2]) * q.inv_den;       // c3
   } else if (threadIdx.x == 0) {
-    const double S1 = s_tot[S_G2], S2 = s_tot[S_GRHO], S3 = s_tot[S_RHO2];   // ||g||^2, <g,rho>, ||rho||^2
-    const double t2 = 2.0 * gs * S2, t3 = gs * gs * S3;
+    const double S1 = s_tot[S_G2];                                       // ||g||^2
     // Step 2 projection: theta = min(1, R / ||g||), R / ||g|| = R rsqrt(S1)
     const double r0 = (double)rsqrt_approx((float)S1);
     const double rs = r0 * fma(-0.5 * S1, r0 * r0, 1.5);
     const double th = (S1 <= q.R * q.R) ? 1.0 : q.R * rs;
-    const double w2 = S1 + t2 + t3;                                      // ||w||^2
-    const double om = 1.0 - th;
-    const double wu2 = fma(om, fma(om, S1, t2), t3);                     // ||w - u+||^2
-    const double kap = (q.tau * q.mu) * sig * om;
-    const double d3 = fma(kap, fma(kap, S1, -2.0 * s_tot[S_AG]), s_tot[S_A2]);
+    double w2, wu2, d3;
+    if (vsums) {
+      const double YG = s_tot[S_GRHO], Y2 = s_tot[S_RHO2];
+      const double eps = theta_prev - th;
+      w2 = fma(theta_prev, fma(theta_prev, S1, 2.0 * YG), Y2);          // ||y + theta_prev g||^2 = ||w||^2
+      wu2 = fma(eps, fma(eps, S1, 2.0 * YG), Y2);                        // ||y + eps g||^2 = ||w - u+||^2
+      const double dlt = (q.tau * q.mu) * sig * eps;                     // kap - khat
+      d3 = fma(dlt, fma(dlt, S1, -2.0 * s_tot[S_AG]), s_tot[S_A2]);      // ||v - dlt g||^2 = ||a - kap g||^2
+    } else {
+      const double t2 = 2.0 * gs * s_tot[S_GRHO], t3 = gs * gs * s_tot[S_RHO2];
+      w2 = S1 + t2 + t3;                                                 // ||w||^2
+      const double om = 1.0 - th;
+      wu2 = fma(om, fma(om, S1, t2), t3);                                // ||w - u+||^2
+      const double kap = (q.tau * q.mu) * sig * om;
+      d3 = fma(kap, fma(kap, S1, -2.0 * s_tot[S_AG]), s_tot[S_A2]);      // ||a - kap g||^2
+    }
     const float wnf = fsqrt_approx((float)w2);
     const double wmr = (w2 - q.R * q.R) * (double)rcp_approx(wnf + (float)q.R);   // ||w|| - R
     s_pd[2] = th;

@@ -35,10 +35,10 @@ enum Scal {
   S_PRIM_XI,    // sum e_i xi_i
   S_DUAL_A,     // sum (wt_i alpha_i)^(q/(q+1))
   S_G2,         // ||g||^2
-  S_GRHO,       // <g, rho>
-  S_RHO2,       // ||rho||^2
-  S_A2,         // ||a||^2, a = Z~ alpha + sqrt(mu)(1 - tau) rho
-  S_AG,         // <a, g>
+  S_GRHO,       // <g, rho> (the iteration kernel: <y, g>, y = (1 - theta_prev) g + rho / (sigma sqrt(mu)))
+  S_RHO2,       // ||rho||^2 (the iteration kernel: ||y||^2)
+  S_A2,         // ||a||^2, a = Z~ alpha + sqrt(mu)(1 - tau) rho (the iteration kernel: ||v||^2, v = a - khat g)
+  S_AG,         // <a, g> (the iteration kernel: <v, g>)
   S_TA2,        // ||Z~ alpha||^2
   S_COUNT = 16
 };

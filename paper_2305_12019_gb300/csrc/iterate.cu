@@ -254,6 +254,12 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
   __shared__ double s_ug[kMaxRowsPerCta];                                 // Z~^T u from the column dots
   __shared__ float2 s_rb[kMaxRowsPerCta];                                 // rhs2 of the CTA's rows
   __shared__ double s_gx[kFuseRowsPerWarp * kWarps * 3];                  // fused products: rows, then p^T
+  // the iteration's double-float constants theta, -tau sigma_prev sqrt(mu)
+  // (1 - theta), khat = tau mu sigma (1 - theta), 1 - theta and gs = 1 / (sigma
+  // sqrt(mu)), formed once per CTA by five lanes during the wait at barrier 4
+  // (a warp-level FP64 instruction occupies the SM's FP64 unit ~19 cycles, so
+  // the same products formed by every warp cost about a microsecond)
+  __shared__ df s_itdf[5];
   const int qcase = q_case(a.q);
   const double sqmu = sqrt(a.mu), inv_mu = 1.0 / a.mu, inv_sqmu = 1.0 / sqmu;
   const df inv_mu_df = df_from(inv_mu), acoef_df = df_from(sqmu * (1.0 - a.tau)), omtau = df_from(1.0 - a.tau);
@@ -420,7 +426,6 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
     double betabar;
     double xb_reg = 0.0;   // fused x-bar of this thread's row (at most one row per thread)
     {
-      const double rcoef = a.tau * sig_prev * sqmu * (1.0 - theta);
       if (pending && dots_prev) {
         // the column dots Z~^T u of the last pass: one warp per row sums its slabs
         for (int t = warp; t < nrows; t += kWarps) {
@@ -430,13 +435,15 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
         __syncthreads();
       }
       // fused: x-bar = a1 X1 + X2 / sigma + X3 from the last pass's products
-      const double a1 = theta - a.tau * (sig_prev * inv_sig) * (1.0 - theta);
+      // (formed only by the threads that use them)
+      const double a1 = fused ? theta - a.tau * (sig_prev * inv_sig) * (1.0 - theta) : 0.0;
       if (fused) betabar = -(a1 * s_gx[nrows * 3] + s_gx[nrows * 3 + 1] * inv_sig + s_gx[nrows * 3 + 2]) * a.inv_s;
       // the per-row work on consecutive threads (few warp instructions of FP64)
       for (int t = threadIdx.x; t < nrows; t += kThreads) {
         const int64_t i = r0 + t;
         double uu = RS(RS_UU, t), ur = RS(RS_UR, t);
         if (pending) {
+          const double rcoef = a.tau * sig_prev * sqmu * (1.0 - theta);
           const double ug = (dots_prev ? s_ug[t] : uu) - RS(RS_KC, t);
           uu = theta * ug;
           ur = (1.0 - a.tau) * ur - rcoef * ug;
@@ -497,7 +504,17 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
     GDWD_BARRIER_SIDE(4, [&]() {
       // double-float on the FP32 pipes: each warp-level FP64 instruction occupies
       // the SM's FP64 unit for ~19 cycles, whatever the number of active lanes
-      const df th = df_from(theta), mrc = df_from(-a.tau * sig_prev * sqmu * (1.0 - theta));
+      if (warp == 1 && lane < 5) {
+        const double omt = 1.0 - theta;
+        const double v = lane == 0 ? theta
+                       : lane == 1 ? -a.tau * sig_prev * sqmu * omt
+                       : lane == 2 ? a.tau * a.mu * sig * omt
+                       : lane == 3 ? omt
+                                   : gs_it;
+        s_itdf[lane] = df_from(v);
+      }
+      asm volatile("bar.sync 1, %0;" ::"r"(kThreads - 32) : "memory");   // the side warps only
+      const df th = s_itdf[0], mrc = s_itdf[1];
       for (int m = threadIdx.x - 32; m < nmy * TB; m += kThreads - 32) {
         const int k = m / TB, j = m - k * TB;
         const int64_t gj = (cta + (int64_t)k * grid) * TB + j;
@@ -623,8 +640,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
       }
       __syncthreads();
       GDWD_MARK(16);
-      IterEpi epi{s_u, s_rho, s_g, inv_mu_df, acoef_df, df_from(a.tau * a.mu * sig * (1.0 - theta)),
-                  df_from(1.0 - theta), df_from(gs_it)};
+      IterEpi epi{s_u, s_rho, s_g, inv_mu_df, acoef_df, s_itdf[2], s_itdf[3], s_itdf[4]};
       PassB<T, IterEpi> pb;
       pb.cv = cv;
       pb.av = av;

@@ -327,3 +327,22 @@ def test_column_dot_period(gdwd_lib, store, dots_every):
         Zref = qv * sc[None, :]
     ref = O.solve(Zref, inst.y, 1.0, 2.0, tol=1e-10)
     _compare(res[0], w[:, 0], ref)
+
+
+def test_large_C_on_the_ball_follows_the_oracle(gdwd_lib):
+    """Heavy-tailed data with d >> n at C = 1000: w sits on the ball (theta < 1)
+    and the residuals reach 1e-7, where eta_P2 and eta_D3 expanded in sums of g,
+    rho and Z~ alpha cancel and the sigma rule then follows rounding.  Both GPU
+    loops must follow the FP64 oracle's residuals and stop at its iteration."""
+    inst = synth.heavy_tailed(seed=5011, d=20000, n=500, n_pos=125)
+    Z = inst.Z.astype(np.float64)
+    ref = O.solve(Z, inst.y, 1.0, 1e3, tol=1e-6, max_iter=20000)
+    assert ref["converged"]
+    for kern in (0, 1):
+        with gdwd_lib.Solver(Z, inst.y, 1.0, 1e3, store="f64", tol=1e-6, kernelized=kern) as s:
+            res, w, _ = s.solve()
+        r = res[0]
+        assert r["status"] == 0, (kern, r)
+        assert abs(r["iters"] - ref["iters"]) <= max(3, ref["iters"] // 50), (kern, r["iters"], ref["iters"])
+        assert abs(r["primal_obj"] - ref["primal"]) <= 1e-6 * (1.0 + abs(ref["primal"]))
+        assert np.linalg.norm(w[:, 0] - ref["w"]) <= 1e-4 * np.linalg.norm(ref["w"])

@@ -234,7 +234,7 @@ def main():
     ap.add_argument("--big-n", type=int, default=5000)
     ap.add_argument("--kern-wide-d", type=int, default=200000)
     ap.add_argument("--kern-steps", type=int, default=3)
-    ap.add_argument("--kern", type=int, default=0, help="uneven_batch / served / largest_fp8: 1 = kernelized iteration")
+    ap.add_argument("--kern", type=int, default=0, help="uneven_batch / served / largest_fp8: 1 = kernelized iteration, -1 = chosen per problem")
     ap.add_argument("--dir-d", type=int, default=200)
     ap.add_argument("--dir-n", type=int, default=1000000)
     args = ap.parse_args()
@@ -366,7 +366,7 @@ def main():
         import bench_workloads
         line["detail"]["hbm_stream"] = bench_workloads.hbm_stream(gdwd, synth)
         sargs = argparse.Namespace(**vars(args))
-        sargs.serve_seconds, sargs.kern = args.extras_serve_seconds, 1
+        sargs.serve_seconds, sargs.kern = args.extras_serve_seconds, -1
         sv = bench_workloads.served(sargs, gdwd, synth)
         line["detail"]["served"] = {k: sv[k] for k in ("value", "unit", "latency_ms_p50", "latency_ms_p99",
                                                       "server_latency_ms_p50", "server_latency_ms_p99", "requests",

@@ -141,7 +141,7 @@ def uneven_batch(args, gdwd, synth):
             "ms_per_step": dt * 1e3,
             "config": {"workload": f"uneven_batch {len(reqs)} instances d 5k-50k n 200-2000 q in 0.5,1,2,4",
                        "store": "bf16", "slots": args.slots,
-                       "iteration": "kernelized" if args.kern else "Z-streaming"},
+                       "iteration": {1: "kernelized", 0: "Z-streaming", -1: "chosen per problem by bytes per iteration"}[args.kern]},
             "status": int(st), "converged": int(sum(r["status"] == 0 for r in res)),
             "not_converged": [{"k": k, "d": shapes[k]["d"], "n": shapes[k]["n"], "q": shapes[k]["q"], "iters": r["iters"],
                                "kkt": r["kkt"], "status": r["status"]} for k, r in enumerate(res) if r["status"] != 0],
@@ -226,7 +226,7 @@ def served(args, gdwd, synth):
             "z_bytes_per_iteration_mean_fp16": 2.0 * dn_done / max(1, len(stats)),
             "config": {"workload": f"served Poisson {lam}/s for {T} s, d 1k-100k, n 50-5000, q in 1,2, C 0.1-100",
                        "store": "f16", "slots": args.slots, "client_in_flight_max": max_out,
-                       "iteration": "kernelized" if args.kern else "Z-streaming"}}
+                       "iteration": {1: "kernelized", 0: "Z-streaming", -1: "chosen per problem by bytes per iteration"}[args.kern]}}
 
 
 def largest_fp8(args, gdwd, synth):
@@ -247,7 +247,7 @@ def largest_fp8(args, gdwd, synth):
     return {"metric": "gDWD C-solves/s at KKT<=1e-6 on the original data (FP8 + FP32 refinement)",
             "value": 16 / dt, "unit": "solves/s", "ms_per_step": dt * 1e3,
             "config": {"workload": f"largest_fp8 d={d} n={n} Student-t 1:3 16 C", "store": "e4m3+refine",
-                       "iteration": "kernelized" if args.kern else "Z-streaming"},
+                       "iteration": {1: "kernelized", 0: "Z-streaming", -1: "chosen per problem by bytes per iteration"}[args.kern]},
             "setup_ms": info["t_setup_ms"], "gram_tensor_cores": info["gram_tensor_cores"],
             "iters": [r["iters"] for r in res],
             "converged": int(sum(r["status"] == 0 for r in res)), "certified_gap_C_ends": gaps}

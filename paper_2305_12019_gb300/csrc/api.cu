@@ -408,17 +408,19 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
   if (opt.gram_path != 0 && opt.gram_path != 1) return fail(nullptr, GDWD_EINVAL, "gdwd_create: gram_path must be 0 or 1");
   if (opt.stop_rule != 0 && opt.stop_rule != 1) return fail(nullptr, GDWD_EINVAL, "gdwd_create: stop_rule must be 0 or 1");
   if (opt.dots_every < 0) return fail(nullptr, GDWD_EINVAL, "gdwd_create: dots_every must be >= 0");
-  if (opt.kernelized != 0 && opt.kernelized != 1) return fail(nullptr, GDWD_EINVAL, "gdwd_create: kernelized must be 0 or 1");
+  if (opt.kernelized < -1 || opt.kernelized > 1)
+    return fail(nullptr, GDWD_EINVAL, "gdwd_create: kernelized must be -1, 0 or 1");
   if (opt.solver < 0 || opt.solver > 2) return fail(nullptr, GDWD_EINVAL, "gdwd_create: solver must be 0, 1 or 2");
-  if (opt.solver == 2 && (opt.refine || opt.kernelized || (opt.store != GDWD_F32 && opt.store != GDWD_F64)))
+  if (opt.solver == 2 && (opt.refine || opt.kernelized == 1 || (opt.store != GDWD_F32 && opt.store != GDWD_F64)))
     return fail(nullptr, GDWD_EUNSUPPORTED,
                 "gdwd_create: the inexact solver runs with F32 or F64 storage, without refine and kernelized");
-  if (opt.solver == 1 && (opt.refine || opt.kernelized || (opt.store != GDWD_F32 && opt.store != GDWD_F64)))
+  if (opt.solver == 1 && (opt.refine || opt.kernelized == 1 || (opt.store != GDWD_F32 && opt.store != GDWD_F64)))
     return fail(nullptr, GDWD_EUNSUPPORTED,
                 "gdwd_create: the direct solver runs with F32 or F64 storage, without refine and kernelized");
 
   gdwd_handle* h = new gdwd_handle();
   h->opt = opt;
+  if (opt.solver != 0) h->opt.kernelized = 0;   // "auto" means the streaming products there
   h->stream = (cudaStream_t)opt.stream;
   h->d = d;
   h->n = n;
@@ -461,9 +463,16 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
   }
   h->inexact = opt.solver == 2;
   plan_layout(h, d, n);
+  if (h->opt.kernelized < 0) {
+    // auto: the loop that reads fewer bytes per iteration.  Both read G^-1
+    // twice (16 n^2); the streaming loop also reads Z once (d n element bytes),
+    // the kernelized one K once (8 n^2, double-float).
+    h->opt.kernelized = (8 * n < d * (int64_t)dtype_size(opt.store) &&
+                         n <= kern_max_n(h->grid, h->smem_optin - 16384)) ? 1 : 0;
+  }
   if (!h->inexact && (n + h->grid - 1) / h->grid > kMaxRowsPerCta)
     return bail(fail(nullptr, GDWD_EUNSUPPORTED, "gdwd_create: n too large for the n x n factor path of this build"));
-  if (opt.kernelized && n > kern_max_n(h->grid, h->smem_optin - 16384))
+  if (h->opt.kernelized && n > kern_max_n(h->grid, h->smem_optin - 16384))
     return bail(fail(nullptr, GDWD_EUNSUPPORTED, "gdwd_create: n too large for the kernelized iteration"));
   st = [&]() -> gdwd_status {
     cudaEvent_t e0, e1, evg, ef0;
@@ -664,6 +673,7 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
     om.store = GDWD_F32;
     om.refine = 0;
     om.grid = h->grid;
+    om.kernelized = h->opt.kernelized;   // the master continues the quantized solve's kind of iterate
     st = gdwd_create(Z, zdt, d, n, ldz, z_on_device, y, q, C, &om, &h->master);
     if (st != GDWD_OK) return bail(st);
   }

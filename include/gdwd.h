@@ -121,10 +121,9 @@ typedef struct {
                          (8 n^2 bytes more).  Several C values are then solved one
                          after the other.  A solve starts only from the iterate of
                          a kernelized handle (the refinement sweep's master is one).
-                         -1: chosen per problem by the bytes an iteration reads: the
-                         kernelized loop when its K (8 n^2 bytes) is smaller than the
-                         stored Z (d n element bytes) and n fits it, else the
-                         streaming loop (solver = 0; the other solvers stream).  */
+                         -1: chosen per problem: the kernelized loop wherever n fits
+                         it, else the streaming loop (solver = 0; the other solvers
+                         stream).  */
   int32_t solver;     /* solver of eq-linsys.  0 (default): SMW2 through the n x n
                          Gram matrix (Sec. 3.3.2), for n << d.  1: the direct solver
                          of Sec. 3.3.1 for d << n: the (d+1) x (d+1) system through

@@ -464,11 +464,13 @@ extern "C" gdwd_status gdwd_create(const void* Z, int32_t zdt, int64_t d, int64_
   h->inexact = opt.solver == 2;
   plan_layout(h, d, n);
   if (h->opt.kernelized < 0) {
-    // auto: the loop that reads fewer bytes per iteration.  Both read G^-1
-    // twice (16 n^2); the streaming loop also reads Z once (d n element bytes),
-    // the kernelized one K once (8 n^2, double-float).
-    h->opt.kernelized = (8 * n < d * (int64_t)dtype_size(opt.store) &&
-                         n <= kern_max_n(h->grid, h->smem_optin - 16384)) ? 1 : 0;
+    // auto: the kernelized loop wherever K fits it.  It was the faster of the
+    // two on every measured workload (no pass over Z between the n-space
+    // phases), and with 16- or 8-bit storage the more robust: all its products
+    // go through the one Gram, while the streaming loop mixes the Gram's
+    // tensor-core rounding with direct products of the stored codes (on a
+    // served FP16 stream 27 of 419 requests then missed kkt 1e-6).
+    h->opt.kernelized = n <= kern_max_n(h->grid, h->smem_optin - 16384) ? 1 : 0;
   }
   if (!h->inexact && (n + h->grid - 1) / h->grid > kMaxRowsPerCta)
     return bail(fail(nullptr, GDWD_EUNSUPPORTED, "gdwd_create: n too large for the n x n factor path of this build"));
@@ -724,7 +726,7 @@ static IterArgs<CT> make_args(gdwd_handle* h, double C, double sigma0, int refre
   a.refresh = refresh;
   a.dots_every = dots_every_of(h);
   a.stall_first_barrier = env_long("GDWD_INJECT_STALL") > 0 ? 1 : 0;
-  a.fuse = 0;
+  a.fuse = 1;   // the fused first solve wherever its operands fit the ring (its products overlap barrier 8 and phase S)
   a.vrhs = h->vrhs;
   a.rhsB = h->rhsB;
   a.cq = (CT*)h->cq;

@@ -140,12 +140,15 @@ __host__ __device__ inline size_t slab_state_bytes(int nslab_rows, int ct_size) 
 // the end of phase N2,
 //     V1 = U_g,  V2 = (1 - tau) U_rho / sqrt(mu) - alpha,  V3 = xi - r,
 //     rhs1 = a1 V1 + V2 / sigma' + V3,  a1 = theta - tau (sigma / sigma') (1 - theta),
-// whose coefficients wait only for phase S (theta, sigma').  So
-// x-bar = G^{-1} rhs1 = a1 X1 + X2 / sigma' + X3 with X_k = G^{-1} V_k, and
-// p^T rhs1 likewise from p^T V_k.  The three products of this CTA's rows (and
-// of the row p^T) are taken during the pass over Z: the rows of G^{-1}, the row
-// p^T and V1..V3 (all double-float, ldP long) come through the ring as extra
-// chunks of W columns each, and every warp multiplies one or two of the rows.
+// whose coefficients wait only for phase S (theta, sigma').  When the sigma rule
+// keeps sigma' = sigma (every iteration but a few) this is
+//     rhs1 = a1 V1 + W,  W = V2 / sigma + V3,  a1 = theta - tau (1 - theta),
+// so x-bar = G^{-1} rhs1 = a1 X1 + XW with X1 = G^{-1} V1, XW = G^{-1} W, and
+// p^T rhs1 likewise.  The two products of this CTA's rows (and of the row p^T)
+// are formed while phase S runs: the rows of G^{-1}, the row p^T, V1 and W (all
+// double-float, ldP long) are copied into the idle ring during the wait at
+// barrier 8, and warps 4-7 multiply them while warps 0-3 run phase S.  If sigma
+// changes, phase R takes Step 1a the ordinary way (barrier, then one product).
 // ---------------------------------------------------------------------------
 constexpr int kFuseRowsPerWarp = 2;
 
@@ -153,7 +156,7 @@ struct FusedGemv {
   const float2* P;
   int ldP;
   const float2* pdf;
-  const float2* vrhs;     // [3][ldP]
+  const float2* vrhs;     // [2][ldP]: V1, W
   int64_t r0;
   int nrows;
   int W;                  // columns per extra chunk (even)
@@ -167,53 +170,44 @@ struct FusedGemv {
     const int j0 = e * W;
     const int w = min(W, ldP - j0);
     const uint32_t bytes = (uint32_t)w * (uint32_t)sizeof(float2);
-    mbar_expect_tx(bar, bytes * (uint32_t)(nrows + 4));
+    mbar_expect_tx(bar, bytes * (uint32_t)(nrows + 3));
     const size_t slice = (size_t)W * sizeof(float2);
     for (int t = 0; t < nrows; ++t) bulk_g2s(dst + t * slice, P + (size_t)(r0 + t) * ldP + j0, bytes, bar);
     bulk_g2s(dst + nrows * slice, pdf + j0, bytes, bar);
-    for (int k = 0; k < 3; ++k) bulk_g2s(dst + (nrows + 1 + k) * slice, vrhs + (size_t)k * ldP + j0, bytes, bar);
+    for (int k = 0; k < 2; ++k) bulk_g2s(dst + (nrows + 1 + k) * slice, vrhs + (size_t)k * ldP + j0, bytes, bar);
   }
-  __device__ void consume(int e, const uint8_t* buf) {
+  // the rows (and p^T, row nrows) on warps w0 .. w0 + nw - 1, one warp per row
+  __device__ void consume(int e, const uint8_t* buf, int w0 = 0, int nw = kWarps) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int w = min(W, ldP - e * W);
     const int npair = w / 2;
     const size_t slice = (size_t)W * sizeof(float2);
     const float4* V1 = reinterpret_cast<const float4*>(buf + (nrows + 1) * slice);
     const float4* V2 = reinterpret_cast<const float4*>(buf + (nrows + 2) * slice);
-    const float4* V3 = reinterpret_cast<const float4*>(buf + (nrows + 3) * slice);
-#pragma unroll
-    for (int rr = 0; rr < kFuseRowsPerWarp; ++rr) {
-      const int t = warp + rr * kWarps;
-      if (t > nrows) break;
+    for (int t = warp - w0; t <= nrows; t += nw) {
       const float4* Pr = reinterpret_cast<const float4*>(buf + t * slice);
-      df a1{0.f, 0.f}, a2{0.f, 0.f}, a3{0.f, 0.f}, b1{0.f, 0.f}, b2{0.f, 0.f}, b3{0.f, 0.f};
+      df a1{0.f, 0.f}, a2{0.f, 0.f}, b1{0.f, 0.f}, b2{0.f, 0.f};
       for (int j = lane; j < npair; j += 32) {
-        const float4 pv = Pr[j], x1 = V1[j], x2 = V2[j], x3 = V3[j];
+        const float4 pv = Pr[j], x1 = V1[j], x2 = V2[j];
         const df p0{pv.x, pv.y}, p1{pv.z, pv.w};
         df_fma(a1, p0, df{x1.x, x1.y});
         df_fma(a2, p0, df{x2.x, x2.y});
-        df_fma(a3, p0, df{x3.x, x3.y});
         df_fma(b1, p1, df{x1.z, x1.w});
         df_fma(b2, p1, df{x2.z, x2.w});
-        df_fma(b3, p1, df{x3.z, x3.w});
       }
       df_add(a1, b1);
       df_add(a2, b2);
-      df_add(a3, b3);
       a1 = df_warp_sum(a1);
       a2 = df_warp_sum(a2);
-      a3 = df_warp_sum(a3);
       if (lane == 0) {
-        double* acc = s_acc + t * 3;
-        const double v1 = df_to_double(a1), v2 = df_to_double(a2), v3 = df_to_double(a3);
+        double* acc = s_acc + t * 2;
+        const double v1 = df_to_double(a1), v2 = df_to_double(a2);
         if (e == 0) {
           acc[0] = v1;
           acc[1] = v2;
-          acc[2] = v3;
         } else {
           acc[0] += v1;
           acc[1] += v2;
-          acc[2] += v3;
         }
       }
     }
@@ -253,7 +247,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
   __shared__ float s_xh[kMaxRowsPerCta + 1], s_xl[kMaxRowsPerCta + 1];   // + the p^T rhs row
   __shared__ double s_ug[kMaxRowsPerCta];                                 // Z~^T u from the column dots
   __shared__ float2 s_rb[kMaxRowsPerCta];                                 // rhs2 of the CTA's rows
-  __shared__ double s_gx[kFuseRowsPerWarp * kWarps * 3];                  // fused products: rows, then p^T
+  __shared__ double s_gx[kFuseRowsPerWarp * kWarps * 2];                  // fused products: rows, then p^T
   // the iteration's double-float constants theta, -tau sigma_prev sqrt(mu)
   // (1 - theta), khat = tau mu sigma (1 - theta), 1 - theta and gs = 1 / (sigma
   // sqrt(mu)), formed once per CTA by five lanes during the wait at barrier 4
@@ -287,11 +281,14 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
   if (threadIdx.x == 0) s_abort = 0;
   ring_init(rg);
   // the fused first solve needs every row of the CTA (and p^T) on at most
-  // kFuseRowsPerWarp rows per warp, and a stage that holds slices of all of
-  // them and of the three right-hand sides
-  const int fuse_w = (int)((size_t)stage_bytes / ((size_t)(rpc + 4) * sizeof(float2))) & ~1;
-  const bool can_fuse = a.fuse && a.vrhs && rpc + 1 <= kFuseRowsPerWarp * kWarps && fuse_w >= 16;
-  FusedGemv fx{a.P, a.ldP, a.pdf, a.vrhs, r0, nrows, fuse_w, can_fuse ? (a.ldP + fuse_w - 1) / fuse_w : 0, s_gx};
+  // kFuseRowsPerWarp rows per warp, and the ring's stages to hold slices of all
+  // of them and of the three right-hand sides at once (their copies are issued
+  // when pass B ends and land during barrier 8 and phase S)
+  const int fuse_w = (int)((size_t)stage_bytes / ((size_t)(rpc + 3) * sizeof(float2))) & ~1;
+  const int fuse_nx = fuse_w >= 16 ? (a.ldP + fuse_w - 1) / fuse_w : 0;
+  const bool can_fuse =
+      a.fuse && a.vrhs && rpc + 1 <= kFuseRowsPerWarp * (kWarps / 2) && fuse_w >= 16 && fuse_nx <= stages;
+  FusedGemv fx{a.P, a.ldP, a.pdf, a.vrhs, r0, nrows, fuse_w, can_fuse ? fuse_nx : 0, s_gx};
 
   unsigned gen = 0;
   // per-phase timing by CTA 0, thread 0 (globaltimer, a few instructions per phase)
@@ -410,7 +407,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
 
   int it = it0;
   bool dots_prev = false;   // the last pass B took the column dots Z~^T u
-  bool fused = false;       // the last pass B made the three products of the fused first solve
+  bool fused = false;       // the last phase S formed the two products of the fused first solve
   double inv_sig = rcp_nr(sig);   // from the last phase S after the first iteration
   for (; it < a.max_iter; ++it) {
     const double gs_it = inv_sig * inv_sqmu;   // 1 / (sigma sqrt(mu)) of this iteration
@@ -418,6 +415,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
     // iteration; otherwise it makes the products of the next fused first solve
     const bool dots_now = ((it - it0) % a.dots_every) == a.dots_every - 1;
     const bool fuse_next = can_fuse && !dots_now;
+    bool use_fused = false;
     // ---------------- phase R (this CTA's rows): U_g = Z~^T g of the last iteration
     // from the pass-B column dots Z~^T u and (G - I) c; the deferred update
     // U_u = theta U_g, U_rho <- (1 - tau) U_rho - tau sigma' sqrt(mu) (1 - theta) U_g;
@@ -434,10 +432,11 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
         }
         __syncthreads();
       }
-      // fused: x-bar = a1 X1 + X2 / sigma + X3 from the last pass's products
-      // (formed only by the threads that use them)
-      const double a1 = fused ? theta - a.tau * (sig_prev * inv_sig) * (1.0 - theta) : 0.0;
-      if (fused) betabar = -(a1 * s_gx[nrows * 3] + s_gx[nrows * 3 + 1] * inv_sig + s_gx[nrows * 3 + 2]) * a.inv_s;
+      // fused (sigma kept): x-bar = a1 X1 + XW from the last phase S's products,
+      // a1 = theta - tau (1 - theta)
+      use_fused = fused && sig == sig_prev;
+      const double a1 = use_fused ? theta - a.tau * (1.0 - theta) : 0.0;
+      if (use_fused) betabar = -(a1 * s_gx[nrows * 2] + s_gx[nrows * 2 + 1]) * a.inv_s;
       // the per-row work on consecutive threads (few warp instructions of FP64)
       for (int t = threadIdx.x; t < nrows; t += kThreads) {
         const int64_t i = r0 + t;
@@ -452,8 +451,8 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
         }
         const double bi = uu + ur * gs_it;
         RS(RS_B, t) = bi;
-        if (fused) {
-          xb_reg = a1 * s_gx[t * 3] + s_gx[t * 3 + 1] * inv_sig + s_gx[t * 3 + 2];
+        if (use_fused) {
+          xb_reg = a1 * s_gx[t * 2] + s_gx[t * 2 + 1];
         } else {
           const double v = RS(RS_XI, t) - RS(RS_R, t) - RS(RS_AL, t) * inv_sig;
           const df r1 = df_from(bi + v);
@@ -461,7 +460,7 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
         }
       }
     }
-    if (!fused) {
+    if (!use_fused) {
       GDWD_BARRIER(2);
       // ---------------- phase N1 (first solve): x-bar = G^{-1} rhs1, beta-bar
       GDWD_MARK(14);
@@ -481,10 +480,10 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
     // ---------------- phase N1 (rows): Step 1b prox, rhs2.  The per-row FP64 work
     // has one row per lane so each FP64 instruction serves up to 32 rows
     {
-      if (fused) GDWD_MARK(2);
+      if (use_fused) GDWD_MARK(2);
       for (int t = threadIdx.x; t < nrows; t += kThreads) {
         const int64_t i = r0 + t;
-        const double xb = fused ? xb_reg : (double)s_xh[t] + (double)s_xl[t];
+        const double xb = use_fused ? xb_reg : (double)s_xh[t] + (double)s_xl[t];
         const double cbar = xb + betabar * RS(RS_P, t);
         const double ri = RS(RS_R, t);
         const double rn = prox_root(cbar + ri, RS(RS_OM, t) * inv_sig, a.q, qcase, ri);
@@ -565,13 +564,12 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
           const double kcn = rh2 - xv + beta * (yi - pi);
           RS(RS_KC, t) = kcn;
           if (fuse_next) {
-            // right-hand sides of the next fused first solve: U_g, (1 - tau) U_rho / sqrt(mu) - alpha, xi - r
+            // right-hand sides of the next fused first solve: V1 = U_g and
+            // W = ((1 - tau) U_rho / sqrt(mu) - alpha) / sigma + xi - r
             const df v1 = df_from(RS(RS_UU, t) - kcn);
-            const df v2 = df_from((1.0 - a.tau) * inv_sqmu * RS(RS_UR, t) - an);
-            const df v3 = df_from(xin - ri);
+            const df w = df_from(((1.0 - a.tau) * inv_sqmu * RS(RS_UR, t) - an) * inv_sig + (xin - ri));
             a.vrhs[i] = make_float2(v1.hi, v1.lo);
-            a.vrhs[a.ldP + i] = make_float2(v2.hi, v2.lo);
-            a.vrhs[2 * (size_t)a.ldP + i] = make_float2(v3.hi, v3.lo);
+            a.vrhs[a.ldP + i] = make_float2(w.hi, w.lo);
           }
           RS(RS_RES, t) = res;
         }
@@ -662,9 +660,6 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
         PassA2<T> pa{s_up, a.partial, TB, NB, Q};
         PassBA<T, IterEpi> pba{&pb, &pa};
         if (!stream_slabs<T>(L, rg, cta, grid, a.err, a.timeout_ns, &s_abort, pba)) return;
-      } else if (fuse_next) {
-        // the products of the next iteration's fused first solve ride on the ring
-        if (!stream_slabs<T>(L, rg, cta, grid, a.err, a.timeout_ns, &s_abort, pb, &fx)) return;
       } else {
         if (!stream_slabs<T>(L, rg, cta, grid, a.err, a.timeout_ns, &s_abort, pb)) return;
       }
@@ -677,13 +672,41 @@ __global__ void __launch_bounds__(kThreads, 1) iterate_kernel(IterArgs<typename 
       rows_sum_df<6>(vals, reinterpret_cast<float2*>(uni), TB,
                      reinterpret_cast<float2*>(a.scal) + (size_t)S_G2 * grid + cta, grid);
     }
-    GDWD_BARRIER(8);
+    // the operands of the next first solve's two G^-1 products (this CTA's rows
+    // of G^-1, p^T and the right-hand sides N2 wrote before barrier 6) go into the
+    // idle ring during the wait at barrier 8 and land while phase S runs
+    if (fused) rg.prefetched = fx.nx;   // drained by an early exit
+    GDWD_BARRIER_SIDE(8, [&]() {
+      if (fused && threadIdx.x == kThreads - 32)
+        for (int e = 0; e < fx.nx; ++e) fx.issue(e, rg.buf + (size_t)e * rg.stage_bytes, &rg.bars[e]);
+    });
 
     // ---------------- phase S: totals, KKT, sigma rule, stop test (same in every CTA)
     grid_totals_df(reinterpret_cast<const float2*>(a.scal), grid, s_tot);
     __syncthreads();
     GDWD_MARK(13);
-    s_phase(s_tot, sq, sig, gs_it, it, beta, status, false, a.ctrl, s_pd, s_etaf, s_ctl, s_ictl, theta, true);
+    if (fused) {
+      // warps 0-3 run phase S while warps 4-7 form the two products of the next
+      // iteration's x-bar (phase R) from the ring
+      if (warp < kWarps / 2) {
+        s_phase(s_tot, sq, sig, gs_it, it, beta, status, false, a.ctrl, s_pd, s_etaf, s_ctl, s_ictl, theta, true,
+                kThreads / 2);
+      } else {
+        for (int e = 0; e < fx.nx; ++e) {
+          if (!mbar_wait(&rg.bars[e], (rg.phase >> e) & 1u, a.err, a.timeout_ns)) s_abort = 1;
+          fx.consume(e, rg.buf + (size_t)e * rg.stage_bytes, kWarps / 2, kWarps / 2);
+        }
+      }
+      for (int e = 0; e < fx.nx; ++e) rg.phase ^= 1u << e;
+      __syncthreads();
+      if (*(volatile int*)&s_abort) {
+        ring_drain(rg, 0, fx.nx, true, a.err, a.timeout_ns);
+        return;
+      }
+      rg.prefetched = 0;
+    } else {
+      s_phase(s_tot, sq, sig, gs_it, it, beta, status, false, a.ctrl, s_pd, s_etaf, s_ctl, s_ictl, theta, true);
+    }
     GDWD_MARK(10);
     sig_prev = sig;
     theta = s_ctl[0];

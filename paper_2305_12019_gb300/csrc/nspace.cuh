@@ -392,7 +392,12 @@ __device__ __forceinline__ void s_report(Ctrl* ctrl, double beta, const double* 
 __device__ __forceinline__ void s_phase(const double* s_tot, const SPhaseArgs& q, double sig, double gs, int it,
                                         double beta, int status, bool report, Ctrl* ctrl, double* s_pd,
                                         float* s_etaf, double* s_ctl, int* s_ictl, double theta_prev = 1.0,
-                                        bool vsums = false) {
+                                        bool vsums = false, int nsync = kThreads) {
+  // nsync < kThreads: only the first nsync threads take part (named barrier 2)
+  auto sync = [nsync]() {
+    if (nsync >= kThreads) __syncthreads();
+    else asm volatile("bar.sync 2, %0;" ::"r"(nsync) : "memory");
+  };
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == 3 && lane < 7) {
     // 1 / sigma' for each value the sigma rule can give (sigma times 1, 1.1, 1.65,
@@ -444,7 +449,7 @@ __device__ __forceinline__ void s_phase(const double* s_tot, const SPhaseArgs& q
     s_etaf[8] = fmaxf((float)wmr, 0.f) * q.inv_den;                   // p3
     s_etaf[9] = fsqrt_approx((float)d3) * q.inv_den;                  // dd3
   }
-  __syncthreads();
+  sync();
   if (threadIdx.x == 0) {
     const float gap = s_etaf[0], p1 = s_etaf[1], dd1 = s_etaf[2], dd2 = s_etaf[3], c1 = s_etaf[4], c2 = s_etaf[5],
                 c3 = s_etaf[6], p2 = s_etaf[7], p3 = s_etaf[8], dd3 = s_etaf[9];
@@ -481,7 +486,7 @@ __device__ __forceinline__ void s_phase(const double* s_tot, const SPhaseArgs& q
     s_etaf[10] = kkt;
     if (report) s_report(ctrl, beta, s_pd, s_etaf);
   }
-  __syncthreads();
+  sync();
 }
 
 // x_i = sum_j P_ij rhs_j for one row, one warp, double-float (result in all lanes).

@@ -165,15 +165,14 @@ def test_kernelized_few_slabs_many_rows(gdwd_lib):
 
 
 def test_auto_iteration_choice(gdwd_lib):
-    """kernelized = -1 picks the loop that reads fewer bytes per iteration (K,
-    8 n^2, against the stored Z, d n element bytes) and reaches the same
-    solution as the loop it picked, forced."""
-    for d, n, store, expect in ((6000, 300, "f32", 1), (400, 900, "f32", 0), (1500, 500, "bf16", 0)):
+    """kernelized = -1 picks the kernelized loop (every n the n x n factor path
+    takes fits it) and reaches the same solution as that loop forced."""
+    for d, n, store, grid, expect in ((6000, 300, "f32", 0, 1), (400, 900, "bf16", 0, 1), (3000, 700, "f16", 8, 1)):
         inst = synth.gaussian(seed=d + n, d=d, n=n, shift=1.0, n_pos=n // 3, q=1.0, C=2.0)
-        with gdwd_lib.Solver(inst.Z, inst.y, 1.0, 2.0, store=store, tol=1e-6, kernelized=-1) as s:
+        with gdwd_lib.Solver(inst.Z, inst.y, 1.0, 2.0, store=store, tol=1e-6, kernelized=-1, grid=grid) as s:
             assert s.info()["kernelized"] == expect, (d, n, store)
             ra, wa, _ = s.solve()
-        with gdwd_lib.Solver(inst.Z, inst.y, 1.0, 2.0, store=store, tol=1e-6, kernelized=expect) as s:
+        with gdwd_lib.Solver(inst.Z, inst.y, 1.0, 2.0, store=store, tol=1e-6, kernelized=expect, grid=grid) as s:
             rf, wf, _ = s.solve()
         assert ra[0]["status"] == 0 and ra[0]["iters"] == rf[0]["iters"]
         assert np.allclose(wa, wf, rtol=1e-12, atol=1e-14 * np.abs(wf).max())

@@ -184,30 +184,45 @@ struct FusedGemv {
     const size_t slice = (size_t)W * sizeof(float2);
     const float4* V1 = reinterpret_cast<const float4*>(buf + (nrows + 1) * slice);
     const float4* V2 = reinterpret_cast<const float4*>(buf + (nrows + 2) * slice);
-    for (int t = warp - w0; t <= nrows; t += nw) {
-      const float4* Pr = reinterpret_cast<const float4*>(buf + t * slice);
+    // two rows per pass: each load of V1 and W serves both
+    for (int t = warp - w0; t <= nrows; t += 2 * nw) {
+      const int tb = t + nw;
+      const bool two = tb <= nrows;
+      const float4* Pa = reinterpret_cast<const float4*>(buf + t * slice);
+      const float4* Pb = reinterpret_cast<const float4*>(buf + (two ? tb : t) * slice);
       df a1{0.f, 0.f}, a2{0.f, 0.f}, b1{0.f, 0.f}, b2{0.f, 0.f};
+      df c1{0.f, 0.f}, c2{0.f, 0.f}, d1{0.f, 0.f}, d2{0.f, 0.f};
       for (int j = lane; j < npair; j += 32) {
-        const float4 pv = Pr[j], x1 = V1[j], x2 = V2[j];
-        const df p0{pv.x, pv.y}, p1{pv.z, pv.w};
-        df_fma(a1, p0, df{x1.x, x1.y});
-        df_fma(a2, p0, df{x2.x, x2.y});
-        df_fma(b1, p1, df{x1.z, x1.w});
-        df_fma(b2, p1, df{x2.z, x2.w});
+        const float4 pa = Pa[j], pb = Pb[j], x1 = V1[j], x2 = V2[j];
+        const df x1a{x1.x, x1.y}, x1b{x1.z, x1.w}, x2a{x2.x, x2.y}, x2b{x2.z, x2.w};
+        df_fma(a1, df{pa.x, pa.y}, x1a);
+        df_fma(a2, df{pa.x, pa.y}, x2a);
+        df_fma(b1, df{pa.z, pa.w}, x1b);
+        df_fma(b2, df{pa.z, pa.w}, x2b);
+        df_fma(c1, df{pb.x, pb.y}, x1a);
+        df_fma(c2, df{pb.x, pb.y}, x2a);
+        df_fma(d1, df{pb.z, pb.w}, x1b);
+        df_fma(d2, df{pb.z, pb.w}, x2b);
       }
       df_add(a1, b1);
       df_add(a2, b2);
+      df_add(c1, d1);
+      df_add(c2, d2);
       a1 = df_warp_sum(a1);
       a2 = df_warp_sum(a2);
+      c1 = df_warp_sum(c1);
+      c2 = df_warp_sum(c2);
       if (lane == 0) {
-        double* acc = s_acc + t * 2;
-        const double v1 = df_to_double(a1), v2 = df_to_double(a2);
-        if (e == 0) {
-          acc[0] = v1;
-          acc[1] = v2;
-        } else {
-          acc[0] += v1;
-          acc[1] += v2;
+        const double v[4] = {df_to_double(a1), df_to_double(a2), df_to_double(c1), df_to_double(c2)};
+        for (int r = 0; r < (two ? 2 : 1); ++r) {
+          double* acc = s_acc + (r ? tb : t) * 2;
+          if (e == 0) {
+            acc[0] = v[2 * r];
+            acc[1] = v[2 * r + 1];
+          } else {
+            acc[0] += v[2 * r];
+            acc[1] += v[2 * r + 1];
+          }
         }
       }
     }

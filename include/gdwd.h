@@ -334,9 +334,9 @@ gdwd_status gdwd_get_stored(const gdwd_handle* h, void* Zq, double* colscale);
  * device memory owned by the caller; work is queued on `stream` (NULL = default
  * stream) and the call returns without waiting for it.
  *
- * For callers that cannot allocate device memory when they need the product
- * (inside a captured region, under an allocator that must not be re-entered, or
- * in an embedder that owns all device memory): the scratch for the split-K
+ * For callers that cannot allocate device memory at the point where they need
+ * the product (code running under an allocator that must not be re-entered, or
+ * an embedder that owns all device memory and hands out none): the scratch for the split-K
  * partial products lives in a fixed 32 MiB array inside the library, which
  * every GPU that loads the library keeps until the process exits.  Limits and
  * rules:

@@ -2,9 +2,9 @@
 // matrix, computed without allocating any memory.
 //
 // Some callers cannot allocate device memory at the point where they need the
-// Gram matrix: code running inside a captured region where allocation is not
-// allowed, allocators that must not be re-entered, or embedders that own all
-// device memory and only hand out input and output buffers.  For them this
+// Gram matrix: code running under an allocator that must not be re-entered, or
+// embedders that own all device memory and only hand out input and output
+// buffers.  For them this
 // entry point keeps its scratch -- the split-K partial products -- in a
 // file-scope __device__ array of fixed size that every GPU which loads the
 // library holds until the process exits.

@@ -9,6 +9,9 @@ against the oracle (no CUDA code is imported).
 * The kernelized iteration: u, rho, g carried as coefficient vectors in the columns
   of Z~, every d-space norm a quadratic form in K = Z~^T Z~; its iterates equal
   those of Algorithm 1 as the oracle runs it.
+* The fused first solve: Step 1a's x-bar from products formed before sigma' is
+  known (three vectors in general, two when sigma is kept).
+* The residual sums taken about the last theta (eta_P2, eta_D3, ||w||).
 """
 import math
 
@@ -67,7 +70,7 @@ def test_kernelized_iterates_equal_algorithm_1():
     d, n, q, C, mu, tau = 30, 14, 1.0, 2.0, 1.0, 1.618
     y = np.where(np.arange(n) < 6, 1.0, -1.0)
     Z = rng.standard_normal((d, n)) * y
-    ref = O.solve(Z, y, q, C, mu=mu, tau=tau, tol=1e-300, max_iter=20, record=True)
+    ref = O.solve(Z, y, q, C, mu=mu, tau=tau, tol=1e-300, max_iter=60, record=True)
     sigmas = [h[0] for h in ref["history"]]
     Zt, zs = O.scale_data(Z)
     K = Zt.T @ Zt
@@ -110,13 +113,16 @@ def test_fused_first_solve_equals_direct_solve():
         rhs1 = a1 U_g + ((1 - tau) U_rho / sqrt(mu) - alpha) / sigma' + (xi - r),
         a1 = theta - tau (sigma / sigma') (1 - theta),
     with U_g = Z~^T g, U_rho = Z~^T rho of iteration k and sigma' the next sigma.
-    Twenty iterations on the oracle's sigma path: the fused x-bar equals the direct
+    When the sigma rule keeps sigma' = sigma this is a1 U_g + W with
+    W = ((1 - tau) U_rho / sqrt(mu) - alpha) / sigma + (xi - r) and
+    a1 = theta - tau (1 - theta): two products, the form the kernel takes.
+    Sixty iterations on the oracle's sigma path: both fused x-bars equal the direct
     one, and the iterates equal the oracle's."""
     rng = np.random.default_rng(4)
     d, n, q, C, mu, tau = 30, 14, 1.0, 2.0, 0.7, 1.618
     y = np.where(np.arange(n) < 6, 1.0, -1.0)
     Z = rng.standard_normal((d, n)) * y
-    ref = O.solve(Z, y, q, C, mu=mu, tau=tau, tol=1e-300, max_iter=20, record=True)
+    ref = O.solve(Z, y, q, C, mu=mu, tau=tau, tol=1e-300, max_iter=60, record=True)
     sigmas = [h[0] for h in ref["history"]]
     Zt, zs = O.scale_data(Z)
     G = np.eye(n) + Zt.T @ Zt / mu
@@ -126,17 +132,22 @@ def test_fused_first_solve_equals_direct_solve():
     sq = math.sqrt(mu)
     r, xi, alpha = np.ones(n), np.ones(n), np.zeros(n)
     u, rho = np.zeros(d), np.zeros(d)
-    prev = None   # (X1, X2, X3, theta, sigma) from the last pass
+    prev = None   # (X1, X2, X3, XW, theta, sigma) from the last pass
+    kept = 0
     for sigma in sigmas:
         gp = u + rho / (sigma * sq)
         b = Zt.T @ gp
         rhs1 = b + xi - r - alpha / sigma
         xb = Gi @ rhs1
         if prev is not None:
-            X1, X2, X3, th, sp = prev
+            X1, X2, X3, XW, th, sp = prev
             a1 = th - tau * (sp / sigma) * (1.0 - th)
             xf = a1 * X1 + X2 / sigma + X3
             assert np.allclose(xf, xb, rtol=1e-10, atol=1e-12 * np.abs(xb).max())
+            if sigma == sp:
+                kept += 1
+                x2 = (th - tau * (1.0 - th)) * X1 + XW
+                assert np.allclose(x2, xb, rtol=1e-10, atol=1e-12 * np.abs(xb).max())
         betab = -(y @ xb) / s
         r = O.prox_r(xb + betab * p + r, sigma, q, r0=r)
         v = xi - r - alpha / sigma
@@ -154,9 +165,55 @@ def test_fused_first_solve_equals_direct_solve():
         V1 = Zt.T @ g
         V2 = (1.0 - tau) * (Zt.T @ rho) / sq - alpha
         V3 = xi - r
-        prev = (Gi @ V1, Gi @ V2, Gi @ V3, theta, sigma)
+        prev = (Gi @ V1, Gi @ V2, Gi @ V3, Gi @ (V2 / sigma + V3), theta, sigma)
         rho = rho - tau * sigma * sq * (w - theta * g)
         u = theta * g
+    assert kept >= 10, kept
     assert np.allclose(r, ref["r"], rtol=1e-9, atol=1e-12)
     assert np.allclose(alpha, ref["alpha"], rtol=1e-9, atol=1e-12)
     assert np.allclose(u, ref["u_scaled"], rtol=1e-9, atol=1e-12)
+
+
+def test_residual_sums_about_the_last_theta():
+    """eta_P2 and eta_D3 need ||(1 - theta) g + gs rho||^2 and ||a - kap g||^2
+    (kap = tau mu sigma (1 - theta)), with theta known only after the pass that
+    forms g.  The kernels sum y = (1 - theta_p) g + gs rho and v = a - khat g
+    (khat = tau mu sigma (1 - theta_p)) about the last theta_p and expand in
+    eps = theta_p - theta:
+        ||w - u+||^2 = ||y||^2 + 2 eps <y, g> + eps^2 ||g||^2,
+        ||a - kap g||^2 = ||v||^2 - 2 dlt <v, g> + dlt^2 ||g||^2, dlt = tau mu sigma eps,
+        ||w||^2 = ||y||^2 + 2 theta_p <y, g> + theta_p^2 ||g||^2.
+    Near convergence (small residuals, theta settled) these keep their relative
+    accuracy, while the expansions in ||g||^2, <g, rho>, ||rho||^2 (or ||a||^2,
+    <a, g>) lose it to cancellation."""
+    rng = np.random.default_rng(11)
+    d, tau, mu, sigma = 4000, 1.618, 0.9, 37.0
+    gs = 1.0 / (sigma * math.sqrt(mu))
+    g = rng.standard_normal(d) * 5.0
+    for theta_p, theta in ((0.31, 0.31), (0.31, 0.3100004), (1.0, 1.0), (0.8, 0.7)):
+        kap = tau * mu * sigma * (1.0 - theta)
+        # rho and a chosen so that both residuals are ~1e-7 of their terms
+        rho = -(1.0 - theta) * g / gs + 1e-7 * rng.standard_normal(d)
+        a = kap * g + 1e-7 * rng.standard_normal(d)
+        true_p2 = np.sum(((1.0 - theta) * g + gs * rho) ** 2)
+        true_d3 = np.sum((a - kap * g) ** 2)
+        # the kernels' sums and expansion
+        y = (1.0 - theta_p) * g + gs * rho
+        v = a - tau * mu * sigma * (1.0 - theta_p) * g
+        eps = theta_p - theta
+        dlt = tau * mu * sigma * eps
+        p2 = y @ y + 2.0 * eps * (y @ g) + eps * eps * (g @ g)
+        d3 = v @ v - 2.0 * dlt * (v @ g) + dlt * dlt * (g @ g)
+        w = g + gs * rho
+        w2 = y @ y + 2.0 * theta_p * (y @ g) + theta_p ** 2 * (g @ g)
+        assert abs(w2 - w @ w) <= 1e-9 * (w @ w)
+        if eps == 0.0:
+            # theta settled: the sums are the residuals themselves
+            assert abs(p2 - true_p2) <= 1e-9 * true_p2
+            assert abs(d3 - true_d3) <= 1e-9 * true_d3
+            # while the old expansions about theta = 1 lose them to cancellation
+            old_d3 = kap * kap * (g @ g) - 2.0 * kap * (a @ g) + a @ a
+            assert abs(old_d3 - true_d3) > 1e-3 * true_d3 or kap == 0.0
+        else:
+            scale = (1.0 - theta) ** 2 * (g @ g)
+            assert abs(p2 - true_p2) <= 1e-12 * scale + 1e-9 * true_p2

@@ -26,7 +26,7 @@ constexpr int64_t kMaxN = 2048;                   // kMaxN * kMaxN == kScratchDo
 constexpr int kTile = 64;
 constexpr int kChunk = 16;
 
-__device__ __align__(256) double g_gram_scratch[kScratchDoubles];
+static __device__ __align__(256) double g_gram_scratch[kScratchDoubles];
 
 // Loads rows [r0, r0+16) of columns [c0, c0+64) of a column-major matrix into sm[16][64].
 __device__ __forceinline__ void load_cm(const float* Z, int64_t d, int64_t n, int64_t ldz, int64_t r0, int64_t r1,

@@ -80,7 +80,8 @@ def test_invalid_arguments_rejected(lib):
     o.store = 9
     assert _create(lib, Z, y, opts=o)[0] == 1
     # option values and combinations checked before any device work
-    for field, val in (("kernelized", 2), ("solver", 3), ("gram_path", 2), ("stop_rule", 3), ("dots_every", -1)):
+    for field, val in (("kernelized", 2), ("kernelized", -2), ("solver", 3), ("gram_path", 2), ("stop_rule", 3),
+                       ("dots_every", -1)):
         o = gdwd.default_options()
         setattr(o, field, val)
         assert _create(lib, Z, y, opts=o)[0] == 1, field
